@@ -1,0 +1,733 @@
+/*
+ * peridem_oracle.c -- plain, slow, FP64 CPU oracle of the PeriDEM force loop.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code with
+ * the GPU library: it has its own mesher, its own bond builder (the exact
+ * segment-in-domain definition of the non-convex horizon, not the paper's
+ * extended-boundary construction), its own contact search and its own time
+ * loop.  Every function follows the paper's notation and cites the passage it
+ * implements.
+ *
+ * Paper: Bhattacharya & Lipton, "Simulating grain shape effects and damage in
+ * granular media using PeriDEM" (arXiv 2108.07212).
+ *
+ * Readings of the paper taken here (each is also listed in the design notes):
+ *   - horizon membership is the strict |xi| < eps of Algorithm 1, evaluated on
+ *     the integer lattice offsets (di^2 + dj^2 < (eps/h)^2);
+ *   - each pair law (bond, contact, self-contact, wall) is evaluated as the
+ *     force on node x; rho V_x u'' = sum of those forces + rho V_x b;
+ *   - normal damping is the Kelvin-Voigt form -beta_d V_x V_y (v(x,y).e) e with
+ *     e pointing from x to y (dissipative sign, Sec. 4.3 energy identity);
+ *   - friction opposes the tangential relative velocity v_perp(x,y); slip when
+ *     |v_perp| > v_thr, otherwise the sticking force -(rho V_x / dt) v_perp;
+ *   - damping and friction use the velocity at the start of the step;
+ *   - a bond whose |s| exceeds s0 breaks at that evaluation and carries no force
+ *     from then on; self-contact acts between same-grain nodes with no intact
+ *     bond; self-contact damping/friction use the contact beta_d and |F_r^self|
+ *     and act only while the self repulsion is active;
+ *   - wall contact uses the literal R_c - |c_l - p| of Eq. (wall-repulsive); a
+ *     node past a wall is treated as touching it (d clamped to 0, counted);
+ *     only adjacent (perpendicular) walls form corners.
+ *
+ * parity unpinned: multi-grain trajectories (only the GPU comparison checks
+ * them; the paper gives no trajectory data).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* geometry helpers                                                          */
+
+static double cross2(double ax, double ay, double bx, double by) { return ax * by - ay * bx; }
+
+/* distance from point (px,py) to the closed segment (ax,ay)-(bx,by) */
+static double point_segment_distance(double px, double py, double ax, double ay, double bx, double by)
+{
+    double ex = bx - ax, ey = by - ay;
+    double len2 = ex * ex + ey * ey;
+    double t = 0.0;
+    if (len2 > 0.0) {
+        t = ((px - ax) * ex + (py - ay) * ey) / len2;
+        if (t < 0.0) t = 0.0;
+        if (t > 1.0) t = 1.0;
+    }
+    double qx = ax + t * ex - px, qy = ay + t * ey - py;
+    return sqrt(qx * qx + qy * qy);
+}
+
+/* even-odd point-in-region test over all loops (outer + holes) */
+static int point_in_loops(double px, double py, const double *xy, const int *loop_start, int n_loops, double scale)
+{
+    int inside = 0;
+    for (int l = 0; l < n_loops; ++l) {
+        int a = loop_start[l], n = loop_start[l + 1] - a;
+        for (int k = 0; k < n; ++k) {
+            int k1 = (k + 1) % n;
+            double x0 = scale * xy[2 * (a + k)], y0 = scale * xy[2 * (a + k) + 1];
+            double x1 = scale * xy[2 * (a + k1)], y1 = scale * xy[2 * (a + k1) + 1];
+            if ((y0 > py) != (y1 > py)) {
+                double xc = x0 + (py - y0) * (x1 - x0) / (y1 - y0);
+                if (px < xc) inside = !inside;
+            }
+        }
+    }
+    return inside;
+}
+
+static double distance_to_loops(double px, double py, const double *xy, const int *loop_start, int n_loops, double scale)
+{
+    double best = 1e300;
+    for (int l = 0; l < n_loops; ++l) {
+        int a = loop_start[l], n = loop_start[l + 1] - a;
+        for (int k = 0; k < n; ++k) {
+            int k1 = (k + 1) % n;
+            double d = point_segment_distance(px, py, scale * xy[2 * (a + k)], scale * xy[2 * (a + k) + 1],
+                                              scale * xy[2 * (a + k1)], scale * xy[2 * (a + k1) + 1]);
+            if (d < best) best = d;
+        }
+    }
+    return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mesh: uniform lattice of spacing h (Sec. 5 intro: nodes inside the grain,  */
+/* V = h^2 per node in 2D).  Lattice points (i h, j h) of the grain frame that */
+/* lie strictly inside the grain (even-odd over all loops) and at least        */
+/* clear*h away from its boundary are kept, ordered by j then i, then rotated  */
+/* by theta and translated to (cx, cy).                                       */
+/* Returns the node count; writes at most max_nodes nodes.                    */
+int or_mesh_grain(const double *xy, const int *loop_start, int n_loops, double R, double h,
+                  double cx, double cy, double theta, double clear, int max_nodes,
+                  double *X, int *lat)
+{
+    int m = (int)ceil(R / h) + 1;
+    double c = cos(theta), s = sin(theta);
+    int n = 0;
+    for (int j = -m; j <= m; ++j) {
+        for (int i = -m; i <= m; ++i) {
+            double lx = (double)i * h, ly = (double)j * h;
+            if (!point_in_loops(lx, ly, xy, loop_start, n_loops, R)) continue;
+            if (distance_to_loops(lx, ly, xy, loop_start, n_loops, R) < clear * h) continue;
+            if (n < max_nodes) {
+                X[2 * n] = cx + (c * lx - s * ly);
+                X[2 * n + 1] = cy + (s * lx + c * ly);
+                lat[2 * n] = i;
+                lat[2 * n + 1] = j;
+            }
+            ++n;
+        }
+    }
+    return n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Non-convex horizon, Sec. 4 "Peridynamic bonds in nonconvex domains":      */
+/* y is removed from the horizon of x when the straight segment x->y leaves   */
+/* the (closed) grain D.  This is the definition of the set C_x itself,       */
+/* evaluated directly: the segment is cut at every crossing or touching with  */
+/* a boundary edge and the midpoint of every piece must lie in closed D       */
+/* (inside, or within tol of the boundary).                                   */
+
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+int or_segment_in_domain(double ax, double ay, double bx, double by, const double *xy,
+                         const int *loop_start, int n_loops, double scale, double tol)
+{
+    int n_edges = loop_start[n_loops];
+    double *ts = (double *)malloc(sizeof(double) * (size_t)(2 * n_edges + 2));
+    int nt = 0;
+    ts[nt++] = 0.0;
+    ts[nt++] = 1.0;
+    double rx = bx - ax, ry = by - ay;
+    double rlen2 = rx * rx + ry * ry;
+    for (int l = 0; l < n_loops; ++l) {
+        int a = loop_start[l], n = loop_start[l + 1] - a;
+        for (int k = 0; k < n; ++k) {
+            int k1 = (k + 1) % n;
+            double cxv = scale * xy[2 * (a + k)], cyv = scale * xy[2 * (a + k) + 1];
+            double dxv = scale * xy[2 * (a + k1)], dyv = scale * xy[2 * (a + k1) + 1];
+            double sx = dxv - cxv, sy = dyv - cyv;
+            double den = cross2(rx, ry, sx, sy);
+            double qx = cxv - ax, qy = cyv - ay;
+            if (fabs(den) > 1e-14 * sqrt(rlen2 * (sx * sx + sy * sy))) {
+                double t = cross2(qx, qy, sx, sy) / den;
+                double u = cross2(qx, qy, rx, ry) / den;
+                if (t >= 0.0 && t <= 1.0 && u >= -1e-12 && u <= 1.0 + 1e-12) ts[nt++] = t;
+            } else if (fabs(cross2(qx, qy, rx, ry)) <= 1e-14 * rlen2) {
+                /* collinear: the edge end points split the segment */
+                double t0 = (qx * rx + qy * ry) / rlen2;
+                double t1 = ((dxv - ax) * rx + (dyv - ay) * ry) / rlen2;
+                if (t0 > 0.0 && t0 < 1.0) ts[nt++] = t0;
+                if (t1 > 0.0 && t1 < 1.0) ts[nt++] = t1;
+            }
+        }
+    }
+    qsort(ts, (size_t)nt, sizeof(double), cmp_double);
+    int ok = 1;
+    for (int k = 0; k + 1 < nt && ok; ++k) {
+        if (ts[k + 1] - ts[k] <= 1e-15) continue;
+        double tm = 0.5 * (ts[k] + ts[k + 1]);
+        double mx = ax + tm * rx, my = ay + tm * ry;
+        if (!point_in_loops(mx, my, xy, loop_start, n_loops, scale) &&
+            distance_to_loops(mx, my, xy, loop_start, n_loops, scale) > tol)
+            ok = 0;
+    }
+    free(ts);
+    return ok;
+}
+
+/* Reference neighbour list S^ref(x) of Algorithm 1 for one grain, in local   */
+/* node indices: every node y != x of the same grain whose lattice offset     */
+/* satisfies di^2 + dj^2 < (eps/h)^2 and whose segment stays inside the grain. */
+/* Columns are ascending.  row_ptr has n+1 entries.  Returns the bond count    */
+/* (writes at most max_bonds columns).                                        */
+int or_grain_bonds(const double *xy, const int *loop_start, int n_loops, double R, double h,
+                   double horizon_ratio, double tol_frac, int n, const int *lat,
+                   int *row_ptr, int *col, int max_bonds)
+{
+    if (n <= 0) {
+        row_ptr[0] = 0;
+        return 0;
+    }
+    int imin = 1 << 30, imax = -(1 << 30), jmin = 1 << 30, jmax = -(1 << 30);
+    for (int k = 0; k < n; ++k) {
+        if (lat[2 * k] < imin) imin = lat[2 * k];
+        if (lat[2 * k] > imax) imax = lat[2 * k];
+        if (lat[2 * k + 1] < jmin) jmin = lat[2 * k + 1];
+        if (lat[2 * k + 1] > jmax) jmax = lat[2 * k + 1];
+    }
+    int W = imax - imin + 1, H = jmax - jmin + 1;
+    int *map = (int *)malloc(sizeof(int) * (size_t)W * (size_t)H);
+    for (int k = 0; k < W * H; ++k) map[k] = -1;
+    for (int k = 0; k < n; ++k) map[(lat[2 * k + 1] - jmin) * W + (lat[2 * k] - imin)] = k;
+    int r = (int)ceil(horizon_ratio);
+    double r2 = horizon_ratio * horizon_ratio;
+    int nb = 0;
+    int cand[1024];
+    for (int x = 0; x < n; ++x) {
+        row_ptr[x] = nb;
+        int nc = 0;
+        int ix = lat[2 * x], jx = lat[2 * x + 1];
+        for (int dj = -r; dj <= r; ++dj) {
+            for (int di = -r; di <= r; ++di) {
+                if (di == 0 && dj == 0) continue;
+                if ((double)(di * di + dj * dj) >= r2) continue;
+                int iy = ix + di, jy = jx + dj;
+                if (iy < imin || iy > imax || jy < jmin || jy > jmax) continue;
+                int y = map[(jy - jmin) * W + (iy - imin)];
+                if (y < 0) continue;
+                if (!or_segment_in_domain((double)ix * h, (double)jx * h, (double)iy * h, (double)jy * h,
+                                          xy, loop_start, n_loops, R, tol_frac * h))
+                    continue;
+                if (nc < 1024) cand[nc++] = y;
+            }
+        }
+        /* ascending column order (insertion sort) */
+        for (int a = 1; a < nc; ++a) {
+            int v = cand[a], b = a - 1;
+            while (b >= 0 && cand[b] > v) { cand[b + 1] = cand[b]; --b; }
+            cand[b + 1] = v;
+        }
+        for (int a = 0; a < nc; ++a) {
+            if (nb < max_bonds) col[nb] = cand[a];
+            ++nb;
+        }
+    }
+    row_ptr[n] = nb;
+    free(map);
+    return nb;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Material constants, Table 1 (tab:2d-peri).                                 */
+/* micromodulus 0: constant w = 1,  c_w = 6E/(pi eps^3 (1-nu)),               */
+/*                 s0 = sqrt(4 pi Gc / (9 E eps))                             */
+/* micromodulus 1: conic w = 1-|xi|/eps, c_w = 24E/(pi eps^3 (1-nu)),          */
+/*                 s0 = sqrt(5 pi Gc / (9 E eps))                             */
+void or_bond_constants(double E, double nu, double Gc, double eps, int micromodulus, double *cw, double *s0)
+{
+    if (micromodulus == 0) {
+        *cw = 6.0 * E / (OR_PI * eps * eps * eps * (1.0 - nu));
+        *s0 = sqrt(4.0 * OR_PI * Gc / (9.0 * E * eps));
+    } else {
+        *cw = 24.0 * E / (OR_PI * eps * eps * eps * (1.0 - nu));
+        *s0 = sqrt(5.0 * OR_PI * Gc / (9.0 * E * eps));
+    }
+}
+
+/* Normal contact stiffness K_n = 18 k / (pi eps^5), Sec. 4.1. */
+double or_contact_stiffness(double k_bulk, double eps)
+{
+    return 18.0 * k_bulk / (OR_PI * eps * eps * eps * eps * eps);
+}
+
+/* Single-wall contact region S_l, Sec. 4.5: area of the circular segment of   */
+/* B_{R_c}(p) beyond a line at distance d, and distance from p to its centroid. */
+void or_wall_segment(double d, double Rc, double *area, double *cdist)
+{
+    double q = Rc * Rc - d * d;
+    double A = 0.5 * OR_PI * Rc * Rc - Rc * Rc * asin(d / Rc) - sqrt(q) * d;
+    *area = A;
+    *cdist = (2.0 / 3.0) * (q * sqrt(q)) / A;
+}
+
+/* Corner region S_li cap S_lj, Sec. 4.5 (polar-coordinate integrals): area   */
+/* and first moments I_x (along the direction towards l_i, distance d_i) and  */
+/* I_y (towards l_j, distance d_j).                                           */
+void or_corner_region(double di, double dj, double Rc, double *area, double *Ix, double *Iy)
+{
+    double R2 = Rc * Rc;
+    double qi = R2 - di * di, qj = R2 - dj * dj;
+    *area = -0.5 * R2 * asin(di / Rc) + 0.5 * R2 * asin(sqrt(qj) / Rc) + di * dj
+            - 0.5 * sqrt(qi) * di - 0.5 * sqrt(qj) * dj;
+    *Ix = dj * dj * dj / 6.0 - 0.5 * qi * dj + (qi * sqrt(qi)) / 3.0;
+    *Iy = -0.5 * R2 * di + di * di * di / 6.0 + 0.5 * di * dj * dj + (qj * sqrt(qj)) / 3.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The time loop.                                                             */
+
+/* parameter vector layout */
+enum {
+    P_RHO = 0, P_KN, P_RC, P_RD, P_MU, P_GX, P_GY, P_DT,
+    P_WX0, P_WX1, P_WY0, P_WY1,          /* wall positions at t = 0: x_lo, x_hi, y_lo, y_hi */
+    P_VX0, P_VX1, P_VY0, P_VY1,          /* wall normal velocities                           */
+    P_MICRO, P_SEARCH, P_NPARAM
+};
+
+/* status word layout */
+enum { ST_PENETRATION = 0, ST_COINCIDENT, ST_NONFINITE, ST_NSTATUS };
+
+typedef struct {
+    const double *prm;
+    int N;
+    const double *X;
+    const double *u, *v;
+    const double *V;
+    const int *grain;
+    const double *g_cw, *g_s0, *g_eps;
+    const int *row_ptr, *col;
+    unsigned char *broken;
+    double t;            /* time at which the walls are evaluated */
+    double *p;           /* scratch: current positions */
+    int *cand;           /* scratch: contact candidates */
+    int max_cand;
+    /* contact grid */
+    int use_grid;
+    double gx0, gy0, cell;
+    int ncx, ncy;
+    int *head, *next;
+    int *status;
+} or_sys;
+
+/* cell index along one axis, clamped to the grid (non-finite -> 0) */
+static int grid_index(double x, double x0, double cell, int n)
+{
+    double f = floor((x - x0) / cell);
+    if (!(f >= 0.0)) return 0;
+    if (f > (double)(n - 1)) return n - 1;
+    return (int)f;
+}
+
+/* S^nbr of Algorithm 1: indices y != x with |p(y) - p(x)| < R_c, ascending.  */
+static int contact_candidates(const or_sys *S, int x, int *out)
+{
+    double Rc = S->prm[P_RC];
+    double px = S->p[2 * x], py = S->p[2 * x + 1];
+    int n = 0;
+    if (!(Rc > 0.0)) return 0;
+    if (!S->use_grid) {
+        for (int y = 0; y < S->N; ++y) {
+            if (y == x) continue;
+            double dx = S->p[2 * y] - px, dy = S->p[2 * y + 1] - py;
+            double d = sqrt(dx * dx + dy * dy);
+            if (d < Rc && n < S->max_cand) out[n++] = y;
+        }
+        return n;
+    }
+    int ci = grid_index(px, S->gx0, S->cell, S->ncx), cj = grid_index(py, S->gy0, S->cell, S->ncy);
+    for (int dj = -1; dj <= 1; ++dj) {
+        for (int di = -1; di <= 1; ++di) {
+            int a = ci + di, b = cj + dj;
+            if (a < 0 || b < 0 || a >= S->ncx || b >= S->ncy) continue;
+            for (int y = S->head[b * S->ncx + a]; y >= 0; y = S->next[y]) {
+                if (y == x) continue;
+                double dx = S->p[2 * y] - px, dy = S->p[2 * y + 1] - py;
+                double d = sqrt(dx * dx + dy * dy);
+                if (d < Rc && n < S->max_cand) out[n++] = y;
+            }
+        }
+    }
+    for (int a = 1; a < n; ++a) {
+        int v = out[a], b = a - 1;
+        while (b >= 0 && out[b] > v) { out[b + 1] = out[b]; --b; }
+        out[b + 1] = v;
+    }
+    return n;
+}
+
+static void build_grid(or_sys *S)
+{
+    double Rc = S->prm[P_RC];
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    for (int k = 0; k < S->N; ++k) {
+        double x = S->p[2 * k], y = S->p[2 * k + 1];
+        if (!isfinite(x) || !isfinite(y)) continue;
+        if (x < xmin) xmin = x;
+        if (x > xmax) xmax = x;
+        if (y < ymin) ymin = y;
+        if (y > ymax) ymax = y;
+    }
+    S->cell = Rc;
+    S->gx0 = xmin - Rc;
+    S->gy0 = ymin - Rc;
+    if (!(xmax >= xmin)) { xmin = xmax = 0.0; ymin = ymax = 0.0; S->gx0 = -Rc; S->gy0 = -Rc; }
+    S->ncx = (int)((xmax - S->gx0) / Rc) + 3;
+    S->ncy = (int)((ymax - S->gy0) / Rc) + 3;
+    size_t nc = (size_t)S->ncx * (size_t)S->ncy;
+    S->head = (int *)malloc(sizeof(int) * nc);
+    S->next = (int *)malloc(sizeof(int) * (size_t)(S->N > 0 ? S->N : 1));
+    for (size_t k = 0; k < nc; ++k) S->head[k] = -1;
+    for (int k = S->N - 1; k >= 0; --k) {
+        int ci = grid_index(S->p[2 * k], S->gx0, Rc, S->ncx), cj = grid_index(S->p[2 * k + 1], S->gy0, Rc, S->ncy);
+        int c = cj * S->ncx + ci;
+        S->next[k] = S->head[c];
+        S->head[c] = k;
+    }
+}
+
+static void free_grid(or_sys *S)
+{
+    free(S->head);
+    free(S->next);
+    S->head = S->next = NULL;
+}
+
+/* Damping + friction of a pair, Sec. 4.2-4.3, with e pointing from x to y,   */
+/* relative velocity vr = v(x) - v(y), repulsion magnitude Fr (>= 0) and the   */
+/* partner volume Vy used in beta_d.  Adds to (fx, fy).                        */
+static void damping_friction(const double *prm, double ex, double ey, double vrx, double vry,
+                             double Fr, double Vx, double Vy, double *fx, double *fy)
+{
+    double rho = prm[P_RHO], dt = prm[P_DT], mu = prm[P_MU];
+    /* normal damping (eq:normal-damp), Kelvin-Voigt reading */
+    double beta = 2.0 * prm[P_RD] * sqrt(prm[P_KN] * rho / Vy);
+    double vn = vrx * ex + vry * ey;
+    double cd = beta * Vx * Vy * vn;
+    double Fdx = -cd * ex, Fdy = -cd * ey;
+    /* friction (eq:friction) with threshold v_thr = mu |F_r| dt / (rho V_x) */
+    double vtx = vrx - vn * ex, vty = vry - vn * ey;
+    double vt = sqrt(vtx * vtx + vty * vty);
+    double vthr = mu * Fr * dt / (rho * Vx);
+    double Ffx, Ffy;
+    if (vt > vthr) {
+        double c = mu * Fr / vt;
+        Ffx = -c * vtx;
+        Ffy = -c * vty;
+    } else {
+        double c = rho * Vx / dt;
+        Ffx = -c * vtx;
+        Ffy = -c * vty;
+    }
+    *fx += Fdx + Ffx;
+    *fy += Fdy + Ffy;
+}
+
+/* Wall force on one node, Sec. 4.5 (eq:wall-repulsive, eq:wall-total), with   */
+/* friction and damping obtained by the substitution e -> e^l, V_y -> |S_l|,   */
+/* p(y) -> c_l.                                                               */
+static void wall_force(const or_sys *S, int x, double *fx, double *fy)
+{
+    const double *prm = S->prm;
+    double Rc = prm[P_RC], Kn = prm[P_KN];
+    double px = S->p[2 * x], py = S->p[2 * x + 1];
+    double vx = S->v[2 * x], vy = S->v[2 * x + 1];
+    double Vx = S->V[x];
+    double t = S->t;
+    double wpos[4], wvel[4], d[4], ex[4], ey[4];
+    for (int l = 0; l < 4; ++l) {
+        wvel[l] = prm[P_VX0 + l];
+        wpos[l] = prm[P_WX0 + l] + wvel[l] * t;
+    }
+    d[0] = px - wpos[0]; ex[0] = -1.0; ey[0] = 0.0;
+    d[1] = wpos[1] - px; ex[1] = 1.0;  ey[1] = 0.0;
+    d[2] = py - wpos[2]; ex[2] = 0.0;  ey[2] = -1.0;
+    d[3] = wpos[3] - py; ex[3] = 0.0;  ey[3] = 1.0;
+    for (int l = 0; l < 4; ++l) {
+        if (d[l] < 0.0) {
+            S->status[ST_PENETRATION]++;
+            d[l] = 0.0;
+        }
+    }
+    double Fx = 0.0, Fy = 0.0;
+    for (int l = 0; l < 4; ++l) {
+        if (!(d[l] < Rc)) continue;
+        double A, cd;
+        or_wall_segment(d[l], Rc, &A, &cd);
+        /* as d -> R_c the segment vanishes and the closed form cancels; a region
+           with no positive area or a centroid not inside B_Rc exerts no force */
+        if (!(A > 0.0) || !(cd < Rc)) continue;
+        double Fr = Kn * (Rc - cd) * Vx * A;
+        double wvx = (l < 2) ? wvel[l] : 0.0, wvy = (l < 2) ? 0.0 : wvel[l];
+        double gx = -Fr * ex[l], gy = -Fr * ey[l];
+        damping_friction(prm, ex[l], ey[l], vx - wvx, vy - wvy, Fr, Vx, A, &gx, &gy);
+        Fx += gx;
+        Fy += gy;
+    }
+    static const int ci[4] = {0, 0, 1, 1}, cj[4] = {2, 3, 2, 3};
+    for (int k = 0; k < 4; ++k) {
+        int i = ci[k], j = cj[k];
+        if (!(sqrt(d[i] * d[i] + d[j] * d[j]) < Rc)) continue;
+        double A, Ix, Iy;
+        or_corner_region(d[i], d[j], Rc, &A, &Ix, &Iy);
+        if (!(A > 0.0)) continue;
+        double cx = (Ix * ex[i] + Iy * ex[j]) / A, cy = (Ix * ey[i] + Iy * ey[j]) / A;
+        double cd = sqrt(cx * cx + cy * cy);
+        if (!(cd < Rc) || !(cd > 0.0)) continue;
+        double ux = cx / cd, uy = cy / cd;
+        double Fr = Kn * (Rc - cd) * Vx * A;
+        double wvx = wvel[i], wvy = wvel[j];
+        double gx = -Fr * ux, gy = -Fr * uy;
+        damping_friction(prm, ux, uy, vx - wvx, vy - wvy, Fr, Vx, A, &gx, &gy);
+        Fx -= gx;
+        Fy -= gy;
+    }
+    *fx = Fx;
+    *fy = Fy;
+}
+
+/* Force on node x from all its interactions (eq:full, Algorithm 1 lines for  */
+/* f^peri, f^self, f^nbr, f^wall).  parts (nullable) receives the four parts.  */
+static void node_force(or_sys *S, int x, double *Fx_out, double *Fy_out, double *parts)
+{
+    const double *prm = S->prm;
+    double Rc = prm[P_RC], Kn = prm[P_KN];
+    int micro = (int)prm[P_MICRO];
+    int g = S->grain[x];
+    double cw = S->g_cw[g], s0 = S->g_s0[g], eps = S->g_eps[g];
+    double px = S->p[2 * x], py = S->p[2 * x + 1];
+    double Xx = S->X[2 * x], Xy = S->X[2 * x + 1];
+    double Vx = S->V[x];
+
+    /* peridynamic bond force with irreversible breaking (eq:peri, pmb, Sec. 3.1) */
+    double Fbx = 0.0, Fby = 0.0;
+    for (int b = S->row_ptr[x]; b < S->row_ptr[x + 1]; ++b) {
+        if (S->broken[b]) continue;
+        int y = S->col[b];
+        double xix = S->X[2 * y] - Xx, xiy = S->X[2 * y + 1] - Xy;
+        double xi = sqrt(xix * xix + xiy * xiy);
+        double dx = S->p[2 * y] - px, dy = S->p[2 * y + 1] - py;
+        double L = sqrt(dx * dx + dy * dy);
+        double s = (L - xi) / xi;
+        if (fabs(s) > s0) {
+            S->broken[b] = 1;
+            continue;
+        }
+        double cws = (micro ? cw * (1.0 - xi / eps) : cw) * s;
+        double q = cws * Vx * S->V[y] / L;
+        Fbx += q * dx;
+        Fby += q * dy;
+    }
+
+    /* contact candidates S^nbr (all grains, ascending index) */
+    int nc = contact_candidates(S, x, S->cand);
+    double Fsx = 0.0, Fsy = 0.0, Fnx = 0.0, Fny = 0.0;
+    for (int k = 0; k < nc; ++k) {
+        int y = S->cand[k];
+        double dx = S->p[2 * y] - px, dy = S->p[2 * y + 1] - py;
+        double d = sqrt(dx * dx + dy * dy);
+        if (d == 0.0) {
+            S->status[ST_COINCIDENT]++;
+            continue;
+        }
+        double ex = dx / d, ey = dy / d;
+        double Vy = S->V[y];
+        double vrx = S->v[2 * x] - S->v[2 * y], vry = S->v[2 * x + 1] - S->v[2 * y + 1];
+        if (S->grain[y] == g) {
+            /* self-contact (Sec. 4.4) between nodes with no intact bond */
+            int bonded = 0;
+            for (int b = S->row_ptr[x]; b < S->row_ptr[x + 1]; ++b)
+                if (S->col[b] == y && !S->broken[b]) bonded = 1;
+            if (bonded) continue;
+            double xix = S->X[2 * y] - Xx, xiy = S->X[2 * y + 1] - Xy;
+            double xi = sqrt(xix * xix + xiy * xiy);
+            double m;
+            if (xi < Rc)
+                m = (d < xi) ? cw * (d - xi) / xi : 0.0;
+            else
+                m = cw * (d - Rc) / Rc;
+            if (m == 0.0) continue;
+            double f = m * Vx * Vy;          /* negative: pushes x away from y */
+            double gx = f * ex, gy = f * ey;
+            damping_friction(prm, ex, ey, vrx, vry, -f, Vx, Vy, &gx, &gy);
+            Fsx += gx;
+            Fsy += gy;
+        } else {
+            /* inter-grain contact: repulsion (eq:law-repulsive), damping, friction */
+            double Fr = Kn * (Rc - d) * Vx * Vy;
+            double gx = -Fr * ex, gy = -Fr * ey;
+            damping_friction(prm, ex, ey, vrx, vry, Fr, Vx, Vy, &gx, &gy);
+            Fnx += gx;
+            Fny += gy;
+        }
+    }
+
+    double Fwx, Fwy;
+    wall_force(S, x, &Fwx, &Fwy);
+
+    *Fx_out = ((Fbx + Fsx) + Fnx) + Fwx;
+    *Fy_out = ((Fby + Fsy) + Fny) + Fwy;
+    if (parts) {
+        parts[2 * x] = Fbx;                 parts[2 * x + 1] = Fby;
+        parts[2 * S->N + 2 * x] = Fsx;      parts[2 * S->N + 2 * x + 1] = Fsy;
+        parts[4 * S->N + 2 * x] = Fnx;      parts[4 * S->N + 2 * x + 1] = Fny;
+        parts[6 * S->N + 2 * x] = Fwx;      parts[6 * S->N + 2 * x + 1] = Fwy;
+    }
+}
+
+static void sys_init(or_sys *S, const double *prm, int N, const double *X, const double *u, const double *v,
+                     const double *V, const int *grain, const double *g_cw, const double *g_s0,
+                     const double *g_eps, const int *row_ptr, const int *col, unsigned char *broken,
+                     int *status)
+{
+    memset(S, 0, sizeof(*S));
+    S->prm = prm; S->N = N; S->X = X; S->u = u; S->v = v; S->V = V; S->grain = grain;
+    S->g_cw = g_cw; S->g_s0 = g_s0; S->g_eps = g_eps; S->row_ptr = row_ptr; S->col = col;
+    S->broken = broken; S->status = status;
+    S->p = (double *)malloc(sizeof(double) * (size_t)(2 * (N > 0 ? N : 1)));
+    S->max_cand = 4096;
+    S->cand = (int *)malloc(sizeof(int) * (size_t)S->max_cand);
+    S->use_grid = ((int)prm[P_SEARCH]) != 0;
+}
+
+static void sys_free(or_sys *S)
+{
+    free(S->p);
+    free(S->cand);
+}
+
+static void all_forces(or_sys *S, double *F, double *parts)
+{
+    for (int k = 0; k < 2 * S->N; ++k) S->p[k] = S->X[k] + S->u[k];
+    int grid = S->use_grid && S->prm[P_RC] > 0.0 && S->N > 0;
+    if (grid) build_grid(S);
+    for (int x = 0; x < S->N; ++x) node_force(S, x, &F[2 * x], &F[2 * x + 1], parts);
+    if (grid) free_grid(S);
+}
+
+/* One force evaluation at the current (u, v) with walls at time t.  Breaks  */
+/* bonds as a side effect (pass a copy of `broken` to keep it).  F: 2N total  */
+/* force; parts (nullable): 8N = bond | self | neighbour | wall.              */
+void or_forces(const double *prm, double t, int N, const double *X, const double *u, const double *v,
+               const double *V, const int *grain, const double *g_cw, const double *g_s0,
+               const double *g_eps, const int *row_ptr, const int *col, unsigned char *broken,
+               double *F, double *parts, int *status)
+{
+    or_sys S;
+    sys_init(&S, prm, N, X, u, v, V, grain, g_cw, g_s0, g_eps, row_ptr, col, broken, status);
+    S.t = t;
+    all_forces(&S, F, parts);
+    sys_free(&S);
+}
+
+/* Algorithm 1: n_steps velocity-Verlet steps starting at step index step0   */
+/* (time t = step0 * dt).  On entry `a` holds the acceleration of the current */
+/* state.  F_last/parts_last (nullable) receive the forces of the last step.  */
+void or_run(const double *prm, long step0, int n_steps, int N, const double *X, double *u, double *v,
+            double *a, const double *V, const int *grain, const double *g_cw, const double *g_s0,
+            const double *g_eps, const int *row_ptr, const int *col, unsigned char *broken,
+            double *F_last, double *parts_last, int *status)
+{
+    double rho = prm[P_RHO], dt = prm[P_DT], gx = prm[P_GX], gy = prm[P_GY];
+    double half_dt = 0.5 * dt, half_dt2 = 0.5 * dt * dt;
+    double *F = (double *)malloc(sizeof(double) * (size_t)(2 * (N > 0 ? N : 1)));
+    or_sys S;
+    sys_init(&S, prm, N, X, u, v, V, grain, g_cw, g_s0, g_eps, row_ptr, col, broken, status);
+    for (int n = 0; n < n_steps; ++n) {
+        long step = step0 + n;
+        /* displacement update, current position (Algorithm 1) */
+        for (int k = 0; k < 2 * N; ++k) u[k] = (u[k] + dt * v[k]) + half_dt2 * a[k];
+        S.t = (double)(step + 1) * dt;
+        all_forces(&S, F, (n == n_steps - 1) ? parts_last : NULL);
+        /* acceleration and velocity update (Algorithm 1) */
+        for (int x = 0; x < N; ++x) {
+            double m = rho * V[x];
+            double ax = F[2 * x] / m + gx, ay = F[2 * x + 1] / m + gy;
+            v[2 * x] = v[2 * x] + half_dt * (a[2 * x] + ax);
+            v[2 * x + 1] = v[2 * x + 1] + half_dt * (a[2 * x + 1] + ay);
+            a[2 * x] = ax;
+            a[2 * x + 1] = ay;
+            if (!isfinite(ax) || !isfinite(ay)) status[ST_NONFINITE]++;
+        }
+    }
+    if (F_last) memcpy(F_last, F, sizeof(double) * (size_t)(2 * N));
+    sys_free(&S);
+    free(F);
+}
+
+/* Initial acceleration a^0 = F(u^0, v^0) / (rho V) + b / rho at t = t0        */
+/* (first line of Algorithm 1).                                               */
+void or_init_accel(const double *prm, double t0, int N, const double *X, const double *u, const double *v,
+                   double *a, const double *V, const int *grain, const double *g_cw, const double *g_s0,
+                   const double *g_eps, const int *row_ptr, const int *col, unsigned char *broken,
+                   int *status)
+{
+    double rho = prm[P_RHO], gx = prm[P_GX], gy = prm[P_GY];
+    double *F = (double *)malloc(sizeof(double) * (size_t)(2 * (N > 0 ? N : 1)));
+    or_forces(prm, t0, N, X, u, v, V, grain, g_cw, g_s0, g_eps, row_ptr, col, broken, F, NULL, status);
+    for (int x = 0; x < N; ++x) {
+        double m = rho * V[x];
+        a[2 * x] = F[2 * x] / m + gx;
+        a[2 * x + 1] = F[2 * x + 1] / m + gy;
+    }
+    free(F);
+}
+
+/* Diagnostics: kinetic energy, bond (micro-potential) energy, node-node     */
+/* contact potential, linear and angular momentum.  out[0..6] =               */
+/* KE, E_bond, E_contact, Px, Py, Lz, n_broken (directed bonds).             */
+void or_diagnostics(const double *prm, int N, const double *X, const double *u, const double *v,
+                    const double *V, const int *grain, const double *g_cw, const double *g_eps,
+                    const int *row_ptr, const int *col, const unsigned char *broken, double *out)
+{
+    double rho = prm[P_RHO], Rc = prm[P_RC], Kn = prm[P_KN];
+    int micro = (int)prm[P_MICRO];
+    double KE = 0, Eb = 0, Ec = 0, Px = 0, Py = 0, Lz = 0, nbk = 0;
+    for (int x = 0; x < N; ++x) {
+        double m = rho * V[x];
+        double vx = v[2 * x], vy = v[2 * x + 1];
+        double px = X[2 * x] + u[2 * x], py = X[2 * x + 1] + u[2 * x + 1];
+        KE += 0.5 * m * (vx * vx + vy * vy);
+        Px += m * vx;
+        Py += m * vy;
+        Lz += m * (px * vy - py * vx);
+        int g = grain[x];
+        for (int b = row_ptr[x]; b < row_ptr[x + 1]; ++b) {
+            if (broken[b]) { nbk += 1; continue; }
+            int y = col[b];
+            double xix = X[2 * y] - X[2 * x], xiy = X[2 * y + 1] - X[2 * x + 1];
+            double xi = sqrt(xix * xix + xiy * xiy);
+            double dx = (X[2 * y] + u[2 * y]) - px, dy = (X[2 * y + 1] + u[2 * y + 1]) - py;
+            double L = sqrt(dx * dx + dy * dy);
+            double s = (L - xi) / xi;
+            double c = micro ? g_cw[g] * (1.0 - xi / g_eps[g]) : g_cw[g];
+            /* pair potential 1/2 c s^2 |xi| per unit volume^2, each bond seen twice */
+            Eb += 0.25 * c * s * s * xi * V[x] * V[y];
+        }
+        for (int y = x + 1; y < N; ++y) {
+            if (grain[y] == grain[x]) continue;
+            double dx = (X[2 * y] + u[2 * y]) - px, dy = (X[2 * y + 1] + u[2 * y + 1]) - py;
+            double d = sqrt(dx * dx + dy * dy);
+            if (d < Rc) Ec += 0.5 * Kn * V[x] * V[y] * (Rc - d) * (Rc - d);
+        }
+    }
+    out[0] = KE; out[1] = Eb; out[2] = Ec; out[3] = Px; out[4] = Py; out[5] = Lz; out[6] = nbk;
+}

@@ -1,0 +1,290 @@
+"""Seeded synthetic inputs for the PeriDEM force loop.
+
+This module is shared by the GPU library's tests/benchmarks and by the CPU
+oracle's tests.  It only *describes* problems -- grain outlines, grain
+placements, material and run parameters -- and holds none of the method's
+arithmetic (no meshing, no bonds, no forces).
+
+Shapes follow Sec. 6.2 of the paper (perturbed disk, square, plus, annulus)
+plus the disk / hexagon / triangle / drop shapes of the synthetic settling
+workloads.  Every shape is a list of closed polygon loops in units of the grain
+radius R (the radius of the grain's security disk): loop 0 is the outer
+boundary in counter-clockwise order, further loops are holes in clockwise
+order, so the material is always on the left of each directed edge.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# ----------------------------------------------------------------------------
+# shapes (units of R)
+
+
+def regular_polygon(n: int, radius: float = 1.0, phase: float = 0.0) -> np.ndarray:
+    """Counter-clockwise regular n-gon inscribed in a circle of ``radius``."""
+    k = np.arange(n, dtype=np.float64)
+    ang = phase + 2.0 * math.pi * k / n
+    return np.stack([radius * np.cos(ang), radius * np.sin(ang)], axis=1)
+
+
+def disk_shape(n_vertices: int = 48) -> list[np.ndarray]:
+    return [regular_polygon(n_vertices)]
+
+
+def hexagon_shape() -> list[np.ndarray]:
+    return [regular_polygon(6)]
+
+
+def triangle_shape() -> list[np.ndarray]:
+    return [regular_polygon(3, phase=math.pi / 2)]
+
+
+def square_shape() -> list[np.ndarray]:
+    """Square inscribed in the unit circle: side sqrt(2) (Sec. 6.2)."""
+    return [regular_polygon(4, phase=math.pi / 4)]
+
+
+def drop_shape(tail_radius: float = 0.5, n_arc: int = 40) -> list[np.ndarray]:
+    """Convex tear drop: convex hull of a tip at (1, 0) and a circle of radius
+    ``tail_radius`` touching the unit circle at (-1, 0)."""
+    b = tail_radius
+    cx = -1.0 + b
+    dist = 1.0 - cx                      # tip to circle centre
+    alpha = math.asin(b / dist)          # half opening angle at the tip
+    # tangent points sit at polar angle +-(pi/2 - alpha) around the circle centre
+    a0 = math.pi / 2 - alpha
+    a1 = 2 * math.pi - a0
+    ang = np.linspace(a0, a1, n_arc)
+    arc = np.stack([cx + b * np.cos(ang), b * np.sin(ang)], axis=1)
+    # the arc already runs counter-clockwise from the upper tangent point
+    return [np.vstack([[1.0, 0.0], arc])]
+
+
+def annulus_shape(tau: float = 0.6, n_outer: int = 48, n_inner: int = 32) -> list[np.ndarray]:
+    """Ring with inner radius tau (Sec. 6.2, tau = 0.6); the hole is clockwise."""
+    outer = regular_polygon(n_outer)
+    inner = regular_polygon(n_inner, radius=tau)[::-1].copy()
+    return [outer, inner]
+
+
+def plus_shape(c: float = 0.2) -> list[np.ndarray]:
+    """Plus (cross) of arm half-width c with arm tips on the unit circle."""
+    r = c
+    a = math.sqrt(1.0 - r * r)
+    pts = [(a, -r), (a, r), (r, r), (r, a), (-r, a), (-r, r), (-a, r), (-a, -r),
+           (-r, -r), (-r, -a), (r, -a), (r, -r)]
+    return [np.array(pts, dtype=np.float64)]
+
+
+def perturbed_disk_shape(rng: np.random.Generator, n: int = 20, phi: float = 0.6) -> list[np.ndarray]:
+    """Disk perturbed inward at n vertices, r_i = 1 - X_i, X_i ~ U[0, 1-phi] (Sec. 6.2)."""
+    x = rng.uniform(0.0, 1.0 - phi, size=n)
+    r = 1.0 - x
+    ang = 2.0 * math.pi * np.arange(n) / n
+    return [np.stack([r * np.cos(ang), r * np.sin(ang)], axis=1)]
+
+
+SHAPE_MAKERS = {
+    "disk": disk_shape,
+    "hexagon": hexagon_shape,
+    "triangle": triangle_shape,
+    "drop": drop_shape,
+    "annulus": annulus_shape,
+    "plus": plus_shape,
+    "square": square_shape,
+}
+
+MIX_SETTLING = ("disk", "hexagon", "triangle", "drop", "annulus", "plus")
+
+
+# ----------------------------------------------------------------------------
+# workload description
+
+
+@dataclasses.dataclass
+class Workload:
+    """A complete synthetic problem.
+
+    shapes      list of shapes, each a list of (n_i, 2) float64 loops (units of R)
+    grain_shape (G,) int32 index into ``shapes``
+    grain_geom  (G, 7) float64 rows (cx, cy, R, theta, vx, vy, h) in SI units;
+                h is the lattice spacing of that grain
+    params      material / contact / wall / time-step parameters (SI units)
+    n_steps     number of time steps of the full run
+    name        label used in reports
+    """
+
+    shapes: list
+    grain_shape: np.ndarray
+    grain_geom: np.ndarray
+    params: dict
+    n_steps: int
+    name: str = ""
+
+    @property
+    def n_grains(self) -> int:
+        return int(self.grain_shape.shape[0])
+
+    def flat_shapes(self):
+        """(shape_loop_start[int32, S+1], loop_vtx_start[int32, L+1], vtx[float64, V*2])."""
+        shape_loop_start = [0]
+        loop_vtx_start = [0]
+        vtx = []
+        for loops in self.shapes:
+            for lp in loops:
+                vtx.append(np.asarray(lp, dtype=np.float64).reshape(-1, 2))
+                loop_vtx_start.append(loop_vtx_start[-1] + vtx[-1].shape[0])
+            shape_loop_start.append(shape_loop_start[-1] + len(loops))
+        return (np.asarray(shape_loop_start, dtype=np.int32),
+                np.asarray(loop_vtx_start, dtype=np.int32),
+                np.ascontiguousarray(np.vstack(vtx)).reshape(-1))
+
+
+def default_params(**over) -> dict:
+    """Material M of the synthetic workloads: E = 1e7 Pa, rho = 1200 kg/m^3, Gc = 50 J/m^2.
+
+    nu is fixed to 1/3 by the bond-based model (Remark after Table 1).  The bulk
+    modulus k only enters the contact stiffness K_n = 18 k / (pi eps^5); with
+    k = E / (3 (1 - 2 nu)) = E the damped contact pair is unstable under explicit
+    Verlet at the workloads' time steps, so each workload picks a smaller k
+    (see :func:`contact_cfl`).
+    """
+    p = dict(
+        E=1.0e7, nu=1.0 / 3.0, k_bulk=1.0e7, rho=1200.0, Gc=50.0,
+        horizon_ratio=3.0,          # eps = 3 h
+        rc_ratio=0.95,              # R_c = 0.95 h_min
+        damping_ratio=0.8, friction=0.5,
+        gx=0.0, gy=-5000.0,
+        dt=1.0e-7,
+        wall_lo=(-5e-3, 0.0), wall_hi=(5e-3, 20e-3),
+        wall_vel_lo=(0.0, 0.0), wall_vel_hi=(0.0, 0.0),
+        micromodulus=0,             # 0 constant, 1 conic (Table 1)
+    )
+    p.update(over)
+    return p
+
+
+def contact_cfl(params: dict, h_min: float) -> dict:
+    """Stability numbers of the stiffest node-node contact pair (equal volumes h_min^2).
+
+    omega_dt   relative-motion angular frequency sqrt(2 K_n V^2 / (rho V)) times dt
+    damp_dt    relative damping rate 2 c / (rho V) times dt, c = beta_d V^2
+    Explicit velocity Verlet with the start-of-step velocity in the damping is
+    stable for damp_dt below about 2 and omega_dt below 2.
+    """
+    eps = params["horizon_ratio"] * h_min
+    kn = 18.0 * params["k_bulk"] / (math.pi * eps ** 5)
+    V = h_min * h_min
+    m = params["rho"] * V
+    beta = 2.0 * params["damping_ratio"] * math.sqrt(kn * params["rho"] / V)
+    c = beta * V * V
+    dt = params["dt"]
+    return dict(omega_dt=math.sqrt(2.0 * kn * V * V / m) * dt, damp_dt=2.0 * c / m * dt)
+
+
+def _mk(shapes, gshape, ggeom, params, n_steps, name):
+    return Workload(shapes=shapes, grain_shape=np.asarray(gshape, dtype=np.int32),
+                    grain_geom=np.ascontiguousarray(np.asarray(ggeom, dtype=np.float64).reshape(-1, 7)),
+                    params=params, n_steps=int(n_steps), name=name)
+
+
+def two_disks(h_ratio: int = 8, gap: float = 0.5e-3, floor_gap: float | None = None,
+              v_upper: float = 0.0, n_steps: int = 10_000, **over) -> Workload:
+    """Two disks of radius 1 mm, h = R / h_ratio; the upper one falls ``gap`` onto
+    the lower one, which rests ``floor_gap`` (default R_c / 2) above the floor."""
+    R = 1e-3
+    h = R / h_ratio
+    params = default_params(k_bulk=1.0e6)
+    params.update(over)
+    rc = params["rc_ratio"] * h
+    if floor_gap is None:
+        floor_gap = rc / 2
+    y0 = R + floor_gap
+    y1 = y0 + 2 * R + gap
+    ggeom = [(0.0, y0, R, 0.0, 0.0, 0.0, h), (0.0, y1, R, 0.0, 0.0, v_upper, h)]
+    return _mk([disk_shape()], [0, 0], ggeom, params, n_steps, f"two_disks_h{h_ratio}")
+
+
+def _rsa_place(rng, radii, box_lo, box_hi, margin, max_tries=200000):
+    """Random sequential addition of non-overlapping disks of radius radii+margin."""
+    placed = []
+    for r in radii:
+        rr = r + margin
+        for _ in range(max_tries):
+            x = rng.uniform(box_lo[0] + rr + margin, box_hi[0] - rr - margin)
+            y = rng.uniform(box_lo[1] + rr + margin, box_hi[1] - rr - margin)
+            ok = True
+            for (px, py, pr) in placed:
+                if (x - px) ** 2 + (y - py) ** 2 < (rr + pr) ** 2:
+                    ok = False
+                    break
+            if ok:
+                placed.append((x, y, rr))
+                break
+        else:
+            raise RuntimeError("random sequential addition failed; box too small")
+    return np.array([(x, y) for (x, y, _) in placed])
+
+
+def settling(n_grains: int = 50, box=(20e-3, 30e-3), r_range=(1e-3, 1.5e-3), h_ratio: int = 15,
+             mix=MIX_SETTLING, seed: int = 1, n_steps: int = 20_000, dt: float = 5e-8,
+             **over) -> Workload:
+    """Seeded mixed-shape grains in a rectangular wall box under gravity.
+
+    Radii ~ U[r_range], shapes drawn uniformly from ``mix``, lattice spacing
+    h = R / h_ratio per grain, random rotations, zero initial velocity.  Grains
+    are placed by random sequential addition of security disks of radius
+    R + R_c / 2 (so no contact force acts at t = 0) kept R_c away from the walls.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    radii = rng.uniform(r_range[0], r_range[1], size=n_grains)
+    kinds = rng.integers(0, len(mix), size=n_grains)
+    theta = rng.uniform(0.0, 2 * math.pi, size=n_grains)
+    params = default_params(dt=dt, friction=0.8, damping_ratio=0.8, k_bulk=5.0e5,
+                            wall_lo=(0.0, 0.0), wall_hi=(box[0], box[1]))
+    params.update(over)
+    h_min = float(np.min(radii)) / h_ratio
+    rc = params["rc_ratio"] * h_min
+    order = np.argsort(-radii, kind="stable")          # place big grains first
+    centres = np.empty((n_grains, 2))
+    centres[order] = _rsa_place(rng, radii[order], (0.0, 0.0), box, rc / 2)
+    shapes = []
+    shape_index = {}
+    gshape = []
+    for g in range(n_grains):
+        name = mix[kinds[g]]
+        if name not in shape_index:
+            shape_index[name] = len(shapes)
+            shapes.append(SHAPE_MAKERS[name]())
+        gshape.append(shape_index[name])
+    ggeom = [(centres[g, 0], centres[g, 1], radii[g], theta[g], 0.0, 0.0, radii[g] / h_ratio)
+             for g in range(n_grains)]
+    return _mk(shapes, gshape, ggeom, params, n_steps, f"settling_{n_grains}g_seed{seed}")
+
+
+def compaction(n_grains: int = 500, width: float = 40e-3, r_range=(0.8e-3, 1.6e-3), h_ratio: int = 23,
+               wall_speed: float = 0.1, seed: int = 3, n_steps: int = 2000, dt: float = 5e-8,
+               **over) -> Workload:
+    """Mixed-shape grains in a box of given width whose top wall moves down."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    radii = rng.uniform(r_range[0], r_range[1], size=n_grains)
+    area = float(np.sum(math.pi * (radii + 0.1e-3) ** 2))
+    height = area / 0.42 / width
+    w = settling(n_grains=n_grains, box=(width, height), r_range=r_range, h_ratio=h_ratio,
+                 seed=seed, n_steps=n_steps, dt=dt, gy=0.0, **over)
+    w.params["wall_vel_hi"] = (0.0, -wall_speed)
+    w.name = f"compaction_{n_grains}g_seed{seed}"
+    return w
+
+
+def perturbed_disks(n_grains: int, seed: int = 7, **kw) -> Workload:
+    """Settling workload made only of perturbed disks (one random outline per grain)."""
+    w = settling(n_grains=n_grains, mix=("disk",), seed=seed, **kw)
+    rng = np.random.Generator(np.random.PCG64(seed + 1000))
+    w.shapes = [perturbed_disk_shape(rng) for _ in range(n_grains)]
+    w.grain_shape = np.arange(n_grains, dtype=np.int32)
+    w.name = f"perturbed_{n_grains}g_seed{seed}"
+    return w
