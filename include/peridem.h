@@ -1,0 +1,243 @@
+/*
+ * peridem.h -- C ABI of the GB300 PeriDEM library (libperidem.so).
+ *
+ * The library advances the PeriDEM equations of motion (eq:full) of an
+ * aggregate of deformable, breakable 2D grains with velocity Verlet
+ * (Algorithm 1).  Everything in the time loop runs in hand-written CUDA
+ * kernels for sm_103a: intra-grain bond forces with irreversible breaking
+ * (eq:peri, eq:pmb, Sec. 3.1), node-to-node contact with repulsion, normal
+ * damping and regularised stick/slip friction (Secs. 4.1-4.3), self-contact
+ * between unbonded nodes of one grain (Sec. 4.4), analytic wall contact with
+ * corner inclusion-exclusion (Sec. 4.5), and the Verlet update.
+ *
+ * Conventions
+ *  - Units are SI.  Vectors are interleaved (x, y) pairs of doubles.
+ *  - Every entry point returns 0 (PD_OK) or a negative PD_E* code; the text of
+ *    the last error of the calling thread is returned by pd_last_error().
+ *    No C++ exception crosses this boundary.
+ *  - Ownership: the caller owns every buffer it passes.  Device memory for the
+ *    simulation state is ONE caller-allocated arena (pd_arena_bytes /
+ *    pd_bind_arena) that must stay alive until pd_destroy; the library never
+ *    frees caller memory.  The context itself owns only host metadata, CUDA
+ *    graphs and its host copies of the mesh.
+ *  - Streams: all device work is enqueued on the stream given to pd_create,
+ *    in stream order; calls return without waiting unless stated otherwise.
+ *  - Device-side error conditions (non-finite acceleration, candidate list
+ *    overflow, a node past a wall) are latched in a device status word and
+ *    reported by pd_status().
+ */
+#ifndef PERIDEM_H
+#define PERIDEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---------------------------------------------------------- */
+#define PD_OK 0
+#define PD_EINVAL -1     /* invalid argument (null pointer, size, value)       */
+#define PD_ESTATE -2     /* call out of order (e.g. pd_step before bind)        */
+#define PD_ECUDA -3      /* a CUDA runtime call failed                          */
+#define PD_ENUMERIC -4   /* non-finite acceleration detected on the device      */
+#define PD_EOVERFLOW -5  /* a node had more contact candidates than supported   */
+#define PD_ENOMEM -6     /* host allocation failed or arena too small           */
+#define PD_ETIMEOUT -7   /* a bounded device wait gave up                       */
+
+/* ---- precision modes ------------------------------------------------------- */
+#define PD_FP64 0        /* plain FP64 everywhere                               */
+#define PD_FP32_SPLIT 1  /* FP32 bond/contact arithmetic, FP64 integration      */
+
+/* ---- micromodulus (Table 1) ------------------------------------------------ */
+#define PD_MICRO_CONSTANT 0
+#define PD_MICRO_CONIC 1
+
+/*
+ * Run parameters.  Material (E, nu, k_bulk, rho, Gc) is shared by all grains.
+ * Each grain has its own lattice spacing h (grain_geom), hence its own horizon
+ * eps = horizon_ratio * h and its own c_w, s0 (Table 1).  The contact radius is
+ * R_c = rc_ratio * h_min and the contact stiffness K_n = 18 k / (pi eps_c^5)
+ * with eps_c = horizon_ratio * h_min (Sec. 4.1), h_min the smallest spacing.
+ * Walls form the rectangle [wall_lo, wall_hi] at t = 0; wall_vel_* are the
+ * normal velocities of the four walls (x_lo, y_lo in wall_vel_lo; x_hi, y_hi
+ * in wall_vel_hi), so a wall is at w0 + v t (Sec. 6.4 moving top wall).
+ */
+typedef struct pd_params {
+    double E;               /* Young's modulus [Pa]                             */
+    double nu;              /* Poisson ratio used in c_w (1/3 for 2D bonds)     */
+    double k_bulk;          /* bulk modulus in K_n [Pa]                         */
+    double rho;             /* density [kg/m^3]                                 */
+    double Gc;              /* critical energy release rate [J/m^2]             */
+    double horizon_ratio;   /* eps / h                                          */
+    double rc_ratio;        /* R_c / h_min                                      */
+    double damping_ratio;   /* r_d in beta_d = 2 r_d sqrt(K_n rho / V_y)         */
+    double friction;        /* mu                                               */
+    double gravity[2];      /* body acceleration b / rho [m/s^2]                */
+    double dt;              /* time step [s]                                    */
+    double wall_lo[2];      /* x_min, y_min at t = 0                            */
+    double wall_hi[2];      /* x_max, y_max at t = 0                            */
+    double wall_vel_lo[2];  /* velocity of the x_min wall (along x), y_min (y)  */
+    double wall_vel_hi[2];  /* velocity of the x_max wall (along x), y_max (y)  */
+    int32_t micromodulus;   /* PD_MICRO_*                                       */
+    int32_t precision;      /* PD_FP64 or PD_FP32_SPLIT                         */
+    int32_t store_parts;    /* nonzero: keep the four force parts of the last   */
+                            /* evaluation (bond|self|neighbour|wall), for tests */
+    int32_t reserved;
+} pd_params;
+
+/* ---- state fields (pd_get_state / pd_set_state) ---------------------------- */
+#define PD_FIELD_X 0            /* double[2N] reference positions (get)              */
+#define PD_FIELD_DISP 1         /* double[2N] displacement u (get/set)               */
+#define PD_FIELD_VEL 2          /* double[2N] velocity (get/set)                     */
+#define PD_FIELD_ACC 3          /* double[2N] acceleration of the last step (get/set)*/
+#define PD_FIELD_POS 4          /* double[2N] current position X + u (get)           */
+#define PD_FIELD_FORCE 5        /* double[2N] total nodal force, last evaluation     */
+#define PD_FIELD_FORCE_PARTS 6  /* double[8N] bond|self|neighbour|wall (store_parts) */
+#define PD_FIELD_BROKEN 7       /* uint8[n_bonds] 1 = broken, CSR order (get/set)    */
+#define PD_FIELD_DAMAGE 8       /* double[N] broken / reference bonds (get)          */
+#define PD_FIELD_GRAIN 9        /* int32[N] grain id of each node (get)              */
+#define PD_FIELD_VOLUME 10      /* double[N] nodal volume h^2 (get)                  */
+#define PD_FIELD_ROW_PTR 11     /* int32[N+1] CSR row pointer of the bond lists      */
+#define PD_FIELD_COL 12         /* int32[n_bonds] CSR columns (ascending per row)    */
+#define PD_FIELD_LATTICE 13     /* int32[2N] lattice indices (i, j) in grain frame   */
+#define PD_FIELD_STEP 14        /* int64[1] number of completed time steps (get/set) */
+
+/* ---- status word slots (pd_status) ------------------------------------------ */
+#define PD_STATUS_PENETRATION 0 /* node found past a wall (treated as touching)     */
+#define PD_STATUS_COINCIDENT 1  /* two nodes at the same position (pair skipped)    */
+#define PD_STATUS_NONFINITE 2   /* non-finite acceleration                          */
+#define PD_STATUS_OVERFLOW 3    /* contact candidates beyond the per-node capacity  */
+#define PD_STATUS_COUNT 8
+
+/* ---- diagnostics (pd_diagnostics) ------------------------------------------- */
+#define PD_DIAG_KE 0            /* kinetic energy sum 1/2 rho V |v|^2                */
+#define PD_DIAG_EBOND 1         /* bond energy sum over bonds 1/2 c w s^2 |xi| V V   */
+#define PD_DIAG_PX 2            /* linear momentum x                                 */
+#define PD_DIAG_PY 3            /* linear momentum y                                 */
+#define PD_DIAG_LZ 4            /* angular momentum about the origin                 */
+#define PD_DIAG_NBROKEN 5       /* number of broken directed bonds                   */
+/* slots 6, 7 reserved (0) */
+#define PD_DIAG_COUNT 8
+
+typedef struct pd_ctx pd_ctx;
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char *pd_last_error(void);
+
+/*
+ * Create a context.  `params` is copied.  `cuda_stream` is a cudaStream_t (may
+ * be NULL for the legacy default stream) on which all later device work of
+ * this context is enqueued; no device work happens before pd_bind_arena, so a
+ * context can mesh and build bonds on a machine without a GPU.
+ * Errors: PD_EINVAL (null out/params, non-positive dt/rho/E/horizon_ratio).
+ */
+int pd_create(pd_ctx **out, const pd_params *params, void *cuda_stream);
+
+/* Destroy a context (waits for its stream).  Safe on NULL. */
+int pd_destroy(pd_ctx *ctx);
+
+/*
+ * Mesh the grains (host).  Grain shapes are polygon loops in units of the
+ * grain radius R: shape s owns loops shape_loop_start[s] .. shape_loop_start[s+1]-1,
+ * loop l owns vertices loop_vtx_start[l] .. loop_vtx_start[l+1]-1 of vtx_xy
+ * (interleaved x, y).  The first loop of a shape is its outer boundary
+ * (counter-clockwise), further loops are holes (clockwise).
+ * grain_geom holds n_grains rows of 7 doubles (cx, cy, R, theta, vx, vy, h).
+ * Each grain is discretised on the lattice (i h, j h) of its own frame: the
+ * points strictly inside the grain and at least 1e-6 h from its boundary, in
+ * order of j then i, rotated by theta and moved to (cx, cy); every node has
+ * volume h^2 (Sec. 5: nodes inside the grain, mesh size = node spacing) and
+ * initial velocity (vx, vy).  Nodes are numbered grain by grain.
+ * Writes the node count to *n_nodes_out.  Errors: PD_EINVAL, PD_ESTATE
+ * (called twice), PD_ENOMEM.
+ */
+int pd_mesh_grains(pd_ctx *ctx, int n_shapes, const int32_t *shape_loop_start,
+                   const int32_t *loop_vtx_start, const double *vtx_xy, int n_grains,
+                   const int32_t *grain_shape, const double *grain_geom, int64_t *n_nodes_out);
+
+/*
+ * Build the reference neighbour (bond) lists S^ref of Algorithm 1 (host):
+ * node y of the same grain is a neighbour of x when their lattice offset has
+ * di^2 + dj^2 < horizon_ratio^2 (strict |xi| < eps) and the segment x-y does
+ * not cross the grain's extended boundary (every boundary loop moved out by
+ * delta along the outward vertex bisectors) nor an outer-angle bisector ray
+ * of a non-convex cusp (Sec. 4 "bonds in nonconvex domains").  Lists are CSR,
+ * sorted by node, columns ascending.  Writes the directed bond count.
+ * Errors: PD_ESTATE (before pd_mesh_grains), PD_ENOMEM.
+ */
+int pd_build_bonds(pd_ctx *ctx, int64_t *n_bonds_out);
+
+/* Bytes of device memory the caller must provide to pd_bind_arena (after
+ * pd_build_bonds).  Errors: PD_ESTATE. */
+int pd_arena_bytes(pd_ctx *ctx, size_t *bytes);
+
+/*
+ * Bind a caller-owned device arena of at least pd_arena_bytes bytes (256-byte
+ * aligned), upload the mesh, bonds and initial state on the context stream and
+ * compute the initial acceleration a^0 = F(u^0, v^0) / (rho V) + b / rho
+ * (Algorithm 1, first line).  Errors: PD_ESTATE, PD_EINVAL (null/misaligned
+ * pointer, too small), PD_ECUDA.
+ */
+int pd_bind_arena(pd_ctx *ctx, void *device_arena, size_t bytes);
+
+/*
+ * Advance n_steps >= 0 velocity-Verlet steps (Algorithm 1) asynchronously on
+ * the context stream; the step sequence runs as captured CUDA graphs.
+ * Errors: PD_ESTATE (not bound), PD_EINVAL (n_steps < 0), PD_ECUDA.
+ */
+int pd_step(pd_ctx *ctx, int n_steps);
+
+/*
+ * Copy a state field (PD_FIELD_*) into dst (bytes must equal the field size).
+ * dst_on_device = 1: device-to-device copy enqueued on the stream; 0: the call
+ * waits for the stream and copies to host memory.  Mesh fields (X, GRAIN,
+ * VOLUME, ROW_PTR, COL, LATTICE) can be read from host copies before
+ * pd_bind_arena.  Errors: PD_EINVAL (unknown field, size mismatch), PD_ESTATE,
+ * PD_ECUDA.
+ */
+int pd_get_state(pd_ctx *ctx, int field, void *dst, size_t bytes, int dst_on_device);
+
+/* Overwrite a settable state field (DISP, VEL, ACC, BROKEN, STEP) from host
+ * (src_on_device = 0) or device memory, stream-ordered.  Errors as above. */
+int pd_set_state(pd_ctx *ctx, int field, const void *src, size_t bytes, int src_on_device);
+
+/* Recompute the forces and acceleration of the current state without moving
+ * it (as for a^0): fills FORCE (and FORCE_PARTS) and sets ACC.  Bonds may
+ * break.  Errors: PD_ESTATE, PD_ECUDA. */
+int pd_eval_forces(pd_ctx *ctx);
+
+/* Reductions of the current state into out[PD_DIAG_COUNT] (waits for the
+ * stream).  Errors: PD_ESTATE, PD_ECUDA. */
+int pd_diagnostics(pd_ctx *ctx, double *out);
+
+/* Copy the device status word into out[PD_STATUS_COUNT] (waits) and return
+ * PD_OK, or the first error code it implies (PD_ENUMERIC, PD_EOVERFLOW). */
+int pd_status(pd_ctx *ctx, int32_t *out);
+
+/* Scalar facts of the context: out[0] N, out[1] directed bonds, out[2] grains,
+ * out[3] h_min, out[4] R_c, out[5] K_n, out[6] dt, out[7] completed steps,
+ * out[8] max bonds per node, out[9] contact hash buckets. */
+int pd_info(pd_ctx *ctx, double *out);
+
+/* ---- kernel timing (instrumentation) ----------------------------------------- */
+#define PD_TIMER_PREDICT 0      /* memset + displacement update / positions / bucket counts */
+#define PD_TIMER_BIN 1          /* scan + scatter of the contact hash grid               */
+#define PD_TIMER_FORCE 2        /* force + acceleration + velocity kernel                */
+#define PD_TIMER_COUNT 4
+
+/* Enable (1) or disable (0) per-kernel timing: while enabled, pd_step runs
+ * one-step graphs that also record CUDA events around each kernel group.
+ * Errors: PD_ESTATE (not bound), PD_ECUDA. */
+int pd_set_timing(pd_ctx *ctx, int enable);
+
+/* Durations in milliseconds of the kernel groups of the LAST step run with
+ * timing enabled (waits for the stream): out[PD_TIMER_*]. */
+int pd_kernel_times(pd_ctx *ctx, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PERIDEM_H */

@@ -1,0 +1,252 @@
+"""Thin Python binding of libperidem.so (the C ABI of include/peridem.h).
+
+Argument marshalling only: every step of the time loop runs in the library's
+CUDA kernels.  PyTorch supplies the device arena and the CUDA stream.  There
+is no fallback: if the library cannot be loaded, :func:`load` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+c_double, c_int32, c_int64, c_size_t, c_void_p = (ctypes.c_double, ctypes.c_int32, ctypes.c_int64,
+                                                   ctypes.c_size_t, ctypes.c_void_p)
+
+PD_OK, PD_EINVAL, PD_ESTATE, PD_ECUDA, PD_ENUMERIC, PD_EOVERFLOW, PD_ENOMEM, PD_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
+PD_FP64, PD_FP32_SPLIT = 0, 1
+FIELDS = dict(X=0, DISP=1, VEL=2, ACC=3, POS=4, FORCE=5, FORCE_PARTS=6, BROKEN=7, DAMAGE=8, GRAIN=9,
+              VOLUME=10, ROW_PTR=11, COL=12, LATTICE=13, STEP=14)
+STATUS_COUNT = 8
+DIAG_COUNT = 8
+DIAG_NAMES = ("KE", "E_bond", "Px", "Py", "Lz", "n_broken")
+
+# public C-ABI symbols (checked by the test-suite against include/peridem.h)
+SYMBOLS = ("pd_last_error", "pd_create", "pd_destroy", "pd_mesh_grains", "pd_build_bonds", "pd_arena_bytes",
+           "pd_bind_arena", "pd_step", "pd_get_state", "pd_set_state", "pd_eval_forces", "pd_diagnostics",
+           "pd_status", "pd_info", "pd_set_timing", "pd_kernel_times")
+
+
+class PdParams(ctypes.Structure):
+    _fields_ = [("E", c_double), ("nu", c_double), ("k_bulk", c_double), ("rho", c_double), ("Gc", c_double),
+                ("horizon_ratio", c_double), ("rc_ratio", c_double), ("damping_ratio", c_double),
+                ("friction", c_double), ("gravity", c_double * 2), ("dt", c_double),
+                ("wall_lo", c_double * 2), ("wall_hi", c_double * 2), ("wall_vel_lo", c_double * 2),
+                ("wall_vel_hi", c_double * 2), ("micromodulus", c_int32), ("precision", c_int32),
+                ("store_parts", c_int32), ("reserved", c_int32)]
+
+
+class PeridemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"peridem error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load():
+    """Load libperidem.so, building it in-tree first if nvcc is available."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not _build.up_to_date():
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libperidem.so is missing; run __graft_entry__.build()")
+            L = ctypes.CDLL(_build.LIB)
+            vp, ip = c_void_p, c_int32
+            L.pd_last_error.restype = ctypes.c_char_p
+            L.pd_create.argtypes = [ctypes.POINTER(c_void_p), ctypes.POINTER(PdParams), vp]
+            L.pd_destroy.argtypes = [vp]
+            L.pd_mesh_grains.argtypes = [vp, ip, vp, vp, vp, ip, vp, vp, ctypes.POINTER(c_int64)]
+            L.pd_build_bonds.argtypes = [vp, ctypes.POINTER(c_int64)]
+            L.pd_arena_bytes.argtypes = [vp, ctypes.POINTER(c_size_t)]
+            L.pd_bind_arena.argtypes = [vp, vp, c_size_t]
+            L.pd_step.argtypes = [vp, ip]
+            L.pd_get_state.argtypes = [vp, ip, vp, c_size_t, ip]
+            L.pd_set_state.argtypes = [vp, ip, vp, c_size_t, ip]
+            L.pd_eval_forces.argtypes = [vp]
+            L.pd_diagnostics.argtypes = [vp, vp]
+            L.pd_status.argtypes = [vp, vp]
+            L.pd_info.argtypes = [vp, vp]
+            L.pd_set_timing.argtypes = [vp, ip]
+            L.pd_kernel_times.argtypes = [vp, vp]
+            for name in SYMBOLS:
+                if name != "pd_last_error":
+                    getattr(L, name).restype = ip
+            _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != PD_OK:
+        raise PeridemError(rc, load().pd_last_error().decode())
+    return rc
+
+
+def make_params(p: dict, precision: int = PD_FP64, store_parts: bool = False) -> PdParams:
+    q = PdParams()
+    for name in ("E", "nu", "k_bulk", "rho", "Gc", "horizon_ratio", "rc_ratio", "damping_ratio", "friction", "dt"):
+        setattr(q, name, float(p[name]))
+    q.gravity[:] = (float(p["gx"]), float(p["gy"]))
+    q.wall_lo[:] = tuple(map(float, p["wall_lo"]))
+    q.wall_hi[:] = tuple(map(float, p["wall_hi"]))
+    q.wall_vel_lo[:] = tuple(map(float, p["wall_vel_lo"]))
+    q.wall_vel_hi[:] = tuple(map(float, p["wall_vel_hi"]))
+    q.micromodulus = int(p["micromodulus"])
+    q.precision = int(precision)
+    q.store_parts = 1 if store_parts else 0
+    return q
+
+
+def _ptr(a: np.ndarray):
+    return c_void_p(a.ctypes.data)
+
+
+class Simulation:
+    """One PeriDEM problem bound to the library.
+
+    ``device=None`` meshes and builds bonds only (host work; no GPU needed).
+    With a CUDA device the state lives in one torch-allocated arena and all
+    work runs on ``stream`` (default: the current torch stream).
+    """
+
+    def __init__(self, workload, precision: int | str = PD_FP64, store_parts: bool = False, device=None,
+                 stream=None):
+        L = load()
+        if isinstance(precision, str):
+            precision = {"fp64": PD_FP64, "fp32": PD_FP32_SPLIT, "fp32_split": PD_FP32_SPLIT}[precision]
+        self.precision = precision
+        self.workload = workload
+        self.device = device
+        self._arena = None
+        self._stream = None
+        sptr = None
+        if device is not None:
+            import torch
+            self._stream = stream if stream is not None else torch.cuda.current_stream(torch.device(device))
+            sptr = c_void_p(self._stream.cuda_stream)
+        self._params = make_params(workload.params, precision, store_parts)
+        ctx = c_void_p()
+        _check(L.pd_create(ctypes.byref(ctx), ctypes.byref(self._params), sptr))
+        self._ctx = ctx
+        sls, lvs, vtx = workload.flat_shapes()
+        gs = np.ascontiguousarray(workload.grain_shape, dtype=np.int32)
+        gg = np.ascontiguousarray(workload.grain_geom, dtype=np.float64)
+        n = c_int64()
+        _check(L.pd_mesh_grains(ctx, len(workload.shapes), _ptr(sls), _ptr(lvs), _ptr(vtx), workload.n_grains,
+                                _ptr(gs), _ptr(gg), ctypes.byref(n)))
+        self.N = n.value
+        nb = c_int64()
+        _check(L.pd_build_bonds(ctx, ctypes.byref(nb)))
+        self.n_bonds = nb.value
+        if device is not None:
+            self.bind()
+
+    # -- lifecycle ----------------------------------------------------------
+    def bind(self):
+        import torch
+        L = load()
+        nbytes = c_size_t()
+        _check(L.pd_arena_bytes(self._ctx, ctypes.byref(nbytes)))
+        with torch.cuda.stream(self._stream):
+            self._arena = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=self.device)
+        base = self._arena.data_ptr()
+        aligned = (base + 255) & ~255
+        _check(L.pd_bind_arena(self._ctx, c_void_p(aligned), nbytes.value))
+        self.arena_bytes = int(nbytes.value)
+
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            load().pd_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- stepping -------------------------------------------------------------
+    def step(self, n: int = 1):
+        _check(load().pd_step(self._ctx, int(n)))
+
+    def eval_forces(self):
+        _check(load().pd_eval_forces(self._ctx))
+
+    # -- state access -----------------------------------------------------------
+    _SHAPES = {
+        "X": (np.float64, 2), "DISP": (np.float64, 2), "VEL": (np.float64, 2), "ACC": (np.float64, 2),
+        "POS": (np.float64, 2), "FORCE": (np.float64, 2), "FORCE_PARTS": (np.float64, 8),
+        "DAMAGE": (np.float64, 1), "GRAIN": (np.int32, 1), "VOLUME": (np.float64, 1),
+        "LATTICE": (np.int32, 2),
+    }
+
+    def _alloc(self, field):
+        if field in self._SHAPES:
+            dt, k = self._SHAPES[field]
+            shape = (self.N, 2) if k == 2 else ((4, self.N, 2) if k == 8 else (self.N,))
+            return np.zeros(shape, dtype=dt)
+        if field == "BROKEN":
+            return np.zeros(self.n_bonds, dtype=np.uint8)
+        if field == "ROW_PTR":
+            return np.zeros(self.N + 1, dtype=np.int32)
+        if field == "COL":
+            return np.zeros(self.n_bonds, dtype=np.int32)
+        if field == "STEP":
+            return np.zeros(1, dtype=np.int64)
+        raise KeyError(field)
+
+    def get(self, field: str) -> np.ndarray:
+        """Host copy of a state field (waits for the stream)."""
+        out = self._alloc(field)
+        _check(load().pd_get_state(self._ctx, FIELDS[field], _ptr(out) if out.nbytes else None, out.nbytes, 0))
+        return out
+
+    def get_device(self, field: str, out):
+        """Stream-ordered device-to-device copy into a torch tensor ``out``."""
+        _check(load().pd_get_state(self._ctx, FIELDS[field], c_void_p(out.data_ptr()),
+                                   out.numel() * out.element_size(), 1))
+        return out
+
+    def set(self, field: str, value) -> None:
+        if hasattr(value, "data_ptr"):
+            _check(load().pd_set_state(self._ctx, FIELDS[field], c_void_p(value.data_ptr()),
+                                       value.numel() * value.element_size(), 1))
+            return
+        ref = self._alloc(field)
+        arr = np.ascontiguousarray(np.asarray(value, dtype=ref.dtype).reshape(ref.shape))
+        _check(load().pd_set_state(self._ctx, FIELDS[field], _ptr(arr), arr.nbytes, 0))
+
+    def diagnostics(self) -> dict:
+        out = np.zeros(DIAG_COUNT)
+        _check(load().pd_diagnostics(self._ctx, _ptr(out)))
+        d = dict(zip(DIAG_NAMES, out[: len(DIAG_NAMES)]))
+        d["n_broken"] = int(d["n_broken"])
+        return d
+
+    def status(self):
+        out = np.zeros(STATUS_COUNT, dtype=np.int32)
+        rc = load().pd_status(self._ctx, _ptr(out))
+        return rc, out
+
+    def set_timing(self, enable: bool):
+        _check(load().pd_set_timing(self._ctx, 1 if enable else 0))
+
+    def kernel_times(self) -> dict:
+        """Milliseconds of the kernel groups of the last timed step."""
+        out = np.zeros(4)
+        _check(load().pd_kernel_times(self._ctx, _ptr(out)))
+        return dict(predict=out[0], bin=out[1], force=out[2], step=out[3])
+
+    def info(self) -> dict:
+        out = np.zeros(10)
+        _check(load().pd_info(self._ctx, _ptr(out)))
+        keys = ("N", "n_bonds", "G", "h_min", "Rc", "Kn", "dt", "steps", "max_row", "buckets")
+        return dict(zip(keys, out))

@@ -1,0 +1,219 @@
+// pd_common.cu -- precision-independent step kernels: displacement update and
+// positions (Algorithm 1), contact binning (hash-grid counting sort: bucket
+// counts, device-wide exclusive scan, scatter), positions for readout and the
+// diagnostics reductions.  Compiled without FMA contraction so the FP64
+// update arithmetic rounds exactly as written.
+#include "pd_device.cuh"
+
+namespace pd {
+
+// u <- u + dt v + dt^2/2 a ; p = X + u ; hash-grid bucket of p (Algorithm 1).
+// Thread 0 also advances the step counter and sets the wall positions of the
+// force evaluation that follows: w(t_{n+1}) = w0 + v_w (n+1) dt.
+__global__ void __launch_bounds__(kBlock) k_predict(DevPtrs d, KParams k, int vin, int advance) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        long long st = *d.step + (advance ? 1 : 0);
+        double t = (double)st * k.dt;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) d.walls_now[l] = k.w0[l] + k.wv[l] * t;
+        if (advance) *d.step = st;
+    }
+    if (i >= k.N) return;
+    double2 u = d.u[i];
+    if (advance) {
+        double2 v = d.v[vin][i], a = d.a[i];
+        u.x = (u.x + k.dt * v.x) + k.half_dt2 * a.x;
+        u.y = (u.y + k.dt * v.y) + k.half_dt2 * a.y;
+        d.u[i] = u;
+    }
+    double2 X = d.X[i];
+    double2 p = make_double2(X.x + u.x, X.y + u.y);
+    d.p[i] = p;
+    unsigned b = cell_bucket(cell_coord(p.x, k.ox, k.cell), cell_coord(p.y, k.oy, k.cell), k.T);
+    d.key[i] = (int)b;
+    atomicAdd(&d.count[b], 1);
+}
+
+// Block-wide exclusive scan of kScanItems values per thread.
+__device__ __forceinline__ int block_exclusive_scan(int (&v)[kScanItems], int *smem_warp) {
+    int local = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        int t = v[q];
+        v[q] = local;
+        local += t;
+    }
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) smem_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = (lane < (kScanThreads / 32)) ? smem_warp[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += y;
+        }
+        smem_warp[lane] = wi - w;           // exclusive warp offsets
+        if (lane == 31) smem_warp[32] = wi; // block total
+    }
+    __syncthreads();
+    int base = smem_warp[warp] + (incl - local);
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) v[q] += base;
+    int total = smem_warp[32];
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int *__restrict__ count, int *blocksums, unsigned T) {
+    __shared__ int sm[33];
+    size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
+    int v[kScanItems];
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) v[q] = (base + q < T) ? count[base + q] : 0;
+    int total = block_exclusive_scan(v, sm);
+    if (threadIdx.x == 0) blocksums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(int *blocksums, int nblocks) {
+    __shared__ int sm[33];
+    int v[kScanItems];
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        int idx = threadIdx.x * kScanItems + q;
+        v[q] = idx < nblocks ? blocksums[idx] : 0;
+    }
+    block_exclusive_scan(v, sm);
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        int idx = threadIdx.x * kScanItems + q;
+        if (idx < nblocks) blocksums[idx] = v[q];
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int *__restrict__ count, const int *__restrict__ blocksums,
+                                                             int *start, int *cursor, unsigned T, int N) {
+    __shared__ int sm[33];
+    size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
+    int v[kScanItems];
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) v[q] = (base + q < T) ? count[base + q] : 0;
+    block_exclusive_scan(v, sm);
+    int off = blocksums[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        if (base + q < T) {
+            start[base + q] = v[q] + off;
+            cursor[base + q] = v[q] + off;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) start[T] = N;
+}
+
+__global__ void __launch_bounds__(kBlock) k_scatter(const int *__restrict__ key, int *cursor, int *sorted, int N) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int pos = atomicAdd(&cursor[key[i]], 1);
+    sorted[pos] = i;
+}
+
+__global__ void __launch_bounds__(kBlock) k_positions(DevPtrs d, KParams k) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k.N) return;
+    double2 X = d.X[i], u = d.u[i];
+    d.p[i] = make_double2(X.x + u.x, X.y + u.y);
+}
+
+// Diagnostics: per-block partial sums (grid-stride, fixed order), then one
+// block adds the partials in block order -- deterministic for a given grid.
+__global__ void __launch_bounds__(kBlock) k_diag_partial(DevPtrs d, KParams k, int vcur) {
+    double acc[PD_DIAG_COUNT];
+#pragma unroll
+    for (int q = 0; q < PD_DIAG_COUNT; ++q) acc[q] = 0.0;
+    const double2 *v = d.v[vcur];
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < k.N; x += gridDim.x * blockDim.x) {
+        double m = k.rho * d.V[x];
+        double2 vx = v[x], X = d.X[x], u = d.u[x];
+        double px = X.x + u.x, py = X.y + u.y;
+        acc[PD_DIAG_KE] += 0.5 * m * (vx.x * vx.x + vx.y * vx.y);
+        acc[PD_DIAG_PX] += m * vx.x;
+        acc[PD_DIAG_PY] += m * vx.y;
+        acc[PD_DIAG_LZ] += m * (px * vx.y - py * vx.x);
+        int g = d.grain[x];
+        double cw = d.g_cw[g], eps = d.g_eps[g];
+        int r0 = d.row_ptr[x], r1 = d.row_ptr[x + 1];
+        for (int b = r0; b < r1; ++b) {
+            int kk = b - r0;
+            if ((d.bits[(size_t)x * k.wpn + (kk >> 5)] >> (kk & 31)) & 1u) {
+                acc[PD_DIAG_NBROKEN] += 1.0;
+                continue;
+            }
+            int y = d.col[b];
+            double xi = d.xi[b];
+            double2 Xy = d.X[y], uy = d.u[y];
+            double dx = (Xy.x + uy.x) - px, dy = (Xy.y + uy.y) - py;
+            double L = sqrt(dx * dx + dy * dy);
+            double s = (L - xi) / xi;
+            double c = k.micro ? cw * (1.0 - xi / eps) : cw;
+            acc[PD_DIAG_EBOND] += 0.25 * c * s * s * xi * d.V[x] * d.V[y];
+        }
+    }
+    __shared__ double sm[PD_DIAG_COUNT][kBlock];
+#pragma unroll
+    for (int q = 0; q < PD_DIAG_COUNT; ++q) sm[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int w = kBlock / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int q = 0; q < PD_DIAG_COUNT; ++q) sm[q][threadIdx.x] += sm[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < PD_DIAG_COUNT) d.diag_part[blockIdx.x * PD_DIAG_COUNT + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+__global__ void k_diag_final(DevPtrs d, int nblocks) {
+    int q = threadIdx.x;
+    if (q >= PD_DIAG_COUNT) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += d.diag_part[b * PD_DIAG_COUNT + q];
+    d.diag_out[q] = s;
+}
+
+// ---------------------------------------------------------------------------
+
+static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+cudaError_t launch_predict(const DevPtrs &d, const KParams &k, int vin, int advance, cudaStream_t s) {
+    k_predict<<<nblk(k.N, kBlock), kBlock, 0, s>>>(d, k, vin, advance);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const DevPtrs &d, const KParams &k, cudaStream_t s) {
+    int nb = nblk(k.T, kScanTile);
+    k_scan_reduce<<<nb, kScanThreads, 0, s>>>(d.count, d.blocksums, k.T);
+    k_scan_top<<<1, kScanThreads, 0, s>>>(d.blocksums, nb);
+    k_scan_apply<<<nb, kScanThreads, 0, s>>>(d.count, d.blocksums, d.start, d.cursor, k.T, k.N);
+    k_scatter<<<nblk(k.N, kBlock), kBlock, 0, s>>>(d.key, d.cursor, d.sorted, k.N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_positions(const DevPtrs &d, const KParams &k, cudaStream_t s) {
+    k_positions<<<nblk(k.N, kBlock), kBlock, 0, s>>>(d, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(const DevPtrs &d, const KParams &k, int vcur, cudaStream_t s) {
+    k_diag_partial<<<k.n_diag_blocks, kBlock, 0, s>>>(d, k, vcur);
+    k_diag_final<<<1, 32, 0, s>>>(d, k.n_diag_blocks);
+    return cudaGetLastError();
+}
+
+}  // namespace pd

@@ -1,0 +1,859 @@
+// pd_host.cpp -- host runtime of the GB300 PeriDEM library: the C ABI of
+// include/peridem.h, the lattice mesher, the reference bond builder of the
+// paper's non-convex rule, arena layout, uploads and the captured step graphs.
+#include "peridem.h"
+#include "pd_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kMeshClear = 1e-6;   // nodes closer than this * h to the boundary are dropped
+constexpr double kExtend = 1e-7;      // extended-boundary offset delta, in units of h
+constexpr int kChunk = 16;            // time steps per captured chunk graph
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define PD_CUDA(call)                                                                    \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(PD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+    } while (0)
+
+struct Vec2 {
+    double x, y;
+};
+inline Vec2 sub(Vec2 a, Vec2 b) { return {a.x - b.x, a.y - b.y}; }
+inline double crs(Vec2 a, Vec2 b) { return a.x * b.y - a.y * b.x; }
+inline double nrm(Vec2 a) { return std::sqrt(a.x * a.x + a.y * a.y); }
+inline Vec2 unit(Vec2 a) {
+    double l = nrm(a);
+    return {a.x / l, a.y / l};
+}
+
+// A grain outline in its own frame, physical units.
+struct Outline {
+    std::vector<std::vector<Vec2>> loops;
+};
+
+// --- lattice mesher -------------------------------------------------------
+
+// Winding number of the region bounded by all loops around q (outer loop
+// counter-clockwise, holes clockwise): nonzero inside the material.
+int winding(const Outline &o, Vec2 q) {
+    int wn = 0;
+    for (const auto &lp : o.loops) {
+        size_t n = lp.size();
+        for (size_t k = 0; k < n; ++k) {
+            Vec2 a = lp[k], b = lp[(k + 1) % n];
+            double side = crs(sub(b, a), sub(q, a));
+            if (a.y <= q.y) {
+                if (b.y > q.y && side > 0) ++wn;
+            } else {
+                if (b.y <= q.y && side < 0) --wn;
+            }
+        }
+    }
+    return wn;
+}
+
+double seg_dist(Vec2 q, Vec2 a, Vec2 b) {
+    Vec2 e = sub(b, a);
+    double l2 = e.x * e.x + e.y * e.y;
+    double t = l2 > 0 ? ((q.x - a.x) * e.x + (q.y - a.y) * e.y) / l2 : 0.0;
+    t = std::min(1.0, std::max(0.0, t));
+    double dx = a.x + t * e.x - q.x, dy = a.y + t * e.y - q.y;
+    return std::sqrt(dx * dx + dy * dy);
+}
+
+double boundary_dist(const Outline &o, Vec2 q) {
+    double best = 1e300;
+    for (const auto &lp : o.loops)
+        for (size_t k = 0; k < lp.size(); ++k) best = std::min(best, seg_dist(q, lp[k], lp[(k + 1) % lp.size()]));
+    return best;
+}
+
+// --- paper's non-convex horizon construction ------------------------------
+
+struct Seg {
+    Vec2 a, b;
+};
+
+// Closed segment intersection by orientation tests.
+bool on_seg(Vec2 a, Vec2 b, Vec2 q) {
+    return std::min(a.x, b.x) <= q.x && q.x <= std::max(a.x, b.x) && std::min(a.y, b.y) <= q.y &&
+           q.y <= std::max(a.y, b.y);
+}
+bool segs_meet(Vec2 a, Vec2 b, Vec2 c, Vec2 d) {
+    double d1 = crs(sub(d, c), sub(a, c)), d2 = crs(sub(d, c), sub(b, c));
+    double d3 = crs(sub(b, a), sub(c, a)), d4 = crs(sub(b, a), sub(d, a));
+    if (((d1 > 0 && d2 < 0) || (d1 < 0 && d2 > 0)) && ((d3 > 0 && d4 < 0) || (d3 < 0 && d4 > 0))) return true;
+    if (d1 == 0 && on_seg(c, d, a)) return true;
+    if (d2 == 0 && on_seg(c, d, b)) return true;
+    if (d3 == 0 && on_seg(a, b, c)) return true;
+    if (d4 == 0 && on_seg(a, b, d)) return true;
+    return false;
+}
+
+// Barriers of one grain (Sec. 4): the extended boundary (every vertex p^i
+// moved by delta along its outward normal n_i, the bisector of the outer angle)
+// and, at each non-convex cusp, the bisector segment from p^i + delta n_i to
+// q^i - delta n_i, where the ray p^i + t n_i meets the boundary again (or, with
+// no hit, to t0 = |p^i| + sup |x|).  A bond is dropped when it meets any barrier.
+std::vector<Seg> barriers(const Outline &o, double delta) {
+    std::vector<Seg> out;
+    double sup = 0;
+    for (const auto &lp : o.loops)
+        for (auto v : lp) sup = std::max(sup, nrm(v));
+    for (const auto &lp : o.loops) {
+        size_t n = lp.size();
+        std::vector<Vec2> ext(n), nrmv(n);
+        std::vector<char> cusp(n, 0);
+        for (size_t i = 0; i < n; ++i) {
+            Vec2 p = lp[i], pm = lp[(i + n - 1) % n], pp = lp[(i + 1) % n];
+            Vec2 vm = unit(sub(p, pm)), vi = unit(sub(pp, p));
+            double c = crs(vm, vi);
+            Vec2 nn;
+            if (c > 0) {
+                nn = unit(Vec2{vm.x - vi.x, vm.y - vi.y});          // convex corner
+            } else if (c < 0) {
+                nn = unit(Vec2{vi.x - vm.x, vi.y - vm.y});          // non-convex cusp
+                cusp[i] = 1;
+            } else {
+                nn = Vec2{vi.y, -vi.x};                               // straight: edge normal
+            }
+            nrmv[i] = nn;
+            ext[i] = Vec2{p.x + delta * nn.x, p.y + delta * nn.y};
+        }
+        for (size_t i = 0; i < n; ++i) out.push_back(Seg{ext[i], ext[(i + 1) % n]});
+        for (size_t i = 0; i < n; ++i) {
+            if (!cusp[i]) continue;
+            Vec2 p = lp[i], nn = nrmv[i];
+            double tbest = 1e300;
+            for (const auto &lq : o.loops) {
+                size_t m = lq.size();
+                for (size_t k = 0; k < m; ++k) {
+                    Vec2 c = lq[k], d = lq[(k + 1) % m];
+                    Vec2 s = sub(d, c);
+                    double den = crs(nn, s);
+                    if (den == 0) continue;
+                    Vec2 w = sub(c, p);
+                    double t = crs(w, s) / den, u = crs(w, nn) / den;
+                    // tolerant end test: a ray through a vertex must not slip between
+                    // the two edges that share it
+                    if (t > delta && u >= -1e-9 && u <= 1.0 + 1e-9) tbest = std::min(tbest, t);
+                }
+            }
+            // the bisector stops delta short of q^i, as it starts delta away from p^i:
+            // a bond that merely touches the boundary at either end point stays
+            double tend = (tbest == 1e300) ? nrm(p) + sup : tbest - delta;
+            out.push_back(Seg{Vec2{p.x + delta * nn.x, p.y + delta * nn.y}, Vec2{p.x + tend * nn.x, p.y + tend * nn.y}});
+        }
+    }
+    return out;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+struct pd_ctx {
+    pd_params prm{};
+    cudaStream_t stream = nullptr;
+    int state = 0;  // 0 created, 1 meshed, 2 bonded, 3 bound
+    // mesh (host)
+    int G = 0;
+    int64_t N = 0;
+    std::vector<double> X;     // 2N
+    std::vector<int32_t> lat;  // 2N
+    std::vector<int32_t> grain;
+    std::vector<double> V, v0;  // N, 2N
+    std::vector<double> g_h, g_cw, g_s0, g_eps, g_cx, g_cy, g_R;
+    std::vector<int64_t> g_start;
+    std::vector<Outline> g_outline;  // per grain, local frame, physical units
+    // bonds (host)
+    std::vector<int32_t> row_ptr, col;
+    std::vector<double> xi;
+    int max_row = 0, wpn = 1;
+    // derived
+    double h_min = 0, Rc = 0, Kn = 0;
+    unsigned T = 0;
+    pd::KParams kp{};
+    pd::DevPtrs d{};
+    size_t arena_bytes = 0;
+    int vcur = 0;
+    int64_t steps_done = 0;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t chunk[2] = {nullptr, nullptr};
+    cudaGraphExec_t single[2] = {nullptr, nullptr};
+    cudaGraphExec_t timed[2] = {nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int timing = 0;
+};
+
+namespace {
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+template <class T>
+void carve(char *base, size_t &off, T *&ptr, size_t count) {
+    ptr = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off = align_up(off + sizeof(T) * std::max<size_t>(count, 1));
+}
+
+size_t layout(pd_ctx *c, char *base) {
+    size_t off = 0;
+    pd::DevPtrs &d = c->d;
+    size_t N = (size_t)c->N, nb = c->col.size(), G = (size_t)c->G;
+    carve(base, off, d.X, N);
+    carve(base, off, d.u, N);
+    carve(base, off, d.v[0], N);
+    carve(base, off, d.v[1], N);
+    carve(base, off, d.a, N);
+    carve(base, off, d.p, N);
+    carve(base, off, d.F, c->prm.store_parts ? N : 0);
+    carve(base, off, d.parts, c->prm.store_parts ? 4 * N : 0);
+    carve(base, off, d.V, N);
+    carve(base, off, d.grain, N);
+    carve(base, off, d.row_ptr, N + 1);
+    carve(base, off, d.col, nb);
+    carve(base, off, d.xi, nb);
+    carve(base, off, d.bits, N * (size_t)c->wpn);
+    carve(base, off, d.g_cw, G);
+    carve(base, off, d.g_s0, G);
+    carve(base, off, d.g_eps, G);
+    carve(base, off, d.key, N);
+    carve(base, off, d.count, c->T);
+    carve(base, off, d.start, (size_t)c->T + 1);
+    carve(base, off, d.cursor, c->T);
+    carve(base, off, d.sorted, N);
+    carve(base, off, d.blocksums, c->T / pd::kScanTile + 2);
+    carve(base, off, d.step, 1);
+    carve(base, off, d.walls_now, 4);
+    carve(base, off, d.status, PD_STATUS_COUNT);
+    carve(base, off, d.diag_part, (size_t)c->kp.n_diag_blocks * PD_DIAG_COUNT);
+    carve(base, off, d.diag_out, PD_DIAG_COUNT);
+    if (c->prm.precision == PD_FP32_SPLIT) {
+        carve(base, off, d.Xl, N);
+        carve(base, off, d.gc, G);
+        carve(base, off, d.xi_f, nb);
+    } else {
+        d.Xl = nullptr;
+        d.gc = nullptr;
+        d.xi_f = nullptr;
+    }
+    return off;
+}
+
+int check_ctx(pd_ctx *c, int min_state) {
+    if (!c) return fail(PD_EINVAL, "null context");
+    if (c->state < min_state) return fail(PD_ESTATE, "call out of order");
+    return PD_OK;
+}
+
+// Record one time step (Algorithm 1) on stream s: displacement update and
+// positions, contact binning, forces + acceleration + velocity update.  With
+// `timed`, event records bracket the three kernel groups.
+cudaError_t record_step(pd_ctx *c, int vin, cudaStream_t s, bool timed = false) {
+    cudaError_t e;
+    if (timed && (e = cudaEventRecord(c->ev[0], s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d.count, 0, sizeof(int) * c->T, s)) != cudaSuccess) return e;
+    if ((e = pd::launch_predict(c->d, c->kp, vin, 1, s)) != cudaSuccess) return e;
+    if (timed && (e = cudaEventRecord(c->ev[1], s)) != cudaSuccess) return e;
+    if ((e = pd::launch_bin(c->d, c->kp, s)) != cudaSuccess) return e;
+    if (timed && (e = cudaEventRecord(c->ev[2], s)) != cudaSuccess) return e;
+    if (c->prm.precision == PD_FP32_SPLIT)
+        e = pd::launch_force_fp32(c->d, c->kp, vin, 1, s);
+    else
+        e = pd::launch_force_fp64(c->d, c->kp, vin, 1, s);
+    if (e != cudaSuccess) return e;
+    if (timed && (e = cudaEventRecord(c->ev[3], s)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+int capture(pd_ctx *c, int vstart, int nsteps, cudaGraphExec_t *out, bool timed = false) {
+    cudaGraph_t g = nullptr;
+    PD_CUDA(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
+    int v = vstart;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+        e = record_step(c, v, c->capture_stream, timed);
+        v ^= 1;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &g);
+    if (e != cudaSuccess) return fail(PD_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    if (e2 != cudaSuccess) return fail(PD_ECUDA, std::string("end capture: ") + cudaGetErrorString(e2));
+    PD_CUDA(cudaGraphInstantiate(out, g, 0));
+    cudaGraphDestroy(g);
+    return PD_OK;
+}
+
+size_t field_bytes(pd_ctx *c, int f) {
+    size_t N = (size_t)c->N;
+    switch (f) {
+        case PD_FIELD_X: case PD_FIELD_DISP: case PD_FIELD_VEL: case PD_FIELD_ACC: case PD_FIELD_POS:
+        case PD_FIELD_FORCE:
+            return 16 * N;
+        case PD_FIELD_FORCE_PARTS: return 64 * N;
+        case PD_FIELD_BROKEN: return c->col.size();
+        case PD_FIELD_DAMAGE: case PD_FIELD_VOLUME: return 8 * N;
+        case PD_FIELD_GRAIN: return 4 * N;
+        case PD_FIELD_ROW_PTR: return 4 * (N + 1);
+        case PD_FIELD_COL: return 4 * c->col.size();
+        case PD_FIELD_LATTICE: return 8 * N;
+        case PD_FIELD_STEP: return 8;
+        default: return 0;
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+
+extern "C" {
+
+const char *pd_last_error(void) { return g_err.c_str(); }
+
+int pd_create(pd_ctx **out, const pd_params *params, void *cuda_stream) {
+    if (!out || !params) return fail(PD_EINVAL, "null argument");
+    const pd_params &p = *params;
+    if (!(p.dt > 0) || !(p.rho > 0) || !(p.E > 0) || !(p.horizon_ratio > 0) || !(p.rc_ratio > 0) ||
+        !(p.nu < 1) || !(p.Gc > 0) || !(p.k_bulk > 0))
+        return fail(PD_EINVAL, "invalid parameters (dt, rho, E, Gc, k, horizon_ratio, rc_ratio must be > 0, nu < 1)");
+    if (p.precision != PD_FP64 && p.precision != PD_FP32_SPLIT) return fail(PD_EINVAL, "unknown precision");
+    if (p.micromodulus != PD_MICRO_CONSTANT && p.micromodulus != PD_MICRO_CONIC)
+        return fail(PD_EINVAL, "unknown micromodulus");
+    pd_ctx *c = new (std::nothrow) pd_ctx();
+    if (!c) return fail(PD_ENOMEM, "out of host memory");
+    c->prm = p;
+    c->stream = (cudaStream_t)cuda_stream;
+    *out = c;
+    return PD_OK;
+}
+
+int pd_destroy(pd_ctx *c) {
+    if (!c) return PD_OK;
+    if (c->state >= 3) {
+        cudaStreamSynchronize(c->stream);
+        for (int k = 0; k < 2; ++k) {
+            if (c->chunk[k]) cudaGraphExecDestroy(c->chunk[k]);
+            if (c->single[k]) cudaGraphExecDestroy(c->single[k]);
+            if (c->timed[k]) cudaGraphExecDestroy(c->timed[k]);
+        }
+        for (auto &e : c->ev)
+            if (e) cudaEventDestroy(e);
+        if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    }
+    delete c;
+    return PD_OK;
+}
+
+int pd_mesh_grains(pd_ctx *c, int n_shapes, const int32_t *shape_loop_start, const int32_t *loop_vtx_start,
+                   const double *vtx, int n_grains, const int32_t *grain_shape, const double *geom,
+                   int64_t *n_nodes_out) {
+    if (int r = check_ctx(c, 0)) return r;
+    if (c->state != 0) return fail(PD_ESTATE, "pd_mesh_grains called twice");
+    if (n_shapes <= 0 || n_grains <= 0 || !shape_loop_start || !loop_vtx_start || !vtx || !grain_shape || !geom)
+        return fail(PD_EINVAL, "empty or null mesh input");
+    for (int s = 0; s < n_shapes; ++s) {
+        if (shape_loop_start[s + 1] <= shape_loop_start[s]) return fail(PD_EINVAL, "shape without loops");
+        for (int l = shape_loop_start[s]; l < shape_loop_start[s + 1]; ++l)
+            if (loop_vtx_start[l + 1] - loop_vtx_start[l] < 3) return fail(PD_EINVAL, "loop with < 3 vertices");
+    }
+    try {
+        c->G = n_grains;
+        c->g_h.resize(n_grains);
+        c->g_cx.resize(n_grains);
+        c->g_cy.resize(n_grains);
+        c->g_R.resize(n_grains);
+        c->g_outline.resize(n_grains);
+        c->g_start.assign(n_grains + 1, 0);
+        for (int g = 0; g < n_grains; ++g) {
+            const double *q = geom + 7 * (size_t)g;
+            double cx = q[0], cy = q[1], R = q[2], th = q[3], vx = q[4], vy = q[5], h = q[6];
+            int s = grain_shape[g];
+            if (s < 0 || s >= n_shapes) return fail(PD_EINVAL, "grain shape index out of range");
+            if (!(R > 0) || !(h > 0) || !(R / h < 1e4)) return fail(PD_EINVAL, "grain radius / spacing invalid");
+            Outline &o = c->g_outline[g];
+            o.loops.clear();
+            for (int l = shape_loop_start[s]; l < shape_loop_start[s + 1]; ++l) {
+                std::vector<Vec2> lp;
+                for (int k = loop_vtx_start[l]; k < loop_vtx_start[l + 1]; ++k)
+                    lp.push_back(Vec2{R * vtx[2 * k], R * vtx[2 * k + 1]});
+                o.loops.push_back(lp);
+            }
+            c->g_h[g] = h;
+            c->g_cx[g] = cx;
+            c->g_cy[g] = cy;
+            c->g_R[g] = R;
+            int m = (int)std::ceil(R / h) + 1;
+            double cs = std::cos(th), sn = std::sin(th);
+            for (int j = -m; j <= m; ++j) {
+                for (int i = -m; i <= m; ++i) {
+                    double lx = (double)i * h, ly = (double)j * h;
+                    Vec2 ql{lx, ly};
+                    if (winding(o, ql) == 0) continue;
+                    if (boundary_dist(o, ql) < kMeshClear * h) continue;
+                    c->X.push_back(cx + (cs * lx - sn * ly));
+                    c->X.push_back(cy + (sn * lx + cs * ly));
+                    c->lat.push_back(i);
+                    c->lat.push_back(j);
+                    c->grain.push_back(g);
+                    c->V.push_back(h * h);
+                    c->v0.push_back(vx);
+                    c->v0.push_back(vy);
+                }
+            }
+            c->g_start[g + 1] = (int64_t)c->grain.size();
+        }
+    } catch (const std::bad_alloc &) {
+        return fail(PD_ENOMEM, "out of host memory while meshing");
+    }
+    c->N = (int64_t)c->grain.size();
+    if (c->N == 0) return fail(PD_EINVAL, "no lattice node inside any grain");
+    if (c->N >= (int64_t(1) << 31)) return fail(PD_EINVAL, "too many nodes for 32-bit indices");
+    // material constants per grain (Table 1) and contact constants (Sec. 4.1)
+    const pd_params &p = c->prm;
+    c->g_cw.resize(c->G);
+    c->g_s0.resize(c->G);
+    c->g_eps.resize(c->G);
+    c->h_min = *std::min_element(c->g_h.begin(), c->g_h.end());
+    for (int g = 0; g < c->G; ++g) {
+        double eps = p.horizon_ratio * c->g_h[g];
+        c->g_eps[g] = eps;
+        if (p.micromodulus == PD_MICRO_CONSTANT) {
+            c->g_cw[g] = 6.0 * p.E / (kPi * eps * eps * eps * (1.0 - p.nu));
+            c->g_s0[g] = std::sqrt(4.0 * kPi * p.Gc / (9.0 * p.E * eps));
+        } else {
+            c->g_cw[g] = 24.0 * p.E / (kPi * eps * eps * eps * (1.0 - p.nu));
+            c->g_s0[g] = std::sqrt(5.0 * kPi * p.Gc / (9.0 * p.E * eps));
+        }
+    }
+    double eps_c = p.horizon_ratio * c->h_min;
+    c->Rc = p.rc_ratio * c->h_min;
+    c->Kn = 18.0 * p.k_bulk / (kPi * eps_c * eps_c * eps_c * eps_c * eps_c);
+    c->state = 1;
+    if (n_nodes_out) *n_nodes_out = c->N;
+    return PD_OK;
+}
+
+int pd_build_bonds(pd_ctx *c, int64_t *n_bonds_out) {
+    if (int r = check_ctx(c, 1)) return r;
+    if (c->state != 1) return fail(PD_ESTATE, "pd_build_bonds called twice");
+    const double hr = c->prm.horizon_ratio;
+    const int rr = (int)std::ceil(hr);
+    std::vector<std::vector<int32_t>> g_row(c->G), g_col(c->G);
+    auto work = [&](int g) {
+        int64_t s0 = c->g_start[g], s1 = c->g_start[g + 1];
+        int n = (int)(s1 - s0);
+        double h = c->g_h[g];
+        std::vector<Seg> bar = barriers(c->g_outline[g], kExtend * h);
+        int imin = 1 << 30, imax = -(1 << 30), jmin = 1 << 30, jmax = -(1 << 30);
+        for (int k = 0; k < n; ++k) {
+            imin = std::min(imin, c->lat[2 * (s0 + k)]);
+            imax = std::max(imax, c->lat[2 * (s0 + k)]);
+            jmin = std::min(jmin, c->lat[2 * (s0 + k) + 1]);
+            jmax = std::max(jmax, c->lat[2 * (s0 + k) + 1]);
+        }
+        int W = imax - imin + 1, H = jmax - jmin + 1;
+        std::vector<int> map((size_t)W * H, -1);
+        for (int k = 0; k < n; ++k)
+            map[(size_t)(c->lat[2 * (s0 + k) + 1] - jmin) * W + (c->lat[2 * (s0 + k)] - imin)] = k;
+        auto &row = g_row[g];
+        auto &col = g_col[g];
+        row.assign(n + 1, 0);
+        std::vector<int> nb;
+        for (int x = 0; x < n; ++x) {
+            nb.clear();
+            int ix = c->lat[2 * (s0 + x)], jx = c->lat[2 * (s0 + x) + 1];
+            Vec2 a{(double)ix * h, (double)jx * h};
+            for (int dj = -rr; dj <= rr; ++dj)
+                for (int di = -rr; di <= rr; ++di) {
+                    if ((di | dj) == 0 || (double)(di * di + dj * dj) >= hr * hr) continue;
+                    int iy = ix + di, jy = jx + dj;
+                    if (iy < imin || iy > imax || jy < jmin || jy > jmax) continue;
+                    int y = map[(size_t)(jy - jmin) * W + (iy - imin)];
+                    if (y < 0) continue;
+                    Vec2 b{(double)iy * h, (double)jy * h};
+                    bool cut = false;
+                    for (const Seg &sg : bar)
+                        if (segs_meet(a, b, sg.a, sg.b)) {
+                            cut = true;
+                            break;
+                        }
+                    if (!cut) nb.push_back(y);
+                }
+            std::sort(nb.begin(), nb.end());
+            for (int y : nb) col.push_back((int32_t)(y + s0));
+            row[x + 1] = (int32_t)col.size();
+        }
+    };
+    try {
+        unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nt; ++t)
+            th.emplace_back([&, t] {
+                for (int g = (int)t; g < c->G; g += (int)nt) work(g);
+            });
+        for (auto &t : th) t.join();
+        size_t total = 0;
+        for (int g = 0; g < c->G; ++g) total += g_col[g].size();
+        if (total >= (size_t(1) << 31)) return fail(PD_EINVAL, "too many bonds for 32-bit indices");
+        c->row_ptr.assign(c->N + 1, 0);
+        c->col.clear();
+        c->col.reserve(total);
+        for (int g = 0; g < c->G; ++g) {
+            int64_t s0 = c->g_start[g];
+            int n = (int)(c->g_start[g + 1] - s0);
+            int32_t base = (int32_t)c->col.size();
+            for (int x = 0; x < n; ++x) c->row_ptr[s0 + x + 1] = base + g_row[g][x + 1];
+            c->col.insert(c->col.end(), g_col[g].begin(), g_col[g].end());
+        }
+        c->xi.resize(c->col.size());
+        c->max_row = 0;
+        for (int64_t x = 0; x < c->N; ++x) {
+            c->max_row = std::max(c->max_row, c->row_ptr[x + 1] - c->row_ptr[x]);
+            for (int32_t b = c->row_ptr[x]; b < c->row_ptr[x + 1]; ++b) {
+                int32_t y = c->col[b];
+                double dx = c->X[2 * y] - c->X[2 * x], dy = c->X[2 * y + 1] - c->X[2 * x + 1];
+                c->xi[b] = std::sqrt(dx * dx + dy * dy);
+            }
+        }
+    } catch (const std::bad_alloc &) {
+        return fail(PD_ENOMEM, "out of host memory while building bonds");
+    }
+    c->wpn = std::max(1, (c->max_row + 31) / 32);
+    // contact hash: power of two >= 2N buckets
+    unsigned T = 1024;
+    while ((int64_t)T < 2 * c->N) T <<= 1;
+    c->T = T;
+    c->state = 2;
+    if (n_bonds_out) *n_bonds_out = (int64_t)c->col.size();
+    return PD_OK;
+}
+
+int pd_arena_bytes(pd_ctx *c, size_t *bytes) {
+    if (int r = check_ctx(c, 2)) return r;
+    if (!bytes) return fail(PD_EINVAL, "null bytes");
+    c->kp.n_diag_blocks = (int)std::min<int64_t>(1024, (c->N + pd::kBlock - 1) / pd::kBlock);
+    *bytes = layout(c, nullptr);
+    return PD_OK;
+}
+
+int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
+    if (int r = check_ctx(c, 2)) return r;
+    if (c->state != 2) return fail(PD_ESTATE, "arena already bound");
+    if (!arena || ((uintptr_t)arena & 255)) return fail(PD_EINVAL, "arena null or not 256-byte aligned");
+    c->kp.n_diag_blocks = (int)std::min<int64_t>(1024, (c->N + pd::kBlock - 1) / pd::kBlock);
+    size_t need = layout(c, nullptr);
+    if (bytes < need) return fail(PD_EINVAL, "arena too small");
+    c->arena_bytes = layout(c, (char *)arena);
+    const pd_params &p = c->prm;
+    pd::KParams &k = c->kp;
+    k.N = (int)c->N;
+    k.G = c->G;
+    k.wpn = c->wpn;
+    k.T = c->T;
+    k.rho = p.rho;
+    k.Kn = c->Kn;
+    k.Rc = c->Rc;
+    k.rd = p.damping_ratio;
+    k.mu = p.friction;
+    k.gx = p.gravity[0];
+    k.gy = p.gravity[1];
+    k.dt = p.dt;
+    k.half_dt = 0.5 * p.dt;
+    k.half_dt2 = 0.5 * p.dt * p.dt;
+    k.w0[0] = p.wall_lo[0];
+    k.w0[1] = p.wall_hi[0];
+    k.w0[2] = p.wall_lo[1];
+    k.w0[3] = p.wall_hi[1];
+    k.wv[0] = p.wall_vel_lo[0];
+    k.wv[1] = p.wall_vel_hi[0];
+    k.wv[2] = p.wall_vel_lo[1];
+    k.wv[3] = p.wall_vel_hi[1];
+    k.cell = c->Rc;
+    k.ox = p.wall_lo[0];
+    k.oy = p.wall_lo[1];
+    k.micro = p.micromodulus;
+    k.store = p.store_parts ? 1 : 0;
+    cudaStream_t s = c->stream;
+    const pd::DevPtrs &d = c->d;
+    size_t N = (size_t)c->N, nb = c->col.size(), G = (size_t)c->G;
+    // host staging (kept alive until the stream drains below)
+    std::vector<uint32_t> bits(N * c->wpn, 0u);
+    PD_CUDA(cudaMemcpyAsync(d.X, c->X.data(), 16 * N, cudaMemcpyHostToDevice, s));
+    PD_CUDA(cudaMemsetAsync(d.u, 0, 16 * N, s));
+    PD_CUDA(cudaMemcpyAsync(d.v[0], c->v0.data(), 16 * N, cudaMemcpyHostToDevice, s));
+    PD_CUDA(cudaMemsetAsync(d.v[1], 0, 16 * N, s));
+    PD_CUDA(cudaMemsetAsync(d.a, 0, 16 * N, s));
+    PD_CUDA(cudaMemcpyAsync(d.V, c->V.data(), 8 * N, cudaMemcpyHostToDevice, s));
+    PD_CUDA(cudaMemcpyAsync(d.grain, c->grain.data(), 4 * N, cudaMemcpyHostToDevice, s));
+    PD_CUDA(cudaMemcpyAsync(d.row_ptr, c->row_ptr.data(), 4 * (N + 1), cudaMemcpyHostToDevice, s));
+    if (nb) {
+        PD_CUDA(cudaMemcpyAsync(d.col, c->col.data(), 4 * nb, cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.xi, c->xi.data(), 8 * nb, cudaMemcpyHostToDevice, s));
+    }
+    PD_CUDA(cudaMemcpyAsync(d.bits, bits.data(), 4 * bits.size(), cudaMemcpyHostToDevice, s));
+    PD_CUDA(cudaMemcpyAsync(d.g_cw, c->g_cw.data(), 8 * G, cudaMemcpyHostToDevice, s));
+    PD_CUDA(cudaMemcpyAsync(d.g_s0, c->g_s0.data(), 8 * G, cudaMemcpyHostToDevice, s));
+    PD_CUDA(cudaMemcpyAsync(d.g_eps, c->g_eps.data(), 8 * G, cudaMemcpyHostToDevice, s));
+    PD_CUDA(cudaMemsetAsync(d.step, 0, 8, s));
+    PD_CUDA(cudaMemsetAsync(d.status, 0, 4 * PD_STATUS_COUNT, s));
+    std::vector<float> xl, xif;
+    std::vector<double> gcv;
+    if (p.precision == PD_FP32_SPLIT) {
+        // grain-local FP32 reference coordinates relative to each grain's centre
+        xl.resize(2 * N);
+        gcv.resize(2 * G);
+        for (size_t g = 0; g < G; ++g) {
+            gcv[2 * g] = c->g_cx[g];
+            gcv[2 * g + 1] = c->g_cy[g];
+            for (int64_t x = c->g_start[g]; x < c->g_start[g + 1]; ++x) {
+                xl[2 * x] = (float)(c->X[2 * x] - c->g_cx[g]);
+                xl[2 * x + 1] = (float)(c->X[2 * x + 1] - c->g_cy[g]);
+            }
+        }
+        xif.resize(std::max<size_t>(nb, 1));
+        for (size_t b = 0; b < nb; ++b) xif[b] = (float)c->xi[b];
+        PD_CUDA(cudaMemcpyAsync(d.Xl, xl.data(), 8 * N, cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.gc, gcv.data(), 16 * G, cudaMemcpyHostToDevice, s));
+        if (nb) PD_CUDA(cudaMemcpyAsync(d.xi_f, xif.data(), 4 * nb, cudaMemcpyHostToDevice, s));
+    }
+    c->vcur = 0;
+    c->steps_done = 0;
+    c->state = 3;
+    // initial acceleration a^0 from the forces of the initial state
+    if (int r = pd_eval_forces(c)) {
+        c->state = 2;
+        return r;
+    }
+    PD_CUDA(cudaStreamSynchronize(s));
+    // capture the step graphs on a private stream (the caller's may be the legacy stream)
+    PD_CUDA(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    for (auto &e : c->ev) PD_CUDA(cudaEventCreate(&e));
+    for (int v = 0; v < 2; ++v) {
+        if (int r = capture(c, v, kChunk, &c->chunk[v])) return r;
+        if (int r = capture(c, v, 1, &c->single[v])) return r;
+        if (int r = capture(c, v, 1, &c->timed[v], true)) return r;
+    }
+    return PD_OK;
+}
+
+int pd_eval_forces(pd_ctx *c) {
+    if (int r = check_ctx(c, 3)) return r;
+    cudaStream_t s = c->stream;
+    PD_CUDA(cudaMemsetAsync(c->d.count, 0, sizeof(int) * c->T, s));
+    PD_CUDA(pd::launch_predict(c->d, c->kp, c->vcur, 0, s));
+    PD_CUDA(pd::launch_bin(c->d, c->kp, s));
+    if (c->prm.precision == PD_FP32_SPLIT)
+        PD_CUDA(pd::launch_force_fp32(c->d, c->kp, c->vcur, 0, s));
+    else
+        PD_CUDA(pd::launch_force_fp64(c->d, c->kp, c->vcur, 0, s));
+    return PD_OK;
+}
+
+int pd_step(pd_ctx *c, int n_steps) {
+    if (int r = check_ctx(c, 3)) return r;
+    if (n_steps < 0) return fail(PD_EINVAL, "negative step count");
+    int n = n_steps;
+    if (c->timing) {
+        for (int k = 0; k < n; ++k) {
+            PD_CUDA(cudaGraphLaunch(c->timed[c->vcur], c->stream));
+            c->vcur ^= 1;
+        }
+        c->steps_done += n_steps;
+        return PD_OK;
+    }
+    while (n >= kChunk) {
+        PD_CUDA(cudaGraphLaunch(c->chunk[c->vcur], c->stream));
+        // kChunk is even: the velocity buffer parity is unchanged
+        n -= kChunk;
+    }
+    while (n > 0) {
+        PD_CUDA(cudaGraphLaunch(c->single[c->vcur], c->stream));
+        c->vcur ^= 1;
+        --n;
+    }
+    c->steps_done += n_steps;
+    return PD_OK;
+}
+
+int pd_get_state(pd_ctx *c, int field, void *dst, size_t bytes, int dst_on_device) {
+    if (int r = check_ctx(c, 1)) return r;
+    size_t fb = field_bytes(c, field);
+    if (fb == 0 && field != PD_FIELD_BROKEN && field != PD_FIELD_COL) return fail(PD_EINVAL, "unknown field");
+    if (bytes != fb) return fail(PD_EINVAL, "size mismatch for field");
+    if (!dst && fb) return fail(PD_EINVAL, "null destination");
+    if (fb == 0) return PD_OK;
+    // host-side mesh fields are available from meshing on
+    const void *host = nullptr;
+    switch (field) {
+        case PD_FIELD_X: host = c->X.data(); break;
+        case PD_FIELD_GRAIN: host = c->grain.data(); break;
+        case PD_FIELD_VOLUME: host = c->V.data(); break;
+        case PD_FIELD_LATTICE: host = c->lat.data(); break;
+        case PD_FIELD_ROW_PTR: if (c->state >= 2) host = c->row_ptr.data(); break;
+        case PD_FIELD_COL: if (c->state >= 2) host = c->col.data(); break;
+        default: break;
+    }
+    if (host) {
+        if (dst_on_device) PD_CUDA(cudaMemcpyAsync(dst, host, fb, cudaMemcpyHostToDevice, c->stream));
+        else std::memcpy(dst, host, fb);
+        if (dst_on_device) PD_CUDA(cudaStreamSynchronize(c->stream));
+        return PD_OK;
+    }
+    if (c->state < 3) return fail(PD_ESTATE, "field needs a bound arena");
+    cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const pd::DevPtrs &d = c->d;
+    cudaStream_t s = c->stream;
+    switch (field) {
+        case PD_FIELD_DISP: PD_CUDA(cudaMemcpyAsync(dst, d.u, fb, kind, s)); break;
+        case PD_FIELD_VEL: PD_CUDA(cudaMemcpyAsync(dst, d.v[c->vcur], fb, kind, s)); break;
+        case PD_FIELD_ACC: PD_CUDA(cudaMemcpyAsync(dst, d.a, fb, kind, s)); break;
+        case PD_FIELD_POS:
+            PD_CUDA(pd::launch_positions(d, c->kp, s));
+            PD_CUDA(cudaMemcpyAsync(dst, d.p, fb, kind, s));
+            break;
+        case PD_FIELD_FORCE:
+            if (!c->prm.store_parts) return fail(PD_ESTATE, "forces are kept only with store_parts");
+            PD_CUDA(cudaMemcpyAsync(dst, d.F, fb, kind, s));
+            break;
+        case PD_FIELD_FORCE_PARTS:
+            if (!c->prm.store_parts) return fail(PD_ESTATE, "forces are kept only with store_parts");
+            PD_CUDA(cudaMemcpyAsync(dst, d.parts, fb, kind, s));
+            break;
+        case PD_FIELD_STEP: PD_CUDA(cudaMemcpyAsync(dst, d.step, 8, kind, s)); break;
+        case PD_FIELD_BROKEN:
+        case PD_FIELD_DAMAGE: {
+            if (dst_on_device) return fail(PD_EINVAL, "BROKEN/DAMAGE are host-only fields");
+            std::vector<uint32_t> bits((size_t)c->N * c->wpn);
+            PD_CUDA(cudaMemcpyAsync(bits.data(), d.bits, 4 * bits.size(), cudaMemcpyDeviceToHost, s));
+            PD_CUDA(cudaStreamSynchronize(s));
+            for (int64_t x = 0; x < c->N; ++x) {
+                int r0 = c->row_ptr[x], r1 = c->row_ptr[x + 1], nbk = 0;
+                for (int b = r0; b < r1; ++b) {
+                    int k = b - r0;
+                    int br = (bits[(size_t)x * c->wpn + k / 32] >> (k % 32)) & 1u;
+                    nbk += br;
+                    if (field == PD_FIELD_BROKEN) ((uint8_t *)dst)[b] = (uint8_t)br;
+                }
+                if (field == PD_FIELD_DAMAGE) ((double *)dst)[x] = r1 > r0 ? (double)nbk / (double)(r1 - r0) : 0.0;
+            }
+            return PD_OK;
+        }
+        default: return fail(PD_EINVAL, "unknown field");
+    }
+    if (!dst_on_device) PD_CUDA(cudaStreamSynchronize(s));
+    return PD_OK;
+}
+
+int pd_set_state(pd_ctx *c, int field, const void *src, size_t bytes, int src_on_device) {
+    if (int r = check_ctx(c, 3)) return r;
+    size_t fb = field_bytes(c, field);
+    if (bytes != fb) return fail(PD_EINVAL, "size mismatch for field");
+    if (!src && fb) return fail(PD_EINVAL, "null source");
+    cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const pd::DevPtrs &d = c->d;
+    cudaStream_t s = c->stream;
+    switch (field) {
+        case PD_FIELD_DISP: PD_CUDA(cudaMemcpyAsync(d.u, src, fb, kind, s)); break;
+        case PD_FIELD_VEL: PD_CUDA(cudaMemcpyAsync(d.v[c->vcur], src, fb, kind, s)); break;
+        case PD_FIELD_ACC: PD_CUDA(cudaMemcpyAsync(d.a, src, fb, kind, s)); break;
+        case PD_FIELD_STEP: {
+            int64_t st = 0;
+            if (src_on_device) PD_CUDA(cudaMemcpy(&st, src, 8, cudaMemcpyDeviceToHost));
+            else std::memcpy(&st, src, 8);
+            PD_CUDA(cudaMemcpyAsync(d.step, src, 8, kind, s));
+            c->steps_done = st;
+            break;
+        }
+        case PD_FIELD_BROKEN: {
+            if (src_on_device) return fail(PD_EINVAL, "BROKEN is a host-only field");
+            std::vector<uint32_t> bits((size_t)c->N * c->wpn, 0u);
+            for (int64_t x = 0; x < c->N; ++x)
+                for (int b = c->row_ptr[x]; b < c->row_ptr[x + 1]; ++b) {
+                    int k = b - c->row_ptr[x];
+                    if (((const uint8_t *)src)[b]) bits[(size_t)x * c->wpn + k / 32] |= 1u << (k % 32);
+                }
+            PD_CUDA(cudaMemcpyAsync(d.bits, bits.data(), 4 * bits.size(), cudaMemcpyHostToDevice, s));
+            PD_CUDA(cudaStreamSynchronize(s));
+            return PD_OK;
+        }
+        default: return fail(PD_EINVAL, "field is not settable");
+    }
+    if (!src_on_device) PD_CUDA(cudaStreamSynchronize(s));
+    return PD_OK;
+}
+
+int pd_diagnostics(pd_ctx *c, double *out) {
+    if (int r = check_ctx(c, 3)) return r;
+    if (!out) return fail(PD_EINVAL, "null output");
+    PD_CUDA(pd::launch_diagnostics(c->d, c->kp, c->vcur, c->stream));
+    PD_CUDA(cudaMemcpyAsync(out, c->d.diag_out, 8 * PD_DIAG_COUNT, cudaMemcpyDeviceToHost, c->stream));
+    PD_CUDA(cudaStreamSynchronize(c->stream));
+    return PD_OK;
+}
+
+int pd_status(pd_ctx *c, int32_t *out) {
+    if (int r = check_ctx(c, 3)) return r;
+    int32_t st[PD_STATUS_COUNT];
+    PD_CUDA(cudaMemcpyAsync(st, c->d.status, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+    PD_CUDA(cudaStreamSynchronize(c->stream));
+    if (out) std::memcpy(out, st, sizeof(st));
+    if (st[PD_STATUS_NONFINITE]) return fail(PD_ENUMERIC, "non-finite acceleration");
+    if (st[PD_STATUS_OVERFLOW]) return fail(PD_EOVERFLOW, "contact candidate overflow");
+    return PD_OK;
+}
+
+int pd_set_timing(pd_ctx *c, int enable) {
+    if (int r = check_ctx(c, 3)) return r;
+    c->timing = enable ? 1 : 0;
+    return PD_OK;
+}
+
+int pd_kernel_times(pd_ctx *c, double *out) {
+    if (int r = check_ctx(c, 3)) return r;
+    if (!out) return fail(PD_EINVAL, "null output");
+    PD_CUDA(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    for (int k = 0; k < 3; ++k) {
+        PD_CUDA(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
+        out[k] = ms;
+    }
+    PD_CUDA(cudaEventElapsedTime(&ms, c->ev[0], c->ev[3]));
+    out[3] = ms;
+    return PD_OK;
+}
+
+int pd_info(pd_ctx *c, double *out) {
+    if (int r = check_ctx(c, 0)) return r;
+    if (!out) return fail(PD_EINVAL, "null output");
+    out[0] = (double)c->N;
+    out[1] = (double)c->col.size();
+    out[2] = (double)c->G;
+    out[3] = c->h_min;
+    out[4] = c->Rc;
+    out[5] = c->Kn;
+    out[6] = c->prm.dt;
+    out[7] = (double)c->steps_done;
+    out[8] = (double)c->max_row;
+    out[9] = (double)c->T;
+    return PD_OK;
+}
+
+}  // extern "C"

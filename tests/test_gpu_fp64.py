@@ -1,0 +1,192 @@
+"""GPU parity of the plain FP64 path against the FP64 CPU oracle.
+
+Tolerances (per-step force 1e-12 relative, displacement 1e-9 relative L2 after
+1000 steps, identical broken-bond sets) are the targets for the FP64 path.
+The kernels evaluate every expression in the same order as the oracle
+without FMA contraction, so most quantities agree bit for bit; only the wall
+terms (arcsine) and the order of contact sums can differ in the last bits.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2108_07212_gb300 import binding as B
+from paper_2108_07212_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FORCE_RTOL = 1e-12
+DISP_RTOL = 1e-9
+
+
+def _contact_disks(**over):
+    """Two disks already close: the upper one moves down at 1 m/s onto the lower
+    one, which sits R_c/4 above the floor -- contact within a few dozen steps."""
+    w = I.two_disks(**over)
+    h = 1e-3 / 8
+    rc = w.params["rc_ratio"] * h
+    w.grain_geom[0, 1] = 1e-3 + rc * 0.25 + 0.0 * h
+    w.grain_geom[1, 0] = 0.25e-3
+    w.grain_geom[1, 1] = w.grain_geom[0, 1] + 14 * h + 1.05 * rc
+    w.grain_geom[1, 5] = -1.0
+    return w
+
+
+def _gpu(w, store=True):
+    return B.Simulation(w, precision=B.PD_FP64, store_parts=store, device="cuda:0")
+
+
+def _push_state(S, P):
+    S.set("DISP", P.u)
+    S.set("VEL", P.v)
+    S.set("ACC", P.a)
+    S.set("BROKEN", P.broken[: S.n_bonds])
+    S.set("STEP", np.array([P.step], np.int64))
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def test_initial_acceleration_matches_oracle():
+    w = _contact_disks()
+    S = _gpu(w)
+    P = O.OracleProblem.from_workload(w).init_accel()
+    assert _rel(S.get("ACC"), P.a) <= FORCE_RTOL
+
+
+@pytest.mark.parametrize("steps", [60, 200, 400])
+def test_force_evaluation_matches_oracle_in_contact(steps):
+    w = _contact_disks()
+    P = O.OracleProblem.from_workload(w).init_accel()
+    P.run(steps)
+    S = _gpu(w)
+    _push_state(S, P)
+    S.eval_forces()
+    Fo, parts_o = P.forces()
+    F = S.get("FORCE")
+    parts = S.get("FORCE_PARTS")
+    assert np.abs(parts_o[2]).max() > 0 or np.abs(parts_o[3]).max() > 0   # contact or wall active
+    scale = np.abs(Fo).max()
+    assert np.abs(F - Fo).max() <= FORCE_RTOL * scale
+    for k in range(4):
+        assert np.abs(parts[k] - parts_o[k]).max() <= FORCE_RTOL * scale, k
+    assert np.array_equal(S.get("BROKEN"), P.broken[: S.n_bonds])
+
+
+def _run_both(w, n, chunks=1):
+    S = _gpu(w)
+    P = O.OracleProblem.from_workload(w).init_accel()
+    for _ in range(chunks):
+        S.step(n // chunks)
+        F_last, parts_last = P.run(n // chunks, want_parts=True)
+    return S, P, F_last, parts_last
+
+
+def _assert_parity(S, P, F_last):
+    u = S.get("DISP")
+    assert np.linalg.norm(u - P.u) <= DISP_RTOL * np.linalg.norm(P.u)
+    assert np.array_equal(S.get("BROKEN"), P.broken[: S.n_bonds])
+    assert np.abs(S.get("FORCE") - F_last).max() <= FORCE_RTOL * np.abs(F_last).max()
+    rc, st = S.status()
+    assert rc == B.PD_OK, st
+    assert int(S.get("STEP")[0]) == P.step
+
+
+def test_two_disks_1000_steps_match_oracle():
+    w = _contact_disks()
+    S, P, F_last, _ = _run_both(w, 1000, chunks=4)
+    assert np.abs(P.v).max() > 0.1
+    _assert_parity(S, P, F_last)
+
+
+def test_settling_50_grains_1000_steps_match_oracle():
+    """The 50-grain settling workload (h = R/15, dt = 5e-8) at full size."""
+    w = I.settling()
+    S, P, F_last, _ = _run_both(w, 1000)
+    assert S.N == P.N
+    _assert_parity(S, P, F_last)
+
+
+def test_fracturing_impact_breaks_identical_bonds():
+    w = _contact_disks(Gc=0.5)
+    w.grain_geom[1, 5] = -6.0
+    S, P, F_last, _ = _run_both(w, 300, chunks=3)
+    assert P.broken.sum() > 0
+    _assert_parity(S, P, F_last)
+    dmg = S.get("DAMAGE")
+    assert np.allclose(dmg, P.damage(), rtol=0, atol=0)
+
+
+def test_moving_walls_and_corners_match_oracle():
+    """Grains pushed into a corner by a moving side wall and a lowering top wall."""
+    w = I.settling(n_grains=6, box=(7e-3, 7e-3), r_range=(1e-3, 1.2e-3), seed=5, h_ratio=10, gy=-5000.0)
+    w.params["wall_vel_hi"] = (-2.0, -3.0)
+    w.params["wall_vel_lo"] = (1.0, 0.0)
+    S, P, F_last, parts = _run_both(w, 600, chunks=2)
+    assert np.abs(parts[3]).max() > 0
+    _assert_parity(S, P, F_last)
+
+
+def test_conic_micromodulus_matches_oracle():
+    w = _contact_disks(micromodulus=1)
+    S, P, F_last, _ = _run_both(w, 300)
+    _assert_parity(S, P, F_last)
+
+
+def test_diagnostics_match_oracle():
+    w = _contact_disks()
+    S, P, F_last, _ = _run_both(w, 200)
+    d = S.diagnostics()
+    o = P.diagnostics()
+    for k in ("KE", "E_bond", "Px", "Py", "Lz"):
+        assert d[k] == pytest.approx(o[k], rel=1e-9, abs=1e-30), k
+    assert d["n_broken"] == o["n_broken"]
+
+
+def test_checkpoint_resume_is_bitwise():
+    w = _contact_disks()
+    A = _gpu(w)
+    A.step(100)
+    ck = {f: A.get(f) for f in ("DISP", "VEL", "ACC", "BROKEN", "STEP")}
+    A.step(100)
+    B2 = _gpu(w)
+    for f, v in ck.items():
+        B2.set(f, v)
+    B2.step(100)
+    for f in ("DISP", "VEL", "ACC", "BROKEN"):
+        assert np.array_equal(A.get(f), B2.get(f)), f
+
+
+def test_runs_are_deterministic():
+    w = I.settling(n_grains=12, seed=9)
+    a = _gpu(w, store=False)
+    b = _gpu(w, store=False)
+    a.step(150)
+    b.step(150)
+    assert np.array_equal(a.get("DISP"), b.get("DISP"))
+    assert np.array_equal(a.get("VEL"), b.get("VEL"))
+
+
+def test_nonfinite_state_is_reported_not_faulted():
+    w = _contact_disks()
+    S = _gpu(w)
+    u = S.get("DISP")
+    u[3] = np.nan
+    S.set("DISP", u)
+    S.step(2)
+    rc, st = S.status()
+    assert rc == B.PD_ENUMERIC
+    assert st[2] > 0
+
+
+def test_single_steps_and_chunks_agree():
+    """pd_step(1) x 20 and pd_step(20) run the same captured kernels."""
+    w = _contact_disks()
+    a = _gpu(w, store=False)
+    b = _gpu(w, store=False)
+    for _ in range(20):
+        a.step(1)
+    b.step(20)
+    assert np.array_equal(a.get("DISP"), b.get("DISP"))
+    assert np.array_equal(a.get("VEL"), b.get("VEL"))
