@@ -269,27 +269,107 @@ double or_contact_stiffness(double k_bulk, double eps)
     return 18.0 * k_bulk / (OR_PI * eps * eps * eps * eps * eps);
 }
 
-/* Single-wall contact region S_l, Sec. 4.5: area of the circular segment of   */
-/* B_{R_c}(p) beyond a line at distance d, and distance from p to its centroid. */
-void or_wall_segment(double d, double Rc, double *area, double *cdist)
+/* Single-wall contact region S_l, Sec. 4.5: the circular segment of B_{R_c}(p)
+ * beyond a line at distance d.  The paper's closed forms
+ *   |S_l| = pi R^2/2 - R^2 asin(d/R) - sqrt(R^2 - d^2) d,
+ *   |c_l - p| = 2/3 (R^2 - d^2)^{3/2} / |S_l|
+ * cancel catastrophically as d -> R (the segment vanishes), so they are
+ * evaluated through the half-angle theta = acos(d/R) = atan2(sqrt(R^2-d^2), d):
+ *   |S_l| = R^2 h1(theta),  h1 = theta - sin(theta) cos(theta),
+ *   R - |c_l - p| = R g(theta) / h1(theta),  g = h1 - 2/3 sin^3(theta),
+ * with the Taylor series of h1 and g (g starts at 0.2 theta^5) for small theta.
+ * gap returns R_c - |c_l - p|, the factor of eq. (wall-repulsive). */
+static void segment_shape(double th, double *h1, double *g)
 {
-    double q = Rc * Rc - d * d;
-    double A = 0.5 * OR_PI * Rc * Rc - Rc * Rc * asin(d / Rc) - sqrt(q) * d;
-    *area = A;
-    *cdist = (2.0 / 3.0) * (q * sqrt(q)) / A;
+    if (th < 0.3) {
+        double t2 = th * th;
+        /* h1 = sum_{k>=1} (-1)^{k+1} 4^k th^{2k+1} / (2k+1)! */
+        double term = 4.0 * th * t2 / 6.0, sum = 0.0;
+        for (int k = 1; k <= 12; ++k) {
+            sum += term;
+            term *= -4.0 * t2 / ((2.0 * k + 2.0) * (2.0 * k + 3.0));
+        }
+        *h1 = sum;
+        /* g = sum_{k>=2} (-1)^k (3^{2k+1}/6 - 4^k - 1/2) th^{2k+1} / (2k+1)! */
+        double t5 = t2 * t2 * th;
+        double a = 243.0 / 6.0 * t5 / 120.0, b = 16.0 * t5 / 120.0, e = 0.5 * t5 / 120.0;
+        double gs = 0.0;
+        for (int k = 2; k <= 14; ++k) {
+            gs += a - b - e;
+            double den = (2.0 * k + 2.0) * (2.0 * k + 3.0);
+            a *= -9.0 * t2 / den;
+            b *= -4.0 * t2 / den;
+            e *= -t2 / den;
+        }
+        *g = gs;
+    } else {
+        double sn = sin(th), cs = cos(th);
+        *h1 = th - sn * cs;
+        *g = *h1 - (2.0 / 3.0) * sn * sn * sn;
+    }
 }
 
-/* Corner region S_li cap S_lj, Sec. 4.5 (polar-coordinate integrals): area   */
-/* and first moments I_x (along the direction towards l_i, distance d_i) and  */
-/* I_y (towards l_j, distance d_j).                                           */
+void or_wall_segment_gap(double d, double Rc, double *area, double *gap)
+{
+    double q = (Rc - d) * (Rc + d);
+    double th = atan2(sqrt(q), d);
+    double h1, g;
+    segment_shape(th, &h1, &g);
+    *area = Rc * Rc * h1;
+    *gap = Rc * g / h1;
+}
+
+void or_wall_segment(double d, double Rc, double *area, double *cdist)
+{
+    double gap;
+    or_wall_segment_gap(d, Rc, area, &gap);
+    *cdist = Rc - gap;
+}
+
+/* Corner region S_li cap S_lj, Sec. 4.5.  Local frame: x towards l_i (at
+ * distance d_i), y towards l_j (distance d_j), p at the origin; the region is
+ * {x >= d_i, y >= d_j, |.| <= R}.  The paper's polar integrals for the area
+ * and the moments I_x, I_y cancel as the corner point approaches the circle,
+ * so the same region is split into the triangle Q P1 P2 (Q = (d_i, d_j),
+ * P1 = (b, d_j), P2 = (d_i, c) on the circle) and the circular segment cut by
+ * the chord P1 P2 (angle dth); both parts have positive area.  Returns the
+ * area and the first moments I_x, I_y (centroid = (I_x, I_y) / area). */
 void or_corner_region(double di, double dj, double Rc, double *area, double *Ix, double *Iy)
 {
-    double R2 = Rc * Rc;
-    double qi = R2 - di * di, qj = R2 - dj * dj;
-    *area = -0.5 * R2 * asin(di / Rc) + 0.5 * R2 * asin(sqrt(qj) / Rc) + di * dj
-            - 0.5 * sqrt(qi) * di - 0.5 * sqrt(qj) * dj;
-    *Ix = dj * dj * dj / 6.0 - 0.5 * qi * dj + (qi * sqrt(qi)) / 3.0;
-    *Iy = -0.5 * R2 * di + di * di * di / 6.0 + 0.5 * di * dj * dj + (qj * sqrt(qj)) / 3.0;
+    double b = sqrt((Rc - dj) * (Rc + dj)), c = sqrt((Rc - di) * (Rc + di));
+    double w = (Rc - di) * (Rc + di) - dj * dj;          /* R^2 - di^2 - dj^2 >= 0 */
+    double bmi = w / (b + di), cmj = w / (c + dj);        /* b - di, c - dj */
+    double T = 0.5 * bmi * cmj;
+    double cr = b * cmj + dj * bmi;                       /* P1 x P2 = b c - di dj */
+    double dt = b * di + dj * c;                          /* P1 . P2 */
+    double dth = atan2(cr, dt);
+    double f;                                             /* dth - sin(dth) */
+    if (dth < 0.5) {
+        double t2 = dth * dth, term = dth * t2 / 6.0;
+        f = 0.0;
+        for (int k = 1; k <= 12; ++k) {
+            f += term;
+            term *= -t2 / ((2.0 * k + 2.0) * (2.0 * k + 3.0));
+        }
+    } else {
+        f = dth - sin(dth);
+    }
+    double Sg = 0.5 * Rc * Rc * f;
+    /* segment centroid: on the chord bisector, at 4 R sin^3(dth/2) / (3 (dth - sin dth)) */
+    double mx = b + di, my = dj + c, ml = sqrt(mx * mx + my * my);
+    double s2 = sin(0.5 * dth);
+    double sd;
+    if (dth < 0.5) {
+        /* 4 sin^3(x/2) / (3 (x - sin x)) -> 1 as x -> 0: evaluate as ratio of series-safe parts */
+        sd = (dth > 0.0) ? Rc * (4.0 * s2 * s2 * s2) / (3.0 * f) : Rc;
+    } else {
+        sd = Rc * (4.0 * s2 * s2 * s2) / (3.0 * f);
+    }
+    double sgx = sd * mx / ml, sgy = sd * my / ml;
+    double tx = (di + b + di) / 3.0, ty = (dj + dj + c) / 3.0;
+    *area = Sg + T;
+    *Ix = Sg * sgx + T * tx;
+    *Iy = Sg * sgy + T * ty;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -470,12 +550,11 @@ static void wall_force(const or_sys *S, int x, double *fx, double *fy)
     double Fx = 0.0, Fy = 0.0;
     for (int l = 0; l < 4; ++l) {
         if (!(d[l] < Rc)) continue;
-        double A, cd;
-        or_wall_segment(d[l], Rc, &A, &cd);
-        /* as d -> R_c the segment vanishes and the closed form cancels; a region
-           with no positive area or a centroid not inside B_Rc exerts no force */
-        if (!(A > 0.0) || !(cd < Rc)) continue;
-        double Fr = Kn * (Rc - cd) * Vx * A;
+        double A, gap;
+        or_wall_segment_gap(d[l], Rc, &A, &gap);
+        /* a vanished region (no positive area) exerts no force */
+        if (!(A > 0.0) || !(gap > 0.0)) continue;
+        double Fr = Kn * gap * Vx * A;
         double wvx = (l < 2) ? wvel[l] : 0.0, wvy = (l < 2) ? 0.0 : wvel[l];
         double gx = -Fr * ex[l], gy = -Fr * ey[l];
         damping_friction(prm, ex[l], ey[l], vx - wvx, vy - wvy, Fr, Vx, A, &gx, &gy);

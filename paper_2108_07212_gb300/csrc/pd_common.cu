@@ -30,6 +30,13 @@ __global__ void __launch_bounds__(kBlock) k_predict(DevPtrs d, KParams k, int vi
     double2 X = d.X[i];
     double2 p = make_double2(X.x + u.x, X.y + u.y);
     d.p[i] = p;
+    if (d.ph) {
+        // FP32-split path: the shifted position as a float-float pair
+        double qx = p.x + k.sx, qy = p.y + k.sy;
+        float2 ph = make_float2((float)qx, (float)qy);
+        d.ph[i] = ph;
+        d.pl[i] = make_float2((float)(qx - (double)ph.x), (float)(qy - (double)ph.y));
+    }
     unsigned b = cell_bucket(cell_coord(p.x, k.ox, k.cell), cell_coord(p.y, k.oy, k.cell), k.T);
     d.key[i] = (int)b;
     atomicAdd(&d.count[b], 1);

@@ -42,14 +42,88 @@ __device__ __forceinline__ void damping_friction64(const KParams &k, double ex, 
     fy += Fdy + Ffy;
 }
 
+// Circular segment of B_R(p) beyond a line at distance d < R (Sec. 4.5).
+// With theta = acos(d/R) = atan2(sqrt(R^2 - d^2), d) the paper's closed forms
+// read |S| = R^2 (theta - sin theta cos theta) and
+// R - |c - p| = R (h1 - 2/3 sin^3 theta) / h1; both are evaluated without
+// cancellation (Taylor series in theta below 0.3), because the printed
+// pi R^2/2 - R^2 asin(d/R) - d sqrt(R^2 - d^2) loses all digits as d -> R.
+__device__ __forceinline__ void wall_segment_stable(double d, double R, double &area, double &gap) {
+    const double th = atan2(sqrt((R - d) * (R + d)), d);
+    double h1, g;
+    if (th < 0.3) {
+        const double t2 = th * th;
+        double term = (4.0 / 6.0) * th * t2;
+        h1 = 0.0;
+#pragma unroll
+        for (int k = 1; k <= 12; ++k) {
+            h1 += term;
+            term *= -4.0 * t2 / ((2.0 * k + 2.0) * (2.0 * k + 3.0));
+        }
+        const double t5 = t2 * t2 * th;
+        double a = (243.0 / 6.0 / 120.0) * t5, b = (16.0 / 120.0) * t5, e = (0.5 / 120.0) * t5;
+        g = 0.0;
+#pragma unroll
+        for (int k = 2; k <= 14; ++k) {
+            g += a - b - e;
+            const double den = (2.0 * k + 2.0) * (2.0 * k + 3.0);
+            a *= -9.0 * t2 / den;
+            b *= -4.0 * t2 / den;
+            e *= -t2 / den;
+        }
+    } else {
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        h1 = th - sn * cs;
+        g = h1 - (2.0 / 3.0) * sn * sn * sn;
+    }
+    area = R * R * h1;
+    gap = R * g / h1;
+}
+
+// Corner region S_li cap S_lj (Sec. 4.5) in the frame x -> wall i, y -> wall j:
+// {x >= di, y >= dj, |.| <= R}, split into the triangle Q P1 P2 (Q = (di, dj),
+// P1 = (b, dj), P2 = (di, c) on the circle) and the circular segment cut by
+// the chord P1 P2, so the area and the centroid stay accurate as the corner
+// point approaches the circle (the paper's polar integrals cancel there).
+__device__ __forceinline__ void corner_region_stable(double di, double dj, double R, double &area, double &cx,
+                                                     double &cy) {
+    const double b = sqrt((R - dj) * (R + dj)), c = sqrt((R - di) * (R + di));
+    const double w = (R - di) * (R + di) - dj * dj;
+    const double bmi = w / (b + di), cmj = w / (c + dj);
+    const double T = 0.5 * bmi * cmj;
+    const double dth = atan2(b * cmj + dj * bmi, b * di + dj * c);
+    double f;
+    if (dth < 0.5) {
+        const double t2 = dth * dth;
+        double term = dth * t2 / 6.0;
+        f = 0.0;
+#pragma unroll
+        for (int k = 1; k <= 12; ++k) {
+            f += term;
+            term *= -t2 / ((2.0 * k + 2.0) * (2.0 * k + 3.0));
+        }
+    } else {
+        f = dth - sin(dth);
+    }
+    const double Sg = 0.5 * R * R * f;
+    const double mx = b + di, my = dj + c, ml = sqrt(mx * mx + my * my);
+    const double s2 = sin(0.5 * dth);
+    const double sd = (dth > 0.0) ? R * (4.0 * s2 * s2 * s2) / (3.0 * f) : R;
+    const double A = Sg + T;
+    area = A;
+    cx = (Sg * (sd * mx / ml) + T * ((di + b + di) / 3.0)) / A;
+    cy = (Sg * (sd * my / ml) + T * ((dj + dj + c) / 3.0)) / A;
+}
+
 // Wall contact (Sec. 4.5, eq:wall-repulsive, eq:wall-total) of a node at p
 // with velocity v and volume Vx against the four walls at positions wn[0..3]
 // (x_lo, x_hi, y_lo, y_hi) moving with normal velocities k.wv.  The repulsion
-// of each wall uses the circular segment S_l of B_Rc(p) beyond the wall (area
-// and centroid distance in closed form); corners subtract the S_li cap S_lj
-// term (inclusion-exclusion); friction and damping follow by substituting
-// e -> e^l, V_y -> |S_l|, p(y) -> c_l.  A node past a wall is treated as
-// touching it and counted in status[PD_STATUS_PENETRATION].
+// of each wall uses the circular segment S_l of B_Rc(p) beyond the wall;
+// corners subtract the S_li cap S_lj term (inclusion-exclusion); friction and
+// damping follow by substituting e -> e^l, V_y -> |S_l|, p(y) -> c_l.  A node
+// past a wall is treated as touching it and counted in
+// status[PD_STATUS_PENETRATION].
 __device__ __forceinline__ void wall_force64(const KParams &k, const double *wn, double px, double py, double vx,
                                              double vy, double Vx, double &Fx_out, double &Fy_out, int *status) {
     const double Rc = k.Rc, Kn = k.Kn;
@@ -69,33 +143,26 @@ __device__ __forceinline__ void wall_force64(const KParams &k, const double *wn,
     }
     double Fx = 0.0, Fy = 0.0;
     if (near) {
-        const double R2 = Rc * Rc;
-#pragma unroll
         for (int l = 0; l < 4; ++l) {
             if (!(d[l] < Rc)) continue;
-            double q = R2 - d[l] * d[l];
-            double A = 0.5 * 3.14159265358979323846 * Rc * Rc - Rc * Rc * asin(d[l] / Rc) - sqrt(q) * d[l];
-            double cd = (2.0 / 3.0) * (q * sqrt(q)) / A;
-            if (!(A > 0.0) || !(cd < Rc)) continue;
-            double Fr = Kn * (Rc - cd) * Vx * A;
+            double A, gap;
+            wall_segment_stable(d[l], Rc, A, gap);
+            if (!(A > 0.0) || !(gap > 0.0)) continue;
+            double Fr = Kn * gap * Vx * A;
             double wvx = (l < 2) ? k.wv[l] : 0.0, wvy = (l < 2) ? 0.0 : k.wv[l];
             double gx = -Fr * ex[l], gy = -Fr * ey[l];
             damping_friction64(k, ex[l], ey[l], vx - wvx, vy - wvy, Fr, Vx, A, gx, gy);
             Fx += gx;
             Fy += gy;
         }
-#pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int i = c >> 1, j = 2 + (c & 1);  // (x_lo|x_hi) x (y_lo|y_hi)
             double di = d[i], dj = d[j];
             if (!(sqrt(di * di + dj * dj) < Rc)) continue;
-            double qi = R2 - di * di, qj = R2 - dj * dj;
-            double A = -0.5 * R2 * asin(di / Rc) + 0.5 * R2 * asin(sqrt(qj) / Rc) + di * dj - 0.5 * sqrt(qi) * di -
-                       0.5 * sqrt(qj) * dj;
+            double A, lx, ly;
+            corner_region_stable(di, dj, Rc, A, lx, ly);
             if (!(A > 0.0)) continue;
-            double Ix = dj * dj * dj / 6.0 - 0.5 * qi * dj + (qi * sqrt(qi)) / 3.0;
-            double Iy = -0.5 * R2 * di + di * di * di / 6.0 + 0.5 * di * dj * dj + (qj * sqrt(qj)) / 3.0;
-            double cx = (Ix * ex[i] + Iy * ex[j]) / A, cy = (Ix * ey[i] + Iy * ey[j]) / A;
+            double cx = lx * ex[i] + ly * ex[j], cy = lx * ey[i] + ly * ey[j];
             double cd = sqrt(cx * cx + cy * cy);
             if (!(cd < Rc) || !(cd > 0.0)) continue;
             double ux = cx / cd, uy = cy / cd;

@@ -247,13 +247,14 @@ size_t layout(pd_ctx *c, char *base) {
     carve(base, off, d.diag_part, (size_t)c->kp.n_diag_blocks * PD_DIAG_COUNT);
     carve(base, off, d.diag_out, PD_DIAG_COUNT);
     if (c->prm.precision == PD_FP32_SPLIT) {
-        carve(base, off, d.Xl, N);
-        carve(base, off, d.gc, G);
-        carve(base, off, d.xi_f, nb);
+        carve(base, off, d.lat, N);
+        carve(base, off, d.gq, G);
+        carve(base, off, d.ph, N);
+        carve(base, off, d.pl, N);
     } else {
-        d.Xl = nullptr;
-        d.gc = nullptr;
-        d.xi_f = nullptr;
+        d.lat = nullptr;
+        d.gq = nullptr;
+        d.ph = d.pl = nullptr;
     }
     return off;
 }
@@ -269,18 +270,18 @@ int check_ctx(pd_ctx *c, int min_state) {
 // `timed`, event records bracket the three kernel groups.
 cudaError_t record_step(pd_ctx *c, int vin, cudaStream_t s, bool timed = false) {
     cudaError_t e;
-    if (timed && (e = cudaEventRecord(c->ev[0], s)) != cudaSuccess) return e;
+    if (timed && (e = cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->d.count, 0, sizeof(int) * c->T, s)) != cudaSuccess) return e;
     if ((e = pd::launch_predict(c->d, c->kp, vin, 1, s)) != cudaSuccess) return e;
-    if (timed && (e = cudaEventRecord(c->ev[1], s)) != cudaSuccess) return e;
+    if (timed && (e = cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     if ((e = pd::launch_bin(c->d, c->kp, s)) != cudaSuccess) return e;
-    if (timed && (e = cudaEventRecord(c->ev[2], s)) != cudaSuccess) return e;
+    if (timed && (e = cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     if (c->prm.precision == PD_FP32_SPLIT)
         e = pd::launch_force_fp32(c->d, c->kp, vin, 1, s);
     else
         e = pd::launch_force_fp64(c->d, c->kp, vin, 1, s);
     if (e != cudaSuccess) return e;
-    if (timed && (e = cudaEventRecord(c->ev[3], s)) != cudaSuccess) return e;
+    if (timed && (e = cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -589,6 +590,19 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     k.cell = c->Rc;
     k.ox = p.wall_lo[0];
     k.oy = p.wall_lo[1];
+    // FP32-split: shift coordinates into [L, 2L) so nearby positions share a
+    // binade and their float differences are exact (Sterbenz)
+    {
+        double Lx = std::max(p.wall_hi[0] - p.wall_lo[0], 1e-6), Ly = std::max(p.wall_hi[1] - p.wall_lo[1], 1e-6);
+        k.sx = Lx - p.wall_lo[0];
+        k.sy = Ly - p.wall_lo[1];
+    }
+    k.guard = 1e-4f;
+    {
+        double rc2 = c->Rc * c->Rc;
+        k.rc2_hi = (float)rc2;
+        k.rc2_lo = (float)(rc2 - (double)k.rc2_hi);
+    }
     k.micro = p.micromodulus;
     k.store = p.store_parts ? 1 : 0;
     cudaStream_t s = c->stream;
@@ -614,25 +628,20 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     PD_CUDA(cudaMemcpyAsync(d.g_eps, c->g_eps.data(), 8 * G, cudaMemcpyHostToDevice, s));
     PD_CUDA(cudaMemsetAsync(d.step, 0, 8, s));
     PD_CUDA(cudaMemsetAsync(d.status, 0, 4 * PD_STATUS_COUNT, s));
-    std::vector<float> xl, xif;
-    std::vector<double> gcv;
+    std::vector<float> gq;
     if (p.precision == PD_FP32_SPLIT) {
-        // grain-local FP32 reference coordinates relative to each grain's centre
-        xl.resize(2 * N);
-        gcv.resize(2 * G);
+        // per grain: h, h^2 as a float-float pair, V as float
+        gq.resize(4 * G);
         for (size_t g = 0; g < G; ++g) {
-            gcv[2 * g] = c->g_cx[g];
-            gcv[2 * g + 1] = c->g_cy[g];
-            for (int64_t x = c->g_start[g]; x < c->g_start[g + 1]; ++x) {
-                xl[2 * x] = (float)(c->X[2 * x] - c->g_cx[g]);
-                xl[2 * x + 1] = (float)(c->X[2 * x + 1] - c->g_cy[g]);
-            }
+            double h = c->g_h[g], h2 = h * h;
+            float hi = (float)h2;
+            gq[4 * g] = (float)h;
+            gq[4 * g + 1] = hi;
+            gq[4 * g + 2] = (float)(h2 - (double)hi);
+            gq[4 * g + 3] = (float)c->V[c->g_start[g]];
         }
-        xif.resize(std::max<size_t>(nb, 1));
-        for (size_t b = 0; b < nb; ++b) xif[b] = (float)c->xi[b];
-        PD_CUDA(cudaMemcpyAsync(d.Xl, xl.data(), 8 * N, cudaMemcpyHostToDevice, s));
-        PD_CUDA(cudaMemcpyAsync(d.gc, gcv.data(), 16 * G, cudaMemcpyHostToDevice, s));
-        if (nb) PD_CUDA(cudaMemcpyAsync(d.xi_f, xif.data(), 4 * nb, cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.lat, c->lat.data(), 8 * N, cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.gq, gq.data(), 16 * G, cudaMemcpyHostToDevice, s));
     }
     c->vcur = 0;
     c->steps_done = 0;

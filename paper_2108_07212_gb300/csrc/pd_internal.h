@@ -37,9 +37,9 @@ struct DevPtrs {
     double *diag_part;  // per-block diagnostic partial sums
     double *diag_out;   // PD_DIAG_COUNT
     // FP32-split path
-    float2 *Xl;         // grain-local FP32 reference coordinates (X - grain centre)
-    double2 *gc;        // per-grain FP64 reference centre
-    float *xi_f;        // FP32 |xi| per bond
+    int2 *lat;          // lattice indices (i, j) of every node in its grain frame
+    float4 *gq;         // per grain: (h, h^2 hi, h^2 lo, V = h^2 as float)
+    float2 *ph, *pl;    // shifted position (p + shift) as a float-float pair
 };
 
 // By-value kernel parameters (baked into captured graphs).
@@ -49,6 +49,9 @@ struct KParams {
     double rho, Kn, Rc, rd, mu, gx, gy, dt, half_dt, half_dt2;
     double w0[4], wv[4];
     double cell, ox, oy;
+    double sx, sy;      // FP32-split position shift: coordinates map to [box, 2 box)
+    float rc2_hi, rc2_lo;  // R_c^2 as a float-float pair
+    float guard;        // FP32-split: |(|s| - s0)| < guard * s0 re-decides breaking in FP64
     int micro, store;
 };
 

@@ -1,0 +1,107 @@
+"""FP32-split path: per-step force error against the FP64 oracle (<= 1e-5 of the
+largest nodal force, from the same state), break decisions equal to the FP64
+path's, and trajectories that stay close to the FP64 ones."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2108_07212_gb300 import binding as B
+from paper_2108_07212_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FORCE_RTOL_FP32 = 1e-5
+
+
+def _contact_disks(**over):
+    w = I.two_disks(**over)
+    h = 1e-3 / 8
+    rc = w.params["rc_ratio"] * h
+    w.grain_geom[0, 1] = 1e-3 + rc * 0.25
+    w.grain_geom[1, 0] = 0.25e-3
+    w.grain_geom[1, 1] = w.grain_geom[0, 1] + 14 * h + 1.05 * rc
+    w.grain_geom[1, 5] = -1.0
+    return w
+
+
+def _sim(w, prec, store=True):
+    return B.Simulation(w, precision=prec, store_parts=store, device="cuda:0")
+
+
+def _push(S, P):
+    S.set("DISP", P.u)
+    S.set("VEL", P.v)
+    S.set("ACC", P.a)
+    S.set("BROKEN", P.broken[: S.n_bonds])
+    S.set("STEP", np.array([P.step], np.int64))
+
+
+def _thrown_settling():
+    """The 50-grain settling aggregate thrown at the floor (vy = -5 m/s), so that
+    wall and grain contacts are loaded within a few hundred steps."""
+    w = I.settling()
+    P = O.OracleProblem.from_workload(w)
+    w.grain_geom[:, 1] -= P.X[:, 1].min() - 1.2 * P.prm[O.P_RC]     # lowest node just above the floor
+    w.grain_geom[:, 5] = -5.0
+    return w
+
+
+@pytest.mark.parametrize("case,steps", [("disks", 100), ("disks", 400), ("settling", 300)])
+def test_fp32_force_error_against_oracle(case, steps):
+    """Per-step force error from the same (loaded) state: the FP32-split forces
+    against the FP64 oracle, relative to the largest nodal force."""
+    w = _contact_disks() if case == "disks" else _thrown_settling()
+    P = O.OracleProblem.from_workload(w).init_accel()
+    P.run(steps)
+    S = _sim(w, B.PD_FP32_SPLIT)
+    _push(S, P)
+    S.eval_forces()
+    Fo, parts_o = P.forces()
+    F = S.get("FORCE")
+    assert np.abs(parts_o[2]).max() > 0 or np.abs(parts_o[3]).max() > 0
+    err = np.abs(F - Fo).max() / np.abs(Fo).max()
+    assert err <= FORCE_RTOL_FP32, err
+    assert np.array_equal(S.get("BROKEN"), P.broken[: S.n_bonds])
+
+
+def test_fp32_bond_force_error_far_from_origin():
+    """Large rigid motion (grain translated by 3 mm): the float-float relative
+    displacement keeps the bond forces accurate."""
+    w = _contact_disks()
+    P = O.OracleProblem.from_workload(w).init_accel()
+    P.run(150)
+    P.u[:, 0] += 3e-3
+    P.u[:, 1] += 2e-3
+    S = _sim(w, B.PD_FP32_SPLIT)
+    _push(S, P)
+    S.eval_forces()
+    Fo, parts_o = P.forces()
+    parts = S.get("FORCE_PARTS")
+    err = np.abs(parts[0] - parts_o[0]).max() / np.abs(parts_o[0]).max()
+    assert err <= FORCE_RTOL_FP32, err
+
+
+def test_fp32_breaks_same_bonds_as_fp64_in_fracturing_impact():
+    w = _contact_disks(Gc=0.5)
+    w.grain_geom[1, 5] = -6.0
+    a = _sim(w, B.PD_FP64, store=False)
+    b = _sim(w, B.PD_FP32_SPLIT, store=False)
+    for _ in range(6):
+        a.step(50)
+        b.step(50)
+    ba, bb = a.get("BROKEN"), b.get("BROKEN")
+    assert ba.sum() > 0
+    assert int(np.sum(ba != bb)) == 0
+    assert np.array_equal(a.get("DAMAGE"), b.get("DAMAGE"))
+
+
+def test_fp32_trajectory_tracks_fp64():
+    w = I.settling()
+    a = _sim(w, B.PD_FP64, store=False)
+    b = _sim(w, B.PD_FP32_SPLIT, store=False)
+    a.step(1000)
+    b.step(1000)
+    ua, ub = a.get("DISP"), b.get("DISP")
+    assert np.linalg.norm(ub - ua) <= 1e-5 * np.linalg.norm(ua)
+    rc, st = b.status()
+    assert rc == B.PD_OK

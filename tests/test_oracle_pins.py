@@ -304,12 +304,28 @@ def test_wall_segment_area_and_centroid_by_quadrature():
         assert c == pytest.approx(Mq / Aq, rel=1e-9)
 
 
+def test_wall_segment_stays_accurate_as_it_vanishes():
+    """As d -> R_c the region shrinks to nothing; area and R_c - |c - p| must keep
+    full relative precision (50-digit evaluation of the same integrals)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    Rc = 1.3e-4
+    for f in (0.99, 0.9999, 0.999999, 0.99999999):
+        d = f * Rc
+        R, D = mpmath.mpf(Rc), mpmath.mpf(d)
+        A = R * R * mpmath.acos(D / R) - D * mpmath.sqrt(R * R - D * D)
+        c = mpmath.mpf(2) / 3 * (R * R - D * D) ** mpmath.mpf(1.5) / A
+        A_o, c_o = O.wall_segment(d, Rc)
+        assert float(abs(A_o - A) / A) < 1e-12
+        assert float(abs((Rc - c_o) - (R - c)) / (R - c)) < 1e-9
+
+
 def test_corner_region_area_and_moments_by_quadrature():
     Rc = 1.3e-4
     A, Ix, Iy = O.corner_region(0.0, 0.0, Rc)
     assert A == pytest.approx(math.pi * Rc ** 2 / 4, rel=1e-14)         # quarter disk (paper)
     assert Ix == pytest.approx(Iy, rel=1e-14)
-    for fi, fj in [(0.1, 0.3), (0.5, 0.2), (0.6, 0.7), (0.0, 0.9), (0.3, 0.0)]:
+    for fi, fj in [(0.1, 0.3), (0.5, 0.2), (0.6, 0.7), (0.0, 0.9), (0.3, 0.0), (0.6, 0.79), (0.7071, 0.7071)]:
         di, dj = fi * Rc, fj * Rc
         if di * di + dj * dj >= Rc * Rc:
             continue
@@ -324,9 +340,9 @@ def test_corner_region_area_and_moments_by_quadrature():
         Ixq = quad(lambda f: Rc * math.sin(f) * (Rc * math.cos(f) - dj) * jac(f), f0, f1, **kw)[0]
         Iyq = quad(lambda f: 0.5 * ((Rc * math.cos(f)) ** 2 - dj * dj) * jac(f), f0, f1, **kw)[0]
         A, Ix, Iy = O.corner_region(di, dj, Rc)
-        assert A == pytest.approx(Aq, rel=1e-9)
-        assert Ix == pytest.approx(Ixq, rel=1e-9)
-        assert Iy == pytest.approx(Iyq, rel=1e-9)
+        assert A == pytest.approx(Aq, rel=1e-8)
+        assert Ix == pytest.approx(Ixq, rel=1e-8)
+        assert Iy == pytest.approx(Iyq, rel=1e-8)
 
 
 # ---------------------------------------------------------------------------
