@@ -236,6 +236,38 @@ int pd_set_timing(pd_ctx *ctx, int enable);
  * timing enabled (waits for the stream): out[PD_TIMER_*]. */
 int pd_kernel_times(pd_ctx *ctx, double *out);
 
+/* ---- diagnostics without device allocation ---------------------------------- */
+#define PD_NOALLOC_MAX_NODES 2097152
+
+/*
+ * The reductions of pd_diagnostics for callers that cannot allocate device
+ * memory (their device memory comes from a fixed budget or another runtime,
+ * or an allocation would synchronise the device inside their loop).  The
+ * paper has no counterpart: this is a deployment variant of the diagnostics
+ * kernel whose scratch (per-block partial sums, 64 KiB) is a fixed device
+ * array inside the library, held by every GPU that loads the library until
+ * the process exits.  The call allocates nothing.
+ *   n_nodes   N, 0 <= N <= PD_NOALLOC_MAX_NODES (larger: PD_EINVAL)
+ *   X, u, v   device double[2N] reference positions, displacements, velocities
+ *   V         device double[N] nodal volumes;  grain device int32[N]
+ *   row_ptr   device int32[N+1], col device int32[n_bonds] (bond lists as
+ *             PD_FIELD_ROW_PTR / PD_FIELD_COL), broken device uint8[n_bonds]
+ *   g_cw, g_eps  device double[G] per-grain c_w and horizon
+ *   rho, micromodulus as in pd_params
+ *   out       device double[PD_DIAG_COUNT] (same slots as pd_diagnostics)
+ *   cuda_stream  the stream the work is enqueued on (returns without waiting)
+ * The first call on a device, with that device current, looks up the device
+ * address of the scratch array; make that first call before any stream
+ * capture.  All calls share the scratch: calls that overlap on the GPU (on
+ * different streams, or concurrently from several threads) race.  Nothing
+ * needs clearing between calls: each call overwrites every partial it reads.
+ * Errors: PD_EINVAL (size, null pointer), PD_ECUDA.
+ */
+int pd_diagnostics_noalloc(int n_nodes, const double *X, const double *u, const double *v, const double *V,
+                           const int32_t *grain, const int32_t *row_ptr, const int32_t *col,
+                           const uint8_t *broken, const double *g_cw, const double *g_eps, double rho,
+                           int micromodulus, double *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

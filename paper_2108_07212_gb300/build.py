@@ -26,6 +26,7 @@ CU_SOURCES = [
     ("pd_common.cu", ["-fmad=false"]),
     ("pd_force_fp64.cu", ["-fmad=false"]),
     ("pd_force_fp32.cu", []),
+    ("pd_noalloc.cu", []),
 ]
 CPP_SOURCES = ["pd_host.cpp"]
 

@@ -322,6 +322,8 @@ size_t field_bytes(pd_ctx *c, int f) {
 
 }  // namespace
 
+int pd::set_error(int code, const char *msg) { return fail(code, msg); }
+
 // ===========================================================================
 // C ABI
 

@@ -55,6 +55,9 @@ struct KParams {
     int micro, store;
 };
 
+// Record an error for pd_last_error() and return `code`.
+int set_error(int code, const char *msg);
+
 // Launch wrappers (stream-ordered, capture-safe).
 cudaError_t launch_predict(const DevPtrs &d, const KParams &k, int vin, int advance, cudaStream_t s);
 cudaError_t launch_bin(const DevPtrs &d, const KParams &k, cudaStream_t s);
