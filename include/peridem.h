@@ -84,7 +84,9 @@ typedef struct pd_params {
     int32_t precision;      /* PD_FP64 or PD_FP32_SPLIT                         */
     int32_t store_parts;    /* nonzero: keep the four force parts of the last   */
                             /* evaluation (bond|self|neighbour|wall), for tests */
-    int32_t reserved;
+    int32_t lanes;          /* threads per node in the force kernels: 1, 4, 8,  */
+                            /* or 0 for the default (8); 1 sums every force in  */
+                            /* the textbook order of eq:full                    */
 } pd_params;
 
 /* ---- state fields (pd_get_state / pd_set_state) ---------------------------- */
@@ -109,6 +111,7 @@ typedef struct pd_params {
 #define PD_STATUS_COINCIDENT 1  /* two nodes at the same position (pair skipped)    */
 #define PD_STATUS_NONFINITE 2   /* non-finite acceleration                          */
 #define PD_STATUS_OVERFLOW 3    /* contact candidates beyond the per-node capacity  */
+#define PD_STATUS_TIMEOUT 4     /* a grid barrier of the persistent kernel gave up  */
 #define PD_STATUS_COUNT 8
 
 /* ---- diagnostics (pd_diagnostics) ------------------------------------------- */
@@ -216,10 +219,46 @@ int pd_diagnostics(pd_ctx *ctx, double *out);
  * PD_OK, or the first error code it implies (PD_ENUMERIC, PD_EOVERFLOW). */
 int pd_status(pd_ctx *ctx, int32_t *out);
 
-/* Scalar facts of the context: out[0] N, out[1] directed bonds, out[2] grains,
- * out[3] h_min, out[4] R_c, out[5] K_n, out[6] dt, out[7] completed steps,
- * out[8] max bonds per node, out[9] contact hash buckets. */
+/* Scalar facts of the context (out has 14 slots): out[0] N, out[1] directed
+ * bonds, out[2] grains, out[3] h_min, out[4] R_c, out[5] K_n (aggregate 0),
+ * out[6] dt, out[7] completed steps, out[8] max bonds per node, out[9] contact
+ * hash buckets, out[10] step path (0 graph of kernels, 1 persistent kernel),
+ * out[11] threads per node, out[12] threads per block of the persistent
+ * kernel, out[13] aggregates. */
 int pd_info(pd_ctx *ctx, double *out);
+
+/*
+ * Batched ensembles: declare that the meshed grains form n_agg independent
+ * aggregates (after pd_mesh_grains, before pd_bind_arena).  grain_agg[g] is
+ * the aggregate of grain g; agg_walls holds 8 doubles per aggregate: the wall
+ * box x_lo, x_hi, y_lo, y_hi at t = 0 and the normal velocities of those four
+ * walls.  Each aggregate gets its own R_c and K_n from its smallest lattice
+ * spacing (Sec. 4.1) and contact never crosses aggregates, so a batched run
+ * advances every aggregate exactly as a run of that aggregate alone would,
+ * with all aggregates in the same launches.  Without this call the context is
+ * one aggregate bounded by the walls of pd_params.
+ * Errors: PD_ESTATE, PD_EINVAL (ids out of range, empty box).
+ */
+int pd_set_aggregates(pd_ctx *ctx, int n_agg, const int32_t *grain_agg, const double *agg_walls);
+
+/*
+ * Autotuner: time candidate step paths on the current state -- a graph of
+ * separate kernels or one persistent cooperative kernel per 16 steps, with 4
+ * or 8 threads per node (fixed when pd_params.lanes is nonzero) and 128 or 256
+ * threads per block -- pick the fastest, and re-capture the step graphs.  The
+ * state is saved and restored around the trials, so the simulation does not
+ * advance.  report (nullable, 4 doubles): path, threads per node, block, best
+ * ms per step.  Different choices only reorder floating-point sums.
+ * Errors: PD_ESTATE, PD_ECUDA.
+ */
+int pd_autotune(pd_ctx *ctx, double *report);
+
+/* Select the step path explicitly (instead of pd_autotune): mode 0 = graph of
+ * separate kernels, 1 = persistent cooperative kernel; lanes 1, 4 or 8
+ * threads per node (1 = textbook summation order); block 128 or 256 threads
+ * (persistent kernel).  Re-captures the step graphs.  Errors: PD_ESTATE,
+ * PD_EINVAL, PD_ECUDA. */
+int pd_set_path(pd_ctx *ctx, int mode, int lanes, int block);
 
 /* ---- kernel timing (instrumentation) ----------------------------------------- */
 #define PD_TIMER_PREDICT 0      /* memset + displacement update / positions / bucket counts */
@@ -235,6 +274,42 @@ int pd_set_timing(pd_ctx *ctx, int enable);
 /* Durations in milliseconds of the kernel groups of the LAST step run with
  * timing enabled (waits for the stream): out[PD_TIMER_*]. */
 int pd_kernel_times(pd_ctx *ctx, double *out);
+
+/* ---- surrogate network: MLP on the tensor cores -------------------------------- */
+#define PD_MLP_IN 32
+#define PD_MLP_HIDDEN 128
+#define PD_MLP_OUT 32
+#define PD_MLP_NPARAMS 24864
+
+/*
+ * A small network for the learned per-grain modal surrogate (not in the paper):
+ * y = W3 g(W2 g(W1 x + b1) + b2) + b3, 32 -> 128 -> 128 -> 32, g = GELU
+ * (x Phi(x), erf form).  Weights and activations enter the tensor cores as BF16
+ * (tcgen05.mma), accumulation is FP32; FP32 master parameters are trained with
+ * Adam on mean squared error by the library's own forward and backward kernels.
+ * Parameters are one flat FP32 array of PD_MLP_NPARAMS values: W1[128][32],
+ * b1[128], W2[128][128], b2[128], W3[32][128], b3[32] (weights [out][in]).
+ * Device memory: one caller-owned arena (pd_mlp_arena_bytes, 256-byte aligned).
+ * Inputs x are FP32 [batch][32] row-major, outputs y FP32 [batch][32], targets t
+ * FP32 [batch][32], all device pointers; 1 <= batch <= max_batch.
+ * Errors: PD_EINVAL, PD_ESTATE (not bound), PD_ECUDA, PD_ETIMEOUT (a bounded
+ * tensor-core wait gave up).
+ */
+typedef struct pd_mlp pd_mlp;
+int pd_mlp_create(pd_mlp **out, int max_batch, void *cuda_stream);
+int pd_mlp_destroy(pd_mlp *mlp);
+int pd_mlp_arena_bytes(pd_mlp *mlp, size_t *bytes);
+int pd_mlp_bind_arena(pd_mlp *mlp, void *device_arena, size_t bytes);
+int pd_mlp_set_params(pd_mlp *mlp, const float *params_host);   /* also resets Adam */
+int pd_mlp_get_params(pd_mlp *mlp, float *params_host);
+/* y = net(x), stream-ordered, no wait. */
+int pd_mlp_forward(pd_mlp *mlp, const float *x, float *y, int batch);
+/* Loss mean((net(x) - t)^2) and its gradient w.r.t. the parameters (host
+ * outputs, nullable; waits).  The parameters do not change. */
+int pd_mlp_loss_grad(pd_mlp *mlp, const float *x, const float *t, int batch, float *loss_host, float *grad_host);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr; the
+ * loss before the step is written to *loss_host when non-null (waits). */
+int pd_mlp_train_step(pd_mlp *mlp, const float *x, const float *t, int batch, float lr, float *loss_host);
 
 /* ---- diagnostics without device allocation ---------------------------------- */
 #define PD_NOALLOC_MAX_NODES 2097152

@@ -28,7 +28,9 @@ DIAG_NAMES = ("KE", "E_bond", "Px", "Py", "Lz", "n_broken")
 # public C-ABI symbols (checked by the test-suite against include/peridem.h)
 SYMBOLS = ("pd_last_error", "pd_create", "pd_destroy", "pd_mesh_grains", "pd_build_bonds", "pd_arena_bytes",
            "pd_bind_arena", "pd_step", "pd_get_state", "pd_set_state", "pd_eval_forces", "pd_diagnostics",
-           "pd_status", "pd_info", "pd_set_timing", "pd_kernel_times")
+           "pd_status", "pd_info", "pd_set_timing", "pd_kernel_times", "pd_set_aggregates", "pd_autotune", "pd_set_path", "pd_mlp_create", "pd_mlp_destroy",
+           "pd_mlp_arena_bytes", "pd_mlp_bind_arena", "pd_mlp_set_params", "pd_mlp_get_params", "pd_mlp_forward",
+           "pd_mlp_loss_grad", "pd_mlp_train_step")
 
 
 class PdParams(ctypes.Structure):
@@ -37,7 +39,7 @@ class PdParams(ctypes.Structure):
                 ("friction", c_double), ("gravity", c_double * 2), ("dt", c_double),
                 ("wall_lo", c_double * 2), ("wall_hi", c_double * 2), ("wall_vel_lo", c_double * 2),
                 ("wall_vel_hi", c_double * 2), ("micromodulus", c_int32), ("precision", c_int32),
-                ("store_parts", c_int32), ("reserved", c_int32)]
+                ("store_parts", c_int32), ("lanes", c_int32)]
 
 
 class PeridemError(RuntimeError):
@@ -77,6 +79,18 @@ def load():
             L.pd_info.argtypes = [vp, vp]
             L.pd_set_timing.argtypes = [vp, ip]
             L.pd_kernel_times.argtypes = [vp, vp]
+            L.pd_set_aggregates.argtypes = [vp, ip, vp, vp]
+            L.pd_autotune.argtypes = [vp, vp]
+            L.pd_set_path.argtypes = [vp, ip, ip, ip]
+            L.pd_mlp_create.argtypes = [ctypes.POINTER(c_void_p), ip, vp]
+            L.pd_mlp_destroy.argtypes = [vp]
+            L.pd_mlp_arena_bytes.argtypes = [vp, ctypes.POINTER(c_size_t)]
+            L.pd_mlp_bind_arena.argtypes = [vp, vp, c_size_t]
+            L.pd_mlp_set_params.argtypes = [vp, vp]
+            L.pd_mlp_get_params.argtypes = [vp, vp]
+            L.pd_mlp_forward.argtypes = [vp, vp, vp, ip]
+            L.pd_mlp_loss_grad.argtypes = [vp, vp, vp, ip, vp, vp]
+            L.pd_mlp_train_step.argtypes = [vp, vp, vp, ip, ctypes.c_float, vp]
             for name in SYMBOLS:
                 if name != "pd_last_error":
                     getattr(L, name).restype = ip
@@ -90,7 +104,7 @@ def _check(rc):
     return rc
 
 
-def make_params(p: dict, precision: int = PD_FP64, store_parts: bool = False) -> PdParams:
+def make_params(p: dict, precision: int = PD_FP64, store_parts: bool = False, lanes: int = 0) -> PdParams:
     q = PdParams()
     for name in ("E", "nu", "k_bulk", "rho", "Gc", "horizon_ratio", "rc_ratio", "damping_ratio", "friction", "dt"):
         setattr(q, name, float(p[name]))
@@ -102,6 +116,7 @@ def make_params(p: dict, precision: int = PD_FP64, store_parts: bool = False) ->
     q.micromodulus = int(p["micromodulus"])
     q.precision = int(precision)
     q.store_parts = 1 if store_parts else 0
+    q.lanes = int(lanes)
     return q
 
 
@@ -118,7 +133,7 @@ class Simulation:
     """
 
     def __init__(self, workload, precision: int | str = PD_FP64, store_parts: bool = False, device=None,
-                 stream=None):
+                 stream=None, lanes: int = 0):
         L = load()
         if isinstance(precision, str):
             precision = {"fp64": PD_FP64, "fp32": PD_FP32_SPLIT, "fp32_split": PD_FP32_SPLIT}[precision]
@@ -132,7 +147,7 @@ class Simulation:
             import torch
             self._stream = stream if stream is not None else torch.cuda.current_stream(torch.device(device))
             sptr = c_void_p(self._stream.cuda_stream)
-        self._params = make_params(workload.params, precision, store_parts)
+        self._params = make_params(workload.params, precision, store_parts, lanes)
         ctx = c_void_p()
         _check(L.pd_create(ctypes.byref(ctx), ctypes.byref(self._params), sptr))
         self._ctx = ctx
@@ -146,6 +161,11 @@ class Simulation:
         nb = c_int64()
         _check(L.pd_build_bonds(ctx, ctypes.byref(nb)))
         self.n_bonds = nb.value
+        agg = getattr(workload, "grain_agg", None)
+        if agg is not None:
+            ga = np.ascontiguousarray(agg, dtype=np.int32)
+            walls = np.ascontiguousarray(workload.agg_walls, dtype=np.float64).reshape(-1)
+            _check(L.pd_set_aggregates(ctx, int(walls.size // 8), _ptr(ga), _ptr(walls)))
         if device is not None:
             self.bind()
 
@@ -246,7 +266,86 @@ class Simulation:
         return dict(predict=out[0], bin=out[1], force=out[2], step=out[3])
 
     def info(self) -> dict:
-        out = np.zeros(10)
+        out = np.zeros(14)
         _check(load().pd_info(self._ctx, _ptr(out)))
-        keys = ("N", "n_bonds", "G", "h_min", "Rc", "Kn", "dt", "steps", "max_row", "buckets")
+        keys = ("N", "n_bonds", "G", "h_min", "Rc", "Kn", "dt", "steps", "max_row", "buckets", "mode", "lanes",
+                "block", "n_agg")
         return dict(zip(keys, out))
+
+    def set_path(self, mode: int, lanes: int = 8, block: int = 128):
+        """0 = graph of separate kernels, 1 = persistent cooperative kernel."""
+        _check(load().pd_set_path(self._ctx, int(mode), int(lanes), int(block)))
+
+    def autotune(self) -> dict:
+        """Time the candidate step paths on the current state and keep the fastest."""
+        out = np.zeros(4)
+        _check(load().pd_autotune(self._ctx, _ptr(out)))
+        return dict(mode=int(out[0]), lanes=int(out[1]), block=int(out[2]), ms_per_step=float(out[3]))
+
+
+MLP_NPARAMS = 24864
+
+
+class MLP:
+    """The surrogate network (32 -> 128 -> 128 -> 32, GELU) on the tensor cores.
+
+    Device arena and stream from PyTorch; inputs and outputs are CUDA float32
+    tensors of shape (batch, 32)."""
+
+    def __init__(self, max_batch: int, device="cuda:0", stream=None, params=None):
+        import torch
+        L = load()
+        self.device = torch.device(device)
+        self._stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = c_void_p()
+        _check(L.pd_mlp_create(ctypes.byref(h), int(max_batch), c_void_p(self._stream.cuda_stream)))
+        self._h = h
+        self.max_batch = int(max_batch)
+        nbytes = c_size_t()
+        _check(L.pd_mlp_arena_bytes(h, ctypes.byref(nbytes)))
+        self._arena = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self._arena.data_ptr() + 255) & ~255
+        _check(L.pd_mlp_bind_arena(h, c_void_p(aligned), nbytes.value))
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(np.asarray(flat, dtype=np.float32).reshape(-1))
+        assert a.size == MLP_NPARAMS
+        _check(load().pd_mlp_set_params(self._h, _ptr(a)))
+
+    def get_params(self) -> np.ndarray:
+        a = np.zeros(MLP_NPARAMS, dtype=np.float32)
+        _check(load().pd_mlp_get_params(self._h, _ptr(a)))
+        return a
+
+    def forward(self, x, y=None):
+        import torch
+        if y is None:
+            y = torch.empty((x.shape[0], 32), dtype=torch.float32, device=self.device)
+        _check(load().pd_mlp_forward(self._h, c_void_p(x.data_ptr()), c_void_p(y.data_ptr()), int(x.shape[0])))
+        return y
+
+    def loss_grad(self, x, t):
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.zeros(MLP_NPARAMS, dtype=np.float32)
+        _check(load().pd_mlp_loss_grad(self._h, c_void_p(x.data_ptr()), c_void_p(t.data_ptr()), int(x.shape[0]),
+                                       _ptr(loss), _ptr(g)))
+        return float(loss[0]), g
+
+    def train_step(self, x, t, lr: float) -> float:
+        loss = np.zeros(1, dtype=np.float32)
+        _check(load().pd_mlp_train_step(self._h, c_void_p(x.data_ptr()), c_void_p(t.data_ptr()), int(x.shape[0]),
+                                        ctypes.c_float(lr), _ptr(loss)))
+        return float(loss[0])
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().pd_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -24,9 +24,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # (source, extra flags)
 CU_SOURCES = [
     ("pd_common.cu", ["-fmad=false"]),
-    ("pd_force_fp64.cu", ["-fmad=false"]),
-    ("pd_force_fp32.cu", []),
+    ("pd_step64.cu", ["-fmad=false"]),
+    ("pd_step32.cu", []),
     ("pd_noalloc.cu", []),
+    ("pd_mlp.cu", []),
 ]
 CPP_SOURCES = ["pd_host.cpp"]
 

@@ -1,45 +1,24 @@
-// pd_common.cu -- precision-independent step kernels: displacement update and
-// positions (Algorithm 1), contact binning (hash-grid counting sort: bucket
-// counts, device-wide exclusive scan, scatter), positions for readout and the
-// diagnostics reductions.  Compiled without FMA contraction so the FP64
-// update arithmetic rounds exactly as written.
+// pd_common.cu -- precision-independent kernels of the multi-kernel step path:
+// displacement update and positions (Algorithm 1), contact binning (hash-grid
+// counting sort: bucket counts, device-wide exclusive scan, scatter),
+// positions for readout and the diagnostics reductions; plus the launch
+// dispatchers.  Compiled without FMA contraction.
 #include "pd_device.cuh"
 
 namespace pd {
 
 // u <- u + dt v + dt^2/2 a ; p = X + u ; hash-grid bucket of p (Algorithm 1).
-// Thread 0 also advances the step counter and sets the wall positions of the
-// force evaluation that follows: w(t_{n+1}) = w0 + v_w (n+1) dt.
+// Thread 0 also advances the step counter and sets the time of the force
+// evaluation that follows: t_{n+1} = (n+1) dt.
 __global__ void __launch_bounds__(kBlock) k_predict(DevPtrs d, KParams k, int vin, int advance) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         long long st = *d.step + (advance ? 1 : 0);
-        double t = (double)st * k.dt;
-#pragma unroll
-        for (int l = 0; l < 4; ++l) d.walls_now[l] = k.w0[l] + k.wv[l] * t;
+        *d.t_now = (double)st * k.dt;
         if (advance) *d.step = st;
     }
     if (i >= k.N) return;
-    double2 u = d.u[i];
-    if (advance) {
-        double2 v = d.v[vin][i], a = d.a[i];
-        u.x = (u.x + k.dt * v.x) + k.half_dt2 * a.x;
-        u.y = (u.y + k.dt * v.y) + k.half_dt2 * a.y;
-        d.u[i] = u;
-    }
-    double2 X = d.X[i];
-    double2 p = make_double2(X.x + u.x, X.y + u.y);
-    d.p[i] = p;
-    if (d.ph) {
-        // FP32-split path: the shifted position as a float-float pair
-        double qx = p.x + k.sx, qy = p.y + k.sy;
-        float2 ph = make_float2((float)qx, (float)qy);
-        d.ph[i] = ph;
-        d.pl[i] = make_float2((float)(qx - (double)ph.x), (float)(qy - (double)ph.y));
-    }
-    unsigned b = cell_bucket(cell_coord(p.x, k.ox, k.cell), cell_coord(p.y, k.oy, k.cell), k.T);
-    d.key[i] = (int)b;
-    atomicAdd(&d.count[b], 1);
+    predict_node<false>(d, k, i, vin, advance);
 }
 
 // Block-wide exclusive scan of kScanItems values per thread.
@@ -61,7 +40,7 @@ __device__ __forceinline__ int block_exclusive_scan(int (&v)[kScanItems], int *s
     if (lane == 31) smem_warp[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        int w = (lane < (kScanThreads / 32)) ? smem_warp[lane] : 0;
+        int w = (lane < (int)(blockDim.x / 32)) ? smem_warp[lane] : 0;
         int wi = w;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -210,6 +189,15 @@ cudaError_t launch_bin(const DevPtrs &d, const KParams &k, cudaStream_t s) {
     k_scan_apply<<<nb, kScanThreads, 0, s>>>(d.count, d.blocksums, d.start, d.cursor, k.T, k.N);
     k_scatter<<<nblk(k.N, kBlock), kBlock, 0, s>>>(d.key, d.cursor, d.sorted, k.N);
     return cudaGetLastError();
+}
+
+cudaError_t launch_force(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s) {
+    return k.fp32 ? launch_force32(d, k, vin, update_v, s) : launch_force64(d, k, vin, update_v, s);
+}
+
+cudaError_t launch_persistent(const DevPtrs &d, const KParams &k, int vin, int nsteps, int block, cudaStream_t s) {
+    return k.fp32 ? launch_persistent32(d, k, vin, nsteps, block, s)
+                  : launch_persistent64(d, k, vin, nsteps, block, s);
 }
 
 cudaError_t launch_positions(const DevPtrs &d, const KParams &k, cudaStream_t s) {

@@ -1,4 +1,6 @@
-// pd_device.cuh -- device helpers shared by the step kernels.
+// pd_device.cuh -- device code shared by the multi-kernel and the persistent
+// step paths: per-node phase functions (displacement update, forces) and the
+// contact / wall / precision helpers they use.
 #pragma once
 
 #include "pd_internal.h"
@@ -6,10 +8,21 @@
 
 namespace pd {
 
-// Contact search grid: square cells of side >= R_c hashed into T buckets
-// (T a power of two >= 2N), so every pair closer than R_c lies in the 3x3
-// cell block around either node.  Aliasing cells only add candidates, which
-// the distance test rejects.
+// Loads of state that other blocks write during a persistent launch must not
+// be served from a stale L1 line: PERSIST selects L2-coherent loads (ld.cg).
+template <bool PERSIST, class T>
+__device__ __forceinline__ T ldm(const T *p) {
+    if constexpr (PERSIST) return __ldcg(p);
+    else return *p;
+}
+
+// ---------------------------------------------------------------------------
+// contact search grid
+
+// Square cells of side >= R_c hashed (with the aggregate id) into T buckets
+// (T a power of two >= 2N): every pair closer than R_c lies in the 3x3 cell
+// block around either node; aliasing cells only add candidates, which the
+// distance test rejects.
 __device__ __forceinline__ int cell_coord(double x, double origin, double cell) {
     double f = floor((x - origin) / cell);
     if (!(f > -1048576.0)) return -1048576;  // also catches NaN
@@ -17,9 +30,12 @@ __device__ __forceinline__ int cell_coord(double x, double origin, double cell) 
     return (int)f;
 }
 
-__device__ __forceinline__ unsigned cell_bucket(int cx, int cy, unsigned T) {
-    return ((unsigned)cx * 73856093u ^ (unsigned)cy * 19349663u) & (T - 1u);
+__device__ __forceinline__ unsigned cell_bucket(int cx, int cy, int agg, unsigned T) {
+    return ((unsigned)cx * 73856093u ^ (unsigned)cy * 19349663u ^ (unsigned)agg * 83492791u) & (T - 1u);
 }
+
+// ---------------------------------------------------------------------------
+// FP64 laws
 
 // Normal damping (Sec. 4.3, Kelvin-Voigt: -beta_d V_x V_y (v(x,y).e) e with
 // beta_d = 2 r_d sqrt(K_n rho / V_y)) and regularised Coulomb friction
@@ -27,9 +43,10 @@ __device__ __forceinline__ unsigned cell_bucket(int cx, int cy, unsigned T) {
 // mu |F_r| dt / (rho V_x), else the sticking force -(rho V_x / dt) v_perp).
 // e points from x to y, (vrx, vry) = v(x) - v(y), Fr = |F_r|, Vy the partner
 // volume (|S_l| for a wall).  Adds to (fx, fy).
-__device__ __forceinline__ void damping_friction64(const KParams &k, double ex, double ey, double vrx, double vry,
-                                                   double Fr, double Vx, double Vy, double &fx, double &fy) {
-    double beta = 2.0 * k.rd * sqrt(k.Kn * k.rho / Vy);
+__device__ __forceinline__ void damping_friction64(const KParams &k, double Kn, double ex, double ey, double vrx,
+                                                   double vry, double Fr, double Vx, double Vy, double &fx,
+                                                   double &fy) {
+    double beta = 2.0 * k.rd * sqrt(Kn * k.rho / Vy);
     double vn = vrx * ex + vry * ey;
     double cd = beta * Vx * Vy * vn;
     double Fdx = -cd * ex, Fdy = -cd * ey;
@@ -117,21 +134,21 @@ __device__ __forceinline__ void corner_region_stable(double di, double dj, doubl
 }
 
 // Wall contact (Sec. 4.5, eq:wall-repulsive, eq:wall-total) of a node at p
-// with velocity v and volume Vx against the four walls at positions wn[0..3]
-// (x_lo, x_hi, y_lo, y_hi) moving with normal velocities k.wv.  The repulsion
-// of each wall uses the circular segment S_l of B_Rc(p) beyond the wall;
-// corners subtract the S_li cap S_lj term (inclusion-exclusion); friction and
-// damping follow by substituting e -> e^l, V_y -> |S_l|, p(y) -> c_l.  A node
-// past a wall is treated as touching it and counted in
-// status[PD_STATUS_PENETRATION].
-__device__ __forceinline__ void wall_force64(const KParams &k, const double *wn, double px, double py, double vx,
-                                             double vy, double Vx, double &Fx_out, double &Fy_out, int *status) {
-    const double Rc = k.Rc, Kn = k.Kn;
+// with velocity v and volume Vx against the four walls of its aggregate at
+// time t (position w0 + v_w t, normal velocity v_w).  The repulsion of each
+// wall uses the circular segment S_l of B_Rc(p) beyond it; corners subtract
+// the S_li cap S_lj term (inclusion-exclusion); friction and damping follow by
+// substituting e -> e^l, V_y -> |S_l|, p(y) -> c_l.  A node past a wall is
+// treated as touching it and counted in status[PD_STATUS_PENETRATION].
+__device__ __forceinline__ void wall_force64(const KParams &k, const AggParams &A, double t, double px, double py,
+                                             double vx, double vy, double Vx, double &Fx_out, double &Fy_out,
+                                             int *status) {
+    const double Rc = A.Rc, Kn = A.Kn;
     double d[4], ex[4], ey[4];
-    d[0] = px - wn[0]; ex[0] = -1.0; ey[0] = 0.0;
-    d[1] = wn[1] - px; ex[1] = 1.0;  ey[1] = 0.0;
-    d[2] = py - wn[2]; ex[2] = 0.0;  ey[2] = -1.0;
-    d[3] = wn[3] - py; ex[3] = 0.0;  ey[3] = 1.0;
+    d[0] = px - (A.w0[0] + A.wv[0] * t); ex[0] = -1.0; ey[0] = 0.0;
+    d[1] = (A.w0[1] + A.wv[1] * t) - px; ex[1] = 1.0;  ey[1] = 0.0;
+    d[2] = py - (A.w0[2] + A.wv[2] * t); ex[2] = 0.0;  ey[2] = -1.0;
+    d[3] = (A.w0[3] + A.wv[3] * t) - py; ex[3] = 0.0;  ey[3] = 1.0;
     bool near = false;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
@@ -145,13 +162,13 @@ __device__ __forceinline__ void wall_force64(const KParams &k, const double *wn,
     if (near) {
         for (int l = 0; l < 4; ++l) {
             if (!(d[l] < Rc)) continue;
-            double A, gap;
-            wall_segment_stable(d[l], Rc, A, gap);
-            if (!(A > 0.0) || !(gap > 0.0)) continue;
-            double Fr = Kn * gap * Vx * A;
-            double wvx = (l < 2) ? k.wv[l] : 0.0, wvy = (l < 2) ? 0.0 : k.wv[l];
+            double Ar, gap;
+            wall_segment_stable(d[l], Rc, Ar, gap);
+            if (!(Ar > 0.0) || !(gap > 0.0)) continue;
+            double Fr = Kn * gap * Vx * Ar;
+            double wvx = (l < 2) ? A.wv[l] : 0.0, wvy = (l < 2) ? 0.0 : A.wv[l];
             double gx = -Fr * ex[l], gy = -Fr * ey[l];
-            damping_friction64(k, ex[l], ey[l], vx - wvx, vy - wvy, Fr, Vx, A, gx, gy);
+            damping_friction64(k, Kn, ex[l], ey[l], vx - wvx, vy - wvy, Fr, Vx, Ar, gx, gy);
             Fx += gx;
             Fy += gy;
         }
@@ -159,22 +176,428 @@ __device__ __forceinline__ void wall_force64(const KParams &k, const double *wn,
             const int i = c >> 1, j = 2 + (c & 1);  // (x_lo|x_hi) x (y_lo|y_hi)
             double di = d[i], dj = d[j];
             if (!(sqrt(di * di + dj * dj) < Rc)) continue;
-            double A, lx, ly;
-            corner_region_stable(di, dj, Rc, A, lx, ly);
-            if (!(A > 0.0)) continue;
+            double Ar, lx, ly;
+            corner_region_stable(di, dj, Rc, Ar, lx, ly);
+            if (!(Ar > 0.0)) continue;
             double cx = lx * ex[i] + ly * ex[j], cy = lx * ey[i] + ly * ey[j];
             double cd = sqrt(cx * cx + cy * cy);
             if (!(cd < Rc) || !(cd > 0.0)) continue;
             double ux = cx / cd, uy = cy / cd;
-            double Fr = Kn * (Rc - cd) * Vx * A;
+            double Fr = Kn * (Rc - cd) * Vx * Ar;
             double gx = -Fr * ux, gy = -Fr * uy;
-            damping_friction64(k, ux, uy, vx - k.wv[i], vy - k.wv[j], Fr, Vx, A, gx, gy);
+            damping_friction64(k, Kn, ux, uy, vx - A.wv[i], vy - A.wv[j], Fr, Vx, Ar, gx, gy);
             Fx -= gx;
             Fy -= gy;
         }
     }
     Fx_out = Fx;
     Fy_out = Fy;
+}
+
+// ---------------------------------------------------------------------------
+// float-float helpers of the FP32-split path
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = fmaf(a, b, -p);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// |d|^2 of d = (dxh + dxl, dyh + dyl) as a float-float pair (hi, lo).
+__device__ __forceinline__ void len2_ff(float dxh, float dxl, float dyh, float dyl, float &hi, float &lo) {
+    float px, ex, py, ey, s, es;
+    two_prod(dxh, dxh, px, ex);
+    two_prod(dyh, dyh, py, ey);
+    two_sum(px, py, s, es);
+    float r = es + (ex + ey) + 2.f * (dxh * dxl + dyh * dyl);
+    hi = __fadd_rn(s, r);
+    lo = __fsub_rn(r, __fsub_rn(hi, s));
+}
+
+// (ah + al) - (bh + bl) rounded to float; the high-part difference is exact
+// when the two values are within a factor of two of each other.
+__device__ __forceinline__ float ff_diff(float ah, float al, float bh, float bl) {
+    return __fsub_rn(ah, bh) + (al - bl);
+}
+
+__device__ __forceinline__ void damping_friction32(float rd, float Kn, float rho, float dt, float mu, float ex,
+                                                   float ey, float vrx, float vry, float Fr, float Vx, float Vy,
+                                                   float &fx, float &fy) {
+    float beta = 2.0f * rd * sqrtf(Kn * rho / Vy);
+    float vn = vrx * ex + vry * ey;
+    float cd = beta * Vx * Vy * vn;
+    float vtx = vrx - vn * ex, vty = vry - vn * ey;
+    float vt = sqrtf(vtx * vtx + vty * vty);
+    float vthr = mu * Fr * dt / (rho * Vx);
+    float c = (vt > vthr) ? (mu * Fr / vt) : (rho * Vx / dt);
+    fx += -cd * ex - c * vtx;
+    fy += -cd * ey - c * vty;
+}
+
+// ---------------------------------------------------------------------------
+// per-node phases
+
+// Algorithm 1: u <- u + dt v + dt^2/2 a (when advancing), p = X + u, the
+// FP32-split float-float copy of the shifted position, and the node's bucket.
+template <bool PERSIST>
+__device__ __forceinline__ void predict_node(const DevPtrs &d, const KParams &k, int i, int vin, int advance) {
+    double2 u = ldm<PERSIST>(&d.u[i]);
+    if (advance) {
+        // explicit round-to-nearest operations: never contracted into FMAs
+        double2 v = ldm<PERSIST>(&d.v[vin][i]), a = ldm<PERSIST>(&d.a[i]);
+        u.x = __dadd_rn(__dadd_rn(u.x, __dmul_rn(k.dt, v.x)), __dmul_rn(k.half_dt2, a.x));
+        u.y = __dadd_rn(__dadd_rn(u.y, __dmul_rn(k.dt, v.y)), __dmul_rn(k.half_dt2, a.y));
+        d.u[i] = u;
+    }
+    const double2 X = __ldg(&d.X[i]);
+    const double2 p = make_double2(X.x + u.x, X.y + u.y);
+    d.p[i] = p;
+    const int ag = __ldg(&d.g_agg[__ldg(&d.grain[i])]);
+    const AggParams &A = d.agg[ag];
+    if (d.ph) {
+        double qx = p.x + A.sx, qy = p.y + A.sy;
+        float2 ph = make_float2((float)qx, (float)qy);
+        d.ph[i] = ph;
+        d.pl[i] = make_float2((float)(qx - (double)ph.x), (float)(qy - (double)ph.y));
+    }
+    unsigned b = cell_bucket(cell_coord(p.x, A.ox, A.cell), cell_coord(p.y, A.oy, A.cell), ag, k.T);
+    d.key[i] = (int)b;
+    atomicAdd(&d.count[b], 1);
+}
+
+// Gather the contact candidates S^nbr of node i (all nodes y != i of the same
+// aggregate with |p(y) - p(i)| < R_c) from the hash-grid
+// cells lane, lane + LANES, ... of the 3x3 block, in ascending node index.
+// DIST(j) returns true when j is within R_c.
+template <bool PERSIST, int LANES, class Dist>
+__device__ __forceinline__ int gather_candidates(const DevPtrs &d, const KParams &k, const AggParams &A, int ag,
+                                                 int i, double px, double py, int lane, bool active, int *cand,
+                                                 Dist within) {
+    int nc = 0;
+    if (!active) return 0;
+    const int cx = cell_coord(px, A.ox, A.cell), cy = cell_coord(py, A.oy, A.cell);
+    unsigned bk[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) bk[c] = cell_bucket(cx + (c % 3) - 1, cy + (c / 3) - 1, ag, k.T);
+    for (int c = lane; c < 9; c += LANES) {
+        bool dup = false;
+        for (int q = 0; q < c; ++q) dup |= bk[q] == bk[c];
+        if (dup) continue;
+        const int t0 = ldm<PERSIST>(&d.start[bk[c]]), t1 = ldm<PERSIST>(&d.start[bk[c] + 1]);
+        for (int t = t0; t < t1; ++t) {
+            const int j = ldm<PERSIST>(&d.sorted[t]);
+            // hash aliasing can bring nodes of another aggregate: never in contact
+            if (j == i || __ldg(&d.g_agg[__ldg(&d.grain[j])]) != ag || !within(j)) continue;
+            if (nc < kMaxCand) {
+                int w = nc++;
+                while (w > 0 && cand[w - 1] > j) {
+                    cand[w] = cand[w - 1];
+                    --w;
+                }
+                cand[w] = j;
+            } else {
+                atomicAdd(&d.status[PD_STATUS_OVERFLOW], 1);
+            }
+        }
+    }
+    return nc;
+}
+
+// Is the bond x -> j intact?  (row columns ascending: binary search; broken
+// flags read past L1, since other lanes may have just set them.)
+__device__ __forceinline__ bool bonded_intact(const DevPtrs &d, const KParams &k, int i, int r0, int r1, int j) {
+    int lo = r0, hi = r1;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(&d.col[mid]) < j) lo = mid + 1; else hi = mid;
+    }
+    if (lo < r1 && __ldg(&d.col[lo]) == j) {
+        const int kk = lo - r0;
+        return !((__ldcg(&d.bits[(size_t)i * k.wpn + (kk >> 5)]) >> (kk & 31)) & 1u);
+    }
+    return false;
+}
+
+// Acceleration and velocity update of node i (Algorithm 1) plus the optional
+// per-part force output; run by one lane per node.
+template <bool PERSIST>
+__device__ __forceinline__ void finish_node(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
+                                            double2 vi, double Vi, double Fbx, double Fby, double Fsx, double Fsy,
+                                            double Fnx, double Fny, double Fwx, double Fwy) {
+    const double Fx = __dadd_rn(__dadd_rn(__dadd_rn(Fbx, Fsx), Fnx), Fwx);
+    const double Fy = __dadd_rn(__dadd_rn(__dadd_rn(Fby, Fsy), Fny), Fwy);
+    const double m = __dmul_rn(k.rho, Vi);
+    const double ax = __dadd_rn(__ddiv_rn(Fx, m), k.gx), ay = __dadd_rn(__ddiv_rn(Fy, m), k.gy);
+    if (update_v) {
+        const double2 ao = ldm<PERSIST>(&d.a[i]);
+        double2 vn;
+        vn.x = __dadd_rn(vi.x, __dmul_rn(k.half_dt, __dadd_rn(ao.x, ax)));
+        vn.y = __dadd_rn(vi.y, __dmul_rn(k.half_dt, __dadd_rn(ao.y, ay)));
+        d.v[vin ^ 1][i] = vn;
+    }
+    d.a[i] = make_double2(ax, ay);
+    if (!isfinite(ax) || !isfinite(ay)) atomicAdd(&d.status[PD_STATUS_NONFINITE], 1);
+    if (k.store) {
+        d.F[i] = make_double2(Fx, Fy);
+        d.parts[i] = make_double2(Fbx, Fby);
+        d.parts[k.N + i] = make_double2(Fsx, Fsy);
+        d.parts[2 * (size_t)k.N + i] = make_double2(Fnx, Fny);
+        d.parts[3 * (size_t)k.N + i] = make_double2(Fwx, Fwy);
+    }
+}
+
+template <int LANES, class T>
+__device__ __forceinline__ T lane_sum(T v) {
+#pragma unroll
+    for (int off = 1; off < LANES; off <<= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// FP64 forces of node i (eq:full, Algorithm 1), LANES threads per node: lane l
+// takes bonds l, l + LANES, ... and grid cells l, l + LANES, ...; partial sums
+// meet in a fixed xor-butterfly (deterministic).  With LANES = 1 every sum is
+// in the textbook order (bonds in CSR order, contacts in ascending index).
+// Every thread of the warp must call this (shuffles); inactive lanes pass
+// active = false.
+template <bool PERSIST, int LANES>
+__device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k, int i, int lane, bool active,
+                                             int vin, int update_v) {
+    const int ii = active ? i : 0;
+    const double2 pi = ldm<PERSIST>(&d.p[ii]);
+    const double2 Xi = __ldg(&d.X[ii]);
+    const double Vi = __ldg(&d.V[ii]);
+    const int gi = __ldg(&d.grain[ii]);
+    const int ag = __ldg(&d.g_agg[gi]);
+    const AggParams &A = d.agg[ag];
+    const double cw = __ldg(&d.g_cw[gi]), s0 = __ldg(&d.g_s0[gi]), eps = __ldg(&d.g_eps[gi]);
+    const int r0 = active ? __ldg(&d.row_ptr[ii]) : 0, r1 = active ? __ldg(&d.row_ptr[ii + 1]) : 0;
+    uint32_t *bw = d.bits + (size_t)ii * k.wpn;
+
+    // peridynamic bonds with breaking (eq:peri, eq:pmb, Sec. 3.1)
+    double Fbx = 0.0, Fby = 0.0;
+    for (int b = r0 + lane; b < r1; b += LANES) {
+        const int kk = b - r0;
+        if ((__ldcg(&bw[kk >> 5]) >> (kk & 31)) & 1u) continue;
+        const int j = __ldg(&d.col[b]);
+        const double xi = __ldg(&d.xi[b]);
+        const double2 pj = ldm<PERSIST>(&d.p[j]);
+        double dx = pj.x - pi.x, dy = pj.y - pi.y;
+        double L = sqrt(dx * dx + dy * dy);
+        double s = (L - xi) / xi;
+        if (fabs(s) > s0) {
+            atomicOr(&bw[kk >> 5], 1u << (kk & 31));
+            continue;
+        }
+        double cws = (k.micro ? cw * (1.0 - xi / eps) : cw) * s;
+        double q = cws * Vi * __ldg(&d.V[j]) / L;
+        Fbx += q * dx;
+        Fby += q * dy;
+    }
+    __syncwarp();
+
+    // contact candidates, self-contact (Sec. 4.4), inter-grain contact (Secs. 4.1-4.3)
+    int cand[kMaxCand];
+    const double Rc = A.Rc;
+    const int nc = gather_candidates<PERSIST, LANES>(d, k, A, ag, ii, pi.x, pi.y, lane, active, cand, [&](int j) {
+        const double2 pj = ldm<PERSIST>(&d.p[j]);
+        double dx = pj.x - pi.x, dy = pj.y - pi.y;
+        return sqrt(dx * dx + dy * dy) < Rc;
+    });
+    const double2 vi = ldm<PERSIST>(&d.v[vin][ii]);
+    double Fsx = 0.0, Fsy = 0.0, Fnx = 0.0, Fny = 0.0;
+    for (int q = 0; q < nc; ++q) {
+        const int j = cand[q];
+        const double2 pj = ldm<PERSIST>(&d.p[j]);
+        double dx = pj.x - pi.x, dy = pj.y - pi.y;
+        double dd = sqrt(dx * dx + dy * dy);
+        if (dd == 0.0) {
+            atomicAdd(&d.status[PD_STATUS_COINCIDENT], 1);
+            continue;
+        }
+        double ex = dx / dd, ey = dy / dd;
+        const double Vj = __ldg(&d.V[j]);
+        const double2 vj = ldm<PERSIST>(&d.v[vin][j]);
+        double vrx = vi.x - vj.x, vry = vi.y - vj.y;
+        if (__ldg(&d.grain[j]) == gi) {
+            if (bonded_intact(d, k, ii, r0, r1, j)) continue;
+            const double2 Xj = __ldg(&d.X[j]);
+            double xix = Xj.x - Xi.x, xiy = Xj.y - Xi.y;
+            double xi = sqrt(xix * xix + xiy * xiy);
+            double m;
+            if (xi < Rc)
+                m = (dd < xi) ? cw * (dd - xi) / xi : 0.0;
+            else
+                m = cw * (dd - Rc) / Rc;
+            if (m == 0.0) continue;
+            double f = m * Vi * Vj;
+            double gx = f * ex, gy = f * ey;
+            damping_friction64(k, A.Kn, ex, ey, vrx, vry, -f, Vi, Vj, gx, gy);
+            Fsx += gx;
+            Fsy += gy;
+        } else {
+            double Fr = A.Kn * (Rc - dd) * Vi * Vj;
+            double gx = -Fr * ex, gy = -Fr * ey;
+            damping_friction64(k, A.Kn, ex, ey, vrx, vry, Fr, Vi, Vj, gx, gy);
+            Fnx += gx;
+            Fny += gy;
+        }
+    }
+    Fbx = lane_sum<LANES>(Fbx);
+    Fby = lane_sum<LANES>(Fby);
+    Fsx = lane_sum<LANES>(Fsx);
+    Fsy = lane_sum<LANES>(Fsy);
+    Fnx = lane_sum<LANES>(Fnx);
+    Fny = lane_sum<LANES>(Fny);
+    if (!active || lane != 0) return;
+    double Fwx, Fwy;
+    wall_force64(k, A, ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, Vi, Fwx, Fwy, d.status);
+    finish_node<PERSIST>(d, k, i, vin, update_v, vi, Vi, Fbx, Fby, Fsx, Fsy, Fnx, Fny, Fwx, Fwy);
+}
+
+// FP32-split forces of node i: the same laws and lane layout, with the bond,
+// self-contact and contact arithmetic on the FP32 pipe.  Positions are
+// float-float pairs of the shifted position (every coordinate of a box lies in
+// [L, 2L), so high-part differences of nearby nodes are exact), |d|^2 is a
+// float-float pair built with exact FMA products, and the reference
+// |xi|^2 = h^2 (di^2 + dj^2) comes from the integer lattice offset: the stretch
+// s = (|d|^2 - |xi|^2) / (|xi| (|d| + |xi|)) (eq:pmb, rearranged) and the
+// contact overlap R_c - |d| = (R_c^2 - |d|^2) / (R_c + |d|) keep ~1e-7 relative
+// accuracy.  Bonds whose FP32 stretch lies within guard * s0 of s0 are
+// re-decided with the FP64 stretch, so break decisions are the FP64 ones.
+template <bool PERSIST, int LANES>
+__device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k, int i, int lane, bool active,
+                                             int vin, int update_v) {
+    const int ii = active ? i : 0;
+    const float2 phi = ldm<PERSIST>(&d.ph[ii]), pli = ldm<PERSIST>(&d.pl[ii]);
+    const int2 li = __ldg(&d.lat[ii]);
+    const int gi = __ldg(&d.grain[ii]);
+    const int ag = __ldg(&d.g_agg[gi]);
+    const AggParams &A = d.agg[ag];
+    const float4 gq = __ldg(&d.gq[gi]);                   // (h, h^2 hi, h^2 lo, V)
+    const float Vi = gq.w;
+    const float cw = (float)__ldg(&d.g_cw[gi]), s0 = (float)__ldg(&d.g_s0[gi]), eps = (float)__ldg(&d.g_eps[gi]);
+    const float s0_lo = s0 * (1.0f - k.guard), s0_hi = s0 * (1.0f + k.guard);
+    const int r0 = active ? __ldg(&d.row_ptr[ii]) : 0, r1 = active ? __ldg(&d.row_ptr[ii + 1]) : 0;
+    uint32_t *bw = d.bits + (size_t)ii * k.wpn;
+    const float Rc = (float)A.Rc, Kn = (float)A.Kn;
+
+    float Fbx = 0.f, Fby = 0.f;
+    const float VV = Vi * Vi;
+    for (int b = r0 + lane; b < r1; b += LANES) {
+        const int kk = b - r0;
+        if ((__ldcg(&bw[kk >> 5]) >> (kk & 31)) & 1u) continue;
+        const int j = __ldg(&d.col[b]);
+        const float2 phj = ldm<PERSIST>(&d.ph[j]), plj = ldm<PERSIST>(&d.pl[j]);
+        const int2 lj = __ldg(&d.lat[j]);
+        const float dxh = __fsub_rn(phj.x, phi.x), dxl = plj.x - pli.x;
+        const float dyh = __fsub_rn(phj.y, phi.y), dyl = plj.y - pli.y;
+        float L2h, L2l;
+        len2_ff(dxh, dxl, dyh, dyl, L2h, L2l);
+        const int di = lj.x - li.x, dj = lj.y - li.y;
+        const float nn = (float)(di * di + dj * dj);
+        float q, eq;
+        two_prod(nn, gq.y, q, eq);                           // |xi|^2 = n h^2
+        const float num = ff_diff(L2h, L2l, q, eq + nn * gq.z);
+        const float xi = gq.x * sqrtf(nn);
+        const float L = sqrtf(L2h);
+        const float s = num / (xi * (L + xi));
+        const float as = fabsf(s);
+        bool brk;
+        if (as > s0_lo && as < s0_hi) {
+            const double2 pi = ldm<PERSIST>(&d.p[ii]), pj = ldm<PERSIST>(&d.p[j]);
+            double ddx = pj.x - pi.x, ddy = pj.y - pi.y;
+            double L64 = sqrt(ddx * ddx + ddy * ddy);
+            double xi64 = __ldg(&d.xi[b]);
+            brk = fabs((L64 - xi64) / xi64) > __ldg(&d.g_s0[gi]);
+        } else {
+            brk = as > s0;
+        }
+        if (brk) {
+            atomicOr(&bw[kk >> 5], 1u << (kk & 31));
+            continue;
+        }
+        const float cws = (k.micro ? cw * (1.0f - xi / eps) : cw) * s;
+        const float qf = cws * VV / L;
+        Fbx += qf * (dxh + dxl);
+        Fby += qf * (dyh + dyl);
+    }
+    __syncwarp();
+
+    int cand[kMaxCand];
+    const double2 pi64 = ldm<PERSIST>(&d.p[ii]);
+    const int nc = gather_candidates<PERSIST, LANES>(d, k, A, ag, ii, pi64.x, pi64.y, lane, active, cand, [&](int j) {
+        const float2 phj = ldm<PERSIST>(&d.ph[j]), plj = ldm<PERSIST>(&d.pl[j]);
+        float L2h, L2l;
+        len2_ff(__fsub_rn(phj.x, phi.x), plj.x - pli.x, __fsub_rn(phj.y, phi.y), plj.y - pli.y, L2h, L2l);
+        return ff_diff(A.rc2_hi, A.rc2_lo, L2h, L2l) > 0.f;
+    });
+    const double2 vi = ldm<PERSIST>(&d.v[vin][ii]);
+    const float rd = (float)k.rd, rho = (float)k.rho, dt = (float)k.dt, mu = (float)k.mu;
+    float Fsx = 0.f, Fsy = 0.f, Fnx = 0.f, Fny = 0.f;
+    for (int q = 0; q < nc; ++q) {
+        const int j = cand[q];
+        const float2 phj = ldm<PERSIST>(&d.ph[j]), plj = ldm<PERSIST>(&d.pl[j]);
+        const float dxh = __fsub_rn(phj.x, phi.x), dxl = plj.x - pli.x;
+        const float dyh = __fsub_rn(phj.y, phi.y), dyl = plj.y - pli.y;
+        float L2h, L2l;
+        len2_ff(dxh, dxl, dyh, dyl, L2h, L2l);
+        const float dd = sqrtf(L2h);
+        if (dd == 0.f) {
+            atomicAdd(&d.status[PD_STATUS_COINCIDENT], 1);
+            continue;
+        }
+        const float ex = (dxh + dxl) / dd, ey = (dyh + dyl) / dd;
+        const float overlap = ff_diff(A.rc2_hi, A.rc2_lo, L2h, L2l) / (Rc + dd);   // R_c - |d|
+        const int gj = __ldg(&d.grain[j]);
+        const float Vj = __ldg(&d.gq[gj]).w;
+        const double2 vj = ldm<PERSIST>(&d.v[vin][j]);
+        const float vrx = (float)(vi.x - vj.x), vry = (float)(vi.y - vj.y);
+        if (gj == gi) {
+            if (bonded_intact(d, k, ii, r0, r1, j)) continue;
+            const int2 lj = __ldg(&d.lat[j]);
+            const int di = lj.x - li.x, dj = lj.y - li.y;
+            const float nn = (float)(di * di + dj * dj);
+            const float xi = gq.x * sqrtf(nn);
+            float m;
+            if (xi < Rc) {
+                float q2, eq2;
+                two_prod(nn, gq.y, q2, eq2);
+                const float dl = ff_diff(L2h, L2l, q2, eq2 + nn * gq.z) / (dd + xi);   // |d| - |xi|
+                m = (dl < 0.f) ? cw * dl / xi : 0.f;
+            } else {
+                m = -cw * overlap / Rc;
+            }
+            if (m == 0.f) continue;
+            const float f = m * Vi * Vj;
+            float gx = f * ex, gy = f * ey;
+            damping_friction32(rd, Kn, rho, dt, mu, ex, ey, vrx, vry, -f, Vi, Vj, gx, gy);
+            Fsx += gx;
+            Fsy += gy;
+        } else {
+            const float Fr = Kn * overlap * Vi * Vj;
+            float gx = -Fr * ex, gy = -Fr * ey;
+            damping_friction32(rd, Kn, rho, dt, mu, ex, ey, vrx, vry, Fr, Vi, Vj, gx, gy);
+            Fnx += gx;
+            Fny += gy;
+        }
+    }
+    Fbx = lane_sum<LANES>(Fbx);
+    Fby = lane_sum<LANES>(Fby);
+    Fsx = lane_sum<LANES>(Fsx);
+    Fsy = lane_sum<LANES>(Fsy);
+    Fnx = lane_sum<LANES>(Fnx);
+    Fny = lane_sum<LANES>(Fny);
+    if (!active || lane != 0) return;
+    const double Vi64 = __ldg(&d.V[i]);
+    double Fwx, Fwy;
+    wall_force64(k, A, ldm<PERSIST>(d.t_now), pi64.x, pi64.y, vi.x, vi.y, Vi64, Fwx, Fwy, d.status);
+    finish_node<PERSIST>(d, k, i, vin, update_v, vi, Vi64, (double)Fbx, (double)Fby, (double)Fsx, (double)Fsy,
+                         (double)Fnx, (double)Fny, Fwx, Fwy);
 }
 
 }  // namespace pd

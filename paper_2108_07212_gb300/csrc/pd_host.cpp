@@ -189,8 +189,15 @@ struct pd_ctx {
     std::vector<double> xi;
     int max_row = 0, wpn = 1;
     // derived
-    double h_min = 0, Rc = 0, Kn = 0;
+    double h_min = 0, Rc = 0, Kn = 0;   // of aggregate 0 (reported by pd_info)
     unsigned T = 0;
+    // aggregates: independent wall boxes (one by default)
+    int n_agg = 1;
+    std::vector<int32_t> g_agg;          // per grain
+    std::vector<double> agg_walls;       // 8 per aggregate: x_lo, x_hi, y_lo, y_hi, v(x_lo), v(x_hi), v(y_lo), v(y_hi)
+    std::vector<pd::AggParams> aggp;
+    // step path: 0 = graph of separate kernels, 1 = persistent cooperative kernel
+    int mode = 0, block = 128;
     pd::KParams kp{};
     pd::DevPtrs d{};
     size_t arena_bytes = 0;
@@ -203,6 +210,47 @@ struct pd_ctx {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int timing = 0;
 };
+
+namespace {
+
+constexpr double kPiAgg = 3.14159265358979323846;
+
+// Per-aggregate contact constants (Sec. 4.1): R_c = rc_ratio h_min and
+// K_n = 18 k / (pi eps_c^5) with eps_c = horizon_ratio h_min, h_min the
+// smallest lattice spacing of the aggregate's grains; hash grid anchored at
+// the aggregate's lower-left wall corner with cells of side R_c.
+void compute_aggregates(pd_ctx *c) {
+    const pd_params &p = c->prm;
+    c->aggp.assign(c->n_agg, pd::AggParams{});
+    std::vector<double> hmin(c->n_agg, 1e300);
+    for (int g = 0; g < c->G; ++g) hmin[c->g_agg[g]] = std::min(hmin[c->g_agg[g]], c->g_h[g]);
+    for (int a = 0; a < c->n_agg; ++a) {
+        pd::AggParams &A = c->aggp[a];
+        double h = hmin[a] < 1e300 ? hmin[a] : c->g_h[0];
+        double eps_c = p.horizon_ratio * h;
+        A.Rc = p.rc_ratio * h;
+        A.Kn = 18.0 * p.k_bulk / (kPiAgg * eps_c * eps_c * eps_c * eps_c * eps_c);
+        const double *w = &c->agg_walls[8 * (size_t)a];
+        A.w0[0] = w[0]; A.w0[1] = w[1]; A.w0[2] = w[2]; A.w0[3] = w[3];
+        A.wv[0] = w[4]; A.wv[1] = w[5]; A.wv[2] = w[6]; A.wv[3] = w[7];
+        A.ox = w[0];
+        A.oy = w[2];
+        A.cell = A.Rc;
+        // FP32 split: shift coordinates of the box into [L, 2L) so nearby
+        // positions share a binade and their float differences are exact
+        double Lx = std::max(w[1] - w[0], 1e-6), Ly = std::max(w[3] - w[2], 1e-6);
+        A.sx = Lx - w[0];
+        A.sy = Ly - w[2];
+        double rc2 = A.Rc * A.Rc;
+        A.rc2_hi = (float)rc2;
+        A.rc2_lo = (float)(rc2 - (double)A.rc2_hi);
+    }
+    c->h_min = hmin[0] < 1e300 ? hmin[0] : c->g_h[0];
+    c->Rc = c->aggp[0].Rc;
+    c->Kn = c->aggp[0].Kn;
+}
+
+}  // namespace
 
 namespace {
 
@@ -235,14 +283,19 @@ size_t layout(pd_ctx *c, char *base) {
     carve(base, off, d.g_cw, G);
     carve(base, off, d.g_s0, G);
     carve(base, off, d.g_eps, G);
+    carve(base, off, d.g_agg, G);
+    carve(base, off, d.agg, (size_t)c->n_agg);
     carve(base, off, d.key, N);
     carve(base, off, d.count, c->T);
     carve(base, off, d.start, (size_t)c->T + 1);
     carve(base, off, d.cursor, c->T);
     carve(base, off, d.sorted, N);
-    carve(base, off, d.blocksums, c->T / pd::kScanTile + 2);
+    // block sums of the scan: one per scan tile (multi-kernel path) or per
+    // block of the persistent kernel (at most 16 blocks per SM)
+    carve(base, off, d.blocksums, std::max<size_t>(c->T / pd::kScanTile + 2, 16 * 1024));
     carve(base, off, d.step, 1);
-    carve(base, off, d.walls_now, 4);
+    carve(base, off, d.t_now, 1);
+    carve(base, off, d.bar, 2);
     carve(base, off, d.status, PD_STATUS_COUNT);
     carve(base, off, d.diag_part, (size_t)c->kp.n_diag_blocks * PD_DIAG_COUNT);
     carve(base, off, d.diag_out, PD_DIAG_COUNT);
@@ -256,6 +309,10 @@ size_t layout(pd_ctx *c, char *base) {
         d.gq = nullptr;
         d.ph = d.pl = nullptr;
     }
+    carve(base, off, d.bu, N);
+    carve(base, off, d.bv, N);
+    carve(base, off, d.ba, N);
+    carve(base, off, d.bbits, N * (size_t)c->wpn);
     return off;
 }
 
@@ -276,11 +333,20 @@ cudaError_t record_step(pd_ctx *c, int vin, cudaStream_t s, bool timed = false) 
     if (timed && (e = cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     if ((e = pd::launch_bin(c->d, c->kp, s)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal)) != cudaSuccess) return e;
-    if (c->prm.precision == PD_FP32_SPLIT)
-        e = pd::launch_force_fp32(c->d, c->kp, vin, 1, s);
-    else
-        e = pd::launch_force_fp64(c->d, c->kp, vin, 1, s);
-    if (e != cudaSuccess) return e;
+    if ((e = pd::launch_force(c->d, c->kp, vin, 1, s)) != cudaSuccess) return e;
+    if (timed && (e = cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+// nsteps time steps as one persistent cooperative launch (bucket counts
+// cleared first); timing brackets the whole launch as the force group.
+cudaError_t record_persistent(pd_ctx *c, int vin, int nsteps, cudaStream_t s, bool timed = false) {
+    cudaError_t e;
+    if (timed && (e = cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->d.count, 0, sizeof(int) * c->T, s)) != cudaSuccess) return e;
+    if (timed && (e = cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal)) != cudaSuccess) return e;
+    if (timed && (e = cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal)) != cudaSuccess) return e;
+    if ((e = pd::launch_persistent(c->d, c->kp, vin, nsteps, c->block, s)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -290,15 +356,33 @@ int capture(pd_ctx *c, int vstart, int nsteps, cudaGraphExec_t *out, bool timed 
     PD_CUDA(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
     int v = vstart;
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
-        e = record_step(c, v, c->capture_stream, timed);
-        v ^= 1;
+    if (c->mode == 1) {
+        e = record_persistent(c, v, nsteps, c->capture_stream, timed);
+    } else {
+        for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+            e = record_step(c, v, c->capture_stream, timed);
+            v ^= 1;
+        }
     }
     cudaError_t e2 = cudaStreamEndCapture(c->capture_stream, &g);
     if (e != cudaSuccess) return fail(PD_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
     if (e2 != cudaSuccess) return fail(PD_ECUDA, std::string("end capture: ") + cudaGetErrorString(e2));
     PD_CUDA(cudaGraphInstantiate(out, g, 0));
     cudaGraphDestroy(g);
+    return PD_OK;
+}
+
+int capture_all(pd_ctx *c) {
+    for (int v = 0; v < 2; ++v) {
+        for (cudaGraphExec_t *g : {&c->chunk[v], &c->single[v], &c->timed[v]})
+            if (*g) {
+                cudaGraphExecDestroy(*g);
+                *g = nullptr;
+            }
+        if (int r = capture(c, v, kChunk, &c->chunk[v])) return r;
+        if (int r = capture(c, v, 1, &c->single[v])) return r;
+        if (int r = capture(c, v, 1, &c->timed[v], true)) return r;
+    }
     return PD_OK;
 }
 
@@ -340,6 +424,8 @@ int pd_create(pd_ctx **out, const pd_params *params, void *cuda_stream) {
     if (p.precision != PD_FP64 && p.precision != PD_FP32_SPLIT) return fail(PD_EINVAL, "unknown precision");
     if (p.micromodulus != PD_MICRO_CONSTANT && p.micromodulus != PD_MICRO_CONIC)
         return fail(PD_EINVAL, "unknown micromodulus");
+    if (p.lanes != 0 && p.lanes != 1 && p.lanes != 4 && p.lanes != 8)
+        return fail(PD_EINVAL, "lanes must be 0, 1, 4 or 8");
     pd_ctx *c = new (std::nothrow) pd_ctx();
     if (!c) return fail(PD_ENOMEM, "out of host memory");
     c->prm = p;
@@ -446,9 +532,11 @@ int pd_mesh_grains(pd_ctx *c, int n_shapes, const int32_t *shape_loop_start, con
             c->g_s0[g] = std::sqrt(5.0 * kPi * p.Gc / (9.0 * p.E * eps));
         }
     }
-    double eps_c = p.horizon_ratio * c->h_min;
-    c->Rc = p.rc_ratio * c->h_min;
-    c->Kn = 18.0 * p.k_bulk / (kPi * eps_c * eps_c * eps_c * eps_c * eps_c);
+    c->n_agg = 1;
+    c->g_agg.assign(c->G, 0);
+    c->agg_walls = {p.wall_lo[0], p.wall_hi[0], p.wall_lo[1], p.wall_hi[1],
+                    p.wall_vel_lo[0], p.wall_vel_hi[0], p.wall_vel_lo[1], p.wall_vel_hi[1]};
+    compute_aggregates(c);
     c->state = 1;
     if (n_nodes_out) *n_nodes_out = c->N;
     return PD_OK;
@@ -571,9 +659,8 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     k.G = c->G;
     k.wpn = c->wpn;
     k.T = c->T;
+    k.n_agg = c->n_agg;
     k.rho = p.rho;
-    k.Kn = c->Kn;
-    k.Rc = c->Rc;
     k.rd = p.damping_ratio;
     k.mu = p.friction;
     k.gx = p.gravity[0];
@@ -581,32 +668,11 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     k.dt = p.dt;
     k.half_dt = 0.5 * p.dt;
     k.half_dt2 = 0.5 * p.dt * p.dt;
-    k.w0[0] = p.wall_lo[0];
-    k.w0[1] = p.wall_hi[0];
-    k.w0[2] = p.wall_lo[1];
-    k.w0[3] = p.wall_hi[1];
-    k.wv[0] = p.wall_vel_lo[0];
-    k.wv[1] = p.wall_vel_hi[0];
-    k.wv[2] = p.wall_vel_lo[1];
-    k.wv[3] = p.wall_vel_hi[1];
-    k.cell = c->Rc;
-    k.ox = p.wall_lo[0];
-    k.oy = p.wall_lo[1];
-    // FP32-split: shift coordinates into [L, 2L) so nearby positions share a
-    // binade and their float differences are exact (Sterbenz)
-    {
-        double Lx = std::max(p.wall_hi[0] - p.wall_lo[0], 1e-6), Ly = std::max(p.wall_hi[1] - p.wall_lo[1], 1e-6);
-        k.sx = Lx - p.wall_lo[0];
-        k.sy = Ly - p.wall_lo[1];
-    }
     k.guard = 1e-4f;
-    {
-        double rc2 = c->Rc * c->Rc;
-        k.rc2_hi = (float)rc2;
-        k.rc2_lo = (float)(rc2 - (double)k.rc2_hi);
-    }
+    k.fp32 = p.precision == PD_FP32_SPLIT ? 1 : 0;
     k.micro = p.micromodulus;
     k.store = p.store_parts ? 1 : 0;
+    k.lanes = p.lanes == 0 ? 8 : p.lanes;
     cudaStream_t s = c->stream;
     const pd::DevPtrs &d = c->d;
     size_t N = (size_t)c->N, nb = c->col.size(), G = (size_t)c->G;
@@ -628,6 +694,10 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     PD_CUDA(cudaMemcpyAsync(d.g_cw, c->g_cw.data(), 8 * G, cudaMemcpyHostToDevice, s));
     PD_CUDA(cudaMemcpyAsync(d.g_s0, c->g_s0.data(), 8 * G, cudaMemcpyHostToDevice, s));
     PD_CUDA(cudaMemcpyAsync(d.g_eps, c->g_eps.data(), 8 * G, cudaMemcpyHostToDevice, s));
+    PD_CUDA(cudaMemcpyAsync(d.g_agg, c->g_agg.data(), 4 * G, cudaMemcpyHostToDevice, s));
+    PD_CUDA(cudaMemcpyAsync(d.agg, c->aggp.data(), sizeof(pd::AggParams) * c->aggp.size(), cudaMemcpyHostToDevice, s));
+    PD_CUDA(cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), s));
+    PD_CUDA(cudaMemsetAsync(d.t_now, 0, sizeof(double), s));
     PD_CUDA(cudaMemsetAsync(d.step, 0, 8, s));
     PD_CUDA(cudaMemsetAsync(d.status, 0, 4 * PD_STATUS_COUNT, s));
     std::vector<float> gq;
@@ -657,12 +727,7 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     // capture the step graphs on a private stream (the caller's may be the legacy stream)
     PD_CUDA(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
     for (auto &e : c->ev) PD_CUDA(cudaEventCreate(&e));
-    for (int v = 0; v < 2; ++v) {
-        if (int r = capture(c, v, kChunk, &c->chunk[v])) return r;
-        if (int r = capture(c, v, 1, &c->single[v])) return r;
-        if (int r = capture(c, v, 1, &c->timed[v], true)) return r;
-    }
-    return PD_OK;
+    return capture_all(c);
 }
 
 int pd_eval_forces(pd_ctx *c) {
@@ -671,10 +736,7 @@ int pd_eval_forces(pd_ctx *c) {
     PD_CUDA(cudaMemsetAsync(c->d.count, 0, sizeof(int) * c->T, s));
     PD_CUDA(pd::launch_predict(c->d, c->kp, c->vcur, 0, s));
     PD_CUDA(pd::launch_bin(c->d, c->kp, s));
-    if (c->prm.precision == PD_FP32_SPLIT)
-        PD_CUDA(pd::launch_force_fp32(c->d, c->kp, c->vcur, 0, s));
-    else
-        PD_CUDA(pd::launch_force_fp64(c->d, c->kp, c->vcur, 0, s));
+    PD_CUDA(pd::launch_force(c->d, c->kp, c->vcur, 0, s));
     return PD_OK;
 }
 
@@ -831,6 +893,124 @@ int pd_status(pd_ctx *c, int32_t *out) {
     return PD_OK;
 }
 
+int pd_set_aggregates(pd_ctx *c, int n_agg, const int32_t *grain_agg, const double *agg_walls) {
+    if (int r = check_ctx(c, 1)) return r;
+    if (c->state > 2) return fail(PD_ESTATE, "pd_set_aggregates must come before pd_bind_arena");
+    if (n_agg < 1 || !grain_agg || !agg_walls) return fail(PD_EINVAL, "n_agg >= 1 and non-null arrays required");
+    for (int g = 0; g < c->G; ++g)
+        if (grain_agg[g] < 0 || grain_agg[g] >= n_agg) return fail(PD_EINVAL, "grain aggregate out of range");
+    for (int a = 0; a < n_agg; ++a) {
+        const double *w = agg_walls + 8 * (size_t)a;
+        if (!(w[1] > w[0]) || !(w[3] > w[2])) return fail(PD_EINVAL, "aggregate wall box is empty");
+    }
+    c->n_agg = n_agg;
+    c->g_agg.assign(grain_agg, grain_agg + c->G);
+    c->agg_walls.assign(agg_walls, agg_walls + 8 * (size_t)n_agg);
+    compute_aggregates(c);
+    return PD_OK;
+}
+
+int pd_autotune(pd_ctx *c, double *report) {
+    if (int r = check_ctx(c, 3)) return r;
+    cudaStream_t s = c->stream;
+    const pd::DevPtrs &d = c->d;
+    const size_t N = (size_t)c->N;
+    // back up the state; every trial starts from it and it is restored at the end
+    PD_CUDA(cudaMemcpyAsync(d.bu, d.u, 16 * N, cudaMemcpyDeviceToDevice, s));
+    PD_CUDA(cudaMemcpyAsync(d.bv, d.v[c->vcur], 16 * N, cudaMemcpyDeviceToDevice, s));
+    PD_CUDA(cudaMemcpyAsync(d.ba, d.a, 16 * N, cudaMemcpyDeviceToDevice, s));
+    PD_CUDA(cudaMemcpyAsync(d.bbits, d.bits, 4 * N * c->wpn, cudaMemcpyDeviceToDevice, s));
+    long long step0 = 0;
+    int32_t st0[PD_STATUS_COUNT];
+    PD_CUDA(cudaMemcpyAsync(&step0, d.step, 8, cudaMemcpyDeviceToHost, s));
+    PD_CUDA(cudaMemcpyAsync(st0, d.status, sizeof(st0), cudaMemcpyDeviceToHost, s));
+    PD_CUDA(cudaStreamSynchronize(s));
+    auto restore = [&]() -> int {
+        PD_CUDA(cudaMemcpyAsync(d.u, d.bu, 16 * N, cudaMemcpyDeviceToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.v[c->vcur], d.bv, 16 * N, cudaMemcpyDeviceToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.a, d.ba, 16 * N, cudaMemcpyDeviceToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.bits, d.bbits, 4 * N * c->wpn, cudaMemcpyDeviceToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.step, &step0, 8, cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.status, st0, sizeof(st0), cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), s));
+        PD_CUDA(cudaStreamSynchronize(s));
+        return PD_OK;
+    };
+    struct Cand {
+        int mode, lanes, block;
+    };
+    std::vector<Cand> cands;
+    const int lane_opts[2] = {4, 8};
+    for (int m = 0; m < 2; ++m)
+        for (int li = 0; li < 2; ++li) {
+            int lanes = c->prm.lanes ? c->prm.lanes : lane_opts[li];
+            if (c->prm.lanes && li == 1) continue;
+            if (m == 0) cands.push_back({0, lanes, 128});
+            else {
+                cands.push_back({1, lanes, 128});
+                cands.push_back({1, lanes, 256});
+            }
+        }
+    const int kTune = 8;
+    cudaEvent_t e0, e1;
+    PD_CUDA(cudaEventCreate(&e0));
+    PD_CUDA(cudaEventCreate(&e1));
+    double best = 1e300;
+    Cand pick = {c->mode, c->kp.lanes, c->block};
+    for (const Cand &cd : cands) {
+        c->mode = cd.mode;
+        c->kp.lanes = cd.lanes;
+        c->block = cd.block;
+        cudaGraphExec_t g = nullptr;
+        if (capture(c, c->vcur, kTune, &g) != PD_OK) {
+            cudaGetLastError();
+            continue;
+        }
+        float ms = 0.f;
+        bool ok = cudaGraphLaunch(g, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+        if (int r = restore()) return r;
+        if (ok) {
+            ok = cudaEventRecord(e0, s) == cudaSuccess && cudaGraphLaunch(g, s) == cudaSuccess &&
+                 cudaEventRecord(e1, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess &&
+                 cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+            int32_t st[PD_STATUS_COUNT];
+            if (ok && cudaMemcpy(st, d.status, sizeof(st), cudaMemcpyDeviceToHost) == cudaSuccess &&
+                st[PD_STATUS_TIMEOUT] != 0)
+                ok = false;
+            if (int r = restore()) return r;
+        }
+        cudaGraphExecDestroy(g);
+        cudaGetLastError();
+        if (ok && ms / kTune < best) {
+            best = ms / kTune;
+            pick = cd;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->mode = pick.mode;
+    c->kp.lanes = pick.lanes;
+    c->block = pick.block;
+    if (int r = capture_all(c)) return r;
+    if (report) {
+        report[0] = pick.mode;
+        report[1] = pick.lanes;
+        report[2] = pick.block;
+        report[3] = best;
+    }
+    return PD_OK;
+}
+
+int pd_set_path(pd_ctx *c, int mode, int lanes, int block) {
+    if (int r = check_ctx(c, 3)) return r;
+    if ((mode != 0 && mode != 1) || (lanes != 1 && lanes != 4 && lanes != 8) || (block != 128 && block != 256))
+        return fail(PD_EINVAL, "mode 0|1, lanes 1|4|8, block 128|256");
+    c->mode = mode;
+    c->kp.lanes = lanes;
+    c->block = block;
+    return capture_all(c);
+}
+
 int pd_set_timing(pd_ctx *c, int enable) {
     if (int r = check_ctx(c, 3)) return r;
     c->timing = enable ? 1 : 0;
@@ -864,6 +1044,10 @@ int pd_info(pd_ctx *c, double *out) {
     out[7] = (double)c->steps_done;
     out[8] = (double)c->max_row;
     out[9] = (double)c->T;
+    out[10] = (double)c->mode;
+    out[11] = (double)(c->state >= 3 ? c->kp.lanes : (c->prm.lanes ? c->prm.lanes : 8));
+    out[12] = (double)c->block;
+    out[13] = (double)c->n_agg;
     return PD_OK;
 }
 

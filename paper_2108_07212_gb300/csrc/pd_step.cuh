@@ -1,0 +1,221 @@
+// pd_step.cuh -- force kernels of the multi-kernel path and the persistent
+// step kernel, instantiated per precision by pd_step64.cu (no FMA
+// contraction) and pd_step32.cu.
+#pragma once
+
+#include "pd_device.cuh"
+
+namespace pd {
+
+template <bool FP32, bool PERSIST, int LANES>
+__device__ __forceinline__ void force_node(const DevPtrs &d, const KParams &k, int i, int lane, bool active, int vin,
+                                           int update_v) {
+    if constexpr (FP32) force_node32<PERSIST, LANES>(d, k, i, lane, active, vin, update_v);
+    else force_node64<PERSIST, LANES>(d, k, i, lane, active, vin, update_v);
+}
+
+// Multi-kernel path: LANES threads per node over the whole grid.
+template <bool FP32, int LANES>
+__global__ void __launch_bounds__(kBlock) k_force(DevPtrs d, KParams k, int vin, int update_v) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = tid / LANES;
+    force_node<FP32, false, LANES>(d, k, i, tid % LANES, i < k.N, vin, update_v);
+}
+
+template <bool FP32>
+cudaError_t launch_force_impl(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s) {
+    const long long threads = (long long)k.lanes * k.N;
+    const unsigned grid = (unsigned)((threads + kBlock - 1) / kBlock);
+    if (k.lanes == 8) k_force<FP32, 8><<<grid, kBlock, 0, s>>>(d, k, vin, update_v);
+    else if (k.lanes == 4) k_force<FP32, 4><<<grid, kBlock, 0, s>>>(d, k, vin, update_v);
+    else k_force<FP32, 1><<<grid, kBlock, 0, s>>>(d, k, vin, update_v);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// persistent step kernel
+
+// Grid barrier with a bounded wait: the last block to arrive resets the
+// arrival count and advances the generation; the others sleep-poll the
+// generation for at most kBarrierSpins rounds, then set
+// status[PD_STATUS_TIMEOUT] and report failure (the kernel then returns, so
+// the device never hangs).  Co-residency of all blocks is guaranteed by the
+// cooperative launch.
+__device__ __forceinline__ bool grid_barrier(const DevPtrs &d) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = d.bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(d.bar, 1u);
+        ok = 1;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(d.bar, 0u);
+            __threadfence();
+            atomicAdd(d.bar + 1, 1u);
+        } else {
+            long long n = 0;
+            while (*gen == g) {
+                if (++n > kBarrierSpins || *(volatile int *)&d.status[PD_STATUS_TIMEOUT]) {
+                    atomicExch(&d.status[PD_STATUS_TIMEOUT], 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <int BLOCK>
+__device__ __forceinline__ int block_sum(int v, int *sm) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    int t = 0;
+    if (threadIdx.x < 32) {
+        t = (lane < BLOCK / 32) ? sm[lane] : 0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0) sm[32] = t;
+    }
+    __syncthreads();
+    return sm[32];
+}
+
+// Exclusive scan of one value per thread over the block; returns the total.
+template <int BLOCK>
+__device__ __forceinline__ int block_scan1(int &v, int *sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    __syncthreads();
+    if (lane == 31) sm[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int w = (lane < BLOCK / 32) ? sm[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += y;
+        }
+        sm[lane] = wi - w;
+        if (lane == 31) sm[32] = wi;
+    }
+    __syncthreads();
+    v = sm[warp] + incl - v;
+    return sm[32];
+}
+
+// All phases of nsteps time steps in one cooperative launch:
+//   A  displacement update, positions, bucket counts      (Algorithm 1)
+//   B  per-block sums of the bucket counts
+//   C  exclusive scan of the counts -> cell starts
+//   D  counting-sort scatter of the node indices
+//   E  forces, acceleration and velocity update; bucket counts cleared
+// Bucket counts must be zero on entry (the host clears them before a launch).
+template <bool FP32, int LANES, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_persistent(DevPtrs d, KParams k, int vin, int nsteps) {
+    __shared__ int sm[33];
+    const int nthreads = gridDim.x * BLOCK;
+    const int gtid = blockIdx.x * BLOCK + threadIdx.x;
+    const unsigned T = k.T;
+    const unsigned slice = (T + gridDim.x - 1) / gridDim.x;
+    const unsigned lo = min(T, blockIdx.x * slice), hi = min(T, lo + slice);
+    for (int st = 0; st < nsteps; ++st) {
+        // A
+        if (gtid == 0) {
+            const long long s = *d.step + 1;
+            *d.step = s;
+            *d.t_now = (double)s * k.dt;
+        }
+        for (int i = gtid; i < k.N; i += nthreads) predict_node<true>(d, k, i, vin, 1);
+        if (!grid_barrier(d)) return;
+        // B
+        int part = 0;
+        for (unsigned b = lo + threadIdx.x; b < hi; b += BLOCK) part += __ldcg(&d.count[b]);
+        part = block_sum<BLOCK>(part, sm);
+        if (threadIdx.x == 0) d.blocksums[blockIdx.x] = part;
+        if (!grid_barrier(d)) return;
+        // C
+        int off = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += BLOCK) off += __ldcg(&d.blocksums[b]);
+        off = block_sum<BLOCK>(off, sm);
+        for (unsigned b0 = lo; b0 < hi; b0 += BLOCK) {
+            const unsigned b = b0 + threadIdx.x;
+            int c = (b < hi) ? __ldcg(&d.count[b]) : 0;
+            const int tot = block_scan1<BLOCK>(c, sm);
+            if (b < hi) {
+                d.start[b] = off + c;
+                d.cursor[b] = off + c;
+            }
+            off += tot;
+        }
+        if (gtid == 0) d.start[T] = k.N;
+        if (!grid_barrier(d)) return;
+        // D
+        for (int i = gtid; i < k.N; i += nthreads) {
+            const int pos = atomicAdd(&d.cursor[__ldcg(&d.key[i])], 1);
+            d.sorted[pos] = i;
+        }
+        if (!grid_barrier(d)) return;
+        // E
+        const long long total = (((long long)LANES * k.N + 31) / 32) * 32;
+        for (long long t = gtid; t < total; t += nthreads) {
+            const int i = (int)(t / LANES);
+            force_node<FP32, true, LANES>(d, k, i, (int)(t % LANES), i < k.N, vin, 1);
+        }
+        for (unsigned b = gtid; b < T; b += nthreads) d.count[b] = 0;
+        if (!grid_barrier(d)) return;
+        vin ^= 1;
+    }
+}
+
+template <bool FP32, int LANES, int BLOCK>
+cudaError_t launch_persistent_cfg(const DevPtrs &d, const KParams &k, int vin, int nsteps, cudaStream_t s) {
+    auto kern = k_persistent<FP32, LANES, BLOCK>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, 0)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long need = ((long long)LANES * k.N + BLOCK - 1) / BLOCK;
+    const int grid = (int)std::max(1LL, std::min<long long>((long long)per_sm * sms, need));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(BLOCK);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, d, k, vin, nsteps);
+}
+
+template <bool FP32>
+cudaError_t launch_persistent_impl(const DevPtrs &d, const KParams &k, int vin, int nsteps, int block, cudaStream_t s) {
+    if (block == 256) {
+        if (k.lanes == 8) return launch_persistent_cfg<FP32, 8, 256>(d, k, vin, nsteps, s);
+        if (k.lanes == 4) return launch_persistent_cfg<FP32, 4, 256>(d, k, vin, nsteps, s);
+        return launch_persistent_cfg<FP32, 1, 256>(d, k, vin, nsteps, s);
+    }
+    if (k.lanes == 8) return launch_persistent_cfg<FP32, 8, 128>(d, k, vin, nsteps, s);
+    if (k.lanes == 4) return launch_persistent_cfg<FP32, 4, 128>(d, k, vin, nsteps, s);
+    return launch_persistent_cfg<FP32, 1, 128>(d, k, vin, nsteps, s);
+}
+
+}  // namespace pd

@@ -123,6 +123,8 @@ class Workload:
     params: dict
     n_steps: int
     name: str = ""
+    grain_agg: np.ndarray | None = None     # aggregate of each grain (batched ensembles)
+    agg_walls: np.ndarray | None = None     # (A, 8): x_lo, x_hi, y_lo, y_hi and their normal velocities
 
     @property
     def n_grains(self) -> int:
@@ -288,3 +290,46 @@ def perturbed_disks(n_grains: int, seed: int = 7, **kw) -> Workload:
     w.grain_shape = np.arange(n_grains, dtype=np.int32)
     w.name = f"perturbed_{n_grains}g_seed{seed}"
     return w
+
+
+def ensemble(n_agg: int = 64, grains_range=(20, 200), r_range=(0.8e-3, 1.2e-3), h_ratio: int = 21,
+             seed: int = 11, dt: float = 2e-8, n_steps: int = 5000) -> Workload:
+    """Batched ensemble of independent settling aggregates of uneven size.
+
+    Aggregate a has n_a ~ U{grains_range} grains (seeded), radii ~ U[r_range],
+    the settling shape mix, its own wall box (width ~ sqrt of its grain count,
+    packing ~0.35 of the box) and its own seed; all aggregates share the
+    material and time step (dt = 2e-8 s keeps the damped contact of the finer
+    h = R/21 lattice stable at k = 5e5 Pa).  Returns one Workload whose grains carry their
+    aggregate id; :func:`split_ensemble` gives the aggregates back one by one.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    counts = rng.integers(grains_range[0], grains_range[1] + 1, size=n_agg)
+    parts = []
+    for a in range(n_agg):
+        n = int(counts[a])
+        rmean = 0.5 * (r_range[0] + r_range[1])
+        area = n * math.pi * (rmean + 0.1e-3) ** 2 / 0.35
+        width = math.sqrt(area / 1.5)
+        parts.append(settling(n_grains=n, box=(width, 1.5 * width), r_range=r_range, h_ratio=h_ratio,
+                              seed=seed * 1000 + a, dt=dt, n_steps=n_steps))
+    return merge_aggregates(parts, name=f"ensemble_{n_agg}agg_seed{seed}")
+
+
+def merge_aggregates(parts, name="ensemble") -> Workload:
+    """Concatenate independent workloads (same material and dt) into one batched workload."""
+    shapes, gshape, ggeom, gagg, walls = [], [], [], [], []
+    for a, w in enumerate(parts):
+        base = len(shapes)
+        shapes.extend(w.shapes)
+        gshape.extend(int(s) + base for s in w.grain_shape)
+        ggeom.append(w.grain_geom)
+        gagg.extend([a] * w.n_grains)
+        p = w.params
+        walls.append([p["wall_lo"][0], p["wall_hi"][0], p["wall_lo"][1], p["wall_hi"][1],
+                      p["wall_vel_lo"][0], p["wall_vel_hi"][0], p["wall_vel_lo"][1], p["wall_vel_hi"][1]])
+    out = _mk(shapes, gshape, np.vstack(ggeom), dict(parts[0].params), parts[0].n_steps, name)
+    out.grain_agg = np.asarray(gagg, dtype=np.int32)
+    out.agg_walls = np.asarray(walls, dtype=np.float64)
+    out.parts = parts
+    return out

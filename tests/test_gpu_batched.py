@@ -1,0 +1,108 @@
+"""Batched ensembles, the persistent cooperative step kernel and the autotuner.
+
+A batched run must advance every aggregate exactly as a run of that aggregate
+alone; the persistent kernel must reproduce the graph of separate kernels; the
+autotuner must not move the simulation."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2108_07212_gb300 import binding as B
+from paper_2108_07212_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _parts():
+    a = I.settling(n_grains=6, box=(9e-3, 12e-3), seed=21)
+    b = I.settling(n_grains=10, box=(11e-3, 14e-3), seed=22, h_ratio=12)
+    c = I.settling(n_grains=3, box=(7e-3, 9e-3), seed=23)
+    for w in (a, b, c):                      # lowest grains on the floor quickly
+        w.grain_geom[:, 5] = -3.0
+    return [a, b, c]
+
+
+def _sim(w, prec, **kw):
+    return B.Simulation(w, precision=prec, device="cuda:0", **kw)
+
+
+@pytest.mark.parametrize("prec", [B.PD_FP64, B.PD_FP32_SPLIT])
+def test_batched_run_equals_separate_runs(prec):
+    parts = _parts()
+    merged = I.merge_aggregates(parts)
+    S = _sim(merged, prec)
+    S.step(400)
+    u = S.get("DISP")
+    br = S.get("BROKEN")
+    off, boff = 0, 0
+    for w in parts:
+        A = _sim(w, prec)
+        A.step(400)
+        ua = A.get("DISP")
+        n = ua.shape[0]
+        # the hash grid of the batched context aliases other cells, which moves
+        # candidates between lanes: only the order of the contact sums differs
+        tol = 1e-10 if prec == B.PD_FP64 else 1e-8
+        assert np.linalg.norm(u[off:off + n] - ua) <= tol * np.linalg.norm(ua)
+        assert np.array_equal(br[boff:boff + A.n_bonds], A.get("BROKEN"))
+        off += n
+        boff += A.n_bonds
+    assert off == S.N
+    rc, st = S.status()
+    assert rc == B.PD_OK
+
+
+def test_batched_aggregate_matches_oracle():
+    parts = _parts()
+    S = _sim(I.merge_aggregates(parts), B.PD_FP64)
+    S.step(300)
+    u = S.get("DISP")
+    n0 = 0
+    for w in parts[:2]:
+        P = O.OracleProblem.from_workload(w).init_accel()
+        P.run(300)
+        n = P.N
+        assert np.linalg.norm(u[n0:n0 + n] - P.u) <= 1e-9 * np.linalg.norm(P.u)
+        n0 += n
+
+
+@pytest.mark.parametrize("prec", [B.PD_FP64, B.PD_FP32_SPLIT])
+@pytest.mark.parametrize("lanes,block", [(8, 128), (4, 256), (1, 128)])
+def test_persistent_kernel_reproduces_kernel_graph(prec, lanes, block):
+    w = I.merge_aggregates(_parts())
+    a = _sim(w, prec)
+    b = _sim(w, prec)
+    a.set_path(0, lanes, 128)
+    b.set_path(1, lanes, block)
+    assert b.info()["mode"] == 1
+    for k in (1, 16, 37):                    # single steps and whole chunks
+        a.step(k)
+        b.step(k)
+    ua, ub = a.get("DISP"), b.get("DISP")
+    if prec == B.PD_FP64:
+        assert np.array_equal(ua, ub)
+        assert np.array_equal(a.get("VEL"), b.get("VEL"))
+    else:
+        assert np.linalg.norm(ua - ub) <= 1e-9 * np.linalg.norm(ua)
+    assert np.array_equal(a.get("BROKEN"), b.get("BROKEN"))
+    assert int(b.get("STEP")[0]) == 54
+    rc, st = b.status()
+    assert rc == B.PD_OK and st[4] == 0
+
+
+def test_autotune_keeps_the_state_and_the_results():
+    w = I.merge_aggregates(_parts())
+    a = _sim(w, B.PD_FP64)
+    b = _sim(w, B.PD_FP64)
+    a.step(50)
+    b.step(50)
+    before = {f: b.get(f) for f in ("DISP", "VEL", "ACC", "BROKEN", "STEP")}
+    rep = b.autotune()
+    assert rep["mode"] in (0, 1) and rep["lanes"] in (4, 8) and rep["ms_per_step"] > 0
+    for f, v in before.items():
+        assert np.array_equal(b.get(f), v), f
+    a.step(100)
+    b.step(100)
+    ua, ub = a.get("DISP"), b.get("DISP")
+    assert np.linalg.norm(ua - ub) <= 1e-12 * np.linalg.norm(ua)
+    assert np.array_equal(a.get("BROKEN"), b.get("BROKEN"))

@@ -1,0 +1,61 @@
+"""The surrogate network on the tensor cores (tcgen05, BF16 operands, FP32
+accumulation): forward and gradients against the NumPy reference network with
+the same bfloat16 rounding, and training that actually reduces the loss."""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+from paper_2108_07212_gb300 import binding as B
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _data(n, seed=0):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=(n, 32)).astype(np.float32)
+    A = rng.normal(scale=0.3, size=(32, 32))
+    t = (np.tanh(x @ A) + 0.1 * x[:, ::-1]).astype(np.float32)
+    return x, t
+
+
+@pytest.mark.parametrize("n", [1, 128, 300])
+def test_forward_matches_reference(n):
+    params = M.init_params(3)
+    x, _ = _data(n, 1)
+    net = B.MLP(max_batch=512, params=params)
+    y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    y_ref, _ = M.forward(params.astype(np.float64), x, bf16=True)
+    err = np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref)
+    assert err < 2e-3, err
+    y64, _ = M.forward(params.astype(np.float64), x)
+    assert np.linalg.norm(y - y64) / np.linalg.norm(y64) < 3e-2
+
+
+@pytest.mark.parametrize("n", [200, 1024])
+def test_gradients_match_reference(n):
+    params = M.init_params(5)
+    x, t = _data(n, 2)
+    net = B.MLP(max_batch=2048, params=params)
+    loss, g = net.loss_grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    loss_ref, g_ref = M.loss_grad(params.astype(np.float64), x, t, bf16=True)
+    assert loss == pytest.approx(loss_ref, rel=2e-3)
+    off = 0
+    for name, shape in M.SIZES:
+        k = int(np.prod(shape))
+        a, b = g[off:off + k], g_ref[off:off + k]
+        assert np.linalg.norm(a - b) <= 5e-3 * np.linalg.norm(b) + 1e-12, name
+        off += k
+
+
+def test_training_reduces_the_loss():
+    params = M.init_params(7)
+    x, t = _data(2048, 3)
+    net = B.MLP(max_batch=2048, params=params)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    first = net.train_step(xd, td, 3e-3)
+    for _ in range(300):
+        last = net.train_step(xd, td, 3e-3)
+    assert last < 0.1 * first, (first, last)
+    p = net.get_params()
+    assert np.all(np.isfinite(p)) and not np.array_equal(p, params)
