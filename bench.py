@@ -224,6 +224,212 @@ def precision_report(B, dev, stream, torch):
             "reference": "FP64 GPU path (matches the FP64 oracle to 1e-12 in the test-suite)"}
 
 
+# ---------------------------------------------------------------------------
+# workload legs at the sizes where HBM, not launch latency, bounds the step
+# (500-grain compaction, 64-aggregate ensemble, 2000-grain surrogate settling)
+
+# algorithmic bytes of one whole FP32-split time step per node (predict 80 B,
+# hash binning ~40 B incl. the bucket scan, force kernel 116 B) + 4 B per bond
+BYTES_PER_NODE_STEP_FP32 = 236
+
+
+def _event_time(stream, torch, fn):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def _force_kernel_ms(sim, n=20):
+    sim.set_timing(True)
+    ms = []
+    for _ in range(n):
+        sim.step(1)
+        ms.append(sim.kernel_times()["force"])
+    sim.set_timing(False)
+    return float(np.median(ms))
+
+
+def _roof_fp32(sim, f_ms, hbm, label):
+    nbytes = BYTES_PER_NODE_FP32 * sim.N + BYTES_PER_BOND_FP32 * sim.n_bonds
+    a = nbytes / (f_ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": "k_force32", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+            "traffic": None, "note": f"{label}: {BYTES_PER_NODE_FP32} B/node + {BYTES_PER_BOND_FP32} B/bond x "
+                                     f"{sim.N} nodes / {sim.n_bonds} bonds, median event time {f_ms * 1e3:.1f} us (of measured)"}
+
+
+def _roof_fp64(sim, f_ms, fp64_peak, label):
+    a = FLOPS_PER_BOND * sim.n_bonds / (f_ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": "k_force64", "achieved": a, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": a / fp64_peak, "traffic": None,
+            "note": f"{label}: {FLOPS_PER_BOND} FP64 ops/bond x {sim.n_bonds} bonds, median event time "
+                    f"{f_ms * 1e3:.1f} us; peak = measured cuBLAS DGEMM (of measured)"}
+
+
+def leg_compaction(B, I, dev, stream, torch, hbm, fp64_peak, steps=200):
+    """500 grains, ~5e5 nodes: FP64 path vs FP32 split, throughput, force error and
+    break disagreements on an agitated (colliding, fracturing) state."""
+    out = {}
+    w = I.compaction()
+    for prec, name in ((B.PD_FP64, "fp64"), (B.PD_FP32_SPLIT, "fp32")):
+        with torch.cuda.stream(stream):
+            sim = B.Simulation(w, precision=prec, device=dev, stream=stream)
+        sim.step(16)
+        dt = _event_time(stream, torch, lambda: sim.step(steps))
+        f_ms = _force_kernel_ms(sim)
+        out[name] = {"value": sim.N * steps / dt, "unit": "node-steps/s", "ms_per_step": 1e3 * dt / steps,
+                     "bond_evals_per_s": sim.n_bonds * steps / dt, "force_kernel_us": 1e3 * f_ms,
+                     "roofline": _roof_fp32(sim, f_ms, hbm, "500-grain compaction") if name == "fp32"
+                     else _roof_fp64(sim, f_ms, fp64_peak, "500-grain compaction"),
+                     "status": int(sim.status()[0])}
+        out["nodes"], out["directed_bonds"] = int(sim.N), int(sim.n_bonds)
+        del sim
+    out["speedup_fp32_vs_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    # precision report on the agitated state (grains thrown at 5 m/s in random directions)
+    wa = I.compaction(agitation=5.0)
+    with torch.cuda.stream(stream):
+        a = B.Simulation(wa, precision=B.PD_FP64, store_parts=True, device=dev, stream=stream)
+        b = B.Simulation(wa, precision=B.PD_FP32_SPLIT, store_parts=True, device=dev, stream=stream)
+    n_win = 600
+    a.step(n_win)
+    b.step(n_win)
+    n_dis = int(np.sum(a.get("BROKEN") != b.get("BROKEN")))
+    n_broken = int(a.get("BROKEN").sum())
+    for f in ("DISP", "VEL", "ACC", "BROKEN", "STEP"):
+        b.set(f, a.get(f))
+    a.eval_forces()
+    b.eval_forces()
+    Fa, Fb = a.get("FORCE"), b.get("FORCE")
+    out["precision_report"] = {
+        "workload": f"the same aggregate with every grain thrown at 5 m/s (seeded directions), {n_win} steps",
+        "force_rel_err_max_norm": float(np.abs(Fb - Fa).max() / np.abs(Fa).max()),
+        "broken_bonds_fp64": n_broken, f"break_disagreements_after_{n_win}_steps": n_dis}
+    out["workload"] = ("compaction of 500 mixed-shape grains, R~U[0.8,1.6] mm, h=R/23, box width 40 mm, "
+                       "top wall 0.1 m/s, dt=2e-8 s")
+    del a, b
+    return out
+
+
+def leg_ensemble(B, I, dev, stream, torch, hbm, steps=40):
+    """64 independent aggregates (20-200 grains each): one batched FP32 context on
+    the autotuned path vs 64 sequential runs of the separate aggregates
+    (FP32 graph of kernels, and the plain FP64 path)."""
+    w = I.ensemble()
+    with torch.cuda.stream(stream):
+        sim = B.Simulation(w, precision=B.PD_FP32_SPLIT, device=dev, stream=stream)
+    tune = sim.autotune()
+    sim.step(16)
+    dt = _event_time(stream, torch, lambda: sim.step(steps))
+    info = sim.info()
+    N = int(sim.N)
+    out = {"workload": "64 independent settling aggregates, 20-200 grains each (seeded), R~U[0.8,1.2] mm, h=R/21, "
+                       "dt=2e-8 s, own wall box each",
+           "nodes": N, "directed_bonds": int(sim.n_bonds),
+           "batched": {"value": N * steps / dt, "unit": "node-steps/s", "ms_per_step": 1e3 * dt / steps,
+                       "path": {"mode": "persistent" if int(info["mode"]) == 1 else "kernel graph",
+                                "lanes": int(info["lanes"]), "block": int(info["block"])},
+                       "autotune": tune, "status": int(sim.status()[0])}}
+    a = BYTES_PER_NODE_STEP_FP32 * N + BYTES_PER_BOND_FP32 * sim.n_bonds
+    out["batched"]["step_roofline"] = {"bound": "hbm", "achieved": a / (dt / steps) / 1e9, "peak": hbm, "unit": "GB/s",
+                                       "frac": a / (dt / steps) / 1e9 / hbm,
+                                       "note": f"{BYTES_PER_NODE_STEP_FP32} B/node + {BYTES_PER_BOND_FP32} B/bond per whole step (of measured)"}
+    del sim
+    torch.cuda.empty_cache()
+    for prec, name in ((B.PD_FP32_SPLIT, "sequential_fp32"), (B.PD_FP64, "sequential_fp64")):
+        sims = []
+        with torch.cuda.stream(stream):
+            for part in w.parts:
+                sims.append(B.Simulation(part, precision=prec, device=dev, stream=stream))
+        for s_ in sims:
+            s_.step(16)
+
+        def run():
+            for s_ in sims:
+                s_.step(steps)
+        dts = _event_time(stream, torch, run)
+        n_tot = sum(int(s_.N) for s_ in sims)
+        out[name] = {"value": n_tot * steps / dts, "unit": "node-steps/s", "ms_per_step": 1e3 * dts / steps}
+        del sims
+        torch.cuda.empty_cache()
+    out["speedup_batched_vs_sequential_fp32"] = out["batched"]["value"] / out["sequential_fp32"]["value"]
+    out["speedup_batched_vs_sequential_fp64"] = out["batched"]["value"] / out["sequential_fp64"]["value"]
+    return out
+
+
+def leg_surrogate(B, I, SU, dev, stream, torch, steps=200):
+    """2000 grains (~2e6 nodes, h=R/23), FP32 split: surrogate (networks trained
+    on snapshots of a small aggregate with the same templates) vs the plain
+    FP32 and FP64 paths."""
+    w = I.surrogate_settling()
+    # training snapshots: 60 grains of the same shapes and h/R, each thrown at
+    # 1 m/s in a seeded random direction so that collisions load them
+    wt = I.surrogate_settling(n_grains=60, seed=6)
+    with torch.cuda.stream(stream):
+        T = B.Simulation(wt, precision=B.PD_FP32_SPLIT, store_parts=True, device=dev, stream=stream,
+                         surrogate=lambda s_: SU.build_basis(s_))
+    ang = np.random.Generator(np.random.PCG64(66)).uniform(0.0, 2 * math.pi, wt.n_grains)
+    vg = np.stack([np.cos(ang), np.sin(ang)], 1)
+    T.set("VEL", vg[T.get("GRAIN")])
+    t0 = time.perf_counter()
+    data = SU.collect_samples(T, 1500, 15)
+    t_collect = time.perf_counter() - t0
+    with torch.cuda.stream(stream):
+        S = B.Simulation(w, precision=B.PD_FP32_SPLIT, device=dev, stream=stream,
+                         surrogate=lambda s_: SU.build_basis(s_, source=(T, T.surrogate_basis)))
+    cfg = S.surrogate_basis
+    lam = cfg["lambda_"].reshape(-1, cfg["n_modes"])
+    t0 = time.perf_counter()
+    src = {k: t for t, k in enumerate(SU.template_keys(T, T.surrogate_basis))}
+    counts = np.bincount(cfg["template_of_grain"])
+    nets, trained = [], 0
+    for t, key in enumerate(SU.template_keys(S, cfg)):
+        tt = src.get(key)
+        params = SU.init_params(0)
+        if tt is not None and tt in data:
+            params = SU.train_template(*data[tt], lam[t], epochs=400)[0]
+            trained += 1
+        nets.append(B.MLP(max_batch=int(counts[t]), stream=stream, params=params))
+        S.surrogate_set_mlp(t, nets[-1])
+    t_train = time.perf_counter() - t0
+    S.surrogate_enable(True)
+    with torch.cuda.stream(stream):
+        P = B.Simulation(w, precision=B.PD_FP32_SPLIT, device=dev, stream=stream)
+    out = {"workload": "settling of 2000 mixed-shape grains, R~U[1,1.5] mm, h=R/23, dt=2.5e-8 s, gravity 5000 m/s^2",
+           "nodes": int(S.N), "directed_bonds": int(S.n_bonds), "templates": len(cfg["templates"]),
+           "networks_trained": trained, "training": {"samples_s": t_collect, "train_s": t_train,
+                                                      "source": "60-grain aggregate of the same templates, 1500 steps"}}
+    res = {}
+    for sim, name in ((P, "plain_fp32"), (S, "surrogate")):
+        sim.step(16)
+        dt = _event_time(stream, torch, lambda: sim.step(steps))
+        res[name] = {"value": sim.N * steps / dt, "unit": "node-steps/s", "ms_per_step": 1e3 * dt / steps}
+    active, err, merr, maxs = S.surrogate_stats()
+    on = active == 1
+    res["surrogate"].update(active_grains=int(on.sum()), judged_err_p50=float(np.median(err[on])) if on.any() else None,
+                            judged_err_max=float(err[on].max()) if on.any() else None,
+                            judged_modal_err_p50=float(np.median(merr[on])) if on.any() else None,
+                            max_stretch_over_s0=float(maxs.max()))
+    u0, u1 = P.get("DISP"), S.get("DISP")
+    res["surrogate"]["traj_rel_l2_vs_plain"] = float(np.linalg.norm(u1 - u0) / max(np.linalg.norm(u0), 1e-300))
+    res["surrogate"]["status"] = int(S.status()[0])
+    del P
+    torch.cuda.empty_cache()
+    with torch.cuda.stream(stream):
+        D = B.Simulation(w, precision=B.PD_FP64, device=dev, stream=stream)
+    D.step(16)
+    dt = _event_time(stream, torch, lambda: D.step(steps // 4))
+    res["plain_fp64"] = {"value": D.N * (steps // 4) / dt, "unit": "node-steps/s", "ms_per_step": 4e3 * dt / steps}
+    out.update(res)
+    out["speedup_vs_plain_fp32"] = res["surrogate"]["value"] / res["plain_fp32"]["value"]
+    out["speedup_vs_plain_fp64"] = res["surrogate"]["value"] / res["plain_fp64"]["value"]
+    del D, S, T
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2108_07212_gb300 import binding as B
@@ -334,6 +540,25 @@ def run_ours(args):
         "gpu_launches": 6 * args.steps * (2 if sim64 is not None else 1),
         "status": int(rc),
     }
+    if world == 1 and args.legs:
+        from paper_2108_07212_gb300 import inputs as I
+        from paper_2108_07212_gb300 import surrogate as SU
+        hbm = float(peaks.get("hbm_gbs") or 6800.0)
+        fp64_peak = fp64_gemm_peak(torch, dev) if prec != B.PD_FP64 else fp64_peak
+        legs = {}
+        del sim, sim64
+        torch.cuda.empty_cache()
+        for name in args.legs.split(","):
+            t0 = time.perf_counter()
+            if name == "compaction":
+                legs[name] = leg_compaction(B, I, dev, stream, torch, hbm, fp64_peak)
+            elif name == "ensemble":
+                legs[name] = leg_ensemble(B, I, dev, stream, torch, hbm)
+            elif name == "surrogate":
+                legs[name] = leg_surrogate(B, I, SU, dev, stream, torch)
+            legs[name]["wall_s"] = time.perf_counter() - t0
+            torch.cuda.empty_cache()
+        line["legs"] = legs
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
@@ -349,6 +574,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--legs", default="compaction,ensemble,surrogate",
+                    help="comma-separated large-workload legs at N=1 ('' for none)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

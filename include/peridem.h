@@ -105,6 +105,7 @@ typedef struct pd_params {
 #define PD_FIELD_COL 12         /* int32[n_bonds] CSR columns (ascending per row)    */
 #define PD_FIELD_LATTICE 13     /* int32[2N] lattice indices (i, j) in grain frame   */
 #define PD_FIELD_STEP 14        /* int64[1] number of completed time steps (get/set) */
+#define PD_FIELD_GRAIN_TEMPLATE 15 /* int32[G] bond-network template of every grain (get) */
 
 /* ---- status word slots (pd_status) ------------------------------------------ */
 #define PD_STATUS_PENETRATION 0 /* node found past a wall (treated as touching)     */
@@ -219,12 +220,13 @@ int pd_diagnostics(pd_ctx *ctx, double *out);
  * PD_OK, or the first error code it implies (PD_ENUMERIC, PD_EOVERFLOW). */
 int pd_status(pd_ctx *ctx, int32_t *out);
 
-/* Scalar facts of the context (out has 14 slots): out[0] N, out[1] directed
+/* Scalar facts of the context (out has 15 slots): out[0] N, out[1] directed
  * bonds, out[2] grains, out[3] h_min, out[4] R_c, out[5] K_n (aggregate 0),
  * out[6] dt, out[7] completed steps, out[8] max bonds per node, out[9] contact
  * hash buckets, out[10] step path (0 graph of kernels, 1 persistent kernel),
  * out[11] threads per node, out[12] threads per block of the persistent
- * kernel, out[13] aggregates. */
+ * kernel, out[13] aggregates, out[14] bond-network templates (grains of one
+ * shape meshed at the same h/R share one lattice and one bond network). */
 int pd_info(pd_ctx *ctx, double *out);
 
 /*
@@ -310,6 +312,54 @@ int pd_mlp_loss_grad(pd_mlp *mlp, const float *x, const float *t, int batch, flo
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr; the
  * loss before the step is written to *loss_host when non-null (waits). */
 int pd_mlp_train_step(pd_mlp *mlp, const float *x, const float *t, int batch, float lr, float *loss_host);
+
+/*
+ * Learned per-grain modal surrogate (not in the paper; FP32-split path only).
+ * Each template t (PD_FIELD_GRAIN_TEMPLATE) has a basis Phi_t of n_modes
+ * vectors over its n_t nodes in the lattice frame of the template.  A grain is
+ * followed in its co-rotated frame (centroid and best-fit rotation of the
+ * current positions onto the reference ones); its deformation w gives modal
+ * coefficients q = Phi^T w / h, a network (pd_mlp) maps q to the modal bond
+ * force f = Phi^T F_bond / (E h), and the force kernel uses R Phi f E h in place
+ * of the bond loop for active grains.  Both basis products run per template
+ * as GEMMs over all of its active grains on the tensor cores (BF16 hi/lo
+ * split operands, FP32 accumulation).  Every judge_every steps the full bond
+ * kernel runs instead; a grain whose largest |s| exceeds gate * s0, or whose
+ * surrogate bond force differs from the full one by more than err_tol
+ * (relative, floored at the grain's weight), leaves the surrogate for good.
+ * Bonds of a surrogate grain do not break between judge steps.
+ */
+/* Before pd_bind_arena.  n_modes: 8, 16, 24 or 32.  basis: for t = 0, 1, ...
+ * the template's nodes in meshing order, per node n_modes x-components then
+ * n_modes y-components (copied; the library keeps its own layouts);
+ * lambda: per template the n_modes eigenvalues of the dimensionless
+ * linearised bond operator K / E (F / (E h) = -(K / E) w / h) for those modes.
+ * The modal force is f = -lambda q + net(q): the network learns the nonlinear
+ * correction (and is optional -- without one, no grain is active). */
+int pd_surrogate_setup(pd_ctx *ctx, int n_modes, const float *basis, const float *lambda, int judge_every,
+                       double gate, double err_tol);
+/* Network of template t (its max_batch >= grains of the template); NULL
+ * removes it and its grains leave the surrogate.  The network must stay alive
+ * while the context may step. */
+int pd_surrogate_set_mlp(pd_ctx *ctx, int tmpl, pd_mlp *mlp);
+/* on = 1: every grain of a template with a network becomes active; 0: off. */
+int pd_surrogate_enable(pd_ctx *ctx, int on);
+/* Training pairs at the current state (needs store_parts): per grain the modal
+ * coefficients q and the modal FULL bond force f, host float[G][n_modes] each
+ * (grains without a template: untouched).  Bonds may break, as in pd_eval_forces. */
+int pd_surrogate_sample(pd_ctx *ctx, float *q_host, float *f_host);
+/* Per grain (host, nullable): active flag, last judged relative error of the
+ * nodal bond force (the fallback criterion), last judged relative error of the
+ * modal bond force f (what the network predicts; floored likewise), last
+ * judged max |s| / s0. */
+int pd_surrogate_stats(pd_ctx *ctx, int32_t *active_host, float *err_host, float *merr_host, float *maxs_host);
+/* The surrogate phases at the current state, as pd_eval_forces (which this
+ * runs; with store_parts the bond part of PD_FIELD_FORCE_PARTS then holds the
+ * surrogate force of active grains unless the step is a judge step): per grain
+ * the network input q and the modal force f = -lambda q + net(q), host
+ * float[G][n_modes] each (zero rows for grains without a template).  Needs the
+ * surrogate enabled; waits. */
+int pd_surrogate_inspect(pd_ctx *ctx, float *q_host, float *y_host);
 
 /* ---- diagnostics without device allocation ---------------------------------- */
 #define PD_NOALLOC_MAX_NODES 2097152

@@ -20,7 +20,7 @@ c_double, c_int32, c_int64, c_size_t, c_void_p = (ctypes.c_double, ctypes.c_int3
 PD_OK, PD_EINVAL, PD_ESTATE, PD_ECUDA, PD_ENUMERIC, PD_EOVERFLOW, PD_ENOMEM, PD_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 PD_FP64, PD_FP32_SPLIT = 0, 1
 FIELDS = dict(X=0, DISP=1, VEL=2, ACC=3, POS=4, FORCE=5, FORCE_PARTS=6, BROKEN=7, DAMAGE=8, GRAIN=9,
-              VOLUME=10, ROW_PTR=11, COL=12, LATTICE=13, STEP=14)
+              VOLUME=10, ROW_PTR=11, COL=12, LATTICE=13, STEP=14, GRAIN_TEMPLATE=15)
 STATUS_COUNT = 8
 DIAG_COUNT = 8
 DIAG_NAMES = ("KE", "E_bond", "Px", "Py", "Lz", "n_broken")
@@ -30,7 +30,9 @@ SYMBOLS = ("pd_last_error", "pd_create", "pd_destroy", "pd_mesh_grains", "pd_bui
            "pd_bind_arena", "pd_step", "pd_get_state", "pd_set_state", "pd_eval_forces", "pd_diagnostics",
            "pd_status", "pd_info", "pd_set_timing", "pd_kernel_times", "pd_set_aggregates", "pd_autotune", "pd_set_path", "pd_mlp_create", "pd_mlp_destroy",
            "pd_mlp_arena_bytes", "pd_mlp_bind_arena", "pd_mlp_set_params", "pd_mlp_get_params", "pd_mlp_forward",
-           "pd_mlp_loss_grad", "pd_mlp_train_step")
+           "pd_mlp_loss_grad", "pd_mlp_train_step", "pd_surrogate_setup", "pd_surrogate_set_mlp",
+           "pd_surrogate_enable", "pd_surrogate_sample", "pd_surrogate_stats", "pd_surrogate_inspect",
+           "pd_diagnostics_noalloc")
 
 
 class PdParams(ctypes.Structure):
@@ -91,6 +93,11 @@ def load():
             L.pd_mlp_forward.argtypes = [vp, vp, vp, ip]
             L.pd_mlp_loss_grad.argtypes = [vp, vp, vp, ip, vp, vp]
             L.pd_mlp_train_step.argtypes = [vp, vp, vp, ip, ctypes.c_float, vp]
+            L.pd_surrogate_setup.argtypes = [vp, ip, vp, vp, ip, c_double, c_double]
+            L.pd_surrogate_set_mlp.argtypes = [vp, ip, vp]
+            L.pd_surrogate_enable.argtypes = [vp, ip]
+            L.pd_surrogate_sample.argtypes = [vp, vp, vp]
+            L.pd_surrogate_stats.argtypes = [vp, vp, vp, vp]
             for name in SYMBOLS:
                 if name != "pd_last_error":
                     getattr(L, name).restype = ip
@@ -133,7 +140,7 @@ class Simulation:
     """
 
     def __init__(self, workload, precision: int | str = PD_FP64, store_parts: bool = False, device=None,
-                 stream=None, lanes: int = 0):
+                 stream=None, lanes: int = 0, surrogate=None):
         L = load()
         if isinstance(precision, str):
             precision = {"fp64": PD_FP64, "fp32": PD_FP32_SPLIT, "fp32_split": PD_FP32_SPLIT}[precision]
@@ -166,6 +173,15 @@ class Simulation:
             ga = np.ascontiguousarray(agg, dtype=np.int32)
             walls = np.ascontiguousarray(workload.agg_walls, dtype=np.float64).reshape(-1)
             _check(L.pd_set_aggregates(ctx, int(walls.size // 8), _ptr(ga), _ptr(walls)))
+        self.surrogate_basis = None
+        if surrogate is not None:
+            # surrogate = dict(basis=..., lambda_=..., n_modes=, judge_every=, gate=, err_tol=) or a callable
+            cfg = surrogate(self) if callable(surrogate) else surrogate
+            basis = np.ascontiguousarray(cfg["basis"], dtype=np.float32)
+            lam = np.ascontiguousarray(cfg["lambda_"], dtype=np.float32)
+            _check(L.pd_surrogate_setup(ctx, int(cfg["n_modes"]), _ptr(basis), _ptr(lam), int(cfg.get("judge_every", 50)),
+                                        float(cfg.get("gate", 0.5)), float(cfg.get("err_tol", 1e-3))))
+            self.surrogate_basis = cfg
         if device is not None:
             self.bind()
 
@@ -221,6 +237,8 @@ class Simulation:
             return np.zeros(self.n_bonds, dtype=np.int32)
         if field == "STEP":
             return np.zeros(1, dtype=np.int64)
+        if field == "GRAIN_TEMPLATE":
+            return np.zeros(self.workload.n_grains, dtype=np.int32)
         raise KeyError(field)
 
     def get(self, field: str) -> np.ndarray:
@@ -266,11 +284,47 @@ class Simulation:
         return dict(predict=out[0], bin=out[1], force=out[2], step=out[3])
 
     def info(self) -> dict:
-        out = np.zeros(14)
+        out = np.zeros(15)
         _check(load().pd_info(self._ctx, _ptr(out)))
         keys = ("N", "n_bonds", "G", "h_min", "Rc", "Kn", "dt", "steps", "max_row", "buckets", "mode", "lanes",
-                "block", "n_agg")
+                "block", "n_agg", "n_templates")
         return dict(zip(keys, out))
+
+    # -- learned modal surrogate ---------------------------------------------------
+    def surrogate_set_mlp(self, tmpl: int, mlp):
+        self._mlps = getattr(self, "_mlps", {})
+        self._mlps[tmpl] = mlp           # keep the network alive while the context uses it
+        _check(load().pd_surrogate_set_mlp(self._ctx, int(tmpl), mlp._h if mlp is not None else None))
+
+    def surrogate_enable(self, on: bool = True):
+        _check(load().pd_surrogate_enable(self._ctx, 1 if on else 0))
+
+    def surrogate_sample(self):
+        M = int(self.surrogate_basis["n_modes"])
+        G = self.workload.n_grains
+        q = np.zeros((G, M), dtype=np.float32)
+        f = np.zeros((G, M), dtype=np.float32)
+        _check(load().pd_surrogate_sample(self._ctx, _ptr(q), _ptr(f)))
+        return q, f
+
+    def surrogate_stats(self):
+        """Per grain: active flag, judged nodal error, judged modal error, judged max |s|/s0."""
+        G = self.workload.n_grains
+        a = np.zeros(G, dtype=np.int32)
+        e = np.zeros(G, dtype=np.float32)
+        me = np.zeros(G, dtype=np.float32)
+        m = np.zeros(G, dtype=np.float32)
+        _check(load().pd_surrogate_stats(self._ctx, _ptr(a), _ptr(e), _ptr(me), _ptr(m)))
+        return a, e, me, m
+
+    def surrogate_inspect(self):
+        """Network input q and modal force f of every grain at the current state."""
+        M = int(self.surrogate_basis["n_modes"])
+        G = self.workload.n_grains
+        q = np.zeros((G, M), dtype=np.float32)
+        y = np.zeros((G, M), dtype=np.float32)
+        _check(load().pd_surrogate_inspect(self._ctx, _ptr(q), _ptr(y)))
+        return q, y
 
     def set_path(self, mode: int, lanes: int = 8, block: int = 128):
         """0 = graph of separate kernels, 1 = persistent cooperative kernel."""

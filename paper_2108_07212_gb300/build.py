@@ -28,6 +28,7 @@ CU_SOURCES = [
     ("pd_step32.cu", []),
     ("pd_noalloc.cu", []),
     ("pd_mlp.cu", []),
+    ("pd_surrogate.cu", []),
 ]
 CPP_SOURCES = ["pd_host.cpp"]
 

@@ -23,8 +23,10 @@ __device__ __forceinline__ T ldm(const T *p) {
 // (T a power of two >= 2N): every pair closer than R_c lies in the 3x3 cell
 // block around either node; aliasing cells only add candidates, which the
 // distance test rejects.
-__device__ __forceinline__ int cell_coord(double x, double origin, double cell) {
-    double f = floor((x - origin) / cell);
+// Hash-grid cell index of a coordinate (inv_cell = 1 / cell side).  Only the
+// binning kernel calls this; the force kernels read the stored cells.
+__device__ __forceinline__ int cell_coord(double x, double origin, double inv_cell) {
+    double f = floor((x - origin) * inv_cell);
     if (!(f > -1048576.0)) return -1048576;  // also catches NaN
     if (f > 1048576.0) return 1048576;
     return (int)f;
@@ -265,7 +267,9 @@ __device__ __forceinline__ void predict_node(const DevPtrs &d, const KParams &k,
         d.ph[i] = ph;
         d.pl[i] = make_float2((float)(qx - (double)ph.x), (float)(qy - (double)ph.y));
     }
-    unsigned b = cell_bucket(cell_coord(p.x, A.ox, A.cell), cell_coord(p.y, A.oy, A.cell), ag, k.T);
+    const int cx = cell_coord(p.x, A.ox, A.inv_cell), cy = cell_coord(p.y, A.oy, A.inv_cell);
+    d.cell[i] = make_int2(cx, cy);
+    unsigned b = cell_bucket(cx, cy, ag, k.T);
     d.key[i] = (int)b;
     atomicAdd(&d.count[b], 1);
 }
@@ -275,20 +279,17 @@ __device__ __forceinline__ void predict_node(const DevPtrs &d, const KParams &k,
 // cells lane, lane + LANES, ... of the 3x3 block, in ascending node index.
 // DIST(j) returns true when j is within R_c.
 template <bool PERSIST, int LANES, class Dist>
-__device__ __forceinline__ int gather_candidates(const DevPtrs &d, const KParams &k, const AggParams &A, int ag,
-                                                 int i, double px, double py, int lane, bool active, int *cand,
-                                                 Dist within) {
+__device__ __forceinline__ int gather_candidates(const DevPtrs &d, const KParams &k, int ag, int i, int lane,
+                                                 bool active, int *cand, Dist within) {
     int nc = 0;
     if (!active) return 0;
-    const int cx = cell_coord(px, A.ox, A.cell), cy = cell_coord(py, A.oy, A.cell);
-    unsigned bk[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) bk[c] = cell_bucket(cx + (c % 3) - 1, cy + (c / 3) - 1, ag, k.T);
+    const int2 cc = ldm<PERSIST>(&d.cell[i]);      // cell of node i, from the binning phase
     for (int c = lane; c < 9; c += LANES) {
+        const unsigned bc = cell_bucket(cc.x + (c % 3) - 1, cc.y + (c / 3) - 1, ag, k.T);
         bool dup = false;
-        for (int q = 0; q < c; ++q) dup |= bk[q] == bk[c];
+        for (int q = 0; q < c; ++q) dup |= cell_bucket(cc.x + (q % 3) - 1, cc.y + (q / 3) - 1, ag, k.T) == bc;
         if (dup) continue;
-        const int t0 = ldm<PERSIST>(&d.start[bk[c]]), t1 = ldm<PERSIST>(&d.start[bk[c] + 1]);
+        const int t0 = ldm<PERSIST>(&d.start[bc]), t1 = ldm<PERSIST>(&d.start[bc + 1]);
         for (int t = t0; t < t1; ++t) {
             const int j = ldm<PERSIST>(&d.sorted[t]);
             // hash aliasing can bring nodes of another aggregate: never in contact
@@ -403,7 +404,7 @@ __device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k,
     // contact candidates, self-contact (Sec. 4.4), inter-grain contact (Secs. 4.1-4.3)
     int cand[kMaxCand];
     const double Rc = A.Rc;
-    const int nc = gather_candidates<PERSIST, LANES>(d, k, A, ag, ii, pi.x, pi.y, lane, active, cand, [&](int j) {
+    const int nc = gather_candidates<PERSIST, LANES>(d, k, ag, ii, lane, active, cand, [&](int j) {
         const double2 pj = ldm<PERSIST>(&d.p[j]);
         double dx = pj.x - pi.x, dy = pj.y - pi.y;
         return sqrt(dx * dx + dy * dy) < Rc;
@@ -488,7 +489,23 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
 
     float Fbx = 0.f, Fby = 0.f;
     const float VV = Vi * Vi;
-    for (int b = r0 + lane; b < r1; b += LANES) {
+    // learned modal surrogate: between judge steps an active grain's bond force
+    // is R(theta + phi) Phi f E h (expanded on the tensor cores) instead of the bond loop
+    bool sur = false, judge = false;
+    if constexpr (!PERSIST) {
+        if (k.sur && active) {
+            sur = d.sur_active[gi] != 0;
+            judge = (*d.step) % k.judge_every == 0;
+        }
+    }
+    if (sur && !judge && lane == 0) {
+        const float2 f = d.sur_f[ii];                     // Phi f, lattice frame, units of E h
+        const float2 rot = d.sur_rot[gi];
+        const float Eh = k.E * gq.x;
+        Fbx = (rot.x * f.x - rot.y * f.y) * Eh;
+        Fby = (rot.y * f.x + rot.x * f.y) * Eh;
+    }
+    for (int b = r0 + lane; b < r1 && !(sur && !judge); b += LANES) {
         const int kk = b - r0;
         if ((__ldcg(&bw[kk >> 5]) >> (kk & 31)) & 1u) continue;
         const int j = __ldg(&d.col[b]);
@@ -529,8 +546,7 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
     __syncwarp();
 
     int cand[kMaxCand];
-    const double2 pi64 = ldm<PERSIST>(&d.p[ii]);
-    const int nc = gather_candidates<PERSIST, LANES>(d, k, A, ag, ii, pi64.x, pi64.y, lane, active, cand, [&](int j) {
+    const int nc = gather_candidates<PERSIST, LANES>(d, k, ag, ii, lane, active, cand, [&](int j) {
         const float2 phj = ldm<PERSIST>(&d.ph[j]), plj = ldm<PERSIST>(&d.pl[j]);
         float L2h, L2l;
         len2_ff(__fsub_rn(phj.x, phi.x), plj.x - pli.x, __fsub_rn(phj.y, phi.y), plj.y - pli.y, L2h, L2l);
@@ -593,8 +609,10 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
     Fnx = lane_sum<LANES>(Fnx);
     Fny = lane_sum<LANES>(Fny);
     if (!active || lane != 0) return;
+    if (sur && judge) d.sur_fb[i] = make_float2(Fbx, Fby);   // full bond force for the judge
     const double Vi64 = __ldg(&d.V[i]);
     double Fwx, Fwy;
+    const double2 pi64 = ldm<PERSIST>(&d.p[i]);
     wall_force64(k, A, ldm<PERSIST>(d.t_now), pi64.x, pi64.y, vi.x, vi.y, Vi64, Fwx, Fwy, d.status);
     finish_node<PERSIST>(d, k, i, vin, update_v, vi, Vi64, (double)Fbx, (double)Fby, (double)Fsx, (double)Fsy,
                          (double)Fnx, (double)Fny, Fwx, Fwy);

@@ -209,6 +209,18 @@ struct pd_ctx {
     cudaGraphExec_t timed[2] = {nullptr, nullptr};
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int timing = 0;
+    // learned modal surrogate
+    std::vector<int32_t> g_shape, g_tmpl, g_slot, tmpl_first, tmpl_count, tmpl_nodes;
+    std::vector<double> g_theta;
+    int n_tmpl = 0;
+    bool sur_cfg = false;
+    int sur_modes = 32, sur_judge = 50;
+    double sur_gate = 0.5, sur_tol = 1e-3;
+    std::vector<float> sur_basis, sur_lambda;   // basis: per template mode-major, padded rows
+    std::vector<uint16_t> bnm_hi, bnm_lo, bmm_hi, bmm_lo;
+    std::vector<int32_t> tmpl_rows, slot_grain;
+    std::vector<int4> proj_work, exp_work;
+    std::vector<pd_mlp *> sur_mlp;
 };
 
 namespace {
@@ -235,7 +247,9 @@ void compute_aggregates(pd_ctx *c) {
         A.wv[0] = w[4]; A.wv[1] = w[5]; A.wv[2] = w[6]; A.wv[3] = w[7];
         A.ox = w[0];
         A.oy = w[2];
-        A.cell = A.Rc;
+        // a hair above R_c: two nodes closer than R_c never land two cells apart
+        A.cell = A.Rc * (1.0 + 1e-9);
+        A.inv_cell = 1.0 / A.cell;
         // FP32 split: shift coordinates of the box into [L, 2L) so nearby
         // positions share a binade and their float differences are exact
         double Lx = std::max(w[1] - w[0], 1e-6), Ly = std::max(w[3] - w[2], 1e-6);
@@ -255,6 +269,35 @@ void compute_aggregates(pd_ctx *c) {
 namespace {
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// BF16 (round to nearest even) of a finite float, and back.
+uint16_t to_bf16(float v) {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+float from_bf16(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float v;
+    std::memcpy(&v, &u, 4);
+    return v;
+}
+
+// v = hi + lo to about 2^-17 relative, both BF16.
+void bf16_split(float v, uint16_t &hi, uint16_t &lo) {
+    hi = to_bf16(v);
+    lo = to_bf16(v - from_bf16(hi));
+}
+
+// Largest number of projection chunks of any template.
+int sur_max_chunks(const pd_ctx *c) {
+    int mx = 0;
+    for (size_t t = 0; t + 1 < c->tmpl_rows.size(); ++t)
+        mx = std::max(mx, (c->tmpl_rows[t + 1] - c->tmpl_rows[t]) / pd::kSurChunk);
+    return mx;
+}
 
 template <class T>
 void carve(char *base, size_t &off, T *&ptr, size_t count) {
@@ -286,6 +329,7 @@ size_t layout(pd_ctx *c, char *base) {
     carve(base, off, d.g_agg, G);
     carve(base, off, d.agg, (size_t)c->n_agg);
     carve(base, off, d.key, N);
+    carve(base, off, d.cell, N);
     carve(base, off, d.count, c->T);
     carve(base, off, d.start, (size_t)c->T + 1);
     carve(base, off, d.cursor, c->T);
@@ -313,6 +357,51 @@ size_t layout(pd_ctx *c, char *base) {
     carve(base, off, d.bv, N);
     carve(base, off, d.ba, N);
     carve(base, off, d.bbits, N * (size_t)c->wpn);
+    if (c->sur_cfg) {
+        const size_t M = (size_t)c->sur_modes, T = (size_t)c->n_tmpl;
+        carve(base, off, d.g_start, G + 1);
+        carve(base, off, d.g_tmpl, G);
+        carve(base, off, d.g_slot, G);
+        carve(base, off, d.tmpl_node, T + 1);
+        carve(base, off, d.tmpl_slot, T + 1);
+        carve(base, off, d.basis, c->sur_basis.size());
+        carve(base, off, d.bnm_hi, c->bnm_hi.size());
+        carve(base, off, d.bnm_lo, c->bnm_lo.size());
+        carve(base, off, d.bmm_hi, c->bmm_hi.size());
+        carve(base, off, d.bmm_lo, c->bmm_lo.size());
+        carve(base, off, d.tmpl_rows, T + 1);
+        carve(base, off, d.slot_grain, G);
+        carve(base, off, d.proj_work, c->proj_work.size());
+        carve(base, off, d.exp_work, c->exp_work.size());
+        carve(base, off, d.sur_w, N);
+        carve(base, off, d.sur_f, N);
+        carve(base, off, d.sur_xpart, (size_t)(c->tmpl_rows.empty() ? 0 : sur_max_chunks(c)) * G * M);
+        carve(base, off, d.sur_merr, G);
+        carve(base, off, d.sur_lambda, T * M);
+        carve(base, off, d.g_theta, G);
+        carve(base, off, d.g_xbar, G);
+        carve(base, off, d.sur_active, G);
+        carve(base, off, d.sur_rot, G);
+        carve(base, off, d.sur_phi, G);
+        carve(base, off, d.sur_x, G * M);
+        carve(base, off, d.sur_y, G * M);
+        carve(base, off, d.sur_fb, N);
+        carve(base, off, d.sur_err, G);
+        carve(base, off, d.sur_maxs, G);
+        carve(base, off, d.sur_qs, G * M);
+        carve(base, off, d.sur_fs, G * M);
+    } else {
+        d.g_start = d.g_tmpl = d.g_slot = d.tmpl_node = d.tmpl_slot = d.sur_active = nullptr;
+        d.tmpl_rows = d.slot_grain = nullptr;
+        d.bnm_hi = d.bnm_lo = d.bmm_hi = d.bmm_lo = nullptr;
+        d.proj_work = d.exp_work = nullptr;
+        d.sur_w = d.sur_f = nullptr;
+        d.sur_xpart = d.sur_merr = nullptr;
+        d.basis = d.sur_x = d.sur_y = d.sur_err = d.sur_maxs = d.sur_qs = d.sur_fs = d.sur_lambda = nullptr;
+        d.g_theta = d.sur_phi = nullptr;
+        d.g_xbar = nullptr;
+        d.sur_rot = d.sur_fb = nullptr;
+    }
     return off;
 }
 
@@ -320,6 +409,28 @@ int check_ctx(pd_ctx *c, int min_state) {
     if (!c) return fail(PD_EINVAL, "null context");
     if (c->state < min_state) return fail(PD_ESTATE, "call out of order");
     return PD_OK;
+}
+
+// Surrogate phases before the force kernel: co-rotated local deformation of
+// the active grains, its projection on the basis (tensor cores), every
+// template's network on its batch of grains, f = -Lambda q + net(q), and the
+// expansion of f to nodal bond forces (tensor cores).
+cudaError_t record_surrogate(pd_ctx *c, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = pd::launch_sur_frame(c->d, c->kp, 0, s)) != cudaSuccess) return e;
+    if ((e = pd::launch_sur_project_tc(c->d, c->kp, s)) != cudaSuccess) return e;
+    if ((e = pd::launch_sur_reduce(c->d, c->kp, s)) != cudaSuccess) return e;
+    int slot0 = 0;
+    for (int t = 0; t < c->n_tmpl; ++t) {
+        if (c->sur_mlp[t]) {
+            const size_t off = (size_t)slot0 * c->sur_modes;
+            if (pd::mlp_forward_stream(c->sur_mlp[t], c->d.sur_x + off, c->d.sur_y + off, c->tmpl_count[t], s) != PD_OK)
+                return cudaErrorLaunchFailure;
+        }
+        slot0 += c->tmpl_count[t];
+    }
+    if ((e = pd::launch_sur_combine(c->d, c->kp, s)) != cudaSuccess) return e;
+    return pd::launch_sur_expand_tc(c->d, c->kp, s);
 }
 
 // Record one time step (Algorithm 1) on stream s: displacement update and
@@ -332,8 +443,10 @@ cudaError_t record_step(pd_ctx *c, int vin, cudaStream_t s, bool timed = false) 
     if ((e = pd::launch_predict(c->d, c->kp, vin, 1, s)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     if ((e = pd::launch_bin(c->d, c->kp, s)) != cudaSuccess) return e;
+    if (c->kp.sur && (e = record_surrogate(c, s)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     if ((e = pd::launch_force(c->d, c->kp, vin, 1, s)) != cudaSuccess) return e;
+    if (c->kp.sur && (e = pd::launch_sur_judge(c->d, c->kp, s)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -356,7 +469,7 @@ int capture(pd_ctx *c, int vstart, int nsteps, cudaGraphExec_t *out, bool timed 
     PD_CUDA(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
     int v = vstart;
     cudaError_t e = cudaSuccess;
-    if (c->mode == 1) {
+    if (c->mode == 1 && !c->kp.sur) {
         e = record_persistent(c, v, nsteps, c->capture_stream, timed);
     } else {
         for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
@@ -400,6 +513,7 @@ size_t field_bytes(pd_ctx *c, int f) {
         case PD_FIELD_COL: return 4 * c->col.size();
         case PD_FIELD_LATTICE: return 8 * N;
         case PD_FIELD_STEP: return 8;
+        case PD_FIELD_GRAIN_TEMPLATE: return 4 * (size_t)c->G;
         default: return 0;
     }
 }
@@ -486,6 +600,8 @@ int pd_mesh_grains(pd_ctx *c, int n_shapes, const int32_t *shape_loop_start, con
                 o.loops.push_back(lp);
             }
             c->g_h[g] = h;
+            c->g_shape.push_back(s);
+            c->g_theta.push_back(th);
             c->g_cx[g] = cx;
             c->g_cy[g] = cy;
             c->g_R[g] = R;
@@ -628,6 +744,39 @@ int pd_build_bonds(pd_ctx *c, int64_t *n_bonds_out) {
         return fail(PD_ENOMEM, "out of host memory while building bonds");
     }
     c->wpn = std::max(1, (c->max_row + 31) / 32);
+    // bond-network templates: grains of one shape meshed at the same h/R have
+    // the same lattice (and so the same bonds) -- verified node by node
+    c->g_tmpl.assign(c->G, -1);
+    c->tmpl_first.clear();
+    c->tmpl_count.clear();
+    c->tmpl_nodes.clear();
+    c->g_slot.assign(c->G, 0);
+    for (int g = 0; g < c->G; ++g) {
+        const int64_t a0 = c->g_start[g], n = c->g_start[g + 1] - a0;
+        for (int t = 0; t < (int)c->tmpl_first.size() && c->g_tmpl[g] < 0; ++t) {
+            const int r = c->tmpl_first[t];
+            const int64_t b0 = c->g_start[r];
+            if (c->g_shape[r] != c->g_shape[g] || c->g_start[r + 1] - b0 != n) continue;
+            if (std::fabs(c->g_R[r] / c->g_h[r] - c->g_R[g] / c->g_h[g]) > 1e-9 * (c->g_R[g] / c->g_h[g])) continue;
+            if (!std::equal(c->lat.begin() + 2 * a0, c->lat.begin() + 2 * (a0 + n), c->lat.begin() + 2 * b0)) continue;
+            bool same = true;
+            for (int64_t x = 0; x < n && same; ++x) {
+                const int32_t ra = c->row_ptr[a0 + x + 1] - c->row_ptr[a0 + x], rb = c->row_ptr[b0 + x + 1] - c->row_ptr[b0 + x];
+                same = ra == rb;
+                for (int32_t q = 0; q < ra && same; ++q)
+                    same = c->col[c->row_ptr[a0 + x] + q] - a0 == c->col[c->row_ptr[b0 + x] + q] - b0;
+            }
+            if (same) c->g_tmpl[g] = t;
+        }
+        if (c->g_tmpl[g] < 0) {
+            c->g_tmpl[g] = (int)c->tmpl_first.size();
+            c->tmpl_first.push_back(g);
+            c->tmpl_count.push_back(0);
+            c->tmpl_nodes.push_back((int)n);
+        }
+        c->g_slot[g] = c->tmpl_count[c->g_tmpl[g]]++;
+    }
+    c->n_tmpl = (int)c->tmpl_first.size();
     // contact hash: power of two >= 2N buckets
     unsigned T = 1024;
     while ((int64_t)T < 2 * c->N) T <<= 1;
@@ -670,6 +819,15 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     k.half_dt2 = 0.5 * p.dt * p.dt;
     k.guard = 1e-4f;
     k.fp32 = p.precision == PD_FP32_SPLIT ? 1 : 0;
+    k.sur = 0;
+    k.n_modes = c->sur_modes;
+    k.judge_every = c->sur_judge;
+    k.E = (float)p.E;
+    k.gate = (float)c->sur_gate;
+    k.err_tol = (float)c->sur_tol;
+    k.n_proj_work = (int)c->proj_work.size();
+    k.n_exp_work = (int)c->exp_work.size();
+    k.n_rows = (int)c->slot_grain.size();
     k.micro = p.micromodulus;
     k.store = p.store_parts ? 1 : 0;
     k.lanes = p.lanes == 0 ? 8 : p.lanes;
@@ -698,6 +856,58 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     PD_CUDA(cudaMemcpyAsync(d.agg, c->aggp.data(), sizeof(pd::AggParams) * c->aggp.size(), cudaMemcpyHostToDevice, s));
     PD_CUDA(cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), s));
     PD_CUDA(cudaMemsetAsync(d.t_now, 0, sizeof(double), s));
+    std::vector<int32_t> gstart32, tnode, tslot;
+    std::vector<double> xbar;
+    if (c->sur_cfg) {
+        gstart32.assign(c->g_start.begin(), c->g_start.end());
+        tnode.assign(c->n_tmpl + 1, 0);
+        tslot.assign(c->n_tmpl + 1, 0);
+        for (int t = 0; t < c->n_tmpl; ++t) {
+            tnode[t + 1] = tnode[t] + c->tmpl_nodes[t];
+            tslot[t + 1] = tslot[t] + c->tmpl_count[t];
+        }
+        xbar.assign(2 * G, 0.0);
+        for (size_t g = 0; g < G; ++g) {
+            double sx = 0, sy = 0;
+            for (int64_t x = c->g_start[g]; x < c->g_start[g + 1]; ++x) {
+                sx += c->X[2 * x];
+                sy += c->X[2 * x + 1];
+            }
+            const double n = (double)(c->g_start[g + 1] - c->g_start[g]);
+            xbar[2 * g] = sx / n;
+            xbar[2 * g + 1] = sy / n;
+        }
+        PD_CUDA(cudaMemcpyAsync(d.g_start, gstart32.data(), 4 * (G + 1), cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.g_tmpl, c->g_tmpl.data(), 4 * G, cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.g_slot, c->g_slot.data(), 4 * G, cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.tmpl_node, tnode.data(), 4 * tnode.size(), cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.tmpl_slot, tslot.data(), 4 * tslot.size(), cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.basis, c->sur_basis.data(), 4 * c->sur_basis.size(), cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.bnm_hi, c->bnm_hi.data(), 2 * c->bnm_hi.size(), cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.bnm_lo, c->bnm_lo.data(), 2 * c->bnm_lo.size(), cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.bmm_hi, c->bmm_hi.data(), 2 * c->bmm_hi.size(), cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.bmm_lo, c->bmm_lo.data(), 2 * c->bmm_lo.size(), cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.tmpl_rows, c->tmpl_rows.data(), 4 * c->tmpl_rows.size(), cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.slot_grain, c->slot_grain.data(), 4 * c->slot_grain.size(), cudaMemcpyHostToDevice, s));
+        if (!c->proj_work.empty())
+            PD_CUDA(cudaMemcpyAsync(d.proj_work, c->proj_work.data(), sizeof(int4) * c->proj_work.size(),
+                                    cudaMemcpyHostToDevice, s));
+        if (!c->exp_work.empty())
+            PD_CUDA(cudaMemcpyAsync(d.exp_work, c->exp_work.data(), sizeof(int4) * c->exp_work.size(),
+                                    cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemsetAsync(d.sur_w, 0, 8 * N, s));
+        PD_CUDA(cudaMemsetAsync(d.sur_f, 0, 8 * N, s));
+        PD_CUDA(cudaMemsetAsync(d.sur_merr, 0, 4 * G, s));
+        PD_CUDA(pd::sur_init_attributes());
+        PD_CUDA(cudaMemcpyAsync(d.sur_lambda, c->sur_lambda.data(), 4 * c->sur_lambda.size(), cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.g_theta, c->g_theta.data(), 8 * G, cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.g_xbar, xbar.data(), 16 * G, cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemsetAsync(d.sur_active, 0, 4 * G, s));
+        PD_CUDA(cudaMemsetAsync(d.sur_y, 0, 4 * G * c->sur_modes, s));
+        PD_CUDA(cudaMemsetAsync(d.sur_err, 0, 4 * G, s));
+        PD_CUDA(cudaMemsetAsync(d.sur_maxs, 0, 4 * G, s));
+        c->sur_mlp.assign(c->n_tmpl, nullptr);
+    }
     PD_CUDA(cudaMemsetAsync(d.step, 0, 8, s));
     PD_CUDA(cudaMemsetAsync(d.status, 0, 4 * PD_STATUS_COUNT, s));
     std::vector<float> gq;
@@ -736,6 +946,7 @@ int pd_eval_forces(pd_ctx *c) {
     PD_CUDA(cudaMemsetAsync(c->d.count, 0, sizeof(int) * c->T, s));
     PD_CUDA(pd::launch_predict(c->d, c->kp, c->vcur, 0, s));
     PD_CUDA(pd::launch_bin(c->d, c->kp, s));
+    if (c->kp.sur) PD_CUDA(record_surrogate(c, s));
     PD_CUDA(pd::launch_force(c->d, c->kp, c->vcur, 0, s));
     return PD_OK;
 }
@@ -782,6 +993,7 @@ int pd_get_state(pd_ctx *c, int field, void *dst, size_t bytes, int dst_on_devic
         case PD_FIELD_LATTICE: host = c->lat.data(); break;
         case PD_FIELD_ROW_PTR: if (c->state >= 2) host = c->row_ptr.data(); break;
         case PD_FIELD_COL: if (c->state >= 2) host = c->col.data(); break;
+        case PD_FIELD_GRAIN_TEMPLATE: if (c->state >= 2) host = c->g_tmpl.data(); break;
         default: break;
     }
     if (host) {
@@ -1011,6 +1223,160 @@ int pd_set_path(pd_ctx *c, int mode, int lanes, int block) {
     return capture_all(c);
 }
 
+int pd_surrogate_setup(pd_ctx *c, int n_modes, const float *basis, const float *lambda, int judge_every, double gate,
+                       double err_tol) {
+    if (int r = check_ctx(c, 2)) return r;
+    if (c->state != 2) return fail(PD_ESTATE, "pd_surrogate_setup must come before pd_bind_arena");
+    if (c->prm.precision != PD_FP32_SPLIT) return fail(PD_EINVAL, "the surrogate runs in the FP32-split path");
+    if (n_modes < 8 || n_modes > 32 || n_modes % 8 || !basis || !lambda || judge_every < 1 || !(gate > 0) ||
+        !(err_tol > 0))
+        return fail(PD_EINVAL,
+                    "n_modes in {8,16,24,32}, basis and lambda non-null, judge_every >= 1, gate and err_tol > 0");
+    const int T = c->n_tmpl, M = n_modes;
+    // padded basis rows per template (2 n_t rounded up to the expansion tile)
+    c->tmpl_rows.assign(T + 1, 0);
+    for (int t = 0; t < T; ++t) {
+        const int rows = 2 * c->tmpl_nodes[t];
+        c->tmpl_rows[t + 1] = c->tmpl_rows[t] + (rows + pd::kSurExpandRows - 1) / pd::kSurExpandRows * pd::kSurExpandRows;
+    }
+    const size_t total = (size_t)c->tmpl_rows[T] * M;
+    c->sur_basis.assign(total, 0.f);
+    c->bnm_hi.assign(total, 0);
+    c->bnm_lo.assign(total, 0);
+    c->bmm_hi.assign(total, 0);
+    c->bmm_lo.assign(total, 0);
+    size_t in = 0;   // input: per template node l, x row then y row of M values
+    for (int t = 0; t < T; ++t) {
+        const size_t base = (size_t)c->tmpl_rows[t] * M;
+        const int rp = c->tmpl_rows[t + 1] - c->tmpl_rows[t];
+        for (int l = 0; l < c->tmpl_nodes[t]; ++l)
+            for (int comp = 0; comp < 2; ++comp)
+                for (int m = 0; m < M; ++m) {
+                    const float v = basis[in++];
+                    const int r = 2 * l + comp;
+                    uint16_t hi, lo;
+                    bf16_split(v, hi, lo);
+                    c->sur_basis[base + (size_t)m * rp + r] = v;
+                    c->bmm_hi[base + (size_t)m * rp + r] = hi;
+                    c->bmm_lo[base + (size_t)m * rp + r] = lo;
+                    c->bnm_hi[base + (size_t)r * M + m] = hi;
+                    c->bnm_lo[base + (size_t)r * M + m] = lo;
+                }
+    }
+    // network rows -> grains, and the tensor-core tiles
+    c->slot_grain.assign(c->G, 0);
+    int rows = 0;
+    std::vector<int> slot0(T + 1, 0);
+    for (int t = 0; t < T; ++t) slot0[t + 1] = slot0[t] + c->tmpl_count[t];
+    for (int g = 0; g < c->G; ++g)
+        if (c->g_tmpl[g] >= 0) {
+            c->slot_grain[slot0[c->g_tmpl[g]] + c->g_slot[g]] = g;
+            ++rows;
+        }
+    c->slot_grain.resize(rows);
+    c->proj_work.clear();
+    c->exp_work.clear();
+    for (int t = 0; t < T; ++t) {
+        const int rp = c->tmpl_rows[t + 1] - c->tmpl_rows[t];
+        for (int s0 = 0; s0 < c->tmpl_count[t]; s0 += pd::kSurTile) {
+            for (int r0 = 0, ch = 0; r0 < rp; r0 += pd::kSurChunk, ++ch) c->proj_work.push_back(make_int4(t, s0, r0, ch));
+            for (int r0 = 0; r0 < rp; r0 += pd::kSurExpandRows) c->exp_work.push_back(make_int4(t, s0, r0, 0));
+        }
+    }
+    c->sur_lambda.assign(lambda, lambda + (size_t)T * M);
+    c->sur_modes = n_modes;
+    c->sur_judge = judge_every;
+    c->sur_gate = gate;
+    c->sur_tol = err_tol;
+    c->sur_cfg = true;
+    return PD_OK;
+}
+
+int pd_surrogate_set_mlp(pd_ctx *c, int tmpl, pd_mlp *mlp) {
+    if (int r = check_ctx(c, 3)) return r;
+    if (!c->sur_cfg) return fail(PD_ESTATE, "pd_surrogate_setup was not called");
+    if (tmpl < 0 || tmpl >= c->n_tmpl) return fail(PD_EINVAL, "template out of range");
+    c->sur_mlp[tmpl] = mlp;
+    if (!mlp) {
+        // grains of a template without a network leave the surrogate
+        std::vector<int32_t> act(c->G);
+        PD_CUDA(cudaMemcpyAsync(act.data(), c->d.sur_active, 4 * act.size(), cudaMemcpyDeviceToHost, c->stream));
+        PD_CUDA(cudaStreamSynchronize(c->stream));
+        for (int g = 0; g < c->G; ++g)
+            if (c->g_tmpl[g] == tmpl) act[g] = 0;
+        PD_CUDA(cudaMemcpyAsync(c->d.sur_active, act.data(), 4 * act.size(), cudaMemcpyHostToDevice, c->stream));
+        PD_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    if (c->kp.sur) return capture_all(c);
+    return PD_OK;
+}
+
+int pd_surrogate_enable(pd_ctx *c, int on) {
+    if (int r = check_ctx(c, 3)) return r;
+    if (!c->sur_cfg) return fail(PD_ESTATE, "pd_surrogate_setup was not called");
+    std::vector<int32_t> act(c->G, 0);
+    for (int g = 0; g < c->G; ++g) act[g] = (on && c->sur_mlp[c->g_tmpl[g]]) ? 1 : 0;
+    PD_CUDA(cudaMemcpyAsync(c->d.sur_active, act.data(), 4 * act.size(), cudaMemcpyHostToDevice, c->stream));
+    PD_CUDA(cudaStreamSynchronize(c->stream));
+    c->kp.sur = on ? 1 : 0;
+    return capture_all(c);
+}
+
+int pd_surrogate_sample(pd_ctx *c, float *q_host, float *f_host) {
+    if (int r = check_ctx(c, 3)) return r;
+    if (!c->sur_cfg || !c->prm.store_parts) return fail(PD_ESTATE, "sampling needs pd_surrogate_setup and store_parts");
+    if (!q_host || !f_host) return fail(PD_EINVAL, "null output");
+    const int sur = c->kp.sur;
+    c->kp.sur = 0;                                       // full bond forces
+    int r = pd_eval_forces(c);
+    c->kp.sur = sur;
+    if (r) return r;
+    cudaStream_t s = c->stream;
+    PD_CUDA(pd::launch_sur_frame(c->d, c->kp, 1, s));
+    PD_CUDA(pd::launch_sur_project_cc(c->d, c->kp, nullptr, c->d.sur_qs, s));
+    PD_CUDA(pd::launch_sur_project_cc(c->d, c->kp, c->d.parts, c->d.sur_fs, s));
+    const size_t bytes = 4 * (size_t)c->G * c->sur_modes;
+    PD_CUDA(cudaMemcpyAsync(q_host, c->d.sur_qs, bytes, cudaMemcpyDeviceToHost, s));
+    PD_CUDA(cudaMemcpyAsync(f_host, c->d.sur_fs, bytes, cudaMemcpyDeviceToHost, s));
+    PD_CUDA(cudaStreamSynchronize(s));
+    return PD_OK;
+}
+
+int pd_surrogate_stats(pd_ctx *c, int32_t *active, float *err, float *merr, float *maxs) {
+    if (int r = check_ctx(c, 3)) return r;
+    if (!c->sur_cfg) return fail(PD_ESTATE, "pd_surrogate_setup was not called");
+    cudaStream_t s = c->stream;
+    if (active) PD_CUDA(cudaMemcpyAsync(active, c->d.sur_active, 4 * (size_t)c->G, cudaMemcpyDeviceToHost, s));
+    if (err) PD_CUDA(cudaMemcpyAsync(err, c->d.sur_err, 4 * (size_t)c->G, cudaMemcpyDeviceToHost, s));
+    if (merr) PD_CUDA(cudaMemcpyAsync(merr, c->d.sur_merr, 4 * (size_t)c->G, cudaMemcpyDeviceToHost, s));
+    if (maxs) PD_CUDA(cudaMemcpyAsync(maxs, c->d.sur_maxs, 4 * (size_t)c->G, cudaMemcpyDeviceToHost, s));
+    PD_CUDA(cudaStreamSynchronize(s));
+    return PD_OK;
+}
+
+int pd_surrogate_inspect(pd_ctx *c, float *q_host, float *y_host) {
+    if (int r = check_ctx(c, 3)) return r;
+    if (!c->sur_cfg || !c->kp.sur) return fail(PD_ESTATE, "the surrogate is not enabled");
+    if (!q_host || !y_host) return fail(PD_EINVAL, "null output");
+    if (int r = pd_eval_forces(c)) return r;
+    const size_t M = (size_t)c->sur_modes, rows = c->slot_grain.size();
+    std::vector<float> x(rows * M), y(rows * M);
+    cudaStream_t s = c->stream;
+    if (rows) {
+        PD_CUDA(cudaMemcpyAsync(x.data(), c->d.sur_x, 4 * x.size(), cudaMemcpyDeviceToHost, s));
+        PD_CUDA(cudaMemcpyAsync(y.data(), c->d.sur_y, 4 * y.size(), cudaMemcpyDeviceToHost, s));
+    }
+    PD_CUDA(cudaStreamSynchronize(s));
+    std::fill(q_host, q_host + (size_t)c->G * M, 0.f);
+    std::fill(y_host, y_host + (size_t)c->G * M, 0.f);
+    for (size_t row = 0; row < rows; ++row) {
+        const int g = c->slot_grain[row];
+        std::copy(x.begin() + row * M, x.begin() + (row + 1) * M, q_host + (size_t)g * M);
+        std::copy(y.begin() + row * M, y.begin() + (row + 1) * M, y_host + (size_t)g * M);
+    }
+    return PD_OK;
+}
+
 int pd_set_timing(pd_ctx *c, int enable) {
     if (int r = check_ctx(c, 3)) return r;
     c->timing = enable ? 1 : 0;
@@ -1048,6 +1414,7 @@ int pd_info(pd_ctx *c, double *out) {
     out[11] = (double)(c->state >= 3 ? c->kp.lanes : (c->prm.lanes ? c->prm.lanes : 8));
     out[12] = (double)c->block;
     out[13] = (double)c->n_agg;
+    out[14] = (double)c->n_tmpl;
     return PD_OK;
 }
 

@@ -25,6 +25,7 @@ struct AggParams {
     double Rc, Kn;
     double w0[4], wv[4];   // walls x_lo, x_hi, y_lo, y_hi at t = 0 and their normal velocities
     double ox, oy, cell;   // hash-grid origin and cell side (>= R_c)
+    double inv_cell;       // 1 / cell
     double sx, sy;         // FP32-split shift: coordinates of the box map to [L, 2L)
     float rc2_hi, rc2_lo;  // R_c^2 as a float-float pair
 };
@@ -45,6 +46,7 @@ struct DevPtrs {
     AggParams *agg;
     // contact hash grid (T buckets)
     int *key, *count, *start, *cursor, *sorted, *blocksums;
+    int2 *cell;         // hash-grid cell (x, y) of every node, written by the binning phase
     // globals
     long long *step;
     double *t_now;      // time of the force evaluation that follows the predict phase
@@ -59,6 +61,35 @@ struct DevPtrs {
     // autotuner backup of the state
     double2 *bu, *bv, *ba;
     uint32_t *bbits;
+    // learned modal surrogate (FP32-split path)
+    int *g_start;       // first node of every grain (G + 1)
+    int *g_tmpl;        // template of every grain (-1: none)
+    int *g_slot;        // row of the grain in its template's network batch
+    int *tmpl_node;     // first basis row of every template (n_tmpl + 1)
+    int *tmpl_slot;     // first network row of every template (n_tmpl + 1)
+    float *basis;       // per template: mode-major [n_modes][2 n_t] (row r = 2 l + c of template node l), lattice frame
+    uint16_t *bnm_hi, *bnm_lo;  // BF16 split of the basis, node-major [2 n_t][n_modes] (tensor-core expansion)
+    uint16_t *bmm_hi, *bmm_lo;  // BF16 split of the basis, mode-major [n_modes][2 n_t] (tensor-core projection)
+    int *slot_grain;    // grain of every network row (inverse of tmpl_slot + g_slot)
+    int *tmpl_rows;     // first padded basis row of every template (n_tmpl + 1; 2 n_t rounded up to kSurExpandRows)
+    int4 *proj_work;    // projection tiles: (template, first row, first basis row, chunk)
+    int4 *exp_work;     // expansion tiles: (template, first row, first basis row, 0)
+    float2 *sur_w;      // co-rotated local deformation / h of every node of an active grain, lattice frame
+    float2 *sur_f;      // surrogate bond force / (E h) of every node of an active grain, lattice frame
+    float *sur_xpart;   // projection partial sums [chunk][network row][mode]
+    double *g_theta;    // grain orientation at meshing
+    double2 *g_xbar;    // reference centroid of every grain
+    int *sur_active;    // 1 while the grain is advanced by the surrogate
+    float2 *sur_rot;    // cos, sin of (theta + phi): lattice frame -> world
+    double *sur_phi;    // co-rotation angle phi of the current step
+    float *sur_x;       // network input rows (modal coefficients / h)
+    float *sur_y;       // network output rows (modal bond force / (E h))
+    float2 *sur_fb;     // full bond force of surrogate nodes on judge steps
+    float *sur_err;     // judged relative error of the surrogate nodal bond force
+    float *sur_merr;    // judged relative error of the surrogate modal bond force
+    float *sur_maxs;    // judged max |s| / s0 over the grain's bonds
+    float *sur_qs, *sur_fs;  // per-grain samples (modal coefficients, modal bond force)
+    float *sur_lambda;  // per template and mode: linearised modal stiffness (dimensionless)
 };
 
 // By-value kernel parameters (baked into captured graphs).
@@ -70,7 +101,41 @@ struct KParams {
     int micro, store;
     int lanes;          // threads per node in the force kernels (1, 4 or 8)
     int fp32;           // precision of the force phase
+    // surrogate
+    int sur;            // surrogate on
+    int n_modes;        // modes of the basis (32)
+    int judge_every;    // full bond kernel every judge_every steps
+    float E;            // Young's modulus (force scale of the network output)
+    float gate;         // fall back when max |s| > gate * s0
+    float err_tol;      // fall back when the judged relative error exceeds this
+    int n_proj_work, n_exp_work;  // tensor-core tiles of the projection / expansion
+    int n_rows;                   // network rows (templated grains)
 };
+
+
+// Surrogate phases (pd_surrogate.cu): co-rotated modal coefficients of the
+// active grains before the force phase, and the judge after it.
+// Tile sizes of the tensor-core projection (rows of 2 n_t per chunk) and expansion.
+constexpr int kSurChunk = 128;
+constexpr int kSurExpandRows = 256;
+constexpr int kSurTile = 128;      // network rows (grains) per tile
+cudaError_t sur_init_attributes();   // shared-memory limits of the tensor-core kernels (not capturable)
+cudaError_t launch_sur_frame(const DevPtrs &d, const KParams &k, int all_templated, cudaStream_t s);
+// CUDA-core projection of a per-node vector field onto the basis, for every
+// templated grain: world-frame bond forces (rotated into the lattice frame and
+// scaled by 1/(E h)) when F is given, else the local deformation sur_w.
+cudaError_t launch_sur_project_cc(const DevPtrs &d, const KParams &k, const double2 *F, float *out, cudaStream_t s);
+cudaError_t launch_sur_project_tc(const DevPtrs &d, const KParams &k, cudaStream_t s);
+cudaError_t launch_sur_reduce(const DevPtrs &d, const KParams &k, cudaStream_t s);
+cudaError_t launch_sur_expand_tc(const DevPtrs &d, const KParams &k, cudaStream_t s);
+cudaError_t launch_sur_judge(const DevPtrs &d, const KParams &k, cudaStream_t s);
+cudaError_t launch_sur_combine(const DevPtrs &d, const KParams &k, cudaStream_t s);
+
+// Forward pass of a surrogate network on a given stream (captured into the step graph).
+}  // namespace pd
+struct pd_mlp;
+namespace pd {
+int mlp_forward_stream(pd_mlp *m, const float *x, float *y, int batch, cudaStream_t s);
 
 // Record an error for pd_last_error() and return `code`.
 int set_error(int code, const char *msg);

@@ -64,19 +64,42 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(Net n, const float *__restrict_
     const int row = blockIdx.x * TILE + tid;
     if (warp == 0) tc::tmem_alloc(&tmem_base, 128);
     if (tid == 0) tc::mbar_init(&mbar, 1);
-    // operands -> canonical K-major shared layout
-    for (int k = 0; k < IN; ++k) {
-        const float x = (row < B) ? X[(size_t)row * IN + k] : 0.f;
-        const __nv_bfloat16 xb = __float2bfloat16(x);
-        *reinterpret_cast<__nv_bfloat16 *>(sA + tc::kmajor_off(tid, k, TILE)) = xb;
-        if (train) n.Xt[(size_t)k * Bp + row] = xb;
+    // operands -> canonical K-major shared layout, 8 values (one 16-byte core
+    // matrix row) per store
+    const bool x16 = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+    for (int k8 = 0; k8 < IN; k8 += 8) {
+        float x[8];
+        if (row < B && x16) {
+            const float4 a = *reinterpret_cast<const float4 *>(X + (size_t)row * IN + k8);
+            const float4 b = *reinterpret_cast<const float4 *>(X + (size_t)row * IN + k8 + 4);
+            x[0] = a.x, x[1] = a.y, x[2] = a.z, x[3] = a.w, x[4] = b.x, x[5] = b.y, x[6] = b.z, x[7] = b.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) x[q] = (row < B) ? X[(size_t)row * IN + k8 + q] : 0.f;
+        }
+        __align__(16) __nv_bfloat16 xb[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            xb[q] = __float2bfloat16(x[q]);
+            if (train) n.Xt[(size_t)(k8 + q) * Bp + row] = xb[q];
+        }
+        *reinterpret_cast<uint4 *>(sA + tc::kmajor_off(tid, k8, TILE)) = *reinterpret_cast<const uint4 *>(xb);
     }
-    for (int e = tid; e < HID * IN; e += 128)
-        *reinterpret_cast<__nv_bfloat16 *>(sW1 + tc::kmajor_off(e / IN, e % IN, HID)) = n.W1[e];
-    for (int e = tid; e < HID * HID; e += 128)
-        *reinterpret_cast<__nv_bfloat16 *>(sW2 + tc::kmajor_off(e / HID, e % HID, HID)) = n.W2[e];
-    for (int e = tid; e < OUT * HID; e += 128)
-        *reinterpret_cast<__nv_bfloat16 *>(sW3 + tc::kmajor_off(e / HID, e % HID, OUT)) = n.W3[e];
+    for (int e = tid; e < HID * IN / 8; e += 128) {
+        const int r = e / (IN / 8), k8 = (e % (IN / 8)) * 8;
+        *reinterpret_cast<uint4 *>(sW1 + tc::kmajor_off(r, k8, HID)) =
+            *reinterpret_cast<const uint4 *>(n.W1 + (size_t)r * IN + k8);
+    }
+    for (int e = tid; e < HID * HID / 8; e += 128) {
+        const int r = e / (HID / 8), k8 = (e % (HID / 8)) * 8;
+        *reinterpret_cast<uint4 *>(sW2 + tc::kmajor_off(r, k8, HID)) =
+            *reinterpret_cast<const uint4 *>(n.W2 + (size_t)r * HID + k8);
+    }
+    for (int e = tid; e < OUT * HID / 8; e += 128) {
+        const int r = e / (HID / 8), k8 = (e % (HID / 8)) * 8;
+        *reinterpret_cast<uint4 *>(sW3 + tc::kmajor_off(r, k8, OUT)) =
+            *reinterpret_cast<const uint4 *>(n.W3 + (size_t)r * HID + k8);
+    }
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -109,6 +132,7 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(Net n, const float *__restrict_
         for (int c0 = 0; c0 < N; c0 += 16) {
             float acc[16];
             tc::tmem_ld16(tmem + lane_base + (uint32_t)c0, acc);
+            __align__(16) __nv_bfloat16 hb[16];
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int c = c0 + q;
@@ -118,10 +142,14 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(Net n, const float *__restrict_
                     if (train) n.Y[(size_t)row * OUT + c] = z;
                 } else {
                     if (train) (layer == 0 ? n.Z1 : n.Z2)[(size_t)row * HID + c] = z;
-                    const __nv_bfloat16 hb = __float2bfloat16(gelu(z));
-                    *reinterpret_cast<__nv_bfloat16 *>(sH + tc::kmajor_off(tid, c, TILE)) = hb;
-                    if (train) (layer == 0 ? n.H1t : n.H2t)[(size_t)c * Bp + row] = hb;
+                    hb[q] = __float2bfloat16(gelu(z));
+                    if (train) (layer == 0 ? n.H1t : n.H2t)[(size_t)c * Bp + row] = hb[q];
                 }
+            }
+            if (layer < 2) {
+                *reinterpret_cast<uint4 *>(sH + tc::kmajor_off(tid, c0, TILE)) = *reinterpret_cast<const uint4 *>(hb);
+                *reinterpret_cast<uint4 *>(sH + tc::kmajor_off(tid, c0 + 8, TILE)) =
+                    *reinterpret_cast<const uint4 *>(hb + 8);
             }
         }
         tc::fence_before_sync();
@@ -411,6 +439,16 @@ int backward(pd_mlp *m, const float *x, const float *t, int batch) {
 }
 
 }  // namespace
+
+int pd::mlp_forward_stream(pd_mlp *m, const float *x, float *y, int batch, cudaStream_t s) {
+    if (!m || !m->bound) return pd::set_error(PD_ESTATE, "mlp not bound");
+    if (batch < 0 || batch > m->max_batch) return pd::set_error(PD_EINVAL, "batch exceeds max_batch");
+    if (batch == 0) return PD_OK;
+    const int tiles = (batch + TILE - 1) / TILE;
+    pd::mlp::k_mlp_fwd<<<tiles, 128, kFwdSmem, s>>>(m->n, x, y, batch, m->Bp, 0);
+    MLP_CUDA(cudaGetLastError());
+    return PD_OK;
+}
 
 extern "C" {
 

@@ -1,0 +1,523 @@
+// pd_surrogate.cu -- kernels of the learned per-grain modal surrogate.
+//
+// A grain whose bond network is a template (same shape, same lattice) is
+// described in its co-rotated lattice frame: centroid c and rotation phi fit
+// the current positions to the reference ones (2D Kabsch: phi = atan2(sum
+// X' x p', sum X' . p')), the local deformation is
+// w_i = R(-theta) (R(-phi) (p_i - c) - (X_i - Xbar)), and its modal
+// coefficients q = Phi^T w / h on the template's basis Phi (lowest modes of the
+// linearised bond operator K, K Phi = Phi Lambda).  The modal bond force
+// f = Phi^T F / (E h) is the linear part -Lambda q plus a network's nonlinear
+// correction: f = -Lambda q + net(q); the force kernel then puts
+// R(theta + phi) Phi f E h in place of the bond loop.  Every judge_every steps
+// the full bond kernel runs instead and the judge compares it with the
+// surrogate force and checks the largest stretch, switching a grain back to
+// the full bond force for good when it nears damage or the surrogate error
+// grows.
+//
+// Per template the two basis products are dense GEMMs over all of its grains
+// and run on the tensor cores (tcgen05, BF16 operands, FP32 accumulation in
+// tensor memory): the projection Q = W Phi (rows: grains, K: the 2 n_t node
+// coordinates, split in chunks of kSurChunk whose partial sums are added in a
+// fixed order) and the expansion F = Y Phi^T (rows: grains, N: node
+// coordinates in tiles of kSurExpandRows, K: the modes).  FP32 accuracy comes
+// from splitting every operand x = hi + lo into two BF16 numbers and adding
+// the three products hi*hi + hi*lo + lo*hi (the split-precision scheme of
+// Henry, Tang & Heinecke, "Leveraging the bfloat16 artificial intelligence
+// datatype for higher-precision computations", ARITH 2019): relative error
+// about 2^-16 per product, far inside the surrogate's 1e-3 tolerance.
+#include <cuda_bf16.h>
+
+#include "pd_device.cuh"
+#include "pd_tc.cuh"
+
+namespace pd {
+
+constexpr int kSurThreads = 128;
+constexpr int kMaxModes = 32;
+constexpr long long kSurSpins = 1LL << 24;   // bounded mbarrier waits
+
+__device__ __forceinline__ double block_sum_d(double v, double *sm) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < kSurThreads / 32; ++w) t += sm[w];
+    return t;
+}
+
+__device__ __forceinline__ float block_max_f(float v, float *sm) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    float t = 0.f;
+    for (int w = 0; w < kSurThreads / 32; ++w) t = fmaxf(t, sm[w]);
+    return t;
+}
+
+// Sum over the block of 32 per-thread mode accumulators; thread m < M gets
+// the total of mode m.
+__device__ __forceinline__ float block_sum_modes(const float (&acc)[kMaxModes], float (*sm)[kSurThreads], int M) {
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < kMaxModes; ++m) sm[m][threadIdx.x] = acc[m];
+    __syncthreads();
+    float v = 0.f;
+    if ((int)threadIdx.x < M)
+        for (int q = 0; q < kSurThreads; ++q) v += sm[threadIdx.x][q];
+    return v;
+}
+
+// Padded basis rows of template t (a multiple of kSurExpandRows).
+__device__ __forceinline__ int tmpl_rows_pad(const DevPtrs &d, int t) { return d.tmpl_rows[t + 1] - d.tmpl_rows[t]; }
+
+// ---------------------------------------------------------------------------
+// co-rotated frame and local deformation
+
+// Co-rotated frame of grain blockIdx.x and its local deformation w / h per node
+// (into sur_w).  Grains without a template, or not active (unless
+// all_templated), are skipped.
+__global__ void __launch_bounds__(kSurThreads) k_sur_frame(DevPtrs d, KParams k, int all_templated) {
+    __shared__ double smd[kSurThreads / 32];
+    const int g = blockIdx.x;
+    const int t = d.g_tmpl[g];
+    if (t < 0 || (!all_templated && !d.sur_active[g])) return;
+    const int s0 = d.g_start[g], s1 = d.g_start[g + 1], n = s1 - s0;
+    const double2 xb = d.g_xbar[g];
+    // one pass: centroid of the current positions and the best-fit rotation
+    // sums sum X' . p, sum X' x p (sum X' = 0, so p need not be centred)
+    double sx = 0.0, sy = 0.0, sdot = 0.0, scross = 0.0;
+    for (int i = s0 + threadIdx.x; i < s1; i += kSurThreads) {
+        const double2 p = d.p[i], X = d.X[i];
+        const double rx = X.x - xb.x, ry = X.y - xb.y;
+        sx += p.x;
+        sy += p.y;
+        sdot += rx * p.x + ry * p.y;
+        scross += rx * p.y - ry * p.x;
+    }
+    const double cx = block_sum_d(sx, smd) / n;
+    const double cy = block_sum_d(sy, smd) / n;
+    const double Sd = block_sum_d(sdot, smd);
+    const double Sc = block_sum_d(scross, smd);
+    const double phi = atan2(Sc, Sd);
+    const double th = d.g_theta[g];
+    double sp, cp, st, ct, sr, cr;
+    sincos(phi, &sp, &cp);
+    sincos(th, &st, &ct);
+    sincos(th + phi, &sr, &cr);
+    if (threadIdx.x == 0) {
+        d.sur_phi[g] = phi;
+        d.sur_rot[g] = make_float2((float)cr, (float)sr);
+    }
+    const double hinv = 1.0 / (double)__ldg(&d.gq[__ldg(&d.grain[s0])]).x;
+    for (int i = s0 + threadIdx.x; i < s1; i += kSurThreads) {
+        const double2 p = d.p[i], X = d.X[i];
+        const double px = p.x - cx, py = p.y - cy, rx = X.x - xb.x, ry = X.y - xb.y;
+        // R(-phi) p' - X'  (world orientation), then R(-theta) to the lattice frame
+        const double ux = (cp * px + sp * py) - rx, uy = (-sp * px + cp * py) - ry;
+        d.sur_w[i] = make_float2((float)((ct * ux + st * uy) * hinv), (float)((-st * ux + ct * uy) * hinv));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-core projection (sampling and checks): out[g] = Phi^T v for every
+// templated grain, v = sur_w, or v = R(-theta - phi) F / (E h) when F is given.
+
+__global__ void __launch_bounds__(kSurThreads) k_sur_project_cc(DevPtrs d, KParams k, const double2 *F,
+                                                                 float *out) {
+    __shared__ float smq[kMaxModes][kSurThreads];
+    const int g = blockIdx.x;
+    const int t = d.g_tmpl[g];
+    if (t < 0) return;
+    const int s0 = d.g_start[g], s1 = d.g_start[g + 1];
+    const int M = k.n_modes;
+    const int rp = tmpl_rows_pad(d, t);
+    const float2 rot = d.sur_rot[g];
+    const float scale = 1.0f / (k.E * __ldg(&d.gq[__ldg(&d.grain[s0])]).x);
+    const float *B = d.basis + (size_t)d.tmpl_rows[t] * M;
+    float acc[kMaxModes];
+#pragma unroll
+    for (int m = 0; m < kMaxModes; ++m) acc[m] = 0.f;
+    for (int i = s0 + threadIdx.x; i < s1; i += kSurThreads) {
+        float lx, ly;
+        if (F) {
+            const double2 f = F[i];
+            const float fx = (float)f.x * scale, fy = (float)f.y * scale;
+            lx = rot.x * fx + rot.y * fy;
+            ly = -rot.y * fx + rot.x * fy;
+        } else {
+            const float2 w = d.sur_w[i];
+            lx = w.x;
+            ly = w.y;
+        }
+        const int r = 2 * (i - s0);
+#pragma unroll
+        for (int m = 0; m < kMaxModes; ++m)
+            if (m < M) {
+                const float2 b = *reinterpret_cast<const float2 *>(B + (size_t)m * rp + r);
+                acc[m] += b.x * lx + b.y * ly;
+            }
+    }
+    const float v = block_sum_modes(acc, smq, M);
+    if ((int)threadIdx.x < M) out[(size_t)g * M + threadIdx.x] = v;
+}
+
+// ---------------------------------------------------------------------------
+// tensor-core basis products
+
+__device__ __forceinline__ uint32_t split_pack(float a, float b, uint32_t &lo) {
+    const __nv_bfloat16 ah = __float2bfloat16_rn(a), bh = __float2bfloat16_rn(b);
+    const __nv_bfloat16 al = __float2bfloat16_rn(a - __bfloat162float(ah));
+    const __nv_bfloat16 bl = __float2bfloat16_rn(b - __bfloat162float(bh));
+    lo = (uint32_t)__bfloat16_as_ushort(al) | ((uint32_t)__bfloat16_as_ushort(bl) << 16);
+    return (uint32_t)__bfloat16_as_ushort(ah) | ((uint32_t)__bfloat16_as_ushort(bh) << 16);
+}
+
+// hi*hi + hi*lo + lo*hi over K/16 steps into the TMEM accumulator; one thread.
+__device__ __forceinline__ void split_mma(uint32_t tmem, const uint8_t *ahi, const uint8_t *alo, const uint8_t *bhi,
+                                          const uint8_t *blo, int arows, int brows, int K, uint32_t idesc) {
+    const uint32_t lbo_a = tc::kmajor_lbo(arows), lbo_b = tc::kmajor_lbo(brows);
+    uint32_t acc = 0;
+    for (int ks = 0; ks < K / 16; ++ks) {
+        const uint32_t oa = (uint32_t)ks * 2 * lbo_a, ob = (uint32_t)ks * 2 * lbo_b;
+        const uint64_t a_h = tc::smem_desc(tc::smem_addr(ahi) + oa, lbo_a, tc::kSbo);
+        const uint64_t a_l = tc::smem_desc(tc::smem_addr(alo) + oa, lbo_a, tc::kSbo);
+        const uint64_t b_h = tc::smem_desc(tc::smem_addr(bhi) + ob, lbo_b, tc::kSbo);
+        const uint64_t b_l = tc::smem_desc(tc::smem_addr(blo) + ob, lbo_b, tc::kSbo);
+        tc::mma_bf16(tmem, a_h, b_h, idesc, acc);
+        acc = 1;
+        tc::mma_bf16(tmem, a_h, b_l, idesc, 1);
+        tc::mma_bf16(tmem, a_l, b_h, idesc, 1);
+    }
+}
+
+constexpr int kProjSmem = 96 * 1024;     // A hi/lo 128 x 128, B hi/lo 32 x 128 (80 KB used)
+constexpr int kExpSmem = 100 * 1024;     // A hi/lo 128 x 32, B hi/lo 256 x 32 (48 KB used); <= 2 CTAs per SM
+
+// Projection tile: network rows [s0, s0 + 128) of template t times basis rows
+// [r0, r0 + kSurChunk): partial modal coefficients into sur_xpart[chunk].
+__global__ void __launch_bounds__(128) k_sur_project_tc(DevPtrs d, KParams k) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    constexpr int KC = kSurChunk, MR = kSurTile, NM = kMaxModes;
+    uint8_t *sAh = sm, *sAl = sm + MR * KC * 2, *sBh = sm + 2 * MR * KC * 2, *sBl = sBh + NM * KC * 2;
+    const int4 wk = d.proj_work[blockIdx.x];
+    const int t = wk.x, s0 = wk.y, r0 = wk.z, chunk = wk.w;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int M = k.n_modes;
+    const int slot0 = d.tmpl_slot[t], Gt = d.tmpl_slot[t + 1] - slot0;
+    const int rows2 = 2 * (d.tmpl_node[t + 1] - d.tmpl_node[t]);
+    const int rp = tmpl_rows_pad(d, t);
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 32);
+    if (tid == 0) tc::mbar_init(&mbar, 1);
+    // A: local deformation rows of the tile's grains (zero outside)
+    {
+        const int s = s0 + tid;
+        int g = -1;
+        if (s < Gt) {
+            g = d.slot_grain[slot0 + s];
+            if (!d.sur_active[g]) g = -1;
+        }
+        const float *w = g >= 0 ? reinterpret_cast<const float *>(d.sur_w) + 2 * (size_t)d.g_start[g] : nullptr;
+        for (int kk = 0; kk < KC; kk += 2) {
+            const int r = r0 + kk;
+            float2 v = make_float2(0.f, 0.f);
+            if (w && r < rows2) v = *reinterpret_cast<const float2 *>(w + r);
+            uint32_t lo;
+            const uint32_t hi = split_pack(v.x, v.y, lo);
+            *reinterpret_cast<uint32_t *>(sAh + tc::kmajor_off(tid, kk, MR)) = hi;
+            *reinterpret_cast<uint32_t *>(sAl + tc::kmajor_off(tid, kk, MR)) = lo;
+        }
+    }
+    // B: the basis, mode-major, padded rows (16-byte pieces of 8 values)
+    {
+        const uint16_t *bh = d.bmm_hi + (size_t)d.tmpl_rows[t] * M;
+        const uint16_t *bl = d.bmm_lo + (size_t)d.tmpl_rows[t] * M;
+        for (int e = tid; e < NM * (KC / 8); e += 128) {
+            const int m = e / (KC / 8), k8 = (e % (KC / 8)) * 8;
+            uint4 vh = make_uint4(0, 0, 0, 0), vl = make_uint4(0, 0, 0, 0);
+            if (m < M) {
+                vh = *reinterpret_cast<const uint4 *>(bh + (size_t)m * rp + r0 + k8);
+                vl = *reinterpret_cast<const uint4 *>(bl + (size_t)m * rp + r0 + k8);
+            }
+            *reinterpret_cast<uint4 *>(sBh + tc::kmajor_off(m, k8, NM)) = vh;
+            *reinterpret_cast<uint4 *>(sBl + tc::kmajor_off(m, k8, NM)) = vl;
+        }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    if (tid == 0) {
+        split_mma(tmem, sAh, sAl, sBh, sBl, MR, NM, KC, tc::idesc_bf16(MR, NM));
+        tc::mma_commit(&mbar);
+    }
+    const bool ok = __syncthreads_and(tc::mbar_wait(&mbar, 0, kSurSpins)) != 0;
+    if (ok) {
+        tc::fence_after_sync();
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        const int s = s0 + tid;
+        float *dst = d.sur_xpart + ((size_t)chunk * k.G + slot0 + s) * M;
+        for (int c0 = 0; c0 < NM; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+            if (s < Gt)
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (c0 + q < M) dst[c0 + q] = v[q];
+        }
+    } else if (tid == 0) {
+        atomicAdd(&d.status[PD_STATUS_TIMEOUT], 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem_base, 32);
+}
+
+// Network input rows: sum of the projection partials in chunk order.
+__global__ void k_sur_reduce(DevPtrs d, KParams k) {
+    const int row = blockIdx.x;                  // network row
+    const int m = threadIdx.x;
+    if (m >= k.n_modes) return;
+    const int g = d.slot_grain[row];
+    const int t = d.g_tmpl[g];
+    const int nch = tmpl_rows_pad(d, t) / kSurChunk;
+    float v = 0.f;
+    for (int c = 0; c < nch; ++c) v += d.sur_xpart[((size_t)c * k.G + row) * k.n_modes + m];
+    d.sur_x[(size_t)row * k.n_modes + m] = v;
+}
+
+// Expansion tile: network rows [s0, s0 + 128) of template t times basis rows
+// [r0, r0 + kSurExpandRows): surrogate bond force / (E h) of the tile's nodes
+// in the lattice frame, into sur_f (active grains only).
+__global__ void __launch_bounds__(128) k_sur_expand_tc(DevPtrs d, KParams k) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    constexpr int NR = kSurExpandRows, MR = kSurTile, KM = kMaxModes;
+    uint8_t *sAh = sm, *sAl = sm + MR * KM * 2, *sBh = sm + 2 * MR * KM * 2, *sBl = sBh + NR * KM * 2;
+    const int4 wk = d.exp_work[blockIdx.x];
+    const int t = wk.x, s0 = wk.y, r0 = wk.z;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int M = k.n_modes;
+    const int slot0 = d.tmpl_slot[t], Gt = d.tmpl_slot[t + 1] - slot0;
+    const int rows2 = 2 * (d.tmpl_node[t + 1] - d.tmpl_node[t]);
+    if (warp == 0) tc::tmem_alloc(&tmem_base, NR);
+    if (tid == 0) tc::mbar_init(&mbar, 1);
+    const int s = s0 + tid;
+    int g = -1;
+    if (s < Gt) {
+        g = d.slot_grain[slot0 + s];
+        if (!d.sur_active[g]) g = -1;
+    }
+    // A: network outputs (modal bond forces) of the tile's grains
+    {
+        const float *y = g >= 0 ? d.sur_y + (size_t)(slot0 + s) * M : nullptr;
+        for (int kk = 0; kk < KM; kk += 2) {
+            float2 v = make_float2(0.f, 0.f);
+            if (y && kk < M) v = make_float2(y[kk], kk + 1 < M ? y[kk + 1] : 0.f);
+            uint32_t lo;
+            const uint32_t hi = split_pack(v.x, v.y, lo);
+            *reinterpret_cast<uint32_t *>(sAh + tc::kmajor_off(tid, kk, MR)) = hi;
+            *reinterpret_cast<uint32_t *>(sAl + tc::kmajor_off(tid, kk, MR)) = lo;
+        }
+    }
+    // B: basis rows, node-major (each row: the modes of one node coordinate)
+    {
+        const uint16_t *bh = d.bnm_hi + ((size_t)d.tmpl_rows[t] + r0) * M;
+        const uint16_t *bl = d.bnm_lo + ((size_t)d.tmpl_rows[t] + r0) * M;
+        for (int e = tid; e < NR * (KM / 8); e += 128) {
+            const int r = e / (KM / 8), k8 = (e % (KM / 8)) * 8;
+            uint4 vh = make_uint4(0, 0, 0, 0), vl = make_uint4(0, 0, 0, 0);
+            if (k8 < M) {
+                vh = *reinterpret_cast<const uint4 *>(bh + (size_t)r * M + k8);
+                vl = *reinterpret_cast<const uint4 *>(bl + (size_t)r * M + k8);
+            }
+            *reinterpret_cast<uint4 *>(sBh + tc::kmajor_off(r, k8, NR)) = vh;
+            *reinterpret_cast<uint4 *>(sBl + tc::kmajor_off(r, k8, NR)) = vl;
+        }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    if (tid == 0) {
+        split_mma(tmem, sAh, sAl, sBh, sBl, MR, NR, KM, tc::idesc_bf16(MR, NR));
+        tc::mma_commit(&mbar);
+    }
+    const bool ok = __syncthreads_and(tc::mbar_wait(&mbar, 0, kSurSpins)) != 0;
+    if (ok) {
+        tc::fence_after_sync();
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        float *dst = g >= 0 ? reinterpret_cast<float *>(d.sur_f) + 2 * (size_t)d.g_start[g] : nullptr;
+        for (int c0 = 0; c0 < NR; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+            if (dst)
+#pragma unroll
+                for (int q = 0; q < 16; q += 2) {
+                    const int r = r0 + c0 + q;
+                    if (r < rows2) *reinterpret_cast<float2 *>(dst + r) = make_float2(v[q], v[q + 1]);
+                }
+        }
+    } else if (tid == 0) {
+        atomicAdd(&d.status[PD_STATUS_TIMEOUT], 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem_base, NR);
+}
+
+// ---------------------------------------------------------------------------
+// judge
+
+// Judge (every judge_every steps): relative error of the surrogate nodal bond
+// force against the full one (floored at the grain's weight), relative error
+// of the modal bond force (what the network predicts), and the largest
+// |s| / s0 over the grain's intact bonds; a grain that exceeds the stretch
+// gate or the nodal error tolerance leaves the surrogate for good.
+__global__ void __launch_bounds__(kSurThreads) k_sur_judge(DevPtrs d, KParams k) {
+    __shared__ double smd[kSurThreads / 32];
+    __shared__ float smf[kSurThreads / 32];
+    __shared__ float smq[kMaxModes][kSurThreads];
+    const int g = blockIdx.x;
+    if ((*d.step) % k.judge_every != 0) return;
+    if (d.g_tmpl[g] < 0 || !d.sur_active[g]) return;
+    const int t = d.g_tmpl[g];
+    const int s0 = d.g_start[g], s1 = d.g_start[g + 1], n = s1 - s0;
+    const int M = k.n_modes;
+    const int rp = tmpl_rows_pad(d, t);
+    const int gi = d.grain[s0];
+    const float4 gq = d.gq[gi];
+    const float Eh = k.E * gq.x;
+    const float2 rot = d.sur_rot[g];
+    const float *B = d.basis + (size_t)d.tmpl_rows[t] * M;
+    const float *y = d.sur_y + (size_t)(d.tmpl_slot[t] + d.g_slot[g]) * M;
+    const float s0g = (float)d.g_s0[gi];
+    double e2 = 0.0, r2 = 0.0;
+    float maxs = 0.f;
+    float acc[kMaxModes];
+#pragma unroll
+    for (int m = 0; m < kMaxModes; ++m) acc[m] = 0.f;
+    for (int i = s0 + threadIdx.x; i < s1; i += kSurThreads) {
+        const float2 fl = d.sur_f[i];
+        const float sx = (rot.x * fl.x - rot.y * fl.y) * Eh, sy = (rot.y * fl.x + rot.x * fl.y) * Eh;
+        const float2 full = d.sur_fb[i];
+        e2 += (double)(sx - full.x) * (sx - full.x) + (double)(sy - full.y) * (sy - full.y);
+        r2 += (double)full.x * full.x + (double)full.y * full.y;
+        // modal projection of the full bond force
+        const float fx = full.x / Eh, fy = full.y / Eh;
+        const float lx = rot.x * fx + rot.y * fy, ly = -rot.y * fx + rot.x * fy;
+        const int r = 2 * (i - s0);
+#pragma unroll
+        for (int m = 0; m < kMaxModes; ++m)
+            if (m < M) {
+                const float2 b = *reinterpret_cast<const float2 *>(B + (size_t)m * rp + r);
+                acc[m] += b.x * lx + b.y * ly;
+            }
+        // largest stretch of the node's intact bonds (float-float, as the force kernel)
+        const float2 phi = d.ph[i], pli = d.pl[i];
+        const int2 li = d.lat[i];
+        const int r0 = d.row_ptr[i], r1 = d.row_ptr[i + 1];
+        for (int b = r0; b < r1; ++b) {
+            const int kk = b - r0;
+            if ((d.bits[(size_t)i * k.wpn + (kk >> 5)] >> (kk & 31)) & 1u) continue;
+            const int j = d.col[b];
+            const float2 phj = d.ph[j], plj = d.pl[j];
+            const int2 lj = d.lat[j];
+            float L2h, L2l;
+            len2_ff(__fsub_rn(phj.x, phi.x), plj.x - pli.x, __fsub_rn(phj.y, phi.y), plj.y - pli.y, L2h, L2l);
+            const int di = lj.x - li.x, dj = lj.y - li.y;
+            const float nn = (float)(di * di + dj * dj);
+            float q, eq;
+            two_prod(nn, gq.y, q, eq);
+            const float xi = gq.x * sqrtf(nn);
+            const float s = ff_diff(L2h, L2l, q, eq + nn * gq.z) / (xi * (sqrtf(L2h) + xi));
+            maxs = fmaxf(maxs, fabsf(s) / s0g);
+        }
+    }
+    const float fm = block_sum_modes(acc, smq, M);
+    const float dm = (int)threadIdx.x < M ? fm - y[threadIdx.x] : 0.f;
+    const double M2 = block_sum_d((double)dm * dm, smd);
+    const double F2 = block_sum_d((int)threadIdx.x < M ? (double)fm * fm : 0.0, smd);
+    const double E2 = block_sum_d(e2, smd);
+    const double R2 = block_sum_d(r2, smd);
+    const float mx = block_max_f(maxs, smf);
+    if (threadIdx.x == 0) {
+        const double floor_f = k.rho * (double)gq.w * fmax(sqrt(k.gx * k.gx + k.gy * k.gy), 100.0);
+        const double err = sqrt(E2 / fmax(R2, (double)n * floor_f * floor_f));
+        const double floor_m = floor_f / (double)Eh;
+        const double merr = sqrt(M2 / fmax(F2, (double)n * floor_m * floor_m));
+        d.sur_err[g] = (float)err;
+        d.sur_merr[g] = (float)merr;
+        d.sur_maxs[g] = mx;
+        if (mx > k.gate || err > k.err_tol) d.sur_active[g] = 0;
+    }
+}
+
+// f = -Lambda q + net(q), in place in the network output rows.
+__global__ void k_sur_combine(DevPtrs d, KParams k) {
+    const int g = blockIdx.x;
+    const int t = d.g_tmpl[g];
+    if (t < 0 || !d.sur_active[g] || (int)threadIdx.x >= k.n_modes) return;
+    const size_t row = (size_t)(d.tmpl_slot[t] + d.g_slot[g]) * k.n_modes + threadIdx.x;
+    d.sur_y[row] -= d.sur_lambda[t * k.n_modes + threadIdx.x] * d.sur_x[row];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+cudaError_t launch_sur_combine(const DevPtrs &d, const KParams &k, cudaStream_t s) {
+    k_sur_combine<<<k.G, 32, 0, s>>>(d, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_frame(const DevPtrs &d, const KParams &k, int all_templated, cudaStream_t s) {
+    k_sur_frame<<<k.G, kSurThreads, 0, s>>>(d, k, all_templated);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_project_cc(const DevPtrs &d, const KParams &k, const double2 *F, float *out, cudaStream_t s) {
+    k_sur_project_cc<<<k.G, kSurThreads, 0, s>>>(d, k, F, out);
+    return cudaGetLastError();
+}
+
+cudaError_t sur_init_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(k_sur_project_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kProjSmem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sur_expand_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kExpSmem);
+}
+
+cudaError_t launch_sur_project_tc(const DevPtrs &d, const KParams &k, cudaStream_t s) {
+    if (k.n_proj_work == 0) return cudaSuccess;
+    k_sur_project_tc<<<k.n_proj_work, 128, kProjSmem, s>>>(d, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_reduce(const DevPtrs &d, const KParams &k, cudaStream_t s) {
+    if (k.n_rows == 0) return cudaSuccess;
+    k_sur_reduce<<<k.n_rows, 32, 0, s>>>(d, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_expand_tc(const DevPtrs &d, const KParams &k, cudaStream_t s) {
+    if (k.n_exp_work == 0) return cudaSuccess;
+    k_sur_expand_tc<<<k.n_exp_work, 128, kExpSmem, s>>>(d, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_judge(const DevPtrs &d, const KParams &k, cudaStream_t s) {
+    k_sur_judge<<<k.G, kSurThreads, 0, s>>>(d, k);
+    return cudaGetLastError();
+}
+
+}  // namespace pd

@@ -212,23 +212,21 @@ def two_disks(h_ratio: int = 8, gap: float = 0.5e-3, floor_gap: float | None = N
 
 def _rsa_place(rng, radii, box_lo, box_hi, margin, max_tries=200000):
     """Random sequential addition of non-overlapping disks of radius radii+margin."""
-    placed = []
-    for r in radii:
+    n = len(radii)
+    P = np.zeros((n, 2))
+    Rr = np.zeros(n)
+    for k, r in enumerate(radii):
         rr = r + margin
         for _ in range(max_tries):
             x = rng.uniform(box_lo[0] + rr + margin, box_hi[0] - rr - margin)
             y = rng.uniform(box_lo[1] + rr + margin, box_hi[1] - rr - margin)
-            ok = True
-            for (px, py, pr) in placed:
-                if (x - px) ** 2 + (y - py) ** 2 < (rr + pr) ** 2:
-                    ok = False
-                    break
-            if ok:
-                placed.append((x, y, rr))
+            if k == 0 or np.all((P[:k, 0] - x) ** 2 + (P[:k, 1] - y) ** 2 >= (Rr[:k] + rr) ** 2):
+                P[k] = (x, y)
+                Rr[k] = rr
                 break
         else:
             raise RuntimeError("random sequential addition failed; box too small")
-    return np.array([(x, y) for (x, y, _) in placed])
+    return P
 
 
 def settling(n_grains: int = 50, box=(20e-3, 30e-3), r_range=(1e-3, 1.5e-3), h_ratio: int = 15,
@@ -268,9 +266,14 @@ def settling(n_grains: int = 50, box=(20e-3, 30e-3), r_range=(1e-3, 1.5e-3), h_r
 
 
 def compaction(n_grains: int = 500, width: float = 40e-3, r_range=(0.8e-3, 1.6e-3), h_ratio: int = 23,
-               wall_speed: float = 0.1, seed: int = 3, n_steps: int = 2000, dt: float = 5e-8,
-               **over) -> Workload:
-    """Mixed-shape grains in a box of given width whose top wall moves down."""
+               wall_speed: float = 0.1, seed: int = 3, n_steps: int = 2000, dt: float = 2e-8,
+               agitation: float = 0.0, **over) -> Workload:
+    """Mixed-shape grains in a box of given width whose top wall moves down
+    (no gravity).  dt = 2e-8 s keeps the damped contact of the h = R/23
+    lattice (h_min = 35 um) stable at k = 5e5 Pa.  With agitation > 0 every
+    grain starts with that speed in a seeded random direction, so that grains
+    collide, load and fracture within a few hundred steps (a loaded window
+    without the long compaction run that would lead to it)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     radii = rng.uniform(r_range[0], r_range[1], size=n_grains)
     area = float(np.sum(math.pi * (radii + 0.1e-3) ** 2))
@@ -278,6 +281,10 @@ def compaction(n_grains: int = 500, width: float = 40e-3, r_range=(0.8e-3, 1.6e-
     w = settling(n_grains=n_grains, box=(width, height), r_range=r_range, h_ratio=h_ratio,
                  seed=seed, n_steps=n_steps, dt=dt, gy=0.0, **over)
     w.params["wall_vel_hi"] = (0.0, -wall_speed)
+    if agitation > 0:
+        ang = np.random.Generator(np.random.PCG64(seed + 77)).uniform(0.0, 2 * math.pi, size=n_grains)
+        w.grain_geom[:, 4] = agitation * np.cos(ang)
+        w.grain_geom[:, 5] = agitation * np.sin(ang)
     w.name = f"compaction_{n_grains}g_seed{seed}"
     return w
 
@@ -333,3 +340,39 @@ def merge_aggregates(parts, name="ensemble") -> Workload:
     out.agg_walls = np.asarray(walls, dtype=np.float64)
     out.parts = parts
     return out
+
+
+def surrogate_settling(n_grains: int = 2000, r_range=(1.0e-3, 1.5e-3), h_ratio: int = 23, seed: int = 5,
+                       dt: float = 2.5e-8, n_steps: int = 5000) -> Workload:
+    """Large settling aggregate for the surrogate: ~1000-node grains (h = R/23) of
+    the settling shape mix in a box of packing ~0.35 (dt = 2.5e-8 s for the finer
+    lattice)."""
+    rmean = 0.5 * (r_range[0] + r_range[1])
+    area = n_grains * math.pi * (rmean + 0.1e-3) ** 2 / 0.35
+    width = math.sqrt(area / 2.0)
+    w = settling(n_grains=n_grains, box=(width, 2.0 * width), r_range=r_range, h_ratio=h_ratio, seed=seed,
+                 n_steps=n_steps, dt=dt)
+    w.name = f"surrogate_settling_{n_grains}g_seed{seed}"
+    return w
+
+
+def free_grains(shapes=("hexagon", "disk"), n_per_shape: int = 8, R: float = 1e-3, h_ratio: int = 10,
+                seed: int = 9, dt: float = 5e-8, n_steps: int = 2000) -> Workload:
+    """Grains of equal size on a grid 3R apart, at rest, no gravity, random
+    orientations: no contact, only the bond forces of whatever deformation a
+    test gives them."""
+    rng = np.random.default_rng(seed)
+    names = [n for n in shapes for _ in range(n_per_shape)]
+    G = len(names)
+    cols = int(math.ceil(math.sqrt(G)))
+    rows = int(math.ceil(G / cols))
+    pitch = 3.0 * R
+    shape_list = [SHAPE_MAKERS[n]() for n in shapes]
+    gs = [shapes.index(n) for n in names]
+    geom = []
+    for k in range(G):
+        cx = (k % cols + 1) * pitch
+        cy = (k // cols + 1) * pitch
+        geom.append([cx, cy, R, rng.uniform(0.0, 2.0 * math.pi), 0.0, 0.0, R / h_ratio])
+    params = default_params(gy=0.0, dt=dt, wall_lo=(0.0, 0.0), wall_hi=((cols + 1) * pitch, (rows + 1) * pitch))
+    return _mk(shape_list, gs, geom, params, n_steps, f"free_grains_{G}g_h{h_ratio}")
