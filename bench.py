@@ -35,8 +35,20 @@ BYTES_PER_BOND_FP32 = 4
 
 
 def workload_for(rank: int, args):
+    """Rank r runs its own seeded aggregate (seed 1 + r): independent problems."""
     from paper_2108_07212_gb300 import inputs as I
     return I.settling(n_grains=50, seed=1 + rank)
+
+
+def max_over_ranks(dist, values, device):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the
+    whole-job time); identity without a process group."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
 
 
 def describe(w, sim=None):
@@ -464,10 +476,7 @@ def run_ours(args):
             step64_ms, force64_ms = _timed_steps(sim64, stream, flush_l2, args.steps, args.warmup, torch)
     elapsed = sum(step_ms) / 1e3
     elapsed64 = sum(step64_ms) / 1e3 if sim64 is not None else elapsed
-    if dist is not None:
-        t = torch.tensor([elapsed, elapsed64], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed, elapsed64 = float(t[0].item()), float(t[1].item())
+    elapsed, elapsed64 = max_over_ranks(dist, [elapsed, elapsed64], dev)
     rc, st = sim.status()
 
     value = sim.N * world * args.steps / elapsed

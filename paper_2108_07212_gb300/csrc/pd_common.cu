@@ -104,11 +104,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int *__restri
     if (blockIdx.x == 0 && threadIdx.x == 0) start[T] = N;
 }
 
-__global__ void __launch_bounds__(kBlock) k_scatter(const int *__restrict__ key, int *cursor, int *sorted, int N) {
+__global__ void __launch_bounds__(kBlock) k_scatter(DevPtrs d, KParams k) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    int pos = atomicAdd(&cursor[key[i]], 1);
-    sorted[pos] = i;
+    if (i >= k.N) return;
+    scatter_node<false>(d, k, i);
 }
 
 __global__ void __launch_bounds__(kBlock) k_positions(DevPtrs d, KParams k) {
@@ -187,7 +186,7 @@ cudaError_t launch_bin(const DevPtrs &d, const KParams &k, cudaStream_t s) {
     k_scan_reduce<<<nb, kScanThreads, 0, s>>>(d.count, d.blocksums, k.T);
     k_scan_top<<<1, kScanThreads, 0, s>>>(d.blocksums, nb);
     k_scan_apply<<<nb, kScanThreads, 0, s>>>(d.count, d.blocksums, d.start, d.cursor, k.T, k.N);
-    k_scatter<<<nblk(k.N, kBlock), kBlock, 0, s>>>(d.key, d.cursor, d.sorted, k.N);
+    k_scatter<<<nblk(k.N, kBlock), kBlock, 0, s>>>(d, k);
     return cudaGetLastError();
 }
 

@@ -210,13 +210,16 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// |d|^2 of d = (dxh + dxl, dyh + dyl) as a float-float pair (hi, lo).
+// |d|^2 of d = (dxh + dxl, dyh + dyl) as a float-float pair (hi, lo).  The low
+// parts are not small against one ulp of the high parts (they carry the
+// position bits below the float grid of the box coordinates), so the square
+// keeps dxl^2 + dyl^2 as well as the cross terms.
 __device__ __forceinline__ void len2_ff(float dxh, float dxl, float dyh, float dyl, float &hi, float &lo) {
     float px, ex, py, ey, s, es;
     two_prod(dxh, dxh, px, ex);
     two_prod(dyh, dyh, py, ey);
     two_sum(px, py, s, es);
-    float r = es + (ex + ey) + 2.f * (dxh * dxl + dyh * dyl);
+    float r = es + (ex + ey) + (2.f * (dxh * dxl + dyh * dyl) + (dxl * dxl + dyl * dyl));
     hi = __fadd_rn(s, r);
     lo = __fsub_rn(r, __fsub_rn(hi, s));
 }
@@ -249,9 +252,16 @@ __device__ __forceinline__ void damping_friction32(float rd, float Kn, float rho
 template <bool PERSIST>
 __device__ __forceinline__ void predict_node(const DevPtrs &d, const KParams &k, int i, int vin, int advance) {
     double2 u = ldm<PERSIST>(&d.u[i]);
+    const double2 v = ldm<PERSIST>(&d.v[vin][i]);
+    if (d.vh) {
+        // FP32 split: the start-of-step velocity as a float-float pair for the contact laws
+        const float2 h = make_float2((float)v.x, (float)v.y);
+        d.vh[i] = h;
+        d.vl[i] = make_float2((float)(v.x - (double)h.x), (float)(v.y - (double)h.y));
+    }
     if (advance) {
         // explicit round-to-nearest operations: never contracted into FMAs
-        double2 v = ldm<PERSIST>(&d.v[vin][i]), a = ldm<PERSIST>(&d.a[i]);
+        const double2 a = ldm<PERSIST>(&d.a[i]);
         u.x = __dadd_rn(__dadd_rn(u.x, __dmul_rn(k.dt, v.x)), __dmul_rn(k.half_dt2, a.x));
         u.y = __dadd_rn(__dadd_rn(u.y, __dmul_rn(k.dt, v.y)), __dmul_rn(k.half_dt2, a.y));
         d.u[i] = u;
@@ -274,6 +284,23 @@ __device__ __forceinline__ void predict_node(const DevPtrs &d, const KParams &k,
     atomicAdd(&d.count[b], 1);
 }
 
+// Counting-sort scatter of node i into its bucket, with its position record.
+template <bool PERSIST>
+__device__ __forceinline__ void scatter_node(const DevPtrs &d, const KParams &k, int i) {
+    const int pos = atomicAdd(&d.cursor[ldm<PERSIST>(&d.key[i])], 1);
+    d.sorted[pos] = i;
+    uint4 rec;
+    if (k.fp32) {
+        const float2 ph = ldm<PERSIST>(&d.ph[i]), pl = ldm<PERSIST>(&d.pl[i]);
+        rec = make_uint4(__float_as_uint(ph.x), __float_as_uint(ph.y), __float_as_uint(pl.x), __float_as_uint(pl.y));
+    } else {
+        const double2 p = ldm<PERSIST>(&d.p[i]);
+        rec = make_uint4((unsigned)__double2loint(p.x), (unsigned)__double2hiint(p.x), (unsigned)__double2loint(p.y),
+                         (unsigned)__double2hiint(p.y));
+    }
+    d.srec[pos] = rec;
+}
+
 // Gather the contact candidates S^nbr of node i (all nodes y != i of the same
 // aggregate with |p(y) - p(i)| < R_c) from the hash-grid
 // cells lane, lane + LANES, ... of the 3x3 block, in ascending node index.
@@ -291,9 +318,12 @@ __device__ __forceinline__ int gather_candidates(const DevPtrs &d, const KParams
         if (dup) continue;
         const int t0 = ldm<PERSIST>(&d.start[bc]), t1 = ldm<PERSIST>(&d.start[bc + 1]);
         for (int t = t0; t < t1; ++t) {
+            // the bucket's positions are stored in bucket order: the distance test
+            // needs no index chase; only nodes within R_c are looked up
+            if (!within(ldm<PERSIST>(&d.srec[t]))) continue;
             const int j = ldm<PERSIST>(&d.sorted[t]);
             // hash aliasing can bring nodes of another aggregate: never in contact
-            if (j == i || __ldg(&d.g_agg[__ldg(&d.grain[j])]) != ag || !within(j)) continue;
+            if (j == i || __ldg(&d.g_agg[__ldg(&d.grain[j])]) != ag) continue;
             if (nc < kMaxCand) {
                 int w = nc++;
                 while (w > 0 && cand[w - 1] > j) {
@@ -365,9 +395,18 @@ __device__ __forceinline__ T lane_sum(T v) {
 // in the textbook order (bonds in CSR order, contacts in ascending index).
 // Every thread of the warp must call this (shuffles); inactive lanes pass
 // active = false.
+// Lane-summed per-node force parts (bond, self-contact, contact), handed from
+// the lanes of a node to the node's epilogue thread.
+struct Sums64 {
+    double bx, by, sx, sy, nx, ny;
+};
+struct Sums32 {
+    float bx, by, sx, sy, nx, ny;
+};
+
 template <bool PERSIST, int LANES>
 __device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k, int i, int lane, bool active,
-                                             int vin, int update_v) {
+                                             int vin, Sums64 &out) {
     const int ii = active ? i : 0;
     const double2 pi = ldm<PERSIST>(&d.p[ii]);
     const double2 Xi = __ldg(&d.X[ii]);
@@ -404,8 +443,8 @@ __device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k,
     // contact candidates, self-contact (Sec. 4.4), inter-grain contact (Secs. 4.1-4.3)
     int cand[kMaxCand];
     const double Rc = A.Rc;
-    const int nc = gather_candidates<PERSIST, LANES>(d, k, ag, ii, lane, active, cand, [&](int j) {
-        const double2 pj = ldm<PERSIST>(&d.p[j]);
+    const int nc = gather_candidates<PERSIST, LANES>(d, k, ag, ii, lane, active, cand, [&](uint4 rec) {
+        const double2 pj = make_double2(__hiloint2double((int)rec.y, (int)rec.x), __hiloint2double((int)rec.w, (int)rec.z));
         double dx = pj.x - pi.x, dy = pj.y - pi.y;
         return sqrt(dx * dx + dy * dy) < Rc;
     });
@@ -448,16 +487,26 @@ __device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k,
             Fny += gy;
         }
     }
-    Fbx = lane_sum<LANES>(Fbx);
-    Fby = lane_sum<LANES>(Fby);
-    Fsx = lane_sum<LANES>(Fsx);
-    Fsy = lane_sum<LANES>(Fsy);
-    Fnx = lane_sum<LANES>(Fnx);
-    Fny = lane_sum<LANES>(Fny);
-    if (!active || lane != 0) return;
+    out.bx = lane_sum<LANES>(Fbx);
+    out.by = lane_sum<LANES>(Fby);
+    out.sx = lane_sum<LANES>(Fsx);
+    out.sy = lane_sum<LANES>(Fsy);
+    out.nx = lane_sum<LANES>(Fnx);
+    out.ny = lane_sum<LANES>(Fny);
+}
+
+// Wall forces and the update of node i from its lane sums, one thread per node
+// (the FP64 work runs with converged warps).
+template <bool PERSIST>
+__device__ __forceinline__ void node_epilogue64(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
+                                                const Sums64 &f) {
+    const double2 pi = ldm<PERSIST>(&d.p[i]);
+    const double2 vi = ldm<PERSIST>(&d.v[vin][i]);
+    const double Vi = __ldg(&d.V[i]);
+    const AggParams &A = d.agg[__ldg(&d.g_agg[__ldg(&d.grain[i])])];
     double Fwx, Fwy;
     wall_force64(k, A, ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, Vi, Fwx, Fwy, d.status);
-    finish_node<PERSIST>(d, k, i, vin, update_v, vi, Vi, Fbx, Fby, Fsx, Fsy, Fnx, Fny, Fwx, Fwy);
+    finish_node<PERSIST>(d, k, i, vin, update_v, vi, Vi, f.bx, f.by, f.sx, f.sy, f.nx, f.ny, Fwx, Fwy);
 }
 
 // FP32-split forces of node i: the same laws and lane layout, with the bond,
@@ -472,7 +521,7 @@ __device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k,
 // re-decided with the FP64 stretch, so break decisions are the FP64 ones.
 template <bool PERSIST, int LANES>
 __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k, int i, int lane, bool active,
-                                             int vin, int update_v) {
+                                             int vin, Sums32 &out) {
     const int ii = active ? i : 0;
     const float2 phi = ldm<PERSIST>(&d.ph[ii]), pli = ldm<PERSIST>(&d.pl[ii]);
     const int2 li = __ldg(&d.lat[ii]);
@@ -481,11 +530,12 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
     const AggParams &A = d.agg[ag];
     const float4 gq = __ldg(&d.gq[gi]);                   // (h, h^2 hi, h^2 lo, V)
     const float Vi = gq.w;
-    const float cw = (float)__ldg(&d.g_cw[gi]), s0 = (float)__ldg(&d.g_s0[gi]), eps = (float)__ldg(&d.g_eps[gi]);
+    const float4 gc = __ldg(&d.gc[gi]);                   // (c_w, s0, eps) as floats
+    const float cw = gc.x, s0 = gc.y, eps = gc.z;
     const float s0_lo = s0 * (1.0f - k.guard), s0_hi = s0 * (1.0f + k.guard);
     const int r0 = active ? __ldg(&d.row_ptr[ii]) : 0, r1 = active ? __ldg(&d.row_ptr[ii + 1]) : 0;
     uint32_t *bw = d.bits + (size_t)ii * k.wpn;
-    const float Rc = (float)A.Rc, Kn = (float)A.Kn;
+    const float Rc = A.rcf, Kn = A.knf;
 
     float Fbx = 0.f, Fby = 0.f;
     const float VV = Vi * Vi;
@@ -505,55 +555,82 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
         Fbx = (rot.x * f.x - rot.y * f.y) * Eh;
         Fby = (rot.y * f.x + rot.x * f.y) * Eh;
     }
-    for (int b = r0 + lane; b < r1 && !(sur && !judge); b += LANES) {
-        const int kk = b - r0;
-        if ((__ldcg(&bw[kk >> 5]) >> (kk & 31)) & 1u) continue;
-        const int j = __ldg(&d.col[b]);
-        const float2 phj = ldm<PERSIST>(&d.ph[j]), plj = ldm<PERSIST>(&d.pl[j]);
-        const int2 lj = __ldg(&d.lat[j]);
-        const float dxh = __fsub_rn(phj.x, phi.x), dxl = plj.x - pli.x;
-        const float dyh = __fsub_rn(phj.y, phi.y), dyl = plj.y - pli.y;
-        float L2h, L2l;
-        len2_ff(dxh, dxl, dyh, dyl, L2h, L2l);
-        const int di = lj.x - li.x, dj = lj.y - li.y;
-        const float nn = (float)(di * di + dj * dj);
-        float q, eq;
-        two_prod(nn, gq.y, q, eq);                           // |xi|^2 = n h^2
-        const float num = ff_diff(L2h, L2l, q, eq + nn * gq.z);
-        const float xi = gq.x * sqrtf(nn);
-        const float L = sqrtf(L2h);
-        const float s = num / (xi * (L + xi));
-        const float as = fabsf(s);
-        bool brk;
-        if (as > s0_lo && as < s0_hi) {
-            const double2 pi = ldm<PERSIST>(&d.p[ii]), pj = ldm<PERSIST>(&d.p[j]);
-            double ddx = pj.x - pi.x, ddy = pj.y - pi.y;
-            double L64 = sqrt(ddx * ddx + ddy * ddy);
-            double xi64 = __ldg(&d.xi[b]);
-            brk = fabs((L64 - xi64) / xi64) > __ldg(&d.g_s0[gi]);
-        } else {
-            brk = as > s0;
+    // bonds in batches of kBondBatch per lane: the column indices, broken words and
+    // neighbour positions of a batch are all in flight before any is used (the
+    // per-lane summation order is unchanged: bonds lane, lane + LANES, ...)
+    constexpr int kBondBatch = 4;
+    for (int b0 = r0 + lane; b0 < r1 && !(sur && !judge); b0 += kBondBatch * LANES) {
+        int jb[kBondBatch];
+        uint32_t wb[kBondBatch];
+#pragma unroll
+        for (int m = 0; m < kBondBatch; ++m) {
+            const int b = b0 + m * LANES;
+            jb[m] = b < r1 ? __ldg(&d.col[b]) : -1;
+            wb[m] = b < r1 ? __ldcg(&bw[(b - r0) >> 5]) : 0u;
         }
-        if (brk) {
-            atomicOr(&bw[kk >> 5], 1u << (kk & 31));
-            continue;
+        float2 phb[kBondBatch], plb[kBondBatch];
+        int2 lb[kBondBatch];
+#pragma unroll
+        for (int m = 0; m < kBondBatch; ++m) {
+            const int j = jb[m] < 0 ? ii : jb[m];
+            phb[m] = ldm<PERSIST>(&d.ph[j]);
+            plb[m] = ldm<PERSIST>(&d.pl[j]);
+            lb[m] = __ldg(&d.lat[j]);
         }
-        const float cws = (k.micro ? cw * (1.0f - xi / eps) : cw) * s;
-        const float qf = cws * VV / L;
-        Fbx += qf * (dxh + dxl);
-        Fby += qf * (dyh + dyl);
+#pragma unroll
+        for (int m = 0; m < kBondBatch; ++m) {
+            const int b = b0 + m * LANES;
+            const int kk = b - r0;
+            if (jb[m] < 0 || ((wb[m] >> (kk & 31)) & 1u)) continue;
+            const int j = jb[m];
+            const float2 phj = phb[m], plj = plb[m];
+            const int2 lj = lb[m];
+            const float dxh = __fsub_rn(phj.x, phi.x), dxl = plj.x - pli.x;
+            const float dyh = __fsub_rn(phj.y, phi.y), dyl = plj.y - pli.y;
+            float L2h, L2l;
+            len2_ff(dxh, dxl, dyh, dyl, L2h, L2l);
+            const int di = lj.x - li.x, dj = lj.y - li.y;
+            const float nn = (float)(di * di + dj * dj);
+            float q, eq;
+            two_prod(nn, gq.y, q, eq);                           // |xi|^2 = n h^2
+            const float num = ff_diff(L2h, L2l, q, eq + nn * gq.z);
+            const float xi = gq.x * sqrtf(nn);
+            const float L = sqrtf(L2h);
+            const float s = num / (xi * (L + xi));
+            const float as = fabsf(s);
+            bool brk;
+            if (as > s0_lo && as < s0_hi) {
+                const double2 pi = ldm<PERSIST>(&d.p[ii]), pj = ldm<PERSIST>(&d.p[j]);
+                double ddx = pj.x - pi.x, ddy = pj.y - pi.y;
+                double L64 = sqrt(ddx * ddx + ddy * ddy);
+                double xi64 = __ldg(&d.xi[b]);
+                brk = fabs((L64 - xi64) / xi64) > __ldg(&d.g_s0[gi]);
+            } else {
+                brk = as > s0;
+            }
+            if (brk) {
+                atomicOr(&bw[kk >> 5], 1u << (kk & 31));
+                continue;
+            }
+            const float cws = (k.micro ? cw * (1.0f - xi / eps) : cw) * s;
+            const float qf = cws * VV / L;
+            Fbx += qf * (dxh + dxl);
+            Fby += qf * (dyh + dyl);
+        }
     }
     __syncwarp();
 
     int cand[kMaxCand];
-    const int nc = gather_candidates<PERSIST, LANES>(d, k, ag, ii, lane, active, cand, [&](int j) {
-        const float2 phj = ldm<PERSIST>(&d.ph[j]), plj = ldm<PERSIST>(&d.pl[j]);
+    const int nc = gather_candidates<PERSIST, LANES>(d, k, ag, ii, lane, active, cand, [&](uint4 rec) {
+        const float2 phj = make_float2(__uint_as_float(rec.x), __uint_as_float(rec.y));
+        const float2 plj = make_float2(__uint_as_float(rec.z), __uint_as_float(rec.w));
         float L2h, L2l;
         len2_ff(__fsub_rn(phj.x, phi.x), plj.x - pli.x, __fsub_rn(phj.y, phi.y), plj.y - pli.y, L2h, L2l);
         return ff_diff(A.rc2_hi, A.rc2_lo, L2h, L2l) > 0.f;
     });
-    const double2 vi = ldm<PERSIST>(&d.v[vin][ii]);
-    const float rd = (float)k.rd, rho = (float)k.rho, dt = (float)k.dt, mu = (float)k.mu;
+    // start-of-step velocity as a float-float pair (written by the binning phase)
+    const float2 vhi = ldm<PERSIST>(&d.vh[ii]), vli = ldm<PERSIST>(&d.vl[ii]);
+    const float rd = k.rdf, rho = k.rhof, dt = k.dtf, mu = k.muf;
     float Fsx = 0.f, Fsy = 0.f, Fnx = 0.f, Fny = 0.f;
     for (int q = 0; q < nc; ++q) {
         const int j = cand[q];
@@ -571,8 +648,9 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
         const float overlap = ff_diff(A.rc2_hi, A.rc2_lo, L2h, L2l) / (Rc + dd);   // R_c - |d|
         const int gj = __ldg(&d.grain[j]);
         const float Vj = __ldg(&d.gq[gj]).w;
-        const double2 vj = ldm<PERSIST>(&d.v[vin][j]);
-        const float vrx = (float)(vi.x - vj.x), vry = (float)(vi.y - vj.y);
+        // v(x) - v(y): exact high-part difference when the two are close (Sterbenz), plus the low parts
+        const float2 vhj = ldm<PERSIST>(&d.vh[j]), vlj = ldm<PERSIST>(&d.vl[j]);
+        const float vrx = __fsub_rn(vhi.x, vhj.x) + (vli.x - vlj.x), vry = __fsub_rn(vhi.y, vhj.y) + (vli.y - vlj.y);
         if (gj == gi) {
             if (bonded_intact(d, k, ii, r0, r1, j)) continue;
             const int2 lj = __ldg(&d.lat[j]);
@@ -602,20 +680,26 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
             Fny += gy;
         }
     }
-    Fbx = lane_sum<LANES>(Fbx);
-    Fby = lane_sum<LANES>(Fby);
-    Fsx = lane_sum<LANES>(Fsx);
-    Fsy = lane_sum<LANES>(Fsy);
-    Fnx = lane_sum<LANES>(Fnx);
-    Fny = lane_sum<LANES>(Fny);
-    if (!active || lane != 0) return;
-    if (sur && judge) d.sur_fb[i] = make_float2(Fbx, Fby);   // full bond force for the judge
-    const double Vi64 = __ldg(&d.V[i]);
+    out.bx = lane_sum<LANES>(Fbx);
+    out.by = lane_sum<LANES>(Fby);
+    out.sx = lane_sum<LANES>(Fsx);
+    out.sy = lane_sum<LANES>(Fsy);
+    out.nx = lane_sum<LANES>(Fnx);
+    out.ny = lane_sum<LANES>(Fny);
+    if (sur && judge && lane == 0) d.sur_fb[i] = make_float2(out.bx, out.by);   // full bond force for the judge
+}
+
+template <bool PERSIST>
+__device__ __forceinline__ void node_epilogue32(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
+                                                const Sums32 &f) {
+    const double2 pi = ldm<PERSIST>(&d.p[i]);
+    const double2 vi = ldm<PERSIST>(&d.v[vin][i]);
+    const double Vi = __ldg(&d.V[i]);
+    const AggParams &A = d.agg[__ldg(&d.g_agg[__ldg(&d.grain[i])])];
     double Fwx, Fwy;
-    const double2 pi64 = ldm<PERSIST>(&d.p[i]);
-    wall_force64(k, A, ldm<PERSIST>(d.t_now), pi64.x, pi64.y, vi.x, vi.y, Vi64, Fwx, Fwy, d.status);
-    finish_node<PERSIST>(d, k, i, vin, update_v, vi, Vi64, (double)Fbx, (double)Fby, (double)Fsx, (double)Fsy,
-                         (double)Fnx, (double)Fny, Fwx, Fwy);
+    wall_force64(k, A, ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, Vi, Fwx, Fwy, d.status);
+    finish_node<PERSIST>(d, k, i, vin, update_v, vi, Vi, (double)f.bx, (double)f.by, (double)f.sx, (double)f.sy,
+                         (double)f.nx, (double)f.ny, Fwx, Fwy);
 }
 
 }  // namespace pd

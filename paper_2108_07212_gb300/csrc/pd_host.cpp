@@ -219,7 +219,7 @@ struct pd_ctx {
     std::vector<float> sur_basis, sur_lambda;   // basis: per template mode-major, padded rows
     std::vector<uint16_t> bnm_hi, bnm_lo, bmm_hi, bmm_lo;
     std::vector<int32_t> tmpl_rows, slot_grain;
-    std::vector<int4> proj_work, exp_work;
+    std::vector<int4> proj_work, exp_work, mlp_work;
     std::vector<pd_mlp *> sur_mlp;
 };
 
@@ -258,6 +258,8 @@ void compute_aggregates(pd_ctx *c) {
         double rc2 = A.Rc * A.Rc;
         A.rc2_hi = (float)rc2;
         A.rc2_lo = (float)(rc2 - (double)A.rc2_hi);
+        A.rcf = (float)A.Rc;
+        A.knf = (float)A.Kn;
     }
     c->h_min = hmin[0] < 1e300 ? hmin[0] : c->g_h[0];
     c->Rc = c->aggp[0].Rc;
@@ -334,6 +336,7 @@ size_t layout(pd_ctx *c, char *base) {
     carve(base, off, d.start, (size_t)c->T + 1);
     carve(base, off, d.cursor, c->T);
     carve(base, off, d.sorted, N);
+    carve(base, off, d.srec, N);
     // block sums of the scan: one per scan tile (multi-kernel path) or per
     // block of the persistent kernel (at most 16 blocks per SM)
     carve(base, off, d.blocksums, std::max<size_t>(c->T / pd::kScanTile + 2, 16 * 1024));
@@ -348,10 +351,15 @@ size_t layout(pd_ctx *c, char *base) {
         carve(base, off, d.gq, G);
         carve(base, off, d.ph, N);
         carve(base, off, d.pl, N);
+        carve(base, off, d.vh, N);
+        carve(base, off, d.vl, N);
+        carve(base, off, d.gc, G);
     } else {
         d.lat = nullptr;
         d.gq = nullptr;
         d.ph = d.pl = nullptr;
+        d.vh = d.vl = nullptr;
+        d.gc = nullptr;
     }
     carve(base, off, d.bu, N);
     carve(base, off, d.bv, N);
@@ -377,6 +385,9 @@ size_t layout(pd_ctx *c, char *base) {
         carve(base, off, d.sur_f, N);
         carve(base, off, d.sur_xpart, (size_t)(c->tmpl_rows.empty() ? 0 : sur_max_chunks(c)) * G * M);
         carve(base, off, d.sur_merr, G);
+        carve(base, off, d.mlp_refs, T);
+        carve(base, off, d.mlp_work, (G + pd::kSurTile - 1) / pd::kSurTile + T);
+        carve(base, off, d.mlp_err, 1);
         carve(base, off, d.sur_lambda, T * M);
         carve(base, off, d.g_theta, G);
         carve(base, off, d.g_xbar, G);
@@ -397,6 +408,9 @@ size_t layout(pd_ctx *c, char *base) {
         d.proj_work = d.exp_work = nullptr;
         d.sur_w = d.sur_f = nullptr;
         d.sur_xpart = d.sur_merr = nullptr;
+        d.mlp_refs = nullptr;
+        d.mlp_work = nullptr;
+        d.mlp_err = nullptr;
         d.basis = d.sur_x = d.sur_y = d.sur_err = d.sur_maxs = d.sur_qs = d.sur_fs = d.sur_lambda = nullptr;
         d.g_theta = d.sur_phi = nullptr;
         d.g_xbar = nullptr;
@@ -420,15 +434,9 @@ cudaError_t record_surrogate(pd_ctx *c, cudaStream_t s) {
     if ((e = pd::launch_sur_frame(c->d, c->kp, 0, s)) != cudaSuccess) return e;
     if ((e = pd::launch_sur_project_tc(c->d, c->kp, s)) != cudaSuccess) return e;
     if ((e = pd::launch_sur_reduce(c->d, c->kp, s)) != cudaSuccess) return e;
-    int slot0 = 0;
-    for (int t = 0; t < c->n_tmpl; ++t) {
-        if (c->sur_mlp[t]) {
-            const size_t off = (size_t)slot0 * c->sur_modes;
-            if (pd::mlp_forward_stream(c->sur_mlp[t], c->d.sur_x + off, c->d.sur_y + off, c->tmpl_count[t], s) != PD_OK)
-                return cudaErrorLaunchFailure;
-        }
-        slot0 += c->tmpl_count[t];
-    }
+    if ((e = pd::launch_mlp_grouped(c->d.mlp_refs, c->d.mlp_work, (int)c->mlp_work.size(), c->d.sur_x, c->d.sur_y,
+                                    c->d.mlp_err, s)) != cudaSuccess)
+        return e;
     if ((e = pd::launch_sur_combine(c->d, c->kp, s)) != cudaSuccess) return e;
     return pd::launch_sur_expand_tc(c->d, c->kp, s);
 }
@@ -817,6 +825,10 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     k.dt = p.dt;
     k.half_dt = 0.5 * p.dt;
     k.half_dt2 = 0.5 * p.dt * p.dt;
+    k.rhof = (float)p.rho;
+    k.rdf = (float)p.damping_ratio;
+    k.muf = (float)p.friction;
+    k.dtf = (float)p.dt;
     k.guard = 1e-4f;
     k.fp32 = p.precision == PD_FP32_SPLIT ? 1 : 0;
     k.sur = 0;
@@ -899,6 +911,8 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
         PD_CUDA(cudaMemsetAsync(d.sur_f, 0, 8 * N, s));
         PD_CUDA(cudaMemsetAsync(d.sur_merr, 0, 4 * G, s));
         PD_CUDA(pd::sur_init_attributes());
+        PD_CUDA(pd::mlp_init_attributes());
+        PD_CUDA(cudaMemsetAsync(d.mlp_err, 0, sizeof(int), s));
         PD_CUDA(cudaMemcpyAsync(d.sur_lambda, c->sur_lambda.data(), 4 * c->sur_lambda.size(), cudaMemcpyHostToDevice, s));
         PD_CUDA(cudaMemcpyAsync(d.g_theta, c->g_theta.data(), 8 * G, cudaMemcpyHostToDevice, s));
         PD_CUDA(cudaMemcpyAsync(d.g_xbar, xbar.data(), 16 * G, cudaMemcpyHostToDevice, s));
@@ -910,7 +924,7 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     }
     PD_CUDA(cudaMemsetAsync(d.step, 0, 8, s));
     PD_CUDA(cudaMemsetAsync(d.status, 0, 4 * PD_STATUS_COUNT, s));
-    std::vector<float> gq;
+    std::vector<float> gq, gcf;
     if (p.precision == PD_FP32_SPLIT) {
         // per grain: h, h^2 as a float-float pair, V as float
         gq.resize(4 * G);
@@ -924,6 +938,14 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
         }
         PD_CUDA(cudaMemcpyAsync(d.lat, c->lat.data(), 8 * N, cudaMemcpyHostToDevice, s));
         PD_CUDA(cudaMemcpyAsync(d.gq, gq.data(), 16 * G, cudaMemcpyHostToDevice, s));
+        gcf.resize(4 * G);
+        for (size_t g = 0; g < G; ++g) {
+            gcf[4 * g] = (float)c->g_cw[g];
+            gcf[4 * g + 1] = (float)c->g_s0[g];
+            gcf[4 * g + 2] = (float)c->g_eps[g];
+            gcf[4 * g + 3] = 0.f;
+        }
+        PD_CUDA(cudaMemcpyAsync(d.gc, gcf.data(), 16 * G, cudaMemcpyHostToDevice, s));
     }
     c->vcur = 0;
     c->steps_done = 0;
@@ -1296,7 +1318,20 @@ int pd_surrogate_set_mlp(pd_ctx *c, int tmpl, pd_mlp *mlp) {
     if (int r = check_ctx(c, 3)) return r;
     if (!c->sur_cfg) return fail(PD_ESTATE, "pd_surrogate_setup was not called");
     if (tmpl < 0 || tmpl >= c->n_tmpl) return fail(PD_EINVAL, "template out of range");
+    pd::MlpRef ref{};
+    if (mlp && pd::mlp_ref(mlp, &ref) != PD_OK) return fail(PD_ESTATE, "network not bound to device memory");
     c->sur_mlp[tmpl] = mlp;
+    // device table of the networks and the inference tiles (template, first row, end row)
+    PD_CUDA(cudaMemcpyAsync(c->d.mlp_refs + tmpl, &ref, sizeof(ref), cudaMemcpyHostToDevice, c->stream));
+    c->mlp_work.clear();
+    for (int t = 0, row = 0; t < c->n_tmpl; row += c->tmpl_count[t], ++t)
+        if (c->sur_mlp[t])
+            for (int r0 = 0; r0 < c->tmpl_count[t]; r0 += pd::kSurTile)
+                c->mlp_work.push_back(make_int4(t, row + r0, row + c->tmpl_count[t], 0));
+    if (!c->mlp_work.empty())
+        PD_CUDA(cudaMemcpyAsync(c->d.mlp_work, c->mlp_work.data(), sizeof(int4) * c->mlp_work.size(),
+                                cudaMemcpyHostToDevice, c->stream));
+    PD_CUDA(cudaStreamSynchronize(c->stream));
     if (!mlp) {
         // grains of a template without a network leave the surrogate
         std::vector<int32_t> act(c->G);

@@ -28,6 +28,7 @@ struct AggParams {
     double inv_cell;       // 1 / cell
     double sx, sy;         // FP32-split shift: coordinates of the box map to [L, 2L)
     float rc2_hi, rc2_lo;  // R_c^2 as a float-float pair
+    float rcf, knf;        // R_c and K_n as floats
 };
 
 // Device pointers carved out of the caller's arena.
@@ -47,6 +48,7 @@ struct DevPtrs {
     // contact hash grid (T buckets)
     int *key, *count, *start, *cursor, *sorted, *blocksums;
     int2 *cell;         // hash-grid cell (x, y) of every node, written by the binning phase
+    uint4 *srec;        // position of sorted[t] in bucket order: FP32 split (ph, pl), FP64 p (16 bytes)
     // globals
     long long *step;
     double *t_now;      // time of the force evaluation that follows the predict phase
@@ -58,6 +60,8 @@ struct DevPtrs {
     int2 *lat;          // lattice indices (i, j) of every node in its grain frame
     float4 *gq;         // per grain: (h, h^2 hi, h^2 lo, V = h^2 as float)
     float2 *ph, *pl;    // shifted position (p + shift) as a float-float pair
+    float2 *vh, *vl;    // start-of-step velocity as a float-float pair
+    float4 *gc;         // per grain: (c_w, s0, eps, 0) as floats
     // autotuner backup of the state
     double2 *bu, *bv, *ba;
     uint32_t *bbits;
@@ -77,6 +81,9 @@ struct DevPtrs {
     float2 *sur_w;      // co-rotated local deformation / h of every node of an active grain, lattice frame
     float2 *sur_f;      // surrogate bond force / (E h) of every node of an active grain, lattice frame
     float *sur_xpart;   // projection partial sums [chunk][network row][mode]
+    struct MlpRef *mlp_refs;  // per template: the network's device parameters
+    int4 *mlp_work;     // inference tiles: (template, first row, end row, 0)
+    int *mlp_err;       // set when a network tile's tensor-core wait gave up
     double *g_theta;    // grain orientation at meshing
     double2 *g_xbar;    // reference centroid of every grain
     int *sur_active;    // 1 while the grain is advanced by the surrogate
@@ -97,6 +104,7 @@ struct KParams {
     int N, G, wpn, n_diag_blocks, n_agg;
     unsigned T;         // hash buckets (power of two)
     double rho, rd, mu, gx, gy, dt, half_dt, half_dt2;
+    float rhof, rdf, muf, dtf;   // the same as floats (FP32-split contact laws)
     float guard;        // FP32-split: |(|s| - s0)| < guard * s0 re-decides breaking in FP64
     int micro, store;
     int lanes;          // threads per node in the force kernels (1, 4 or 8)
@@ -131,11 +139,22 @@ cudaError_t launch_sur_expand_tc(const DevPtrs &d, const KParams &k, cudaStream_
 cudaError_t launch_sur_judge(const DevPtrs &d, const KParams &k, cudaStream_t s);
 cudaError_t launch_sur_combine(const DevPtrs &d, const KParams &k, cudaStream_t s);
 
-// Forward pass of a surrogate network on a given stream (captured into the step graph).
+// Device pointers of one network's inference parameters (BF16 weights, FP32
+// parameter vector with the biases).
+struct MlpRef {
+    const void *W1, *W2, *W3;
+    const float *p;
+};
 }  // namespace pd
 struct pd_mlp;
 namespace pd {
+// Forward pass of a surrogate network on a given stream (captured into the step graph).
 int mlp_forward_stream(pd_mlp *m, const float *x, float *y, int batch, cudaStream_t s);
+int mlp_ref(pd_mlp *m, MlpRef *out);
+// Several networks in one launch: work item (network, first row, end row), rows of x / y.
+cudaError_t launch_mlp_grouped(const MlpRef *refs, const int4 *work, int n_work, const float *x, float *y, int *err,
+                               cudaStream_t s);
+cudaError_t mlp_init_attributes();
 
 // Record an error for pd_last_error() and return `code`.
 int set_error(int code, const char *msg);

@@ -50,8 +50,13 @@ __device__ __forceinline__ float gelu_grad(float z) {
 // ---------------------------------------------------------------------------
 // fused forward of one 128-sample tile
 
-__global__ void __launch_bounds__(128) k_mlp_fwd(Net n, const float *__restrict__ X, float *__restrict__ Yout,
-                                                 int B, int Bp, int train) {
+// Rows [row0, row0 + 128) of X (rows >= B are zero) through the network whose
+// BF16 weights are W1, W2, W3 and FP32 parameters p (biases); with train,
+// the activations are kept in the training buffers of n.
+__device__ __forceinline__ void fwd_tile(const __nv_bfloat16 *__restrict__ W1, const __nv_bfloat16 *__restrict__ W2,
+                                         const __nv_bfloat16 *__restrict__ W3, const float *__restrict__ P,
+                                         const float *__restrict__ X, float *__restrict__ Yout, int row0, int B,
+                                         int Bp, int train, const Net &n, int *err) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_base;
@@ -61,7 +66,7 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(Net n, const float *__restrict_
     uint8_t *sW2 = sm + 48 * 1024;        // W2       128 x 128 (32 KB)
     uint8_t *sW3 = sm + 80 * 1024;        // W3        32 x 128 (8 KB)
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int row = blockIdx.x * TILE + tid;
+    const int row = row0 + tid;
     if (warp == 0) tc::tmem_alloc(&tmem_base, 128);
     if (tid == 0) tc::mbar_init(&mbar, 1);
     // operands -> canonical K-major shared layout, 8 values (one 16-byte core
@@ -88,17 +93,17 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(Net n, const float *__restrict_
     for (int e = tid; e < HID * IN / 8; e += 128) {
         const int r = e / (IN / 8), k8 = (e % (IN / 8)) * 8;
         *reinterpret_cast<uint4 *>(sW1 + tc::kmajor_off(r, k8, HID)) =
-            *reinterpret_cast<const uint4 *>(n.W1 + (size_t)r * IN + k8);
+            *reinterpret_cast<const uint4 *>(W1 + (size_t)r * IN + k8);
     }
     for (int e = tid; e < HID * HID / 8; e += 128) {
         const int r = e / (HID / 8), k8 = (e % (HID / 8)) * 8;
         *reinterpret_cast<uint4 *>(sW2 + tc::kmajor_off(r, k8, HID)) =
-            *reinterpret_cast<const uint4 *>(n.W2 + (size_t)r * HID + k8);
+            *reinterpret_cast<const uint4 *>(W2 + (size_t)r * HID + k8);
     }
     for (int e = tid; e < OUT * HID / 8; e += 128) {
         const int r = e / (HID / 8), k8 = (e % (HID / 8)) * 8;
         *reinterpret_cast<uint4 *>(sW3 + tc::kmajor_off(r, k8, OUT)) =
-            *reinterpret_cast<const uint4 *>(n.W3 + (size_t)r * HID + k8);
+            *reinterpret_cast<const uint4 *>(W3 + (size_t)r * HID + k8);
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -128,7 +133,7 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(Net n, const float *__restrict_
         phase ^= 1;
         if (!ok) break;
         tc::fence_after_sync();
-        const float *bias = n.p + (layer == 0 ? OB1 : (layer == 1 ? OB2 : OB3));
+        const float *bias = P + (layer == 0 ? OB1 : (layer == 1 ? OB2 : OB3));
         for (int c0 = 0; c0 < N; c0 += 16) {
             float acc[16];
             tc::tmem_ld16(tmem + lane_base + (uint32_t)c0, acc);
@@ -157,10 +162,25 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(Net n, const float *__restrict_
         __syncthreads();
         tc::fence_after_sync();
     }
-    if (!ok && tid == 0) atomicExch(n.err, 1);
+    if (!ok && tid == 0) atomicExch(err, 1);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem_base, 128);
+}
+
+__global__ void __launch_bounds__(128) k_mlp_fwd(Net n, const float *__restrict__ X, float *__restrict__ Yout,
+                                                 int B, int Bp, int train) {
+    fwd_tile(n.W1, n.W2, n.W3, n.p, X, Yout, blockIdx.x * TILE, B, Bp, train, n, n.err);
+}
+
+// Inference of several networks in one launch: tile blockIdx.x is rows
+// [w.y, min(w.y + 128, w.z)) of X / Y through network refs[w.x].
+__global__ void __launch_bounds__(128) k_mlp_fwd_grouped(const MlpRef *__restrict__ refs, const int4 *__restrict__ work,
+                                                         const float *__restrict__ X, float *__restrict__ Y, int *err) {
+    const int4 w = work[blockIdx.x];
+    const MlpRef r = refs[w.x];
+    fwd_tile(static_cast<const __nv_bfloat16 *>(r.W1), static_cast<const __nv_bfloat16 *>(r.W2),
+             static_cast<const __nv_bfloat16 *>(r.W3), r.p, X, Y, w.y, w.z, 0, 0, Net{}, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -439,6 +459,27 @@ int backward(pd_mlp *m, const float *x, const float *t, int batch) {
 }
 
 }  // namespace
+
+int pd::mlp_ref(pd_mlp *m, MlpRef *out) {
+    if (!m || !m->bound || !out) return pd::set_error(PD_ESTATE, "mlp not bound");
+    out->W1 = m->n.W1;
+    out->W2 = m->n.W2;
+    out->W3 = m->n.W3;
+    out->p = m->n.p;
+    return PD_OK;
+}
+
+cudaError_t pd::launch_mlp_grouped(const MlpRef *refs, const int4 *work, int n_work, const float *x, float *y,
+                                   int *err, cudaStream_t s) {
+    if (n_work == 0) return cudaSuccess;
+    static_assert(sizeof(MlpRef) == 32, "MlpRef layout");
+    pd::mlp::k_mlp_fwd_grouped<<<n_work, 128, kFwdSmem, s>>>(refs, work, x, y, err);
+    return cudaGetLastError();
+}
+
+cudaError_t pd::mlp_init_attributes() {
+    return cudaFuncSetAttribute(pd::mlp::k_mlp_fwd_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
+}
 
 int pd::mlp_forward_stream(pd_mlp *m, const float *x, float *y, int batch, cudaStream_t s) {
     if (!m || !m->bound) return pd::set_error(PD_ESTATE, "mlp not bound");

@@ -3,23 +3,39 @@
 // contraction) and pd_step32.cu.
 #pragma once
 
+#include <type_traits>
+
 #include "pd_device.cuh"
 
 namespace pd {
 
-template <bool FP32, bool PERSIST, int LANES>
-__device__ __forceinline__ void force_node(const DevPtrs &d, const KParams &k, int i, int lane, bool active, int vin,
-                                           int update_v) {
-    if constexpr (FP32) force_node32<PERSIST, LANES>(d, k, i, lane, active, vin, update_v);
-    else force_node64<PERSIST, LANES>(d, k, i, lane, active, vin, update_v);
+// Forces and update of nodes [node0, node0 + BLOCK / LANES): LANES threads per
+// node compute the lane-summed bond / self-contact / contact parts, which meet
+// in shared memory; then one thread per node adds the wall forces and
+// integrates (FP64, converged warps).  Every thread of the block must call it.
+template <bool FP32, bool PERSIST, int LANES, int BLOCK>
+__device__ __forceinline__ void force_block(const DevPtrs &d, const KParams &k, int node0, int vin, int update_v) {
+    constexpr int NB = BLOCK / LANES;
+    using Sums = typename std::conditional<FP32, Sums32, Sums64>::type;
+    __shared__ Sums sm[NB];
+    const int local = threadIdx.x / LANES, lane = threadIdx.x % LANES;
+    const int i = node0 + local;
+    Sums f;
+    if constexpr (FP32) force_node32<PERSIST, LANES>(d, k, i, lane, i < k.N, vin, f);
+    else force_node64<PERSIST, LANES>(d, k, i, lane, i < k.N, vin, f);
+    if (lane == 0) sm[local] = f;
+    __syncthreads();
+    if ((int)threadIdx.x < NB && node0 + (int)threadIdx.x < k.N) {
+        if constexpr (FP32) node_epilogue32<PERSIST>(d, k, node0 + threadIdx.x, vin, update_v, sm[threadIdx.x]);
+        else node_epilogue64<PERSIST>(d, k, node0 + threadIdx.x, vin, update_v, sm[threadIdx.x]);
+    }
+    __syncthreads();
 }
 
-// Multi-kernel path: LANES threads per node over the whole grid.
+// Multi-kernel path: one block per BLOCK / LANES nodes.
 template <bool FP32, int LANES>
-__global__ void __launch_bounds__(kBlock) k_force(DevPtrs d, KParams k, int vin, int update_v) {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i = tid / LANES;
-    force_node<FP32, false, LANES>(d, k, i, tid % LANES, i < k.N, vin, update_v);
+__global__ void __launch_bounds__(kBlock, FP32 ? 5 : 4) k_force(DevPtrs d, KParams k, int vin, int update_v) {
+    force_block<FP32, false, LANES, kBlock>(d, k, blockIdx.x * (kBlock / LANES), vin, update_v);
 }
 
 template <bool FP32>
@@ -166,17 +182,11 @@ __global__ void __launch_bounds__(BLOCK) k_persistent(DevPtrs d, KParams k, int 
         if (gtid == 0) d.start[T] = k.N;
         if (!grid_barrier(d)) return;
         // D
-        for (int i = gtid; i < k.N; i += nthreads) {
-            const int pos = atomicAdd(&d.cursor[__ldcg(&d.key[i])], 1);
-            d.sorted[pos] = i;
-        }
+        for (int i = gtid; i < k.N; i += nthreads) scatter_node<true>(d, k, i);
         if (!grid_barrier(d)) return;
         // E
-        const long long total = (((long long)LANES * k.N + 31) / 32) * 32;
-        for (long long t = gtid; t < total; t += nthreads) {
-            const int i = (int)(t / LANES);
-            force_node<FP32, true, LANES>(d, k, i, (int)(t % LANES), i < k.N, vin, 1);
-        }
+        for (int node0 = blockIdx.x * (BLOCK / LANES); node0 < k.N; node0 += gridDim.x * (BLOCK / LANES))
+            force_block<FP32, true, LANES, BLOCK>(d, k, node0, vin, 1);
         for (unsigned b = gtid; b < T; b += nthreads) d.count[b] = 0;
         if (!grid_barrier(d)) return;
         vin ^= 1;
