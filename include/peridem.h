@@ -84,9 +84,9 @@ typedef struct pd_params {
     int32_t precision;      /* PD_FP64 or PD_FP32_SPLIT                         */
     int32_t store_parts;    /* nonzero: keep the four force parts of the last   */
                             /* evaluation (bond|self|neighbour|wall), for tests */
-    int32_t lanes;          /* threads per node in the force kernels: 1, 4, 8,  */
-                            /* or 0 for the default (8); 1 sums every force in  */
-                            /* the textbook order of eq:full                    */
+    int32_t lanes;          /* threads per node in the force kernels: 1, 2, 4,  */
+                            /* 8, or 0 for the default (4); 1 sums every force  */
+                            /* in the textbook order of eq:full                 */
 } pd_params;
 
 /* ---- state fields (pd_get_state / pd_set_state) ---------------------------- */
@@ -245,9 +245,11 @@ int pd_set_aggregates(pd_ctx *ctx, int n_agg, const int32_t *grain_agg, const do
 
 /*
  * Autotuner: time candidate step paths on the current state -- a graph of
- * separate kernels or one persistent cooperative kernel per 16 steps, with 4
- * or 8 threads per node (fixed when pd_params.lanes is nonzero) and 128 or 256
- * threads per block -- pick the fastest, and re-capture the step graphs.  The
+ * separate kernels or one persistent cooperative kernel per 16 steps, each with
+ * the force phase fused (4 or 8 threads per node) or split (1, 2, 4 or 8),
+ * pd_set_path modes 0-3 (threads per node fixed when pd_params.lanes is
+ * nonzero), 128 or 256 threads per persistent block -- pick the fastest, and
+ * re-capture the step graphs.  The
  * state is saved and restored around the trials, so the simulation does not
  * advance.  report (nullable, 4 doubles): path, threads per node, block, best
  * ms per step.  Different choices only reorder floating-point sums.
@@ -256,10 +258,12 @@ int pd_set_aggregates(pd_ctx *ctx, int n_agg, const int32_t *grain_agg, const do
 int pd_autotune(pd_ctx *ctx, double *report);
 
 /* Select the step path explicitly (instead of pd_autotune): mode 0 = graph of
- * separate kernels, 1 = persistent cooperative kernel; lanes 1, 4 or 8
- * threads per node (1 = textbook summation order); block 128 or 256 threads
- * (persistent kernel).  Re-captures the step graphs.  Errors: PD_ESTATE,
- * PD_EINVAL, PD_ECUDA. */
+ * separate kernels, 1 = persistent cooperative kernel, 2 and 3 = the same with
+ * the force phase split in two passes (lane sums through device memory, then
+ * walls and update one thread per node); lanes 1, 2, 4 or 8 threads per node
+ * (1 = textbook summation order); block 128 or 256 threads (persistent
+ * kernel).  The default path is mode 2 with 4 threads per node.  Re-captures
+ * the step graphs.  Errors: PD_ESTATE, PD_EINVAL, PD_ECUDA. */
 int pd_set_path(pd_ctx *ctx, int mode, int lanes, int block);
 
 /* ---- kernel timing (instrumentation) ----------------------------------------- */

@@ -197,7 +197,7 @@ struct pd_ctx {
     std::vector<double> agg_walls;       // 8 per aggregate: x_lo, x_hi, y_lo, y_hi, v(x_lo), v(x_hi), v(y_lo), v(y_hi)
     std::vector<pd::AggParams> aggp;
     // step path: 0 = graph of separate kernels, 1 = persistent cooperative kernel
-    int mode = 0, block = 128;
+    int mode = 2, block = 128;
     pd::KParams kp{};
     pd::DevPtrs d{};
     size_t arena_bytes = 0;
@@ -337,6 +337,7 @@ size_t layout(pd_ctx *c, char *base) {
     carve(base, off, d.cursor, c->T);
     carve(base, off, d.sorted, N);
     carve(base, off, d.srec, N);
+    carve(base, off, d.fsum, 6 * N * (c->prm.precision == PD_FP32_SPLIT ? 4 : 8));
     // block sums of the scan: one per scan tile (multi-kernel path) or per
     // block of the persistent kernel (at most 16 blocks per SM)
     carve(base, off, d.blocksums, std::max<size_t>(c->T / pd::kScanTile + 2, 16 * 1024));
@@ -477,7 +478,7 @@ int capture(pd_ctx *c, int vstart, int nsteps, cudaGraphExec_t *out, bool timed 
     PD_CUDA(cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal));
     int v = vstart;
     cudaError_t e = cudaSuccess;
-    if (c->mode == 1 && !c->kp.sur) {
+    if ((c->mode & 1) && !c->kp.sur) {
         e = record_persistent(c, v, nsteps, c->capture_stream, timed);
     } else {
         for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
@@ -546,8 +547,8 @@ int pd_create(pd_ctx **out, const pd_params *params, void *cuda_stream) {
     if (p.precision != PD_FP64 && p.precision != PD_FP32_SPLIT) return fail(PD_EINVAL, "unknown precision");
     if (p.micromodulus != PD_MICRO_CONSTANT && p.micromodulus != PD_MICRO_CONIC)
         return fail(PD_EINVAL, "unknown micromodulus");
-    if (p.lanes != 0 && p.lanes != 1 && p.lanes != 4 && p.lanes != 8)
-        return fail(PD_EINVAL, "lanes must be 0, 1, 4 or 8");
+    if (p.lanes != 0 && p.lanes != 1 && p.lanes != 2 && p.lanes != 4 && p.lanes != 8)
+        return fail(PD_EINVAL, "lanes must be 0, 1, 2, 4 or 8");
     pd_ctx *c = new (std::nothrow) pd_ctx();
     if (!c) return fail(PD_ENOMEM, "out of host memory");
     c->prm = p;
@@ -842,7 +843,8 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     k.n_rows = (int)c->slot_grain.size();
     k.micro = p.micromodulus;
     k.store = p.store_parts ? 1 : 0;
-    k.lanes = p.lanes == 0 ? 8 : p.lanes;
+    k.lanes = p.lanes == 0 ? 4 : p.lanes;
+    k.split = 1;          // default path: kernel graph, split force phase (pd_set_path mode 2)
     cudaStream_t s = c->stream;
     const pd::DevPtrs &d = c->d;
     size_t N = (size_t)c->N, nb = c->col.size(), G = (size_t)c->G;
@@ -1174,17 +1176,15 @@ int pd_autotune(pd_ctx *c, double *report) {
         int mode, lanes, block;
     };
     std::vector<Cand> cands;
-    const int lane_opts[2] = {4, 8};
-    for (int m = 0; m < 2; ++m)
-        for (int li = 0; li < 2; ++li) {
-            int lanes = c->prm.lanes ? c->prm.lanes : lane_opts[li];
-            if (c->prm.lanes && li == 1) continue;
-            if (m == 0) cands.push_back({0, lanes, 128});
-            else {
-                cands.push_back({1, lanes, 128});
-                cands.push_back({1, lanes, 256});
-            }
+    // fused force phase: 4 or 8 threads per node; split: 1, 2, 4 or 8
+    for (int m = 0; m < 4; ++m) {
+        const bool split = (m >> 1) != 0;
+        for (int lanes : {1, 2, 4, 8}) {
+            if (c->prm.lanes ? lanes != c->prm.lanes : (!split && lanes < 4)) continue;
+            cands.push_back({m, lanes, 128});
+            if (m & 1) cands.push_back({m, lanes, 256});
         }
+    }
     const int kTune = 8;
     cudaEvent_t e0, e1;
     PD_CUDA(cudaEventCreate(&e0));
@@ -1193,6 +1193,7 @@ int pd_autotune(pd_ctx *c, double *report) {
     Cand pick = {c->mode, c->kp.lanes, c->block};
     for (const Cand &cd : cands) {
         c->mode = cd.mode;
+        c->kp.split = cd.mode >> 1;
         c->kp.lanes = cd.lanes;
         c->block = cd.block;
         cudaGraphExec_t g = nullptr;
@@ -1223,6 +1224,7 @@ int pd_autotune(pd_ctx *c, double *report) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->mode = pick.mode;
+    c->kp.split = pick.mode >> 1;
     c->kp.lanes = pick.lanes;
     c->block = pick.block;
     if (int r = capture_all(c)) return r;
@@ -1237,9 +1239,11 @@ int pd_autotune(pd_ctx *c, double *report) {
 
 int pd_set_path(pd_ctx *c, int mode, int lanes, int block) {
     if (int r = check_ctx(c, 3)) return r;
-    if ((mode != 0 && mode != 1) || (lanes != 1 && lanes != 4 && lanes != 8) || (block != 128 && block != 256))
-        return fail(PD_EINVAL, "mode 0|1, lanes 1|4|8, block 128|256");
+    if (mode < 0 || mode > 3 || (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) ||
+        (block != 128 && block != 256))
+        return fail(PD_EINVAL, "mode 0..3, lanes 1|2|4|8, block 128|256");
     c->mode = mode;
+    c->kp.split = mode >> 1;
     c->kp.lanes = lanes;
     c->block = block;
     return capture_all(c);

@@ -49,6 +49,7 @@ struct DevPtrs {
     int *key, *count, *start, *cursor, *sorted, *blocksums;
     int2 *cell;         // hash-grid cell (x, y) of every node, written by the binning phase
     uint4 *srec;        // position of sorted[t] in bucket order: FP32 split (ph, pl), FP64 p (16 bytes)
+    void *fsum;         // split force phase: per-node lane sums, six components of N floats (FP32) or doubles
     // globals
     long long *step;
     double *t_now;      // time of the force evaluation that follows the predict phase
@@ -108,6 +109,7 @@ struct KParams {
     float guard;        // FP32-split: |(|s| - s0)| < guard * s0 re-decides breaking in FP64
     int micro, store;
     int lanes;          // threads per node in the force kernels (1, 4 or 8)
+    int split;          // 1: lane sums through global memory and a separate epilogue pass
     int fp32;           // precision of the force phase
     // surrogate
     int sur;            // surrogate on

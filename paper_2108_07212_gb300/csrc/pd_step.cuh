@@ -38,12 +38,74 @@ __global__ void __launch_bounds__(kBlock, FP32 ? 5 : 4) k_force(DevPtrs d, KPara
     force_block<FP32, false, LANES, kBlock>(d, k, blockIdx.x * (kBlock / LANES), vin, update_v);
 }
 
+// Split variant: the lane sums of node i go to global memory (structure of
+// arrays, six components) and a second pass adds walls and integrates.
+template <bool FP32, bool PERSIST, int LANES>
+__device__ __forceinline__ void sums_node(const DevPtrs &d, const KParams &k, int i, int lane, int vin) {
+    const bool active = i < k.N;
+    const size_t N = (size_t)k.N;
+    if constexpr (FP32) {
+        Sums32 f;
+        force_node32<PERSIST, LANES>(d, k, i, lane, active, vin, f);
+        if (active && lane == 0) {
+            float *o = static_cast<float *>(d.fsum);
+            o[i] = f.bx, o[N + i] = f.by, o[2 * N + i] = f.sx, o[3 * N + i] = f.sy, o[4 * N + i] = f.nx,
+            o[5 * N + i] = f.ny;
+        }
+    } else {
+        Sums64 f;
+        force_node64<PERSIST, LANES>(d, k, i, lane, active, vin, f);
+        if (active && lane == 0) {
+            double *o = static_cast<double *>(d.fsum);
+            o[i] = f.bx, o[N + i] = f.by, o[2 * N + i] = f.sx, o[3 * N + i] = f.sy, o[4 * N + i] = f.nx,
+            o[5 * N + i] = f.ny;
+        }
+    }
+}
+
+template <bool FP32, bool PERSIST>
+__device__ __forceinline__ void epilogue_node(const DevPtrs &d, const KParams &k, int i, int vin, int update_v) {
+    const size_t N = (size_t)k.N;
+    if constexpr (FP32) {
+        const float *o = static_cast<const float *>(d.fsum);
+        const Sums32 f{ldm<PERSIST>(o + i), ldm<PERSIST>(o + N + i), ldm<PERSIST>(o + 2 * N + i),
+                       ldm<PERSIST>(o + 3 * N + i), ldm<PERSIST>(o + 4 * N + i), ldm<PERSIST>(o + 5 * N + i)};
+        node_epilogue32<PERSIST>(d, k, i, vin, update_v, f);
+    } else {
+        const double *o = static_cast<const double *>(d.fsum);
+        const Sums64 f{ldm<PERSIST>(o + i), ldm<PERSIST>(o + N + i), ldm<PERSIST>(o + 2 * N + i),
+                       ldm<PERSIST>(o + 3 * N + i), ldm<PERSIST>(o + 4 * N + i), ldm<PERSIST>(o + 5 * N + i)};
+        node_epilogue64<PERSIST>(d, k, i, vin, update_v, f);
+    }
+}
+
+template <bool FP32, int LANES>
+__global__ void __launch_bounds__(kBlock, FP32 ? 6 : 4) k_sums(DevPtrs d, KParams k, int vin) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    sums_node<FP32, false, LANES>(d, k, tid / LANES, tid % LANES, vin);
+}
+
+template <bool FP32>
+__global__ void __launch_bounds__(256) k_epilogue(DevPtrs d, KParams k, int vin, int update_v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k.N) epilogue_node<FP32, false>(d, k, i, vin, update_v);
+}
+
 template <bool FP32>
 cudaError_t launch_force_impl(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s) {
     const long long threads = (long long)k.lanes * k.N;
     const unsigned grid = (unsigned)((threads + kBlock - 1) / kBlock);
+    if (k.split) {
+        if (k.lanes == 8) k_sums<FP32, 8><<<grid, kBlock, 0, s>>>(d, k, vin);
+        else if (k.lanes == 4) k_sums<FP32, 4><<<grid, kBlock, 0, s>>>(d, k, vin);
+        else if (k.lanes == 2) k_sums<FP32, 2><<<grid, kBlock, 0, s>>>(d, k, vin);
+        else k_sums<FP32, 1><<<grid, kBlock, 0, s>>>(d, k, vin);
+        k_epilogue<FP32><<<(unsigned)((k.N + 255) / 256), 256, 0, s>>>(d, k, vin, update_v);
+        return cudaGetLastError();
+    }
     if (k.lanes == 8) k_force<FP32, 8><<<grid, kBlock, 0, s>>>(d, k, vin, update_v);
     else if (k.lanes == 4) k_force<FP32, 4><<<grid, kBlock, 0, s>>>(d, k, vin, update_v);
+    else if (k.lanes == 2) k_force<FP32, 2><<<grid, kBlock, 0, s>>>(d, k, vin, update_v);
     else k_force<FP32, 1><<<grid, kBlock, 0, s>>>(d, k, vin, update_v);
     return cudaGetLastError();
 }
@@ -185,8 +247,15 @@ __global__ void __launch_bounds__(BLOCK) k_persistent(DevPtrs d, KParams k, int 
         for (int i = gtid; i < k.N; i += nthreads) scatter_node<true>(d, k, i);
         if (!grid_barrier(d)) return;
         // E
-        for (int node0 = blockIdx.x * (BLOCK / LANES); node0 < k.N; node0 += gridDim.x * (BLOCK / LANES))
-            force_block<FP32, true, LANES, BLOCK>(d, k, node0, vin, 1);
+        if (k.split) {
+            const long long total = (((long long)LANES * k.N + 31) / 32) * 32;
+            for (long long t = gtid; t < total; t += nthreads) sums_node<FP32, true, LANES>(d, k, (int)(t / LANES), (int)(t % LANES), vin);
+            if (!grid_barrier(d)) return;
+            for (int i = gtid; i < k.N; i += nthreads) epilogue_node<FP32, true>(d, k, i, vin, 1);
+        } else {
+            for (int node0 = blockIdx.x * (BLOCK / LANES); node0 < k.N; node0 += gridDim.x * (BLOCK / LANES))
+                force_block<FP32, true, LANES, BLOCK>(d, k, node0, vin, 1);
+        }
         for (unsigned b = gtid; b < T; b += nthreads) d.count[b] = 0;
         if (!grid_barrier(d)) return;
         vin ^= 1;
@@ -221,10 +290,12 @@ cudaError_t launch_persistent_impl(const DevPtrs &d, const KParams &k, int vin, 
     if (block == 256) {
         if (k.lanes == 8) return launch_persistent_cfg<FP32, 8, 256>(d, k, vin, nsteps, s);
         if (k.lanes == 4) return launch_persistent_cfg<FP32, 4, 256>(d, k, vin, nsteps, s);
+        if (k.lanes == 2) return launch_persistent_cfg<FP32, 2, 256>(d, k, vin, nsteps, s);
         return launch_persistent_cfg<FP32, 1, 256>(d, k, vin, nsteps, s);
     }
     if (k.lanes == 8) return launch_persistent_cfg<FP32, 8, 128>(d, k, vin, nsteps, s);
     if (k.lanes == 4) return launch_persistent_cfg<FP32, 4, 128>(d, k, vin, nsteps, s);
+    if (k.lanes == 2) return launch_persistent_cfg<FP32, 2, 128>(d, k, vin, nsteps, s);
     return launch_persistent_cfg<FP32, 1, 128>(d, k, vin, nsteps, s);
 }
 

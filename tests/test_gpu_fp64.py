@@ -237,11 +237,11 @@ def test_nonfinite_state_is_reported_not_faulted():
     assert st[2] > 0
 
 
-@pytest.mark.parametrize("lanes", [1, 4])
+@pytest.mark.parametrize("lanes", [1, 2, 4])
 def test_lane_split_matches_textbook_order(lanes):
-    """lanes = 1 sums every force in the oracle's order; 4 and the default 8
-    only reorder the sums: same broken bonds, displacements within the
-    trajectory tolerance (a fracturing impact amplifies round-off)."""
+    """lanes = 1 sums every force in the oracle's order; 2, 4 and 8 only
+    reorder the sums: same broken bonds, displacements within the trajectory
+    tolerance (a fracturing impact amplifies round-off)."""
     w = _contact_disks(Gc=0.5)
     w.grain_geom[1, 5] = -6.0
     a = _gpu(w, store=False, lanes=lanes)
