@@ -34,10 +34,27 @@ BYTES_PER_NODE_FP32 = 116
 BYTES_PER_BOND_FP32 = 4
 
 
+WORKLOADS = {
+    # name: (generator, default seed, description)
+    "settling50": ("settling", 1, "settling of 50 mixed-shape grains (disk/hexagon/triangle/drop/annulus/plus), "
+                                  "R~U[1,1.5] mm, h=R/15, dt=5e-8 s, box 20x30 mm, gravity 5000 m/s^2"),
+    "compaction500": ("compaction", 3, "compaction of 500 mixed-shape grains, R~U[0.8,1.6] mm, h=R/23, box width "
+                                       "40 mm, top wall 0.1 m/s, dt=2e-8 s"),
+    "ensemble64": ("ensemble", 11, "64 independent settling aggregates of 20-200 grains, R~U[0.8,1.2] mm, h=R/21, "
+                                   "dt=2e-8 s, own wall box each"),
+    "surrogate2000": ("surrogate_settling", 5, "settling of 2000 mixed-shape grains, R~U[1,1.5] mm, h=R/23, "
+                                               "dt=2.5e-8 s, gravity 5000 m/s^2 (plain FP32 path)"),
+}
+
+
 def workload_for(rank: int, args):
-    """Rank r runs its own seeded aggregate (seed 1 + r): independent problems."""
+    """Rank r runs its own seeded aggregate (default seed + r): independent problems."""
     from paper_2108_07212_gb300 import inputs as I
-    return I.settling(n_grains=50, seed=1 + rank)
+    name = getattr(args, "workload", None) or "settling50"
+    gen, seed, _ = WORKLOADS[name]
+    if gen == "settling":
+        return I.settling(n_grains=50, seed=seed + rank)
+    return getattr(I, gen)(seed=seed + rank)
 
 
 def max_over_ranks(dist, values, device):
@@ -51,9 +68,9 @@ def max_over_ranks(dist, values, device):
     return [float(x) for x in t.tolist()]
 
 
-def describe(w, sim=None):
-    d = {"workload": f"settling of {w.n_grains} mixed-shape grains (disk/hexagon/triangle/drop/annulus/plus), "
-                     f"R~U[1,1.5] mm, h=R/15, dt={w.params['dt']:g} s, box 20x30 mm, gravity 5000 m/s^2"}
+def describe(w, sim=None, args=None):
+    name = getattr(args, "workload", None) or "settling50"
+    d = {"workload": WORKLOADS[name][2], "name": name}
     if sim is not None:
         d.update(nodes=int(sim.N), directed_bonds=int(sim.n_bonds))
     return d
@@ -178,7 +195,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "node-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": describe(w) | {"nodes": int(P.N), "directed_bonds": int(len(P.col))},
+            "config": describe(w, None, args) | {"nodes": int(P.N), "directed_bonds": int(len(P.col))},
             "cpu_baseline": {"value": value, "unit": "node-steps/s", "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} time steps after {args.warmup} warm-up steps"},
             "e2e": {"value": value, "unit": "node-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -243,6 +260,55 @@ def precision_report(B, dev, stream, torch):
 # algorithmic bytes of one whole FP32-split time step per node (predict 80 B,
 # hash binning ~40 B incl. the bucket scan, force kernel 116 B) + 4 B per bond
 BYTES_PER_NODE_STEP_FP32 = 236
+
+
+# DRAM bytes (read + write) per launch of the force-phase kernels on the
+# settling50 workload, from one ncu capture of
+#   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -c 3000
+#       --csv python bench.py --steps 20 --warmup 3 --legs= --no-cpu
+# (ncu flushes caches before every launch, as the bench flushes L2 before every
+# step; medians over the launches; profiles/traffic_settling50.md).  They hold
+# while the kernel sources hash to TRAFFIC_DIGEST; otherwise traffic is null.
+TRAFFIC_SETTLING50 = {
+    "k_epilogue<0>": 2363136,
+    "k_epilogue<1>": 1566720,
+    "k_force<0, 4>": 7299840,
+    "k_force<0, 8>": 7300992,
+    "k_force<1, 4>": 3966208,
+    "k_force<1, 8>": 3966464,
+    "k_sums<0, 1>": 6641408,
+    "k_sums<0, 2>": 6654592,
+    "k_sums<0, 4>": 6652672,
+    "k_sums<0, 8>": 6651776,
+    "k_sums<1, 1>": 3146752,
+    "k_sums<1, 2>": 3156096,
+    "k_sums<1, 4>": 3153152,
+    "k_sums<1, 8>": 3152000,
+}
+TRAFFIC_DIGEST = "b3ce2e9b4bc361a509a7a4de04a911056aa030c4"
+TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu", "pd_common.cu", "pd_internal.h")
+
+
+def kernel_digest() -> str:
+    import hashlib
+    hsh = hashlib.sha1()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2108_07212_gb300", "csrc", f), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()
+
+
+def force_phase_traffic(path: dict, fp32: bool, workload: str):
+    """Measured DRAM bytes of one force phase of the chosen path, or None."""
+    if workload != "settling50" or not TRAFFIC_SETTLING50 or kernel_digest() != TRAFFIC_DIGEST:
+        return None
+    p, m, l = ("1" if fp32 else "0"), path["mode"], path["lanes"]
+    if m & 1:
+        return None                      # the persistent kernel's phases are not separable
+    names = [f"k_sums<{p}, {l}>", f"k_epilogue<{p}>"] if m >> 1 else [f"k_force<{p}, {l}>"]
+    if not all(n in TRAFFIC_SETTLING50 for n in names):
+        return None
+    return float(sum(TRAFFIC_SETTLING50[n] for n in names))
 
 
 def _force_kernels(mode: int, fp32: bool) -> str:
@@ -479,10 +545,18 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         sim = B.Simulation(w, precision=prec, device=dev, stream=stream)
         sim64 = B.Simulation(w, precision=B.PD_FP64, device=dev, stream=stream) if prec != B.PD_FP64 else None
-    # both paths run the step variant their own autotuner picks (state unchanged)
-    tuned = {"fp32" if prec != B.PD_FP64 else "fp64": sim.autotune()}
+    # both paths run the step variant their own autotuner picks (state unchanged),
+    # unless --path fixes it
+    def pick(x):
+        if args.path:
+            v = [int(t) for t in args.path.split(",")]
+            x.set_path(v[0], v[1], v[2] if len(v) > 2 else 128)
+            inf = x.info()
+            return {"mode": int(inf["mode"]), "lanes": int(inf["lanes"]), "block": int(inf["block"]), "fixed": True}
+        return x.autotune()
+    tuned = {"fp32" if prec != B.PD_FP64 else "fp64": pick(sim)}
     if sim64 is not None:
-        tuned["fp64"] = sim64.autotune()
+        tuned["fp64"] = pick(sim64)
     flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
     def flush_l2():
@@ -538,7 +612,7 @@ def run_ours(args):
         achieved = flops / (f_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": _force_kernels(tuned["fp64"]["mode"], False), "achieved": achieved,
                 "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None,
+                "frac": achieved / fp64_peak, "traffic": force_phase_traffic(tuned["fp64"], False, args.workload),
                 "note": f"{FLOPS_PER_BOND} algorithmic FP64 ops per directed bond x {sim.n_bonds} bonds per launch / "
                         f"mean CUDA-event duration {f_ms * 1e3:.1f} us; peak = measured cuBLAS DGEMM (of measured)"}
     else:
@@ -547,17 +621,18 @@ def run_ours(args):
         hbm = float(peaks.get("hbm_gbs") or 6800.0)
         roof = {"bound": "hbm", "kernel": _force_kernels(tuned["fp32"]["mode"], True), "achieved": achieved, "peak": hbm,
                 "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None,
+                "frac": achieved / hbm, "traffic": force_phase_traffic(tuned["fp32"], True, args.workload),
                 "note": f"{BYTES_PER_NODE_FP32} B per node + {BYTES_PER_BOND_FP32} B per directed bond (algorithmic) x "
                         f"{sim.N} nodes / {sim.n_bonds} bonds per force phase / mean CUDA-event duration of the "
-                        f"force phase {f_ms * 1e3:.1f} us; peak = measured copy bandwidth (of measured); the "
-                        "20k-node workload is too small to load 152 SMs, so the phase is latency-bound"}
+                        f"force phase {f_ms * 1e3:.1f} us; peak = measured copy bandwidth (of measured)"
+                        + ("; the 20k-node workload is too small to load 152 SMs, so the phase is latency-bound"
+                           if sim.N < 100000 else "")}
     line = {
         "metric": METRIC, "value": value, "unit": "node-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == B.PD_FP64 else "f32+f64",
         "data": "synthetic",
-        "config": describe(w, sim) | {"precision": "fp64" if prec == B.PD_FP64 else "fp32 split (FP32 forces, FP64 integration)",
+        "config": describe(w, sim, args) | {"precision": "fp64" if prec == B.PD_FP64 else "fp32 split (FP32 forces, FP64 integration)",
                                       "l2": "flushed (256 MB write) before every timed step",
                                       "ranks": "independent seeded aggregates per rank",
                                       "step_path": tuned},
@@ -610,6 +685,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--legs", default="compaction,ensemble,surrogate",
                     help="comma-separated large-workload legs at N=1 ('' for none)")
+    ap.add_argument("--workload", default="settling50", choices=sorted(WORKLOADS),
+                    help="workload of the main line (settling50 is the benchmark configuration)")
+    ap.add_argument("--path", default="", help="fix the step path: MODE,LANES[,BLOCK] (pd_set_path) instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

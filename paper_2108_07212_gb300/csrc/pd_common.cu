@@ -16,6 +16,7 @@ __global__ void __launch_bounds__(kBlock) k_predict(DevPtrs d, KParams k, int vi
         long long st = *d.step + (advance ? 1 : 0);
         *d.t_now = (double)st * k.dt;
         if (advance) *d.step = st;
+        wall_cells(d, k, (double)st * k.dt);
     }
     if (i >= k.N) return;
     predict_node<false>(d, k, i, vin, advance);

@@ -284,6 +284,26 @@ __device__ __forceinline__ void predict_node(const DevPtrs &d, const KParams &k,
     atomicAdd(&d.count[b], 1);
 }
 
+// Hash-grid cells of the four walls of every aggregate at time t (written once
+// per force evaluation by one thread): a node two or more cells away from all
+// of them is farther than R_c from every wall and feels no wall force.
+__device__ __forceinline__ void wall_cells(const DevPtrs &d, const KParams &k, double t) {
+    for (int a = 0; a < k.n_agg; ++a) {
+        const AggParams &A = d.agg[a];
+        d.wall_cell[a] = make_int4(cell_coord(A.w0[0] + A.wv[0] * t, A.ox, A.inv_cell),
+                                   cell_coord(A.w0[1] + A.wv[1] * t, A.ox, A.inv_cell),
+                                   cell_coord(A.w0[2] + A.wv[2] * t, A.oy, A.inv_cell),
+                                   cell_coord(A.w0[3] + A.wv[3] * t, A.oy, A.inv_cell));
+    }
+}
+
+template <bool PERSIST>
+__device__ __forceinline__ bool far_from_walls(const DevPtrs &d, int i, int ag) {
+    const int2 c = ldm<PERSIST>(&d.cell[i]);
+    const int4 w = ldm<PERSIST>(&d.wall_cell[ag]);
+    return c.x - w.x >= 2 && w.y - c.x >= 2 && c.y - w.z >= 2 && w.w - c.y >= 2;
+}
+
 // Counting-sort scatter of node i into its bucket, with its position record.
 template <bool PERSIST>
 __device__ __forceinline__ void scatter_node(const DevPtrs &d, const KParams &k, int i) {
@@ -356,14 +376,22 @@ __device__ __forceinline__ bool bonded_intact(const DevPtrs &d, const KParams &k
 
 // Acceleration and velocity update of node i (Algorithm 1) plus the optional
 // per-part force output; run by one lane per node.
-template <bool PERSIST>
+template <bool PERSIST, bool RECIP = false>
 __device__ __forceinline__ void finish_node(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
                                             double2 vi, double Vi, double Fbx, double Fby, double Fsx, double Fsy,
-                                            double Fnx, double Fny, double Fwx, double Fwy) {
+                                            double Fnx, double Fny, double Fwx, double Fwy, double inv_m = 0.0) {
     const double Fx = __dadd_rn(__dadd_rn(__dadd_rn(Fbx, Fsx), Fnx), Fwx);
     const double Fy = __dadd_rn(__dadd_rn(__dadd_rn(Fby, Fsy), Fny), Fwy);
-    const double m = __dmul_rn(k.rho, Vi);
-    const double ax = __dadd_rn(__ddiv_rn(Fx, m), k.gx), ay = __dadd_rn(__ddiv_rn(Fy, m), k.gy);
+    double ax, ay;
+    if constexpr (RECIP) {
+        // FP32-split path: F / m as F * (1 / m) (one rounding more, far below the FP32 force error)
+        ax = __dadd_rn(__dmul_rn(Fx, inv_m), k.gx);
+        ay = __dadd_rn(__dmul_rn(Fy, inv_m), k.gy);
+    } else {
+        const double m = __dmul_rn(k.rho, Vi);
+        ax = __dadd_rn(__ddiv_rn(Fx, m), k.gx);
+        ay = __dadd_rn(__ddiv_rn(Fy, m), k.gy);
+    }
     if (update_v) {
         const double2 ao = ldm<PERSIST>(&d.a[i]);
         double2 vn;
@@ -503,9 +531,10 @@ __device__ __forceinline__ void node_epilogue64(const DevPtrs &d, const KParams 
     const double2 pi = ldm<PERSIST>(&d.p[i]);
     const double2 vi = ldm<PERSIST>(&d.v[vin][i]);
     const double Vi = __ldg(&d.V[i]);
-    const AggParams &A = d.agg[__ldg(&d.g_agg[__ldg(&d.grain[i])])];
-    double Fwx, Fwy;
-    wall_force64(k, A, ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, Vi, Fwx, Fwy, d.status);
+    const int ag = __ldg(&d.g_agg[__ldg(&d.grain[i])]);
+    double Fwx = 0.0, Fwy = 0.0;
+    if (!far_from_walls<PERSIST>(d, i, ag))
+        wall_force64(k, d.agg[ag], ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, Vi, Fwx, Fwy, d.status);
     finish_node<PERSIST>(d, k, i, vin, update_v, vi, Vi, f.bx, f.by, f.sx, f.sy, f.nx, f.ny, Fwx, Fwy);
 }
 
@@ -692,14 +721,17 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
 template <bool PERSIST>
 __device__ __forceinline__ void node_epilogue32(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
                                                 const Sums32 &f) {
-    const double2 pi = ldm<PERSIST>(&d.p[i]);
     const double2 vi = ldm<PERSIST>(&d.v[vin][i]);
     const double Vi = __ldg(&d.V[i]);
-    const AggParams &A = d.agg[__ldg(&d.g_agg[__ldg(&d.grain[i])])];
-    double Fwx, Fwy;
-    wall_force64(k, A, ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, Vi, Fwx, Fwy, d.status);
-    finish_node<PERSIST>(d, k, i, vin, update_v, vi, Vi, (double)f.bx, (double)f.by, (double)f.sx, (double)f.sy,
-                         (double)f.nx, (double)f.ny, Fwx, Fwy);
+    const int gi = __ldg(&d.grain[i]);
+    const int ag = __ldg(&d.g_agg[gi]);
+    double Fwx = 0.0, Fwy = 0.0;
+    if (!far_from_walls<PERSIST>(d, i, ag)) {
+        const double2 pi = ldm<PERSIST>(&d.p[i]);
+        wall_force64(k, d.agg[ag], ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, Vi, Fwx, Fwy, d.status);
+    }
+    finish_node<PERSIST, true>(d, k, i, vin, update_v, vi, Vi, (double)f.bx, (double)f.by, (double)f.sx,
+                               (double)f.sy, (double)f.nx, (double)f.ny, Fwx, Fwy, __ldg(&d.g_invm[gi]));
 }
 
 }  // namespace pd

@@ -332,6 +332,7 @@ size_t layout(pd_ctx *c, char *base) {
     carve(base, off, d.agg, (size_t)c->n_agg);
     carve(base, off, d.key, N);
     carve(base, off, d.cell, N);
+    carve(base, off, d.wall_cell, (size_t)c->n_agg);
     carve(base, off, d.count, c->T);
     carve(base, off, d.start, (size_t)c->T + 1);
     carve(base, off, d.cursor, c->T);
@@ -355,12 +356,14 @@ size_t layout(pd_ctx *c, char *base) {
         carve(base, off, d.vh, N);
         carve(base, off, d.vl, N);
         carve(base, off, d.gc, G);
+        carve(base, off, d.g_invm, G);
     } else {
         d.lat = nullptr;
         d.gq = nullptr;
         d.ph = d.pl = nullptr;
         d.vh = d.vl = nullptr;
         d.gc = nullptr;
+        d.g_invm = nullptr;
     }
     carve(base, off, d.bu, N);
     carve(base, off, d.bv, N);
@@ -391,7 +394,7 @@ size_t layout(pd_ctx *c, char *base) {
         carve(base, off, d.mlp_err, 1);
         carve(base, off, d.sur_lambda, T * M);
         carve(base, off, d.g_theta, G);
-        carve(base, off, d.g_xbar, G);
+        carve(base, off, d.sur_fc, G);
         carve(base, off, d.sur_active, G);
         carve(base, off, d.sur_rot, G);
         carve(base, off, d.sur_phi, G);
@@ -414,7 +417,7 @@ size_t layout(pd_ctx *c, char *base) {
         d.mlp_err = nullptr;
         d.basis = d.sur_x = d.sur_y = d.sur_err = d.sur_maxs = d.sur_qs = d.sur_fs = d.sur_lambda = nullptr;
         d.g_theta = d.sur_phi = nullptr;
-        d.g_xbar = nullptr;
+        d.sur_fc = nullptr;
         d.sur_rot = d.sur_fb = nullptr;
     }
     return off;
@@ -871,7 +874,7 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     PD_CUDA(cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), s));
     PD_CUDA(cudaMemsetAsync(d.t_now, 0, sizeof(double), s));
     std::vector<int32_t> gstart32, tnode, tslot;
-    std::vector<double> xbar;
+    std::vector<float> fc;
     if (c->sur_cfg) {
         gstart32.assign(c->g_start.begin(), c->g_start.end());
         tnode.assign(c->n_tmpl + 1, 0);
@@ -880,16 +883,20 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
             tnode[t + 1] = tnode[t] + c->tmpl_nodes[t];
             tslot[t + 1] = tslot[t] + c->tmpl_count[t];
         }
-        xbar.assign(2 * G, 0.0);
+        // per grain: h as a float-float pair and the centroid of its lattice indices
+        fc.assign(4 * G, 0.f);
         for (size_t g = 0; g < G; ++g) {
-            double sx = 0, sy = 0;
+            double si = 0, sj = 0;
             for (int64_t x = c->g_start[g]; x < c->g_start[g + 1]; ++x) {
-                sx += c->X[2 * x];
-                sy += c->X[2 * x + 1];
+                si += c->lat[2 * x];
+                sj += c->lat[2 * x + 1];
             }
             const double n = (double)(c->g_start[g + 1] - c->g_start[g]);
-            xbar[2 * g] = sx / n;
-            xbar[2 * g + 1] = sy / n;
+            const float hh = (float)c->g_h[g];
+            fc[4 * g] = hh;
+            fc[4 * g + 1] = (float)(c->g_h[g] - (double)hh);
+            fc[4 * g + 2] = (float)(si / n);
+            fc[4 * g + 3] = (float)(sj / n);
         }
         PD_CUDA(cudaMemcpyAsync(d.g_start, gstart32.data(), 4 * (G + 1), cudaMemcpyHostToDevice, s));
         PD_CUDA(cudaMemcpyAsync(d.g_tmpl, c->g_tmpl.data(), 4 * G, cudaMemcpyHostToDevice, s));
@@ -917,7 +924,7 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
         PD_CUDA(cudaMemsetAsync(d.mlp_err, 0, sizeof(int), s));
         PD_CUDA(cudaMemcpyAsync(d.sur_lambda, c->sur_lambda.data(), 4 * c->sur_lambda.size(), cudaMemcpyHostToDevice, s));
         PD_CUDA(cudaMemcpyAsync(d.g_theta, c->g_theta.data(), 8 * G, cudaMemcpyHostToDevice, s));
-        PD_CUDA(cudaMemcpyAsync(d.g_xbar, xbar.data(), 16 * G, cudaMemcpyHostToDevice, s));
+        PD_CUDA(cudaMemcpyAsync(d.sur_fc, fc.data(), 16 * G, cudaMemcpyHostToDevice, s));
         PD_CUDA(cudaMemsetAsync(d.sur_active, 0, 4 * G, s));
         PD_CUDA(cudaMemsetAsync(d.sur_y, 0, 4 * G * c->sur_modes, s));
         PD_CUDA(cudaMemsetAsync(d.sur_err, 0, 4 * G, s));
@@ -927,6 +934,7 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     PD_CUDA(cudaMemsetAsync(d.step, 0, 8, s));
     PD_CUDA(cudaMemsetAsync(d.status, 0, 4 * PD_STATUS_COUNT, s));
     std::vector<float> gq, gcf;
+    std::vector<double> invm;
     if (p.precision == PD_FP32_SPLIT) {
         // per grain: h, h^2 as a float-float pair, V as float
         gq.resize(4 * G);
@@ -948,6 +956,9 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
             gcf[4 * g + 3] = 0.f;
         }
         PD_CUDA(cudaMemcpyAsync(d.gc, gcf.data(), 16 * G, cudaMemcpyHostToDevice, s));
+        invm.resize(G);
+        for (size_t g = 0; g < G; ++g) invm[g] = 1.0 / (p.rho * c->V[c->g_start[g]]);
+        PD_CUDA(cudaMemcpyAsync(d.g_invm, invm.data(), 8 * G, cudaMemcpyHostToDevice, s));
     }
     c->vcur = 0;
     c->steps_done = 0;

@@ -63,6 +63,8 @@ struct DevPtrs {
     float2 *ph, *pl;    // shifted position (p + shift) as a float-float pair
     float2 *vh, *vl;    // start-of-step velocity as a float-float pair
     float4 *gc;         // per grain: (c_w, s0, eps, 0) as floats
+    double *g_invm;     // per grain: 1 / (rho V)
+    int4 *wall_cell;    // per aggregate: hash-grid cells of its walls x_lo, x_hi, y_lo, y_hi at the current time
     // autotuner backup of the state
     double2 *bu, *bv, *ba;
     uint32_t *bbits;
@@ -86,7 +88,7 @@ struct DevPtrs {
     int4 *mlp_work;     // inference tiles: (template, first row, end row, 0)
     int *mlp_err;       // set when a network tile's tensor-core wait gave up
     double *g_theta;    // grain orientation at meshing
-    double2 *g_xbar;    // reference centroid of every grain
+    float4 *sur_fc;     // per grain: h as a float-float pair (hi, lo), centroid of its lattice indices (i, j)
     int *sur_active;    // 1 while the grain is advanced by the surrogate
     float2 *sur_rot;    // cos, sin of (theta + phi): lattice frame -> world
     double *sur_phi;    // co-rotation angle phi of the current step

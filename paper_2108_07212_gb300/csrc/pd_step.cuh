@@ -218,6 +218,7 @@ __global__ void __launch_bounds__(BLOCK) k_persistent(DevPtrs d, KParams k, int 
             const long long s = *d.step + 1;
             *d.step = s;
             *d.t_now = (double)s * k.dt;
+            wall_cells(d, k, (double)s * k.dt);
         }
         for (int i = gtid; i < k.N; i += nthreads) predict_node<true>(d, k, i, vin, 1);
         if (!grid_barrier(d)) return;

@@ -80,48 +80,108 @@ __device__ __forceinline__ int tmpl_rows_pad(const DevPtrs &d, int t) { return d
 // ---------------------------------------------------------------------------
 // co-rotated frame and local deformation
 
+__device__ __forceinline__ float block_sum_f(float v, float *sm) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[warp] = v;
+    __syncthreads();
+    float t = 0.f;
+    for (int w = 0; w < kSurThreads / 32; ++w) t += sm[w];
+    return t;
+}
+
+// (ah + al) * (bh + bl) as a float-float pair (the al * bl term is below the pair's precision).
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float &ph, float &pl) {
+    float e;
+    two_prod(ah, bh, ph, e);
+    pl = e + (ah * bl + al * bh);
+}
+
 // Co-rotated frame of grain blockIdx.x and its local deformation w / h per node
 // (into sur_w).  Grains without a template, or not active (unless
 // all_templated), are skipped.
+//
+// Everything runs on the FP32 pipe.  The frame (centroid c, rotation phi)
+// needs no more than float accuracy: an error in it adds a rigid translation
+// or rotation to w, and the basis, orthogonal to the rigid modes, projects it
+// out.  The deformation itself is a small difference of two quantities of the
+// size of the grain, so positions relative to the grain's first node are
+// float-float pairs (exact high-part differences of the shifted positions
+// plus the low parts), and the rotation R(-theta - phi) and the reference
+// offset h (lattice index - lattice centroid) are applied in float-float.
 __global__ void __launch_bounds__(kSurThreads) k_sur_frame(DevPtrs d, KParams k, int all_templated) {
-    __shared__ double smd[kSurThreads / 32];
+    __shared__ float smf[kSurThreads / 32];
+    __shared__ float frame[6];
     const int g = blockIdx.x;
     const int t = d.g_tmpl[g];
     if (t < 0 || (!all_templated && !d.sur_active[g])) return;
     const int s0 = d.g_start[g], s1 = d.g_start[g + 1], n = s1 - s0;
-    const double2 xb = d.g_xbar[g];
-    // one pass: centroid of the current positions and the best-fit rotation
-    // sums sum X' . p, sum X' x p (sum X' = 0, so p need not be centred)
-    double sx = 0.0, sy = 0.0, sdot = 0.0, scross = 0.0;
+    const float4 fc = d.sur_fc[g];                 // (h hi, h lo, lattice centroid i, j)
+    const float2 ph0 = d.ph[s0], pl0 = d.pl[s0];
+    // one pass: centroid and the best-fit rotation sums in the lattice frame,
+    // A = sum l . d, B = sum l x d (l: centred lattice index, d = p - p_first)
+    float sx = 0.f, sy = 0.f, sa = 0.f, sb = 0.f;
     for (int i = s0 + threadIdx.x; i < s1; i += kSurThreads) {
-        const double2 p = d.p[i], X = d.X[i];
-        const double rx = X.x - xb.x, ry = X.y - xb.y;
-        sx += p.x;
-        sy += p.y;
-        sdot += rx * p.x + ry * p.y;
-        scross += rx * p.y - ry * p.x;
+        const float2 ph = d.ph[i], pl = d.pl[i];
+        const int2 li = d.lat[i];
+        const float dx = __fsub_rn(ph.x, ph0.x) + (pl.x - pl0.x), dy = __fsub_rn(ph.y, ph0.y) + (pl.y - pl0.y);
+        const float lx = (float)li.x - fc.z, ly = (float)li.y - fc.w;
+        sx += dx;
+        sy += dy;
+        sa += lx * dx + ly * dy;
+        sb += lx * dy - ly * dx;
     }
-    const double cx = block_sum_d(sx, smd) / n;
-    const double cy = block_sum_d(sy, smd) / n;
-    const double Sd = block_sum_d(sdot, smd);
-    const double Sc = block_sum_d(scross, smd);
-    const double phi = atan2(Sc, Sd);
-    const double th = d.g_theta[g];
-    double sp, cp, st, ct, sr, cr;
-    sincos(phi, &sp, &cp);
-    sincos(th, &st, &ct);
-    sincos(th + phi, &sr, &cr);
+    const float Sx = block_sum_f(sx, smf), Sy = block_sum_f(sy, smf);
+    const float A = block_sum_f(sa, smf), Bs = block_sum_f(sb, smf);
     if (threadIdx.x == 0) {
+        // reference offsets X' = R(theta) h l: sum X' . p' = cos A + sin B, sum X' x p' = cos B - sin A
+        const double th = d.g_theta[g];
+        double st, ct;
+        sincos(th, &st, &ct);
+        const double phi = atan2(ct * Bs - st * A, ct * A + st * Bs);
+        double sr, cr;
+        sincos(th + phi, &sr, &cr);
         d.sur_phi[g] = phi;
         d.sur_rot[g] = make_float2((float)cr, (float)sr);
+        const float ch = (float)cr, sh = (float)sr;
+        frame[0] = ch;
+        frame[1] = (float)(cr - (double)ch);
+        frame[2] = sh;
+        frame[3] = (float)(sr - (double)sh);
+        frame[4] = Sx / (float)n;                  // centroid, relative to the first node
+        frame[5] = Sy / (float)n;
     }
-    const double hinv = 1.0 / (double)__ldg(&d.gq[__ldg(&d.grain[s0])]).x;
+    __syncthreads();
+    const float ch = frame[0], cl = frame[1], sh = frame[2], sl = frame[3], cx = frame[4], cy = frame[5];
+    const float hinv = 1.0f / fc.x;
     for (int i = s0 + threadIdx.x; i < s1; i += kSurThreads) {
-        const double2 p = d.p[i], X = d.X[i];
-        const double px = p.x - cx, py = p.y - cy, rx = X.x - xb.x, ry = X.y - xb.y;
-        // R(-phi) p' - X'  (world orientation), then R(-theta) to the lattice frame
-        const double ux = (cp * px + sp * py) - rx, uy = (-sp * px + cp * py) - ry;
-        d.sur_w[i] = make_float2((float)((ct * ux + st * uy) * hinv), (float)((-st * ux + ct * uy) * hinv));
+        const float2 ph = d.ph[i], pl = d.pl[i];
+        const int2 li = d.lat[i];
+        // e = p - c as float-float pairs
+        float exh, exe, eyh, eye;
+        two_sum(__fsub_rn(ph.x, ph0.x), -cx, exh, exe);
+        two_sum(__fsub_rn(ph.y, ph0.y), -cy, eyh, eye);
+        const float exl = exe + (pl.x - pl0.x), eyl = eye + (pl.y - pl0.y);
+        // u = R(-theta - phi) e
+        float p1h, p1l, p2h, p2l, q1h, q1l, q2h, q2l;
+        ff_mul(ch, cl, exh, exl, p1h, p1l);        // c ex
+        ff_mul(sh, sl, eyh, eyl, p2h, p2l);        // s ey
+        ff_mul(sh, sl, exh, exl, q1h, q1l);        // s ex
+        ff_mul(ch, cl, eyh, eyl, q2h, q2l);        // c ey
+        float uxh, uxe, uyh, uye;
+        two_sum(p1h, p2h, uxh, uxe);
+        two_sum(q2h, -q1h, uyh, uye);
+        const float uxl = uxe + (p1l + p2l), uyl = uye + (q2l - q1l);
+        // reference offset h l as float-float pairs
+        const float lx = (float)li.x - fc.z, ly = (float)li.y - fc.w;
+        float rxh, rxe, ryh, rye;
+        two_prod(fc.x, lx, rxh, rxe);
+        two_prod(fc.x, ly, ryh, rye);
+        const float rxl = rxe + fc.y * lx, ryl = rye + fc.y * ly;
+        const float wx = __fsub_rn(uxh, rxh) + (uxl - rxl), wy = __fsub_rn(uyh, ryh) + (uyl - ryl);
+        d.sur_w[i] = make_float2(wx * hinv, wy * hinv);
     }
 }
 
