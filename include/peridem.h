@@ -365,6 +365,27 @@ int pd_surrogate_stats(pd_ctx *ctx, int32_t *active_host, float *err_host, float
  * surrogate enabled; waits. */
 int pd_surrogate_inspect(pd_ctx *ctx, float *q_host, float *y_host);
 
+/* ---- observables of the settling and compaction sections (Sec. 6) ---------- */
+#define PD_OBS_PHI 0            /* volume fraction: particle volume / container area      */
+#define PD_OBS_BULK_DAMAGE 1    /* bulk damage: mean particle damage of the aggregate     */
+#define PD_OBS_FORCE_TOP 2      /* y force the aggregate exerts on its top wall (y_hi)    */
+#define PD_OBS_FORCE_BOTTOM 3   /* y force the aggregate exerts on its bottom wall (y_lo) */
+#define PD_OBS_COUNT 4
+
+/*
+ * Per aggregate a, out[PD_OBS_COUNT * a + PD_OBS_*] (host, n_agg x 4 doubles)
+ * at the current state and time t = step dt.  Volume fraction phi(t) = sum of
+ * the node volumes / ((x_hi - x_lo)(y_hi - y_lo)) with the walls at time t
+ * (the compaction section's sum V_i / (l (h - v t))).  Particle damage is the
+ * mean over a grain's nodes of the node damage (broken / reference bonds,
+ * Sec. 3.1); bulk damage is the mean particle damage over the aggregate's
+ * grains.  The force on a wall is minus the sum over nodes of that wall's
+ * force on them (eq:wall-total): its own segment term less half of each
+ * corner term it shares with a neighbouring wall.  Runs on the caller's stream
+ * and waits.  Errors: PD_ESTATE, PD_EINVAL, PD_ECUDA.
+ */
+int pd_observables(pd_ctx *ctx, double *out_host);
+
 /* ---- diagnostics without device allocation ---------------------------------- */
 #define PD_NOALLOC_MAX_NODES 2097152
 

@@ -70,6 +70,7 @@ def lib():
             L.or_run.argtypes = [dp, c_l, c_i, c_i, dp, dp, dp, dp, dp, ip, dp, dp, dp, ip, ip, up, dp, dp, ip]
             L.or_init_accel.argtypes = [dp, c_d, c_i, dp, dp, dp, dp, dp, ip, dp, dp, dp, ip, ip, up, ip]
             L.or_diagnostics.argtypes = [dp, c_i, dp, dp, dp, dp, ip, dp, dp, ip, ip, up, dp]
+            L.or_wall_sums.argtypes = [dp, c_d, c_i, dp, dp, dp, dp, dp]
             _lib = L
     return _lib
 
@@ -300,3 +301,43 @@ class OracleProblem:
         csum = np.concatenate([[0], np.cumsum(self.broken.astype(np.int64))])
         br = csum[self.row_ptr[1:]] - csum[self.row_ptr[:-1]]
         return np.where(cnt > 0, br / np.maximum(cnt, 1), 0.0)
+
+    # -- observables of the settling and compaction sections (Sec. 6) -------
+    def walls(self, t=None):
+        """Wall positions x_lo, x_hi, y_lo, y_hi at time t (default: now)."""
+        if t is None:
+            t = self.step * self.prm[P_DT]
+        return np.array([self.prm[P_WX0 + l] + self.prm[P_VX0 + l] * t for l in range(4)])
+
+    def volume_fraction(self, t=None):
+        """phi(t) = sum of particle volumes / (container width x height)."""
+        w = self.walls(t)
+        return float(self.V.sum() / ((w[1] - w[0]) * (w[3] - w[2])))
+
+    def particle_damage(self):
+        """Mean node damage of every grain."""
+        dmg = self.damage()
+        G = int(self.grain.max()) + 1
+        return np.bincount(self.grain, weights=dmg, minlength=G) / np.bincount(self.grain, minlength=G)
+
+    def bulk_damage(self):
+        """Average particle damage over all particles."""
+        return float(self.particle_damage().mean())
+
+    def wall_sums(self, t=None):
+        """Sums over nodes of each wall's own term (4 x 2) and of the corner
+        terms (4 x 2) that eq:wall-total subtracts."""
+        if t is None:
+            t = self.step * self.prm[P_DT]
+        out = np.zeros(16)
+        lib().or_wall_sums(_dp(self.prm), t, self.N, _dp(self.X), _dp(self.u), _dp(self.v), _dp(self.V), _dp(out))
+        return out[:8].reshape(4, 2), out[8:].reshape(4, 2)
+
+    def wall_reaction(self, wall, t=None):
+        """Force the aggregate exerts on wall l (x_lo, x_hi, y_lo, y_hi): minus the
+        force of that wall on the nodes, its own term less half of each corner
+        term it shares (a corner region belongs to two walls)."""
+        single, corner = self.wall_sums(t)
+        shares = {0: (0, 1), 1: (2, 3), 2: (0, 2), 3: (1, 3)}[wall]   # corners (x_lo,y_lo),(x_lo,y_hi),(x_hi,y_lo),(x_hi,y_hi)
+        f = single[wall] - 0.5 * (corner[shares[0]] + corner[shares[1]])
+        return -f

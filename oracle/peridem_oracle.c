@@ -521,10 +521,13 @@ static void damping_friction(const double *prm, double ex, double ey, double vrx
     *fy += Fdy + Ffy;
 }
 
-/* Wall force on one node, Sec. 4.5 (eq:wall-repulsive, eq:wall-total), with   */
+/* Wall terms on one node, Sec. 4.5 (eq:wall-repulsive, eq:wall-total), with   */
 /* friction and damping obtained by the substitution e -> e^l, V_y -> |S_l|,   */
-/* p(y) -> c_l.                                                               */
-static void wall_force(const or_sys *S, int x, double *fx, double *fy)
+/* p(y) -> c_l: single[l] is the force of wall l (x_lo, x_hi, y_lo, y_hi) by   */
+/* its own segment, corner[k] the term of the corner region S_i cap S_j that   */
+/* eq:wall-total subtracts (k: (x_lo,y_lo), (x_lo,y_hi), (x_hi,y_lo),          */
+/* (x_hi,y_hi)).  The node's wall force is sum single - sum corner.            */
+static void wall_terms(const or_sys *S, int x, double single[4][2], double corner[4][2])
 {
     const double *prm = S->prm;
     double Rc = prm[P_RC], Kn = prm[P_KN];
@@ -547,7 +550,10 @@ static void wall_force(const or_sys *S, int x, double *fx, double *fy)
             d[l] = 0.0;
         }
     }
-    double Fx = 0.0, Fy = 0.0;
+    for (int l = 0; l < 4; ++l) {
+        single[l][0] = single[l][1] = 0.0;
+        corner[l][0] = corner[l][1] = 0.0;
+    }
     for (int l = 0; l < 4; ++l) {
         if (!(d[l] < Rc)) continue;
         double A, gap;
@@ -558,8 +564,8 @@ static void wall_force(const or_sys *S, int x, double *fx, double *fy)
         double wvx = (l < 2) ? wvel[l] : 0.0, wvy = (l < 2) ? 0.0 : wvel[l];
         double gx = -Fr * ex[l], gy = -Fr * ey[l];
         damping_friction(prm, ex[l], ey[l], vx - wvx, vy - wvy, Fr, Vx, A, &gx, &gy);
-        Fx += gx;
-        Fy += gy;
+        single[l][0] = gx;
+        single[l][1] = gy;
     }
     static const int ci[4] = {0, 0, 1, 1}, cj[4] = {2, 3, 2, 3};
     for (int k = 0; k < 4; ++k) {
@@ -576,8 +582,24 @@ static void wall_force(const or_sys *S, int x, double *fx, double *fy)
         double wvx = wvel[i], wvy = wvel[j];
         double gx = -Fr * ux, gy = -Fr * uy;
         damping_friction(prm, ux, uy, vx - wvx, vy - wvy, Fr, Vx, A, &gx, &gy);
-        Fx -= gx;
-        Fy -= gy;
+        corner[k][0] = gx;
+        corner[k][1] = gy;
+    }
+}
+
+/* Wall force on one node: eq:wall-total, walls in order then corners. */
+static void wall_force(const or_sys *S, int x, double *fx, double *fy)
+{
+    double single[4][2], corner[4][2];
+    wall_terms(S, x, single, corner);
+    double Fx = 0.0, Fy = 0.0;
+    for (int l = 0; l < 4; ++l) {
+        Fx += single[l][0];
+        Fy += single[l][1];
+    }
+    for (int k = 0; k < 4; ++k) {
+        Fx -= corner[k][0];
+        Fy -= corner[k][1];
     }
     *fx = Fx;
     *fy = Fy;
@@ -714,6 +736,33 @@ void or_forces(const double *prm, double t, int N, const double *X, const double
     sys_init(&S, prm, N, X, u, v, V, grain, g_cw, g_s0, g_eps, row_ptr, col, broken, status);
     S.t = t;
     all_forces(&S, F, parts);
+    sys_free(&S);
+}
+
+/* Sums over all nodes of the wall terms at the current state (walls at time */
+/* t): out[2 l + c] for wall l's own segment, out[8 + 2 k + c] for corner k   */
+/* (the orders of wall_terms).  Used for the force the aggregate exerts on a  */
+/* wall (Sec. 6, compaction: force on the top wall).                          */
+void or_wall_sums(const double *prm, double t, int N, const double *X, const double *u, const double *v,
+                  const double *V, double *out)
+{
+    or_sys S;
+    sys_init(&S, prm, N, X, u, v, V, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
+    S.t = t;
+    int status[8] = {0};
+    S.status = status;
+    for (int q = 0; q < 16; ++q) out[q] = 0.0;
+    for (int k = 0; k < 2 * N; ++k) S.p[k] = X[k] + u[k];
+    for (int x = 0; x < N; ++x) {
+        double single[4][2], corner[4][2];
+        wall_terms(&S, x, single, corner);
+        for (int l = 0; l < 4; ++l) {
+            out[2 * l] += single[l][0];
+            out[2 * l + 1] += single[l][1];
+            out[8 + 2 * l] += corner[l][0];
+            out[8 + 2 * l + 1] += corner[l][1];
+        }
+    }
     sys_free(&S);
 }
 

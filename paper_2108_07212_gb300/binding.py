@@ -32,7 +32,7 @@ SYMBOLS = ("pd_last_error", "pd_create", "pd_destroy", "pd_mesh_grains", "pd_bui
            "pd_mlp_arena_bytes", "pd_mlp_bind_arena", "pd_mlp_set_params", "pd_mlp_get_params", "pd_mlp_forward",
            "pd_mlp_loss_grad", "pd_mlp_train_step", "pd_surrogate_setup", "pd_surrogate_set_mlp",
            "pd_surrogate_enable", "pd_surrogate_sample", "pd_surrogate_stats", "pd_surrogate_inspect",
-           "pd_diagnostics_noalloc")
+           "pd_diagnostics_noalloc", "pd_observables")
 
 
 class PdParams(ctypes.Structure):
@@ -268,6 +268,14 @@ class Simulation:
         d = dict(zip(DIAG_NAMES, out[: len(DIAG_NAMES)]))
         d["n_broken"] = int(d["n_broken"])
         return d
+
+    def observables(self) -> np.ndarray:
+        """Per aggregate: volume fraction, bulk damage, y force on the top wall,
+        y force on the bottom wall (pd_observables)."""
+        n_agg = int(self.info()["n_agg"])
+        out = np.zeros((n_agg, 4))
+        _check(load().pd_observables(self._ctx, _ptr(out)))
+        return out
 
     def status(self):
         out = np.zeros(STATUS_COUNT, dtype=np.int32)

@@ -205,6 +205,69 @@ cudaError_t launch_positions(const DevPtrs &d, const KParams &k, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Particle damage (Sec. 6): mean over the grain's nodes of the node damage
+// broken / reference bonds (Sec. 3.1); one block per grain.
+__global__ void __launch_bounds__(kBlock) k_grain_damage(DevPtrs d, KParams k, double *out) {
+    __shared__ double sm[kBlock / 32];
+    const int g = blockIdx.x;
+    const int s0 = d.g_start[g], s1 = d.g_start[g + 1];
+    double sum = 0.0;
+    for (int i = s0 + threadIdx.x; i < s1; i += kBlock) {
+        const int r0 = d.row_ptr[i], r1 = d.row_ptr[i + 1];
+        int broken = 0;
+        for (int kk = 0; kk < r1 - r0; kk += 32) {
+            uint32_t w = d.bits[(size_t)i * k.wpn + (kk >> 5)];
+            const int rest = r1 - r0 - kk;
+            if (rest < 32) w &= (1u << rest) - 1u;
+            broken += __popc(w);
+        }
+        if (r1 > r0) sum += (double)broken / (double)(r1 - r0);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) t += sm[w];
+        out[g] = s1 > s0 ? t / (double)(s1 - s0) : 0.0;
+    }
+}
+
+// Sums per aggregate of the wall terms of all nodes near a wall at the
+// current state: out[16 a + 2 l + c] own segment of wall l, out[16 a + 8 + 2 q + c]
+// corner q (the order of wall_terms64).
+__global__ void __launch_bounds__(kBlock) k_wall_sums(DevPtrs d, KParams k, int vcur, double *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k.N) return;
+    const int ag = d.g_agg[d.grain[i]];
+    if (far_from_walls<false>(d, i, ag)) return;
+    const double2 p = d.p[i], v = d.v[vcur][i];
+    double single[4][2], corner[4][2];
+    wall_terms64(k, d.agg[ag], *d.t_now, p.x, p.y, v.x, v.y, d.V[i], single, corner, nullptr);
+    double *o = out + 16 * (size_t)ag;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        if (single[l][0] != 0.0) atomicAdd(&o[2 * l], single[l][0]);
+        if (single[l][1] != 0.0) atomicAdd(&o[2 * l + 1], single[l][1]);
+        if (corner[l][0] != 0.0) atomicAdd(&o[8 + 2 * l], corner[l][0]);
+        if (corner[l][1] != 0.0) atomicAdd(&o[8 + 2 * l + 1], corner[l][1]);
+    }
+}
+
+cudaError_t launch_observables(const DevPtrs &d, const KParams &k, int vcur, double *gdam, double *wsum,
+                               cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(wsum, 0, sizeof(double) * 16 * (size_t)k.n_agg, s);
+    if (e != cudaSuccess) return e;
+    // positions, cells and wall cells of the current state (no advance)
+    if ((e = cudaMemsetAsync(d.count, 0, sizeof(int) * k.T, s)) != cudaSuccess) return e;
+    if ((e = launch_predict(d, k, vcur, 0, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(d.count, 0, sizeof(int) * k.T, s)) != cudaSuccess) return e;
+    k_grain_damage<<<k.G, kBlock, 0, s>>>(d, k, gdam);
+    k_wall_sums<<<nblk(k.N, kBlock), kBlock, 0, s>>>(d, k, vcur, wsum);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_diagnostics(const DevPtrs &d, const KParams &k, int vcur, cudaStream_t s) {
     k_diag_partial<<<k.n_diag_blocks, kBlock, 0, s>>>(d, k, vcur);
     k_diag_final<<<1, 32, 0, s>>>(d, k.n_diag_blocks);

@@ -142,9 +142,9 @@ __device__ __forceinline__ void corner_region_stable(double di, double dj, doubl
 // the S_li cap S_lj term (inclusion-exclusion); friction and damping follow by
 // substituting e -> e^l, V_y -> |S_l|, p(y) -> c_l.  A node past a wall is
 // treated as touching it and counted in status[PD_STATUS_PENETRATION].
-__device__ __forceinline__ void wall_force64(const KParams &k, const AggParams &A, double t, double px, double py,
-                                             double vx, double vy, double Vx, double &Fx_out, double &Fy_out,
-                                             int *status) {
+__device__ __forceinline__ void wall_terms64(const KParams &k, const AggParams &A, double t, double px, double py,
+                                             double vx, double vy, double Vx, double (&single)[4][2],
+                                             double (&corner)[4][2], int *status) {
     const double Rc = A.Rc, Kn = A.Kn;
     double d[4], ex[4], ey[4];
     d[0] = px - (A.w0[0] + A.wv[0] * t); ex[0] = -1.0; ey[0] = 0.0;
@@ -154,43 +154,62 @@ __device__ __forceinline__ void wall_force64(const KParams &k, const AggParams &
     bool near = false;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
+        single[l][0] = single[l][1] = corner[l][0] = corner[l][1] = 0.0;
         if (d[l] < 0.0) {
-            atomicAdd(&status[PD_STATUS_PENETRATION], 1);
+            if (status) atomicAdd(&status[PD_STATUS_PENETRATION], 1);
             d[l] = 0.0;
         }
         near |= d[l] < Rc;
     }
+    if (!near) return;
+    for (int l = 0; l < 4; ++l) {
+        if (!(d[l] < Rc)) continue;
+        double Ar, gap;
+        wall_segment_stable(d[l], Rc, Ar, gap);
+        if (!(Ar > 0.0) || !(gap > 0.0)) continue;
+        double Fr = Kn * gap * Vx * Ar;
+        double wvx = (l < 2) ? A.wv[l] : 0.0, wvy = (l < 2) ? 0.0 : A.wv[l];
+        double gx = -Fr * ex[l], gy = -Fr * ey[l];
+        damping_friction64(k, Kn, ex[l], ey[l], vx - wvx, vy - wvy, Fr, Vx, Ar, gx, gy);
+        single[l][0] = gx;
+        single[l][1] = gy;
+    }
+    for (int c = 0; c < 4; ++c) {
+        const int i = c >> 1, j = 2 + (c & 1);  // (x_lo|x_hi) x (y_lo|y_hi)
+        double di = d[i], dj = d[j];
+        if (!(sqrt(di * di + dj * dj) < Rc)) continue;
+        double Ar, lx, ly;
+        corner_region_stable(di, dj, Rc, Ar, lx, ly);
+        if (!(Ar > 0.0)) continue;
+        double cx = lx * ex[i] + ly * ex[j], cy = lx * ey[i] + ly * ey[j];
+        double cd = sqrt(cx * cx + cy * cy);
+        if (!(cd < Rc) || !(cd > 0.0)) continue;
+        double ux = cx / cd, uy = cy / cd;
+        double Fr = Kn * (Rc - cd) * Vx * Ar;
+        double gx = -Fr * ux, gy = -Fr * uy;
+        damping_friction64(k, Kn, ux, uy, vx - A.wv[i], vy - A.wv[j], Fr, Vx, Ar, gx, gy);
+        corner[c][0] = gx;
+        corner[c][1] = gy;
+    }
+}
+
+// Wall force on a node at (px, py) with velocity (vx, vy) and volume Vx:
+// eq:wall-total, the walls' own segments in order minus the corner terms.
+__device__ __forceinline__ void wall_force64(const KParams &k, const AggParams &A, double t, double px, double py,
+                                             double vx, double vy, double Vx, double &Fx_out, double &Fy_out,
+                                             int *status) {
+    double single[4][2], corner[4][2];
+    wall_terms64(k, A, t, px, py, vx, vy, Vx, single, corner, status);
     double Fx = 0.0, Fy = 0.0;
-    if (near) {
-        for (int l = 0; l < 4; ++l) {
-            if (!(d[l] < Rc)) continue;
-            double Ar, gap;
-            wall_segment_stable(d[l], Rc, Ar, gap);
-            if (!(Ar > 0.0) || !(gap > 0.0)) continue;
-            double Fr = Kn * gap * Vx * Ar;
-            double wvx = (l < 2) ? A.wv[l] : 0.0, wvy = (l < 2) ? 0.0 : A.wv[l];
-            double gx = -Fr * ex[l], gy = -Fr * ey[l];
-            damping_friction64(k, Kn, ex[l], ey[l], vx - wvx, vy - wvy, Fr, Vx, Ar, gx, gy);
-            Fx += gx;
-            Fy += gy;
-        }
-        for (int c = 0; c < 4; ++c) {
-            const int i = c >> 1, j = 2 + (c & 1);  // (x_lo|x_hi) x (y_lo|y_hi)
-            double di = d[i], dj = d[j];
-            if (!(sqrt(di * di + dj * dj) < Rc)) continue;
-            double Ar, lx, ly;
-            corner_region_stable(di, dj, Rc, Ar, lx, ly);
-            if (!(Ar > 0.0)) continue;
-            double cx = lx * ex[i] + ly * ex[j], cy = lx * ey[i] + ly * ey[j];
-            double cd = sqrt(cx * cx + cy * cy);
-            if (!(cd < Rc) || !(cd > 0.0)) continue;
-            double ux = cx / cd, uy = cy / cd;
-            double Fr = Kn * (Rc - cd) * Vx * Ar;
-            double gx = -Fr * ux, gy = -Fr * uy;
-            damping_friction64(k, Kn, ux, uy, vx - A.wv[i], vy - A.wv[j], Fr, Vx, Ar, gx, gy);
-            Fx -= gx;
-            Fy -= gy;
-        }
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        Fx += single[l][0];
+        Fy += single[l][1];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        Fx -= corner[c][0];
+        Fy -= corner[c][1];
     }
     Fx_out = Fx;
     Fy_out = Fy;
@@ -331,28 +350,51 @@ __device__ __forceinline__ int gather_candidates(const DevPtrs &d, const KParams
     int nc = 0;
     if (!active) return 0;
     const int2 cc = ldm<PERSIST>(&d.cell[i]);      // cell of node i, from the binning phase
-    for (int c = lane; c < 9; c += LANES) {
-        const unsigned bc = cell_bucket(cc.x + (c % 3) - 1, cc.y + (c / 3) - 1, ag, k.T);
-        bool dup = false;
-        for (int q = 0; q < c; ++q) dup |= cell_bucket(cc.x + (q % 3) - 1, cc.y + (q / 3) - 1, ag, k.T) == bc;
-        if (dup) continue;
-        const int t0 = ldm<PERSIST>(&d.start[bc]), t1 = ldm<PERSIST>(&d.start[bc + 1]);
-        for (int t = t0; t < t1; ++t) {
-            // the bucket's positions are stored in bucket order: the distance test
-            // needs no index chase; only nodes within R_c are looked up
-            if (!within(ldm<PERSIST>(&d.srec[t]))) continue;
-            const int j = ldm<PERSIST>(&d.sorted[t]);
-            // hash aliasing can bring nodes of another aggregate: never in contact
-            if (j == i || __ldg(&d.g_agg[__ldg(&d.grain[j])]) != ag) continue;
-            if (nc < kMaxCand) {
-                int w = nc++;
-                while (w > 0 && cand[w - 1] > j) {
-                    cand[w] = cand[w - 1];
-                    --w;
+    // cells lane, lane + LANES, ... of the 3x3 block, staged S at a time: first
+    // all bucket ranges, then the first record of every bucket, then the rest,
+    // so that the dependent loads of several cells are in flight together
+    constexpr int MC = (9 + LANES - 1) / LANES;
+    constexpr int S = MC < 3 ? MC : 3;
+#pragma unroll
+    for (int m0 = 0; m0 < MC; m0 += S) {
+        int t0[S], t1[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int c = lane + (m0 + s) * LANES;
+            t0[s] = 0;
+            t1[s] = 0;
+            if (m0 + s < MC && c < 9) {
+                const unsigned bc = cell_bucket(cc.x + (c % 3) - 1, cc.y + (c / 3) - 1, ag, k.T);
+                bool dup = false;      // two cells of the block hashed to one bucket: visit it once
+                for (int q = 0; q < c; ++q) dup |= cell_bucket(cc.x + (q % 3) - 1, cc.y + (q / 3) - 1, ag, k.T) == bc;
+                if (!dup) {
+                    t0[s] = ldm<PERSIST>(&d.start[bc]);
+                    t1[s] = ldm<PERSIST>(&d.start[bc + 1]);
                 }
-                cand[w] = j;
-            } else {
-                atomicAdd(&d.status[PD_STATUS_OVERFLOW], 1);
+            }
+        }
+        uint4 first[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) first[s] = t0[s] < t1[s] ? ldm<PERSIST>(&d.srec[t0[s]]) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            for (int t = t0[s]; t < t1[s]; ++t) {
+                // the bucket's positions are stored in bucket order: the distance test
+                // needs no index chase; only nodes within R_c are looked up
+                if (!within(t == t0[s] ? first[s] : ldm<PERSIST>(&d.srec[t]))) continue;
+                const int j = ldm<PERSIST>(&d.sorted[t]);
+                // hash aliasing can bring nodes of another aggregate: never in contact
+                if (j == i || __ldg(&d.g_agg[__ldg(&d.grain[j])]) != ag) continue;
+                if (nc < kMaxCand) {
+                    int w = nc++;
+                    while (w > 0 && cand[w - 1] > j) {
+                        cand[w] = cand[w - 1];
+                        --w;
+                    }
+                    cand[w] = j;
+                } else {
+                    atomicAdd(&d.status[PD_STATUS_OVERFLOW], 1);
+                }
             }
         }
     }

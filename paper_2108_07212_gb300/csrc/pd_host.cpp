@@ -348,6 +348,9 @@ size_t layout(pd_ctx *c, char *base) {
     carve(base, off, d.status, PD_STATUS_COUNT);
     carve(base, off, d.diag_part, (size_t)c->kp.n_diag_blocks * PD_DIAG_COUNT);
     carve(base, off, d.diag_out, PD_DIAG_COUNT);
+    carve(base, off, d.g_start, G + 1);
+    carve(base, off, d.obs_gdam, G);
+    carve(base, off, d.obs_wall, 16 * (size_t)c->n_agg);
     if (c->prm.precision == PD_FP32_SPLIT) {
         carve(base, off, d.lat, N);
         carve(base, off, d.gq, G);
@@ -371,7 +374,6 @@ size_t layout(pd_ctx *c, char *base) {
     carve(base, off, d.bbits, N * (size_t)c->wpn);
     if (c->sur_cfg) {
         const size_t M = (size_t)c->sur_modes, T = (size_t)c->n_tmpl;
-        carve(base, off, d.g_start, G + 1);
         carve(base, off, d.g_tmpl, G);
         carve(base, off, d.g_slot, G);
         carve(base, off, d.tmpl_node, T + 1);
@@ -406,7 +408,7 @@ size_t layout(pd_ctx *c, char *base) {
         carve(base, off, d.sur_qs, G * M);
         carve(base, off, d.sur_fs, G * M);
     } else {
-        d.g_start = d.g_tmpl = d.g_slot = d.tmpl_node = d.tmpl_slot = d.sur_active = nullptr;
+        d.g_tmpl = d.g_slot = d.tmpl_node = d.tmpl_slot = d.sur_active = nullptr;
         d.tmpl_rows = d.slot_grain = nullptr;
         d.bnm_hi = d.bnm_lo = d.bmm_hi = d.bmm_lo = nullptr;
         d.proj_work = d.exp_work = nullptr;
@@ -873,10 +875,10 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     PD_CUDA(cudaMemcpyAsync(d.agg, c->aggp.data(), sizeof(pd::AggParams) * c->aggp.size(), cudaMemcpyHostToDevice, s));
     PD_CUDA(cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), s));
     PD_CUDA(cudaMemsetAsync(d.t_now, 0, sizeof(double), s));
-    std::vector<int32_t> gstart32, tnode, tslot;
+    std::vector<int32_t> gstart32(c->g_start.begin(), c->g_start.end()), tnode, tslot;
+    PD_CUDA(cudaMemcpyAsync(d.g_start, gstart32.data(), 4 * (G + 1), cudaMemcpyHostToDevice, s));
     std::vector<float> fc;
     if (c->sur_cfg) {
-        gstart32.assign(c->g_start.begin(), c->g_start.end());
         tnode.assign(c->n_tmpl + 1, 0);
         tslot.assign(c->n_tmpl + 1, 0);
         for (int t = 0; t < c->n_tmpl; ++t) {
@@ -898,7 +900,7 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
             fc[4 * g + 2] = (float)(si / n);
             fc[4 * g + 3] = (float)(sj / n);
         }
-        PD_CUDA(cudaMemcpyAsync(d.g_start, gstart32.data(), 4 * (G + 1), cudaMemcpyHostToDevice, s));
+
         PD_CUDA(cudaMemcpyAsync(d.g_tmpl, c->g_tmpl.data(), 4 * G, cudaMemcpyHostToDevice, s));
         PD_CUDA(cudaMemcpyAsync(d.g_slot, c->g_slot.data(), 4 * G, cudaMemcpyHostToDevice, s));
         PD_CUDA(cudaMemcpyAsync(d.tmpl_node, tnode.data(), 4 * tnode.size(), cudaMemcpyHostToDevice, s));
@@ -1126,6 +1128,43 @@ int pd_diagnostics(pd_ctx *c, double *out) {
     PD_CUDA(pd::launch_diagnostics(c->d, c->kp, c->vcur, c->stream));
     PD_CUDA(cudaMemcpyAsync(out, c->d.diag_out, 8 * PD_DIAG_COUNT, cudaMemcpyDeviceToHost, c->stream));
     PD_CUDA(cudaStreamSynchronize(c->stream));
+    return PD_OK;
+}
+
+int pd_observables(pd_ctx *c, double *out) {
+    if (int r = check_ctx(c, 3)) return r;
+    if (!out) return fail(PD_EINVAL, "null output");
+    const size_t G = (size_t)c->G, A = (size_t)c->n_agg;
+    PD_CUDA(pd::launch_observables(c->d, c->kp, c->vcur, c->d.obs_gdam, c->d.obs_wall, c->stream));
+    std::vector<double> gdam(G), wsum(16 * A);
+    long long step = 0;
+    PD_CUDA(cudaMemcpyAsync(gdam.data(), c->d.obs_gdam, 8 * G, cudaMemcpyDeviceToHost, c->stream));
+    PD_CUDA(cudaMemcpyAsync(wsum.data(), c->d.obs_wall, 8 * 16 * A, cudaMemcpyDeviceToHost, c->stream));
+    PD_CUDA(cudaMemcpyAsync(&step, c->d.step, 8, cudaMemcpyDeviceToHost, c->stream));
+    PD_CUDA(cudaStreamSynchronize(c->stream));
+    const double t = (double)step * c->prm.dt;
+    std::vector<double> vol(A, 0.0), dsum(A, 0.0);
+    std::vector<int> ng(A, 0);
+    for (size_t g = 0; g < G; ++g) {
+        const int a = c->g_agg[g];
+        for (int64_t x = c->g_start[g]; x < c->g_start[g + 1]; ++x) vol[a] += c->V[x];
+        dsum[a] += gdam[g];
+        ng[a] += 1;
+    }
+    for (size_t a = 0; a < A; ++a) {
+        const double *w = &c->agg_walls[8 * a];
+        const double xlo = w[0] + w[4] * t, xhi = w[1] + w[5] * t, ylo = w[2] + w[6] * t, yhi = w[3] + w[7] * t;
+        const double *ws = &wsum[16 * a];
+        // force of wall l on the nodes: its own segment term less half of each
+        // corner term it shares; the aggregate exerts the opposite force
+        // (corners: 0 (x_lo,y_lo), 1 (x_lo,y_hi), 2 (x_hi,y_lo), 3 (x_hi,y_hi))
+        const double top = ws[2 * 3 + 1] - 0.5 * (ws[8 + 2 * 1 + 1] + ws[8 + 2 * 3 + 1]);
+        const double bottom = ws[2 * 2 + 1] - 0.5 * (ws[8 + 2 * 0 + 1] + ws[8 + 2 * 2 + 1]);
+        out[PD_OBS_COUNT * a + PD_OBS_PHI] = vol[a] / ((xhi - xlo) * (yhi - ylo));
+        out[PD_OBS_COUNT * a + PD_OBS_BULK_DAMAGE] = ng[a] ? dsum[a] / ng[a] : 0.0;
+        out[PD_OBS_COUNT * a + PD_OBS_FORCE_TOP] = -top;
+        out[PD_OBS_COUNT * a + PD_OBS_FORCE_BOTTOM] = -bottom;
+    }
     return PD_OK;
 }
 

@@ -57,6 +57,8 @@ struct DevPtrs {
     unsigned *bar;      // grid barrier: [0] arrivals, [1] generation
     double *diag_part;  // per-block diagnostic partial sums
     double *diag_out;   // PD_DIAG_COUNT
+    double *obs_gdam;   // particle damage of every grain (G)
+    double *obs_wall;   // per aggregate: sums of the wall terms (16 n_agg)
     // FP32-split path
     int2 *lat;          // lattice indices (i, j) of every node in its grain frame
     float4 *gq;         // per grain: (h, h^2 hi, h^2 lo, V = h^2 as float)
@@ -171,6 +173,10 @@ cudaError_t launch_force64(const DevPtrs &d, const KParams &k, int vin, int upda
 cudaError_t launch_force32(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s);
 cudaError_t launch_positions(const DevPtrs &d, const KParams &k, cudaStream_t s);
 cudaError_t launch_diagnostics(const DevPtrs &d, const KParams &k, int vcur, cudaStream_t s);
+// Particle damage of every grain (gdam[G]) and per-aggregate sums of the wall
+// terms (wsum[16 n_agg]) at the current state.
+cudaError_t launch_observables(const DevPtrs &d, const KParams &k, int vcur, double *gdam, double *wsum,
+                               cudaStream_t s);
 
 // Persistent cooperative step kernel: nsteps full time steps in one launch
 // (phases separated by bounded grid barriers).  block = threads per block
