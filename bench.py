@@ -304,8 +304,9 @@ def force_phase_traffic(path: dict, fp32: bool, workload: str):
         return None
     p, m, l = ("1" if fp32 else "0"), path["mode"], path["lanes"]
     if m & 1:
-        return None                      # the persistent kernel's phases are not separable
-    names = [f"k_sums<{p}, {l}>", f"k_epilogue<{p}>"] if m >> 1 else [f"k_force<{p}, {l}>"]
+        names = [f"k_persistent<{p}, {l}, {path.get('block', 128)}>"]     # the whole step
+    else:
+        names = [f"k_sums<{p}, {l}>", f"k_epilogue<{p}>"] if m >> 1 else [f"k_force<{p}, {l}>"]
     if not all(n in TRAFFIC_SETTLING50 for n in names):
         return None
     return float(sum(TRAFFIC_SETTLING50[n] for n in names))
@@ -629,15 +630,17 @@ def run_ours(args):
                 "note": f"{FLOPS_PER_BOND} algorithmic FP64 ops per directed bond x {sim.n_bonds} bonds per launch / "
                         f"mean CUDA-event duration {f_ms * 1e3:.1f} us; peak = measured cuBLAS DGEMM (of measured)"}
     else:
-        nbytes = BYTES_PER_NODE_FP32 * sim.N + BYTES_PER_BOND_FP32 * sim.n_bonds
+        whole = bool(tuned["fp32"]["mode"] & 1)          # persistent kernel: one launch for the whole step
+        per_node = BYTES_PER_NODE_STEP_FP32 if whole else BYTES_PER_NODE_FP32
+        nbytes = per_node * sim.N + BYTES_PER_BOND_FP32 * sim.n_bonds
         achieved = nbytes / (f_ms / 1e3) / 1e9
         hbm = float(peaks.get("hbm_gbs") or 6800.0)
         roof = {"bound": "hbm", "kernel": _force_kernels(tuned["fp32"]["mode"], True), "achieved": achieved, "peak": hbm,
                 "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": force_phase_traffic(tuned["fp32"], True, args.workload),
-                "note": f"{BYTES_PER_NODE_FP32} B per node + {BYTES_PER_BOND_FP32} B per directed bond (algorithmic) x "
-                        f"{sim.N} nodes / {sim.n_bonds} bonds per force phase / mean CUDA-event duration of the "
-                        f"force phase {f_ms * 1e3:.1f} us; peak = measured copy bandwidth (of measured)"
+                "note": f"{per_node} B per node + {BYTES_PER_BOND_FP32} B per directed bond (algorithmic) x "
+                        f"{sim.N} nodes / {sim.n_bonds} bonds per {'step' if whole else 'force phase'} / mean "
+                        f"CUDA-event duration {f_ms * 1e3:.1f} us; peak = measured copy bandwidth (of measured)"
                         + ("; the 20k-node workload is too small to load 152 SMs, so the phase is latency-bound"
                            if sim.N < 100000 else "")}
     line = {

@@ -25,6 +25,13 @@ __device__ __forceinline__ T ldm(const T *p) {
 // distance test rejects.
 // Hash-grid cell index of a coordinate (inv_cell = 1 / cell side).  Only the
 // binning kernel calls this; the force kernels read the stored cells.
+__device__ __forceinline__ int cell_coord_f(float x, float inv_cell) {
+    float f = floorf(x * inv_cell);
+    if (!(f > -1048576.0f)) return -1048576;  // also catches NaN
+    if (f > 1048576.0f) return 1048576;
+    return (int)f;
+}
+
 __device__ __forceinline__ int cell_coord(double x, double origin, double inv_cell) {
     double f = floor((x - origin) * inv_cell);
     if (!(f > -1048576.0)) return -1048576;  // also catches NaN
@@ -290,13 +297,21 @@ __device__ __forceinline__ void predict_node(const DevPtrs &d, const KParams &k,
     d.p[i] = p;
     const int ag = __ldg(&d.g_agg[__ldg(&d.grain[i])]);
     const AggParams &A = d.agg[ag];
+    int cx, cy;
     if (d.ph) {
         double qx = p.x + A.sx, qy = p.y + A.sy;
         float2 ph = make_float2((float)qx, (float)qy);
+        const float2 pl = make_float2((float)(qx - (double)ph.x), (float)(qy - (double)ph.y));
         d.ph[i] = ph;
-        d.pl[i] = make_float2((float)(qx - (double)ph.x), (float)(qy - (double)ph.y));
+        d.pl[i] = pl;
+        // FP32-split: the cell from the shifted float position (error below 1e-3
+        // cell; the cells of this path are 0.4 % wider than R_c to absorb it)
+        cx = cell_coord_f((ph.x - A.oxs) + pl.x, A.inv_cell_f);
+        cy = cell_coord_f((ph.y - A.oys) + pl.y, A.inv_cell_f);
+    } else {
+        cx = cell_coord(p.x, A.ox, A.inv_cell);
+        cy = cell_coord(p.y, A.oy, A.inv_cell);
     }
-    const int cx = cell_coord(p.x, A.ox, A.inv_cell), cy = cell_coord(p.y, A.oy, A.inv_cell);
     d.cell[i] = make_int2(cx, cy);
     unsigned b = cell_bucket(cx, cy, ag, k.T);
     d.key[i] = (int)b;

@@ -248,7 +248,8 @@ void compute_aggregates(pd_ctx *c) {
         A.ox = w[0];
         A.oy = w[2];
         // a hair above R_c: two nodes closer than R_c never land two cells apart
-        A.cell = A.Rc * (1.0 + 1e-9);
+        // (FP32 split: 0.4 % above, the margin of its float cell coordinates)
+        A.cell = A.Rc * (p.precision == PD_FP32_SPLIT ? 1.004 : 1.0 + 1e-9);
         A.inv_cell = 1.0 / A.cell;
         // FP32 split: shift coordinates of the box into [L, 2L) so nearby
         // positions share a binade and their float differences are exact
@@ -260,6 +261,9 @@ void compute_aggregates(pd_ctx *c) {
         A.rc2_lo = (float)(rc2 - (double)A.rc2_hi);
         A.rcf = (float)A.Rc;
         A.knf = (float)A.Kn;
+        A.oxs = (float)(A.ox + A.sx);
+        A.oys = (float)(A.oy + A.sy);
+        A.inv_cell_f = (float)A.inv_cell;
     }
     c->h_min = hmin[0] < 1e300 ? hmin[0] : c->g_h[0];
     c->Rc = c->aggp[0].Rc;

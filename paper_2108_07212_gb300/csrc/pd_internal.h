@@ -29,6 +29,7 @@ struct AggParams {
     double sx, sy;         // FP32-split shift: coordinates of the box map to [L, 2L)
     float rc2_hi, rc2_lo;  // R_c^2 as a float-float pair
     float rcf, knf;        // R_c and K_n as floats
+    float oxs, oys, inv_cell_f;  // FP32 split: grid origin in shifted coordinates, 1 / cell
 };
 
 // Device pointers carved out of the caller's arena.

@@ -82,8 +82,17 @@ def test_volume_fraction_follows_the_moving_lid():
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", [B.PD_FP64, B.PD_FP32_SPLIT])
+def _lid_and_floor():
+    """Grains thrown at the floor under a lid that moves down at 3 m/s: both
+    walls carry load within a few hundred steps."""
+    w = I.settling(n_grains=8, box=(8e-3, 8e-3), seed=4)
+    w.params["wall_vel_hi"] = (0.0, -3.0)
+    w.grain_geom[:, 5] = -2.0
+    return w
+
+
 def test_gpu_observables_match_the_oracle(prec):
-    w = I.compaction(n_grains=12, width=10e-3, seed=4, wall_speed=2.0, agitation=3.0)
+    w = _lid_and_floor()
     S = B.Simulation(w, precision=prec, device="cuda:0")
     S.step(1500)
     obs = S.observables()
@@ -104,7 +113,12 @@ def test_gpu_observables_match_the_oracle(prec):
 
 @pytest.mark.gpu
 def test_gpu_observables_per_aggregate():
-    parts = [I.compaction(n_grains=6, width=8e-3, seed=5 + a, wall_speed=1.0 + a, agitation=2.0) for a in range(3)]
+    parts = []
+    for a in range(3):
+        w = I.settling(n_grains=6, box=(8e-3, 8e-3), seed=5 + a)
+        w.params["wall_vel_hi"] = (0.0, -2.0 - a)
+        w.grain_geom[:, 5] = -2.0
+        parts.append(w)
     merged = I.merge_aggregates(parts)
     S = B.Simulation(merged, precision=B.PD_FP64, device="cuda:0")
     S.step(800)
