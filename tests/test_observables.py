@@ -80,17 +80,17 @@ def test_volume_fraction_follows_the_moving_lid():
     assert P.volume_fraction(t) / P.volume_fraction(0.0) == pytest.approx(H / (H - 0.5 * t), rel=1e-14)
 
 
-@pytest.mark.gpu
-@pytest.mark.parametrize("prec", [B.PD_FP64, B.PD_FP32_SPLIT])
 def _lid_and_floor():
     """Grains thrown at the floor under a lid that moves down at 3 m/s: both
     walls carry load within a few hundred steps."""
-    w = I.settling(n_grains=8, box=(8e-3, 8e-3), seed=4)
+    w = I.settling(n_grains=8, box=(12e-3, 12e-3), seed=4)
     w.params["wall_vel_hi"] = (0.0, -3.0)
     w.grain_geom[:, 5] = -2.0
     return w
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", [B.PD_FP64, B.PD_FP32_SPLIT])
 def test_gpu_observables_match_the_oracle(prec):
     w = _lid_and_floor()
     S = B.Simulation(w, precision=prec, device="cuda:0")
@@ -115,7 +115,7 @@ def test_gpu_observables_match_the_oracle(prec):
 def test_gpu_observables_per_aggregate():
     parts = []
     for a in range(3):
-        w = I.settling(n_grains=6, box=(8e-3, 8e-3), seed=5 + a)
+        w = I.settling(n_grains=6, box=(11e-3, 11e-3), seed=5 + a)
         w.params["wall_vel_hi"] = (0.0, -2.0 - a)
         w.grain_geom[:, 5] = -2.0
         parts.append(w)
