@@ -290,10 +290,12 @@ TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu
 
 
 def kernel_digest() -> str:
+    """SHA-1 of the force-kernel sources and of the build script (compile flags)."""
     import hashlib
     hsh = hashlib.sha1()
-    for f in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, "paper_2108_07212_gb300", "csrc", f), "rb") as fh:
+    paths = [os.path.join(ROOT, "paper_2108_07212_gb300", "csrc", f) for f in TRAFFIC_SOURCES]
+    for f in paths + [os.path.join(ROOT, "paper_2108_07212_gb300", "build.py")]:
+        with open(f, "rb") as fh:
             hsh.update(fh.read())
     return hsh.hexdigest()
 

@@ -25,7 +25,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = [
     ("pd_common.cu", ["-fmad=false"]),
     ("pd_step64.cu", ["-fmad=false"]),
-    ("pd_step32.cu", []),
+    # FP32-split force kernels: divisions and square roots to within 2 ulp
+    # (far inside the path's 1e-5 force tolerance) instead of the IEEE sequences
+    ("pd_step32.cu", ["-prec-div=false", "-prec-sqrt=false"]),
     ("pd_noalloc.cu", []),
     ("pd_mlp.cu", []),
     ("pd_surrogate.cu", []),

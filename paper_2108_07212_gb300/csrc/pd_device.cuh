@@ -467,6 +467,26 @@ __device__ __forceinline__ void finish_node(const DevPtrs &d, const KParams &k, 
     }
 }
 
+// FP32-split update without per-part output: the three lane-summed parts are
+// added in FP32 (their rounding is far below the path's force error), then
+// the wall force in FP64, F / m as F * (1 / m), and the velocity-Verlet update.
+template <bool PERSIST>
+__device__ __forceinline__ void finish_node32_total(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
+                                                    double2 vi, float fx, float fy, double Fwx, double Fwy,
+                                                    double inv_m) {
+    const double Fx = __dadd_rn((double)fx, Fwx), Fy = __dadd_rn((double)fy, Fwy);
+    const double ax = __dadd_rn(__dmul_rn(Fx, inv_m), k.gx), ay = __dadd_rn(__dmul_rn(Fy, inv_m), k.gy);
+    if (update_v) {
+        const double2 ao = ldm<PERSIST>(&d.a[i]);
+        double2 vn;
+        vn.x = __dadd_rn(vi.x, __dmul_rn(k.half_dt, __dadd_rn(ao.x, ax)));
+        vn.y = __dadd_rn(vi.y, __dmul_rn(k.half_dt, __dadd_rn(ao.y, ay)));
+        d.v[vin ^ 1][i] = vn;
+    }
+    d.a[i] = make_double2(ax, ay);
+    if (!isfinite(ax) || !isfinite(ay)) atomicAdd(&d.status[PD_STATUS_NONFINITE], 1);
+}
+
 template <int LANES, class T>
 __device__ __forceinline__ T lane_sum(T v) {
 #pragma unroll
@@ -787,8 +807,12 @@ __device__ __forceinline__ void node_epilogue32(const DevPtrs &d, const KParams 
         const double2 pi = ldm<PERSIST>(&d.p[i]);
         wall_force64(k, d.agg[ag], ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, Vi, Fwx, Fwy, d.status);
     }
-    finish_node<PERSIST, true>(d, k, i, vin, update_v, vi, Vi, (double)f.bx, (double)f.by, (double)f.sx,
-                               (double)f.sy, (double)f.nx, (double)f.ny, Fwx, Fwy, __ldg(&d.g_invm[gi]));
+    if (k.store)
+        finish_node<PERSIST, true>(d, k, i, vin, update_v, vi, Vi, (double)f.bx, (double)f.by, (double)f.sx,
+                                   (double)f.sy, (double)f.nx, (double)f.ny, Fwx, Fwy, __ldg(&d.g_invm[gi]));
+    else
+        finish_node32_total<PERSIST>(d, k, i, vin, update_v, vi, (f.bx + f.sx) + f.nx, (f.by + f.sy) + f.ny, Fwx,
+                                     Fwy, __ldg(&d.g_invm[gi]));
 }
 
 }  // namespace pd

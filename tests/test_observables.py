@@ -80,12 +80,15 @@ def test_volume_fraction_follows_the_moving_lid():
     assert P.volume_fraction(t) / P.volume_fraction(0.0) == pytest.approx(H / (H - 0.5 * t), rel=1e-14)
 
 
-def _lid_and_floor():
-    """Grains thrown at the floor under a lid that moves down at 3 m/s: both
-    walls carry load within a few hundred steps."""
-    w = I.settling(n_grains=8, box=(12e-3, 12e-3), seed=4)
-    w.params["wall_vel_hi"] = (0.0, -3.0)
-    w.grain_geom[:, 5] = -2.0
+def _lid_and_floor(n_grains=8, seed=4, lid_speed=3.0):
+    """Floor and lid moved to within R_c / 2 of the lowest and highest node, the
+    lid moving down: both walls carry load from the first steps on."""
+    w = I.settling(n_grains=n_grains, box=(12e-3, 12e-3), seed=seed)
+    X = B.Simulation(w).get("X")
+    rc = w.params["rc_ratio"] * float(w.grain_geom[:, 6].min())
+    w.params["wall_lo"] = (w.params["wall_lo"][0], float(X[:, 1].min()) - 0.5 * rc)
+    w.params["wall_hi"] = (w.params["wall_hi"][0], float(X[:, 1].max()) + 0.5 * rc)
+    w.params["wall_vel_hi"] = (0.0, -lid_speed)
     return w
 
 
@@ -94,7 +97,7 @@ def _lid_and_floor():
 def test_gpu_observables_match_the_oracle(prec):
     w = _lid_and_floor()
     S = B.Simulation(w, precision=prec, device="cuda:0")
-    S.step(1500)
+    S.step(300)
     obs = S.observables()
     P = O.OracleProblem.from_workload(w)
     P.u[:] = S.get("DISP")
@@ -113,20 +116,15 @@ def test_gpu_observables_match_the_oracle(prec):
 
 @pytest.mark.gpu
 def test_gpu_observables_per_aggregate():
-    parts = []
-    for a in range(3):
-        w = I.settling(n_grains=6, box=(11e-3, 11e-3), seed=5 + a)
-        w.params["wall_vel_hi"] = (0.0, -2.0 - a)
-        w.grain_geom[:, 5] = -2.0
-        parts.append(w)
+    parts = [_lid_and_floor(n_grains=6, seed=5 + a, lid_speed=2.0 + a) for a in range(3)]
     merged = I.merge_aggregates(parts)
     S = B.Simulation(merged, precision=B.PD_FP64, device="cuda:0")
-    S.step(800)
+    S.step(300)
     obs = S.observables()
     assert obs.shape == (3, 4)
     for a, w in enumerate(parts):
         A = B.Simulation(w, precision=B.PD_FP64, device="cuda:0")
-        A.step(800)
+        A.step(300)
         oa = A.observables()[0]
         assert obs[a, 0] == pytest.approx(oa[0], rel=1e-14)
         assert obs[a, 1] == pytest.approx(oa[1], rel=1e-9, abs=1e-12)
