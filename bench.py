@@ -32,6 +32,7 @@ FLOPS_PER_BOND = 17      # algorithmic FP64 ops of one bond evaluation (sqrt, di
 # pointer, broken word (12 B), FP64 p, v, a read and v, a written (80 B); per bond the column (4 B)
 BYTES_PER_NODE_FP32 = 116
 BYTES_PER_BOND_FP32 = 4
+B_STATUS_REBUILDS = 5    # status slot counting the contact candidate-list rebuilds
 
 
 WORKLOADS = {
@@ -204,15 +205,19 @@ def run_reference(args):
 
 
 def _timed_steps(sim, stream, flush, steps, warmup, torch):
-    """Per-step CUDA-event times (L2 flushed before every step) and the force
-    kernel's event-node durations."""
+    """Per-step CUDA-event times (L2 flushed before every step), the force
+    kernel's event-node durations and the candidate-list rebuilds of the timed
+    steps.  The timed steps run between cudaProfilerStart/Stop, so an ncu launch
+    list taken with --profile-from-start off holds exactly them."""
     sim.set_timing(True)
     for _ in range(warmup):
         flush()
         sim.step(1)
     stream.synchronize()
+    rebuilds0 = int(sim.status()[1][B_STATUS_REBUILDS])
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     force_ms = []
+    torch.cuda.profiler.start()
     for k in range(steps):
         flush()
         ev[k][0].record(stream)
@@ -220,8 +225,10 @@ def _timed_steps(sim, stream, flush, steps, warmup, torch):
         ev[k][1].record(stream)
         force_ms.append(sim.kernel_times()["force"])
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     sim.set_timing(False)
-    return [a.elapsed_time(b) for a, b in ev], force_ms
+    rebuilds = int(sim.status()[1][B_STATUS_REBUILDS]) - rebuilds0
+    return [a.elapsed_time(b) for a, b in ev], force_ms, rebuilds
 
 
 def precision_report(B, dev, stream, torch):
@@ -257,9 +264,10 @@ def precision_report(B, dev, stream, torch):
 # workload legs at the sizes where HBM, not launch latency, bounds the step
 # (500-grain compaction, 64-aggregate ensemble, 2000-grain surrogate settling)
 
-# algorithmic bytes of one whole FP32-split time step per node (predict 80 B,
-# hash binning ~40 B incl. the bucket scan, force kernel 116 B) + 4 B per bond
-BYTES_PER_NODE_STEP_FP32 = 236
+# algorithmic bytes of one whole FP32-split time step per node (displacement
+# update 80 B: X, u, v, a read, u and p written; force kernel 116 B) + 4 B per
+# bond; the candidate-list rebuild runs only in some steps and is not counted
+BYTES_PER_NODE_STEP_FP32 = 196
 
 
 # DRAM bytes (read + write) per launch of the force-phase kernels on the
@@ -322,10 +330,14 @@ def _force_kernels(mode: int, fp32: bool) -> str:
     return f"k_sums<{p},...> + k_epilogue<{p}>" if mode >> 1 else f"k_force<{p},...>"
 
 
-def _launches_per_step(mode: int) -> int:
-    """Kernels of one timed step: predict, three scan kernels, scatter and the
-    force phase (one or two kernels); the persistent kernel is one launch."""
-    return 1 if mode & 1 else 6 + (mode >> 1)
+def _launches(mode: int, steps: int, rebuilds: int) -> int:
+    """Kernels launched by `steps` timed steps: the displacement update and the
+    force phase (one or two kernels) every step, plus the six rebuild kernels
+    (bin, three scan kernels, scatter, lists) in the steps whose conditional
+    node ran them; the persistent kernel is one launch per step."""
+    if mode & 1:
+        return steps
+    return steps * (2 + (mode >> 1)) + 6 * rebuilds
 
 
 def _event_time(stream, torch, fn):
@@ -583,9 +595,9 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
-        step_ms, force_ms = _timed_steps(sim, stream, flush_l2, args.steps, args.warmup, torch)
+        step_ms, force_ms, rebuilds = _timed_steps(sim, stream, flush_l2, args.steps, args.warmup, torch)
         if sim64 is not None:
-            step64_ms, force64_ms = _timed_steps(sim64, stream, flush_l2, args.steps, args.warmup, torch)
+            step64_ms, force64_ms, rebuilds64 = _timed_steps(sim64, stream, flush_l2, args.steps, args.warmup, torch)
     elapsed = sum(step_ms) / 1e3
     elapsed64 = sum(step64_ms) / 1e3 if sim64 is not None else elapsed
     elapsed, elapsed64 = max_over_ranks(dist, [elapsed, elapsed64], dev)
@@ -660,11 +672,16 @@ def run_ours(args):
         "speedup_vs_fp64_path": value / value64,
         "roofline": roof,
         "force_kernel_us": 1e3 * f_ms,
+        "list_rebuilds": {"timed_steps": args.steps, "fp32" if prec != B.PD_FP64 else "fp64": rebuilds,
+                          **({"fp64": rebuilds64} if sim64 is not None else {}),
+                          "note": "contact candidate lists (radius R_c + 0.05 R_c) rebuilt in a conditional graph "
+                                  "node only when a node has moved 0.45 skin"},
         "precision_report": precision_report(B, dev, stream, torch) if prec != B.PD_FP64 else None,
         "cpu_baseline": cpu_baseline(w) if not args.no_cpu else None,
         "e2e": e2e,
         "clocks": clocks.summary(),
-        "gpu_launches": args.steps * sum(_launches_per_step(t["mode"]) for t in tuned.values()),
+        "gpu_launches": _launches(tuned["fp32" if prec != B.PD_FP64 else "fp64"]["mode"], args.steps, rebuilds)
+                        + (_launches(tuned["fp64"]["mode"], args.steps, rebuilds64) if sim64 is not None else 0),
         "status": int(rc),
     }
     if world == 1 and args.legs:

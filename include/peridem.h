@@ -113,6 +113,7 @@ typedef struct pd_params {
 #define PD_STATUS_NONFINITE 2   /* non-finite acceleration                          */
 #define PD_STATUS_OVERFLOW 3    /* contact candidates beyond the per-node capacity  */
 #define PD_STATUS_TIMEOUT 4     /* a grid barrier of the persistent kernel gave up  */
+#define PD_STATUS_REBUILDS 5    /* rebuilds of the contact candidate lists (not an error) */
 #define PD_STATUS_COUNT 8
 
 /* ---- diagnostics (pd_diagnostics) ------------------------------------------- */
@@ -188,7 +189,13 @@ int pd_bind_arena(pd_ctx *ctx, void *device_arena, size_t bytes);
 
 /*
  * Advance n_steps >= 0 velocity-Verlet steps (Algorithm 1) asynchronously on
- * the context stream; the step sequence runs as captured CUDA graphs.
+ * the context stream; the step sequence runs as captured CUDA graphs.  The
+ * contact neighbourhoods S^nbr (Algorithm 1, nodes within R_c) are taken from
+ * per-node candidate lists of radius R_c + skin (skin = 0.05 R_c), rebuilt by
+ * a hash-grid counting sort in a conditional graph node only in steps where
+ * some node has moved more than 0.45 skin since the last rebuild; every pair
+ * is still tested against R_c exactly, so the forces are those of a full
+ * search.  status[PD_STATUS_REBUILDS] counts the rebuilds.
  * Errors: PD_ESTATE (not bound), PD_EINVAL (n_steps < 0), PD_ECUDA.
  */
 int pd_step(pd_ctx *ctx, int n_steps);

@@ -22,6 +22,7 @@ PD_FP64, PD_FP32_SPLIT = 0, 1
 FIELDS = dict(X=0, DISP=1, VEL=2, ACC=3, POS=4, FORCE=5, FORCE_PARTS=6, BROKEN=7, DAMAGE=8, GRAIN=9,
               VOLUME=10, ROW_PTR=11, COL=12, LATTICE=13, STEP=14, GRAIN_TEMPLATE=15)
 STATUS_COUNT = 8
+STATUS_REBUILDS = 5          # slot of the candidate-list rebuild counter (not an error)
 DIAG_COUNT = 8
 DIAG_NAMES = ("KE", "E_bond", "Px", "Py", "Lz", "n_broken")
 

@@ -7,19 +7,57 @@
 
 namespace pd {
 
-// u <- u + dt v + dt^2/2 a ; p = X + u ; hash-grid bucket of p (Algorithm 1).
-// Thread 0 also advances the step counter and sets the time of the force
-// evaluation that follows: t_{n+1} = (n+1) dt.
-__global__ void __launch_bounds__(kBlock) k_predict(DevPtrs d, KParams k, int vin, int advance) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+// u <- u + dt v + dt^2/2 a ; p = X + u (Algorithm 1).  Thread 0 also advances
+// the step counter and sets the time of the force evaluation that follows:
+// t_{n+1} = (n+1) dt.  A node that moved kSkinTrigger * skin since the last
+// rebuild raises the rebuild flag; the last block to finish hands the flag to
+// the conditional node of the step graph (use_cond), which runs the rebuild
+// kernels only when it is set.
+__global__ void __launch_bounds__(kBlock) k_predict(DevPtrs d, KParams k, int vin, int advance,
+                                                    cudaGraphConditionalHandle cond, int use_cond) {
+    __shared__ bool last;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         long long st = *d.step + (advance ? 1 : 0);
         *d.t_now = (double)st * k.dt;
         if (advance) *d.step = st;
         wall_cells(d, k, (double)st * k.dt);
     }
-    if (i >= k.N) return;
-    predict_node<false>(d, k, i, vin, advance);
+    const bool need = i < k.N && predict_node<false>(d, k, i, vin, advance);
+    if (__any_sync(0xffffffffu, need) && (threadIdx.x & 31) == 0) {
+        *(volatile int *)d.rebuild = 1;
+        __threadfence();
+    }
+    if (!use_cond) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(d.pred_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const int f = *(volatile int *)d.rebuild;
+        *d.pred_done = 0u;
+        cudaGraphSetConditional(cond, f ? 1u : 0u);
+    }
+}
+
+// Rebuild of the contact candidate lists: bucket counts, a device-wide
+// exclusive scan of the counts (reduce, top, apply; apply clears the counts
+// for the next rebuild), the counting-sort scatter and the lists.  Every
+// kernel returns at once when the rebuild flag is clear.
+__global__ void __launch_bounds__(kBlock) k_bin(DevPtrs d, KParams k) {
+    if (!*(volatile int *)d.rebuild) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k.N) bin_node<false>(d, k, i);
+}
+
+__global__ void __launch_bounds__(kBlock) k_build_list(DevPtrs d, KParams k) {
+    if (!*(volatile int *)d.rebuild) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) atomicAdd(&d.status[PD_STATUS_REBUILDS], 1);
+    if (i < k.N) build_list_node<false>(d, k, i);
 }
 
 // Block-wide exclusive scan of kScanItems values per thread.
@@ -60,7 +98,9 @@ __device__ __forceinline__ int block_exclusive_scan(int (&v)[kScanItems], int *s
     return total;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int *__restrict__ count, int *blocksums, unsigned T) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int *__restrict__ count, int *blocksums, unsigned T,
+                                                              const int *flag) {
+    if (!*(volatile const int *)flag) return;
     __shared__ int sm[33];
     size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
     int v[kScanItems];
@@ -70,7 +110,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int *__restr
     if (threadIdx.x == 0) blocksums[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_top(int *blocksums, int nblocks) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(int *blocksums, int nblocks, const int *flag) {
+    if (!*(volatile const int *)flag) return;
     __shared__ int sm[33];
     int v[kScanItems];
 #pragma unroll
@@ -86,13 +127,18 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(int *blocksums, int n
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int *__restrict__ count, const int *__restrict__ blocksums,
-                                                             int *start, int *cursor, unsigned T, int N) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(int *count, const int *__restrict__ blocksums,
+                                                             int *start, int *cursor, unsigned T, int N,
+                                                             const int *flag) {
+    if (!*(volatile const int *)flag) return;
     __shared__ int sm[33];
     size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
     int v[kScanItems];
 #pragma unroll
-    for (int q = 0; q < kScanItems; ++q) v[q] = (base + q < T) ? count[base + q] : 0;
+    for (int q = 0; q < kScanItems; ++q) {
+        v[q] = (base + q < T) ? count[base + q] : 0;
+        if (base + q < T) count[base + q] = 0;
+    }
     block_exclusive_scan(v, sm);
     int off = blocksums[blockIdx.x];
 #pragma unroll
@@ -106,6 +152,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int *__restri
 }
 
 __global__ void __launch_bounds__(kBlock) k_scatter(DevPtrs d, KParams k) {
+    if (!*(volatile int *)d.rebuild) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= k.N) return;
     scatter_node<false>(d, k, i);
@@ -177,17 +224,20 @@ __global__ void k_diag_final(DevPtrs d, int nblocks) {
 
 static inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
 
-cudaError_t launch_predict(const DevPtrs &d, const KParams &k, int vin, int advance, cudaStream_t s) {
-    k_predict<<<nblk(k.N, kBlock), kBlock, 0, s>>>(d, k, vin, advance);
+cudaError_t launch_predict(const DevPtrs &d, const KParams &k, int vin, int advance, cudaStream_t s,
+                           cudaGraphConditionalHandle cond, int use_cond) {
+    k_predict<<<nblk(k.N, kBlock), kBlock, 0, s>>>(d, k, vin, advance, cond, use_cond);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin(const DevPtrs &d, const KParams &k, cudaStream_t s) {
-    int nb = nblk(k.T, kScanTile);
-    k_scan_reduce<<<nb, kScanThreads, 0, s>>>(d.count, d.blocksums, k.T);
-    k_scan_top<<<1, kScanThreads, 0, s>>>(d.blocksums, nb);
-    k_scan_apply<<<nb, kScanThreads, 0, s>>>(d.count, d.blocksums, d.start, d.cursor, k.T, k.N);
-    k_scatter<<<nblk(k.N, kBlock), kBlock, 0, s>>>(d, k);
+cudaError_t launch_rebuild(const DevPtrs &d, const KParams &k, cudaStream_t s) {
+    const int nb = nblk(k.T, kScanTile), nn = nblk(k.N, kBlock);
+    k_bin<<<nn, kBlock, 0, s>>>(d, k);
+    k_scan_reduce<<<nb, kScanThreads, 0, s>>>(d.count, d.blocksums, k.T, d.rebuild);
+    k_scan_top<<<1, kScanThreads, 0, s>>>(d.blocksums, nb, d.rebuild);
+    k_scan_apply<<<nb, kScanThreads, 0, s>>>(d.count, d.blocksums, d.start, d.cursor, k.T, k.N, d.rebuild);
+    k_scatter<<<nn, kBlock, 0, s>>>(d, k);
+    k_build_list<<<nn, kBlock, 0, s>>>(d, k);
     return cudaGetLastError();
 }
 
@@ -259,10 +309,10 @@ cudaError_t launch_observables(const DevPtrs &d, const KParams &k, int vcur, dou
                                cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(wsum, 0, sizeof(double) * 16 * (size_t)k.n_agg, s);
     if (e != cudaSuccess) return e;
-    // positions, cells and wall cells of the current state (no advance)
-    if ((e = cudaMemsetAsync(d.count, 0, sizeof(int) * k.T, s)) != cudaSuccess) return e;
-    if ((e = launch_predict(d, k, vcur, 0, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(d.count, 0, sizeof(int) * k.T, s)) != cudaSuccess) return e;
+    // positions, cells and wall cells of the current state (no advance, forced rebuild)
+    if ((e = launch_predict(d, k, vcur, 0, s, 0, 0)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(d.rebuild, 1, sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = launch_rebuild(d, k, s)) != cudaSuccess) return e;
     k_grain_damage<<<k.G, kBlock, 0, s>>>(d, k, gdam);
     k_wall_sums<<<nblk(k.N, kBlock), kBlock, 0, s>>>(d, k, vcur, wsum);
     return cudaGetLastError();

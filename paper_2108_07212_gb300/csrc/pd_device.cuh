@@ -273,10 +273,12 @@ __device__ __forceinline__ void damping_friction32(float rd, float Kn, float rho
 // ---------------------------------------------------------------------------
 // per-node phases
 
-// Algorithm 1: u <- u + dt v + dt^2/2 a (when advancing), p = X + u, the
-// FP32-split float-float copy of the shifted position, and the node's bucket.
+// Algorithm 1: u <- u + dt v + dt^2/2 a (when advancing), p = X + u and the
+// FP32-split float-float copy of the shifted position.  Returns true when the
+// node has moved farther than kSkinTrigger * skin since the last rebuild of
+// the candidate lists (or its displacement is not finite).
 template <bool PERSIST>
-__device__ __forceinline__ void predict_node(const DevPtrs &d, const KParams &k, int i, int vin, int advance) {
+__device__ __forceinline__ bool predict_node(const DevPtrs &d, const KParams &k, int i, int vin, int advance) {
     double2 u = ldm<PERSIST>(&d.u[i]);
     const double2 v = ldm<PERSIST>(&d.v[vin][i]);
     if (d.vh) {
@@ -297,18 +299,35 @@ __device__ __forceinline__ void predict_node(const DevPtrs &d, const KParams &k,
     d.p[i] = p;
     const int ag = __ldg(&d.g_agg[__ldg(&d.grain[i])]);
     const AggParams &A = d.agg[ag];
-    int cx, cy;
     if (d.ph) {
         double qx = p.x + A.sx, qy = p.y + A.sy;
         float2 ph = make_float2((float)qx, (float)qy);
         const float2 pl = make_float2((float)(qx - (double)ph.x), (float)(qy - (double)ph.y));
         d.ph[i] = ph;
         d.pl[i] = pl;
+    }
+    // |u - u_ref| in float: its rounding (1e-7 |u|) is far below the margin
+    // (1/2 - kSkinTrigger) skin of the trigger
+    const float2 ur = ldm<PERSIST>(&d.u_ref[i]);
+    const float ex = (float)u.x - ur.x, ey = (float)u.y - ur.y;
+    return !(ex * ex + ey * ey <= A.dmax2);
+}
+
+// Rebuild, step 1: hash-grid cell and bucket of node i at its current
+// position, counted into its bucket.
+template <bool PERSIST>
+__device__ __forceinline__ void bin_node(const DevPtrs &d, const KParams &k, int i) {
+    const int ag = __ldg(&d.g_agg[__ldg(&d.grain[i])]);
+    const AggParams &A = d.agg[ag];
+    int cx, cy;
+    if (d.ph) {
         // FP32-split: the cell from the shifted float position (error below 1e-3
-        // cell; the cells of this path are 0.4 % wider than R_c to absorb it)
+        // cell; the cells of this path are 0.4 % wider to absorb it)
+        const float2 ph = ldm<PERSIST>(&d.ph[i]), pl = ldm<PERSIST>(&d.pl[i]);
         cx = cell_coord_f((ph.x - A.oxs) + pl.x, A.inv_cell_f);
         cy = cell_coord_f((ph.y - A.oys) + pl.y, A.inv_cell_f);
     } else {
+        const double2 p = ldm<PERSIST>(&d.p[i]);
         cx = cell_coord(p.x, A.ox, A.inv_cell);
         cy = cell_coord(p.y, A.oy, A.inv_cell);
     }
@@ -331,6 +350,9 @@ __device__ __forceinline__ void wall_cells(const DevPtrs &d, const KParams &k, d
     }
 }
 
+// The node cell is the one of the last rebuild: the node has moved less than
+// kSkinTrigger * skin since, and cells are wider than R_c + skin, so two cells
+// from a wall's cell still means farther than R_c from the wall.
 template <bool PERSIST>
 __device__ __forceinline__ bool far_from_walls(const DevPtrs &d, int i, int ag) {
     const int2 c = ldm<PERSIST>(&d.cell[i]);
@@ -355,65 +377,72 @@ __device__ __forceinline__ void scatter_node(const DevPtrs &d, const KParams &k,
     d.srec[pos] = rec;
 }
 
-// Gather the contact candidates S^nbr of node i (all nodes y != i of the same
-// aggregate with |p(y) - p(i)| < R_c) from the hash-grid
-// cells lane, lane + LANES, ... of the 3x3 block, in ascending node index.
-// DIST(j) returns true when j is within R_c.
-template <bool PERSIST, int LANES, class Dist>
-__device__ __forceinline__ int gather_candidates(const DevPtrs &d, const KParams &k, int ag, int i, int lane,
-                                                 bool active, int *cand, Dist within) {
-    int nc = 0;
-    if (!active) return 0;
-    const int2 cc = ldm<PERSIST>(&d.cell[i]);      // cell of node i, from the binning phase
-    // cells lane, lane + LANES, ... of the 3x3 block, staged S at a time: first
-    // all bucket ranges, then the first record of every bucket, then the rest,
-    // so that the dependent loads of several cells are in flight together
-    constexpr int MC = (9 + LANES - 1) / LANES;
-    constexpr int S = MC < 3 ? MC : 3;
+// Rebuild, last step: the candidate list of node i -- every node y != i of
+// its aggregate with |p(y) - p(i)| < R_c + skin, gathered from the 3x3 block
+// of hash-grid cells around its cell (cells are wider than R_c + skin) and
+// kept in ascending node index -- and the displacement it was built at.  The
+// bucket records hold the positions in bucket order, so only nodes inside
+// the radius are looked up.
+template <bool PERSIST>
+__device__ __forceinline__ void build_list_node(const DevPtrs &d, const KParams &k, int i) {
+    const int ag = __ldg(&d.g_agg[__ldg(&d.grain[i])]);
+    const AggParams &A = d.agg[ag];
+    const int2 cc = ldm<PERSIST>(&d.cell[i]);
+    unsigned bk[9];
 #pragma unroll
-    for (int m0 = 0; m0 < MC; m0 += S) {
-        int t0[S], t1[S];
+    for (int c = 0; c < 9; ++c) bk[c] = cell_bucket(cc.x + (c % 3) - 1, cc.y + (c / 3) - 1, ag, k.T);
+    float pix, piy;
+    double2 pi = make_double2(0.0, 0.0);
+    if (d.ph) {
+        const float2 ph = ldm<PERSIST>(&d.ph[i]);
+        pix = ph.x;
+        piy = ph.y;
+    } else {
+        pi = ldm<PERSIST>(&d.p[i]);
+        pix = piy = 0.f;
+    }
+    const float2 pli = d.ph ? ldm<PERSIST>(&d.pl[i]) : make_float2(0.f, 0.f);
+    int lst[kMaxList];
+    int n = 0, over = 0;
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const int c = lane + (m0 + s) * LANES;
-            t0[s] = 0;
-            t1[s] = 0;
-            if (m0 + s < MC && c < 9) {
-                const unsigned bc = cell_bucket(cc.x + (c % 3) - 1, cc.y + (c / 3) - 1, ag, k.T);
-                bool dup = false;      // two cells of the block hashed to one bucket: visit it once
-                for (int q = 0; q < c; ++q) dup |= cell_bucket(cc.x + (q % 3) - 1, cc.y + (q / 3) - 1, ag, k.T) == bc;
-                if (!dup) {
-                    t0[s] = ldm<PERSIST>(&d.start[bc]);
-                    t1[s] = ldm<PERSIST>(&d.start[bc + 1]);
-                }
+    for (int c = 0; c < 9; ++c) {
+        bool dup = false;      // two cells of the block hashed to one bucket: visit it once
+#pragma unroll
+        for (int q = 0; q < c; ++q) dup |= bk[q] == bk[c];
+        if (dup) continue;
+        const int t0 = ldm<PERSIST>(&d.start[bk[c]]), t1 = ldm<PERSIST>(&d.start[bk[c] + 1]);
+        for (int t = t0; t < t1; ++t) {
+            const uint4 rec = ldm<PERSIST>(&d.srec[t]);
+            float dx, dy;
+            if (d.ph) {
+                dx = (__uint_as_float(rec.x) - pix) + (__uint_as_float(rec.z) - pli.x);
+                dy = (__uint_as_float(rec.y) - piy) + (__uint_as_float(rec.w) - pli.y);
+            } else {
+                dx = (float)(__hiloint2double((int)rec.y, (int)rec.x) - pi.x);
+                dy = (float)(__hiloint2double((int)rec.w, (int)rec.z) - pi.y);
             }
-        }
-        uint4 first[S];
-#pragma unroll
-        for (int s = 0; s < S; ++s) first[s] = t0[s] < t1[s] ? ldm<PERSIST>(&d.srec[t0[s]]) : make_uint4(0, 0, 0, 0);
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            for (int t = t0[s]; t < t1[s]; ++t) {
-                // the bucket's positions are stored in bucket order: the distance test
-                // needs no index chase; only nodes within R_c are looked up
-                if (!within(t == t0[s] ? first[s] : ldm<PERSIST>(&d.srec[t]))) continue;
-                const int j = ldm<PERSIST>(&d.sorted[t]);
-                // hash aliasing can bring nodes of another aggregate: never in contact
-                if (j == i || __ldg(&d.g_agg[__ldg(&d.grain[j])]) != ag) continue;
-                if (nc < kMaxCand) {
-                    int w = nc++;
-                    while (w > 0 && cand[w - 1] > j) {
-                        cand[w] = cand[w - 1];
-                        --w;
-                    }
-                    cand[w] = j;
-                } else {
-                    atomicAdd(&d.status[PD_STATUS_OVERFLOW], 1);
+            if (!(dx * dx + dy * dy < A.rs2)) continue;
+            const int j = ldm<PERSIST>(&d.sorted[t]);
+            // hash aliasing can bring nodes of another aggregate: never in contact
+            if (j == i || __ldg(&d.g_agg[__ldg(&d.grain[j])]) != ag) continue;
+            if (n < kMaxList) {
+                int w = n++;
+                while (w > 0 && lst[w - 1] > j) {
+                    lst[w] = lst[w - 1];
+                    --w;
                 }
+                lst[w] = j;
+            } else {
+                over = 1;
             }
         }
     }
-    return nc;
+    const size_t N = (size_t)k.N;
+    for (int q = 0; q < n; ++q) d.nbr[q * N + i] = lst[q];
+    d.nbr_cnt[i] = n;
+    const double2 u = ldm<PERSIST>(&d.u[i]);
+    d.u_ref[i] = make_float2((float)u.x, (float)u.y);
+    if (over) atomicAdd(&d.status[PD_STATUS_OVERFLOW], 1);
 }
 
 // Is the bond x -> j intact?  (row columns ascending: binary search; broken
@@ -545,21 +574,19 @@ __device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k,
     }
     __syncwarp();
 
-    // contact candidates, self-contact (Sec. 4.4), inter-grain contact (Secs. 4.1-4.3)
-    int cand[kMaxCand];
+    // contact candidates (the node's list: every pair closer than R_c is in it,
+    // ascending node index), self-contact (Sec. 4.4), inter-grain contact
+    // (Secs. 4.1-4.3)
     const double Rc = A.Rc;
-    const int nc = gather_candidates<PERSIST, LANES>(d, k, ag, ii, lane, active, cand, [&](uint4 rec) {
-        const double2 pj = make_double2(__hiloint2double((int)rec.y, (int)rec.x), __hiloint2double((int)rec.w, (int)rec.z));
-        double dx = pj.x - pi.x, dy = pj.y - pi.y;
-        return sqrt(dx * dx + dy * dy) < Rc;
-    });
+    const int nc = active ? ldm<PERSIST>(&d.nbr_cnt[ii]) : 0;
     const double2 vi = ldm<PERSIST>(&d.v[vin][ii]);
     double Fsx = 0.0, Fsy = 0.0, Fnx = 0.0, Fny = 0.0;
-    for (int q = 0; q < nc; ++q) {
-        const int j = cand[q];
+    for (int q = lane; q < nc; q += LANES) {
+        const int j = ldm<PERSIST>(&d.nbr[(size_t)q * k.N + ii]);
         const double2 pj = ldm<PERSIST>(&d.p[j]);
         double dx = pj.x - pi.x, dy = pj.y - pi.y;
         double dd = sqrt(dx * dx + dy * dy);
+        if (!(dd < Rc)) continue;
         if (dd == 0.0) {
             atomicAdd(&d.status[PD_STATUS_COINCIDENT], 1);
             continue;
@@ -726,25 +753,21 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
     }
     __syncwarp();
 
-    int cand[kMaxCand];
-    const int nc = gather_candidates<PERSIST, LANES>(d, k, ag, ii, lane, active, cand, [&](uint4 rec) {
-        const float2 phj = make_float2(__uint_as_float(rec.x), __uint_as_float(rec.y));
-        const float2 plj = make_float2(__uint_as_float(rec.z), __uint_as_float(rec.w));
-        float L2h, L2l;
-        len2_ff(__fsub_rn(phj.x, phi.x), plj.x - pli.x, __fsub_rn(phj.y, phi.y), plj.y - pli.y, L2h, L2l);
-        return ff_diff(A.rc2_hi, A.rc2_lo, L2h, L2l) > 0.f;
-    });
-    // start-of-step velocity as a float-float pair (written by the binning phase)
+    // contact candidates from the node's list (ascending node index); the
+    // R_c test is exact in float-float
+    const int nc = active ? ldm<PERSIST>(&d.nbr_cnt[ii]) : 0;
+    // start-of-step velocity as a float-float pair (written by the displacement update)
     const float2 vhi = ldm<PERSIST>(&d.vh[ii]), vli = ldm<PERSIST>(&d.vl[ii]);
     const float rd = k.rdf, rho = k.rhof, dt = k.dtf, mu = k.muf;
     float Fsx = 0.f, Fsy = 0.f, Fnx = 0.f, Fny = 0.f;
-    for (int q = 0; q < nc; ++q) {
-        const int j = cand[q];
+    for (int q = lane; q < nc; q += LANES) {
+        const int j = ldm<PERSIST>(&d.nbr[(size_t)q * k.N + ii]);
         const float2 phj = ldm<PERSIST>(&d.ph[j]), plj = ldm<PERSIST>(&d.pl[j]);
         const float dxh = __fsub_rn(phj.x, phi.x), dxl = plj.x - pli.x;
         const float dyh = __fsub_rn(phj.y, phi.y), dyl = plj.y - pli.y;
         float L2h, L2l;
         len2_ff(dxh, dxl, dyh, dyl, L2h, L2l);
+        if (!(ff_diff(A.rc2_hi, A.rc2_lo, L2h, L2l) > 0.f)) continue;
         const float dd = sqrtf(L2h);
         if (dd == 0.f) {
             atomicAdd(&d.status[PD_STATUS_COINCIDENT], 1);

@@ -204,6 +204,7 @@ struct pd_ctx {
     int vcur = 0;
     int64_t steps_done = 0;
     cudaStream_t capture_stream = nullptr;
+    cudaStream_t body_stream = nullptr;    // captures the bodies of the rebuild conditionals
     cudaGraphExec_t chunk[2] = {nullptr, nullptr};
     cudaGraphExec_t single[2] = {nullptr, nullptr};
     cudaGraphExec_t timed[2] = {nullptr, nullptr};
@@ -247,9 +248,13 @@ void compute_aggregates(pd_ctx *c) {
         A.wv[0] = w[4]; A.wv[1] = w[5]; A.wv[2] = w[6]; A.wv[3] = w[7];
         A.ox = w[0];
         A.oy = w[2];
-        // a hair above R_c: two nodes closer than R_c never land two cells apart
-        // (FP32 split: 0.4 % above, the margin of its float cell coordinates)
-        A.cell = A.Rc * (p.precision == PD_FP32_SPLIT ? 1.004 : 1.0 + 1e-9);
+        // candidate lists of radius R_c + skin: a hair above it, two nodes closer
+        // than R_c + skin never land two cells apart (FP32 split: 0.4 % above,
+        // the margin of its float cell coordinates)
+        const double skin = pd::kSkinRatio * A.Rc;
+        A.cell = (A.Rc + skin) * (p.precision == PD_FP32_SPLIT ? 1.004 : 1.0 + 1e-9);
+        A.rs2 = (float)((A.Rc + skin) * (A.Rc + skin));
+        A.dmax2 = (float)(pd::kSkinTrigger * skin * pd::kSkinTrigger * skin);
         A.inv_cell = 1.0 / A.cell;
         // FP32 split: shift coordinates of the box into [L, 2L) so nearby
         // positions share a binade and their float differences are exact
@@ -342,6 +347,11 @@ size_t layout(pd_ctx *c, char *base) {
     carve(base, off, d.cursor, c->T);
     carve(base, off, d.sorted, N);
     carve(base, off, d.srec, N);
+    carve(base, off, d.nbr_cnt, N);
+    carve(base, off, d.nbr, N * (size_t)pd::kMaxList);
+    carve(base, off, d.u_ref, N);
+    carve(base, off, d.rebuild, 1);
+    carve(base, off, d.pred_done, 1);
     carve(base, off, d.fsum, 6 * N * (c->prm.precision == PD_FP32_SPLIT ? 4 : 8));
     // block sums of the scan: one per scan tile (multi-kernel path) or per
     // block of the persistent kernel (at most 16 blocks per SM)
@@ -451,16 +461,46 @@ cudaError_t record_surrogate(pd_ctx *c, cudaStream_t s) {
     return pd::launch_sur_expand_tc(c->d, c->kp, s);
 }
 
-// Record one time step (Algorithm 1) on stream s: displacement update and
-// positions, contact binning, forces + acceleration + velocity update.  With
-// `timed`, event records bracket the three kernel groups.
+// Record one time step (Algorithm 1) on the capturing stream s: displacement
+// update and positions, the rebuild of the contact candidate lists as the
+// body of a conditional node (run only when the displacement update raised
+// the rebuild flag), forces + acceleration + velocity update.  With `timed`,
+// event records bracket the three kernel groups.
 cudaError_t record_step(pd_ctx *c, int vin, cudaStream_t s, bool timed = false) {
     cudaError_t e;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g)) != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive || !g) return cudaErrorStreamCaptureUnmatched;
+    cudaGraphConditionalHandle cond;
+    if ((e = cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(c->d.count, 0, sizeof(int) * c->T, s)) != cudaSuccess) return e;
-    if ((e = pd::launch_predict(c->d, c->kp, vin, 1, s)) != cudaSuccess) return e;
+    if ((e = pd::launch_predict(c->d, c->kp, vin, 1, s, cond, 1)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal)) != cudaSuccess) return e;
-    if ((e = pd::launch_bin(c->d, c->kp, s)) != cudaSuccess) return e;
+    {
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd)) != cudaSuccess) return e;
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        if ((e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np)) != cudaSuccess) return e;
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        if ((e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaStreamBeginCaptureToGraph(c->body_stream, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return e;
+        const cudaError_t eb = pd::launch_rebuild(c->d, c->kp, c->body_stream);
+        cudaGraph_t done = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(c->body_stream, &done);
+        if (eb != cudaSuccess) return eb;
+        if (ee != cudaSuccess) return ee;
+    }
     if (c->kp.sur && (e = record_surrogate(c, s)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     if ((e = pd::launch_force(c->d, c->kp, vin, 1, s)) != cudaSuccess) return e;
@@ -469,12 +509,11 @@ cudaError_t record_step(pd_ctx *c, int vin, cudaStream_t s, bool timed = false) 
     return cudaSuccess;
 }
 
-// nsteps time steps as one persistent cooperative launch (bucket counts
-// cleared first); timing brackets the whole launch as the force group.
+// nsteps time steps as one persistent cooperative launch; timing brackets the
+// whole launch as the force group.
 cudaError_t record_persistent(pd_ctx *c, int vin, int nsteps, cudaStream_t s, bool timed = false) {
     cudaError_t e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(c->d.count, 0, sizeof(int) * c->T, s)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     if ((e = pd::launch_persistent(c->d, c->kp, vin, nsteps, c->block, s)) != cudaSuccess) return e;
@@ -578,6 +617,7 @@ int pd_destroy(pd_ctx *c) {
         for (auto &e : c->ev)
             if (e) cudaEventDestroy(e);
         if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+        if (c->body_stream) cudaStreamDestroy(c->body_stream);
     }
     delete c;
     return PD_OK;
@@ -879,6 +919,12 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     PD_CUDA(cudaMemcpyAsync(d.agg, c->aggp.data(), sizeof(pd::AggParams) * c->aggp.size(), cudaMemcpyHostToDevice, s));
     PD_CUDA(cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), s));
     PD_CUDA(cudaMemsetAsync(d.t_now, 0, sizeof(double), s));
+    // bucket counts are zero between rebuilds; the first force evaluation rebuilds
+    PD_CUDA(cudaMemsetAsync(d.count, 0, sizeof(int) * c->T, s));
+    PD_CUDA(cudaMemsetAsync(d.nbr_cnt, 0, 4 * N, s));
+    PD_CUDA(cudaMemsetAsync(d.u_ref, 0, 8 * N, s));
+    PD_CUDA(cudaMemsetAsync(d.rebuild, 1, sizeof(int), s));
+    PD_CUDA(cudaMemsetAsync(d.pred_done, 0, sizeof(unsigned), s));
     std::vector<int32_t> gstart32(c->g_start.begin(), c->g_start.end()), tnode, tslot;
     PD_CUDA(cudaMemcpyAsync(d.g_start, gstart32.data(), 4 * (G + 1), cudaMemcpyHostToDevice, s));
     std::vector<float> fc;
@@ -977,6 +1023,7 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     PD_CUDA(cudaStreamSynchronize(s));
     // capture the step graphs on a private stream (the caller's may be the legacy stream)
     PD_CUDA(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    PD_CUDA(cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking));
     for (auto &e : c->ev) PD_CUDA(cudaEventCreate(&e));
     return capture_all(c);
 }
@@ -984,9 +1031,9 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
 int pd_eval_forces(pd_ctx *c) {
     if (int r = check_ctx(c, 3)) return r;
     cudaStream_t s = c->stream;
-    PD_CUDA(cudaMemsetAsync(c->d.count, 0, sizeof(int) * c->T, s));
-    PD_CUDA(pd::launch_predict(c->d, c->kp, c->vcur, 0, s));
-    PD_CUDA(pd::launch_bin(c->d, c->kp, s));
+    PD_CUDA(pd::launch_predict(c->d, c->kp, c->vcur, 0, s, 0, 0));
+    PD_CUDA(cudaMemsetAsync(c->d.rebuild, 1, sizeof(int), s));     // fresh candidate lists
+    PD_CUDA(pd::launch_rebuild(c->d, c->kp, s));
     if (c->kp.sur) PD_CUDA(record_surrogate(c, s));
     PD_CUDA(pd::launch_force(c->d, c->kp, c->vcur, 0, s));
     return PD_OK;

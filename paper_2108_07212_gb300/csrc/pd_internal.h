@@ -7,8 +7,14 @@
 
 namespace pd {
 
-// Upper bound on contact candidates (nodes within R_c) gathered per lane.
-constexpr int kMaxCand = 16;
+// Contact candidate list (Verlet list with a skin): every node keeps the nodes
+// y of its aggregate with |p(y) - p(x)| < R_c + skin at the last rebuild, at
+// most kMaxList of them, in ascending index.  A rebuild runs when some node
+// has moved more than kSkinTrigger * skin since the last one, so every pair
+// closer than R_c is always in the list (the force phase tests R_c exactly).
+constexpr int kMaxList = 24;
+constexpr double kSkinRatio = 0.05;     // skin = kSkinRatio * R_c
+constexpr double kSkinTrigger = 0.45;   // < 1/2: margin for the float displacement test
 // Threads per block of the node-parallel multi-kernel path.
 constexpr int kBlock = 128;
 // Scan tile: threads x items per thread.
@@ -30,6 +36,8 @@ struct AggParams {
     float rc2_hi, rc2_lo;  // R_c^2 as a float-float pair
     float rcf, knf;        // R_c and K_n as floats
     float oxs, oys, inv_cell_f;  // FP32 split: grid origin in shifted coordinates, 1 / cell
+    float rs2;             // (R_c + skin)^2 as a float: radius of the candidate lists
+    float dmax2;           // (kSkinTrigger skin)^2: displacement since the last rebuild that triggers the next
 };
 
 // Device pointers carved out of the caller's arena.
@@ -48,7 +56,13 @@ struct DevPtrs {
     AggParams *agg;
     // contact hash grid (T buckets)
     int *key, *count, *start, *cursor, *sorted, *blocksums;
-    int2 *cell;         // hash-grid cell (x, y) of every node, written by the binning phase
+    int2 *cell;         // hash-grid cell (x, y) of every node at the last rebuild
+    // contact candidate lists (rebuilt when a node has moved kSkinTrigger * skin)
+    int *nbr_cnt;       // list length of every node
+    int *nbr;           // list entry q of node i at nbr[q N + i] (kMaxList slots), ascending node index
+    float2 *u_ref;      // displacement of every node at the last rebuild
+    int *rebuild;       // nonzero: rebuild the lists before the next force phase (cleared by the force phase)
+    unsigned *pred_done;  // blocks of the displacement update that have finished (last-block election)
     uint4 *srec;        // position of sorted[t] in bucket order: FP32 split (ph, pl), FP64 p (16 bytes)
     void *fsum;         // split force phase: per-node lane sums, six components of N floats (FP32) or doubles
     // globals
@@ -167,8 +181,13 @@ cudaError_t mlp_init_attributes();
 int set_error(int code, const char *msg);
 
 // Launch wrappers (stream-ordered, capture-safe).
-cudaError_t launch_predict(const DevPtrs &d, const KParams &k, int vin, int advance, cudaStream_t s);
-cudaError_t launch_bin(const DevPtrs &d, const KParams &k, cudaStream_t s);
+// Displacement update and positions; with use_cond, the last block sets the
+// graph conditional `cond` to the rebuild flag.
+cudaError_t launch_predict(const DevPtrs &d, const KParams &k, int vin, int advance, cudaStream_t s,
+                           cudaGraphConditionalHandle cond, int use_cond);
+// Rebuild of the contact candidate lists (kernels return at once when the
+// rebuild flag is clear).
+cudaError_t launch_rebuild(const DevPtrs &d, const KParams &k, cudaStream_t s);
 cudaError_t launch_force(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s);
 cudaError_t launch_force64(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s);
 cudaError_t launch_force32(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s);

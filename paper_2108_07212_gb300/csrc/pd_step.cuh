@@ -32,9 +32,16 @@ __device__ __forceinline__ void force_block(const DevPtrs &d, const KParams &k, 
     __syncthreads();
 }
 
+// The force phase reads the candidate lists of this step: it clears the
+// rebuild flag for the next one.
+__device__ __forceinline__ void clear_rebuild(const DevPtrs &d) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d.rebuild = 0;
+}
+
 // Multi-kernel path: one block per BLOCK / LANES nodes.
 template <bool FP32, int LANES>
 __global__ void __launch_bounds__(kBlock, FP32 ? 5 : 4) k_force(DevPtrs d, KParams k, int vin, int update_v) {
+    clear_rebuild(d);
     force_block<FP32, false, LANES, kBlock>(d, k, blockIdx.x * (kBlock / LANES), vin, update_v);
 }
 
@@ -81,6 +88,7 @@ __device__ __forceinline__ void epilogue_node(const DevPtrs &d, const KParams &k
 
 template <bool FP32, int LANES>
 __global__ void __launch_bounds__(kBlock, FP32 ? 6 : 4) k_sums(DevPtrs d, KParams k, int vin) {
+    clear_rebuild(d);
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     sums_node<FP32, false, LANES>(d, k, tid / LANES, tid % LANES, vin);
 }
@@ -198,12 +206,15 @@ __device__ __forceinline__ int block_scan1(int &v, int *sm) {
 }
 
 // All phases of nsteps time steps in one cooperative launch:
-//   A  displacement update, positions, bucket counts      (Algorithm 1)
-//   B  per-block sums of the bucket counts
-//   C  exclusive scan of the counts -> cell starts
-//   D  counting-sort scatter of the node indices
-//   E  forces, acceleration and velocity update; bucket counts cleared
-// Bucket counts must be zero on entry (the host clears them before a launch).
+//   A  displacement update, positions, rebuild test       (Algorithm 1)
+//   when some node moved kSkinTrigger * skin since the last rebuild:
+//     R1 bucket counts
+//     R2 per-block sums of the bucket counts
+//     R3 exclusive scan of the counts -> cell starts (counts cleared)
+//     R4 counting-sort scatter of the node indices
+//     R5 candidate lists
+//   E  forces, acceleration and velocity update
+// Bucket counts are zero on entry and on exit.
 template <bool FP32, int LANES, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_persistent(DevPtrs d, KParams k, int vin, int nsteps) {
     __shared__ int sm[33];
@@ -220,33 +231,48 @@ __global__ void __launch_bounds__(BLOCK) k_persistent(DevPtrs d, KParams k, int 
             *d.t_now = (double)s * k.dt;
             wall_cells(d, k, (double)s * k.dt);
         }
-        for (int i = gtid; i < k.N; i += nthreads) predict_node<true>(d, k, i, vin, 1);
+        bool need = false;
+        for (int i = gtid; i < k.N; i += nthreads) need |= predict_node<true>(d, k, i, vin, 1);
+        if (__any_sync(0xffffffffu, need) && (threadIdx.x & 31) == 0) *(volatile int *)d.rebuild = 1;
         if (!grid_barrier(d)) return;
-        // B
-        int part = 0;
-        for (unsigned b = lo + threadIdx.x; b < hi; b += BLOCK) part += __ldcg(&d.count[b]);
-        part = block_sum<BLOCK>(part, sm);
-        if (threadIdx.x == 0) d.blocksums[blockIdx.x] = part;
-        if (!grid_barrier(d)) return;
-        // C
-        int off = 0;
-        for (int b = threadIdx.x; b < (int)blockIdx.x; b += BLOCK) off += __ldcg(&d.blocksums[b]);
-        off = block_sum<BLOCK>(off, sm);
-        for (unsigned b0 = lo; b0 < hi; b0 += BLOCK) {
-            const unsigned b = b0 + threadIdx.x;
-            int c = (b < hi) ? __ldcg(&d.count[b]) : 0;
-            const int tot = block_scan1<BLOCK>(c, sm);
-            if (b < hi) {
-                d.start[b] = off + c;
-                d.cursor[b] = off + c;
+        if (__ldcg(d.rebuild)) {
+            // R1
+            for (int i = gtid; i < k.N; i += nthreads) bin_node<true>(d, k, i);
+            if (!grid_barrier(d)) return;
+            // R2
+            int part = 0;
+            for (unsigned b = lo + threadIdx.x; b < hi; b += BLOCK) part += __ldcg(&d.count[b]);
+            part = block_sum<BLOCK>(part, sm);
+            if (threadIdx.x == 0) d.blocksums[blockIdx.x] = part;
+            if (!grid_barrier(d)) return;
+            // R3
+            int off = 0;
+            for (int b = threadIdx.x; b < (int)blockIdx.x; b += BLOCK) off += __ldcg(&d.blocksums[b]);
+            off = block_sum<BLOCK>(off, sm);
+            for (unsigned b0 = lo; b0 < hi; b0 += BLOCK) {
+                const unsigned b = b0 + threadIdx.x;
+                int c = (b < hi) ? __ldcg(&d.count[b]) : 0;
+                if (b < hi) d.count[b] = 0;
+                const int tot = block_scan1<BLOCK>(c, sm);
+                if (b < hi) {
+                    d.start[b] = off + c;
+                    d.cursor[b] = off + c;
+                }
+                off += tot;
             }
-            off += tot;
+            if (gtid == 0) d.start[T] = k.N;
+            if (!grid_barrier(d)) return;
+            // R4
+            for (int i = gtid; i < k.N; i += nthreads) scatter_node<true>(d, k, i);
+            if (!grid_barrier(d)) return;
+            // R5 (every block has read the flag: clear it for the next step)
+            if (gtid == 0) {
+                *d.rebuild = 0;
+                atomicAdd(&d.status[PD_STATUS_REBUILDS], 1);
+            }
+            for (int i = gtid; i < k.N; i += nthreads) build_list_node<true>(d, k, i);
+            if (!grid_barrier(d)) return;
         }
-        if (gtid == 0) d.start[T] = k.N;
-        if (!grid_barrier(d)) return;
-        // D
-        for (int i = gtid; i < k.N; i += nthreads) scatter_node<true>(d, k, i);
-        if (!grid_barrier(d)) return;
         // E
         if (k.split) {
             const long long total = (((long long)LANES * k.N + 31) / 32) * 32;
@@ -257,7 +283,6 @@ __global__ void __launch_bounds__(BLOCK) k_persistent(DevPtrs d, KParams k, int 
             for (int node0 = blockIdx.x * (BLOCK / LANES); node0 < k.N; node0 += gridDim.x * (BLOCK / LANES))
                 force_block<FP32, true, LANES, BLOCK>(d, k, node0, vin, 1);
         }
-        for (unsigned b = gtid; b < T; b += nthreads) d.count[b] = 0;
         if (!grid_barrier(d)) return;
         vin ^= 1;
     }
