@@ -270,30 +270,19 @@ def precision_report(B, dev, stream, torch):
 BYTES_PER_NODE_STEP_FP32 = 196
 
 
-# DRAM bytes (read + write) per launch of the force-phase kernels on the
-# settling50 workload, from one ncu capture of
-#   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -c 3000
-#       --csv python bench.py --steps 20 --warmup 3 --legs= --no-cpu
-# (ncu flushes caches before every launch, as the bench flushes L2 before every
-# step; medians over the launches; profiles/traffic_settling50.md).  They hold
-# while the kernel sources hash to TRAFFIC_DIGEST; otherwise traffic is null.
+# DRAM bytes (read + write) per launch of the step kernels on the settling50
+# workload, from one ncu capture of the timed steps (the bench marks them with
+# cudaProfilerStart/Stop):
+#   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+#       --profile-from-start off -c 2000 --csv python bench.py --steps 50 --warmup 3 --legs= --no-cpu
+# (L2 flushed before every step as in the bench; medians over the launches;
+# profiles/traffic_settling50.md).  They hold while the kernel sources hash to
+# TRAFFIC_DIGEST; otherwise, or for a variant not captured, traffic is null.
 TRAFFIC_SETTLING50 = {
-    "k_epilogue<0>": 2363136,
-    "k_epilogue<1>": 1566720,
-    "k_force<0, 4>": 7299840,
-    "k_force<0, 8>": 7300992,
-    "k_force<1, 4>": 3966208,
-    "k_force<1, 8>": 3966464,
-    "k_sums<0, 1>": 6641408,
-    "k_sums<0, 2>": 6654592,
-    "k_sums<0, 4>": 6652672,
-    "k_sums<0, 8>": 6651776,
-    "k_sums<1, 1>": 3146752,
-    "k_sums<1, 2>": 3156096,
-    "k_sums<1, 4>": 3153152,
-    "k_sums<1, 8>": 3152000,
+    "k_persistent<1, 4, 128>": 3579392,
+    "k_persistent<0, 4, 128>": 6918144,
 }
-TRAFFIC_DIGEST = "b3ce2e9b4bc361a509a7a4de04a911056aa030c4"
+TRAFFIC_DIGEST = "27415c17631c242c5897cd580370d5bf7f046b69"
 TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu", "pd_common.cu", "pd_internal.h")
 
 
@@ -316,7 +305,7 @@ def force_phase_traffic(path: dict, fp32: bool, workload: str):
     if m & 1:
         names = [f"k_persistent<{p}, {l}, {path.get('block', 128)}>"]     # the whole step
     else:
-        names = [f"k_sums<{p}, {l}>", f"k_epilogue<{p}>"] if m >> 1 else [f"k_force<{p}, {l}>"]
+        names = [f"k_sums<{p}, {l}>", f"k_epilogue<{p}>"] if (m >> 1) & 1 else [f"k_force<{p}, {l}>"]
     if not all(n in TRAFFIC_SETTLING50 for n in names):
         return None
     return float(sum(TRAFFIC_SETTLING50[n] for n in names))
@@ -327,7 +316,7 @@ def _force_kernels(mode: int, fp32: bool) -> str:
     p = "1" if fp32 else "0"
     if mode & 1:
         return f"k_persistent<{p},...> (whole step)"
-    return f"k_sums<{p},...> + k_epilogue<{p}>" if mode >> 1 else f"k_force<{p},...>"
+    return f"k_sums<{p},...> + k_epilogue<{p}>" if (mode >> 1) & 1 else f"k_force<{p},...>"
 
 
 def _launches(mode: int, steps: int, rebuilds: int) -> int:
@@ -337,7 +326,9 @@ def _launches(mode: int, steps: int, rebuilds: int) -> int:
     node ran them; the persistent kernel is one launch per step."""
     if mode & 1:
         return steps
-    return steps * (2 + (mode >> 1)) + 6 * rebuilds
+    if mode & 4:      # rebuild kernels launched every step
+        return steps * (8 + ((mode >> 1) & 1))
+    return steps * (2 + ((mode >> 1) & 1)) + 6 * rebuilds
 
 
 def _event_time(stream, torch, fn):
@@ -438,7 +429,7 @@ def leg_ensemble(B, I, dev, stream, torch, hbm, steps=40):
            "nodes": N, "directed_bonds": int(sim.n_bonds),
            "batched": {"value": N * steps / dt, "unit": "node-steps/s", "ms_per_step": 1e3 * dt / steps,
                        "path": {"mode": "persistent" if int(info["mode"]) & 1 else "kernel graph",
-                                "split_force_phase": bool(int(info["mode"]) >> 1),
+                                "split_force_phase": bool((int(info["mode"]) >> 1) & 1),
                                 "lanes": int(info["lanes"]), "block": int(info["block"])},
                        "autotune": tune, "status": int(sim.status()[0])}}
     # the same batch as one persistent cooperative launch per 16 steps (best of its block sizes)
@@ -582,6 +573,13 @@ def run_ours(args):
             inf = x.info()
             return {"mode": int(inf["mode"]), "lanes": int(inf["lanes"]), "block": int(inf["block"]), "fixed": True}
         return x.autotune()
+    # the timed window starts mid-run (steps advance..advance+steps of the
+    # 20,000-step settling), where the grains move and collide and the contact
+    # lists are rebuilt as often as they are in a whole run
+    if args.advance:
+        sim.step(args.advance)
+        if sim64 is not None:
+            sim64.step(args.advance)
     tuned = {"fp32" if prec != B.PD_FP64 else "fp64": pick(sim)}
     if sim64 is not None:
         tuned["fp64"] = pick(sim64)
@@ -664,6 +662,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": describe(w, sim, args) | {"precision": "fp64" if prec == B.PD_FP64 else "fp32 split (FP32 forces, FP64 integration)",
                                       "l2": "flushed (256 MB write) before every timed step",
+                                      "window": f"steps {args.advance}..{args.advance + args.steps} of the run",
                                       "ranks": "independent seeded aggregates per rank",
                                       "step_path": tuned},
         "bond_evals_per_s": bond_evals,
@@ -722,6 +721,8 @@ def main():
                     help="comma-separated large-workload legs at N=1 ('' for none)")
     ap.add_argument("--workload", default="settling50", choices=sorted(WORKLOADS),
                     help="workload of the main line (settling50 is the benchmark configuration)")
+    ap.add_argument("--advance", type=int, default=10000,
+                    help="untimed steps before the timed window (the window starts mid-run)")
     ap.add_argument("--path", default="", help="fix the step path: MODE,LANES[,BLOCK] (pd_set_path) instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:

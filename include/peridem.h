@@ -254,7 +254,7 @@ int pd_set_aggregates(pd_ctx *ctx, int n_agg, const int32_t *grain_agg, const do
  * Autotuner: time candidate step paths on the current state -- a graph of
  * separate kernels or one persistent cooperative kernel per 16 steps, each with
  * the force phase fused (4 or 8 threads per node) or split (1, 2, 4 or 8),
- * pd_set_path modes 0-3 (threads per node fixed when pd_params.lanes is
+ * pd_set_path modes 0-4 and 6 (threads per node fixed when pd_params.lanes is
  * nonzero), 128 or 256 threads per persistent block -- pick the fastest, and
  * re-capture the step graphs.  The
  * state is saved and restored around the trials, so the simulation does not
@@ -267,8 +267,12 @@ int pd_autotune(pd_ctx *ctx, double *report);
 /* Select the step path explicitly (instead of pd_autotune): mode 0 = graph of
  * separate kernels, 1 = persistent cooperative kernel, 2 and 3 = the same with
  * the force phase split in two passes (lane sums through device memory, then
- * walls and update one thread per node); lanes 1, 2, 4 or 8 threads per node
- * (1 = textbook summation order); block 128 or 256 threads (persistent
+ * walls and update one thread per node); modes 4-7 = modes 0-3 with the
+ * candidate-list rebuild kernels launched every step (returning at once when no
+ * rebuild is due) instead of behind a conditional graph node (same results;
+ * the persistent kernel ignores this bit; profilers that cannot trace kernels
+ * of graphs with conditional nodes need it); lanes 1, 2, 4 or 8 threads per
+ * node (1 = textbook summation order); block 128 or 256 threads (persistent
  * kernel).  The default path is mode 2 with 4 threads per node.  Re-captures
  * the step graphs.  Errors: PD_ESTATE, PD_EINVAL, PD_ECUDA. */
 int pd_set_path(pd_ctx *ctx, int mode, int lanes, int block);

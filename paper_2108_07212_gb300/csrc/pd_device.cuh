@@ -281,11 +281,10 @@ template <bool PERSIST>
 __device__ __forceinline__ bool predict_node(const DevPtrs &d, const KParams &k, int i, int vin, int advance) {
     double2 u = ldm<PERSIST>(&d.u[i]);
     const double2 v = ldm<PERSIST>(&d.v[vin][i]);
-    if (d.vh) {
+    if (d.vq) {
         // FP32 split: the start-of-step velocity as a float-float pair for the contact laws
-        const float2 h = make_float2((float)v.x, (float)v.y);
-        d.vh[i] = h;
-        d.vl[i] = make_float2((float)(v.x - (double)h.x), (float)(v.y - (double)h.y));
+        const float hx = (float)v.x, hy = (float)v.y;
+        d.vq[i] = make_float4(hx, hy, (float)(v.x - (double)hx), (float)(v.y - (double)hy));
     }
     if (advance) {
         // explicit round-to-nearest operations: never contracted into FMAs
@@ -299,12 +298,10 @@ __device__ __forceinline__ bool predict_node(const DevPtrs &d, const KParams &k,
     d.p[i] = p;
     const int ag = __ldg(&d.g_agg[__ldg(&d.grain[i])]);
     const AggParams &A = d.agg[ag];
-    if (d.ph) {
-        double qx = p.x + A.sx, qy = p.y + A.sy;
-        float2 ph = make_float2((float)qx, (float)qy);
-        const float2 pl = make_float2((float)(qx - (double)ph.x), (float)(qy - (double)ph.y));
-        d.ph[i] = ph;
-        d.pl[i] = pl;
+    if (d.pq) {
+        const double qx = p.x + A.sx, qy = p.y + A.sy;
+        const float hx = (float)qx, hy = (float)qy;
+        d.pq[i] = make_float4(hx, hy, (float)(qx - (double)hx), (float)(qy - (double)hy));
     }
     // |u - u_ref| in float: its rounding (1e-7 |u|) is far below the margin
     // (1/2 - kSkinTrigger) skin of the trigger
@@ -320,12 +317,12 @@ __device__ __forceinline__ void bin_node(const DevPtrs &d, const KParams &k, int
     const int ag = __ldg(&d.g_agg[__ldg(&d.grain[i])]);
     const AggParams &A = d.agg[ag];
     int cx, cy;
-    if (d.ph) {
+    if (d.pq) {
         // FP32-split: the cell from the shifted float position (error below 1e-3
         // cell; the cells of this path are 0.4 % wider to absorb it)
-        const float2 ph = ldm<PERSIST>(&d.ph[i]), pl = ldm<PERSIST>(&d.pl[i]);
-        cx = cell_coord_f((ph.x - A.oxs) + pl.x, A.inv_cell_f);
-        cy = cell_coord_f((ph.y - A.oys) + pl.y, A.inv_cell_f);
+        const float4 q = ldm<PERSIST>(&d.pq[i]);
+        cx = cell_coord_f((q.x - A.oxs) + q.z, A.inv_cell_f);
+        cy = cell_coord_f((q.y - A.oys) + q.w, A.inv_cell_f);
     } else {
         const double2 p = ldm<PERSIST>(&d.p[i]);
         cx = cell_coord(p.x, A.ox, A.inv_cell);
@@ -367,8 +364,8 @@ __device__ __forceinline__ void scatter_node(const DevPtrs &d, const KParams &k,
     d.sorted[pos] = i;
     uint4 rec;
     if (k.fp32) {
-        const float2 ph = ldm<PERSIST>(&d.ph[i]), pl = ldm<PERSIST>(&d.pl[i]);
-        rec = make_uint4(__float_as_uint(ph.x), __float_as_uint(ph.y), __float_as_uint(pl.x), __float_as_uint(pl.y));
+        const float4 q = ldm<PERSIST>(&d.pq[i]);
+        rec = make_uint4(__float_as_uint(q.x), __float_as_uint(q.y), __float_as_uint(q.z), __float_as_uint(q.w));
     } else {
         const double2 p = ldm<PERSIST>(&d.p[i]);
         rec = make_uint4((unsigned)__double2loint(p.x), (unsigned)__double2hiint(p.x), (unsigned)__double2loint(p.y),
@@ -391,17 +388,10 @@ __device__ __forceinline__ void build_list_node(const DevPtrs &d, const KParams 
     unsigned bk[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) bk[c] = cell_bucket(cc.x + (c % 3) - 1, cc.y + (c / 3) - 1, ag, k.T);
-    float pix, piy;
+    float4 qi = make_float4(0.f, 0.f, 0.f, 0.f);
     double2 pi = make_double2(0.0, 0.0);
-    if (d.ph) {
-        const float2 ph = ldm<PERSIST>(&d.ph[i]);
-        pix = ph.x;
-        piy = ph.y;
-    } else {
-        pi = ldm<PERSIST>(&d.p[i]);
-        pix = piy = 0.f;
-    }
-    const float2 pli = d.ph ? ldm<PERSIST>(&d.pl[i]) : make_float2(0.f, 0.f);
+    if (d.pq) qi = ldm<PERSIST>(&d.pq[i]);
+    else pi = ldm<PERSIST>(&d.p[i]);
     int lst[kMaxList];
     int n = 0, over = 0;
 #pragma unroll
@@ -414,9 +404,9 @@ __device__ __forceinline__ void build_list_node(const DevPtrs &d, const KParams 
         for (int t = t0; t < t1; ++t) {
             const uint4 rec = ldm<PERSIST>(&d.srec[t]);
             float dx, dy;
-            if (d.ph) {
-                dx = (__uint_as_float(rec.x) - pix) + (__uint_as_float(rec.z) - pli.x);
-                dy = (__uint_as_float(rec.y) - piy) + (__uint_as_float(rec.w) - pli.y);
+            if (d.pq) {
+                dx = (__uint_as_float(rec.x) - qi.x) + (__uint_as_float(rec.z) - qi.z);
+                dy = (__uint_as_float(rec.y) - qi.y) + (__uint_as_float(rec.w) - qi.w);
             } else {
                 dx = (float)(__hiloint2double((int)rec.y, (int)rec.x) - pi.x);
                 dy = (float)(__hiloint2double((int)rec.w, (int)rec.z) - pi.y);
@@ -656,8 +646,8 @@ template <bool PERSIST, int LANES>
 __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k, int i, int lane, bool active,
                                              int vin, Sums32 &out) {
     const int ii = active ? i : 0;
-    const float2 phi = ldm<PERSIST>(&d.ph[ii]), pli = ldm<PERSIST>(&d.pl[ii]);
-    const int2 li = __ldg(&d.lat[ii]);
+    const float4 qi = ldm<PERSIST>(&d.pq[ii]);
+    const float2 phi = make_float2(qi.x, qi.y), pli = make_float2(qi.z, qi.w);
     const int gi = __ldg(&d.grain[ii]);
     const int ag = __ldg(&d.g_agg[gi]);
     const AggParams &A = d.agg[ag];
@@ -693,37 +683,31 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
     // per-lane summation order is unchanged: bonds lane, lane + LANES, ...)
     constexpr int kBondBatch = 4;
     for (int b0 = r0 + lane; b0 < r1 && !(sur && !judge); b0 += kBondBatch * LANES) {
-        int jb[kBondBatch];
-        uint32_t wb[kBondBatch];
+        uint32_t cb[kBondBatch], wb[kBondBatch];
 #pragma unroll
         for (int m = 0; m < kBondBatch; ++m) {
             const int b = b0 + m * LANES;
-            jb[m] = b < r1 ? __ldg(&d.col[b]) : -1;
+            cb[m] = b < r1 ? __ldg(&d.colx[b]) : 0xFFFFFFFFu;
             wb[m] = b < r1 ? __ldcg(&bw[(b - r0) >> 5]) : 0u;
         }
-        float2 phb[kBondBatch], plb[kBondBatch];
-        int2 lb[kBondBatch];
+        float4 qb[kBondBatch];
 #pragma unroll
         for (int m = 0; m < kBondBatch; ++m) {
-            const int j = jb[m] < 0 ? ii : jb[m];
-            phb[m] = ldm<PERSIST>(&d.ph[j]);
-            plb[m] = ldm<PERSIST>(&d.pl[j]);
-            lb[m] = __ldg(&d.lat[j]);
+            const int j = cb[m] == 0xFFFFFFFFu ? ii : (int)(cb[m] & kColMask);
+            qb[m] = ldm<PERSIST>(&d.pq[j]);
         }
 #pragma unroll
         for (int m = 0; m < kBondBatch; ++m) {
             const int b = b0 + m * LANES;
             const int kk = b - r0;
-            if (jb[m] < 0 || ((wb[m] >> (kk & 31)) & 1u)) continue;
-            const int j = jb[m];
-            const float2 phj = phb[m], plj = plb[m];
-            const int2 lj = lb[m];
-            const float dxh = __fsub_rn(phj.x, phi.x), dxl = plj.x - pli.x;
-            const float dyh = __fsub_rn(phj.y, phi.y), dyl = plj.y - pli.y;
+            if (cb[m] == 0xFFFFFFFFu || ((wb[m] >> (kk & 31)) & 1u)) continue;
+            const int j = (int)(cb[m] & kColMask);
+            const float4 qj = qb[m];
+            const float dxh = __fsub_rn(qj.x, phi.x), dxl = qj.z - pli.x;
+            const float dyh = __fsub_rn(qj.y, phi.y), dyl = qj.w - pli.y;
             float L2h, L2l;
             len2_ff(dxh, dxl, dyh, dyl, L2h, L2l);
-            const int di = lj.x - li.x, dj = lj.y - li.y;
-            const float nn = (float)(di * di + dj * dj);
+            const float nn = (float)(cb[m] >> kColBits);         // lattice offset di^2 + dj^2
             float q, eq;
             two_prod(nn, gq.y, q, eq);                           // |xi|^2 = n h^2
             const float num = ff_diff(L2h, L2l, q, eq + nn * gq.z);
@@ -757,14 +741,15 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
     // R_c test is exact in float-float
     const int nc = active ? ldm<PERSIST>(&d.nbr_cnt[ii]) : 0;
     // start-of-step velocity as a float-float pair (written by the displacement update)
-    const float2 vhi = ldm<PERSIST>(&d.vh[ii]), vli = ldm<PERSIST>(&d.vl[ii]);
+    const float4 vqi = ldm<PERSIST>(&d.vq[ii]);
+    const float2 vhi = make_float2(vqi.x, vqi.y), vli = make_float2(vqi.z, vqi.w);
     const float rd = k.rdf, rho = k.rhof, dt = k.dtf, mu = k.muf;
     float Fsx = 0.f, Fsy = 0.f, Fnx = 0.f, Fny = 0.f;
     for (int q = lane; q < nc; q += LANES) {
         const int j = ldm<PERSIST>(&d.nbr[(size_t)q * k.N + ii]);
-        const float2 phj = ldm<PERSIST>(&d.ph[j]), plj = ldm<PERSIST>(&d.pl[j]);
-        const float dxh = __fsub_rn(phj.x, phi.x), dxl = plj.x - pli.x;
-        const float dyh = __fsub_rn(phj.y, phi.y), dyl = plj.y - pli.y;
+        const float4 qj = ldm<PERSIST>(&d.pq[j]);
+        const float dxh = __fsub_rn(qj.x, phi.x), dxl = qj.z - pli.x;
+        const float dyh = __fsub_rn(qj.y, phi.y), dyl = qj.w - pli.y;
         float L2h, L2l;
         len2_ff(dxh, dxl, dyh, dyl, L2h, L2l);
         if (!(ff_diff(A.rc2_hi, A.rc2_lo, L2h, L2l) > 0.f)) continue;
@@ -778,11 +763,11 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
         const int gj = __ldg(&d.grain[j]);
         const float Vj = __ldg(&d.gq[gj]).w;
         // v(x) - v(y): exact high-part difference when the two are close (Sterbenz), plus the low parts
-        const float2 vhj = ldm<PERSIST>(&d.vh[j]), vlj = ldm<PERSIST>(&d.vl[j]);
-        const float vrx = __fsub_rn(vhi.x, vhj.x) + (vli.x - vlj.x), vry = __fsub_rn(vhi.y, vhj.y) + (vli.y - vlj.y);
+        const float4 vqj = ldm<PERSIST>(&d.vq[j]);
+        const float vrx = __fsub_rn(vhi.x, vqj.x) + (vli.x - vqj.z), vry = __fsub_rn(vhi.y, vqj.y) + (vli.y - vqj.w);
         if (gj == gi) {
             if (bonded_intact(d, k, ii, r0, r1, j)) continue;
-            const int2 lj = __ldg(&d.lat[j]);
+            const int2 li = __ldg(&d.lat[ii]), lj = __ldg(&d.lat[j]);
             const int di = lj.x - li.x, dj = lj.y - li.y;
             const float nn = (float)(di * di + dj * dj);
             const float xi = gq.x * sqrtf(nn);

@@ -368,17 +368,16 @@ size_t layout(pd_ctx *c, char *base) {
     if (c->prm.precision == PD_FP32_SPLIT) {
         carve(base, off, d.lat, N);
         carve(base, off, d.gq, G);
-        carve(base, off, d.ph, N);
-        carve(base, off, d.pl, N);
-        carve(base, off, d.vh, N);
-        carve(base, off, d.vl, N);
+        carve(base, off, d.pq, N);
+        carve(base, off, d.vq, N);
+        carve(base, off, d.colx, nb);
         carve(base, off, d.gc, G);
         carve(base, off, d.g_invm, G);
     } else {
         d.lat = nullptr;
         d.gq = nullptr;
-        d.ph = d.pl = nullptr;
-        d.vh = d.vl = nullptr;
+        d.pq = d.vq = nullptr;
+        d.colx = nullptr;
         d.gc = nullptr;
         d.g_invm = nullptr;
     }
@@ -472,12 +471,18 @@ cudaError_t record_step(pd_ctx *c, int vin, cudaStream_t s, bool timed = false) 
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g)) != cudaSuccess) return e;
     if (cs != cudaStreamCaptureStatusActive || !g) return cudaErrorStreamCaptureUnmatched;
-    cudaGraphConditionalHandle cond;
-    if ((e = cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+    const int use_cond = (c->mode & 4) ? 0 : 1;
+    cudaGraphConditionalHandle cond = 0;
+    if (use_cond && (e = cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal)) != cudaSuccess) return e;
-    if ((e = pd::launch_predict(c->d, c->kp, vin, 1, s, cond, 1)) != cudaSuccess) return e;
+    if ((e = pd::launch_predict(c->d, c->kp, vin, 1, s, cond, use_cond)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal)) != cudaSuccess) return e;
-    {
+    if (c->mode & 4) {
+        // path modes 4-7: the rebuild kernels run every step and return at once
+        // when the flag is clear (no conditional node)
+        if ((e = pd::launch_rebuild(c->d, c->kp, s)) != cudaSuccess) return e;
+    } else {
         const cudaGraphNode_t *deps = nullptr;
         size_t nd = 0;
         if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd)) != cudaSuccess) return e;
@@ -987,6 +992,7 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     PD_CUDA(cudaMemsetAsync(d.status, 0, 4 * PD_STATUS_COUNT, s));
     std::vector<float> gq, gcf;
     std::vector<double> invm;
+    std::vector<uint32_t> colx;
     if (p.precision == PD_FP32_SPLIT) {
         // per grain: h, h^2 as a float-float pair, V as float
         gq.resize(4 * G);
@@ -999,6 +1005,20 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
             gq[4 * g + 3] = (float)c->V[c->g_start[g]];
         }
         PD_CUDA(cudaMemcpyAsync(d.lat, c->lat.data(), 8 * N, cudaMemcpyHostToDevice, s));
+        // bond columns with the lattice offset n = di^2 + dj^2 in the top bits
+        // (the FP32 bond kernel's |xi|^2 = n h^2 needs no neighbour lattice load)
+        if (N > (size_t)pd::kColMask) return fail(PD_EINVAL, "FP32-split path: at most 2^28 - 1 nodes");
+        colx.resize(nb);
+        for (size_t x = 0; x < N; ++x)
+            for (int b = c->row_ptr[x]; b < c->row_ptr[x + 1]; ++b) {
+                const int j = c->col[b];
+                const int64_t di = c->lat[2 * (size_t)j] - c->lat[2 * x], dj = c->lat[2 * (size_t)j + 1] - c->lat[2 * x + 1];
+                const int64_t n = di * di + dj * dj;
+                if (n >= (int64_t)1 << (32 - pd::kColBits))
+                    return fail(PD_EINVAL, "FP32-split path: horizons up to 4 lattice spacings");
+                colx[b] = (uint32_t)j | ((uint32_t)n << pd::kColBits);
+            }
+        if (nb) PD_CUDA(cudaMemcpyAsync(d.colx, colx.data(), 4 * nb, cudaMemcpyHostToDevice, s));
         PD_CUDA(cudaMemcpyAsync(d.gq, gq.data(), 16 * G, cudaMemcpyHostToDevice, s));
         gcf.resize(4 * G);
         for (size_t g = 0; g < G; ++g) {
@@ -1278,8 +1298,10 @@ int pd_autotune(pd_ctx *c, double *report) {
     };
     std::vector<Cand> cands;
     // fused force phase: 4 or 8 threads per node; split: 1, 2, 4 or 8
-    for (int m = 0; m < 4; ++m) {
-        const bool split = (m >> 1) != 0;
+    // modes 4 and 6: the kernel graph with the rebuild kernels launched every
+    // step (returning at once without the flag) instead of the conditional node
+    for (int m : {0, 1, 2, 3, 4, 6}) {
+        const bool split = ((m >> 1) & 1) != 0;
         for (int lanes : {1, 2, 4, 8}) {
             if (c->prm.lanes ? lanes != c->prm.lanes : (!split && lanes < 4)) continue;
             cands.push_back({m, lanes, 128});
@@ -1294,7 +1316,7 @@ int pd_autotune(pd_ctx *c, double *report) {
     Cand pick = {c->mode, c->kp.lanes, c->block};
     for (const Cand &cd : cands) {
         c->mode = cd.mode;
-        c->kp.split = cd.mode >> 1;
+        c->kp.split = (cd.mode >> 1) & 1;
         c->kp.lanes = cd.lanes;
         c->block = cd.block;
         cudaGraphExec_t g = nullptr;
@@ -1325,7 +1347,7 @@ int pd_autotune(pd_ctx *c, double *report) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->mode = pick.mode;
-    c->kp.split = pick.mode >> 1;
+    c->kp.split = (pick.mode >> 1) & 1;
     c->kp.lanes = pick.lanes;
     c->block = pick.block;
     if (int r = capture_all(c)) return r;
@@ -1340,11 +1362,11 @@ int pd_autotune(pd_ctx *c, double *report) {
 
 int pd_set_path(pd_ctx *c, int mode, int lanes, int block) {
     if (int r = check_ctx(c, 3)) return r;
-    if (mode < 0 || mode > 3 || (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) ||
+    if (mode < 0 || mode > 7 || (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) ||
         (block != 128 && block != 256))
-        return fail(PD_EINVAL, "mode 0..3, lanes 1|2|4|8, block 128|256");
+        return fail(PD_EINVAL, "mode 0..7, lanes 1|2|4|8, block 128|256");
     c->mode = mode;
-    c->kp.split = mode >> 1;
+    c->kp.split = (mode >> 1) & 1;
     c->kp.lanes = lanes;
     c->block = block;
     return capture_all(c);

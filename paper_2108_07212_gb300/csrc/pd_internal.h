@@ -15,6 +15,10 @@ namespace pd {
 constexpr int kMaxList = 24;
 constexpr double kSkinRatio = 0.05;     // skin = kSkinRatio * R_c
 constexpr double kSkinTrigger = 0.45;   // < 1/2: margin for the float displacement test
+// FP32-split bond columns: node index in the low kColBits bits, the bond's
+// lattice offset di^2 + dj^2 (< 16 for horizons up to 4 h) in the top bits.
+constexpr int kColBits = 28;
+constexpr uint32_t kColMask = (1u << kColBits) - 1u;
 // Threads per block of the node-parallel multi-kernel path.
 constexpr int kBlock = 128;
 // Scan tile: threads x items per thread.
@@ -77,8 +81,9 @@ struct DevPtrs {
     // FP32-split path
     int2 *lat;          // lattice indices (i, j) of every node in its grain frame
     float4 *gq;         // per grain: (h, h^2 hi, h^2 lo, V = h^2 as float)
-    float2 *ph, *pl;    // shifted position (p + shift) as a float-float pair
-    float2 *vh, *vl;    // start-of-step velocity as a float-float pair
+    float4 *pq;         // shifted position (p + shift) as a float-float pair: (hi x, hi y, lo x, lo y)
+    float4 *vq;         // start-of-step velocity as a float-float pair: (hi x, hi y, lo x, lo y)
+    uint32_t *colx;     // bond columns with the lattice offset n = di^2 + dj^2 in the top 4 bits
     float4 *gc;         // per grain: (c_w, s0, eps, 0) as floats
     double *g_invm;     // per grain: 1 / (rho V)
     int4 *wall_cell;    // per aggregate: hash-grid cells of its walls x_lo, x_hi, y_lo, y_hi at the current time

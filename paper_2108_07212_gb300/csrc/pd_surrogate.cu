@@ -119,12 +119,14 @@ __global__ void __launch_bounds__(kSurThreads) k_sur_frame(DevPtrs d, KParams k,
     if (t < 0 || (!all_templated && !d.sur_active[g])) return;
     const int s0 = d.g_start[g], s1 = d.g_start[g + 1], n = s1 - s0;
     const float4 fc = d.sur_fc[g];                 // (h hi, h lo, lattice centroid i, j)
-    const float2 ph0 = d.ph[s0], pl0 = d.pl[s0];
+    const float4 q0 = d.pq[s0];
+    const float2 ph0 = make_float2(q0.x, q0.y), pl0 = make_float2(q0.z, q0.w);
     // one pass: centroid and the best-fit rotation sums in the lattice frame,
     // A = sum l . d, B = sum l x d (l: centred lattice index, d = p - p_first)
     float sx = 0.f, sy = 0.f, sa = 0.f, sb = 0.f;
     for (int i = s0 + threadIdx.x; i < s1; i += kSurThreads) {
-        const float2 ph = d.ph[i], pl = d.pl[i];
+        const float4 qn = d.pq[i];
+        const float2 ph = make_float2(qn.x, qn.y), pl = make_float2(qn.z, qn.w);
         const int2 li = d.lat[i];
         const float dx = __fsub_rn(ph.x, ph0.x) + (pl.x - pl0.x), dy = __fsub_rn(ph.y, ph0.y) + (pl.y - pl0.y);
         const float lx = (float)li.x - fc.z, ly = (float)li.y - fc.w;
@@ -157,7 +159,8 @@ __global__ void __launch_bounds__(kSurThreads) k_sur_frame(DevPtrs d, KParams k,
     const float ch = frame[0], cl = frame[1], sh = frame[2], sl = frame[3], cx = frame[4], cy = frame[5];
     const float hinv = 1.0f / fc.x;
     for (int i = s0 + threadIdx.x; i < s1; i += kSurThreads) {
-        const float2 ph = d.ph[i], pl = d.pl[i];
+        const float4 qn = d.pq[i];
+        const float2 ph = make_float2(qn.x, qn.y), pl = make_float2(qn.z, qn.w);
         const int2 li = d.lat[i];
         // e = p - c as float-float pairs
         float exh, exe, eyh, eye;
@@ -485,14 +488,16 @@ __global__ void __launch_bounds__(kSurThreads) k_sur_judge(DevPtrs d, KParams k)
                 acc[m] += b.x * lx + b.y * ly;
             }
         // largest stretch of the node's intact bonds (float-float, as the force kernel)
-        const float2 phi = d.ph[i], pli = d.pl[i];
+        const float4 qi = d.pq[i];
+        const float2 phi = make_float2(qi.x, qi.y), pli = make_float2(qi.z, qi.w);
         const int2 li = d.lat[i];
         const int r0 = d.row_ptr[i], r1 = d.row_ptr[i + 1];
         for (int b = r0; b < r1; ++b) {
             const int kk = b - r0;
             if ((d.bits[(size_t)i * k.wpn + (kk >> 5)] >> (kk & 31)) & 1u) continue;
             const int j = d.col[b];
-            const float2 phj = d.ph[j], plj = d.pl[j];
+            const float4 qj = d.pq[j];
+            const float2 phj = make_float2(qj.x, qj.y), plj = make_float2(qj.z, qj.w);
             const int2 lj = d.lat[j];
             float L2h, L2l;
             len2_ff(__fsub_rn(phj.x, phi.x), plj.x - pli.x, __fsub_rn(phj.y, phi.y), plj.y - pli.y, L2h, L2l);
