@@ -311,6 +311,7 @@ cudaError_t launch_observables(const DevPtrs &d, const KParams &k, int vcur, dou
     if (e != cudaSuccess) return e;
     // positions, cells and wall cells of the current state (no advance, forced rebuild)
     if ((e = launch_predict(d, k, vcur, 0, s, 0, 0)) != cudaSuccess) return e;
+    if ((e = launch_positions(d, k, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(d.rebuild, 1, sizeof(int), s)) != cudaSuccess) return e;
     if ((e = launch_rebuild(d, k, s)) != cudaSuccess) return e;
     k_grain_damage<<<k.G, kBlock, 0, s>>>(d, k, gdam);

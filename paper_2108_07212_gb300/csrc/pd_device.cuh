@@ -273,41 +273,59 @@ __device__ __forceinline__ void damping_friction32(float rd, float Kn, float rho
 // ---------------------------------------------------------------------------
 // per-node phases
 
-// Algorithm 1: u <- u + dt v + dt^2/2 a (when advancing), p = X + u and the
-// FP32-split float-float copy of the shifted position.  Returns true when the
-// node has moved farther than kSkinTrigger * skin since the last rebuild of
-// the candidate lists (or its displacement is not finite).
+// Algorithm 1: u <- u + dt v + dt^2/2 a (when advancing) and the positions.
+// Returns true when the node has moved farther than kSkinTrigger * skin since
+// the last rebuild of the candidate lists (or its position is not finite).
+//  * FP64 path: p = X + u in FP64, every operation rounded as written (no FMA).
+//  * FP32 split: u advances in FP64 with fused multiply-adds; the shifted
+//    position q = (X + shift) + u is kept only as a float-float pair (the FP64
+//    p is formed where it is needed: walls, near-threshold bonds, readout).
+//    GB300 issues FP64 at 2 lanes per SM cycle, so the node update is written
+//    with as few FP64 operations as the FP64 state allows.
 template <bool PERSIST>
 __device__ __forceinline__ bool predict_node(const DevPtrs &d, const KParams &k, int i, int vin, int advance) {
     double2 u = ldm<PERSIST>(&d.u[i]);
-    const double2 v = ldm<PERSIST>(&d.v[vin][i]);
-    if (d.vq) {
-        // FP32 split: the start-of-step velocity as a float-float pair for the contact laws
-        const float hx = (float)v.x, hy = (float)v.y;
-        d.vq[i] = make_float4(hx, hy, (float)(v.x - (double)hx), (float)(v.y - (double)hy));
+    const int ag = __ldg(&d.g_agg[__ldg(&d.grain[i])]);
+    const float dmax2 = d.agg[ag].dmax2;
+    if (d.pq) {
+        if (advance) {
+            const double2 v = ldm<PERSIST>(&d.v[vin][i]), a = ldm<PERSIST>(&d.a[i]);
+            u.x = fma(k.dt, v.x, fma(k.half_dt2, a.x, u.x));
+            u.y = fma(k.dt, v.y, fma(k.half_dt2, a.y, u.y));
+            d.u[i] = u;
+        }
+        const double2 xs = __ldg(&d.xs[i]);
+        const double qx = xs.x + u.x, qy = xs.y + u.y;
+        const float hx = (float)qx, hy = (float)qy;
+        const float4 q = make_float4(hx, hy, (float)(qx - (double)hx), (float)(qy - (double)hy));
+        d.pq[i] = q;
+        // displacement since the last rebuild from the float-float positions
+        // (error ~1e-7 of the displacement, far below the trigger's margin)
+        const float4 r = ldm<PERSIST>(&d.sref[i]);
+        const float ex = __fsub_rn(q.x, r.x) + (q.z - r.z), ey = __fsub_rn(q.y, r.y) + (q.w - r.w);
+        return !(ex * ex + ey * ey <= dmax2);
     }
     if (advance) {
         // explicit round-to-nearest operations: never contracted into FMAs
-        const double2 a = ldm<PERSIST>(&d.a[i]);
+        const double2 v = ldm<PERSIST>(&d.v[vin][i]), a = ldm<PERSIST>(&d.a[i]);
         u.x = __dadd_rn(__dadd_rn(u.x, __dmul_rn(k.dt, v.x)), __dmul_rn(k.half_dt2, a.x));
         u.y = __dadd_rn(__dadd_rn(u.y, __dmul_rn(k.dt, v.y)), __dmul_rn(k.half_dt2, a.y));
         d.u[i] = u;
     }
     const double2 X = __ldg(&d.X[i]);
-    const double2 p = make_double2(X.x + u.x, X.y + u.y);
-    d.p[i] = p;
-    const int ag = __ldg(&d.g_agg[__ldg(&d.grain[i])]);
-    const AggParams &A = d.agg[ag];
-    if (d.pq) {
-        const double qx = p.x + A.sx, qy = p.y + A.sy;
-        const float hx = (float)qx, hy = (float)qy;
-        d.pq[i] = make_float4(hx, hy, (float)(qx - (double)hx), (float)(qy - (double)hy));
-    }
+    d.p[i] = make_double2(__dadd_rn(X.x, u.x), __dadd_rn(X.y, u.y));
     // |u - u_ref| in float: its rounding (1e-7 |u|) is far below the margin
     // (1/2 - kSkinTrigger) skin of the trigger
-    const float2 ur = ldm<PERSIST>(&d.u_ref[i]);
-    const float ex = (float)u.x - ur.x, ey = (float)u.y - ur.y;
-    return !(ex * ex + ey * ey <= A.dmax2);
+    const float4 r = ldm<PERSIST>(&d.sref[i]);
+    const float ex = (float)u.x - r.x, ey = (float)u.y - r.y;
+    return !(ex * ex + ey * ey <= dmax2);
+}
+
+// FP64 position X + u of node i (the FP32-split path does not store p).
+template <bool PERSIST>
+__device__ __forceinline__ double2 position64(const DevPtrs &d, int i) {
+    const double2 X = __ldg(&d.X[i]), u = ldm<PERSIST>(&d.u[i]);
+    return make_double2(__dadd_rn(X.x, u.x), __dadd_rn(X.y, u.y));
 }
 
 // Rebuild, step 1: hash-grid cell and bucket of node i at its current
@@ -430,8 +448,12 @@ __device__ __forceinline__ void build_list_node(const DevPtrs &d, const KParams 
     const size_t N = (size_t)k.N;
     for (int q = 0; q < n; ++q) d.nbr[q * N + i] = lst[q];
     d.nbr_cnt[i] = n;
-    const double2 u = ldm<PERSIST>(&d.u[i]);
-    d.u_ref[i] = make_float2((float)u.x, (float)u.y);
+    if (d.pq) {
+        d.sref[i] = qi;
+    } else {
+        const double2 u = ldm<PERSIST>(&d.u[i]);
+        d.sref[i] = make_float4((float)u.x, (float)u.y, 0.f, 0.f);
+    }
     if (over) atomicAdd(&d.status[PD_STATUS_OVERFLOW], 1);
 }
 
@@ -460,9 +482,9 @@ __device__ __forceinline__ void finish_node(const DevPtrs &d, const KParams &k, 
     const double Fy = __dadd_rn(__dadd_rn(__dadd_rn(Fby, Fsy), Fny), Fwy);
     double ax, ay;
     if constexpr (RECIP) {
-        // FP32-split path: F / m as F * (1 / m) (one rounding more, far below the FP32 force error)
-        ax = __dadd_rn(__dmul_rn(Fx, inv_m), k.gx);
-        ay = __dadd_rn(__dmul_rn(Fy, inv_m), k.gy);
+        // FP32-split path: F / m as F * (1 / m) + g, fused (far below the FP32 force error)
+        ax = fma(Fx, inv_m, k.gx);
+        ay = fma(Fy, inv_m, k.gy);
     } else {
         const double m = __dmul_rn(k.rho, Vi);
         ax = __dadd_rn(__ddiv_rn(Fx, m), k.gx);
@@ -471,8 +493,13 @@ __device__ __forceinline__ void finish_node(const DevPtrs &d, const KParams &k, 
     if (update_v) {
         const double2 ao = ldm<PERSIST>(&d.a[i]);
         double2 vn;
-        vn.x = __dadd_rn(vi.x, __dmul_rn(k.half_dt, __dadd_rn(ao.x, ax)));
-        vn.y = __dadd_rn(vi.y, __dmul_rn(k.half_dt, __dadd_rn(ao.y, ay)));
+        if constexpr (RECIP) {
+            vn.x = fma(k.half_dt, ao.x + ax, vi.x);
+            vn.y = fma(k.half_dt, ao.y + ay, vi.y);
+        } else {
+            vn.x = __dadd_rn(vi.x, __dmul_rn(k.half_dt, __dadd_rn(ao.x, ax)));
+            vn.y = __dadd_rn(vi.y, __dmul_rn(k.half_dt, __dadd_rn(ao.y, ay)));
+        }
         d.v[vin ^ 1][i] = vn;
     }
     d.a[i] = make_double2(ax, ay);
@@ -487,23 +514,27 @@ __device__ __forceinline__ void finish_node(const DevPtrs &d, const KParams &k, 
 }
 
 // FP32-split update without per-part output: the three lane-summed parts are
-// added in FP32 (their rounding is far below the path's force error), then
-// the wall force in FP64, F / m as F * (1 / m), and the velocity-Verlet update.
+// added in FP32 (their rounding is far below the path's force error), the wall
+// force in FP64 where there is one, then a = F (1 / m) + g and the
+// velocity-Verlet update in FP64 with fused multiply-adds (the fewest FP64
+// operations on GB300's narrow FP64 pipe).
 template <bool PERSIST>
 __device__ __forceinline__ void finish_node32_total(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
-                                                    double2 vi, float fx, float fy, double Fwx, double Fwy,
-                                                    double inv_m) {
-    const double Fx = __dadd_rn((double)fx, Fwx), Fy = __dadd_rn((double)fy, Fwy);
-    const double ax = __dadd_rn(__dmul_rn(Fx, inv_m), k.gx), ay = __dadd_rn(__dmul_rn(Fy, inv_m), k.gy);
+                                                    double2 vi, float fx, float fy, bool walls, double Fwx,
+                                                    double Fwy, double inv_m) {
+    double Fx = (double)fx, Fy = (double)fy;
+    if (walls) {
+        Fx += Fwx;
+        Fy += Fwy;
+    }
+    const double ax = fma(Fx, inv_m, k.gx), ay = fma(Fy, inv_m, k.gy);
     if (update_v) {
         const double2 ao = ldm<PERSIST>(&d.a[i]);
-        double2 vn;
-        vn.x = __dadd_rn(vi.x, __dmul_rn(k.half_dt, __dadd_rn(ao.x, ax)));
-        vn.y = __dadd_rn(vi.y, __dmul_rn(k.half_dt, __dadd_rn(ao.y, ay)));
-        d.v[vin ^ 1][i] = vn;
+        d.v[vin ^ 1][i] = make_double2(fma(k.half_dt, ao.x + ax, vi.x), fma(k.half_dt, ao.y + ay, vi.y));
     }
     d.a[i] = make_double2(ax, ay);
-    if (!isfinite(ax) || !isfinite(ay)) atomicAdd(&d.status[PD_STATUS_NONFINITE], 1);
+    if (!isfinite(fx) || !isfinite(fy) || (walls && (!isfinite(Fwx) || !isfinite(Fwy))))
+        atomicAdd(&d.status[PD_STATUS_NONFINITE], 1);
 }
 
 template <int LANES, class T>
@@ -678,6 +709,9 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
         Fbx = (rot.x * f.x - rot.y * f.y) * Eh;
         Fby = (rot.y * f.x + rot.x * f.y) * Eh;
     }
+    // broken-bond bits of the node's first 32 bonds: only the node's own threads
+    // set them, each for its own bonds, so one load at the start serves the loop
+    const uint32_t w0 = active ? __ldcg(bw) : 0u;
     // bonds in batches of kBondBatch per lane: the column indices, broken words and
     // neighbour positions of a batch are all in flight before any is used (the
     // per-lane summation order is unchanged: bonds lane, lane + LANES, ...)
@@ -688,7 +722,8 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
         for (int m = 0; m < kBondBatch; ++m) {
             const int b = b0 + m * LANES;
             cb[m] = b < r1 ? __ldg(&d.colx[b]) : 0xFFFFFFFFu;
-            wb[m] = b < r1 ? __ldcg(&bw[(b - r0) >> 5]) : 0u;
+            // the node's first broken-bond word is loaded once (rows of up to 32 bonds)
+            wb[m] = b - r0 < 32 ? w0 : (b < r1 ? __ldcg(&bw[(b - r0) >> 5]) : 0u);
         }
         float4 qb[kBondBatch];
 #pragma unroll
@@ -717,11 +752,12 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
             const float as = fabsf(s);
             bool brk;
             if (as > s0_lo && as < s0_hi) {
-                const double2 pi = ldm<PERSIST>(&d.p[ii]), pj = ldm<PERSIST>(&d.p[j]);
-                double ddx = pj.x - pi.x, ddy = pj.y - pi.y;
-                double L64 = sqrt(ddx * ddx + ddy * ddy);
-                double xi64 = __ldg(&d.xi[b]);
-                brk = fabs((L64 - xi64) / xi64) > __ldg(&d.g_s0[gi]);
+                // near the threshold: the FP64 path's decision, operation by operation
+                const double2 pi = position64<PERSIST>(d, ii), pj = position64<PERSIST>(d, j);
+                const double ddx = __dsub_rn(pj.x, pi.x), ddy = __dsub_rn(pj.y, pi.y);
+                const double L64 = __dsqrt_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)));
+                const double xi64 = __ldg(&d.xi[b]);
+                brk = fabs(__ddiv_rn(__dsub_rn(L64, xi64), xi64)) > __ldg(&d.g_s0[gi]);
             } else {
                 brk = as > s0;
             }
@@ -740,9 +776,8 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
     // contact candidates from the node's list (ascending node index); the
     // R_c test is exact in float-float
     const int nc = active ? ldm<PERSIST>(&d.nbr_cnt[ii]) : 0;
-    // start-of-step velocity as a float-float pair (written by the displacement update)
-    const float4 vqi = ldm<PERSIST>(&d.vq[ii]);
-    const float2 vhi = make_float2(vqi.x, vqi.y), vli = make_float2(vqi.z, vqi.w);
+    // start-of-step velocity (FP64; read only by nodes with candidates)
+    const double2 vi64 = nc > 0 ? ldm<PERSIST>(&d.v[vin][ii]) : make_double2(0.0, 0.0);
     const float rd = k.rdf, rho = k.rhof, dt = k.dtf, mu = k.muf;
     float Fsx = 0.f, Fsy = 0.f, Fnx = 0.f, Fny = 0.f;
     for (int q = lane; q < nc; q += LANES) {
@@ -762,9 +797,10 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
         const float overlap = ff_diff(A.rc2_hi, A.rc2_lo, L2h, L2l) / (Rc + dd);   // R_c - |d|
         const int gj = __ldg(&d.grain[j]);
         const float Vj = __ldg(&d.gq[gj]).w;
-        // v(x) - v(y): exact high-part difference when the two are close (Sterbenz), plus the low parts
-        const float4 vqj = ldm<PERSIST>(&d.vq[j]);
-        const float vrx = __fsub_rn(vhi.x, vqj.x) + (vli.x - vqj.z), vry = __fsub_rn(vhi.y, vqj.y) + (vli.y - vqj.w);
+        // v(x) - v(y) in FP64, rounded once to float (nearby nodes move alike:
+        // a float difference of float velocities would cancel)
+        const double2 vj64 = ldm<PERSIST>(&d.v[vin][j]);
+        const float vrx = (float)__dsub_rn(vi64.x, vj64.x), vry = (float)__dsub_rn(vi64.y, vj64.y);
         if (gj == gi) {
             if (bonded_intact(d, k, ii, r0, r1, j)) continue;
             const int2 li = __ldg(&d.lat[ii]), lj = __ldg(&d.lat[j]);
@@ -807,20 +843,21 @@ template <bool PERSIST>
 __device__ __forceinline__ void node_epilogue32(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
                                                 const Sums32 &f) {
     const double2 vi = ldm<PERSIST>(&d.v[vin][i]);
-    const double Vi = __ldg(&d.V[i]);
     const int gi = __ldg(&d.grain[i]);
     const int ag = __ldg(&d.g_agg[gi]);
     double Fwx = 0.0, Fwy = 0.0;
-    if (!far_from_walls<PERSIST>(d, i, ag)) {
-        const double2 pi = ldm<PERSIST>(&d.p[i]);
-        wall_force64(k, d.agg[ag], ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, Vi, Fwx, Fwy, d.status);
+    const bool walls = !far_from_walls<PERSIST>(d, i, ag);
+    if (walls) {
+        const double2 pi = position64<PERSIST>(d, i);
+        wall_force64(k, d.agg[ag], ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, __ldg(&d.V[i]), Fwx, Fwy,
+                     d.status);
     }
     if (k.store)
-        finish_node<PERSIST, true>(d, k, i, vin, update_v, vi, Vi, (double)f.bx, (double)f.by, (double)f.sx,
+        finish_node<PERSIST, true>(d, k, i, vin, update_v, vi, 0.0, (double)f.bx, (double)f.by, (double)f.sx,
                                    (double)f.sy, (double)f.nx, (double)f.ny, Fwx, Fwy, __ldg(&d.g_invm[gi]));
     else
-        finish_node32_total<PERSIST>(d, k, i, vin, update_v, vi, (f.bx + f.sx) + f.nx, (f.by + f.sy) + f.ny, Fwx,
-                                     Fwy, __ldg(&d.g_invm[gi]));
+        finish_node32_total<PERSIST>(d, k, i, vin, update_v, vi, (f.bx + f.sx) + f.nx, (f.by + f.sy) + f.ny, walls,
+                                     Fwx, Fwy, __ldg(&d.g_invm[gi]));
 }
 
 }  // namespace pd

@@ -349,7 +349,7 @@ size_t layout(pd_ctx *c, char *base) {
     carve(base, off, d.srec, N);
     carve(base, off, d.nbr_cnt, N);
     carve(base, off, d.nbr, N * (size_t)pd::kMaxList);
-    carve(base, off, d.u_ref, N);
+    carve(base, off, d.sref, N);
     carve(base, off, d.rebuild, 1);
     carve(base, off, d.pred_done, 1);
     carve(base, off, d.fsum, 6 * N * (c->prm.precision == PD_FP32_SPLIT ? 4 : 8));
@@ -369,14 +369,15 @@ size_t layout(pd_ctx *c, char *base) {
         carve(base, off, d.lat, N);
         carve(base, off, d.gq, G);
         carve(base, off, d.pq, N);
-        carve(base, off, d.vq, N);
+        carve(base, off, d.xs, N);
         carve(base, off, d.colx, nb);
         carve(base, off, d.gc, G);
         carve(base, off, d.g_invm, G);
     } else {
         d.lat = nullptr;
         d.gq = nullptr;
-        d.pq = d.vq = nullptr;
+        d.pq = nullptr;
+        d.xs = nullptr;
         d.colx = nullptr;
         d.gc = nullptr;
         d.g_invm = nullptr;
@@ -927,7 +928,7 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     // bucket counts are zero between rebuilds; the first force evaluation rebuilds
     PD_CUDA(cudaMemsetAsync(d.count, 0, sizeof(int) * c->T, s));
     PD_CUDA(cudaMemsetAsync(d.nbr_cnt, 0, 4 * N, s));
-    PD_CUDA(cudaMemsetAsync(d.u_ref, 0, 8 * N, s));
+    PD_CUDA(cudaMemsetAsync(d.sref, 0, 16 * N, s));
     PD_CUDA(cudaMemsetAsync(d.rebuild, 1, sizeof(int), s));
     PD_CUDA(cudaMemsetAsync(d.pred_done, 0, sizeof(unsigned), s));
     std::vector<int32_t> gstart32(c->g_start.begin(), c->g_start.end()), tnode, tslot;
@@ -993,6 +994,7 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     std::vector<float> gq, gcf;
     std::vector<double> invm;
     std::vector<uint32_t> colx;
+    std::vector<double> xs;
     if (p.precision == PD_FP32_SPLIT) {
         // per grain: h, h^2 as a float-float pair, V as float
         gq.resize(4 * G);
@@ -1019,6 +1021,14 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
                 colx[b] = (uint32_t)j | ((uint32_t)n << pd::kColBits);
             }
         if (nb) PD_CUDA(cudaMemcpyAsync(d.colx, colx.data(), 4 * nb, cudaMemcpyHostToDevice, s));
+        // X + the aggregate's shift (FP64): the FP32-split positions are (X + shift) + u
+        xs.resize(2 * N);
+        for (size_t x = 0; x < N; ++x) {
+            const pd::AggParams &A = c->aggp[c->g_agg[c->grain[x]]];
+            xs[2 * x] = c->X[2 * x] + A.sx;
+            xs[2 * x + 1] = c->X[2 * x + 1] + A.sy;
+        }
+        PD_CUDA(cudaMemcpyAsync(d.xs, xs.data(), 16 * N, cudaMemcpyHostToDevice, s));
         PD_CUDA(cudaMemcpyAsync(d.gq, gq.data(), 16 * G, cudaMemcpyHostToDevice, s));
         gcf.resize(4 * G);
         for (size_t g = 0; g < G; ++g) {

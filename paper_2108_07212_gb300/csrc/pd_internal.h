@@ -64,7 +64,7 @@ struct DevPtrs {
     // contact candidate lists (rebuilt when a node has moved kSkinTrigger * skin)
     int *nbr_cnt;       // list length of every node
     int *nbr;           // list entry q of node i at nbr[q N + i] (kMaxList slots), ascending node index
-    float2 *u_ref;      // displacement of every node at the last rebuild
+    float4 *sref;       // at the last rebuild: FP32 split pq, FP64 path (float u, 0, 0)
     int *rebuild;       // nonzero: rebuild the lists before the next force phase (cleared by the force phase)
     unsigned *pred_done;  // blocks of the displacement update that have finished (last-block election)
     uint4 *srec;        // position of sorted[t] in bucket order: FP32 split (ph, pl), FP64 p (16 bytes)
@@ -82,7 +82,7 @@ struct DevPtrs {
     int2 *lat;          // lattice indices (i, j) of every node in its grain frame
     float4 *gq;         // per grain: (h, h^2 hi, h^2 lo, V = h^2 as float)
     float4 *pq;         // shifted position (p + shift) as a float-float pair: (hi x, hi y, lo x, lo y)
-    float4 *vq;         // start-of-step velocity as a float-float pair: (hi x, hi y, lo x, lo y)
+    double2 *xs;        // X + the aggregate's shift (FP64)
     uint32_t *colx;     // bond columns with the lattice offset n = di^2 + dj^2 in the top 4 bits
     float4 *gc;         // per grain: (c_w, s0, eps, 0) as floats
     double *g_invm;     // per grain: 1 / (rho V)

@@ -87,7 +87,7 @@ __device__ __forceinline__ void epilogue_node(const DevPtrs &d, const KParams &k
 }
 
 template <bool FP32, int LANES>
-__global__ void __launch_bounds__(kBlock, FP32 ? 6 : 4) k_sums(DevPtrs d, KParams k, int vin) {
+__global__ void __launch_bounds__(kBlock, FP32 ? 8 : 4) k_sums(DevPtrs d, KParams k, int vin) {
     clear_rebuild(d);
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     sums_node<FP32, false, LANES>(d, k, tid / LANES, tid % LANES, vin);
