@@ -170,7 +170,8 @@ int pd_mesh_grains(pd_ctx *ctx, int n_shapes, const int32_t *shape_loop_start,
  * delta along the outward vertex bisectors) nor an outer-angle bisector ray
  * of a non-convex cusp (Sec. 4 "bonds in nonconvex domains").  Lists are CSR,
  * sorted by node, columns ascending.  Writes the directed bond count.
- * Errors: PD_ESTATE (before pd_mesh_grains), PD_ENOMEM.
+ * Errors: PD_ESTATE (before pd_mesh_grains), PD_ENOMEM, PD_EINVAL (more than
+ * 8,388,608 nodes: the contact grid's two-level bucket scan).
  */
 int pd_build_bonds(pd_ctx *ctx, int64_t *n_bonds_out);
 

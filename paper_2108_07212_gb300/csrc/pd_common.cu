@@ -3,6 +3,8 @@
 // counting sort: bucket counts, device-wide exclusive scan, scatter),
 // positions for readout and the diagnostics reductions; plus the launch
 // dispatchers.  Compiled without FMA contraction.
+#include <algorithm>
+
 #include "pd_device.cuh"
 
 namespace pd {
@@ -44,8 +46,9 @@ __global__ void __launch_bounds__(kBlock) k_predict(DevPtrs d, KParams k, int vi
 }
 
 // Rebuild of the contact candidate lists: bucket counts, a device-wide
-// exclusive scan of the counts (reduce, top, apply; apply clears the counts
-// for the next rebuild), the counting-sort scatter and the lists.  Every
+// exclusive scan of the counts (reduce, top, apply), the counting-sort
+// scatter and the lists (the list kernel clears the counts for the next
+// rebuild).  Every
 // kernel returns at once when the rebuild flag is clear.
 __global__ void __launch_bounds__(kBlock) k_bin(DevPtrs d, KParams k) {
     if (!*(volatile int *)d.rebuild) return;
@@ -57,6 +60,9 @@ __global__ void __launch_bounds__(kBlock) k_build_list(DevPtrs d, KParams k) {
     if (!*(volatile int *)d.rebuild) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) atomicAdd(&d.status[PD_STATUS_REBUILDS], 1);
+    // the bucket counts were consumed by the scan: zero them for the next
+    // rebuild (the grid covers max(N, T / 4) threads: one int4 per thread)
+    if ((unsigned)i < k.T / 4) reinterpret_cast<int4 *>(d.count)[i] = make_int4(0, 0, 0, 0);
     if (i < k.N) build_list_node<false>(d, k, i);
 }
 
@@ -102,10 +108,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int *__restr
                                                               const int *flag) {
     if (!*(volatile const int *)flag) return;
     __shared__ int sm[33];
-    size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
-    int v[kScanItems];
-#pragma unroll
-    for (int q = 0; q < kScanItems; ++q) v[q] = (base + q < T) ? count[base + q] : 0;
+    static_assert(kScanItems == 4, "one int4 per thread");
+    const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
+    const int4 c4 = base < T ? *reinterpret_cast<const int4 *>(count + base) : make_int4(0, 0, 0, 0);
+    int v[kScanItems] = {c4.x, c4.y, c4.z, c4.w};
     int total = block_exclusive_scan(v, sm);
     if (threadIdx.x == 0) blocksums[blockIdx.x] = total;
 }
@@ -132,21 +138,19 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(int *count, const i
                                                              const int *flag) {
     if (!*(volatile const int *)flag) return;
     __shared__ int sm[33];
-    size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
-    int v[kScanItems];
-#pragma unroll
-    for (int q = 0; q < kScanItems; ++q) {
-        v[q] = (base + q < T) ? count[base + q] : 0;
-        if (base + q < T) count[base + q] = 0;
+    // T is a power of two >= 1024 and bases are multiples of 4: whole int4 per thread
+    const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanItems;
+    int4 c4 = make_int4(0, 0, 0, 0);
+    if (base < T) {
+        c4 = *reinterpret_cast<const int4 *>(count + base);
     }
+    int v[kScanItems] = {c4.x, c4.y, c4.z, c4.w};
     block_exclusive_scan(v, sm);
-    int off = blocksums[blockIdx.x];
-#pragma unroll
-    for (int q = 0; q < kScanItems; ++q) {
-        if (base + q < T) {
-            start[base + q] = v[q] + off;
-            cursor[base + q] = v[q] + off;
-        }
+    const int off = blocksums[blockIdx.x];
+    if (base < T) {
+        const int4 st = make_int4(v[0] + off, v[1] + off, v[2] + off, v[3] + off);
+        *reinterpret_cast<int4 *>(start + base) = st;
+        *reinterpret_cast<int4 *>(cursor + base) = st;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) start[T] = N;
 }
@@ -237,7 +241,7 @@ cudaError_t launch_rebuild(const DevPtrs &d, const KParams &k, cudaStream_t s) {
     k_scan_top<<<1, kScanThreads, 0, s>>>(d.blocksums, nb, d.rebuild);
     k_scan_apply<<<nb, kScanThreads, 0, s>>>(d.count, d.blocksums, d.start, d.cursor, k.T, k.N, d.rebuild);
     k_scatter<<<nn, kBlock, 0, s>>>(d, k);
-    k_build_list<<<nn, kBlock, 0, s>>>(d, k);
+    k_build_list<<<nblk(std::max<long long>(k.N, k.T / 4), kBlock), kBlock, 0, s>>>(d, k);
     return cudaGetLastError();
 }
 

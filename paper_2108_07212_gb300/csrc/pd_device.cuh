@@ -39,8 +39,10 @@ __device__ __forceinline__ int cell_coord(double x, double origin, double inv_ce
     return (int)f;
 }
 
+constexpr unsigned kHashX = 73856093u, kHashY = 19349663u, kHashA = 83492791u;
+
 __device__ __forceinline__ unsigned cell_bucket(int cx, int cy, int agg, unsigned T) {
-    return ((unsigned)cx * 73856093u ^ (unsigned)cy * 19349663u ^ (unsigned)agg * 83492791u) & (T - 1u);
+    return ((unsigned)cx * kHashX ^ (unsigned)cy * kHashY ^ (unsigned)agg * kHashA) & (T - 1u);
 }
 
 // ---------------------------------------------------------------------------
@@ -395,17 +397,26 @@ __device__ __forceinline__ void scatter_node(const DevPtrs &d, const KParams &k,
 // Rebuild, last step: the candidate list of node i -- every node y != i of
 // its aggregate with |p(y) - p(i)| < R_c + skin, gathered from the 3x3 block
 // of hash-grid cells around its cell (cells are wider than R_c + skin) and
-// kept in ascending node index -- and the displacement it was built at.  The
+// kept in ascending node index -- and the position it was built at.  The
 // bucket records hold the positions in bucket order, so only nodes inside
-// the radius are looked up.
+// the radius are looked up.  The three buckets of a row of the block are
+// walked as one range of records, so that the threads of a warp step through
+// rows rather than through nine buckets of different lengths.
 template <bool PERSIST>
 __device__ __forceinline__ void build_list_node(const DevPtrs &d, const KParams &k, int i) {
     const int ag = __ldg(&d.g_agg[__ldg(&d.grain[i])]);
     const AggParams &A = d.agg[ag];
     const int2 cc = ldm<PERSIST>(&d.cell[i]);
-    unsigned bk[9];
+    const unsigned ha = (unsigned)ag * kHashA, mask = k.T - 1u;
+    unsigned hx[3], bk[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) bk[c] = cell_bucket(cc.x + (c % 3) - 1, cc.y + (c / 3) - 1, ag, k.T);
+    for (int c = 0; c < 3; ++c) hx[c] = (unsigned)(cc.x + c - 1) * kHashX;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const unsigned hy = (unsigned)(cc.y + r - 1) * kHashY ^ ha;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) bk[3 * r + c] = (hx[c] ^ hy) & mask;
+    }
     float4 qi = make_float4(0.f, 0.f, 0.f, 0.f);
     double2 pi = make_double2(0.0, 0.0);
     if (d.pq) qi = ldm<PERSIST>(&d.pq[i]);
@@ -413,13 +424,20 @@ __device__ __forceinline__ void build_list_node(const DevPtrs &d, const KParams 
     int lst[kMaxList];
     int n = 0, over = 0;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) {
-        bool dup = false;      // two cells of the block hashed to one bucket: visit it once
+    for (int r = 0; r < 3; ++r) {
+        int t0[3], m[3];
 #pragma unroll
-        for (int q = 0; q < c; ++q) dup |= bk[q] == bk[c];
-        if (dup) continue;
-        const int t0 = ldm<PERSIST>(&d.start[bk[c]]), t1 = ldm<PERSIST>(&d.start[bk[c] + 1]);
-        for (int t = t0; t < t1; ++t) {
+        for (int c = 0; c < 3; ++c) {
+            const int cell = 3 * r + c;
+            bool dup = false;      // two cells of the block hashed to one bucket: visit it once
+#pragma unroll
+            for (int q = 0; q < cell; ++q) dup |= bk[q] == bk[cell];
+            t0[c] = dup ? 0 : ldm<PERSIST>(&d.start[bk[cell]]);
+            m[c] = dup ? 0 : ldm<PERSIST>(&d.start[bk[cell] + 1]) - t0[c];
+        }
+        const int tot = m[0] + m[1] + m[2];
+        for (int e = 0; e < tot; ++e) {
+            const int t = e < m[0] ? t0[0] + e : (e < m[0] + m[1] ? t0[1] + (e - m[0]) : t0[2] + (e - m[0] - m[1]));
             const uint4 rec = ldm<PERSIST>(&d.srec[t]);
             float dx, dy;
             if (d.pq) {
