@@ -288,10 +288,10 @@ BYTES_PER_NODE_STEP_FP32 = 196
 # profiles/traffic_settling50.md).  They hold while the kernel sources hash to
 # TRAFFIC_DIGEST; otherwise, or for a variant not captured, traffic is null.
 TRAFFIC_SETTLING50 = {
-    "k_persistent<1, 4, 128>": 3579392,
-    "k_persistent<0, 4, 128>": 6918144,
+    "k_persistent<1, 4, 256>": 3738368,
+    "k_persistent<0, 4, 128>": 7075200,
 }
-TRAFFIC_DIGEST = "27415c17631c242c5897cd580370d5bf7f046b69"
+TRAFFIC_DIGEST = "6d692a84cd657db9551718d45d35ede27579a75e"
 TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu", "pd_common.cu", "pd_internal.h")
 
 
@@ -641,6 +641,11 @@ def run_ours(args):
 
     peaks = measured_peaks()
     f_ms = float(np.mean(force_ms))
+    # the persistent kernel is the whole step: its duration is bounded by the
+    # event-timed plain step (graph launch included), which the instrumented
+    # graph's event nodes would otherwise inflate
+    if tuned["fp32" if prec != B.PD_FP64 else "fp64"]["mode"] & 1:
+        f_ms = min(f_ms, float(np.mean(step_ms)))
     if prec == B.PD_FP64:
         fp64_peak = fp64_gemm_peak(torch, dev)
         flops = FLOPS_PER_BOND * sim.n_bonds
@@ -661,7 +666,9 @@ def run_ours(args):
                 "frac": achieved / hbm, "traffic": force_phase_traffic(tuned["fp32"], True, args.workload),
                 "note": f"{per_node} B per node + {BYTES_PER_BOND_FP32} B per directed bond (algorithmic) x "
                         f"{sim.N} nodes / {sim.n_bonds} bonds per {'step' if whole else 'force phase'} / mean "
-                        f"CUDA-event duration {f_ms * 1e3:.1f} us; peak = measured copy bandwidth (of measured)"
+                        f"CUDA-event duration {f_ms * 1e3:.1f} us"
+                        + (" (persistent kernel = the whole step: event-timed step, graph launch included)" if whole else "")
+                        + "; peak = measured copy bandwidth (of measured)"
                         + ("; the 20k-node workload is too small to load 152 SMs, so the phase is latency-bound"
                            if sim.N < 100000 else "")}
     line = {
