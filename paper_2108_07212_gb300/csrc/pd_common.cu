@@ -19,10 +19,13 @@ __global__ void __launch_bounds__(kBlock) k_predict(DevPtrs d, KParams k, int vi
                                                     cudaGraphConditionalHandle cond, int use_cond) {
     __shared__ bool last;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0) {
-        long long st = *d.step + (advance ? 1 : 0);
-        *d.t_now = (double)st * k.dt;
-        if (advance) *d.step = st;
+    if (blockIdx.x == 0) {
+        const long long st = *d.step + (advance ? 1 : 0);
+        __syncthreads();                   // every thread of block 0 has read the counter
+        if (threadIdx.x == 0) {
+            *d.t_now = (double)st * k.dt;
+            if (advance) *d.step = st;
+        }
         wall_cells(d, k, (double)st * k.dt);
     }
     const bool need = i < k.N && predict_node<false>(d, k, i, vin, advance);

@@ -287,8 +287,7 @@ __device__ __forceinline__ void damping_friction32(float rd, float Kn, float rho
 template <bool PERSIST>
 __device__ __forceinline__ bool predict_node(const DevPtrs &d, const KParams &k, int i, int vin, int advance) {
     double2 u = ldm<PERSIST>(&d.u[i]);
-    const int ag = __ldg(&d.g_agg[__ldg(&d.grain[i])]);
-    const float dmax2 = d.agg[ag].dmax2;
+    const float dmax2 = k.dmax2;
     if (d.pq) {
         if (advance) {
             const double2 v = ldm<PERSIST>(&d.v[vin][i]), a = ldm<PERSIST>(&d.a[i]);
@@ -355,10 +354,11 @@ __device__ __forceinline__ void bin_node(const DevPtrs &d, const KParams &k, int
 }
 
 // Hash-grid cells of the four walls of every aggregate at time t (written once
-// per force evaluation by one thread): a node two or more cells away from all
-// of them is farther than R_c from every wall and feels no wall force.
+// per force evaluation by the threads of one block, one aggregate each): a node
+// two or more cells away from all of them is farther than R_c from every wall
+// and feels no wall force.
 __device__ __forceinline__ void wall_cells(const DevPtrs &d, const KParams &k, double t) {
-    for (int a = 0; a < k.n_agg; ++a) {
+    for (int a = threadIdx.x; a < k.n_agg; a += blockDim.x) {
         const AggParams &A = d.agg[a];
         d.wall_cell[a] = make_int4(cell_coord(A.w0[0] + A.wv[0] * t, A.ox, A.inv_cell),
                                    cell_coord(A.w0[1] + A.wv[1] * t, A.ox, A.inv_cell),

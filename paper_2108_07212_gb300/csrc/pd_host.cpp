@@ -889,6 +889,9 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     k.muf = (float)p.friction;
     k.dtf = (float)p.dt;
     k.guard = 1e-4f;
+    // one rebuild trigger for all aggregates: the smallest (the most cautious)
+    k.dmax2 = c->aggp[0].dmax2;
+    for (const pd::AggParams &A : c->aggp) k.dmax2 = std::min(k.dmax2, A.dmax2);
     k.fp32 = p.precision == PD_FP32_SPLIT ? 1 : 0;
     k.sur = 0;
     k.n_modes = c->sur_modes;

@@ -131,6 +131,7 @@ struct KParams {
     double rho, rd, mu, gx, gy, dt, half_dt, half_dt2;
     float rhof, rdf, muf, dtf;   // the same as floats (FP32-split contact laws)
     float guard;        // FP32-split: |(|s| - s0)| < guard * s0 re-decides breaking in FP64
+    float dmax2;        // smallest (kSkinTrigger skin)^2 of the aggregates: rebuild trigger
     int micro, store;
     int lanes;          // threads per node in the force kernels (1, 4 or 8)
     int split;          // 1: lane sums through global memory and a separate epilogue pass

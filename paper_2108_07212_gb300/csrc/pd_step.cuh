@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kBlock, FP32 ? 8 : 4) k_sums(DevPtrs d, KParam
 }
 
 template <bool FP32>
-__global__ void __launch_bounds__(256) k_epilogue(DevPtrs d, KParams k, int vin, int update_v) {
+__global__ void __launch_bounds__(256, 4) k_epilogue(DevPtrs d, KParams k, int vin, int update_v) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < k.N) epilogue_node<FP32, false>(d, k, i, vin, update_v);
 }
@@ -225,10 +225,13 @@ __global__ void __launch_bounds__(BLOCK) k_persistent(DevPtrs d, KParams k, int 
     const unsigned lo = min(T, blockIdx.x * slice), hi = min(T, lo + slice);
     for (int st = 0; st < nsteps; ++st) {
         // A
-        if (gtid == 0) {
-            const long long s = *d.step + 1;
-            *d.step = s;
-            *d.t_now = (double)s * k.dt;
+        if (blockIdx.x == 0) {
+            const long long s = __ldcg(d.step) + 1;
+            __syncthreads();               // every thread of block 0 has read the counter
+            if (threadIdx.x == 0) {
+                *d.step = s;
+                *d.t_now = (double)s * k.dt;
+            }
             wall_cells(d, k, (double)s * k.dt);
         }
         bool need = false;
