@@ -171,7 +171,7 @@ int pd_mesh_grains(pd_ctx *ctx, int n_shapes, const int32_t *shape_loop_start,
  * of a non-convex cusp (Sec. 4 "bonds in nonconvex domains").  Lists are CSR,
  * sorted by node, columns ascending.  Writes the directed bond count.
  * Errors: PD_ESTATE (before pd_mesh_grains), PD_ENOMEM, PD_EINVAL (more than
- * 8,388,608 nodes: the contact grid's two-level bucket scan).
+ * 2^29 nodes, the limit of the contact grid's 32-bit buckets).
  */
 int pd_build_bonds(pd_ctx *ctx, int64_t *n_bonds_out);
 

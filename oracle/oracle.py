@@ -28,7 +28,7 @@ _lib = None
 # parameter-vector slots (mirror of the enum in peridem_oracle.c)
 P_RHO, P_KN, P_RC, P_RD, P_MU, P_GX, P_GY, P_DT = range(8)
 P_WX0, P_WX1, P_WY0, P_WY1, P_VX0, P_VX1, P_VY0, P_VY1 = range(8, 16)
-P_MICRO, P_SEARCH, P_NPARAM = 16, 17, 18
+P_MICRO, P_SEARCH, P_PE5, P_NPARAM = 16, 17, 18, 19
 
 MESH_CLEARANCE = 1e-6      # nodes closer than this * h to the boundary are dropped
 SEGMENT_TOL = 1e-10        # closed-domain tolerance of the visibility test, * h
@@ -66,11 +66,12 @@ def lib():
             L.or_contact_stiffness.restype = c_d
             L.or_wall_segment.argtypes = [c_d, c_d, dp, dp]
             L.or_corner_region.argtypes = [c_d, c_d, c_d, dp, dp, dp]
-            L.or_forces.argtypes = [dp, c_d, c_i, dp, dp, dp, dp, ip, dp, dp, dp, ip, ip, up, dp, dp, ip]
-            L.or_run.argtypes = [dp, c_l, c_i, c_i, dp, dp, dp, dp, dp, ip, dp, dp, dp, ip, ip, up, dp, dp, ip]
-            L.or_init_accel.argtypes = [dp, c_d, c_i, dp, dp, dp, dp, dp, ip, dp, dp, dp, ip, ip, up, ip]
-            L.or_diagnostics.argtypes = [dp, c_i, dp, dp, dp, dp, ip, dp, dp, ip, ip, up, dp]
-            L.or_wall_sums.argtypes = [dp, c_d, c_i, dp, dp, dp, dp, dp]
+            L.or_forces.argtypes = [dp, c_d, c_i, dp, dp, dp, dp, ip, dp, dp, dp, dp, ip, ip, up, dp, dp, ip]
+            L.or_run.argtypes = [dp, c_l, c_i, c_i, dp, dp, dp, dp, dp, ip, dp, dp, dp, dp, ip, ip, up, dp, dp,
+                                 ip]
+            L.or_init_accel.argtypes = [dp, c_d, c_i, dp, dp, dp, dp, dp, ip, dp, dp, dp, dp, ip, ip, up, ip]
+            L.or_diagnostics.argtypes = [dp, c_i, dp, dp, dp, dp, ip, dp, dp, dp, ip, ip, up, dp]
+            L.or_wall_sums.argtypes = [dp, c_d, c_i, dp, dp, dp, dp, ip, dp, dp]
             _lib = L
     return _lib
 
@@ -81,6 +82,11 @@ def _p(a, ct):
 
 def _dp(a):
     return _p(a, ctypes.c_double)
+
+
+def _dpn(a):
+    """Double pointer, or NULL for None."""
+    return None if a is None else _dp(a)
 
 
 def _ip(a):
@@ -173,6 +179,8 @@ def param_vector(params: dict, h_min: float, search_grid: bool = True) -> np.nda
     prm[P_VX1], prm[P_VY1] = params["wall_vel_hi"]
     prm[P_MICRO] = params["micromodulus"]
     prm[P_SEARCH] = 1.0 if search_grid else 0.0
+    eps_c = params["horizon_ratio"] * h_min
+    prm[P_PE5] = math.pi * eps_c * eps_c * eps_c * eps_c * eps_c     # K_n = 18 k / (pi eps_c^5)
     return prm
 
 
@@ -181,10 +189,11 @@ class OracleProblem:
 
     X (N,2) reference positions, V (N,) volumes, grain (N,) grain ids,
     row_ptr/col the CSR reference neighbour lists (ascending columns),
-    g_cw/g_s0/g_eps per-grain bond constants, prm the parameter vector.
+    g_cw/g_s0/g_eps per-grain bond constants, prm the parameter vector,
+    g_mat (G,2) per-grain (density, bulk modulus) or None (one material: prm).
     """
 
-    def __init__(self, X, V, grain, row_ptr, col, g_cw, g_s0, g_eps, prm, v0=None):
+    def __init__(self, X, V, grain, row_ptr, col, g_cw, g_s0, g_eps, prm, v0=None, g_mat=None):
         self.X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 2)
         self.N = self.X.shape[0]
         self.V = np.ascontiguousarray(V, dtype=np.float64)
@@ -197,6 +206,7 @@ class OracleProblem:
         self.g_s0 = np.ascontiguousarray(g_s0, dtype=np.float64)
         self.g_eps = np.ascontiguousarray(g_eps, dtype=np.float64)
         self.prm = np.ascontiguousarray(prm, dtype=np.float64)
+        self.g_mat = None if g_mat is None else np.ascontiguousarray(g_mat, dtype=np.float64).reshape(-1, 2)
         self.broken = np.zeros(max(len(self.col), 1), dtype=np.uint8)
         self.u = np.zeros((self.N, 2))
         self.v = np.zeros((self.N, 2)) if v0 is None else np.array(v0, dtype=np.float64).reshape(-1, 2)
@@ -212,6 +222,13 @@ class OracleProblem:
         g_s0 = np.zeros(w.n_grains)
         g_eps = np.zeros(w.n_grains)
         grain_start = np.zeros(w.n_grains + 1, dtype=np.int64)
+        # materials (E, k_bulk, rho, Gc) per grain; the workload's params are material 0
+        mats = getattr(w, "materials", None)
+        if mats is not None:
+            props, gmat = np.asarray(mats[0], dtype=np.float64).reshape(-1, 4), np.asarray(mats[1])
+        else:
+            props = np.array([[p["E"], p["k_bulk"], p["rho"], p["Gc"]]])
+            gmat = np.zeros(w.n_grains, dtype=np.int64)
         node0 = 0
         bond0 = 0
         vel = []
@@ -230,15 +247,17 @@ class OracleProblem:
             vel.append(np.tile([vx, vy], (n, 1)))
             eps = p["horizon_ratio"] * h
             g_eps[g] = eps
-            g_cw[g], g_s0[g] = bond_constants(p["E"], p["nu"], p["Gc"], eps, int(p["micromodulus"]))
+            E_g, Gc_g = props[gmat[g], 0], props[gmat[g], 3]
+            g_cw[g], g_s0[g] = bond_constants(E_g, p["nu"], Gc_g, eps, int(p["micromodulus"]))
             node0 += n
             bond0 += len(col)
             grain_start[g + 1] = node0
         h_min = float(np.min(w.grain_geom[:, 6]))
         prm = param_vector(p, h_min, search_grid)
+        g_mat = np.stack([props[gmat, 2], props[gmat, 1]], 1) if mats is not None else None
         self = cls(np.vstack(Xs), np.concatenate(Vs), np.concatenate(grains),
                    np.concatenate(rows + [np.array([bond0], dtype=np.int32)]),
-                   np.concatenate(cols), g_cw, g_s0, g_eps, prm, np.vstack(vel))
+                   np.concatenate(cols), g_cw, g_s0, g_eps, prm, np.vstack(vel), g_mat)
         self.w = w
         self.lat = np.vstack(lats)
         self.grain_start = grain_start
@@ -254,7 +273,7 @@ class OracleProblem:
         L = lib()
         L.or_init_accel(_dp(self.prm), self.step * self.prm[P_DT], self.N, _dp(self.X), _dp(self.u),
                         _dp(self.v), _dp(self.a), _dp(self.V), _ip(self.grain), _dp(self.g_cw),
-                        _dp(self.g_s0), _dp(self.g_eps), _ip(self.row_ptr), _ip(self.col),
+                        _dp(self.g_s0), _dp(self.g_eps), _dpn(self.g_mat), _ip(self.row_ptr), _ip(self.col),
                         _up(self.broken), _ip(self.status))
         return self
 
@@ -265,7 +284,7 @@ class OracleProblem:
         parts = np.zeros((4, self.N, 2)) if want_parts else None
         L.or_run(_dp(self.prm), self.step, n_steps, self.N, _dp(self.X), _dp(self.u), _dp(self.v),
                  _dp(self.a), _dp(self.V), _ip(self.grain), _dp(self.g_cw), _dp(self.g_s0),
-                 _dp(self.g_eps), _ip(self.row_ptr), _ip(self.col), _up(self.broken),
+                 _dp(self.g_eps), _dpn(self.g_mat), _ip(self.row_ptr), _ip(self.col), _up(self.broken),
                  _dp(F), _dp(parts) if parts is not None else None, _ip(self.status))
         self.step += n_steps
         return F, parts
@@ -279,15 +298,15 @@ class OracleProblem:
         parts = np.zeros((4, self.N, 2))
         br = self.broken.copy() if keep_broken else self.broken
         L.or_forces(_dp(self.prm), t, self.N, _dp(self.X), _dp(self.u), _dp(self.v), _dp(self.V),
-                    _ip(self.grain), _dp(self.g_cw), _dp(self.g_s0), _dp(self.g_eps), _ip(self.row_ptr),
-                    _ip(self.col), _up(br), _dp(F), _dp(parts), _ip(self.status))
+                    _ip(self.grain), _dp(self.g_cw), _dp(self.g_s0), _dp(self.g_eps), _dpn(self.g_mat),
+                    _ip(self.row_ptr), _ip(self.col), _up(br), _dp(F), _dp(parts), _ip(self.status))
         return F, parts
 
     def diagnostics(self):
         out = np.zeros(7)
         lib().or_diagnostics(_dp(self.prm), self.N, _dp(self.X), _dp(self.u), _dp(self.v), _dp(self.V),
-                             _ip(self.grain), _dp(self.g_cw), _dp(self.g_eps), _ip(self.row_ptr),
-                             _ip(self.col), _up(self.broken), _dp(out))
+                             _ip(self.grain), _dp(self.g_cw), _dp(self.g_eps), _dpn(self.g_mat),
+                             _ip(self.row_ptr), _ip(self.col), _up(self.broken), _dp(out))
         return dict(KE=out[0], E_bond=out[1], E_contact=out[2], Px=out[3], Py=out[4], Lz=out[5],
                     n_broken=int(out[6]))
 
@@ -330,7 +349,8 @@ class OracleProblem:
         if t is None:
             t = self.step * self.prm[P_DT]
         out = np.zeros(16)
-        lib().or_wall_sums(_dp(self.prm), t, self.N, _dp(self.X), _dp(self.u), _dp(self.v), _dp(self.V), _dp(out))
+        lib().or_wall_sums(_dp(self.prm), t, self.N, _dp(self.X), _dp(self.u), _dp(self.v), _dp(self.V),
+                           _ip(self.grain), _dpn(self.g_mat), _dp(out))
         return out[:8].reshape(4, 2), out[8:].reshape(4, 2)
 
     def wall_reaction(self, wall, t=None):

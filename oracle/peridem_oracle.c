@@ -380,7 +380,9 @@ enum {
     P_RHO = 0, P_KN, P_RC, P_RD, P_MU, P_GX, P_GY, P_DT,
     P_WX0, P_WX1, P_WY0, P_WY1,          /* wall positions at t = 0: x_lo, x_hi, y_lo, y_hi */
     P_VX0, P_VX1, P_VY0, P_VY1,          /* wall normal velocities                           */
-    P_MICRO, P_SEARCH, P_NPARAM
+    P_MICRO, P_SEARCH,
+    P_PE5,                               /* pi eps_c^5 of K_n = 18 k / (pi eps_c^5) (materials) */
+    P_NPARAM
 };
 
 /* status word layout */
@@ -394,6 +396,7 @@ typedef struct {
     const double *V;
     const int *grain;
     const double *g_cw, *g_s0, *g_eps;
+    const double *g_mat; /* nullable: per grain (rho, k_bulk); NULL = prm's rho and K_n */
     const int *row_ptr, *col;
     unsigned char *broken;
     double t;            /* time at which the walls are evaluated */
@@ -407,6 +410,22 @@ typedef struct {
     int *head, *next;
     int *status;
 } or_sys;
+
+/* Materials (Sec. 4.1 and the material table of Sec. 5): each grain has its */
+/* own density and bulk modulus.  Contact between grains of bulk moduli k1   */
+/* and k2 uses K_n = 18 k / (pi eps_c^5) with the harmonic mean              */
+/* k = 2 k1 k2 / (k1 + k2) (equal moduli: k itself); a wall uses the grain's  */
+/* own k; damping uses the harmonic mean of the two densities (equal: rho),  */
+/* friction and mass the node's own density.                                  */
+static double harmonic(double a, double b) { return a == b ? a : 2.0 * a * b / (a + b); }
+
+static double rho_of(const or_sys *S, int g) { return S->g_mat ? S->g_mat[2 * g] : S->prm[P_RHO]; }
+
+static double kn_pair(const or_sys *S, int g, int h)
+{
+    if (!S->g_mat) return S->prm[P_KN];
+    return 18.0 * harmonic(S->g_mat[2 * g + 1], S->g_mat[2 * h + 1]) / S->prm[P_PE5];
+}
 
 /* cell index along one axis, clamped to the grid (non-finite -> 0) */
 static int grid_index(double x, double x0, double cell, int n)
@@ -494,12 +513,13 @@ static void free_grid(or_sys *S)
 /* Damping + friction of a pair, Sec. 4.2-4.3, with e pointing from x to y,   */
 /* relative velocity vr = v(x) - v(y), repulsion magnitude Fr (>= 0) and the   */
 /* partner volume Vy used in beta_d.  Adds to (fx, fy).                        */
-static void damping_friction(const double *prm, double ex, double ey, double vrx, double vry,
-                             double Fr, double Vx, double Vy, double *fx, double *fy)
+static void damping_friction(const double *prm, double Kn, double rho_d, double rho, double ex, double ey,
+                             double vrx, double vry, double Fr, double Vx, double Vy, double *fx, double *fy)
 {
-    double rho = prm[P_RHO], dt = prm[P_DT], mu = prm[P_MU];
-    /* normal damping (eq:normal-damp), Kelvin-Voigt reading */
-    double beta = 2.0 * prm[P_RD] * sqrt(prm[P_KN] * rho / Vy);
+    double dt = prm[P_DT], mu = prm[P_MU];
+    /* normal damping (eq:normal-damp), Kelvin-Voigt reading; rho_d the pair's */
+    /* density, rho the density of x (friction's eps_f = dt / (rho V_x))       */
+    double beta = 2.0 * prm[P_RD] * sqrt(Kn * rho_d / Vy);
     double vn = vrx * ex + vry * ey;
     double cd = beta * Vx * Vy * vn;
     double Fdx = -cd * ex, Fdy = -cd * ey;
@@ -530,7 +550,10 @@ static void damping_friction(const double *prm, double ex, double ey, double vrx
 static void wall_terms(const or_sys *S, int x, double single[4][2], double corner[4][2])
 {
     const double *prm = S->prm;
-    double Rc = prm[P_RC], Kn = prm[P_KN];
+    /* a rigid wall: K_n and densities of the node's own material */
+    int g = S->grain ? S->grain[x] : 0;
+    double Rc = prm[P_RC], Kn = S->grain ? kn_pair(S, g, g) : prm[P_KN];
+    double rho = S->grain ? rho_of(S, g) : prm[P_RHO];
     double px = S->p[2 * x], py = S->p[2 * x + 1];
     double vx = S->v[2 * x], vy = S->v[2 * x + 1];
     double Vx = S->V[x];
@@ -563,7 +586,7 @@ static void wall_terms(const or_sys *S, int x, double single[4][2], double corne
         double Fr = Kn * gap * Vx * A;
         double wvx = (l < 2) ? wvel[l] : 0.0, wvy = (l < 2) ? 0.0 : wvel[l];
         double gx = -Fr * ex[l], gy = -Fr * ey[l];
-        damping_friction(prm, ex[l], ey[l], vx - wvx, vy - wvy, Fr, Vx, A, &gx, &gy);
+        damping_friction(prm, Kn, rho, rho, ex[l], ey[l], vx - wvx, vy - wvy, Fr, Vx, A, &gx, &gy);
         single[l][0] = gx;
         single[l][1] = gy;
     }
@@ -581,7 +604,7 @@ static void wall_terms(const or_sys *S, int x, double single[4][2], double corne
         double Fr = Kn * (Rc - cd) * Vx * A;
         double wvx = wvel[i], wvy = wvel[j];
         double gx = -Fr * ux, gy = -Fr * uy;
-        damping_friction(prm, ux, uy, vx - wvx, vy - wvy, Fr, Vx, A, &gx, &gy);
+        damping_friction(prm, Kn, rho, rho, ux, uy, vx - wvx, vy - wvy, Fr, Vx, A, &gx, &gy);
         corner[k][0] = gx;
         corner[k][1] = gy;
     }
@@ -610,9 +633,10 @@ static void wall_force(const or_sys *S, int x, double *fx, double *fy)
 static void node_force(or_sys *S, int x, double *Fx_out, double *Fy_out, double *parts)
 {
     const double *prm = S->prm;
-    double Rc = prm[P_RC], Kn = prm[P_KN];
+    double Rc = prm[P_RC];
     int micro = (int)prm[P_MICRO];
     int g = S->grain[x];
+    double rho_x = rho_of(S, g);
     double cw = S->g_cw[g], s0 = S->g_s0[g], eps = S->g_eps[g];
     double px = S->p[2 * x], py = S->p[2 * x + 1];
     double Xx = S->X[2 * x], Xy = S->X[2 * x + 1];
@@ -668,14 +692,17 @@ static void node_force(or_sys *S, int x, double *Fx_out, double *Fy_out, double 
             if (m == 0.0) continue;
             double f = m * Vx * Vy;          /* negative: pushes x away from y */
             double gx = f * ex, gy = f * ey;
-            damping_friction(prm, ex, ey, vrx, vry, -f, Vx, Vy, &gx, &gy);
+            damping_friction(prm, kn_pair(S, g, g), rho_x, rho_x, ex, ey, vrx, vry, -f, Vx, Vy, &gx, &gy);
             Fsx += gx;
             Fsy += gy;
         } else {
             /* inter-grain contact: repulsion (eq:law-repulsive), damping, friction */
+            int gy_ = S->grain[y];
+            double Kn = kn_pair(S, g, gy_);
             double Fr = Kn * (Rc - d) * Vx * Vy;
             double gx = -Fr * ex, gy = -Fr * ey;
-            damping_friction(prm, ex, ey, vrx, vry, Fr, Vx, Vy, &gx, &gy);
+            damping_friction(prm, Kn, harmonic(rho_x, rho_of(S, gy_)), rho_x, ex, ey, vrx, vry, Fr, Vx, Vy, &gx,
+                             &gy);
             Fnx += gx;
             Fny += gy;
         }
@@ -696,12 +723,12 @@ static void node_force(or_sys *S, int x, double *Fx_out, double *Fy_out, double 
 
 static void sys_init(or_sys *S, const double *prm, int N, const double *X, const double *u, const double *v,
                      const double *V, const int *grain, const double *g_cw, const double *g_s0,
-                     const double *g_eps, const int *row_ptr, const int *col, unsigned char *broken,
-                     int *status)
+                     const double *g_eps, const double *g_mat, const int *row_ptr, const int *col,
+                     unsigned char *broken, int *status)
 {
     memset(S, 0, sizeof(*S));
     S->prm = prm; S->N = N; S->X = X; S->u = u; S->v = v; S->V = V; S->grain = grain;
-    S->g_cw = g_cw; S->g_s0 = g_s0; S->g_eps = g_eps; S->row_ptr = row_ptr; S->col = col;
+    S->g_cw = g_cw; S->g_s0 = g_s0; S->g_eps = g_eps; S->g_mat = g_mat; S->row_ptr = row_ptr; S->col = col;
     S->broken = broken; S->status = status;
     S->p = (double *)malloc(sizeof(double) * (size_t)(2 * (N > 0 ? N : 1)));
     S->max_cand = 4096;
@@ -729,11 +756,11 @@ static void all_forces(or_sys *S, double *F, double *parts)
 /* force; parts (nullable): 8N = bond | self | neighbour | wall.              */
 void or_forces(const double *prm, double t, int N, const double *X, const double *u, const double *v,
                const double *V, const int *grain, const double *g_cw, const double *g_s0,
-               const double *g_eps, const int *row_ptr, const int *col, unsigned char *broken,
-               double *F, double *parts, int *status)
+               const double *g_eps, const double *g_mat, const int *row_ptr, const int *col,
+               unsigned char *broken, double *F, double *parts, int *status)
 {
     or_sys S;
-    sys_init(&S, prm, N, X, u, v, V, grain, g_cw, g_s0, g_eps, row_ptr, col, broken, status);
+    sys_init(&S, prm, N, X, u, v, V, grain, g_cw, g_s0, g_eps, g_mat, row_ptr, col, broken, status);
     S.t = t;
     all_forces(&S, F, parts);
     sys_free(&S);
@@ -744,10 +771,10 @@ void or_forces(const double *prm, double t, int N, const double *X, const double
 /* (the orders of wall_terms).  Used for the force the aggregate exerts on a  */
 /* wall (Sec. 6, compaction: force on the top wall).                          */
 void or_wall_sums(const double *prm, double t, int N, const double *X, const double *u, const double *v,
-                  const double *V, double *out)
+                  const double *V, const int *grain, const double *g_mat, double *out)
 {
     or_sys S;
-    sys_init(&S, prm, N, X, u, v, V, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL);
+    sys_init(&S, prm, N, X, u, v, V, grain, NULL, NULL, NULL, g_mat, NULL, NULL, NULL, NULL);
     S.t = t;
     int status[8] = {0};
     S.status = status;
@@ -771,14 +798,14 @@ void or_wall_sums(const double *prm, double t, int N, const double *X, const dou
 /* state.  F_last/parts_last (nullable) receive the forces of the last step.  */
 void or_run(const double *prm, long step0, int n_steps, int N, const double *X, double *u, double *v,
             double *a, const double *V, const int *grain, const double *g_cw, const double *g_s0,
-            const double *g_eps, const int *row_ptr, const int *col, unsigned char *broken,
-            double *F_last, double *parts_last, int *status)
+            const double *g_eps, const double *g_mat, const int *row_ptr, const int *col,
+            unsigned char *broken, double *F_last, double *parts_last, int *status)
 {
-    double rho = prm[P_RHO], dt = prm[P_DT], gx = prm[P_GX], gy = prm[P_GY];
+    double dt = prm[P_DT], gx = prm[P_GX], gy = prm[P_GY];
     double half_dt = 0.5 * dt, half_dt2 = 0.5 * dt * dt;
     double *F = (double *)malloc(sizeof(double) * (size_t)(2 * (N > 0 ? N : 1)));
     or_sys S;
-    sys_init(&S, prm, N, X, u, v, V, grain, g_cw, g_s0, g_eps, row_ptr, col, broken, status);
+    sys_init(&S, prm, N, X, u, v, V, grain, g_cw, g_s0, g_eps, g_mat, row_ptr, col, broken, status);
     for (int n = 0; n < n_steps; ++n) {
         long step = step0 + n;
         /* displacement update, current position (Algorithm 1) */
@@ -787,7 +814,7 @@ void or_run(const double *prm, long step0, int n_steps, int N, const double *X, 
         all_forces(&S, F, (n == n_steps - 1) ? parts_last : NULL);
         /* acceleration and velocity update (Algorithm 1) */
         for (int x = 0; x < N; ++x) {
-            double m = rho * V[x];
+            double m = rho_of(&S, grain[x]) * V[x];
             double ax = F[2 * x] / m + gx, ay = F[2 * x + 1] / m + gy;
             v[2 * x] = v[2 * x] + half_dt * (a[2 * x] + ax);
             v[2 * x + 1] = v[2 * x + 1] + half_dt * (a[2 * x + 1] + ay);
@@ -805,14 +832,14 @@ void or_run(const double *prm, long step0, int n_steps, int N, const double *X, 
 /* (first line of Algorithm 1).                                               */
 void or_init_accel(const double *prm, double t0, int N, const double *X, const double *u, const double *v,
                    double *a, const double *V, const int *grain, const double *g_cw, const double *g_s0,
-                   const double *g_eps, const int *row_ptr, const int *col, unsigned char *broken,
-                   int *status)
+                   const double *g_eps, const double *g_mat, const int *row_ptr, const int *col,
+                   unsigned char *broken, int *status)
 {
-    double rho = prm[P_RHO], gx = prm[P_GX], gy = prm[P_GY];
+    double gx = prm[P_GX], gy = prm[P_GY];
     double *F = (double *)malloc(sizeof(double) * (size_t)(2 * (N > 0 ? N : 1)));
-    or_forces(prm, t0, N, X, u, v, V, grain, g_cw, g_s0, g_eps, row_ptr, col, broken, F, NULL, status);
+    or_forces(prm, t0, N, X, u, v, V, grain, g_cw, g_s0, g_eps, g_mat, row_ptr, col, broken, F, NULL, status);
     for (int x = 0; x < N; ++x) {
-        double m = rho * V[x];
+        double m = (g_mat ? g_mat[2 * grain[x]] : prm[P_RHO]) * V[x];
         a[2 * x] = F[2 * x] / m + gx;
         a[2 * x + 1] = F[2 * x + 1] / m + gy;
     }
@@ -824,13 +851,18 @@ void or_init_accel(const double *prm, double t0, int N, const double *X, const d
 /* KE, E_bond, E_contact, Px, Py, Lz, n_broken (directed bonds).             */
 void or_diagnostics(const double *prm, int N, const double *X, const double *u, const double *v,
                     const double *V, const int *grain, const double *g_cw, const double *g_eps,
-                    const int *row_ptr, const int *col, const unsigned char *broken, double *out)
+                    const double *g_mat, const int *row_ptr, const int *col, const unsigned char *broken,
+                    double *out)
 {
-    double rho = prm[P_RHO], Rc = prm[P_RC], Kn = prm[P_KN];
+    double Rc = prm[P_RC];
     int micro = (int)prm[P_MICRO];
     double KE = 0, Eb = 0, Ec = 0, Px = 0, Py = 0, Lz = 0, nbk = 0;
+    or_sys S;
+    memset(&S, 0, sizeof(S));
+    S.prm = prm;
+    S.g_mat = g_mat;
     for (int x = 0; x < N; ++x) {
-        double m = rho * V[x];
+        double m = rho_of(&S, grain[x]) * V[x];
         double vx = v[2 * x], vy = v[2 * x + 1];
         double px = X[2 * x] + u[2 * x], py = X[2 * x + 1] + u[2 * x + 1];
         KE += 0.5 * m * (vx * vx + vy * vy);
@@ -854,7 +886,7 @@ void or_diagnostics(const double *prm, int N, const double *X, const double *u, 
             if (grain[y] == grain[x]) continue;
             double dx = (X[2 * y] + u[2 * y]) - px, dy = (X[2 * y + 1] + u[2 * y + 1]) - py;
             double d = sqrt(dx * dx + dy * dy);
-            if (d < Rc) Ec += 0.5 * Kn * V[x] * V[y] * (Rc - d) * (Rc - d);
+            if (d < Rc) Ec += 0.5 * kn_pair(&S, grain[x], grain[y]) * V[x] * V[y] * (Rc - d) * (Rc - d);
         }
     }
     out[0] = KE; out[1] = Eb; out[2] = Ec; out[3] = Px; out[4] = Py; out[5] = Lz; out[6] = nbk;

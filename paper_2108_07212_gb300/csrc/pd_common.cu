@@ -119,20 +119,26 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int *__restr
     if (threadIdx.x == 0) blocksums[blockIdx.x] = total;
 }
 
+// Exclusive scan of the per-tile sums in place, kScanTile at a time with a
+// running carry (any number of tiles; one block).
 __global__ void __launch_bounds__(kScanThreads) k_scan_top(int *blocksums, int nblocks, const int *flag) {
     if (!*(volatile const int *)flag) return;
     __shared__ int sm[33];
-    int v[kScanItems];
+    int carry = 0;
+    for (int base = 0; base < nblocks; base += kScanTile) {
+        int v[kScanItems];
 #pragma unroll
-    for (int q = 0; q < kScanItems; ++q) {
-        int idx = threadIdx.x * kScanItems + q;
-        v[q] = idx < nblocks ? blocksums[idx] : 0;
-    }
-    block_exclusive_scan(v, sm);
+        for (int q = 0; q < kScanItems; ++q) {
+            const int idx = base + threadIdx.x * kScanItems + q;
+            v[q] = idx < nblocks ? blocksums[idx] : 0;
+        }
+        const int total = block_exclusive_scan(v, sm);
 #pragma unroll
-    for (int q = 0; q < kScanItems; ++q) {
-        int idx = threadIdx.x * kScanItems + q;
-        if (idx < nblocks) blocksums[idx] = v[q];
+        for (int q = 0; q < kScanItems; ++q) {
+            const int idx = base + threadIdx.x * kScanItems + q;
+            if (idx < nblocks) blocksums[idx] = v[q] + carry;
+        }
+        carry += total;
     }
 }
 

@@ -842,11 +842,9 @@ int pd_build_bonds(pd_ctx *c, int64_t *n_bonds_out) {
     }
     c->n_tmpl = (int)c->tmpl_first.size();
     // contact hash: power of two >= 2N buckets
+    if (c->N > (int64_t(1) << 29)) return fail(PD_EINVAL, "too many nodes for the contact grid (at most 2^29)");
     unsigned T = 1024;
     while ((int64_t)T < 2 * c->N) T <<= 1;
-    // the bucket scan has two levels of kScanTile: at most kScanTile^2 buckets
-    if ((int64_t)T > (int64_t)pd::kScanTile * pd::kScanTile)
-        return fail(PD_EINVAL, "at most 8,388,608 nodes per context (contact-grid scan)");
     c->T = T;
     c->state = 2;
     if (n_bonds_out) *n_bonds_out = (int64_t)c->col.size();

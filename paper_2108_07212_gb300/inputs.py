@@ -125,6 +125,8 @@ class Workload:
     name: str = ""
     grain_agg: np.ndarray | None = None     # aggregate of each grain (batched ensembles)
     agg_walls: np.ndarray | None = None     # (A, 8): x_lo, x_hi, y_lo, y_hi and their normal velocities
+    # (props (M, 4): E, k_bulk, rho, Gc per material; grain_material (G,)); None: params is the one material
+    materials: tuple | None = None
 
     @property
     def n_grains(self) -> int:

@@ -527,3 +527,78 @@ def test_damage_is_monotone_in_fracturing_impact():
         grew |= bool(np.any(dmg > prev))
         prev = dmg
     assert grew
+
+
+# ---------------------------------------------------------------------------
+# materials (Sec. 4.1 harmonic-mean bulk modulus; material table of Sec. 5)
+
+
+def _two_material_nodes(Rc, h, gap, v_rel, mats, rd=0.0):
+    """Two single-node grains of materials mats = [(rho1, k1), (rho2, k2)],
+    approaching head-on; K_n from the harmonic mean of k1, k2 and eps_c = 3h."""
+    V = h * h
+    (r1, k1), (r2, k2) = mats
+    keff = 2 * k1 * k2 / (k1 + k2) if k1 != k2 else k1
+    Kn = O.contact_stiffness(keff, 3 * h)
+    mu_red = r1 * r2 * V / (r1 + r2)
+    omega = math.sqrt(Kn * V * V / mu_red)
+    dt = 0.002 / omega
+    prm = _prm(1.0, Rc, rho=1.0, dt=dt, rd=rd)          # the table replaces rho and K_n
+    eps = 3 * h
+    prm[O.P_PE5] = math.pi * eps * eps * eps * eps * eps
+    X = np.array([[0.0, 0.0], [Rc + gap, 0.0]])
+    # equal and opposite momenta: the centre of mass is at rest
+    v0 = np.array([[v_rel * r2 / (r1 + r2), 0.0], [-v_rel * r1 / (r1 + r2), 0.0]])
+    P = O.OracleProblem(X, [V, V], [0, 1], [0, 0, 0], [], [1.0, 1.0], [1.0, 1.0], [1.0, 1.0], prm, v0,
+                        g_mat=[[r1, k1], [r2, k2]])
+    return P, omega, dt, V
+
+
+def test_two_materials_contact_is_spring_on_reduced_mass():
+    """Grains of densities rho1, rho2 and bulk moduli k1, k2: eq. (law-repulsive)
+    with K_n = 18 k / (pi eps^5), k = 2 k1 k2 / (k1 + k2) (Sec. 4.1), is a
+    linear spring K_n V^2 on the reduced mass m1 m2 / (m1 + m2): the contact
+    lasts pi / omega, momentum is conserved and the relative speed reverses."""
+    h, Rc = 1e-4, 0.95e-4
+    mats = [(1200.0, 1e6), (4800.0, 3e6)]
+    P, omega, dt, V = _two_material_nodes(Rc, h, 1e-9, 0.1, mats)
+    m = np.array([mats[0][0] * V, mats[1][0] * V])
+    steps = _collide(P, Rc, max_steps=400000)
+    assert steps * dt == pytest.approx(math.pi / omega, rel=0.01)
+    assert abs(m @ P.v[:, 0]) <= 1e-12 * m[0] * 0.1
+    assert P.v[0, 0] - P.v[1, 0] == pytest.approx(-0.1, rel=1e-4)
+
+
+def test_two_materials_damping_restitution_independent_of_densities():
+    """The damping reading (beta_d with the harmonic mean of the two densities)
+    keeps the pair's damping ratio at sqrt(2) r_d for any two materials, so the
+    restitution is exp(-pi zeta / sqrt(1 - zeta^2)) as for one material."""
+    h, Rc, rd = 1e-4, 0.95e-4, 0.1
+    P, omega, dt, V = _two_material_nodes(Rc, h, 1e-9, 0.1, [(1200.0, 1e6), (4800.0, 3e6)], rd=rd)
+    _collide(P, Rc, max_steps=400000)
+    zeta = math.sqrt(2.0) * rd
+    e = math.exp(-math.pi * zeta / math.sqrt(1 - zeta ** 2))
+    assert -(P.v[0, 0] - P.v[1, 0]) / 0.1 == pytest.approx(e, rel=0.01)
+
+
+def test_one_material_table_equals_single_material_run():
+    """A material table whose every grain has the parameter vector's rho and k
+    gives bit-identical forces and trajectories: the harmonic mean of equal
+    moduli is the modulus and K_n is formed in the same operation order."""
+    w = I.two_disks()
+    h = 1e-3 / 8
+    rc = w.params["rc_ratio"] * h
+    w.grain_geom[0, 1] = 1e-3 + rc * 0.25
+    w.grain_geom[1, 1] = w.grain_geom[0, 1] + 16 * h + 1.05 * rc
+    w.grain_geom[1, 5] = -1.0
+    a = O.OracleProblem.from_workload(w).init_accel()
+    p = w.params
+    w.materials = (np.array([[p["E"], p["k_bulk"], p["rho"], p["Gc"]]]), np.zeros(w.n_grains, dtype=np.int64))
+    b = O.OracleProblem.from_workload(w).init_accel()
+    assert b.g_mat is not None
+    a.run(200)
+    b.run(200)
+    assert np.array_equal(a.u, b.u) and np.array_equal(a.v, b.v)
+    Fa, _ = a.forces()
+    Fb, _ = b.forces()
+    assert np.array_equal(Fa, Fb)
