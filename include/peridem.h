@@ -252,6 +252,25 @@ int pd_info(pd_ctx *ctx, double *out);
 int pd_set_aggregates(pd_ctx *ctx, int n_agg, const int32_t *grain_agg, const double *agg_walls);
 
 /*
+ * Materials (Sec. 4.1 and the material table of Sec. 5): grain g takes the
+ * properties of material grain_material[g] (int32[G], 0 <= m < n_mat), read
+ * from props (double[4 n_mat], caller-owned, copied): E (Pa), bulk modulus k
+ * (Pa), density rho (kg/m^3) and fracture energy Gc (J/m^2).  Its bond
+ * constants c_w and s0 (Table 1) follow from its E and Gc.  Contact between
+ * grains of bulk moduli k1 and k2 uses K_n = 18 k / (pi eps_c^5) with the
+ * harmonic mean k = 2 k1 k2 / (k1 + k2) (Sec. 4.1); a wall, a rigid body,
+ * uses the grain's own k.  The damping coefficient beta_d takes the harmonic
+ * mean of the two densities (so that a pair's damping ratio stays sqrt(2) r_d);
+ * friction's regularisation dt / (rho V_x) and the nodal mass rho V take the
+ * node's own density.  Without this call every grain has the material of
+ * pd_params.  Call after pd_mesh_grains and before pd_bind_arena; the learned
+ * surrogate runs with one material only.
+ * Errors: PD_ESTATE (order, or a surrogate configured), PD_EINVAL (non-positive
+ * or non-finite property, material index out of range).
+ */
+int pd_set_materials(pd_ctx *ctx, int n_mat, const double *props, const int32_t *grain_material);
+
+/*
  * Autotuner: time candidate step paths on the current state -- a graph of
  * separate kernels or one persistent cooperative kernel per 16 steps, each with
  * the force phase fused (4 or 8 threads per node) or split (1, 2, 4 or 8),

@@ -33,7 +33,7 @@ SYMBOLS = ("pd_last_error", "pd_create", "pd_destroy", "pd_mesh_grains", "pd_bui
            "pd_mlp_arena_bytes", "pd_mlp_bind_arena", "pd_mlp_set_params", "pd_mlp_get_params", "pd_mlp_forward",
            "pd_mlp_loss_grad", "pd_mlp_train_step", "pd_surrogate_setup", "pd_surrogate_set_mlp",
            "pd_surrogate_enable", "pd_surrogate_sample", "pd_surrogate_stats", "pd_surrogate_inspect",
-           "pd_diagnostics_noalloc", "pd_observables")
+           "pd_diagnostics_noalloc", "pd_observables", "pd_set_materials")
 
 
 class PdParams(ctypes.Structure):
@@ -83,6 +83,7 @@ def load():
             L.pd_set_timing.argtypes = [vp, ip]
             L.pd_kernel_times.argtypes = [vp, vp]
             L.pd_set_aggregates.argtypes = [vp, ip, vp, vp]
+            L.pd_set_materials.argtypes = [vp, ip, vp, vp]
             L.pd_autotune.argtypes = [vp, vp]
             L.pd_set_path.argtypes = [vp, ip, ip, ip]
             L.pd_mlp_create.argtypes = [ctypes.POINTER(c_void_p), ip, vp]
@@ -174,6 +175,11 @@ class Simulation:
             ga = np.ascontiguousarray(agg, dtype=np.int32)
             walls = np.ascontiguousarray(workload.agg_walls, dtype=np.float64).reshape(-1)
             _check(L.pd_set_aggregates(ctx, int(walls.size // 8), _ptr(ga), _ptr(walls)))
+        mats = getattr(workload, "materials", None)
+        if mats is not None:
+            props = np.ascontiguousarray(mats[0], dtype=np.float64).reshape(-1)
+            gm = np.ascontiguousarray(mats[1], dtype=np.int32)
+            _check(L.pd_set_materials(ctx, int(props.size // 4), _ptr(props), _ptr(gm)))
         self.surrogate_basis = None
         if surrogate is not None:
             # surrogate = dict(basis=..., lambda_=..., n_modes=, judge_every=, gate=, err_tol=) or a callable

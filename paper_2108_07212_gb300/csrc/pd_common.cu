@@ -186,14 +186,14 @@ __global__ void __launch_bounds__(kBlock) k_diag_partial(DevPtrs d, KParams k, i
     for (int q = 0; q < PD_DIAG_COUNT; ++q) acc[q] = 0.0;
     const double2 *v = d.v[vcur];
     for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < k.N; x += gridDim.x * blockDim.x) {
-        double m = k.rho * d.V[x];
+        int g = d.grain[x];
+        double m = (k.mat ? d.g_rho[g] : k.rho) * d.V[x];
         double2 vx = v[x], X = d.X[x], u = d.u[x];
         double px = X.x + u.x, py = X.y + u.y;
         acc[PD_DIAG_KE] += 0.5 * m * (vx.x * vx.x + vx.y * vx.y);
         acc[PD_DIAG_PX] += m * vx.x;
         acc[PD_DIAG_PY] += m * vx.y;
         acc[PD_DIAG_LZ] += m * (px * vx.y - py * vx.x);
-        int g = d.grain[x];
         double cw = d.g_cw[g], eps = d.g_eps[g];
         int r0 = d.row_ptr[x], r1 = d.row_ptr[x + 1];
         for (int b = r0; b < r1; ++b) {
@@ -306,8 +306,11 @@ __global__ void __launch_bounds__(kBlock) k_wall_sums(DevPtrs d, KParams k, int 
     const int ag = d.g_agg[d.grain[i]];
     if (far_from_walls<false>(d, i, ag)) return;
     const double2 p = d.p[i], v = d.v[vcur][i];
+    const int g = d.grain[i];
+    const AggParams &A = d.agg[ag];
     double single[4][2], corner[4][2];
-    wall_terms64(k, d.agg[ag], *d.t_now, p.x, p.y, v.x, v.y, d.V[i], single, corner, nullptr);
+    wall_terms64(k, A, k.mat ? 18.0 * d.g_k[g] / A.pe5 : A.Kn, k.mat ? d.g_rho[g] : k.rho, *d.t_now, p.x, p.y, v.x,
+                 v.y, d.V[i], single, corner, nullptr);
     double *o = out + 16 * (size_t)ag;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {

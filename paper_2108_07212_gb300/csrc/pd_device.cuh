@@ -46,25 +46,34 @@ __device__ __forceinline__ unsigned cell_bucket(int cx, int cy, int agg, unsigne
 }
 
 // ---------------------------------------------------------------------------
+// materials (Sec. 4.1): contact between bulk moduli k1, k2 uses the harmonic
+// mean 2 k1 k2 / (k1 + k2) in K_n = 18 k / (pi eps_c^5); damping the harmonic
+// mean of the two densities; equal values give the value itself
+__device__ __forceinline__ double harmonic64(double a, double b) { return a == b ? a : 2.0 * a * b / (a + b); }
+// (float: the contact stiffnesses reach 1e25, so a * b would overflow; a * (b / (a + b)) does not)
+__device__ __forceinline__ float harmonic32(float a, float b) { return a == b ? a : 2.0f * a * (b / (a + b)); }
+
+// ---------------------------------------------------------------------------
 // FP64 laws
 
 // Normal damping (Sec. 4.3, Kelvin-Voigt: -beta_d V_x V_y (v(x,y).e) e with
-// beta_d = 2 r_d sqrt(K_n rho / V_y)) and regularised Coulomb friction
+// beta_d = 2 r_d sqrt(K_n rho_d / V_y)) and regularised Coulomb friction
 // (Sec. 4.2: slip -mu |F_r| v_perp/|v_perp| when |v_perp| > v_thr =
 // mu |F_r| dt / (rho V_x), else the sticking force -(rho V_x / dt) v_perp).
 // e points from x to y, (vrx, vry) = v(x) - v(y), Fr = |F_r|, Vy the partner
-// volume (|S_l| for a wall).  Adds to (fx, fy).
-__device__ __forceinline__ void damping_friction64(const KParams &k, double Kn, double ex, double ey, double vrx,
-                                                   double vry, double Fr, double Vx, double Vy, double &fx,
-                                                   double &fy) {
-    double beta = 2.0 * k.rd * sqrt(Kn * k.rho / Vy);
+// volume (|S_l| for a wall); rho_d the pair's density (the harmonic mean of
+// the two grains' densities), rho the density of x.  Adds to (fx, fy).
+__device__ __forceinline__ void damping_friction64(const KParams &k, double Kn, double rho_d, double rho,
+                                                   double ex, double ey, double vrx, double vry, double Fr, double Vx,
+                                                   double Vy, double &fx, double &fy) {
+    double beta = 2.0 * k.rd * sqrt(Kn * rho_d / Vy);
     double vn = vrx * ex + vry * ey;
     double cd = beta * Vx * Vy * vn;
     double Fdx = -cd * ex, Fdy = -cd * ey;
     double vtx = vrx - vn * ex, vty = vry - vn * ey;
     double vt = sqrt(vtx * vtx + vty * vty);
-    double vthr = k.mu * Fr * k.dt / (k.rho * Vx);
-    double c = (vt > vthr) ? (k.mu * Fr / vt) : (k.rho * Vx / k.dt);
+    double vthr = k.mu * Fr * k.dt / (rho * Vx);
+    double c = (vt > vthr) ? (k.mu * Fr / vt) : (rho * Vx / k.dt);
     double Ffx = -c * vtx, Ffy = -c * vty;
     fx += Fdx + Ffx;
     fy += Fdy + Ffy;
@@ -145,16 +154,17 @@ __device__ __forceinline__ void corner_region_stable(double di, double dj, doubl
 }
 
 // Wall contact (Sec. 4.5, eq:wall-repulsive, eq:wall-total) of a node at p
-// with velocity v and volume Vx against the four walls of its aggregate at
+// with velocity v, volume Vx, contact stiffness Kn and density rho (its own
+// material: a wall is rigid) against the four walls of its aggregate at
 // time t (position w0 + v_w t, normal velocity v_w).  The repulsion of each
 // wall uses the circular segment S_l of B_Rc(p) beyond it; corners subtract
 // the S_li cap S_lj term (inclusion-exclusion); friction and damping follow by
 // substituting e -> e^l, V_y -> |S_l|, p(y) -> c_l.  A node past a wall is
 // treated as touching it and counted in status[PD_STATUS_PENETRATION].
-__device__ __forceinline__ void wall_terms64(const KParams &k, const AggParams &A, double t, double px, double py,
-                                             double vx, double vy, double Vx, double (&single)[4][2],
-                                             double (&corner)[4][2], int *status) {
-    const double Rc = A.Rc, Kn = A.Kn;
+__device__ __forceinline__ void wall_terms64(const KParams &k, const AggParams &A, double Kn, double rho, double t,
+                                             double px, double py, double vx, double vy, double Vx,
+                                             double (&single)[4][2], double (&corner)[4][2], int *status) {
+    const double Rc = A.Rc;
     double d[4], ex[4], ey[4];
     d[0] = px - (A.w0[0] + A.wv[0] * t); ex[0] = -1.0; ey[0] = 0.0;
     d[1] = (A.w0[1] + A.wv[1] * t) - px; ex[1] = 1.0;  ey[1] = 0.0;
@@ -179,7 +189,7 @@ __device__ __forceinline__ void wall_terms64(const KParams &k, const AggParams &
         double Fr = Kn * gap * Vx * Ar;
         double wvx = (l < 2) ? A.wv[l] : 0.0, wvy = (l < 2) ? 0.0 : A.wv[l];
         double gx = -Fr * ex[l], gy = -Fr * ey[l];
-        damping_friction64(k, Kn, ex[l], ey[l], vx - wvx, vy - wvy, Fr, Vx, Ar, gx, gy);
+        damping_friction64(k, Kn, rho, rho, ex[l], ey[l], vx - wvx, vy - wvy, Fr, Vx, Ar, gx, gy);
         single[l][0] = gx;
         single[l][1] = gy;
     }
@@ -196,7 +206,7 @@ __device__ __forceinline__ void wall_terms64(const KParams &k, const AggParams &
         double ux = cx / cd, uy = cy / cd;
         double Fr = Kn * (Rc - cd) * Vx * Ar;
         double gx = -Fr * ux, gy = -Fr * uy;
-        damping_friction64(k, Kn, ux, uy, vx - A.wv[i], vy - A.wv[j], Fr, Vx, Ar, gx, gy);
+        damping_friction64(k, Kn, rho, rho, ux, uy, vx - A.wv[i], vy - A.wv[j], Fr, Vx, Ar, gx, gy);
         corner[c][0] = gx;
         corner[c][1] = gy;
     }
@@ -204,11 +214,11 @@ __device__ __forceinline__ void wall_terms64(const KParams &k, const AggParams &
 
 // Wall force on a node at (px, py) with velocity (vx, vy) and volume Vx:
 // eq:wall-total, the walls' own segments in order minus the corner terms.
-__device__ __forceinline__ void wall_force64(const KParams &k, const AggParams &A, double t, double px, double py,
-                                             double vx, double vy, double Vx, double &Fx_out, double &Fy_out,
-                                             int *status) {
+__device__ __forceinline__ void wall_force64(const KParams &k, const AggParams &A, double Kn, double rho, double t,
+                                             double px, double py, double vx, double vy, double Vx, double &Fx_out,
+                                             double &Fy_out, int *status) {
     double single[4][2], corner[4][2];
-    wall_terms64(k, A, t, px, py, vx, vy, Vx, single, corner, status);
+    wall_terms64(k, A, Kn, rho, t, px, py, vx, vy, Vx, single, corner, status);
     double Fx = 0.0, Fy = 0.0;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
@@ -258,10 +268,10 @@ __device__ __forceinline__ float ff_diff(float ah, float al, float bh, float bl)
     return __fsub_rn(ah, bh) + (al - bl);
 }
 
-__device__ __forceinline__ void damping_friction32(float rd, float Kn, float rho, float dt, float mu, float ex,
-                                                   float ey, float vrx, float vry, float Fr, float Vx, float Vy,
-                                                   float &fx, float &fy) {
-    float beta = 2.0f * rd * sqrtf(Kn * rho / Vy);
+__device__ __forceinline__ void damping_friction32(float rd, float Kn, float rho_d, float rho, float dt, float mu,
+                                                   float ex, float ey, float vrx, float vry, float Fr, float Vx,
+                                                   float Vy, float &fx, float &fy) {
+    float beta = 2.0f * rd * sqrtf(Kn * rho_d / Vy);
     float vn = vrx * ex + vry * ey;
     float cd = beta * Vx * Vy * vn;
     float vtx = vrx - vn * ex, vty = vry - vn * ey;
@@ -491,10 +501,11 @@ __device__ __forceinline__ bool bonded_intact(const DevPtrs &d, const KParams &k
 }
 
 // Acceleration and velocity update of node i (Algorithm 1) plus the optional
-// per-part force output; run by one lane per node.
+// per-part force output; run by one lane per node.  m = rho V (FP64 path) or
+// inv_m = 1 / (rho V) (RECIP, FP32 split).
 template <bool PERSIST, bool RECIP = false>
 __device__ __forceinline__ void finish_node(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
-                                            double2 vi, double Vi, double Fbx, double Fby, double Fsx, double Fsy,
+                                            double2 vi, double m, double Fbx, double Fby, double Fsx, double Fsy,
                                             double Fnx, double Fny, double Fwx, double Fwy, double inv_m = 0.0) {
     const double Fx = __dadd_rn(__dadd_rn(__dadd_rn(Fbx, Fsx), Fnx), Fwx);
     const double Fy = __dadd_rn(__dadd_rn(__dadd_rn(Fby, Fsy), Fny), Fwy);
@@ -504,7 +515,6 @@ __device__ __forceinline__ void finish_node(const DevPtrs &d, const KParams &k, 
         ax = fma(Fx, inv_m, k.gx);
         ay = fma(Fy, inv_m, k.gy);
     } else {
-        const double m = __dmul_rn(k.rho, Vi);
         ax = __dadd_rn(__ddiv_rn(Fx, m), k.gx);
         ay = __dadd_rn(__ddiv_rn(Fy, m), k.gy);
     }
@@ -617,6 +627,7 @@ __device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k,
     // ascending node index), self-contact (Sec. 4.4), inter-grain contact
     // (Secs. 4.1-4.3)
     const double Rc = A.Rc;
+    const double rho_i = k.mat ? __ldg(&d.g_rho[gi]) : k.rho;
     const int nc = active ? ldm<PERSIST>(&d.nbr_cnt[ii]) : 0;
     const double2 vi = ldm<PERSIST>(&d.v[vin][ii]);
     double Fsx = 0.0, Fsy = 0.0, Fnx = 0.0, Fny = 0.0;
@@ -634,7 +645,8 @@ __device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k,
         const double Vj = __ldg(&d.V[j]);
         const double2 vj = ldm<PERSIST>(&d.v[vin][j]);
         double vrx = vi.x - vj.x, vry = vi.y - vj.y;
-        if (__ldg(&d.grain[j]) == gi) {
+        const int gj = __ldg(&d.grain[j]);
+        if (gj == gi) {
             if (bonded_intact(d, k, ii, r0, r1, j)) continue;
             const double2 Xj = __ldg(&d.X[j]);
             double xix = Xj.x - Xi.x, xiy = Xj.y - Xi.y;
@@ -647,13 +659,19 @@ __device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k,
             if (m == 0.0) continue;
             double f = m * Vi * Vj;
             double gx = f * ex, gy = f * ey;
-            damping_friction64(k, A.Kn, ex, ey, vrx, vry, -f, Vi, Vj, gx, gy);
+            const double Kn = k.mat ? 18.0 * __ldg(&d.g_k[gi]) / A.pe5 : A.Kn;
+            damping_friction64(k, Kn, rho_i, rho_i, ex, ey, vrx, vry, -f, Vi, Vj, gx, gy);
             Fsx += gx;
             Fsy += gy;
         } else {
-            double Fr = A.Kn * (Rc - dd) * Vi * Vj;
+            double Kn = A.Kn, rho_d = rho_i;
+            if (k.mat) {
+                Kn = 18.0 * harmonic64(__ldg(&d.g_k[gi]), __ldg(&d.g_k[gj])) / A.pe5;
+                rho_d = harmonic64(rho_i, __ldg(&d.g_rho[gj]));
+            }
+            double Fr = Kn * (Rc - dd) * Vi * Vj;
             double gx = -Fr * ex, gy = -Fr * ey;
-            damping_friction64(k, A.Kn, ex, ey, vrx, vry, Fr, Vi, Vj, gx, gy);
+            damping_friction64(k, Kn, rho_d, rho_i, ex, ey, vrx, vry, Fr, Vi, Vj, gx, gy);
             Fnx += gx;
             Fny += gy;
         }
@@ -674,11 +692,17 @@ __device__ __forceinline__ void node_epilogue64(const DevPtrs &d, const KParams 
     const double2 pi = ldm<PERSIST>(&d.p[i]);
     const double2 vi = ldm<PERSIST>(&d.v[vin][i]);
     const double Vi = __ldg(&d.V[i]);
-    const int ag = __ldg(&d.g_agg[__ldg(&d.grain[i])]);
+    const int gi = __ldg(&d.grain[i]);
+    const int ag = __ldg(&d.g_agg[gi]);
+    const AggParams &A = d.agg[ag];
+    const double rho = k.mat ? __ldg(&d.g_rho[gi]) : k.rho;
     double Fwx = 0.0, Fwy = 0.0;
-    if (!far_from_walls<PERSIST>(d, i, ag))
-        wall_force64(k, d.agg[ag], ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, Vi, Fwx, Fwy, d.status);
-    finish_node<PERSIST>(d, k, i, vin, update_v, vi, Vi, f.bx, f.by, f.sx, f.sy, f.nx, f.ny, Fwx, Fwy);
+    if (!far_from_walls<PERSIST>(d, i, ag)) {
+        const double Kn = k.mat ? 18.0 * __ldg(&d.g_k[gi]) / A.pe5 : A.Kn;
+        wall_force64(k, A, Kn, rho, ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, Vi, Fwx, Fwy, d.status);
+    }
+    finish_node<PERSIST>(d, k, i, vin, update_v, vi, __dmul_rn(rho, Vi), f.bx, f.by, f.sx, f.sy, f.nx, f.ny, Fwx,
+                         Fwy);
 }
 
 // FP32-split forces of node i: the same laws and lane layout, with the bond,
@@ -796,7 +820,7 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
     const int nc = active ? ldm<PERSIST>(&d.nbr_cnt[ii]) : 0;
     // start-of-step velocity (FP64; read only by nodes with candidates)
     const double2 vi64 = nc > 0 ? ldm<PERSIST>(&d.v[vin][ii]) : make_double2(0.0, 0.0);
-    const float rd = k.rdf, rho = k.rhof, dt = k.dtf, mu = k.muf;
+    const float rd = k.rdf, rho = gc.w, dt = k.dtf, mu = k.muf;     // rho: this grain's density
     float Fsx = 0.f, Fsy = 0.f, Fnx = 0.f, Fny = 0.f;
     for (int q = lane; q < nc; q += LANES) {
         const int j = ldm<PERSIST>(&d.nbr[(size_t)q * k.N + ii]);
@@ -837,13 +861,17 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
             if (m == 0.f) continue;
             const float f = m * Vi * Vj;
             float gx = f * ex, gy = f * ey;
-            damping_friction32(rd, Kn, rho, dt, mu, ex, ey, vrx, vry, -f, Vi, Vj, gx, gy);
+            const float Kns = k.mat ? __ldg(&d.g_kf[gi]) : Kn;
+            damping_friction32(rd, Kns, rho, rho, dt, mu, ex, ey, vrx, vry, -f, Vi, Vj, gx, gy);
             Fsx += gx;
             Fsy += gy;
         } else {
-            const float Fr = Kn * overlap * Vi * Vj;
+            // the harmonic mean of the grains' own K_n is K_n of the harmonic-mean modulus
+            const float Knp = k.mat ? harmonic32(__ldg(&d.g_kf[gi]), __ldg(&d.g_kf[gj])) : Kn;
+            const float Fr = Knp * overlap * Vi * Vj;
             float gx = -Fr * ex, gy = -Fr * ey;
-            damping_friction32(rd, Kn, rho, dt, mu, ex, ey, vrx, vry, Fr, Vi, Vj, gx, gy);
+            damping_friction32(rd, Knp, harmonic32(rho, __ldg(&d.gc[gj]).w), rho, dt, mu, ex, ey, vrx, vry, Fr, Vi,
+                               Vj, gx, gy);
             Fnx += gx;
             Fny += gy;
         }
@@ -867,7 +895,10 @@ __device__ __forceinline__ void node_epilogue32(const DevPtrs &d, const KParams 
     const bool walls = !far_from_walls<PERSIST>(d, i, ag);
     if (walls) {
         const double2 pi = position64<PERSIST>(d, i);
-        wall_force64(k, d.agg[ag], ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, __ldg(&d.V[i]), Fwx, Fwy,
+        const AggParams &A = d.agg[ag];
+        const double Kn = k.mat ? 18.0 * __ldg(&d.g_k[gi]) / A.pe5 : A.Kn;
+        const double rho = k.mat ? __ldg(&d.g_rho[gi]) : k.rho;
+        wall_force64(k, A, Kn, rho, ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, __ldg(&d.V[i]), Fwx, Fwy,
                      d.status);
     }
     if (k.store)

@@ -182,6 +182,9 @@ struct pd_ctx {
     std::vector<int32_t> grain;
     std::vector<double> V, v0;  // N, 2N
     std::vector<double> g_h, g_cw, g_s0, g_eps, g_cx, g_cy, g_R;
+    // materials (pd_set_materials): per grain density and bulk modulus
+    std::vector<double> g_rho, g_k;
+    bool has_mat = false;
     std::vector<int64_t> g_start;
     std::vector<Outline> g_outline;  // per grain, local frame, physical units
     // bonds (host)
@@ -242,7 +245,8 @@ void compute_aggregates(pd_ctx *c) {
         double h = hmin[a] < 1e300 ? hmin[a] : c->g_h[0];
         double eps_c = p.horizon_ratio * h;
         A.Rc = p.rc_ratio * h;
-        A.Kn = 18.0 * p.k_bulk / (kPiAgg * eps_c * eps_c * eps_c * eps_c * eps_c);
+        A.pe5 = kPiAgg * eps_c * eps_c * eps_c * eps_c * eps_c;
+        A.Kn = 18.0 * p.k_bulk / A.pe5;
         const double *w = &c->agg_walls[8 * (size_t)a];
         A.w0[0] = w[0]; A.w0[1] = w[1]; A.w0[2] = w[2]; A.w0[3] = w[3];
         A.wv[0] = w[4]; A.wv[1] = w[5]; A.wv[2] = w[6]; A.wv[3] = w[7];
@@ -338,6 +342,9 @@ size_t layout(pd_ctx *c, char *base) {
     carve(base, off, d.g_s0, G);
     carve(base, off, d.g_eps, G);
     carve(base, off, d.g_agg, G);
+    carve(base, off, d.g_rho, G);
+    carve(base, off, d.g_k, G);
+    carve(base, off, d.g_kf, G);
     carve(base, off, d.agg, (size_t)c->n_agg);
     carve(base, off, d.key, N);
     carve(base, off, d.cell, N);
@@ -712,6 +719,9 @@ int pd_mesh_grains(pd_ctx *c, int n_shapes, const int32_t *shape_loop_start, con
             c->g_s0[g] = std::sqrt(5.0 * kPi * p.Gc / (9.0 * p.E * eps));
         }
     }
+    c->g_rho.assign(c->G, p.rho);
+    c->g_k.assign(c->G, p.k_bulk);
+    c->has_mat = false;
     c->n_agg = 1;
     c->g_agg.assign(c->G, 0);
     c->agg_walls = {p.wall_lo[0], p.wall_hi[0], p.wall_lo[1], p.wall_hi[1],
@@ -887,6 +897,7 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     k.muf = (float)p.friction;
     k.dtf = (float)p.dt;
     k.guard = 1e-4f;
+    k.mat = c->has_mat ? 1 : 0;
     // one rebuild trigger for all aggregates: the smallest (the most cautious)
     k.dmax2 = c->aggp[0].dmax2;
     for (const pd::AggParams &A : c->aggp) k.dmax2 = std::min(k.dmax2, A.dmax2);
@@ -926,6 +937,11 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     PD_CUDA(cudaMemcpyAsync(d.g_s0, c->g_s0.data(), 8 * G, cudaMemcpyHostToDevice, s));
     PD_CUDA(cudaMemcpyAsync(d.g_eps, c->g_eps.data(), 8 * G, cudaMemcpyHostToDevice, s));
     PD_CUDA(cudaMemcpyAsync(d.g_agg, c->g_agg.data(), 4 * G, cudaMemcpyHostToDevice, s));
+    PD_CUDA(cudaMemcpyAsync(d.g_rho, c->g_rho.data(), 8 * G, cudaMemcpyHostToDevice, s));
+    PD_CUDA(cudaMemcpyAsync(d.g_k, c->g_k.data(), 8 * G, cudaMemcpyHostToDevice, s));
+    std::vector<float> gkf(G);
+    for (size_t g = 0; g < G; ++g) gkf[g] = (float)(18.0 * c->g_k[g] / c->aggp[c->g_agg[g]].pe5);
+    PD_CUDA(cudaMemcpyAsync(d.g_kf, gkf.data(), 4 * G, cudaMemcpyHostToDevice, s));
     PD_CUDA(cudaMemcpyAsync(d.agg, c->aggp.data(), sizeof(pd::AggParams) * c->aggp.size(), cudaMemcpyHostToDevice, s));
     PD_CUDA(cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), s));
     PD_CUDA(cudaMemsetAsync(d.t_now, 0, sizeof(double), s));
@@ -1039,11 +1055,11 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
             gcf[4 * g] = (float)c->g_cw[g];
             gcf[4 * g + 1] = (float)c->g_s0[g];
             gcf[4 * g + 2] = (float)c->g_eps[g];
-            gcf[4 * g + 3] = 0.f;
+            gcf[4 * g + 3] = (float)c->g_rho[g];
         }
         PD_CUDA(cudaMemcpyAsync(d.gc, gcf.data(), 16 * G, cudaMemcpyHostToDevice, s));
         invm.resize(G);
-        for (size_t g = 0; g < G; ++g) invm[g] = 1.0 / (p.rho * c->V[c->g_start[g]]);
+        for (size_t g = 0; g < G; ++g) invm[g] = 1.0 / (c->g_rho[g] * c->V[c->g_start[g]]);
         PD_CUDA(cudaMemcpyAsync(d.g_invm, invm.data(), 8 * G, cudaMemcpyHostToDevice, s));
     }
     c->vcur = 0;
@@ -1264,6 +1280,35 @@ int pd_status(pd_ctx *c, int32_t *out) {
     return PD_OK;
 }
 
+int pd_set_materials(pd_ctx *c, int n_mat, const double *props, const int32_t *grain_material) {
+    if (int r = check_ctx(c, 1)) return r;
+    if (c->state > 2) return fail(PD_ESTATE, "pd_set_materials must come before pd_bind_arena");
+    if (c->sur_cfg) return fail(PD_ESTATE, "the surrogate runs with one material: set materials before it");
+    if (n_mat < 1 || !props || !grain_material) return fail(PD_EINVAL, "n_mat >= 1 and non-null arrays required");
+    for (int m = 0; m < n_mat; ++m)
+        for (int q = 0; q < 4; ++q)
+            if (!(props[4 * m + q] > 0.0) || !std::isfinite(props[4 * m + q]))
+                return fail(PD_EINVAL, "material properties must be positive and finite");
+    for (int g = 0; g < c->G; ++g)
+        if (grain_material[g] < 0 || grain_material[g] >= n_mat) return fail(PD_EINVAL, "grain material out of range");
+    const pd_params &p = c->prm;
+    for (int g = 0; g < c->G; ++g) {
+        const double *m = props + 4 * (size_t)grain_material[g];
+        const double E = m[0], Gc = m[3], eps = c->g_eps[g];
+        if (p.micromodulus == PD_MICRO_CONSTANT) {
+            c->g_cw[g] = 6.0 * E / (kPi * eps * eps * eps * (1.0 - p.nu));
+            c->g_s0[g] = std::sqrt(4.0 * kPi * Gc / (9.0 * E * eps));
+        } else {
+            c->g_cw[g] = 24.0 * E / (kPi * eps * eps * eps * (1.0 - p.nu));
+            c->g_s0[g] = std::sqrt(5.0 * kPi * Gc / (9.0 * E * eps));
+        }
+        c->g_k[g] = m[1];
+        c->g_rho[g] = m[2];
+    }
+    c->has_mat = true;
+    return PD_OK;
+}
+
 int pd_set_aggregates(pd_ctx *c, int n_agg, const int32_t *grain_agg, const double *agg_walls) {
     if (int r = check_ctx(c, 1)) return r;
     if (c->state > 2) return fail(PD_ESTATE, "pd_set_aggregates must come before pd_bind_arena");
@@ -1391,6 +1436,7 @@ int pd_surrogate_setup(pd_ctx *c, int n_modes, const float *basis, const float *
     if (int r = check_ctx(c, 2)) return r;
     if (c->state != 2) return fail(PD_ESTATE, "pd_surrogate_setup must come before pd_bind_arena");
     if (c->prm.precision != PD_FP32_SPLIT) return fail(PD_EINVAL, "the surrogate runs in the FP32-split path");
+    if (c->has_mat) return fail(PD_EINVAL, "the surrogate runs with one material");
     if (n_modes < 8 || n_modes > 32 || n_modes % 8 || !basis || !lambda || judge_every < 1 || !(gate > 0) ||
         !(err_tol > 0))
         return fail(PD_EINVAL,

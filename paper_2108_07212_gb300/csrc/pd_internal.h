@@ -33,6 +33,7 @@ constexpr long long kBarrierSpins = 16LL * 1000 * 1000;
 // aggregate's smallest lattice spacing).
 struct AggParams {
     double Rc, Kn;
+    double pe5;            // pi eps_c^5: K_n = 18 k / pe5 for a pair's bulk modulus k (materials)
     double w0[4], wv[4];   // walls x_lo, x_hi, y_lo, y_hi at t = 0 and their normal velocities
     double ox, oy, cell;   // hash-grid origin and cell side (>= R_c)
     double inv_cell;       // 1 / cell
@@ -58,6 +59,10 @@ struct DevPtrs {
     double *g_cw, *g_s0, *g_eps;
     int *g_agg;
     AggParams *agg;
+    // materials: per grain density, bulk modulus (FP64) and its own-material
+    // contact stiffness 18 k / (pi eps_c^5) as a float (FP32-split contact laws)
+    double *g_rho, *g_k;
+    float *g_kf;
     // contact hash grid (T buckets)
     int *key, *count, *start, *cursor, *sorted, *blocksums;
     int2 *cell;         // hash-grid cell (x, y) of every node at the last rebuild
@@ -84,7 +89,7 @@ struct DevPtrs {
     float4 *pq;         // shifted position (p + shift) as a float-float pair: (hi x, hi y, lo x, lo y)
     double2 *xs;        // X + the aggregate's shift (FP64)
     uint32_t *colx;     // bond columns with the lattice offset n = di^2 + dj^2 in the top 4 bits
-    float4 *gc;         // per grain: (c_w, s0, eps, 0) as floats
+    float4 *gc;         // per grain: (c_w, s0, eps, rho) as floats
     double *g_invm;     // per grain: 1 / (rho V)
     int4 *wall_cell;    // per aggregate: hash-grid cells of its walls x_lo, x_hi, y_lo, y_hi at the current time
     // autotuner backup of the state
@@ -132,6 +137,7 @@ struct KParams {
     float rhof, rdf, muf, dtf;   // the same as floats (FP32-split contact laws)
     float guard;        // FP32-split: |(|s| - s0)| < guard * s0 re-decides breaking in FP64
     float dmax2;        // smallest (kSkinTrigger skin)^2 of the aggregates: rebuild trigger
+    int mat;            // 1: per-grain materials (K_n per pair, densities per grain)
     int micro, store;
     int lanes;          // threads per node in the force kernels (1, 4 or 8)
     int split;          // 1: lane sums through global memory and a separate epilogue pass

@@ -212,6 +212,28 @@ def two_disks(h_ratio: int = 8, gap: float = 0.5e-3, floor_gap: float | None = N
     return _mk([disk_shape()], [0, 0], ggeom, params, n_steps, f"two_disks_h{h_ratio}")
 
 
+def two_material_disks(**over) -> Workload:
+    """Two disks of different materials (the material table of Sec. 5 lists a
+    stiff and a soft one): the lower disk has the default soft material (E =
+    1e7 Pa, k = 1e6 Pa, rho = 1200 kg/m^3, Gc = 50 J/m^2), the upper one twice
+    its E, density and Gc and three times its bulk modulus (the same elastic
+    wave speed, so the same stable time step).  They start R_c / 4 above the
+    floor and 1.05 R_c apart, the upper one moving down at 1 m/s."""
+    w = two_disks(**over)
+    h = 1e-3 / 8
+    rc = w.params["rc_ratio"] * h
+    w.grain_geom[0, 1] = 1e-3 + 0.25 * rc
+    w.grain_geom[1, 0] = 0.25e-3
+    w.grain_geom[1, 1] = w.grain_geom[0, 1] + 14 * h + 1.05 * rc
+    w.grain_geom[1, 5] = -1.0
+    p = w.params
+    soft = (p["E"], p["k_bulk"], p["rho"], p["Gc"])
+    stiff = (2 * p["E"], 3 * p["k_bulk"], 2 * p["rho"], 2 * p["Gc"])
+    w.materials = (np.array([soft, stiff], dtype=np.float64), np.array([0, 1], dtype=np.int32))
+    w.name = "two_material_disks"
+    return w
+
+
 def _rsa_place(rng, radii, box_lo, box_hi, margin, max_tries=200000):
     """Random sequential addition of non-overlapping disks of radius radii+margin."""
     n = len(radii)
