@@ -234,6 +234,51 @@ def two_material_disks(**over) -> Workload:
     return w
 
 
+def notched_square_shape(notch_w: float, notch_y: float) -> list[np.ndarray]:
+    """Square of side 2 (units of R) with a straight notch of width notch_w from
+    the middle of its left edge to its centre, centred at height notch_y."""
+    yb, yt = notch_y - 0.5 * notch_w, notch_y + 0.5 * notch_w
+    return [np.array([(-1.0, -1.0), (1.0, -1.0), (1.0, 1.0), (-1.0, 1.0), (-1.0, yt), (0.0, yt), (0.0, yb),
+                      (-1.0, yb)], dtype=np.float64)]
+
+
+def rectangle_shape(aspect: float = 0.5) -> list[np.ndarray]:
+    """Rectangle 2 x 2 aspect (units of R)."""
+    return [np.array([(-1.0, -aspect), (1.0, -aspect), (1.0, aspect), (-1.0, aspect)], dtype=np.float64)]
+
+
+def three_particles(gc_a: float = 135.0, h_ratio: int = 10, v: float = 20.0, n_steps: int = 2500,
+                    **over) -> Workload:
+    """The symmetric-impact test of Sec. 5.3: particle A, a 1 mm square with a
+    0.5 mm notch from its left edge to its centre, is hit from below and from
+    above by particles B and C, 1 mm x 0.5 mm rectangles at +v and -v (20 m/s).
+    Damping and friction are off; dt = 20 ns (Sec. 5.1).  The paper gives no
+    material for this test: all three take E and rho of M2 of the material
+    table (E = 1.23 GPa, rho = 1200 kg/m^3), A with fracture energy gc_a (135
+    or 13.5 J/m^2 in the paper), B and C with 135 J/m^2.  The contact bulk
+    modulus is 5 MPa, not M2's 2 GPa: with K_n = 18 k / (pi eps^5) at h = 50 um
+    and dt = 20 ns, 2 GPa gives a contact pair omega dt of 16 (explicit Verlet
+    needs < 2), 5 MPa gives 0.8 (see contact_cfl).  Lattice h = R / h_ratio
+    (R = 0.5 mm); the notch, 2 % of h wide, lies between two lattice rows, so
+    it removes the bonds across it and no node; B and C start 1.02 R_c from A."""
+    R = 0.5e-3
+    h = R / h_ratio
+    params = default_params(E=1.23e9, k_bulk=5.0e6, rho=1200.0, Gc=135.0, damping_ratio=0.0, friction=0.0,
+                            gx=0.0, gy=0.0, dt=2.0e-8, wall_lo=(-5e-3, -5e-3), wall_hi=(5e-3, 5e-3))
+    params.update(over)
+    rc = params["rc_ratio"] * h
+    na = h_ratio - 1                  # outermost lattice row of A (nodes strictly inside)
+    nb = h_ratio // 2 - 1             # outermost lattice row of B and C (half-height R / 2)
+    off = (na + nb) * h + 1.02 * rc   # centre distance: node rows 1.02 R_c apart
+    shapes = [notched_square_shape(0.02 / h_ratio, 0.5 / h_ratio), rectangle_shape(0.5)]
+    ggeom = [(0.0, 0.0, R, 0.0, 0.0, 0.0, h), (0.0, -off, R, 0.0, 0.0, v, h), (0.0, off, R, 0.0, 0.0, -v, h)]
+    w = _mk(shapes, [0, 1, 1], ggeom, params, n_steps, f"three_particles_gc{gc_a:g}")
+    p = w.params
+    w.materials = (np.array([[p["E"], p["k_bulk"], p["rho"], gc_a], [p["E"], p["k_bulk"], p["rho"], p["Gc"]]]),
+                   np.array([0, 1, 1], dtype=np.int32))
+    return w
+
+
 def _rsa_place(rng, radii, box_lo, box_hi, margin, max_tries=200000):
     """Random sequential addition of non-overlapping disks of radius radii+margin."""
     n = len(radii)

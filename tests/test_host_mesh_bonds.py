@@ -69,3 +69,22 @@ def test_non_convex_grains_lose_bonds():
                         missing += 1
     assert missing > 0
     assert full.n_bonds > 0
+
+
+def test_notched_square_has_no_bond_across_the_notch():
+    """No bond of the notched square crosses the notch (the segment of every
+    bond of A stays on one side of the slit where both ends lie left of the tip)."""
+    w = I.three_particles()
+    S = B.Simulation(w)
+    X, row, col, grain = S.get("X"), S.get("ROW_PTR"), S.get("COL"), S.get("GRAIN")
+    h = 0.5e-3 / 10
+    y_notch = 0.5 * h
+    crossing = 0
+    for x in np.nonzero(grain == 0)[0]:
+        for y in col[row[x]:row[x + 1]]:
+            a, b = X[x], X[y]
+            if (a[1] - y_notch) * (b[1] - y_notch) < 0:
+                t = (y_notch - a[1]) / (b[1] - a[1])
+                crossing += a[0] + t * (b[0] - a[0]) < 0.0          # crosses the slit, left of the tip
+    assert crossing == 0
+    assert S.n_bonds > 0
