@@ -45,7 +45,10 @@ WORKLOADS = {
                                    "dt=2e-8 s, own wall box each"),
     "surrogate2000": ("surrogate_settling", 5, "settling of 2000 mixed-shape grains, R~U[1,1.5] mm, h=R/23, "
                                                "dt=2.5e-8 s, gravity 5000 m/s^2 (plain FP32 path)"),
+    "agitated500": ("compaction", 3, "the 500-grain compaction aggregate with every grain thrown at 5 m/s in a seeded "
+                                     "direction (collisions and fracture; contact lists rebuilt every few steps)"),
 }
+WORKLOAD_ARGS = {"agitated500": {"agitation": 5.0}}
 
 
 def workload_for(rank: int, args):
@@ -55,7 +58,7 @@ def workload_for(rank: int, args):
     gen, seed, _ = WORKLOADS[name]
     if gen == "settling":
         return I.settling(n_grains=50, seed=seed + rank)
-    return getattr(I, gen)(seed=seed + rank)
+    return getattr(I, gen)(seed=seed + rank, **WORKLOAD_ARGS.get(name, {}))
 
 
 def max_over_ranks(dist, values, device):
@@ -288,10 +291,10 @@ BYTES_PER_NODE_STEP_FP32 = 196
 # profiles/traffic_settling50.md).  They hold while the kernel sources hash to
 # TRAFFIC_DIGEST; otherwise, or for a variant not captured, traffic is null.
 TRAFFIC_SETTLING50 = {
-    "k_persistent<1, 4, 256>": 3738368,
-    "k_persistent<0, 4, 128>": 7075200,
+    "k_persistent<1, 4, 128>": 3739648,
+    "k_persistent<0, 4, 128>": 7076352,
 }
-TRAFFIC_DIGEST = "6d692a84cd657db9551718d45d35ede27579a75e"
+TRAFFIC_DIGEST = "a35259b52bdab566c61da50ffb6cb4b4cc702540"
 TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu", "pd_common.cu", "pd_internal.h")
 
 
