@@ -28,9 +28,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "node-steps/s and bond evals/s vs plain FP64 GPU path at stated error; % HBM peak"
 FLOPS_PER_BOND = 17      # algorithmic FP64 ops of one bond evaluation (sqrt, div counted once)
-# algorithmic bytes of the FP32-split force kernel: per node ph, pl, lattice (24 B), grain, row
-# pointer, broken word (12 B), FP64 p, v, a read and v, a written (80 B); per bond the column (4 B)
-BYTES_PER_NODE_FP32 = 116
+# algorithmic bytes of the FP32-split force phase: per node the float-float position pq (16 B),
+# grain, row pointer, broken-bond word and contact-list length (16 B), hash-grid cell for the wall
+# test (8 B), FP64 v and a read and written (64 B); per bond the column (4 B)
+BYTES_PER_NODE_FP32 = 104
 BYTES_PER_BOND_FP32 = 4
 B_STATUS_REBUILDS = 5    # status slot counting the contact candidate-list rebuilds
 
@@ -277,9 +278,10 @@ def precision_report(B, dev, stream, torch):
 # (500-grain compaction, 64-aggregate ensemble, 2000-grain surrogate settling)
 
 # algorithmic bytes of one whole FP32-split time step per node (displacement
-# update 80 B: X, u, v, a read, u and p written; force kernel 116 B) + 4 B per
-# bond; the candidate-list rebuild runs only in some steps and is not counted
-BYTES_PER_NODE_STEP_FP32 = 196
+# update 112 B: X + shift, u, v, a and the rebuild reference read, u and pq
+# written; force phase 104 B) + 4 B per bond; the candidate-list rebuild runs
+# only in some steps and is not counted
+BYTES_PER_NODE_STEP_FP32 = 216
 
 
 # DRAM bytes (read + write) per launch of the step kernels on the settling50
