@@ -434,7 +434,8 @@ int pd_observables(pd_ctx *ctx, double *out_host);
  *   row_ptr   device int32[N+1], col device int32[n_bonds] (bond lists as
  *             PD_FIELD_ROW_PTR / PD_FIELD_COL), broken device uint8[n_bonds]
  *   g_cw, g_eps  device double[G] per-grain c_w and horizon
- *   rho, micromodulus as in pd_params
+ *   rho, micromodulus as in pd_params (one density for every node: with
+ *             per-grain materials, pd_diagnostics weighs each node by its own)
  *   out       device double[PD_DIAG_COUNT] (same slots as pd_diagnostics)
  *   cuda_stream  the stream the work is enqueued on (returns without waiting)
  * The first call on a device, with that device current, looks up the device
