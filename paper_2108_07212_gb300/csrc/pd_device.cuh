@@ -754,6 +754,7 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
     // broken-bond bits of the node's first 32 bonds: only the node's own threads
     // set them, each for its own bonds, so one load at the start serves the loop
     const uint32_t w0 = active ? __ldcg(bw) : 0u;
+    bool pending = false;      // a bond of this lane lies in the guard band
     // bonds in batches of kBondBatch per lane: the column indices, broken words and
     // neighbour positions of a batch are all in flight before any is used (the
     // per-lane summation order is unchanged: bonds lane, lane + LANES, ...)
@@ -792,18 +793,50 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
             const float L = sqrtf(L2h);
             const float s = num / (xi * (L + xi));
             const float as = fabsf(s);
-            bool brk;
+            // near the threshold the FP64 path decides, after the loop (its FP64
+            // registers stay out of the hot loop)
             if (as > s0_lo && as < s0_hi) {
-                // near the threshold: the FP64 path's decision, operation by operation
-                const double2 pi = position64<PERSIST>(d, ii), pj = position64<PERSIST>(d, j);
-                const double ddx = __dsub_rn(pj.x, pi.x), ddy = __dsub_rn(pj.y, pi.y);
-                const double L64 = __dsqrt_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)));
-                const double xi64 = __ldg(&d.xi[b]);
-                brk = fabs(__ddiv_rn(__dsub_rn(L64, xi64), xi64)) > __ldg(&d.g_s0[gi]);
-            } else {
-                brk = as > s0;
+                pending = true;
+                continue;
             }
+            const bool brk = as > s0;
             if (brk) {
+                atomicOr(&bw[kk >> 5], 1u << (kk & 31));
+                continue;
+            }
+            const float cws = (k.micro ? cw * (1.0f - xi / eps) : cw) * s;
+            const float qf = cws * VV / L;
+            Fbx += qf * (dxh + dxl);
+            Fby += qf * (dyh + dyl);
+        }
+    }
+    if (pending) {
+        // the lane's bonds in the guard band, in its order: FP64 break decision,
+        // else the FP32 force
+        for (int b = r0 + lane; b < r1; b += LANES) {
+            const int kk = b - r0;
+            if ((__ldcg(&bw[kk >> 5]) >> (kk & 31)) & 1u) continue;
+            const uint32_t c = __ldg(&d.colx[b]);
+            const int j = (int)(c & kColMask);
+            const float4 qj = ldm<PERSIST>(&d.pq[j]);
+            const float dxh = __fsub_rn(qj.x, phi.x), dxl = qj.z - pli.x;
+            const float dyh = __fsub_rn(qj.y, phi.y), dyl = qj.w - pli.y;
+            float L2h, L2l;
+            len2_ff(dxh, dxl, dyh, dyl, L2h, L2l);
+            const float nn = (float)(c >> kColBits);
+            float q, eq;
+            two_prod(nn, gq.y, q, eq);
+            const float num = ff_diff(L2h, L2l, q, eq + nn * gq.z);
+            const float xi = gq.x * sqrtf(nn);
+            const float L = sqrtf(L2h);
+            const float s = num / (xi * (L + xi));
+            const float as = fabsf(s);
+            if (!(as > s0_lo && as < s0_hi)) continue;
+            const double2 pi = position64<PERSIST>(d, ii), pj = position64<PERSIST>(d, j);
+            const double ddx = __dsub_rn(pj.x, pi.x), ddy = __dsub_rn(pj.y, pi.y);
+            const double L64 = __dsqrt_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)));
+            const double xi64 = __ldg(&d.xi[b]);
+            if (fabs(__ddiv_rn(__dsub_rn(L64, xi64), xi64)) > __ldg(&d.g_s0[gi])) {
                 atomicOr(&bw[kk >> 5], 1u << (kk & 31));
                 continue;
             }
