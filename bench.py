@@ -293,10 +293,10 @@ BYTES_PER_NODE_STEP_FP32 = 216
 # profiles/traffic_settling50.md).  They hold while the kernel sources hash to
 # TRAFFIC_DIGEST; otherwise, or for a variant not captured, traffic is null.
 TRAFFIC_SETTLING50 = {
-    "k_persistent<1, 4, 128>": 3739648,
-    "k_persistent<0, 4, 128>": 7076352,
+    "k_persistent<1, 4, 256>": 3736320,
+    "k_persistent<0, 4, 128>": 7077632,
 }
-TRAFFIC_DIGEST = "a35259b52bdab566c61da50ffb6cb4b4cc702540"
+TRAFFIC_DIGEST = "e3a35491fa0761b31e4472907455baf2a3da13b5"
 TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu", "pd_common.cu", "pd_internal.h")
 
 
