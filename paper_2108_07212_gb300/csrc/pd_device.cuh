@@ -325,7 +325,7 @@ __device__ __forceinline__ bool predict_node(const DevPtrs &d, const KParams &k,
     }
     const double2 X = __ldg(&d.X[i]);
     d.p[i] = make_double2(__dadd_rn(X.x, u.x), __dadd_rn(X.y, u.y));
-    // |u - u_ref| in float: its rounding (1e-7 |u|) is far below the margin
+    // |u - u at the last rebuild| in float: its rounding (1e-7 |u|) is far below the margin
     // (1/2 - kSkinTrigger) skin of the trigger
     const float4 r = ldm<PERSIST>(&d.sref[i]);
     const float ex = (float)u.x - r.x, ey = (float)u.y - r.y;

@@ -72,7 +72,7 @@ struct DevPtrs {
     float4 *sref;       // at the last rebuild: FP32 split pq, FP64 path (float u, 0, 0)
     int *rebuild;       // nonzero: rebuild the lists before the next force phase (cleared by the force phase)
     unsigned *pred_done;  // blocks of the displacement update that have finished (last-block election)
-    uint4 *srec;        // position of sorted[t] in bucket order: FP32 split (ph, pl), FP64 p (16 bytes)
+    uint4 *srec;        // position of sorted[t] in bucket order: FP32 split pq, FP64 p (16 bytes)
     void *fsum;         // split force phase: per-node lane sums, six components of N floats (FP32) or doubles
     // globals
     long long *step;
