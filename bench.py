@@ -296,7 +296,7 @@ TRAFFIC_SETTLING50 = {
     "k_persistent<1, 4, 256>": 3736320,
     "k_persistent<0, 4, 128>": 7077632,
 }
-TRAFFIC_DIGEST = "e3a35491fa0761b31e4472907455baf2a3da13b5"
+TRAFFIC_DIGEST = "ae05c53f4334bf02427c80cab930e0fe7abaf4a2"
 TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu", "pd_common.cu", "pd_internal.h")
 
 
