@@ -694,7 +694,7 @@ def run_ours(args):
         "force_kernel_us": 1e3 * f_ms,
         "list_rebuilds": {"timed_steps": args.steps, "fp32" if prec != B.PD_FP64 else "fp64": rebuilds,
                           **({"fp64": rebuilds64} if sim64 is not None else {}),
-                          "note": "contact candidate lists (radius R_c + 0.05 R_c) rebuilt in a conditional graph "
+                          "note": "contact candidate lists (radius R_c + 0.1 R_c) rebuilt in a conditional graph "
                                   "node only when a node has moved 0.45 skin"},
         "precision_report": precision_report(B, dev, stream, torch) if prec != B.PD_FP64 else None,
         "cpu_baseline": cpu_baseline(w) if not args.no_cpu else None,

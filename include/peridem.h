@@ -192,7 +192,7 @@ int pd_bind_arena(pd_ctx *ctx, void *device_arena, size_t bytes);
  * Advance n_steps >= 0 velocity-Verlet steps (Algorithm 1) asynchronously on
  * the context stream; the step sequence runs as captured CUDA graphs.  The
  * contact neighbourhoods S^nbr (Algorithm 1, nodes within R_c) are taken from
- * per-node candidate lists of radius R_c + skin (skin = 0.05 R_c), rebuilt by
+ * per-node candidate lists of radius R_c + skin (skin = 0.1 R_c), rebuilt by
  * a hash-grid counting sort in a conditional graph node only in steps where
  * some node has moved more than 0.45 skin since the last rebuild; every pair
  * is still tested against R_c exactly, so the forces are those of a full

@@ -254,8 +254,8 @@ cudaError_t launch_rebuild(const DevPtrs &d, const KParams &k, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_force(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s) {
-    return k.fp32 ? launch_force32(d, k, vin, update_v, s) : launch_force64(d, k, vin, update_v, s);
+cudaError_t launch_force(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s, int phase) {
+    return k.fp32 ? launch_force32(d, k, vin, update_v, s, phase) : launch_force64(d, k, vin, update_v, s, phase);
 }
 
 cudaError_t launch_persistent(const DevPtrs &d, const KParams &k, int vin, int nsteps, int block, cudaStream_t s) {

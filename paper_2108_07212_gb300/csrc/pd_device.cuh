@@ -735,21 +735,14 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
 
     float Fbx = 0.f, Fby = 0.f;
     const float VV = Vi * Vi;
-    // learned modal surrogate: between judge steps an active grain's bond force
-    // is R(theta + phi) Phi f E h (expanded on the tensor cores) instead of the bond loop
+    // learned modal surrogate: between judge steps an active grain skips the
+    // bond loop; the epilogue adds its surrogate bond force instead
     bool sur = false, judge = false;
     if constexpr (!PERSIST) {
         if (k.sur && active) {
             sur = d.sur_active[gi] != 0;
             judge = (*d.step) % k.judge_every == 0;
         }
-    }
-    if (sur && !judge && lane == 0) {
-        const float2 f = d.sur_f[ii];                     // Phi f, lattice frame, units of E h
-        const float2 rot = d.sur_rot[gi];
-        const float Eh = k.E * gq.x;
-        Fbx = (rot.x * f.x - rot.y * f.y) * Eh;
-        Fby = (rot.y * f.x + rot.x * f.y) * Eh;
     }
     // broken-bond bits of the node's first 32 bonds: only the node's own threads
     // set them, each for its own bonds, so one load at the start serves the loop
@@ -920,9 +913,22 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
 
 template <bool PERSIST>
 __device__ __forceinline__ void node_epilogue32(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
-                                                const Sums32 &f) {
+                                                const Sums32 &fin) {
     const double2 vi = ldm<PERSIST>(&d.v[vin][i]);
     const int gi = __ldg(&d.grain[i]);
+    Sums32 f = fin;
+    if constexpr (!PERSIST) {
+        // learned modal surrogate: between judge steps an active grain's bond force
+        // is R(theta + phi) Phi f E h (expanded on the tensor cores), in place of
+        // the bond loop the sums skipped
+        if (k.sur && d.sur_active[gi] && (*d.step) % k.judge_every != 0) {
+            const float2 sf = d.sur_f[i];                     // Phi f, lattice frame, units of E h
+            const float2 rot = d.sur_rot[gi];
+            const float Eh = k.E * __ldg(&d.gq[gi]).x;
+            f.bx += (rot.x * sf.x - rot.y * sf.y) * Eh;
+            f.by += (rot.y * sf.x + rot.x * sf.y) * Eh;
+        }
+    }
     const int ag = __ldg(&d.g_agg[gi]);
     double Fwx = 0.0, Fwy = 0.0;
     const bool walls = !far_from_walls<PERSIST>(d, i, ag);

@@ -208,6 +208,8 @@ struct pd_ctx {
     int64_t steps_done = 0;
     cudaStream_t capture_stream = nullptr;
     cudaStream_t body_stream = nullptr;    // captures the bodies of the rebuild conditionals
+    cudaStream_t sur_stream = nullptr;     // captures the surrogate chain beside the lane sums
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t chunk[2] = {nullptr, nullptr};
     cudaGraphExec_t single[2] = {nullptr, nullptr};
     cudaGraphExec_t timed[2] = {nullptr, nullptr};
@@ -485,6 +487,17 @@ cudaError_t record_step(pd_ctx *c, int vin, cudaStream_t s, bool timed = false) 
         return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     if ((e = pd::launch_predict(c->d, c->kp, vin, 1, s, cond, use_cond)) != cudaSuccess) return e;
+    // surrogate with the split force phase: its chain (frame, projection,
+    // networks, expansion) runs on a second stream beside the rebuild and the
+    // lane sums, which skip the bond loop of surrogate grains; the epilogue,
+    // which adds the surrogate forces, waits for it
+    const bool fork = c->kp.sur && c->kp.split;
+    if (fork) {
+        if ((e = cudaEventRecord(c->ev_fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(c->sur_stream, c->ev_fork, 0)) != cudaSuccess) return e;
+        if ((e = record_surrogate(c, c->sur_stream)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(c->ev_join, c->sur_stream)) != cudaSuccess) return e;
+    }
     if (timed && (e = cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     if (c->mode & 4) {
         // path modes 4-7: the rebuild kernels run every step and return at once
@@ -514,9 +527,15 @@ cudaError_t record_step(pd_ctx *c, int vin, cudaStream_t s, bool timed = false) 
         if (eb != cudaSuccess) return eb;
         if (ee != cudaSuccess) return ee;
     }
-    if (c->kp.sur && (e = record_surrogate(c, s)) != cudaSuccess) return e;
+    if (c->kp.sur && !fork && (e = record_surrogate(c, s)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal)) != cudaSuccess) return e;
-    if ((e = pd::launch_force(c->d, c->kp, vin, 1, s)) != cudaSuccess) return e;
+    if (fork) {
+        if ((e = pd::launch_force(c->d, c->kp, vin, 1, s, 1)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s, c->ev_join, 0)) != cudaSuccess) return e;
+        if ((e = pd::launch_force(c->d, c->kp, vin, 1, s, 2)) != cudaSuccess) return e;
+    } else if ((e = pd::launch_force(c->d, c->kp, vin, 1, s)) != cudaSuccess) {
+        return e;
+    }
     if (c->kp.sur && (e = pd::launch_sur_judge(c->d, c->kp, s)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     return cudaSuccess;
@@ -631,6 +650,9 @@ int pd_destroy(pd_ctx *c) {
             if (e) cudaEventDestroy(e);
         if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
         if (c->body_stream) cudaStreamDestroy(c->body_stream);
+        if (c->sur_stream) cudaStreamDestroy(c->sur_stream);
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        if (c->ev_join) cudaEventDestroy(c->ev_join);
     }
     delete c;
     return PD_OK;
@@ -1074,6 +1096,9 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     // capture the step graphs on a private stream (the caller's may be the legacy stream)
     PD_CUDA(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
     PD_CUDA(cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking));
+    PD_CUDA(cudaStreamCreateWithFlags(&c->sur_stream, cudaStreamNonBlocking));
+    PD_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    PD_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     for (auto &e : c->ev) PD_CUDA(cudaEventCreate(&e));
     return capture_all(c);
 }

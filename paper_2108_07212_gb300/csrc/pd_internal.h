@@ -13,7 +13,7 @@ namespace pd {
 // has moved more than kSkinTrigger * skin since the last one, so every pair
 // closer than R_c is always in the list (the force phase tests R_c exactly).
 constexpr int kMaxList = 24;
-constexpr double kSkinRatio = 0.05;     // skin = kSkinRatio * R_c
+constexpr double kSkinRatio = 0.10;     // skin = kSkinRatio * R_c
 constexpr double kSkinTrigger = 0.45;   // < 1/2: margin for the float displacement test
 // FP32-split bond columns: node index in the low kColBits bits, the bond's
 // lattice offset di^2 + dj^2 (< 16 for horizons up to 4 h) in the top bits.
@@ -200,9 +200,11 @@ cudaError_t launch_predict(const DevPtrs &d, const KParams &k, int vin, int adva
 // Rebuild of the contact candidate lists (kernels return at once when the
 // rebuild flag is clear).
 cudaError_t launch_rebuild(const DevPtrs &d, const KParams &k, cudaStream_t s);
-cudaError_t launch_force(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s);
-cudaError_t launch_force64(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s);
-cudaError_t launch_force32(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s);
+// Force phase; with the split variant, phase 1 launches only the lane sums
+// and phase 2 only the epilogue (0: both; the fused variant takes only 0).
+cudaError_t launch_force(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s, int phase = 0);
+cudaError_t launch_force64(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s, int phase = 0);
+cudaError_t launch_force32(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s, int phase = 0);
 cudaError_t launch_positions(const DevPtrs &d, const KParams &k, cudaStream_t s);
 cudaError_t launch_diagnostics(const DevPtrs &d, const KParams &k, int vcur, cudaStream_t s);
 // Particle damage of every grain (gdam[G]) and per-aggregate sums of the wall

@@ -99,18 +99,22 @@ __global__ void __launch_bounds__(256, 4) k_epilogue(DevPtrs d, KParams k, int v
     if (i < k.N) epilogue_node<FP32, false>(d, k, i, vin, update_v);
 }
 
+// phase (split force phase only): 0 both passes, 1 the lane sums, 2 the epilogue.
 template <bool FP32>
-cudaError_t launch_force_impl(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s) {
+cudaError_t launch_force_impl(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s, int phase) {
     const long long threads = (long long)k.lanes * k.N;
     const unsigned grid = (unsigned)((threads + kBlock - 1) / kBlock);
     if (k.split) {
-        if (k.lanes == 8) k_sums<FP32, 8><<<grid, kBlock, 0, s>>>(d, k, vin);
-        else if (k.lanes == 4) k_sums<FP32, 4><<<grid, kBlock, 0, s>>>(d, k, vin);
-        else if (k.lanes == 2) k_sums<FP32, 2><<<grid, kBlock, 0, s>>>(d, k, vin);
-        else k_sums<FP32, 1><<<grid, kBlock, 0, s>>>(d, k, vin);
-        k_epilogue<FP32><<<(unsigned)((k.N + 255) / 256), 256, 0, s>>>(d, k, vin, update_v);
+        if (phase != 2) {
+            if (k.lanes == 8) k_sums<FP32, 8><<<grid, kBlock, 0, s>>>(d, k, vin);
+            else if (k.lanes == 4) k_sums<FP32, 4><<<grid, kBlock, 0, s>>>(d, k, vin);
+            else if (k.lanes == 2) k_sums<FP32, 2><<<grid, kBlock, 0, s>>>(d, k, vin);
+            else k_sums<FP32, 1><<<grid, kBlock, 0, s>>>(d, k, vin);
+        }
+        if (phase != 1) k_epilogue<FP32><<<(unsigned)((k.N + 255) / 256), 256, 0, s>>>(d, k, vin, update_v);
         return cudaGetLastError();
     }
+    if (phase != 0) return cudaErrorInvalidValue;
     if (k.lanes == 8) k_force<FP32, 8><<<grid, kBlock, 0, s>>>(d, k, vin, update_v);
     else if (k.lanes == 4) k_force<FP32, 4><<<grid, kBlock, 0, s>>>(d, k, vin, update_v);
     else if (k.lanes == 2) k_force<FP32, 2><<<grid, kBlock, 0, s>>>(d, k, vin, update_v);

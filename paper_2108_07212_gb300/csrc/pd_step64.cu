@@ -6,8 +6,8 @@
 
 namespace pd {
 
-cudaError_t launch_force64(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s) {
-    return launch_force_impl<false>(d, k, vin, update_v, s);
+cudaError_t launch_force64(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s, int phase) {
+    return launch_force_impl<false>(d, k, vin, update_v, s, phase);
 }
 
 cudaError_t launch_persistent64(const DevPtrs &d, const KParams &k, int vin, int nsteps, int block, cudaStream_t s) {
