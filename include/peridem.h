@@ -201,18 +201,31 @@ int pd_bind_arena(pd_ctx *ctx, void *device_arena, size_t bytes);
  */
 int pd_step(pd_ctx *ctx, int n_steps);
 
+/* Where the caller's buffer of pd_get_state / pd_set_state lives. */
+#define PD_MEM_HOST 0        /* host memory: the call waits for the stream        */
+#define PD_MEM_DEVICE 1      /* device memory: a copy enqueued on the stream      */
+#define PD_MEM_HOST_ASYNC 2  /* page-locked host memory: a copy enqueued on the   */
+                             /* stream; the call does not wait, and the caller   */
+                             /* keeps the buffer valid (and, for a get, reads it) */
+                             /* only after synchronising the stream              */
+
 /*
  * Copy a state field (PD_FIELD_*) into dst (bytes must equal the field size).
- * dst_on_device = 1: device-to-device copy enqueued on the stream; 0: the call
- * waits for the stream and copies to host memory.  Mesh fields (X, GRAIN,
- * VOLUME, ROW_PTR, COL, LATTICE) can be read from host copies before
+ * dst_on_device: PD_MEM_HOST (the call waits for the stream and copies to host
+ * memory), PD_MEM_DEVICE (device-to-device copy enqueued on the stream) or
+ * PD_MEM_HOST_ASYNC (copy to page-locked host memory enqueued on the stream;
+ * BROKEN and DAMAGE, converted on the host, always wait).  Mesh fields (X,
+ * GRAIN, VOLUME, ROW_PTR, COL, LATTICE) can be read from host copies before
  * pd_bind_arena.  Errors: PD_EINVAL (unknown field, size mismatch), PD_ESTATE,
  * PD_ECUDA.
  */
 int pd_get_state(pd_ctx *ctx, int field, void *dst, size_t bytes, int dst_on_device);
 
 /* Overwrite a settable state field (DISP, VEL, ACC, BROKEN, STEP) from host
- * (src_on_device = 0) or device memory, stream-ordered.  Errors as above. */
+ * memory (src_on_device = PD_MEM_HOST: the call waits), device memory
+ * (PD_MEM_DEVICE) or page-locked host memory without waiting
+ * (PD_MEM_HOST_ASYNC; BROKEN and STEP, read on the host, always wait),
+ * stream-ordered.  Errors as above. */
 int pd_set_state(pd_ctx *ctx, int field, const void *src, size_t bytes, int src_on_device);
 
 /* Recompute the forces and acceleration of the current state without moving

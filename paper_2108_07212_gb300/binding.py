@@ -19,6 +19,7 @@ c_double, c_int32, c_int64, c_size_t, c_void_p = (ctypes.c_double, ctypes.c_int3
 
 PD_OK, PD_EINVAL, PD_ESTATE, PD_ECUDA, PD_ENUMERIC, PD_EOVERFLOW, PD_ENOMEM, PD_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 PD_FP64, PD_FP32_SPLIT = 0, 1
+PD_MEM_HOST, PD_MEM_DEVICE, PD_MEM_HOST_ASYNC = 0, 1, 2     # buffer kinds of pd_get_state / pd_set_state
 FIELDS = dict(X=0, DISP=1, VEL=2, ACC=3, POS=4, FORCE=5, FORCE_PARTS=6, BROKEN=7, DAMAGE=8, GRAIN=9,
               VOLUME=10, ROW_PTR=11, COL=12, LATTICE=13, STEP=14, GRAIN_TEMPLATE=15)
 STATUS_COUNT = 8
@@ -262,9 +263,16 @@ class Simulation:
 
     def set(self, field: str, value) -> None:
         if hasattr(value, "data_ptr"):
-            _check(load().pd_set_state(self._ctx, FIELDS[field], c_void_p(value.data_ptr()),
-                                       value.numel() * value.element_size(), 1))
-            return
+            if getattr(value, "is_cuda", True):
+                _check(load().pd_set_state(self._ctx, FIELDS[field], c_void_p(value.data_ptr()),
+                                           value.numel() * value.element_size(), PD_MEM_DEVICE))
+                return
+            if value.is_pinned():
+                # page-locked host tensor: enqueued on the stream without waiting
+                _check(load().pd_set_state(self._ctx, FIELDS[field], c_void_p(value.data_ptr()),
+                                           value.numel() * value.element_size(), PD_MEM_HOST_ASYNC))
+                return
+            value = value.numpy()
         ref = self._alloc(field)
         arr = np.ascontiguousarray(np.asarray(value, dtype=ref.dtype).reshape(ref.shape))
         _check(load().pd_set_state(self._ctx, FIELDS[field], _ptr(arr), arr.nbytes, 0))

@@ -1159,14 +1159,15 @@ int pd_get_state(pd_ctx *c, int field, void *dst, size_t bytes, int dst_on_devic
         case PD_FIELD_GRAIN_TEMPLATE: if (c->state >= 2) host = c->g_tmpl.data(); break;
         default: break;
     }
+    if (dst_on_device < PD_MEM_HOST || dst_on_device > PD_MEM_HOST_ASYNC) return fail(PD_EINVAL, "unknown memory kind");
     if (host) {
-        if (dst_on_device) PD_CUDA(cudaMemcpyAsync(dst, host, fb, cudaMemcpyHostToDevice, c->stream));
+        if (dst_on_device == PD_MEM_DEVICE) PD_CUDA(cudaMemcpyAsync(dst, host, fb, cudaMemcpyHostToDevice, c->stream));
         else std::memcpy(dst, host, fb);
-        if (dst_on_device) PD_CUDA(cudaStreamSynchronize(c->stream));
+        if (dst_on_device == PD_MEM_DEVICE) PD_CUDA(cudaStreamSynchronize(c->stream));
         return PD_OK;
     }
     if (c->state < 3) return fail(PD_ESTATE, "field needs a bound arena");
-    cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaMemcpyKind kind = dst_on_device == PD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const pd::DevPtrs &d = c->d;
     cudaStream_t s = c->stream;
     switch (field) {
@@ -1188,7 +1189,7 @@ int pd_get_state(pd_ctx *c, int field, void *dst, size_t bytes, int dst_on_devic
         case PD_FIELD_STEP: PD_CUDA(cudaMemcpyAsync(dst, d.step, 8, kind, s)); break;
         case PD_FIELD_BROKEN:
         case PD_FIELD_DAMAGE: {
-            if (dst_on_device) return fail(PD_EINVAL, "BROKEN/DAMAGE are host-only fields");
+            if (dst_on_device == PD_MEM_DEVICE) return fail(PD_EINVAL, "BROKEN/DAMAGE are host-only fields");
             std::vector<uint32_t> bits((size_t)c->N * c->wpn);
             PD_CUDA(cudaMemcpyAsync(bits.data(), d.bits, 4 * bits.size(), cudaMemcpyDeviceToHost, s));
             PD_CUDA(cudaStreamSynchronize(s));
@@ -1206,7 +1207,7 @@ int pd_get_state(pd_ctx *c, int field, void *dst, size_t bytes, int dst_on_devic
         }
         default: return fail(PD_EINVAL, "unknown field");
     }
-    if (!dst_on_device) PD_CUDA(cudaStreamSynchronize(s));
+    if (dst_on_device == PD_MEM_HOST) PD_CUDA(cudaStreamSynchronize(s));
     return PD_OK;
 }
 
@@ -1215,7 +1216,8 @@ int pd_set_state(pd_ctx *c, int field, const void *src, size_t bytes, int src_on
     size_t fb = field_bytes(c, field);
     if (bytes != fb) return fail(PD_EINVAL, "size mismatch for field");
     if (!src && fb) return fail(PD_EINVAL, "null source");
-    cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (src_on_device < PD_MEM_HOST || src_on_device > PD_MEM_HOST_ASYNC) return fail(PD_EINVAL, "unknown memory kind");
+    cudaMemcpyKind kind = src_on_device == PD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const pd::DevPtrs &d = c->d;
     cudaStream_t s = c->stream;
     switch (field) {
@@ -1224,14 +1226,14 @@ int pd_set_state(pd_ctx *c, int field, const void *src, size_t bytes, int src_on
         case PD_FIELD_ACC: PD_CUDA(cudaMemcpyAsync(d.a, src, fb, kind, s)); break;
         case PD_FIELD_STEP: {
             int64_t st = 0;
-            if (src_on_device) PD_CUDA(cudaMemcpy(&st, src, 8, cudaMemcpyDeviceToHost));
+            if (src_on_device == PD_MEM_DEVICE) PD_CUDA(cudaMemcpy(&st, src, 8, cudaMemcpyDeviceToHost));
             else std::memcpy(&st, src, 8);
             PD_CUDA(cudaMemcpyAsync(d.step, src, 8, kind, s));
             c->steps_done = st;
             break;
         }
         case PD_FIELD_BROKEN: {
-            if (src_on_device) return fail(PD_EINVAL, "BROKEN is a host-only field");
+            if (src_on_device == PD_MEM_DEVICE) return fail(PD_EINVAL, "BROKEN is a host-only field");
             std::vector<uint32_t> bits((size_t)c->N * c->wpn, 0u);
             for (int64_t x = 0; x < c->N; ++x)
                 for (int b = c->row_ptr[x]; b < c->row_ptr[x + 1]; ++b) {
@@ -1244,7 +1246,7 @@ int pd_set_state(pd_ctx *c, int field, const void *src, size_t bytes, int src_on
         }
         default: return fail(PD_EINVAL, "field is not settable");
     }
-    if (!src_on_device) PD_CUDA(cudaStreamSynchronize(s));
+    if (src_on_device == PD_MEM_HOST || field == PD_FIELD_STEP) PD_CUDA(cudaStreamSynchronize(s));
     return PD_OK;
 }
 

@@ -229,6 +229,32 @@ def test_checkpoint_resume_is_bitwise():
         assert np.array_equal(A.get(f), B2.get(f)), f
 
 
+def test_page_locked_async_copies_match_synchronous_ones():
+    """PD_MEM_HOST_ASYNC: copies enqueued on the stream from and to page-locked
+    host memory give the same state as the synchronous copies."""
+    import torch
+
+    w = _contact_disks()
+    A = _gpu(w)
+    A.step(60)
+    ck = {f: A.get(f) for f in ("DISP", "VEL", "ACC")}
+    B2 = _gpu(w)
+    B2.set("STEP", A.get("STEP"))
+    B2.set("BROKEN", A.get("BROKEN"))
+    for f, v in ck.items():
+        t = torch.from_numpy(v.copy()).pin_memory()
+        B2.set(f, t)                                    # enqueued, no wait
+    A.step(40)
+    B2.step(40)
+    out = torch.empty((B2.N, 2), dtype=torch.float64).pin_memory()
+    lib = B.load()
+    B._check(lib.pd_get_state(B2._ctx, B.FIELDS["DISP"], B._ptr(out.numpy()), out.numel() * 8,
+                              B.PD_MEM_HOST_ASYNC))
+    B2._stream.synchronize()
+    assert np.array_equal(out.numpy(), A.get("DISP"))
+    assert np.array_equal(B2.get("VEL"), A.get("VEL"))
+
+
 def test_runs_are_deterministic():
     w = I.settling(n_grains=12, seed=9)
     a = _gpu(w, store=False)
