@@ -293,10 +293,10 @@ BYTES_PER_NODE_STEP_FP32 = 216
 # profiles/traffic_settling50.md).  They hold while the kernel sources hash to
 # TRAFFIC_DIGEST; otherwise, or for a variant not captured, traffic is null.
 TRAFFIC_SETTLING50 = {
-    "k_persistent<1, 4, 256>": 3736320,
-    "k_persistent<0, 4, 128>": 7077632,
+    "k_persistent<1, 4, 256>": 3765504,
+    "k_persistent<0, 4, 128>": 7105536,
 }
-TRAFFIC_DIGEST = "ae05c53f4334bf02427c80cab930e0fe7abaf4a2"
+TRAFFIC_DIGEST = "53dd520589907ff4eae988dc5a8c360a0f1ba83c"
 TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu", "pd_common.cu", "pd_internal.h")
 
 
