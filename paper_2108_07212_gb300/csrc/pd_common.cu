@@ -19,6 +19,7 @@ __global__ void __launch_bounds__(kBlock) k_predict(DevPtrs d, KParams k, int vi
                                                     cudaGraphConditionalHandle cond, int use_cond) {
     __shared__ bool last;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    prefetch_force_inputs(d, k, i, (long long)gridDim.x * blockDim.x);
     if (blockIdx.x == 0) {
         const long long st = *d.step + (advance ? 1 : 0);
         __syncthreads();                   // every thread of block 0 has read the counter

@@ -363,6 +363,59 @@ __device__ __forceinline__ void bin_node(const DevPtrs &d, const KParams &k, int
     atomicAdd(&d.count[b], 1);
 }
 
+// L2 prefetch of a byte range, one 128-byte line per index of a grid stride g
+// that counts on from range to range (a hint: it never faults, and every
+// address issued lies inside the range).
+__device__ __forceinline__ void prefetch_range(const void *p, size_t bytes, long long &g, long long nt) {
+    const long long lines = (long long)((bytes + 127) >> 7);
+    for (; g < lines; g += nt) asm volatile("prefetch.global.L2 [%0];" ::"l"((const char *)p + (g << 7)));
+    g -= lines;
+}
+
+// The read-only arrays of the force phase (CSR rows, grain ids, broken-bond
+// words, candidate-list lengths and first rows, bond columns, per-grain and
+// per-aggregate constants) and the lines of the step counter, rebuild flag,
+// status words and grid barrier, prefetched into L2 by all threads of a grid
+// before the displacement update: their DRAM latency then overlaps the update
+// instead of lengthening the dependent load chains that follow.  Off
+// (k.pf_bonds = 0) when the arrays do not fit comfortably in L2.
+__device__ __forceinline__ void prefetch_force_inputs(const DevPtrs &d, const KParams &k, long long t, long long nt) {
+    if (k.pf_bonds <= 0) return;
+    const size_t N = (size_t)k.N, nb = (size_t)k.pf_bonds, G = (size_t)k.G;
+    long long g = t;
+    prefetch_range(d.step, sizeof(long long), g, nt);
+    prefetch_range(d.rebuild, sizeof(int), g, nt);
+    prefetch_range(d.status, sizeof(int) * PD_STATUS_COUNT, g, nt);
+    prefetch_range(d.bar, 2 * sizeof(unsigned), g, nt);
+    prefetch_range(d.g_agg, 4 * G, g, nt);
+    prefetch_range(d.agg, sizeof(AggParams) * (size_t)k.n_agg, g, nt);
+    if (d.pq) {
+        prefetch_range(d.gq, 16 * G, g, nt);
+        prefetch_range(d.gc, 16 * G, g, nt);
+        prefetch_range(d.g_invm, 8 * G, g, nt);
+        if (k.mat) prefetch_range(d.g_kf, 4 * G, g, nt);
+    } else {
+        prefetch_range(d.g_cw, 8 * G, g, nt);
+        prefetch_range(d.g_s0, 8 * G, g, nt);
+        prefetch_range(d.g_eps, 8 * G, g, nt);
+        if (k.mat) {
+            prefetch_range(d.g_rho, 8 * G, g, nt);
+            prefetch_range(d.g_k, 8 * G, g, nt);
+        }
+    }
+    prefetch_range(d.row_ptr, 4 * (N + 1), g, nt);
+    prefetch_range(d.grain, 4 * N, g, nt);
+    prefetch_range(d.bits, 4 * N * (size_t)k.wpn, g, nt);
+    prefetch_range(d.nbr_cnt, 4 * N, g, nt);
+    prefetch_range(d.nbr, 4 * N * (size_t)kPrefetchListRows, g, nt);
+    if (d.pq) {
+        prefetch_range(d.colx, 4 * nb, g, nt);
+    } else {
+        prefetch_range(d.col, 4 * nb, g, nt);
+        prefetch_range(d.xi, 8 * nb, g, nt);
+    }
+}
+
 // Hash-grid cells of the four walls of every aggregate at time t (written once
 // per force evaluation by the threads of one block, one aggregate each): a node
 // two or more cells away from all of them is farther than R_c from every wall

@@ -937,6 +937,13 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     k.store = p.store_parts ? 1 : 0;
     k.lanes = p.lanes == 0 ? 4 : p.lanes;
     k.split = 1;          // default path: kernel graph, split force phase (pd_set_path mode 2)
+    {
+        // L2 prefetch of the force phase's read-only arrays when they fit well in L2
+        const size_t nb = c->col.size();
+        const size_t pf = (size_t)c->N * (16 + 4 * (size_t)c->wpn + 4 * pd::kPrefetchListRows) +
+                          nb * (k.fp32 ? 4 : 12);
+        k.pf_bonds = (nb > 0 && nb < ((size_t)1 << 31) && pf < pd::kPrefetchMaxBytes) ? (int)nb : 0;
+    }
     cudaStream_t s = c->stream;
     const pd::DevPtrs &d = c->d;
     size_t N = (size_t)c->N, nb = c->col.size(), G = (size_t)c->G;

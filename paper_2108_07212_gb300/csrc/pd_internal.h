@@ -15,6 +15,12 @@ namespace pd {
 constexpr int kMaxList = 24;
 constexpr double kSkinRatio = 0.10;     // skin = kSkinRatio * R_c
 constexpr double kSkinTrigger = 0.45;   // < 1/2: margin for the float displacement test
+// Rows q < kPrefetchListRows of the candidate lists are prefetched into L2 with
+// the other read-only arrays of the force phase (most lists are shorter).
+constexpr int kPrefetchListRows = 4;
+// The force phase's read-only arrays are prefetched into L2 at the start of a
+// step only when they take less than this (a fifth of the 129 MB L2).
+constexpr size_t kPrefetchMaxBytes = 24u << 20;
 // FP32-split bond columns: node index in the low kColBits bits, the bond's
 // lattice offset di^2 + dj^2 (< 16 for horizons up to 4 h) in the top bits.
 constexpr int kColBits = 28;
@@ -142,6 +148,7 @@ struct KParams {
     int lanes;          // threads per node in the force kernels (1, 4 or 8)
     int split;          // 1: lane sums through global memory and a separate epilogue pass
     int fp32;           // precision of the force phase
+    int pf_bonds;       // > 0: prefetch the force phase's read-only arrays (this many bonds) into L2
     // surrogate
     int sur;            // surrogate on
     int n_modes;        // modes of the basis (32)

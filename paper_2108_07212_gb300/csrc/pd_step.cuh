@@ -222,25 +222,29 @@ __device__ __forceinline__ int block_scan1(int &v, int *sm) {
 template <bool FP32, int LANES, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_persistent(DevPtrs d, KParams k, int vin, int nsteps) {
     __shared__ int sm[33];
+    __shared__ long long s_step;
     const int nthreads = gridDim.x * BLOCK;
     const int gtid = blockIdx.x * BLOCK + threadIdx.x;
     const unsigned T = k.T;
     const unsigned slice = (T + gridDim.x - 1) / gridDim.x;
     const unsigned lo = min(T, blockIdx.x * slice), hi = min(T, lo + slice);
     for (int st = 0; st < nsteps; ++st) {
-        // A
-        if (blockIdx.x == 0) {
-            const long long s = __ldcg(d.step) + 1;
-            __syncthreads();               // every thread of block 0 has read the counter
-            if (threadIdx.x == 0) {
-                *d.step = s;
-                *d.t_now = (double)s * k.dt;
-            }
-            wall_cells(d, k, (double)s * k.dt);
-        }
+        // A (the step counter's load is issued first, so that its latency
+        // overlaps the displacement update of block 0's nodes)
+        const long long s = (blockIdx.x == 0 && threadIdx.x == 0) ? __ldcg(d.step) + 1 : 0;
+        if (st == 0) prefetch_force_inputs(d, k, gtid, nthreads);
         bool need = false;
         for (int i = gtid; i < k.N; i += nthreads) need |= predict_node<true>(d, k, i, vin, 1);
         if (__any_sync(0xffffffffu, need) && (threadIdx.x & 31) == 0) *(volatile int *)d.rebuild = 1;
+        if (blockIdx.x == 0) {
+            if (threadIdx.x == 0) {
+                *d.step = s;
+                *d.t_now = (double)s * k.dt;
+                s_step = s;
+            }
+            __syncthreads();
+            wall_cells(d, k, (double)s_step * k.dt);
+        }
         if (!grid_barrier(d)) return;
         if (__ldcg(d.rebuild)) {
             // R1
@@ -290,7 +294,8 @@ __global__ void __launch_bounds__(BLOCK) k_persistent(DevPtrs d, KParams k, int 
             for (int node0 = blockIdx.x * (BLOCK / LANES); node0 < k.N; node0 += gridDim.x * (BLOCK / LANES))
                 force_block<FP32, true, LANES, BLOCK>(d, k, node0, vin, 1);
         }
-        if (!grid_barrier(d)) return;
+        // the end of the launch orders the last step before whatever follows
+        if (st + 1 < nsteps && !grid_barrier(d)) return;
         vin ^= 1;
     }
 }
