@@ -79,6 +79,50 @@ __device__ __forceinline__ void damping_friction64(const KParams &k, double Kn, 
     fy += Fdy + Ffy;
 }
 
+// Taylor coefficients, about theta = 0, of the shape functions of the wall
+// contact regions (Sec. 4.5), evaluated by the C++ front end at compile time:
+//   h1(theta) / theta^3 = sum_{k>=1} H_k theta^(2k-2),
+//       H_1 = 2/3, H_{k+1} = -4 H_k / ((2k+2)(2k+3))  (theta - sin theta cos theta);
+//   g(theta) / theta^5 = sum_{k>=2} G_k theta^(2k-4),  G_k = a_k - b_k - e_k, the
+//       terms of 3^(2k+1)/6, 4^k and 1/2 over (2k+1)! with alternating signs
+//       (h1 - 2/3 sin^3 theta);
+//   f(x) / x^3 = sum_{k>=1} F_k x^(2k-2),  F_1 = 1/6, F_{k+1} = -F_k / ((2k+2)(2k+3))
+//       (x - sin x).
+// Below theta = 0.3 (x = 0.5) nine, nine and eight terms leave a tail below
+// 1e-18 of the sum.
+__host__ __device__ constexpr double seg_h1_coef(int k) {
+    double c = 4.0 / 6.0;
+    for (int m = 1; m < k; ++m) c *= -4.0 / ((2.0 * m + 2.0) * (2.0 * m + 3.0));
+    return c;
+}
+__host__ __device__ constexpr double seg_g_coef(int k) {
+    double a = 243.0 / 6.0 / 120.0, b = 16.0 / 120.0, e = 0.5 / 120.0;
+    for (int m = 2; m < k; ++m) {
+        const double den = (2.0 * m + 2.0) * (2.0 * m + 3.0);
+        a *= -9.0 / den;
+        b *= -4.0 / den;
+        e *= -1.0 / den;
+    }
+    return a - b - e;
+}
+__host__ __device__ constexpr double seg_f_coef(int k) {
+    double c = 1.0 / 6.0;
+    for (int m = 1; m < k; ++m) c *= -1.0 / ((2.0 * m + 2.0) * (2.0 * m + 3.0));
+    return c;
+}
+constexpr int kSegH1Terms = 9, kSegGTerms = 9, kSegFTerms = 8;
+
+// Horner evaluation of sum_{k=K..KMAX} C_k t2^(k-K0) with the coefficients above
+// (WHICH: 0 = H, 1 = G, 2 = F), one FMA per term: a dependent chain of FMAs
+// instead of the recurrence's chain of divisions, which at GB300's FP64 rate
+// held a whole step back on the one node that touched a wall.
+template <int WHICH, int K, int KMAX>
+__device__ __forceinline__ double seg_horner(double t2) {
+    constexpr double c = WHICH == 0 ? seg_h1_coef(K) : (WHICH == 1 ? seg_g_coef(K) : seg_f_coef(K));
+    if constexpr (K == KMAX) return c;
+    else return fma(seg_horner<WHICH, K + 1, KMAX>(t2), t2, c);
+}
+
 // Circular segment of B_R(p) beyond a line at distance d < R (Sec. 4.5).
 // With theta = acos(d/R) = atan2(sqrt(R^2 - d^2), d) the paper's closed forms
 // read |S| = R^2 (theta - sin theta cos theta) and
@@ -86,29 +130,17 @@ __device__ __forceinline__ void damping_friction64(const KParams &k, double Kn, 
 // cancellation (Taylor series in theta below 0.3), because the printed
 // pi R^2/2 - R^2 asin(d/R) - d sqrt(R^2 - d^2) loses all digits as d -> R.
 __device__ __forceinline__ void wall_segment_stable(double d, double R, double &area, double &gap) {
-    const double th = atan2(sqrt((R - d) * (R + d)), d);
+    const double y = sqrt((R - d) * (R + d));
+    const double th = atan2(y, d);
     double h1, g;
     if (th < 0.3) {
         const double t2 = th * th;
-        double term = (4.0 / 6.0) * th * t2;
-        h1 = 0.0;
-#pragma unroll
-        for (int k = 1; k <= 12; ++k) {
-            h1 += term;
-            term *= -4.0 * t2 / ((2.0 * k + 2.0) * (2.0 * k + 3.0));
-        }
-        const double t5 = t2 * t2 * th;
-        double a = (243.0 / 6.0 / 120.0) * t5, b = (16.0 / 120.0) * t5, e = (0.5 / 120.0) * t5;
-        g = 0.0;
-#pragma unroll
-        for (int k = 2; k <= 14; ++k) {
-            g += a - b - e;
-            const double den = (2.0 * k + 2.0) * (2.0 * k + 3.0);
-            a *= -9.0 * t2 / den;
-            b *= -4.0 * t2 / den;
-            e *= -t2 / den;
-        }
+        h1 = (th * t2) * seg_horner<0, 1, kSegH1Terms>(t2);
+        g = (t2 * t2 * th) * seg_horner<1, 2, kSegGTerms + 1>(t2);
     } else {
+        // sin and cos of the rounded angle itself: with sqrt(R^2 - d^2) / R and
+        // d / R instead, the cancellation in g (about 30-fold at theta = 0.3)
+        // doubles the rounding error of the gap
         double sn, cs;
         sincos(th, &sn, &cs);
         h1 = th - sn * cs;
@@ -133,13 +165,7 @@ __device__ __forceinline__ void corner_region_stable(double di, double dj, doubl
     double f;
     if (dth < 0.5) {
         const double t2 = dth * dth;
-        double term = dth * t2 / 6.0;
-        f = 0.0;
-#pragma unroll
-        for (int k = 1; k <= 12; ++k) {
-            f += term;
-            term *= -t2 / ((2.0 * k + 2.0) * (2.0 * k + 3.0));
-        }
+        f = (dth * t2) * seg_horner<2, 1, kSegFTerms>(t2);
     } else {
         f = dth - sin(dth);
     }
