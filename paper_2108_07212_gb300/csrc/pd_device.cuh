@@ -297,7 +297,9 @@ __device__ __forceinline__ float ff_diff(float ah, float al, float bh, float bl)
 __device__ __forceinline__ void damping_friction32(float rd, float Kn, float rho_d, float rho, float dt, float mu,
                                                    float ex, float ey, float vrx, float vry, float Fr, float Vx,
                                                    float Vy, float &fx, float &fy) {
-    float beta = 2.0f * rd * sqrtf(Kn * rho_d / Vy);
+    // sqrt(K_n) sqrt(rho_d / V_y): K_n of GPa-range materials (~1e28) times a
+    // density over a node volume would overflow float
+    float beta = 2.0f * rd * sqrtf(Kn) * sqrtf(rho_d / Vy);
     float vn = vrx * ex + vry * ey;
     float cd = beta * Vx * Vy * vn;
     float vtx = vrx - vn * ex, vty = vry - vn * ey;
@@ -306,6 +308,86 @@ __device__ __forceinline__ void damping_friction32(float rd, float Kn, float rho
     float c = (vt > vthr) ? (mu * Fr / vt) : (rho * Vx / dt);
     fx += -cd * ex - c * vtx;
     fy += -cd * ey - c * vty;
+}
+
+// Float Horner evaluation of the wall-region series (coefficients as above).
+template <int WHICH, int K, int KMAX>
+__device__ __forceinline__ float seg_horner_f(float t2) {
+    constexpr float c = (float)(WHICH == 0 ? seg_h1_coef(K) : (WHICH == 1 ? seg_g_coef(K) : seg_f_coef(K)));
+    if constexpr (K == KMAX) return c;
+    else return fmaf(seg_horner_f<WHICH, K + 1, KMAX>(t2), t2, c);
+}
+
+// Wall force of the FP32-split path (Sec. 4.5, eq:wall-total): the same terms
+// as wall_force64, with the single-wall segments in float.  Each wall distance
+// d is formed in FP64 and the segment is evaluated from R_c - d and R_c + d,
+// each rounded once to float, so the small-angle quantities keep float's
+// relative precision (the gap to about 1e-6 relative).  The small-angle series
+// covers theta < 0.6 (six and eight terms leave a tail below 1e-8), where
+// the closed form's cancellation in g stays below tenfold.  A node within R_c
+// of a corner takes the FP64 terms.  Knf, rhof: the node's own contact
+// stiffness and density as floats; Kn, rho, V: the same in FP64.
+__device__ __forceinline__ void wall_force32(const KParams &k, const AggParams &A, float Knf, float rhof, double Kn,
+                                             double rho, double t, double px, double py, double vx, double vy,
+                                             double V, double &Fx_out, double &Fy_out, int *status) {
+    const double Rc = A.Rc;
+    double d[4];
+    d[0] = px - (A.w0[0] + A.wv[0] * t);
+    d[1] = (A.w0[1] + A.wv[1] * t) - px;
+    d[2] = py - (A.w0[2] + A.wv[2] * t);
+    d[3] = (A.w0[3] + A.wv[3] * t) - py;
+    bool near = false, corner = false;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) near |= d[l] < Rc;
+    if (!near) {
+        Fx_out = Fy_out = 0.0;
+        return;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const double di = fmax(d[c >> 1], 0.0), dj = fmax(d[2 + (c & 1)], 0.0);
+        corner |= di * di + dj * dj < Rc * Rc;
+    }
+    if (corner) {
+        wall_force64(k, A, Kn, rho, t, px, py, vx, vy, V, Fx_out, Fy_out, status);
+        return;
+    }
+    const float Rf = (float)Rc, Vx = (float)V, rd = k.rdf, dt = k.dtf, mu = k.muf;
+    float Fx = 0.f, Fy = 0.f;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        if (d[l] < 0.0) {
+            if (status) atomicAdd(&status[PD_STATUS_PENETRATION], 1);
+            d[l] = 0.0;
+        }
+        if (!(d[l] < Rc)) continue;
+        const float e = (float)(Rc - d[l]), sp = (float)(Rc + d[l]), df = (float)d[l];
+        const float y = sqrtf(e * sp);
+        const float th = atan2f(y, df);
+        float h1, g;
+        if (th < 0.6f) {
+            const float t2 = th * th;
+            h1 = (th * t2) * seg_horner_f<0, 1, 6>(t2);
+            g = (t2 * t2 * th) * seg_horner_f<1, 2, 9>(t2);
+        } else {
+            float sn, cs;
+            sincosf(th, &sn, &cs);
+            h1 = th - sn * cs;
+            g = h1 - (2.0f / 3.0f) * sn * sn * sn;
+        }
+        const float Ar = Rf * Rf * h1, gap = Rf * g / h1;
+        // (a region below 1e-30 R_c^2 carries no force float can represent)
+        if (!(h1 > 1e-30f) || !(gap > 0.f)) continue;
+        const float Fr = ((Knf * gap) * Vx) * Ar;
+        const float ex = (l == 0) ? -1.f : (l == 1 ? 1.f : 0.f), ey = (l == 2) ? -1.f : (l == 3 ? 1.f : 0.f);
+        const float vrx = (float)(vx - ((l < 2) ? A.wv[l] : 0.0)), vry = (float)(vy - ((l < 2) ? 0.0 : A.wv[l]));
+        float gx = -Fr * ex, gy = -Fr * ey;
+        damping_friction32(rd, Knf, rhof, rhof, dt, mu, ex, ey, vrx, vry, Fr, Vx, Ar, gx, gy);
+        Fx += gx;
+        Fy += gy;
+    }
+    Fx_out = (double)Fx;
+    Fy_out = (double)Fy;
 }
 
 // ---------------------------------------------------------------------------
@@ -1016,8 +1098,9 @@ __device__ __forceinline__ void node_epilogue32(const DevPtrs &d, const KParams 
         const AggParams &A = d.agg[ag];
         const double Kn = k.mat ? 18.0 * __ldg(&d.g_k[gi]) / A.pe5 : A.Kn;
         const double rho = k.mat ? __ldg(&d.g_rho[gi]) : k.rho;
-        wall_force64(k, A, Kn, rho, ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, __ldg(&d.V[i]), Fwx, Fwy,
-                     d.status);
+        const float Knf = k.mat ? __ldg(&d.g_kf[gi]) : A.knf, rhof = __ldg(&d.gc[gi]).w;
+        wall_force32(k, A, Knf, rhof, Kn, rho, ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, __ldg(&d.V[i]), Fwx,
+                     Fwy, d.status);
     }
     if (k.store)
         finish_node<PERSIST, true>(d, k, i, vin, update_v, vi, 0.0, (double)f.bx, (double)f.by, (double)f.sx,

@@ -105,3 +105,66 @@ def test_fp32_trajectory_tracks_fp64():
     assert np.linalg.norm(ub - ua) <= 1e-5 * np.linalg.norm(ua)
     rc, st = b.status()
     assert rc == B.PD_OK
+
+
+def _corner_workload():
+    """A square grain in the lower-left corner and a disk at the right wall, all
+    four walls moving (single walls, corners, wall damping and friction)."""
+    R = 1e-3
+    h = R / 8
+    p = I.default_params(k_bulk=1.0e6, wall_lo=(0.0, 0.0), wall_hi=(3.2e-3, 3.2e-3), wall_vel_lo=(0.5, 0.3),
+                         wall_vel_hi=(-0.4, -0.6), gy=-5000.0)
+    rc = p["rc_ratio"] * h
+    geom = [(5 * h + 1.1 * rc, 5 * h + 1.2 * rc, R, 0.0, -0.5, -0.4, h),
+            (3.2e-3 - 7 * h - 1.05 * rc, 2.0e-3, R * 0.999, 0.2, 0.6, 0.1, h)]
+    return I.Workload(shapes=[I.square_shape(), I.disk_shape()], grain_shape=np.array([0, 1], np.int32),
+                      grain_geom=np.array(geom), params=p, n_steps=600, name="corner")
+
+
+def test_fp32_wall_and_corner_forces_on_a_grid_of_positions():
+    """The FP32-split wall terms (float single-wall segments, FP64 corner zones)
+    against the oracle for nodes on a grid over the single-wall bands and the
+    four corner zones, with random velocities: per node within 1e-5 of the
+    largest wall force."""
+    w = _corner_workload()
+    P = O.OracleProblem.from_workload(w).init_accel()
+    S = _sim(w, B.PD_FP32_SPLIT)
+    rc = P.prm[O.P_RC]
+    lo, hi = np.array(w.params["wall_lo"]), np.array(w.params["wall_hi"])
+    rng = np.random.default_rng(4)
+    g = np.linspace(0.02, 1.3, 9) * rc
+    targets = [(cx + sx * a, cy + sy * b) for cx, sx in ((lo[0], 1), (hi[0], -1)) for cy, sy in ((lo[1], 1), (hi[1], -1))
+               for a in g for b in g]
+    targets = np.array(targets)[: P.N]
+    n = len(targets)
+    P.u[:n] = targets - P.X[:n]
+    P.v[:] = rng.normal(scale=0.3, size=P.v.shape)
+    P.broken[:] = 1                      # no bond forces
+    _push(S, P)
+    S.eval_forces()
+    _, parts_o = P.forces()
+    parts = S.get("FORCE_PARTS")
+    single = np.array([(min(a, b) < rc) and np.hypot(a, b) >= rc for a in g for b in g] * 4)[:n]
+    assert single.sum() > 50             # nodes on the float single-wall path
+    assert np.count_nonzero(parts_o[3][:n, 0]) > 200
+    scale = np.abs(parts_o[3]).max()
+    assert np.abs(parts[3] - parts_o[3]).max() <= FORCE_RTOL_FP32 * scale
+
+
+def test_fp32_stiff_material_contact_and_walls_stay_finite():
+    """A GPa-range bulk modulus (K_n ~ 1e28 in float) in grain and wall contact:
+    the FP32-split damping must not overflow; the force matches the oracle."""
+    w = _contact_disks(k_bulk=2.0e9)
+    rc = w.params["rc_ratio"] * 1e-3 / 8
+    w.grain_geom[1, 1] -= 0.5 * rc        # the disks overlap: node-node contact from the start
+    X = O.OracleProblem.from_workload(w).X
+    w.grain_geom[:, 1] -= X[:, 1].min() - 0.5 * rc     # lowest node R_c / 2 above the floor
+    P = O.OracleProblem.from_workload(w).init_accel()
+    S = _sim(w, B.PD_FP32_SPLIT)
+    _push(S, P)
+    S.eval_forces()
+    Fo, parts_o = P.forces()
+    F = S.get("FORCE")
+    assert np.abs(parts_o[2]).max() > 0 and np.abs(parts_o[3]).max() > 0
+    assert np.all(np.isfinite(F))
+    assert np.abs(F - Fo).max() <= FORCE_RTOL_FP32 * np.abs(Fo).max()
