@@ -294,6 +294,18 @@ __device__ __forceinline__ float ff_diff(float ah, float al, float bh, float bl)
     return __fsub_rn(ah, bh) + (al - bl);
 }
 
+// Square root and quotient of the bond loop by the approximate special-function
+// instructions (relative error about 2^-22) instead of the correctly rounded
+// sequences: the FP32-split bond force carries a 1e-5 tolerance, and stretches
+// within 1e-4 of the critical one are re-decided in FP64 after the loop, so
+// the break decisions do not change.  (The operands here are far from the
+// ranges where __fdividef returns 0.)
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ void damping_friction32(float rd, float Kn, float rho_d, float rho, float dt, float mu,
                                                    float ex, float ey, float vrx, float vry, float Fr, float Vx,
                                                    float Vy, float &fx, float &fy) {
@@ -943,9 +955,9 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
             float q, eq;
             two_prod(nn, gq.y, q, eq);                           // |xi|^2 = n h^2
             const float num = ff_diff(L2h, L2l, q, eq + nn * gq.z);
-            const float xi = gq.x * sqrtf(nn);
-            const float L = sqrtf(L2h);
-            const float s = num / (xi * (L + xi));
+            const float xi = gq.x * sqrt_approx(nn);
+            const float L = sqrt_approx(L2h);
+            const float s = __fdividef(num, xi * (L + xi));
             const float as = fabsf(s);
             // near the threshold the FP64 path decides, after the loop (its FP64
             // registers stay out of the hot loop)
@@ -959,7 +971,7 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
                 continue;
             }
             const float cws = (k.micro ? cw * (1.0f - xi / eps) : cw) * s;
-            const float qf = cws * VV / L;
+            const float qf = __fdividef(cws * VV, L);
             Fbx += qf * (dxh + dxl);
             Fby += qf * (dyh + dyl);
         }
@@ -981,9 +993,9 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
             float q, eq;
             two_prod(nn, gq.y, q, eq);
             const float num = ff_diff(L2h, L2l, q, eq + nn * gq.z);
-            const float xi = gq.x * sqrtf(nn);
-            const float L = sqrtf(L2h);
-            const float s = num / (xi * (L + xi));
+            const float xi = gq.x * sqrt_approx(nn);
+            const float L = sqrt_approx(L2h);
+            const float s = __fdividef(num, xi * (L + xi));
             const float as = fabsf(s);
             if (!(as > s0_lo && as < s0_hi)) continue;
             const double2 pi = position64<PERSIST>(d, ii), pj = position64<PERSIST>(d, j);
@@ -995,7 +1007,7 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
                 continue;
             }
             const float cws = (k.micro ? cw * (1.0f - xi / eps) : cw) * s;
-            const float qf = cws * VV / L;
+            const float qf = __fdividef(cws * VV, L);
             Fbx += qf * (dxh + dxl);
             Fby += qf * (dyh + dyl);
         }
