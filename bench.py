@@ -294,10 +294,10 @@ BYTES_PER_NODE_STEP_FP32 = 216
 # profiles/traffic_settling50.md).  They hold while the kernel sources hash to
 # TRAFFIC_DIGEST; otherwise, or for a variant not captured, traffic is null.
 TRAFFIC_SETTLING50 = {
-    "k_persistent<1, 4, 256>": 3765504,
-    "k_persistent<0, 4, 128>": 7105536,
+    "k_persistent<1, 4, 128>": 4047104,
+    "k_persistent<0, 4, 128>": 7392896,
 }
-TRAFFIC_DIGEST = "53dd520589907ff4eae988dc5a8c360a0f1ba83c"
+TRAFFIC_DIGEST = "57574a31de53c30ff2fcef15b2260e980ca3a15b"
 TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu", "pd_common.cu", "pd_internal.h")
 
 
