@@ -90,20 +90,44 @@ __device__ __forceinline__ void fwd_tile(const __nv_bfloat16 *__restrict__ W1, c
         }
         *reinterpret_cast<uint4 *>(sA + tc::kmajor_off(tid, k8, TILE)) = *reinterpret_cast<const uint4 *>(xb);
     }
-    for (int e = tid; e < HID * IN / 8; e += 128) {
-        const int r = e / (IN / 8), k8 = (e % (IN / 8)) * 8;
-        *reinterpret_cast<uint4 *>(sW1 + tc::kmajor_off(r, k8, HID)) =
-            *reinterpret_cast<const uint4 *>(W1 + (size_t)r * IN + k8);
-    }
-    for (int e = tid; e < HID * HID / 8; e += 128) {
-        const int r = e / (HID / 8), k8 = (e % (HID / 8)) * 8;
-        *reinterpret_cast<uint4 *>(sW2 + tc::kmajor_off(r, k8, HID)) =
-            *reinterpret_cast<const uint4 *>(W2 + (size_t)r * HID + k8);
-    }
-    for (int e = tid; e < OUT * HID / 8; e += 128) {
-        const int r = e / (HID / 8), k8 = (e % (HID / 8)) * 8;
-        *reinterpret_cast<uint4 *>(sW3 + tc::kmajor_off(r, k8, OUT)) =
-            *reinterpret_cast<const uint4 *>(W3 + (size_t)r * HID + k8);
+    {
+        // the three weight matrices, 16 bytes per load: every load of the thread
+        // is issued before the first store, so the copy costs one L2 (or DRAM)
+        // latency instead of one per row chunk
+        static_assert((HID * IN / 8) % 128 == 0 && (HID * HID / 8) % 128 == 0 && (OUT * HID / 8) % 128 == 0,
+                      "weight chunks must divide over the 128 threads");
+        constexpr int n1 = HID * IN / 8 / 128, n2 = HID * HID / 8 / 128, n3 = OUT * HID / 8 / 128;
+        uint4 w1[n1], w2[n2], w3[n3];
+#pragma unroll
+        for (int q = 0; q < n1; ++q) {
+            const int e = tid + q * 128, r = e / (IN / 8), k8 = (e % (IN / 8)) * 8;
+            w1[q] = *reinterpret_cast<const uint4 *>(W1 + (size_t)r * IN + k8);
+        }
+#pragma unroll
+        for (int q = 0; q < n2; ++q) {
+            const int e = tid + q * 128, r = e / (HID / 8), k8 = (e % (HID / 8)) * 8;
+            w2[q] = *reinterpret_cast<const uint4 *>(W2 + (size_t)r * HID + k8);
+        }
+#pragma unroll
+        for (int q = 0; q < n3; ++q) {
+            const int e = tid + q * 128, r = e / (HID / 8), k8 = (e % (HID / 8)) * 8;
+            w3[q] = *reinterpret_cast<const uint4 *>(W3 + (size_t)r * HID + k8);
+        }
+#pragma unroll
+        for (int q = 0; q < n1; ++q) {
+            const int e = tid + q * 128, r = e / (IN / 8), k8 = (e % (IN / 8)) * 8;
+            *reinterpret_cast<uint4 *>(sW1 + tc::kmajor_off(r, k8, HID)) = w1[q];
+        }
+#pragma unroll
+        for (int q = 0; q < n2; ++q) {
+            const int e = tid + q * 128, r = e / (HID / 8), k8 = (e % (HID / 8)) * 8;
+            *reinterpret_cast<uint4 *>(sW2 + tc::kmajor_off(r, k8, HID)) = w2[q];
+        }
+#pragma unroll
+        for (int q = 0; q < n3; ++q) {
+            const int e = tid + q * 128, r = e / (HID / 8), k8 = (e % (HID / 8)) * 8;
+            *reinterpret_cast<uint4 *>(sW3 + tc::kmajor_off(r, k8, OUT)) = w3[q];
+        }
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
