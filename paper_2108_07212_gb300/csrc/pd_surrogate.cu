@@ -289,29 +289,49 @@ __global__ void __launch_bounds__(128) k_sur_project_tc(DevPtrs d, KParams k) {
             if (!d.sur_active[g]) g = -1;
         }
         const float *w = g >= 0 ? reinterpret_cast<const float *>(d.sur_w) + 2 * (size_t)d.g_start[g] : nullptr;
-        for (int kk = 0; kk < KC; kk += 2) {
-            const int r = r0 + kk;
-            float2 v = make_float2(0.f, 0.f);
-            if (w && r < rows2) v = *reinterpret_cast<const float2 *>(w + r);
-            uint32_t lo;
-            const uint32_t hi = split_pack(v.x, v.y, lo);
-            *reinterpret_cast<uint32_t *>(sAh + tc::kmajor_off(tid, kk, MR)) = hi;
-            *reinterpret_cast<uint32_t *>(sAl + tc::kmajor_off(tid, kk, MR)) = lo;
+        // batches of kLoadBatch pairs: all loads of a batch are in flight before
+        // its stores (one L2 latency per batch, not per pair)
+        constexpr int kLoadBatch = 16;
+        static_assert(KC % (2 * kLoadBatch) == 0, "chunk must hold whole batches");
+#pragma unroll 1
+        for (int kb = 0; kb < KC; kb += 2 * kLoadBatch) {
+            float2 v[kLoadBatch];
+#pragma unroll
+            for (int q = 0; q < kLoadBatch; ++q) {
+                const int r = r0 + kb + 2 * q;
+                v[q] = (w && r < rows2) ? *reinterpret_cast<const float2 *>(w + r) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < kLoadBatch; ++q) {
+                const int kk = kb + 2 * q;
+                uint32_t lo;
+                const uint32_t hi = split_pack(v[q].x, v[q].y, lo);
+                *reinterpret_cast<uint32_t *>(sAh + tc::kmajor_off(tid, kk, MR)) = hi;
+                *reinterpret_cast<uint32_t *>(sAl + tc::kmajor_off(tid, kk, MR)) = lo;
+            }
         }
     }
     // B: the basis, mode-major, padded rows (16-byte pieces of 8 values)
     {
         const uint16_t *bh = d.bmm_hi + (size_t)d.tmpl_rows[t] * M;
         const uint16_t *bl = d.bmm_lo + (size_t)d.tmpl_rows[t] * M;
-        for (int e = tid; e < NM * (KC / 8); e += 128) {
-            const int m = e / (KC / 8), k8 = (e % (KC / 8)) * 8;
-            uint4 vh = make_uint4(0, 0, 0, 0), vl = make_uint4(0, 0, 0, 0);
+        constexpr int nb = NM * (KC / 8) / 128;
+        static_assert(NM * (KC / 8) % 128 == 0, "basis pieces must divide over the 128 threads");
+        uint4 vh[nb], vl[nb];
+#pragma unroll
+        for (int q = 0; q < nb; ++q) {
+            const int e = tid + q * 128, m = e / (KC / 8), k8 = (e % (KC / 8)) * 8;
+            vh[q] = vl[q] = make_uint4(0, 0, 0, 0);
             if (m < M) {
-                vh = *reinterpret_cast<const uint4 *>(bh + (size_t)m * rp + r0 + k8);
-                vl = *reinterpret_cast<const uint4 *>(bl + (size_t)m * rp + r0 + k8);
+                vh[q] = *reinterpret_cast<const uint4 *>(bh + (size_t)m * rp + r0 + k8);
+                vl[q] = *reinterpret_cast<const uint4 *>(bl + (size_t)m * rp + r0 + k8);
             }
-            *reinterpret_cast<uint4 *>(sBh + tc::kmajor_off(m, k8, NM)) = vh;
-            *reinterpret_cast<uint4 *>(sBl + tc::kmajor_off(m, k8, NM)) = vl;
+        }
+#pragma unroll
+        for (int q = 0; q < nb; ++q) {
+            const int e = tid + q * 128, m = e / (KC / 8), k8 = (e % (KC / 8)) * 8;
+            *reinterpret_cast<uint4 *>(sBh + tc::kmajor_off(m, k8, NM)) = vh[q];
+            *reinterpret_cast<uint4 *>(sBl + tc::kmajor_off(m, k8, NM)) = vl[q];
         }
     }
     tc::fence_async_smem();
@@ -384,11 +404,13 @@ __global__ void __launch_bounds__(128) k_sur_expand_tc(DevPtrs d, KParams k) {
     // A: network outputs (modal bond forces) of the tile's grains
     {
         const float *y = g >= 0 ? d.sur_y + (size_t)(slot0 + s) * M : nullptr;
+        float yv[KM];                      // every load before the first store
+#pragma unroll
+        for (int kk = 0; kk < KM; ++kk) yv[kk] = (y && kk < M) ? y[kk] : 0.f;
+#pragma unroll
         for (int kk = 0; kk < KM; kk += 2) {
-            float2 v = make_float2(0.f, 0.f);
-            if (y && kk < M) v = make_float2(y[kk], kk + 1 < M ? y[kk + 1] : 0.f);
             uint32_t lo;
-            const uint32_t hi = split_pack(v.x, v.y, lo);
+            const uint32_t hi = split_pack(yv[kk], yv[kk + 1], lo);
             *reinterpret_cast<uint32_t *>(sAh + tc::kmajor_off(tid, kk, MR)) = hi;
             *reinterpret_cast<uint32_t *>(sAl + tc::kmajor_off(tid, kk, MR)) = lo;
         }
@@ -397,15 +419,23 @@ __global__ void __launch_bounds__(128) k_sur_expand_tc(DevPtrs d, KParams k) {
     {
         const uint16_t *bh = d.bnm_hi + ((size_t)d.tmpl_rows[t] + r0) * M;
         const uint16_t *bl = d.bnm_lo + ((size_t)d.tmpl_rows[t] + r0) * M;
-        for (int e = tid; e < NR * (KM / 8); e += 128) {
-            const int r = e / (KM / 8), k8 = (e % (KM / 8)) * 8;
-            uint4 vh = make_uint4(0, 0, 0, 0), vl = make_uint4(0, 0, 0, 0);
+        constexpr int nb = NR * (KM / 8) / 128;
+        static_assert(NR * (KM / 8) % 128 == 0, "basis pieces must divide over the 128 threads");
+        uint4 vh[nb], vl[nb];             // every load before the first store
+#pragma unroll
+        for (int q = 0; q < nb; ++q) {
+            const int e = tid + q * 128, r = e / (KM / 8), k8 = (e % (KM / 8)) * 8;
+            vh[q] = vl[q] = make_uint4(0, 0, 0, 0);
             if (k8 < M) {
-                vh = *reinterpret_cast<const uint4 *>(bh + (size_t)r * M + k8);
-                vl = *reinterpret_cast<const uint4 *>(bl + (size_t)r * M + k8);
+                vh[q] = *reinterpret_cast<const uint4 *>(bh + (size_t)r * M + k8);
+                vl[q] = *reinterpret_cast<const uint4 *>(bl + (size_t)r * M + k8);
             }
-            *reinterpret_cast<uint4 *>(sBh + tc::kmajor_off(r, k8, NR)) = vh;
-            *reinterpret_cast<uint4 *>(sBl + tc::kmajor_off(r, k8, NR)) = vl;
+        }
+#pragma unroll
+        for (int q = 0; q < nb; ++q) {
+            const int e = tid + q * 128, r = e / (KM / 8), k8 = (e % (KM / 8)) * 8;
+            *reinterpret_cast<uint4 *>(sBh + tc::kmajor_off(r, k8, NR)) = vh[q];
+            *reinterpret_cast<uint4 *>(sBl + tc::kmajor_off(r, k8, NR)) = vl[q];
         }
     }
     tc::fence_async_smem();
