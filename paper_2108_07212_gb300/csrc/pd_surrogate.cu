@@ -124,16 +124,31 @@ __global__ void __launch_bounds__(kSurThreads) k_sur_frame(DevPtrs d, KParams k,
     // one pass: centroid and the best-fit rotation sums in the lattice frame,
     // A = sum l . d, B = sum l x d (l: centred lattice index, d = p - p_first)
     float sx = 0.f, sy = 0.f, sa = 0.f, sb = 0.f;
-    for (int i = s0 + threadIdx.x; i < s1; i += kSurThreads) {
-        const float4 qn = d.pq[i];
+    // nodes in batches of kFrameBatch per thread, all loads of a batch first
+    // (the per-thread order of the sums is unchanged)
+    constexpr int kFrameBatch = 4;
+    for (int i0 = s0 + threadIdx.x; i0 < s1; i0 += kFrameBatch * kSurThreads) {
+      float4 qb[kFrameBatch];
+      int2 lb[kFrameBatch];
+#pragma unroll
+      for (int m = 0; m < kFrameBatch; ++m) {
+          const int i = min(i0 + m * kSurThreads, s1 - 1);
+          qb[m] = d.pq[i];
+          lb[m] = d.lat[i];
+      }
+#pragma unroll
+      for (int m = 0; m < kFrameBatch; ++m) {
+        if (i0 + m * kSurThreads >= s1) break;
+        const float4 qn = qb[m];
         const float2 ph = make_float2(qn.x, qn.y), pl = make_float2(qn.z, qn.w);
-        const int2 li = d.lat[i];
+        const int2 li = lb[m];
         const float dx = __fsub_rn(ph.x, ph0.x) + (pl.x - pl0.x), dy = __fsub_rn(ph.y, ph0.y) + (pl.y - pl0.y);
         const float lx = (float)li.x - fc.z, ly = (float)li.y - fc.w;
         sx += dx;
         sy += dy;
         sa += lx * dx + ly * dy;
         sb += lx * dy - ly * dx;
+      }
     }
     const float Sx = block_sum_f(sx, smf), Sy = block_sum_f(sy, smf);
     const float A = block_sum_f(sa, smf), Bs = block_sum_f(sb, smf);
@@ -158,10 +173,22 @@ __global__ void __launch_bounds__(kSurThreads) k_sur_frame(DevPtrs d, KParams k,
     __syncthreads();
     const float ch = frame[0], cl = frame[1], sh = frame[2], sl = frame[3], cx = frame[4], cy = frame[5];
     const float hinv = 1.0f / fc.x;
-    for (int i = s0 + threadIdx.x; i < s1; i += kSurThreads) {
-        const float4 qn = d.pq[i];
+    for (int i0 = s0 + threadIdx.x; i0 < s1; i0 += kFrameBatch * kSurThreads) {
+      float4 qb[kFrameBatch];
+      int2 lb[kFrameBatch];
+#pragma unroll
+      for (int m = 0; m < kFrameBatch; ++m) {
+          const int i = min(i0 + m * kSurThreads, s1 - 1);
+          qb[m] = d.pq[i];
+          lb[m] = d.lat[i];
+      }
+#pragma unroll
+      for (int m = 0; m < kFrameBatch; ++m) {
+        const int i = i0 + m * kSurThreads;
+        if (i >= s1) break;
+        const float4 qn = qb[m];
         const float2 ph = make_float2(qn.x, qn.y), pl = make_float2(qn.z, qn.w);
-        const int2 li = d.lat[i];
+        const int2 li = lb[m];
         // e = p - c as float-float pairs
         float exh, exe, eyh, eye;
         two_sum(__fsub_rn(ph.x, ph0.x), -cx, exh, exe);
@@ -185,6 +212,7 @@ __global__ void __launch_bounds__(kSurThreads) k_sur_frame(DevPtrs d, KParams k,
         const float rxl = rxe + fc.y * lx, ryl = rye + fc.y * ly;
         const float wx = __fsub_rn(uxh, rxh) + (uxl - rxl), wy = __fsub_rn(uyh, ryh) + (uyl - ryl);
         d.sur_w[i] = make_float2(wx * hinv, wy * hinv);
+      }
     }
 }
 
