@@ -72,20 +72,24 @@ __device__ __forceinline__ void fwd_tile(const __nv_bfloat16 *__restrict__ W1, c
     // operands -> canonical K-major shared layout, 8 values (one 16-byte core
     // matrix row) per store
     const bool x16 = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
-    for (int k8 = 0; k8 < IN; k8 += 8) {
-        float x[8];
-        if (row < B && x16) {
-            const float4 a = *reinterpret_cast<const float4 *>(X + (size_t)row * IN + k8);
-            const float4 b = *reinterpret_cast<const float4 *>(X + (size_t)row * IN + k8 + 4);
-            x[0] = a.x, x[1] = a.y, x[2] = a.z, x[3] = a.w, x[4] = b.x, x[5] = b.y, x[6] = b.z, x[7] = b.w;
-        } else {
+    // the thread's whole input row is loaded before any store
+    float x[IN];
+    if (row < B && x16) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) x[q] = (row < B) ? X[(size_t)row * IN + k8 + q] : 0.f;
+        for (int k4 = 0; k4 < IN; k4 += 4) {
+            const float4 a = *reinterpret_cast<const float4 *>(X + (size_t)row * IN + k4);
+            x[k4] = a.x, x[k4 + 1] = a.y, x[k4 + 2] = a.z, x[k4 + 3] = a.w;
         }
+    } else {
+#pragma unroll
+        for (int q = 0; q < IN; ++q) x[q] = (row < B) ? X[(size_t)row * IN + q] : 0.f;
+    }
+#pragma unroll
+    for (int k8 = 0; k8 < IN; k8 += 8) {
         __align__(16) __nv_bfloat16 xb[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            xb[q] = __float2bfloat16(x[q]);
+            xb[q] = __float2bfloat16(x[k8 + q]);
             if (train) n.Xt[(size_t)(k8 + q) * Bp + row] = xb[q];
         }
         *reinterpret_cast<uint4 *>(sA + tc::kmajor_off(tid, k8, TILE)) = *reinterpret_cast<const uint4 *>(xb);
