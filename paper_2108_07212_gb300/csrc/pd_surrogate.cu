@@ -153,14 +153,18 @@ __global__ void __launch_bounds__(kSurThreads) k_sur_frame(DevPtrs d, KParams k,
     const float Sx = block_sum_f(sx, smf), Sy = block_sum_f(sy, smf);
     const float A = block_sum_f(sa, smf), Bs = block_sum_f(sb, smf);
     if (threadIdx.x == 0) {
-        // reference offsets X' = R(theta) h l: sum X' . p' = cos A + sin B, sum X' x p' = cos B - sin A
-        const double th = d.g_theta[g];
-        double st, ct;
-        sincos(th, &st, &ct);
-        const double phi = atan2(ct * Bs - st * A, ct * A + st * Bs);
-        double sr, cr;
-        sincos(th + phi, &sr, &cr);
-        d.sur_phi[g] = phi;
+        // reference offsets X' = R(theta) h l: sum X' . p' = cos A + sin B, sum X' x p' = cos B - sin A,
+        // so the best-fit phi = atan2(cos B - sin A, cos A + sin B), and the angle sum reduces to
+        // (cos, sin)(theta + phi) = (A, B) / |(A, B)|: no trigonometry on the block's critical path
+        const double Ad = A, Bd = Bs, r2 = Ad * Ad + Bd * Bd;
+        double cr, sr;
+        if (r2 > 0.0) {
+            const double ir = 1.0 / sqrt(r2);
+            cr = Ad * ir;
+            sr = Bd * ir;
+        } else {
+            sincos(d.g_theta[g], &sr, &cr);      // no deformation information: phi = 0
+        }
         d.sur_rot[g] = make_float2((float)cr, (float)sr);
         const float ch = (float)cr, sh = (float)sr;
         frame[0] = ch;
@@ -171,6 +175,13 @@ __global__ void __launch_bounds__(kSurThreads) k_sur_frame(DevPtrs d, KParams k,
         frame[5] = Sy / (float)n;
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        // the angle phi itself (state only; after the barrier, off the other threads' path)
+        const double th = d.g_theta[g];
+        double st, ct;
+        sincos(th, &st, &ct);
+        d.sur_phi[g] = atan2(ct * Bs - st * A, ct * A + st * Bs);
+    }
     const float ch = frame[0], cl = frame[1], sh = frame[2], sl = frame[3], cx = frame[4], cy = frame[5];
     const float hinv = 1.0f / fc.x;
     for (int i0 = s0 + threadIdx.x; i0 < s1; i0 += kFrameBatch * kSurThreads) {
