@@ -257,6 +257,73 @@ def test_self_contact_equals_contact_when_cw_over_Rc_is_Kn():
     assert np.allclose(ps[1], pp[2], rtol=1e-12, atol=0)
 
 
+# ---------------------------------------------------------------------------
+# self-contact of nodes whose reference distance is below R_c (Sec. 4.4, first branch)
+
+
+def _self_pair(xi, Rc, Kn, d, v_rel=0.0, dt=1e-9):
+    """Two unbonded nodes of one grain, reference distance xi, current distance d."""
+    h = 1e-4
+    V = h * h
+    prm = _prm(Kn, Rc, dt=dt)
+    X = np.array([[0.0, 0.0], [xi, 0.0]])
+    v = np.array([[v_rel / 2, 0.0], [-v_rel / 2, 0.0]])
+    P = O.OracleProblem(X, [V, V], [0, 0], [0, 0, 0], [], [Kn * Rc], [1.0], [3 * h], prm, v)
+    P.u[1, 0] = d - xi
+    return P, V
+
+
+def test_self_contact_below_Rc_is_a_one_sided_spring_about_the_reference_distance():
+    """For |xi| < R_c the self-contact force c_w (d - |xi|) / |xi| V_x V_y acts only
+    while d < |xi|: a linear spring of stiffness c_w V^2 / |xi| on the reduced mass
+    rho V / 2 that is compressed from its rest length.  An approaching pair
+    therefore stays in contact for half a period pi / omega and leaves with its
+    impact speed (no damping, no friction), and the pair feels nothing while
+    |xi| <= d < R_c (no attraction back to the reference distance)."""
+    h, Rc = 1e-4, 0.95e-4
+    Kn = O.contact_stiffness(1e6, 3 * h)
+    cw = Kn * Rc
+    xi = 0.5 * Rc
+    V = h * h
+    omega = math.sqrt(2.0 * (cw * V * V / xi) / (1200.0 * V))
+    dt = 0.005 / omega
+    P, _ = _self_pair(xi, Rc, Kn, d=xi + 1e-9, v_rel=0.1, dt=dt)
+    P.init_accel()
+    inside = 0
+    started = False
+    for _ in range(20000):
+        P.run(1)
+        dist = np.linalg.norm(P.positions[1] - P.positions[0])
+        if dist < xi:
+            started = True
+            inside += 1
+        elif started:
+            break
+    assert inside * dt == pytest.approx(math.pi / omega, rel=0.01)
+    assert (P.v[0, 0] - P.v[1, 0]) == pytest.approx(-0.1, rel=1e-4)
+    # between |xi| and R_c: inside the contact radius, yet no force
+    for frac in (0.55, 0.75, 0.99):
+        Q, _ = _self_pair(xi, Rc, Kn, d=frac * Rc, v_rel=0.3)
+        F, parts = Q.forces()
+        assert np.all(F == 0.0) and np.all(parts == 0.0)
+
+
+def test_self_contact_branches_meet_at_Rc():
+    """The two self-contact branches (|xi| < R_c: rest length |xi|; |xi| >= R_c:
+    rest length R_c) give the same force as |xi| crosses R_c from either side,
+    at any compression d < R_c."""
+    h, Rc = 1e-4, 0.95e-4
+    Kn = O.contact_stiffness(1e6, 3 * h)
+    for frac in (0.3, 0.7, 0.95):
+        d = frac * Rc
+        below, _ = _self_pair(Rc * (1 - 1e-10), Rc, Kn, d)
+        above, _ = _self_pair(Rc * (1 + 1e-10), Rc, Kn, d)
+        Fb, pb = below.forces()
+        Fa, pa = above.forces()
+        assert np.abs(pb[1]).max() > 0
+        assert np.allclose(pb[1], pa[1], rtol=1e-8, atol=0)
+
+
 def test_friction_on_floor_gives_coulomb_deceleration_then_sticks():
     """Sec. 4.2 + 4.5: a node resting on the floor (|F_r| = rho V g) sliding at v0
     decelerates at mu g (slip) and then sticks (zero relative speed kept)."""
