@@ -72,6 +72,9 @@ def lib():
             L.or_init_accel.argtypes = [dp, c_d, c_i, dp, dp, dp, dp, dp, ip, dp, dp, dp, dp, ip, ip, up, ip]
             L.or_diagnostics.argtypes = [dp, c_i, dp, dp, dp, dp, ip, dp, dp, dp, ip, ip, up, dp]
             L.or_wall_sums.argtypes = [dp, c_d, c_i, dp, dp, dp, dp, ip, dp, dp]
+            L.or_wall_segment_energy.argtypes = [c_d, c_d]
+            L.or_wall_segment_energy.restype = c_d
+            L.or_energies.argtypes = [dp, c_d, c_i, dp, dp, dp, ip, dp, dp, ip, ip, up, dp]
             _lib = L
     return _lib
 
@@ -121,6 +124,11 @@ def corner_region(di, dj, Rc):
     A, Ix, Iy = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     lib().or_corner_region(di, dj, Rc, ctypes.byref(A), ctypes.byref(Ix), ctypes.byref(Iy))
     return A.value, Ix.value, Iy.value
+
+
+def wall_segment_energy(d, Rc):
+    """R_c^4 J(theta): the single-wall contact potential of Sec. 4.5 per unit K_n V_x."""
+    return lib().or_wall_segment_energy(d, Rc)
 
 
 def _loops_arrays(loops):
@@ -309,6 +317,18 @@ class OracleProblem:
                              _ip(self.row_ptr), _ip(self.col), _up(self.broken), _dp(out))
         return dict(KE=out[0], E_bond=out[1], E_contact=out[2], Px=out[3], Py=out[4], Lz=out[5],
                     n_broken=int(out[6]))
+
+    def energies(self, t=None):
+        """Potential energies of the contact laws at the current state (walls at
+        time t, default now): E_contact (inter-grain), E_self (self-contact),
+        E_wall (single-wall segments)."""
+        if t is None:
+            t = self.step * self.prm[P_DT]
+        out = np.zeros(3)
+        lib().or_energies(_dp(self.prm), t, self.N, _dp(self.X), _dp(self.u), _dp(self.V), _ip(self.grain),
+                          _dp(self.g_cw), _dpn(self.g_mat), _ip(self.row_ptr), _ip(self.col), _up(self.broken),
+                          _dp(out))
+        return dict(E_contact=out[0], E_self=out[1], E_wall=out[2])
 
     @property
     def positions(self):

@@ -891,3 +891,109 @@ void or_diagnostics(const double *prm, int N, const double *X, const double *u, 
     }
     out[0] = KE; out[1] = Eb; out[2] = Ec; out[3] = Px; out[4] = Py; out[5] = Lz; out[6] = nbk;
 }
+
+/* Single-wall contact potential, Sec. 4.5: the energy whose negative        */
+/* derivative along the wall normal is the repulsion of eq. (wall-repulsive),*/
+/*   W(d) = int_d^{R_c} K_n V_x |S_l(s)| (R_c - |c_l(s) - p|) ds.            */
+/* With s = R cos(t), |S_l| (R - |c_l - p|) = R^3 g(t) (segment_shape), so    */
+/* W = K_n V_x R^4 J(theta) with J(theta) = int_0^theta g(t) sin(t) dt        */
+/*   = sin th - th cos th - sin^3 th / 3 - th / 4 + sin(2 th)/6 - sin(4 th)/48 */
+/* (int t sin t, int sin^2 t cos t and int sin^4 t written out).  J starts at */
+/* th^7 / 35, so below th = 1 the terms of that closed form cancel; there the */
+/* sum of its Taylor series is used: expanding every term in odd powers,      */
+/*   J = sum_{m>=3} (-1)^m c_m th^(2m+1) / (2m+1)!,                           */
+/*   c_m = 1 - (2m+1) - (3 - 3^(2m+1)) / 12 + 2^(2m+1) / 6 - 4^(2m+1) / 48    */
+/* (the m = 0, 1, 2 coefficients vanish).  Returns R^4 J; the energy is that */
+/* times K_n V_x.  A node past the wall (d < 0) is taken at d = 0, as its     */
+/* force is.                                                                  */
+double or_wall_segment_energy(double d, double Rc)
+{
+    if (!(d < Rc)) return 0.0;
+    if (d < 0.0) d = 0.0;
+    double th = atan2(sqrt((Rc - d) * (Rc + d)), d);
+    double J;
+    if (th < 1.0) {
+        double t2 = th * th;
+        double pw = th * t2 * t2 * t2;                    /* th^7      */
+        double fact = 5040.0;                             /* 7!        */
+        double p2 = 128.0, p3 = 2187.0, p4 = 16384.0;     /* 2^7, 3^7, 4^7 */
+        double sign = -1.0;
+        J = 0.0;
+        for (int m = 3; m <= 22; ++m) {
+            double c = 1.0 - (2.0 * m + 1.0) - (3.0 - p3) / 12.0 + p2 / 6.0 - p4 / 48.0;
+            J += sign * c * pw / fact;
+            pw *= t2;
+            fact *= (2.0 * m + 2.0) * (2.0 * m + 3.0);
+            p2 *= 4.0;
+            p3 *= 9.0;
+            p4 *= 16.0;
+            sign = -sign;
+        }
+    } else {
+        double sn = sin(th), cs = cos(th);
+        J = sn - th * cs - sn * sn * sn / 3.0 - th / 4.0 + sin(2.0 * th) / 6.0 - sin(4.0 * th) / 48.0;
+    }
+    double R2 = Rc * Rc;
+    return R2 * R2 * J;
+}
+
+/* Potential energies of the contact laws at the current state, walls at    */
+/* time t.  out[0] E_contact: inter-grain pairs within R_c, the energy       */
+/* 1/2 K_n V_x V_y (R_c - d)^2 of eq. (law-repulsive); out[1] E_self: pairs   */
+/* of one grain with no intact bond (Sec. 4.4), 1/2 (c_w / R_c) V_x V_y       */
+/* (R_c - d)^2 when |xi| >= R_c and 1/2 (c_w / |xi|) V_x V_y (|xi| - d)^2     */
+/* while d < |xi| < R_c -- the energies of the two self-contact branches;    */
+/* out[2] E_wall: the single-wall potentials K_n V_x W(d_l) of every node and */
+/* wall (corner regions excluded: the corner term of eq. (wall-total) is not  */
+/* the gradient of a potential).  Pairs come from S^nbr (grid search).       */
+void or_energies(const double *prm, double t, int N, const double *X, const double *u, const double *V,
+                 const int *grain, const double *g_cw, const double *g_mat, const int *row_ptr, const int *col,
+                 const unsigned char *broken, double *out)
+{
+    or_sys S;
+    sys_init(&S, prm, N, X, u, NULL, V, grain, g_cw, NULL, NULL, g_mat, row_ptr, col, NULL, NULL);
+    S.t = t;
+    S.use_grid = 1;
+    double Rc = prm[P_RC];
+    double Ec = 0.0, Es = 0.0, Ew = 0.0;
+    for (int k = 0; k < 2 * N; ++k) S.p[k] = X[k] + u[k];
+    int grid = Rc > 0.0 && N > 0;
+    if (grid) build_grid(&S);
+    for (int x = 0; x < N; ++x) {
+        double px = S.p[2 * x], py = S.p[2 * x + 1];
+        int g = grain[x];
+        int nc = grid ? contact_candidates(&S, x, S.cand) : 0;
+        for (int k = 0; k < nc; ++k) {
+            int y = S.cand[k];
+            if (y < x) continue;
+            double dx = S.p[2 * y] - px, dy = S.p[2 * y + 1] - py;
+            double d = sqrt(dx * dx + dy * dy);
+            if (grain[y] != g) {
+                Ec += 0.5 * kn_pair(&S, g, grain[y]) * V[x] * V[y] * (Rc - d) * (Rc - d);
+                continue;
+            }
+            int bonded = 0;
+            for (int b = row_ptr[x]; b < row_ptr[x + 1]; ++b)
+                if (col[b] == y && !broken[b]) bonded = 1;
+            if (bonded) continue;
+            double xix = X[2 * y] - X[2 * x], xiy = X[2 * y + 1] - X[2 * x + 1];
+            double xi = sqrt(xix * xix + xiy * xiy);
+            if (xi < Rc) {
+                if (d < xi) Es += 0.5 * (g_cw[g] / xi) * V[x] * V[y] * (xi - d) * (xi - d);
+            } else {
+                Es += 0.5 * (g_cw[g] / Rc) * V[x] * V[y] * (Rc - d) * (Rc - d);
+            }
+        }
+        /* walls at time t: x_lo, x_hi, y_lo, y_hi */
+        double w[4];
+        for (int l = 0; l < 4; ++l) w[l] = prm[P_WX0 + l] + prm[P_VX0 + l] * t;
+        double dl[4] = {px - w[0], w[1] - px, py - w[2], w[3] - py};
+        double Kn = kn_pair(&S, g, g);
+        for (int l = 0; l < 4; ++l) Ew += Kn * V[x] * or_wall_segment_energy(dl[l], Rc);
+    }
+    if (grid) free_grid(&S);
+    sys_free(&S);
+    out[0] = Ec;
+    out[1] = Es;
+    out[2] = Ew;
+}

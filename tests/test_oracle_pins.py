@@ -669,3 +669,91 @@ def test_one_material_table_equals_single_material_run():
     Fa, _ = a.forces()
     Fb, _ = b.forces()
     assert np.array_equal(Fa, Fb)
+
+
+# ---------------------------------------------------------------------------
+# potential energies of the contact laws (Secs. 4.1, 4.4, 4.5)
+
+
+@pytest.mark.parametrize("frac", [0.0, 0.2, 0.5, 0.5403, 0.55, 0.9, 0.99, 0.9999])
+def test_wall_potential_is_the_integral_of_the_wall_repulsion(frac):
+    """W(d) = int_d^{R_c} |S_l(s)| (R_c - |c_l(s) - p|) ds per unit K_n V_x: the
+    potential whose derivative is the repulsion of eq. (wall-repulsive), by
+    quadrature of the (separately pinned) segment area and centroid."""
+    Rc = 1.0e-4
+    d = frac * Rc
+
+    def force(s):
+        A, c = O.wall_segment(s, Rc)
+        return A * (Rc - c)
+
+    val, _ = quad(force, d, Rc, epsabs=0.0, epsrel=1e-13, limit=200)
+    assert O.wall_segment_energy(d, Rc) == pytest.approx(val, rel=1e-9)
+
+
+@pytest.mark.parametrize("theta", [1e-3, 0.05, 0.3, 0.9, 0.999, 1.001, 1.3, math.pi / 2])
+def test_wall_potential_matches_50_digit_closed_form(theta):
+    """J(theta) = sin th - th cos th - sin^3 th / 3 - th / 4 + sin 2th / 6 - sin 4th / 48
+    evaluated with 50 digits at the angle of the rounded d (R_c = 1): the series
+    below theta = 1 and the closed form above it both keep full precision,
+    including theta -> 0 where J ~ theta^7 / 35 and every closed-form term cancels."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    d = math.cos(theta)
+    th = mp.acos(mp.mpf(d))
+    J = mp.sin(th) - th * mp.cos(th) - mp.sin(th) ** 3 / 3 - th / 4 + mp.sin(2 * th) / 6 - mp.sin(4 * th) / 48
+    assert O.wall_segment_energy(d, 1.0) == pytest.approx(float(J), rel=1e-12)
+    if theta == math.pi / 2:
+        assert O.wall_segment_energy(0.0, 1.0) == pytest.approx(2.0 / 3.0 - math.pi / 8.0, rel=1e-15)
+
+
+def test_self_contact_energy_falls_by_the_work_of_the_self_contact_force():
+    """E_self of a compressed unbonded same-grain pair (both branches) changes by
+    minus the work of the self-contact force along a small separation step."""
+    h, Rc = 1e-4, 0.95e-4
+    Kn = O.contact_stiffness(1e6, 3 * h)
+    for xi, d in ((0.5 * Rc, 0.3 * Rc), (2.0 * Rc, 0.6 * Rc)):
+        P, _ = _self_pair(xi, Rc, Kn, d)
+        e0 = P.energies()["E_self"]
+        F, _ = P.forces()
+        delta = 1e-6 * Rc
+        P.u[1, 0] += delta                      # node 1 moves away along +x
+        e1 = P.energies()["E_self"]
+        work = F[1, 0] * delta                  # force on node 1 along the move
+        assert e0 > 0 and (e0 - e1) == pytest.approx(work, rel=1e-5)
+
+
+def test_energy_is_conserved_for_a_grain_bouncing_on_the_floor():
+    """Sec. 4.3 energy identity with the wall (r_d = 0, mu = 0, no breaking): a
+    disk dropped on the floor under gravity conserves kinetic + bond + wall +
+    gravitational energy to the O(dt^2) error of velocity Verlet, and the wall
+    energy really takes part (it peaks at a sizeable share)."""
+    w = I.two_disks(gy=-5000.0, friction=0.0, damping_ratio=0.0, Gc=1e9, dt=2e-8)
+    h = 1e-3 / 8
+    rc = w.params["rc_ratio"] * h
+    w.grain_shape = w.grain_shape[:1]
+    w.grain_geom = w.grain_geom[:1].copy()
+    low = O.OracleProblem.from_workload(w).positions[:, 1].min()
+    w.grain_geom[0, 1] += 1.02 * rc - low          # lowest nodes 1.02 R_c above the floor
+    w.grain_geom[0, 5] = -1.0
+    P = O.OracleProblem.from_workload(w)
+    P.init_accel()
+    m = P.prm[O.P_RHO] * P.V
+
+    def total():
+        d = P.diagnostics()
+        e = P.energies()
+        grav = -np.sum(m * (P.prm[O.P_GX] * P.positions[:, 0] + P.prm[O.P_GY] * P.positions[:, 1]))
+        return d["KE"] + d["E_bond"] + e["E_wall"] + e["E_self"] + grav, e["E_wall"]
+
+    E0, _ = total()
+    ke0 = P.diagnostics()["KE"]
+    worst, peak = 0.0, 0.0
+    for _ in range(40):
+        P.run(100)
+        Et, ew = total()
+        peak = max(peak, ew)
+        worst = max(worst, abs(Et - E0) / ke0)
+    assert peak > 0.05 * ke0
+    assert worst < 1e-4
+    assert P.v[:, 1].mean() > 0.9                  # it bounced back up
