@@ -22,8 +22,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "peridem_oracle.c")
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "libperidem_oracle.so")
+# the same source built with -fopenmp: the node loop of the force evaluation and
+# the update loops split over the host cores (same arithmetic per node)
+_LIB_OMP = os.path.join(_LIBDIR, "libperidem_oracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 # parameter-vector slots (mirror of the enum in peridem_oracle.c)
 P_RHO, P_KN, P_RC, P_RD, P_MU, P_GX, P_GY, P_DT = range(8)
@@ -35,22 +38,31 @@ SEGMENT_TOL = 1e-10        # closed-domain tolerance of the visibility test, * h
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction, plain -O2)."""
+    """Compile the oracle with gcc (no FMA contraction, plain -O2): the
+    single-threaded library and the all-core (-fopenmp) one."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+    for path, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+            tmp = path + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", *extra,
+                                   "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, path)
     return _LIB
 
 
-def lib():
-    global _lib
+def threads_available() -> int:
+    """Host threads the all-core build uses (OMP_NUM_THREADS, else the cores)."""
+    env = os.environ.get("OMP_NUM_THREADS")
+    if env and env.isdigit():
+        return int(env)
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def lib(omp: bool = False):
     with _lock:
-        if _lib is None:
+        if omp not in _libs:
             build()
-            L = ctypes.CDLL(_LIB)
+            L = ctypes.CDLL(_LIB_OMP if omp else _LIB)
             dp = ctypes.POINTER(ctypes.c_double)
             ip = ctypes.POINTER(ctypes.c_int)
             up = ctypes.POINTER(ctypes.c_ubyte)
@@ -75,8 +87,8 @@ def lib():
             L.or_wall_segment_energy.argtypes = [c_d, c_d]
             L.or_wall_segment_energy.restype = c_d
             L.or_energies.argtypes = [dp, c_d, c_i, dp, dp, dp, ip, dp, dp, ip, ip, up, dp]
-            _lib = L
-    return _lib
+            _libs[omp] = L
+    return _libs[omp]
 
 
 def _p(a, ct):
@@ -201,6 +213,8 @@ class OracleProblem:
     g_mat (G,2) per-grain (density, bulk modulus) or None (one material: prm).
     """
 
+    omp = False     # True: time steps and force evaluations run in the all-core build
+
     def __init__(self, X, V, grain, row_ptr, col, g_cw, g_s0, g_eps, prm, v0=None, g_mat=None):
         self.X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 2)
         self.N = self.X.shape[0]
@@ -278,7 +292,7 @@ class OracleProblem:
 
     def init_accel(self):
         """a^0 from the forces of the initial state (first line of Algorithm 1)."""
-        L = lib()
+        L = lib(self.omp)
         L.or_init_accel(_dp(self.prm), self.step * self.prm[P_DT], self.N, _dp(self.X), _dp(self.u),
                         _dp(self.v), _dp(self.a), _dp(self.V), _ip(self.grain), _dp(self.g_cw),
                         _dp(self.g_s0), _dp(self.g_eps), _dpn(self.g_mat), _ip(self.row_ptr), _ip(self.col),
@@ -287,7 +301,7 @@ class OracleProblem:
 
     def run(self, n_steps: int, want_parts: bool = False):
         """Advance n_steps; returns (F_last, parts_last) of the final step."""
-        L = lib()
+        L = lib(self.omp)
         F = np.zeros((self.N, 2))
         parts = np.zeros((4, self.N, 2)) if want_parts else None
         L.or_run(_dp(self.prm), self.step, n_steps, self.N, _dp(self.X), _dp(self.u), _dp(self.v),
@@ -299,7 +313,7 @@ class OracleProblem:
 
     def forces(self, t=None, keep_broken=True):
         """Force evaluation at the current state; returns (F, parts[4,N,2])."""
-        L = lib()
+        L = lib(self.omp)
         if t is None:
             t = self.step * self.prm[P_DT]
         F = np.zeros((self.N, 2))

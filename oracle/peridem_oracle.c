@@ -569,6 +569,7 @@ static void wall_terms(const or_sys *S, int x, double single[4][2], double corne
     d[3] = wpos[3] - py; ex[3] = 0.0;  ey[3] = 1.0;
     for (int l = 0; l < 4; ++l) {
         if (d[l] < 0.0) {
+#pragma omp atomic
             S->status[ST_PENETRATION]++;
             d[l] = 0.0;
         }
@@ -630,7 +631,7 @@ static void wall_force(const or_sys *S, int x, double *fx, double *fy)
 
 /* Force on node x from all its interactions (eq:full, Algorithm 1 lines for  */
 /* f^peri, f^self, f^nbr, f^wall).  parts (nullable) receives the four parts.  */
-static void node_force(or_sys *S, int x, double *Fx_out, double *Fy_out, double *parts)
+static void node_force(or_sys *S, int x, int *cand, double *Fx_out, double *Fy_out, double *parts)
 {
     const double *prm = S->prm;
     double Rc = prm[P_RC];
@@ -663,13 +664,14 @@ static void node_force(or_sys *S, int x, double *Fx_out, double *Fy_out, double 
     }
 
     /* contact candidates S^nbr (all grains, ascending index) */
-    int nc = contact_candidates(S, x, S->cand);
+    int nc = contact_candidates(S, x, cand);
     double Fsx = 0.0, Fsy = 0.0, Fnx = 0.0, Fny = 0.0;
     for (int k = 0; k < nc; ++k) {
-        int y = S->cand[k];
+        int y = cand[k];
         double dx = S->p[2 * y] - px, dy = S->p[2 * y + 1] - py;
         double d = sqrt(dx * dx + dy * dy);
         if (d == 0.0) {
+#pragma omp atomic
             S->status[ST_COINCIDENT]++;
             continue;
         }
@@ -744,10 +746,21 @@ static void sys_free(or_sys *S)
 
 static void all_forces(or_sys *S, double *F, double *parts)
 {
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < 2 * S->N; ++k) S->p[k] = S->X[k] + S->u[k];
     int grid = S->use_grid && S->prm[P_RC] > 0.0 && S->N > 0;
     if (grid) build_grid(S);
-    for (int x = 0; x < S->N; ++x) node_force(S, x, &F[2 * x], &F[2 * x + 1], parts);
+    /* Nodes are independent: each writes only its own force and the broken  */
+    /* flags of its own bonds.  The all-core build (-fopenmp) splits them     */
+    /* over threads, each with its own candidate scratch; the arithmetic of   */
+    /* every node is the same as in the single-threaded build.                */
+#pragma omp parallel
+    {
+        int *cand = (int *)malloc(sizeof(int) * (size_t)S->max_cand);
+#pragma omp for schedule(static)
+        for (int x = 0; x < S->N; ++x) node_force(S, x, cand, &F[2 * x], &F[2 * x + 1], parts);
+        free(cand);
+    }
     if (grid) free_grid(S);
 }
 
@@ -809,10 +822,12 @@ void or_run(const double *prm, long step0, int n_steps, int N, const double *X, 
     for (int n = 0; n < n_steps; ++n) {
         long step = step0 + n;
         /* displacement update, current position (Algorithm 1) */
+#pragma omp parallel for schedule(static)
         for (int k = 0; k < 2 * N; ++k) u[k] = (u[k] + dt * v[k]) + half_dt2 * a[k];
         S.t = (double)(step + 1) * dt;
         all_forces(&S, F, (n == n_steps - 1) ? parts_last : NULL);
         /* acceleration and velocity update (Algorithm 1) */
+#pragma omp parallel for schedule(static)
         for (int x = 0; x < N; ++x) {
             double m = rho_of(&S, grain[x]) * V[x];
             double ax = F[2 * x] / m + gx, ay = F[2 * x + 1] / m + gy;
@@ -820,7 +835,10 @@ void or_run(const double *prm, long step0, int n_steps, int N, const double *X, 
             v[2 * x + 1] = v[2 * x + 1] + half_dt * (a[2 * x + 1] + ay);
             a[2 * x] = ax;
             a[2 * x + 1] = ay;
-            if (!isfinite(ax) || !isfinite(ay)) status[ST_NONFINITE]++;
+            if (!isfinite(ax) || !isfinite(ay)) {
+#pragma omp atomic
+                status[ST_NONFINITE]++;
+            }
         }
     }
     if (F_last) memcpy(F_last, F, sizeof(double) * (size_t)(2 * N));

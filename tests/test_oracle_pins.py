@@ -757,3 +757,19 @@ def test_energy_is_conserved_for_a_grain_bouncing_on_the_floor():
     assert peak > 0.05 * ke0
     assert worst < 1e-4
     assert P.v[:, 1].mean() > 0.9                  # it bounced back up
+
+
+def test_all_core_build_is_bitwise_the_single_threaded_one():
+    """The OpenMP build of the oracle splits the node loop over host threads and
+    changes no arithmetic: a fracturing, contacting run is bitwise identical."""
+    a = _colliding_disks(mu=0.5, rd=0.8, Gc=0.5, v=6.0)
+    b = _colliding_disks(mu=0.5, rd=0.8, Gc=0.5, v=6.0)
+    b.omp = True
+    a.init_accel()
+    b.init_accel()
+    Fa, pa = a.run(1500, want_parts=True)
+    Fb, pb = b.run(1500, want_parts=True)
+    assert a.broken.sum() > 0
+    assert np.array_equal(a.u, b.u) and np.array_equal(a.v, b.v) and np.array_equal(Fa, Fb)
+    assert np.array_equal(pa, pb) and np.array_equal(a.broken, b.broken)
+    assert np.array_equal(a.status, b.status)
