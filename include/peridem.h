@@ -123,7 +123,14 @@ typedef struct pd_params {
 #define PD_DIAG_PY 3            /* linear momentum y                                 */
 #define PD_DIAG_LZ 4            /* angular momentum about the origin                 */
 #define PD_DIAG_NBROKEN 5       /* number of broken directed bonds                   */
-/* slots 6, 7 reserved (0) */
+#define PD_DIAG_ECONTACT 6      /* contact potential: 1/2 K_n V_x V_y (R_c - d)^2 over  */
+                                /* pairs of grains within R_c (eq:law-repulsive) plus  */
+                                /* the self-contact springs of unbonded nodes of one   */
+                                /* grain (Sec. 4.4: stiffness c_w / R_c about R_c, or  */
+                                /* c_w / |xi| about |xi| when |xi| < R_c)               */
+#define PD_DIAG_EWALL 7         /* single-wall potential: sum over nodes and walls of  */
+                                /* K_n V_x int_d^{R_c} |S_l| (R_c - |c_l - p|) ds       */
+                                /* (Sec. 4.5); corner regions carry none               */
 #define PD_DIAG_COUNT 8
 
 typedef struct pd_ctx pd_ctx;
@@ -234,7 +241,12 @@ int pd_set_state(pd_ctx *ctx, int field, const void *src, size_t bytes, int src_
 int pd_eval_forces(pd_ctx *ctx);
 
 /* Reductions of the current state into out[PD_DIAG_COUNT] (waits for the
- * stream).  Errors: PD_ESTATE, PD_ECUDA. */
+ * stream).  The kinetic energy, momenta and the bond, contact and wall
+ * potentials give the energy balance of Sec. 4.3 (with r_d = mu = 0 and no
+ * breaking, KE + E_bond + E_contact + E_wall minus the work of the body force
+ * is conserved away from wall corners).  The contact candidate lists are
+ * rebuilt for the current state first (counted in
+ * status[PD_STATUS_REBUILDS]).  Errors: PD_ESTATE, PD_ECUDA. */
 int pd_diagnostics(pd_ctx *ctx, double *out);
 
 /* Copy the device status word into out[PD_STATUS_COUNT] (waits) and return
@@ -449,7 +461,9 @@ int pd_observables(pd_ctx *ctx, double *out_host);
  *   g_cw, g_eps  device double[G] per-grain c_w and horizon
  *   rho, micromodulus as in pd_params (one density for every node: with
  *             per-grain materials, pd_diagnostics weighs each node by its own)
- *   out       device double[PD_DIAG_COUNT] (same slots as pd_diagnostics)
+ *   out       device double[PD_DIAG_COUNT] (same slots as pd_diagnostics;
+ *             PD_DIAG_ECONTACT and PD_DIAG_EWALL, which need the context's
+ *             contact lists and walls, are written as 0)
  *   cuda_stream  the stream the work is enqueued on (returns without waiting)
  * The first call on a device, with that device current, looks up the device
  * address of the scratch array; make that first call before any stream

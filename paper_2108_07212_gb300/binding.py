@@ -25,7 +25,7 @@ FIELDS = dict(X=0, DISP=1, VEL=2, ACC=3, POS=4, FORCE=5, FORCE_PARTS=6, BROKEN=7
 STATUS_COUNT = 8
 STATUS_REBUILDS = 5          # slot of the candidate-list rebuild counter (not an error)
 DIAG_COUNT = 8
-DIAG_NAMES = ("KE", "E_bond", "Px", "Py", "Lz", "n_broken")
+DIAG_NAMES = ("KE", "E_bond", "Px", "Py", "Lz", "n_broken", "E_contact", "E_wall")
 
 # public C-ABI symbols (checked by the test-suite against include/peridem.h)
 SYMBOLS = ("pd_last_error", "pd_create", "pd_destroy", "pd_mesh_grains", "pd_build_bonds", "pd_arena_bytes",

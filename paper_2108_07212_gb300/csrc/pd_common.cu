@@ -179,8 +179,55 @@ __global__ void __launch_bounds__(kBlock) k_positions(DevPtrs d, KParams k) {
     d.p[i] = make_double2(X.x + u.x, X.y + u.y);
 }
 
+// Single-wall contact potential (Sec. 4.5): the energy whose derivative along
+// the wall normal is minus the repulsion K_n V_x |S_l| (R_c - |c_l - p|) of
+// eq. (wall-repulsive).  With the segment half-angle theta (d = R_c cos theta),
+// |S_l| (R_c - |c_l - p|) = R_c^3 g(theta) and the potential is
+// K_n V_x R_c^4 J(theta), J = int_0^theta g(t) sin t dt
+//   = sin th - th cos th - sin^3 th / 3 - th / 4 + sin(2 th) / 6 - sin(4 th) / 48.
+// J starts at th^7 / 35 and those terms cancel below th = 1; there J is
+// summed from its Taylor series, J / th^7 = sum_{m>=3} C_m th^(2m-6) with
+// C_m = (-1)^m c_m / (2m+1)!, c_m = 1 - (2m+1) - (3 - 3^(2m+1)) / 12
+// + 2^(2m+1) / 6 - 4^(2m+1) / 48, coefficients evaluated at compile time.
+__host__ __device__ constexpr double wall_energy_coef(int m) {
+    double p2 = 2.0, p3 = 3.0, p4 = 4.0, fact = 1.0;
+    for (int q = 1; q <= m; ++q) {
+        p2 *= 4.0;
+        p3 *= 9.0;
+        p4 *= 16.0;
+    }
+    for (int q = 2; q <= 2 * m + 1; ++q) fact *= (double)q;
+    const double c = 1.0 - (2.0 * m + 1.0) - (3.0 - p3) / 12.0 + p2 / 6.0 - p4 / 48.0;
+    return ((m & 1) ? -c : c) / fact;
+}
+template <int M, int MMAX>
+__device__ __forceinline__ double wall_energy_horner(double t2) {
+    constexpr double c = wall_energy_coef(M);
+    if constexpr (M == MMAX) return c;
+    else return fma(wall_energy_horner<M + 1, MMAX>(t2), t2, c);
+}
+// R^4 J(theta) of a node at distance d from a wall (d < 0: taken at 0, as the force).
+__device__ __forceinline__ double wall_energy_r4j(double d, double R) {
+    if (!(d < R)) return 0.0;
+    d = fmax(d, 0.0);
+    const double th = atan2(sqrt((R - d) * (R + d)), d);
+    double J;
+    if (th < 1.0) {
+        const double t2 = th * th;
+        J = (th * t2 * t2 * t2) * wall_energy_horner<3, 22>(t2);
+    } else {
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        J = sn - th * cs - sn * sn * sn / 3.0 - th / 4.0 + sin(2.0 * th) / 6.0 - sin(4.0 * th) / 48.0;
+    }
+    const double R2 = R * R;
+    return R2 * R2 * J;
+}
+
 // Diagnostics: per-block partial sums (grid-stride, fixed order), then one
 // block adds the partials in block order -- deterministic for a given grid.
+// The contact potentials walk the candidate lists, which must be current (the
+// caller rebuilds them first).
 __global__ void __launch_bounds__(kBlock) k_diag_partial(DevPtrs d, KParams k, int vcur) {
     double acc[PD_DIAG_COUNT];
 #pragma unroll
@@ -211,6 +258,49 @@ __global__ void __launch_bounds__(kBlock) k_diag_partial(DevPtrs d, KParams k, i
             double s = (L - xi) / xi;
             double c = k.micro ? cw * (1.0 - xi / eps) : cw;
             acc[PD_DIAG_EBOND] += 0.25 * c * s * s * xi * d.V[x] * d.V[y];
+        }
+        // contact potentials (Secs. 4.1, 4.4): 1/2 K_n V_x V_y (R_c - d)^2 between
+        // grains; between unbonded nodes of one grain 1/2 (c_w / R_c) V_x V_y
+        // (R_c - d)^2 for |xi| >= R_c and 1/2 (c_w / |xi|) V_x V_y (|xi| - d)^2
+        // while d < |xi| < R_c.  Every pair is met from both of its nodes: each
+        // adds half.
+        const int ag = d.g_agg[g];
+        const AggParams &A = d.agg[ag];
+        const double Rc = A.Rc, Vx = d.V[x];
+        const int nc = d.nbr_cnt[x];
+        for (int q = 0; q < nc; ++q) {
+            const int y = d.nbr[(size_t)q * k.N + x];
+            const double2 Xy = d.X[y], uy = d.u[y];
+            const double dx = (Xy.x + uy.x) - px, dy = (Xy.y + uy.y) - py;
+            const double dd = sqrt(dx * dx + dy * dy);
+            if (!(dd < Rc)) continue;
+            const int gy = d.grain[y];
+            if (gy != g) {
+                const double Kn = k.mat ? 18.0 * harmonic64(d.g_k[g], d.g_k[gy]) / A.pe5 : A.Kn;
+                acc[PD_DIAG_ECONTACT] += 0.25 * Kn * Vx * d.V[y] * (Rc - dd) * (Rc - dd);
+                continue;
+            }
+            if (bonded_intact(d, k, x, r0, r1, y)) continue;
+            const double xix = Xy.x - X.x, xiy = Xy.y - X.y;
+            const double xi = sqrt(xix * xix + xiy * xiy);
+            if (xi < Rc) {
+                if (dd < xi) acc[PD_DIAG_ECONTACT] += 0.25 * (cw / xi) * Vx * d.V[y] * (xi - dd) * (xi - dd);
+            } else {
+                acc[PD_DIAG_ECONTACT] += 0.25 * (cw / Rc) * Vx * d.V[y] * (Rc - dd) * (Rc - dd);
+            }
+        }
+        // single-wall potentials (Sec. 4.5) with the walls at the current time;
+        // corner regions carry none (their term of eq. wall-total is not the
+        // gradient of a potential)
+        if (!far_from_walls<false>(d, x, ag)) {
+            const double t = *d.t_now;
+            const double Kn = k.mat ? 18.0 * d.g_k[g] / A.pe5 : A.Kn;
+            const double dl[4] = {px - (A.w0[0] + A.wv[0] * t), (A.w0[1] + A.wv[1] * t) - px,
+                                  py - (A.w0[2] + A.wv[2] * t), (A.w0[3] + A.wv[3] * t) - py};
+            double e = 0.0;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) e += wall_energy_r4j(dl[l], Rc);
+            acc[PD_DIAG_EWALL] += Kn * Vx * e;
         }
     }
     __shared__ double sm[PD_DIAG_COUNT][kBlock];
@@ -337,6 +427,12 @@ cudaError_t launch_observables(const DevPtrs &d, const KParams &k, int vcur, dou
 }
 
 cudaError_t launch_diagnostics(const DevPtrs &d, const KParams &k, int vcur, cudaStream_t s) {
+    // positions, cells and candidate lists of the current state (no advance, forced rebuild)
+    cudaError_t e = launch_predict(d, k, vcur, 0, s, 0, 0);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_positions(d, k, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(d.rebuild, 1, sizeof(int), s)) != cudaSuccess) return e;
+    if ((e = launch_rebuild(d, k, s)) != cudaSuccess) return e;
     k_diag_partial<<<k.n_diag_blocks, kBlock, 0, s>>>(d, k, vcur);
     k_diag_final<<<1, 32, 0, s>>>(d, k.n_diag_blocks);
     return cudaGetLastError();

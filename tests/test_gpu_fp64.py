@@ -207,6 +207,10 @@ def test_diagnostics_match_oracle():
     o = P.diagnostics()
     for k in ("KE", "E_bond"):
         assert d[k] == pytest.approx(o[k], rel=1e-9), k
+    e = P.energies()
+    assert e["E_contact"] > 0
+    assert d["E_contact"] == pytest.approx(e["E_contact"] + e["E_self"], rel=1e-9)
+    assert d["E_wall"] == pytest.approx(e["E_wall"], rel=1e-9, abs=1e-30)
     m = P.prm[O.P_RHO] * P.V
     pscale = np.sum(m * np.abs(P.v).sum(axis=1))
     lscale = pscale * np.abs(P.positions).max()

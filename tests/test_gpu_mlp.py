@@ -11,6 +11,24 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
+# Element-wise tolerance of the BF16 network against the reference with the
+# same bfloat16 rounding.  Both round every operand to BF16 at the same places;
+# they differ in accumulation (FP32 on the tensor cores, FP64 here) and in the
+# float erf of the GELU.  Those differences are ~1e-6 relative, but one of them
+# can move a hidden activation across a BF16 rounding boundary: that changes it
+# by one BF16 unit (2^-8 relative), and the change reaches an output through one
+# weight.  So an output may differ by a few 2^-8 of the output scale, never by
+# more: |y - y_ref| <= TOL (max|y_ref| + |y_ref|) with TOL = 2^-6 (four units).
+TOL = 2.0 ** -6
+
+
+def _elementwise_ok(a, b, tol=TOL):
+    """|a - b| <= tol (max|b| + |b|) for every element; returns the worst ratio."""
+    bound = tol * (np.abs(b).max() + np.abs(b))
+    ratio = np.abs(a - b) / np.maximum(bound, 1e-300)
+    return float(ratio.max())
+
+
 def _data(n, seed=0):
     rng = np.random.default_rng(seed)
     x = rng.normal(size=(n, 32)).astype(np.float32)
@@ -26,10 +44,13 @@ def test_forward_matches_reference(n):
     net = B.MLP(max_batch=512, params=params)
     y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
     y_ref, _ = M.forward(params.astype(np.float64), x, bf16=True)
-    err = np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref)
-    assert err < 2e-3, err
+    worst = _elementwise_ok(y, y_ref)
+    assert worst <= 1.0, worst
+    # against the unrounded FP64 network: BF16 weights and activations (8-bit
+    # mantissas, 2^-9 relative each) over three layers, element-wise
     y64, _ = M.forward(params.astype(np.float64), x)
-    assert np.linalg.norm(y - y64) / np.linalg.norm(y64) < 3e-2
+    worst64 = _elementwise_ok(y, y64, tol=2.0 ** -4)
+    assert worst64 <= 1.0, worst64
 
 
 @pytest.mark.parametrize("n", [200, 1024])
@@ -44,7 +65,10 @@ def test_gradients_match_reference(n):
     for name, shape in M.SIZES:
         k = int(np.prod(shape))
         a, b = g[off:off + k], g_ref[off:off + k]
-        assert np.linalg.norm(a - b) <= 5e-3 * np.linalg.norm(b) + 1e-12, name
+        # element-wise, block by block: the backward signals are BF16-rounded as
+        # in the forward pass, and each gradient entry sums n products of them
+        worst = _elementwise_ok(a, b)
+        assert worst <= 1.0, (name, worst)
         off += k
 
 
