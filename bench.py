@@ -1,15 +1,19 @@
 """Benchmark of the PeriDEM time step on GB300.
 
-Default workload: the 50-grain mixed-shape settling aggregate (radii U[1, 1.5] mm,
-h = R/15, dt = 5e-8 s, 20x30 mm wall box, seed 1).  One "step" is one full
-velocity-Verlet time step of Algorithm 1 over all nodes (displacement update,
-contact binning, bond + contact + self-contact + wall forces, velocity update).
+Default workload: the batched ensemble of 64 independent settling aggregates
+(20-200 grains each, seed 11; 6.69M nodes, 145M directed bonds) advanced in one
+context, FP32-split precision, on the step path its autotuner picks.  One
+"step" is one full velocity-Verlet time step of Algorithm 1 over all nodes of
+all aggregates (displacement update, contact-list rebuild when due, bond +
+contact + self-contact + wall forces, velocity update).  The plain FP64 path is
+timed on the same state beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32]
+                  [--workload ensemble64|compaction500|settling50|...] [--legs ...]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 
 Prints one JSON line (rank 0).  Under torchrun every rank runs its own seeded
-aggregate (independent problems, no collective on the data path): weak scaling.
+ensemble (independent problems, no collective on the data path): weak scaling.
 """
 from __future__ import annotations
 
@@ -29,7 +33,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "node-steps/s and bond evals/s vs plain FP64 GPU path at stated error; % HBM peak"
-FLOPS_PER_BOND = 17      # algorithmic FP64 ops of one bond evaluation (sqrt, div counted once)
+# algorithmic bytes of the plain FP64 force phase: per node the FP64 position p,
+# v and a read (48 B), v and a written (32 B), volume (8 B), grain, row pointer,
+# broken-bond word and contact-list length (16 B), hash-grid cell (8 B); per
+# directed bond the column and the FP64 reference length (12 B)
+BYTES_PER_NODE_FP64 = 112
+BYTES_PER_BOND_FP64 = 12
+# GB300 FP64 pipe: 2 lanes per SM per cycle on 152 SMs; a warp instruction on
+# the FP64 pipe occupies it for 32 / 2 = 16 SM cycles whatever its active lanes
+FP64_LANES_PER_SM_CYCLE = 2
+N_SM = 152
 # algorithmic bytes of the FP32-split force phase: per node the float-float position pq (16 B),
 # grain, row pointer, broken-bond word and contact-list length (16 B), hash-grid cell for the wall
 # test (8 B), FP64 v and a read and written (64 B); per bond the column (4 B)
@@ -52,12 +65,16 @@ WORKLOADS = {
                                      "direction (collisions and fracture; contact lists rebuilt every few steps)"),
 }
 WORKLOAD_ARGS = {"agitated500": {"agitation": 5.0}}
+# untimed steps before the timed window of each workload (the window starts
+# mid-run, where grains move and collide and the contact lists are rebuilt)
+DEFAULT_ADVANCE = {"settling50": 10000, "ensemble64": 2000, "compaction500": 200, "surrogate2000": 1000,
+                   "agitated500": 200}
 
 
 def workload_for(rank: int, args):
     """Rank r runs its own seeded aggregate (default seed + r): independent problems."""
     from paper_2108_07212_gb300 import inputs as I
-    name = getattr(args, "workload", None) or "settling50"
+    name = getattr(args, "workload", None) or "ensemble64"
     gen, seed, _ = WORKLOADS[name]
     if gen == "settling":
         return I.settling(n_grains=50, seed=seed + rank)
@@ -76,7 +93,7 @@ def max_over_ranks(dist, values, device):
 
 
 def describe(w, sim=None, args=None):
-    name = getattr(args, "workload", None) or "settling50"
+    name = getattr(args, "workload", None) or "ensemble64"
     d = {"workload": WORKLOADS[name][2], "name": name}
     if sim is not None:
         d.update(nodes=int(sim.N), directed_bonds=int(sim.n_bonds))
@@ -148,63 +165,84 @@ def measured_peaks():
         return {}
 
 
-def fp64_gemm_peak(torch, device):
-    """Measured FP64 rate of a cuBLAS DGEMM (TFLOP/s): the FP64 denominator."""
-    n = 4096
-    a = torch.randn(n, n, dtype=torch.float64, device=device)
-    b = torch.randn(n, n, dtype=torch.float64, device=device)
-    for _ in range(2):
-        torch.mm(a, b)
-    torch.cuda.synchronize()
-    best = math.inf
-    for _ in range(5):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        torch.mm(a, b)
-        e1.record()
-        torch.cuda.synchronize()
-        best = min(best, e0.elapsed_time(e1) / 1e3)
-    del a, b
-    return 2.0 * n ** 3 / best / 1e12
-
-
-def cpu_baseline(w, budget_s: float = 12.0):
-    """The FP64 CPU oracle, as it stands, on a bounded sample of the same workload."""
+def oracle_sample(w, min_nodes: int):
+    """Oracle problems of a bounded sample of the workload: for a batched ensemble
+    its first aggregates (each an independent problem with its own walls) until
+    they hold min_nodes nodes; otherwise the whole workload."""
     from oracle import oracle as O
-    P = O.OracleProblem.from_workload(w).init_accel()
+    parts = getattr(w, "parts", None)
+    if parts is None:
+        return [O.OracleProblem.from_workload(w)], "the whole workload"
+    probs, n = [], 0
+    for p in parts:
+        probs.append(O.OracleProblem.from_workload(p))
+        n += probs[-1].N
+        if n >= min_nodes:
+            break
+    return probs, f"its first {len(probs)} of {len(parts)} aggregates ({n} nodes)"
+
+
+def _time_oracle(probs, omp: bool, n_steps: int) -> float:
+    for P in probs:
+        P.omp = omp
     t0 = time.perf_counter()
-    P.run(5)
-    per = (time.perf_counter() - t0) / 5
-    n = max(5, int(budget_s / max(per, 1e-6)))
-    t0 = time.perf_counter()
-    P.run(n)
-    dt = time.perf_counter() - t0
-    return {"value": P.N * n / dt, "unit": "node-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} time steps of the full {P.N}-node workload from t=0 (single-threaded C, FP64)"}
+    for P in probs:
+        P.run(n_steps)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(w, budget_s: float = 20.0, min_nodes: int = 200_000):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the same
+    workload: the single-threaded build and the all-core (OpenMP) build, each
+    for about half the budget, from t = 0."""
+    from oracle import oracle as O
+    probs, what = oracle_sample(w, min_nodes)
+    for P in probs:
+        P.init_accel()
+    n_nodes = sum(P.N for P in probs)
+    per = _time_oracle(probs, False, 2) / 2
+    n1 = max(3, int(0.5 * budget_s / max(per, 1e-6)))
+    dt1 = _time_oracle(probs, False, n1)
+    per = _time_oracle(probs, True, 2) / 2
+    n2 = max(3, int(0.5 * budget_s / max(per, 1e-6)))
+    dt2 = _time_oracle(probs, True, n2)
+    cores = O.threads_available()
+    return {"value": n_nodes * n2 / dt2, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{what}: {n2} time steps with the all-core build (OpenMP, {cores} threads), FP64 C",
+            "single_thread": {"value": n_nodes * n1 / dt1, "unit": "node-steps/s", "cores": 1,
+                              "sample": f"{what}: {n1} time steps, single-threaded build"}}
 
 
 # ---------------------------------------------------------------------------
 
 
 def run_reference(args):
+    """The oracle as the reference arm: the all-core build on a bounded sample of
+    the main line's workload (for the ensemble: its first aggregates, about 1M
+    nodes), W untimed and K timed steps."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     from oracle import oracle as O
     w = workload_for(0, args)
-    P = O.OracleProblem.from_workload(w).init_accel()
-    for _ in range(args.warmup):
-        P.run(1)
-    t0 = time.perf_counter()
-    P.run(args.steps)
-    dt = time.perf_counter() - t0
-    value = P.N * args.steps / dt
+    probs, what = oracle_sample(w, 1_000_000)
+    for P in probs:
+        P.omp = True
+        P.init_accel()
+    _time_oracle(probs, True, args.warmup)
+    dt = _time_oracle(probs, True, args.steps)
+    n_nodes = sum(P.N for P in probs)
+    n_bonds = sum(len(P.col) for P in probs)
+    value = n_nodes * args.steps / dt
+    cores = O.threads_available()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "node-steps/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": describe(w, None, args) | {"nodes": int(P.N), "directed_bonds": int(len(P.col))},
-            "cpu_baseline": {"value": value, "unit": "node-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} time steps after {args.warmup} warm-up steps"},
+            "config": describe(w, None, args) | {"sample": what, "sample_nodes": int(n_nodes),
+                                                 "sample_directed_bonds": int(n_bonds)},
+            "cpu_baseline": {"value": value, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{what}: {args.steps} time steps after {args.warmup} warm-up steps, "
+                                       f"all-core build (OpenMP, {cores} threads)"},
             "e2e": {"value": value, "unit": "node-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -246,35 +284,6 @@ def _timed_steps(sim, stream, flush, steps, warmup, torch):
     return step_ms, force_ms, rebuilds
 
 
-def precision_report(B, dev, stream, torch):
-    """FP32-split vs FP64 on a loaded state of the same aggregate (thrown at the
-    floor at 5 m/s): per-step force error from the same state, and broken-bond
-    disagreements after 300 steps of each path."""
-    w = workload_for(0, None)
-    probe = B.Simulation(w, precision=B.PD_FP64, device=dev, stream=stream)
-    X = probe.get("X")
-    rc = probe.info()["Rc"]
-    w.grain_geom[:, 1] -= X[:, 1].min() - 1.2 * rc
-    w.grain_geom[:, 5] = -5.0
-    del probe
-    a = B.Simulation(w, precision=B.PD_FP64, store_parts=True, device=dev, stream=stream)
-    b = B.Simulation(w, precision=B.PD_FP32_SPLIT, store_parts=True, device=dev, stream=stream)
-    a.step(300)
-    b.step(300)
-    n_dis = int(np.sum(a.get("BROKEN") != b.get("BROKEN")))
-    n_broken = int(a.get("BROKEN").sum())
-    for f in ("DISP", "VEL", "ACC", "BROKEN", "STEP"):
-        b.set(f, a.get(f))
-    a.eval_forces()
-    b.eval_forces()
-    Fa, Fb = a.get("FORCE"), b.get("FORCE")
-    err = float(np.abs(Fb - Fa).max() / np.abs(Fa).max())
-    return {"workload": "the bench aggregate thrown at the floor (5 m/s), state after 300 steps",
-            "force_rel_err_max_norm": err, "broken_bonds_fp64": n_broken,
-            "break_disagreements_after_300_steps": n_dis,
-            "reference": "FP64 GPU path (matches the FP64 oracle to 1e-12 in the test-suite)"}
-
-
 # ---------------------------------------------------------------------------
 # workload legs at the sizes where HBM, not launch latency, bounds the step
 # (500-grain compaction, 64-aggregate ensemble, 2000-grain surrogate settling)
@@ -286,19 +295,16 @@ def precision_report(B, dev, stream, torch):
 BYTES_PER_NODE_STEP_FP32 = 216
 
 
-# DRAM bytes (read + write) per launch of the step kernels on the settling50
-# workload, from one ncu capture of the timed steps (the bench marks them with
-# cudaProfilerStart/Stop):
+# DRAM bytes (read + write) per launch of the force-phase kernels, per workload,
+# from one ncu capture of the timed steps (the bench marks them with
+# cudaProfilerStart/Stop), e.g.
 #   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
-#       --profile-from-start off -c 2000 --csv python bench.py --steps 50 --warmup 3 --legs= --no-cpu
-# (L2 flushed before every step as in the bench; medians over the launches;
-# profiles/traffic_settling50.md).  They hold while the kernel sources hash to
-# TRAFFIC_DIGEST; otherwise, or for a variant not captured, traffic is null.
-TRAFFIC_SETTLING50 = {
-    "k_persistent<1, 4, 128>": 4047104,
-    "k_persistent<0, 4, 128>": 7392896,
-}
-TRAFFIC_DIGEST = "57574a31de53c30ff2fcef15b2260e980ca3a15b"
+#       --profile-from-start off -k regex:k_sums -c 3 --csv python bench.py --steps 3 --warmup 3 --legs= --no-cpu
+# (medians over the captured launches; the summaries are committed under
+# profiles/).  They hold while the kernel sources hash to TRAFFIC_DIGEST;
+# otherwise, or for a kernel not captured, traffic is null.
+TRAFFIC = {}
+TRAFFIC_DIGEST = ""
 TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu", "pd_common.cu", "pd_internal.h")
 
 
@@ -315,16 +321,17 @@ def kernel_digest() -> str:
 
 def force_phase_traffic(path: dict, fp32: bool, workload: str):
     """Measured DRAM bytes of one force phase of the chosen path, or None."""
-    if workload != "settling50" or not TRAFFIC_SETTLING50 or kernel_digest() != TRAFFIC_DIGEST:
+    table = TRAFFIC.get(workload, {})
+    if not table or kernel_digest() != TRAFFIC_DIGEST:
         return None
     p, m, l = ("1" if fp32 else "0"), path["mode"], path["lanes"]
     if m & 1:
         names = [f"k_persistent<{p}, {l}, {path.get('block', 128)}>"]     # the whole step
     else:
         names = [f"k_sums<{p}, {l}>", f"k_epilogue<{p}>"] if (m >> 1) & 1 else [f"k_force<{p}, {l}>"]
-    if not all(n in TRAFFIC_SETTLING50 for n in names):
+    if not all(n in table for n in names):
         return None
-    return float(sum(TRAFFIC_SETTLING50[n] for n in names))
+    return float(sum(table[n] for n in names))
 
 
 def _force_kernels(mode: int, fp32: bool) -> str:
@@ -375,15 +382,42 @@ def _roof_fp32(sim, f_ms, hbm, label):
                                      f"{sim.N} nodes / {sim.n_bonds} bonds, median event time {f_ms * 1e3:.1f} us (of measured)"}
 
 
-def _roof_fp64(sim, f_ms, fp64_peak, label):
-    a = FLOPS_PER_BOND * sim.n_bonds / (f_ms / 1e3) / 1e12
-    return {"bound": "alu", "kernel": "k_force64", "achieved": a, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": a / fp64_peak, "traffic": None,
-            "note": f"{label}: {FLOPS_PER_BOND} FP64 ops/bond x {sim.n_bonds} bonds, median event time "
-                    f"{f_ms * 1e3:.1f} us; peak = measured cuBLAS DGEMM (of measured)"}
+# Warp instructions on the FP64 pipe per launch of the FP64 force-phase kernels
+# (ncu smsp__inst_executed_pipe_fp64.sum, one launch each, --clock-control none;
+# profiles/force64_*.md), per workload; they hold while the kernel sources hash
+# to FP64_INST_DIGEST, otherwise the ALU roofline is left unmeasured.
+FP64_INST = {}
+FP64_INST_DIGEST = ""
 
 
-def leg_compaction(B, I, dev, stream, torch, hbm, fp64_peak, steps=200):
+def _roof_fp64(sim, f_ms, path, workload, clk, hbm):
+    """Roofline of the plain FP64 force phase.  Bound: the FP64 pipe.  Peak =
+    152 SMs x 2 FP64 lanes per cycle x the median SM clock sampled during the
+    timed steps (lane operations per second); achieved = 32 x the FP64-pipe warp
+    instructions of one launch (ncu) / its CUDA-event duration, i.e. frac is the
+    share of the phase the FP64 pipe is busy.  The HBM fraction of the same
+    phase (algorithmic bytes / duration) is reported beside it."""
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    peak = N_SM * FP64_LANES_PER_SM_CYCLE * mhz * 1e6 / 1e12          # tera lane-ops/s
+    m, l = path["mode"], path["lanes"]
+    names = [f"k_persistent<0, {l}, {path.get('block', 128)}>"] if m & 1 else (
+        [f"k_sums<0, {l}>", f"k_epilogue<0>"] if (m >> 1) & 1 else [f"k_force<0, {l}>"])
+    table = FP64_INST.get(workload, {}) if kernel_digest() == FP64_INST_DIGEST else {}
+    inst = sum(table[n] for n in names) if all(n in table for n in names) else None
+    nbytes = BYTES_PER_NODE_FP64 * sim.N + BYTES_PER_BOND_FP64 * sim.n_bonds
+    hbm_a = nbytes / (f_ms / 1e3) / 1e9
+    achieved = None if inst is None else 32.0 * inst / (f_ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": _force_kernels(m, False), "achieved": achieved, "peak": peak,
+            "unit": "T FP64 lane-ops/s", "frac": None if achieved is None else achieved / peak, "traffic": None,
+            "hbm": {"achieved": hbm_a, "peak": hbm, "unit": "GB/s", "frac": hbm_a / hbm,
+                    "note": f"{BYTES_PER_NODE_FP64} B/node + {BYTES_PER_BOND_FP64} B/bond (of measured)"},
+            "note": f"peak = {N_SM} SMs x {FP64_LANES_PER_SM_CYCLE} FP64 lanes/cycle x {mhz:.0f} MHz (derived); "
+                    + ("achieved = 32 x %d FP64-pipe warp instructions (ncu) / mean event time %.1f us"
+                       % (inst, f_ms * 1e3) if inst is not None else
+                       "FP64 instruction count not captured for this kernel build (achieved unmeasured)")}
+
+
+def leg_compaction(B, I, dev, stream, torch, hbm, clk, steps=200):
     """500 grains, ~5e5 nodes: FP64 path vs FP32 split, throughput, force error and
     break disagreements on an agitated (colliding, fracturing) state."""
     out = {}
@@ -398,7 +432,7 @@ def leg_compaction(B, I, dev, stream, torch, hbm, fp64_peak, steps=200):
         out[name] = {"value": sim.N * steps / dt, "unit": "node-steps/s", "ms_per_step": 1e3 * dt / steps,
                      "bond_evals_per_s": sim.n_bonds * steps / dt, "force_kernel_us": 1e3 * f_ms,
                      "roofline": _roof_fp32(sim, f_ms, hbm, "500-grain compaction") if name == "fp32"
-                     else _roof_fp64(sim, f_ms, fp64_peak, "500-grain compaction"),
+                     else _roof_fp64(sim, f_ms, tune, "compaction500", clk, hbm),
                      "step_path": tune, "status": int(sim.status()[0])}
         out["nodes"], out["directed_bonds"] = int(sim.N), int(sim.n_bonds)
         del sim
@@ -421,69 +455,12 @@ def leg_compaction(B, I, dev, stream, torch, hbm, fp64_peak, steps=200):
     out["precision_report"] = {
         "workload": f"the same aggregate with every grain thrown at 5 m/s (seeded directions), {n_win} steps",
         "force_rel_err_max_norm": float(np.abs(Fb - Fa).max() / np.abs(Fa).max()),
-        "broken_bonds_fp64": n_broken, f"break_disagreements_after_{n_win}_steps": n_dis}
+        "broken_bonds_fp64": n_broken, f"break_disagreements_after_{n_win}_steps": n_dis,
+        "reference": "the plain FP64 GPU path (its parity with the FP64 oracle on this agitated state: "
+                     "tests/test_gpu_fullsize.py, 1e-12 per force part, identical broken bonds)"}
     out["workload"] = ("compaction of 500 mixed-shape grains, R~U[0.8,1.6] mm, h=R/23, box width 40 mm, "
                        "top wall 0.1 m/s, dt=2e-8 s")
     del a, b
-    return out
-
-
-def leg_ensemble(B, I, dev, stream, torch, hbm, steps=40):
-    """64 independent aggregates (20-200 grains each): one batched FP32 context on
-    the autotuned path vs 64 sequential runs of the separate aggregates
-    (FP32 graph of kernels, and the plain FP64 path)."""
-    w = I.ensemble()
-    with torch.cuda.stream(stream):
-        sim = B.Simulation(w, precision=B.PD_FP32_SPLIT, device=dev, stream=stream)
-    tune = sim.autotune()
-    sim.step(16)
-    dt = _event_time(stream, torch, lambda: sim.step(steps))
-    info = sim.info()
-    N = int(sim.N)
-    out = {"workload": "64 independent settling aggregates, 20-200 grains each (seeded), R~U[0.8,1.2] mm, h=R/21, "
-                       "dt=2e-8 s, own wall box each",
-           "nodes": N, "directed_bonds": int(sim.n_bonds),
-           "batched": {"value": N * steps / dt, "unit": "node-steps/s", "ms_per_step": 1e3 * dt / steps,
-                       "path": {"mode": "persistent" if int(info["mode"]) & 1 else "kernel graph",
-                                "split_force_phase": bool((int(info["mode"]) >> 1) & 1),
-                                "lanes": int(info["lanes"]), "block": int(info["block"])},
-                       "autotune": tune, "status": int(sim.status()[0])}}
-    # the same batch as one persistent cooperative launch per 16 steps (best of its block sizes)
-    best = None
-    for blk in (128, 256):
-        sim.set_path(3, int(info["lanes"]), blk)
-        sim.step(16)
-        dtp = _event_time(stream, torch, lambda: sim.step(steps - steps % 16 or 16))
-        n = steps - steps % 16 or 16
-        if best is None or dtp / n < best[0]:
-            best = (dtp / n, blk)
-    out["batched_persistent"] = {"value": N / best[0], "unit": "node-steps/s", "ms_per_step": 1e3 * best[0],
-                                 "path": {"mode": 3, "lanes": int(info["lanes"]), "block": best[1]},
-                                 "status": int(sim.status()[0])}
-    a = BYTES_PER_NODE_STEP_FP32 * N + BYTES_PER_BOND_FP32 * sim.n_bonds
-    out["batched"]["step_roofline"] = {"bound": "hbm", "achieved": a / (dt / steps) / 1e9, "peak": hbm, "unit": "GB/s",
-                                       "frac": a / (dt / steps) / 1e9 / hbm,
-                                       "note": f"{BYTES_PER_NODE_STEP_FP32} B/node + {BYTES_PER_BOND_FP32} B/bond per whole step (of measured)"}
-    del sim
-    torch.cuda.empty_cache()
-    for prec, name in ((B.PD_FP32_SPLIT, "sequential_fp32"), (B.PD_FP64, "sequential_fp64")):
-        sims = []
-        with torch.cuda.stream(stream):
-            for part in w.parts:
-                sims.append(B.Simulation(part, precision=prec, device=dev, stream=stream))
-        for s_ in sims:
-            s_.step(16)
-
-        def run():
-            for s_ in sims:
-                s_.step(steps)
-        dts = _event_time(stream, torch, run)
-        n_tot = sum(int(s_.N) for s_ in sims)
-        out[name] = {"value": n_tot * steps / dts, "unit": "node-steps/s", "ms_per_step": 1e3 * dts / steps}
-        del sims
-        torch.cuda.empty_cache()
-    out["speedup_batched_vs_sequential_fp32"] = out["batched"]["value"] / out["sequential_fp32"]["value"]
-    out["speedup_batched_vs_sequential_fp64"] = out["batched"]["value"] / out["sequential_fp64"]["value"]
     return out
 
 
@@ -561,6 +538,82 @@ def leg_surrogate(B, I, SU, dev, stream, torch, steps=200):
     return out
 
 
+def _same_state_force_report(B, sim32, sim64, w):
+    """FP32-split vs FP64 path at one state: the FP64 context's state is pushed
+    into the FP32 one, both evaluate forces once, and the nodal forces
+    rho V (a - g) and the broken bonds are compared."""
+    for f in ("DISP", "VEL", "ACC", "BROKEN", "STEP"):
+        sim32.set(f, sim64.get(f))
+    sim64.eval_forces()
+    sim32.eval_forces()
+    g = np.array([w.params["gx"], w.params["gy"]])
+    a64, a32 = sim64.get("ACC") - g, sim32.get("ACC") - g
+    m = w.params["rho"] * sim64.get("VOLUME")[:, None]
+    F64, F32 = m * a64, m * a32
+    # scale: the largest nodal force, floored at the largest nodal weight (in free
+    # fall the forces vanish and the float path's absolute floor would dominate)
+    scale = max(np.abs(F64).max(), float(m.max()) * max(float(np.abs(g).max()), 100.0))
+    return {"force_rel_err_max_norm": float(np.abs(F32 - F64).max() / scale),
+            "force_scale_N": scale, "largest_force_N": float(np.abs(F64).max()),
+            "broken_bonds_fp64": int(sim64.get("BROKEN").sum()),
+            "break_disagreements": int(np.sum(sim64.get("BROKEN") != sim32.get("BROKEN"))),
+            "reference": "the plain FP64 GPU path at the same state (its parity with the FP64 oracle at this size: "
+                         "tests/test_gpu_fullsize.py, 1e-12)"}
+
+
+def leg_settling(B, I, dev, stream, torch, steps=200, advance=10000):
+    """The 50-grain settling (19,681 nodes): small enough to live in L2, so the
+    step is bound by launch and dependency latency; FP32 split vs FP64, L2
+    flushed before every timed step."""
+    w = I.settling(n_grains=50, seed=1)
+    flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    out = {"workload": WORKLOADS["settling50"][2], "window": f"steps {advance}..{advance + steps}",
+           "l2": "flushed (256 MB write) before every timed step"}
+
+    def flush():
+        with torch.cuda.stream(stream):
+            flush_buf.zero_()
+
+    for prec, name in ((B.PD_FP32_SPLIT, "fp32"), (B.PD_FP64, "fp64")):
+        with torch.cuda.stream(stream):
+            sim = B.Simulation(w, precision=prec, device=dev, stream=stream)
+        sim.step(advance)
+        tune = sim.autotune()
+        step_ms, force_ms, rebuilds = _timed_steps(sim, stream, flush, steps, 5, torch)
+        dt = sum(step_ms) / 1e3
+        out[name] = {"value": sim.N * steps / dt, "unit": "node-steps/s", "ms_per_step": 1e3 * dt / steps,
+                     "force_kernel_us": 1e3 * float(np.mean(force_ms)), "rebuilds": rebuilds, "step_path": tune,
+                     "status": int(sim.status()[0])}
+        out["nodes"], out["directed_bonds"] = int(sim.N), int(sim.n_bonds)
+        del sim
+    del flush_buf
+    out["speedup_fp32_vs_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def leg_sequential(B, w, dev, stream, torch, steps=40):
+    """The ensemble's 64 aggregates run one after another in separate contexts
+    (FP32 split, and the plain FP64 path): the baseline of the batched form."""
+    out = {}
+    for prec, name in ((B.PD_FP32_SPLIT, "sequential_fp32"), (B.PD_FP64, "sequential_fp64")):
+        sims = []
+        with torch.cuda.stream(stream):
+            for part in w.parts:
+                sims.append(B.Simulation(part, precision=prec, device=dev, stream=stream))
+        for s_ in sims:
+            s_.step(16)
+
+        def run():
+            for s_ in sims:
+                s_.step(steps)
+        dts = _event_time(stream, torch, run)
+        n_tot = sum(int(s_.N) for s_ in sims)
+        out[name] = {"value": n_tot * steps / dts, "unit": "node-steps/s", "ms_per_step": 1e3 * dts / steps}
+        del sims
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2108_07212_gb300 import binding as B
@@ -577,9 +630,20 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     prec = B.PD_FP32_SPLIT if args.precision == "fp32" else B.PD_FP64
     w = workload_for(rank, args)
+    advance = DEFAULT_ADVANCE.get(args.workload, 0) if args.advance is None else args.advance
     with torch.cuda.stream(stream):
         sim = B.Simulation(w, precision=prec, device=dev, stream=stream)
-        sim64 = B.Simulation(w, precision=B.PD_FP64, device=dev, stream=stream) if prec != B.PD_FP64 else None
+    # the timed window starts mid-run (steps advance..advance+steps)
+    if advance:
+        sim.step(advance)
+    # the plain FP64 path from the same state (pushed), timed on the same window
+    sim64 = None
+    if prec != B.PD_FP64:
+        with torch.cuda.stream(stream):
+            sim64 = B.Simulation(w, precision=B.PD_FP64, device=dev, stream=stream)
+        for f in ("DISP", "VEL", "ACC", "BROKEN", "STEP"):
+            sim64.set(f, sim.get(f))
+
     # both paths run the step variant their own autotuner picks (state unchanged),
     # unless --path fixes it
     def pick(x):
@@ -589,21 +653,17 @@ def run_ours(args):
             inf = x.info()
             return {"mode": int(inf["mode"]), "lanes": int(inf["lanes"]), "block": int(inf["block"]), "fixed": True}
         return x.autotune()
-    # the timed window starts mid-run (steps advance..advance+steps of the
-    # 20,000-step settling), where the grains move and collide and the contact
-    # lists are rebuilt as often as they are in a whole run
-    if args.advance:
-        sim.step(args.advance)
-        if sim64 is not None:
-            sim64.step(args.advance)
-    tuned = {"fp32" if prec != B.PD_FP64 else "fp64": pick(sim)}
+    key = "fp32" if prec != B.PD_FP64 else "fp64"
+    tuned = {key: pick(sim)}
     if sim64 is not None:
         tuned["fp64"] = pick(sim64)
-    flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    big = sim.N * BYTES_PER_NODE_STEP_FP32 > 512 * 1024 * 1024
+    flush_buf = None if big else torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
     def flush_l2():
-        with torch.cuda.stream(stream):
-            flush_buf.zero_()
+        if flush_buf is not None:
+            with torch.cuda.stream(stream):
+                flush_buf.zero_()
 
     if dist is not None:
         dist.barrier()
@@ -642,8 +702,10 @@ def run_ours(args):
         stream.synchronize()
     torch.cuda.synchronize()
     e2e_dt = time.perf_counter() - t0
+    e2e_dt = max_over_ranks(dist, [e2e_dt], dev)[0]
     e2e = {"value": sim.N * world * e2e_steps / e2e_dt, "unit": "node-steps/s",
            "h2d_bytes_per_step": 3 * 16 * sim.N, "d2h_bytes_per_step": 16 * sim.N, "steps": e2e_steps}
+    del pin
 
     if rank != 0:
         if dist is not None:
@@ -652,27 +714,21 @@ def run_ours(args):
         return 0
 
     peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs") or 6800.0)
+    clk = clocks.summary()
     f_ms = float(np.mean(force_ms))
     # the persistent kernel is the whole step: its duration is bounded by the
     # event-timed plain step (graph launch included), which the instrumented
     # graph's event nodes would otherwise inflate
-    if tuned["fp32" if prec != B.PD_FP64 else "fp64"]["mode"] & 1:
+    if tuned[key]["mode"] & 1:
         f_ms = min(f_ms, float(np.mean(step_ms)))
     if prec == B.PD_FP64:
-        fp64_peak = fp64_gemm_peak(torch, dev)
-        flops = FLOPS_PER_BOND * sim.n_bonds
-        achieved = flops / (f_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": _force_kernels(tuned["fp64"]["mode"], False), "achieved": achieved,
-                "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": force_phase_traffic(tuned["fp64"], False, args.workload),
-                "note": f"{FLOPS_PER_BOND} algorithmic FP64 ops per directed bond x {sim.n_bonds} bonds per launch / "
-                        f"mean CUDA-event duration {f_ms * 1e3:.1f} us; peak = measured cuBLAS DGEMM (of measured)"}
+        roof = _roof_fp64(sim, f_ms, tuned["fp64"], args.workload, clk, hbm)
     else:
         whole = bool(tuned["fp32"]["mode"] & 1)          # persistent kernel: one launch for the whole step
         per_node = BYTES_PER_NODE_STEP_FP32 if whole else BYTES_PER_NODE_FP32
         nbytes = per_node * sim.N + BYTES_PER_BOND_FP32 * sim.n_bonds
         achieved = nbytes / (f_ms / 1e3) / 1e9
-        hbm = float(peaks.get("hbm_gbs") or 6800.0)
         roof = {"bound": "hbm", "kernel": _force_kernels(tuned["fp32"]["mode"], True), "achieved": achieved, "peak": hbm,
                 "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": force_phase_traffic(tuned["fp32"], True, args.workload),
@@ -681,52 +737,66 @@ def run_ours(args):
                         f"CUDA-event duration {f_ms * 1e3:.1f} us"
                         + (" (persistent kernel = the whole step: event-timed step, graph launch included)" if whole else "")
                         + "; peak = measured copy bandwidth (of measured)"
-                        + ("; the 20k-node workload is too small to load 152 SMs, so the phase is latency-bound"
+                        + ("; the workload is too small to load 152 SMs, so the phase is latency-bound"
                            if sim.N < 100000 else "")}
+    step_bytes = BYTES_PER_NODE_STEP_FP32 * sim.N + BYTES_PER_BOND_FP32 * sim.n_bonds
+    step_s = elapsed / args.steps / world
     line = {
         "metric": METRIC, "value": value, "unit": "node-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == B.PD_FP64 else "f32+f64",
         "data": "synthetic",
         "config": describe(w, sim, args) | {"precision": "fp64" if prec == B.PD_FP64 else "fp32 split (FP32 forces, FP64 integration)",
-                                      "l2": "flushed (256 MB write) before every timed step",
-                                      "window": f"steps {args.advance}..{args.advance + args.steps} of the run",
-                                      "ranks": "independent seeded aggregates per rank",
+                                      "l2": ("inputs larger than L2 (%.2f GB of algorithmic traffic per step)" % (step_bytes / 1e9))
+                                      if flush_buf is None else "flushed (256 MB write) before every timed step",
+                                      "window": f"steps {advance}..{advance + args.steps} of the run",
+                                      "ranks": "independent seeded problems per rank",
                                       "step_path": tuned},
         "bond_evals_per_s": bond_evals,
         "fp64_path": {"value": value64, "unit": "node-steps/s", "ms_per_step": 1e3 * elapsed64 / args.steps,
-                      "force_kernel_us": 1e3 * float(np.mean(force64_ms)) if sim64 is not None else 1e3 * f_ms},
+                      "force_kernel_us": 1e3 * float(np.mean(force64_ms)) if sim64 is not None else 1e3 * f_ms,
+                      "roofline": _roof_fp64(sim64, float(np.mean(force64_ms)), tuned["fp64"], args.workload, clk, hbm)
+                      if sim64 is not None else roof},
         "speedup_vs_fp64_path": value / value64,
         "roofline": roof,
+        "step_roofline": {"bound": "hbm", "achieved": step_bytes / step_s / 1e9, "peak": hbm, "unit": "GB/s",
+                          "frac": step_bytes / step_s / 1e9 / hbm,
+                          "note": f"whole step: {BYTES_PER_NODE_STEP_FP32} B/node + {BYTES_PER_BOND_FP32} B/bond "
+                                  "(rebuilds not counted) / event-timed step (of measured)"},
         "force_kernel_us": 1e3 * f_ms,
-        "list_rebuilds": {"timed_steps": args.steps, "fp32" if prec != B.PD_FP64 else "fp64": rebuilds,
+        "list_rebuilds": {"timed_steps": args.steps, key: rebuilds,
                           **({"fp64": rebuilds64} if sim64 is not None else {}),
                           "note": "contact candidate lists (radius R_c + 0.1 R_c) rebuilt in a conditional graph "
                                   "node only when a node has moved 0.45 skin"},
-        "precision_report": precision_report(B, dev, stream, torch) if prec != B.PD_FP64 else None,
         "cpu_baseline": cpu_baseline(w) if not args.no_cpu else None,
         "e2e": e2e,
-        "clocks": clocks.summary(),
-        "gpu_launches": _launches(tuned["fp32" if prec != B.PD_FP64 else "fp64"]["mode"], args.steps, rebuilds)
+        "clocks": clk,
+        "gpu_launches": _launches(tuned[key]["mode"], args.steps, rebuilds)
                         + (_launches(tuned["fp64"]["mode"], args.steps, rebuilds64) if sim64 is not None else 0),
         "status": int(rc),
     }
+    if sim64 is not None:
+        line["precision_report"] = _same_state_force_report(B, sim, sim64, w)
+    del sim, sim64
+    torch.cuda.empty_cache()
     if world == 1 and args.legs:
         from paper_2108_07212_gb300 import inputs as I
         from paper_2108_07212_gb300 import surrogate as SU
-        hbm = float(peaks.get("hbm_gbs") or 6800.0)
-        fp64_peak = fp64_gemm_peak(torch, dev) if prec != B.PD_FP64 else fp64_peak
         legs = {}
-        del sim, sim64
-        torch.cuda.empty_cache()
         for name in args.legs.split(","):
             t0 = time.perf_counter()
-            if name == "compaction":
-                legs[name] = leg_compaction(B, I, dev, stream, torch, hbm, fp64_peak)
-            elif name == "ensemble":
-                legs[name] = leg_ensemble(B, I, dev, stream, torch, hbm)
+            if name == "sequential" and getattr(w, "parts", None) is not None:
+                legs[name] = leg_sequential(B, w, dev, stream, torch)
+                legs[name]["speedup_batched_vs_sequential_fp32"] = value / legs[name]["sequential_fp32"]["value"]
+                legs[name]["speedup_batched_vs_sequential_fp64"] = value / legs[name]["sequential_fp64"]["value"]
+            elif name == "compaction":
+                legs[name] = leg_compaction(B, I, dev, stream, torch, hbm, clk)
+            elif name == "settling":
+                legs[name] = leg_settling(B, I, dev, stream, torch)
             elif name == "surrogate":
                 legs[name] = leg_surrogate(B, I, SU, dev, stream, torch)
+            else:
+                continue
             legs[name]["wall_s"] = time.perf_counter() - t0
             torch.cuda.empty_cache()
         line["legs"] = legs
@@ -745,12 +815,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--legs", default="compaction,ensemble,surrogate",
-                    help="comma-separated large-workload legs at N=1 ('' for none)")
-    ap.add_argument("--workload", default="settling50", choices=sorted(WORKLOADS),
-                    help="workload of the main line (settling50 is the benchmark configuration)")
-    ap.add_argument("--advance", type=int, default=10000,
-                    help="untimed steps before the timed window (the window starts mid-run)")
+    ap.add_argument("--legs", default="sequential,compaction,surrogate,settling",
+                    help="comma-separated further workloads at N=1 ('' for none)")
+    ap.add_argument("--workload", default="ensemble64", choices=sorted(WORKLOADS),
+                    help="workload of the main line (ensemble64 is the benchmark configuration)")
+    ap.add_argument("--advance", type=int, default=None,
+                    help="untimed steps before the timed window (default: per workload; the window starts mid-run)")
     ap.add_argument("--path", default="", help="fix the step path: MODE,LANES[,BLOCK] (pd_set_path) instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
