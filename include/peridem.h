@@ -442,6 +442,21 @@ int pd_surrogate_inspect(pd_ctx *ctx, float *q_host, float *y_host);
  */
 int pd_observables(pd_ctx *ctx, double *out_host);
 
+/*
+ * Check of the FP64 path's square root (no counterpart in the paper).  The
+ * plain FP64 bond loop takes L = sqrt(|d|^2) from integer and FP32 arithmetic
+ * instead of GB300's 2-lane FP64 pipe and relies on it being the correctly
+ * rounded IEEE value, as the FP64 definition of the stretch (eq:pmb) is.  This
+ * call compares it with the hardware's IEEE square root on n pseudo-random
+ * positive doubles (splitmix64 of seed; magnitudes 2^-80 .. 2^20) on the given
+ * stream, waits, and writes the number of differing results to *mismatches and
+ * the first differing input to *first_mismatch (nullable; unchanged when there
+ * is none).  Allocates 16 bytes of device memory for the count.
+ * Errors: PD_EINVAL (n < 0, null mismatches), PD_ECUDA.
+ */
+int pd_check_sqrt(long long n, unsigned long long seed, void *cuda_stream, long long *mismatches,
+                  double *first_mismatch);
+
 /* ---- diagnostics without device allocation ---------------------------------- */
 #define PD_NOALLOC_MAX_NODES 2097152
 

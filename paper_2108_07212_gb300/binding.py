@@ -34,7 +34,7 @@ SYMBOLS = ("pd_last_error", "pd_create", "pd_destroy", "pd_mesh_grains", "pd_bui
            "pd_mlp_arena_bytes", "pd_mlp_bind_arena", "pd_mlp_set_params", "pd_mlp_get_params", "pd_mlp_forward",
            "pd_mlp_loss_grad", "pd_mlp_train_step", "pd_surrogate_setup", "pd_surrogate_set_mlp",
            "pd_surrogate_enable", "pd_surrogate_sample", "pd_surrogate_stats", "pd_surrogate_inspect",
-           "pd_diagnostics_noalloc", "pd_observables", "pd_set_materials")
+           "pd_diagnostics_noalloc", "pd_observables", "pd_set_materials", "pd_check_sqrt")
 
 
 class PdParams(ctypes.Structure):
@@ -101,6 +101,8 @@ def load():
             L.pd_surrogate_enable.argtypes = [vp, ip]
             L.pd_surrogate_sample.argtypes = [vp, vp, vp]
             L.pd_surrogate_stats.argtypes = [vp, vp, vp, vp]
+            L.pd_check_sqrt.argtypes = [ctypes.c_longlong, ctypes.c_ulonglong, vp, ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.POINTER(c_double)]
             for name in SYMBOLS:
                 if name != "pd_last_error":
                     getattr(L, name).restype = ip
@@ -128,6 +130,16 @@ def make_params(p: dict, precision: int = PD_FP64, store_parts: bool = False, la
     q.store_parts = 1 if store_parts else 0
     q.lanes = int(lanes)
     return q
+
+
+def check_sqrt(n: int, seed: int = 1, stream=None) -> tuple:
+    """pd_check_sqrt: (mismatches, first mismatching input or None) of the FP64
+    path's integer square root against the hardware IEEE square root."""
+    mm = ctypes.c_longlong(0)
+    first = c_double(float("nan"))
+    s = c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(load().pd_check_sqrt(int(n), int(seed), s, ctypes.byref(mm), ctypes.byref(first)))
+    return int(mm.value), (None if mm.value == 0 else first.value)
 
 
 def _ptr(a: np.ndarray):

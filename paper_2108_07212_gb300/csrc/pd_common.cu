@@ -4,6 +4,7 @@
 // positions for readout and the diagnostics reductions; plus the launch
 // dispatchers.  Compiled without FMA contraction.
 #include <algorithm>
+#include <cstring>
 
 #include "pd_device.cuh"
 
@@ -426,6 +427,32 @@ cudaError_t launch_observables(const DevPtrs &d, const KParams &k, int vcur, dou
     return cudaGetLastError();
 }
 
+// Check of the integer square root of the FP64 bond loop: n pseudo-random
+// positive doubles (splitmix64 of seed + i * golden ratio; exponents 2^-80 ..
+// 2^20, uniform significands; every other one the exact square of a 26-bit
+// significand) against the hardware's IEEE square root.
+// out[0] counts mismatches, out[1] holds the bits of the first one found.
+__global__ void k_check_sqrt(long long n, unsigned long long seed, unsigned long long *out) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        unsigned long long z = seed + (unsigned long long)i * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const unsigned long long e = 943ull + (z >> 52) % 101ull;
+        double x = __longlong_as_double((long long)((e << 52) | (z & 0xFFFFFFFFFFFFFull)));
+        if (i & 1) {
+            // every other input an exact square: y with a 26-bit significand, y^2 exact
+            const double y = __longlong_as_double((long long)(((1023ull - 40ull + (z >> 52) % 50ull) << 52) |
+                                                              (z & 0xFFFFFF8000000ull)));
+            x = __dmul_rn(y, y);
+        }
+        if (__double_as_longlong(sqrt_rn_int(x)) != __double_as_longlong(__dsqrt_rn(x))) {
+            if (atomicAdd(&out[0], 1ull) == 0ull) out[1] = (unsigned long long)__double_as_longlong(x);
+        }
+    }
+}
+
 cudaError_t launch_diagnostics(const DevPtrs &d, const KParams &k, int vcur, cudaStream_t s) {
     // positions, cells and candidate lists of the current state (no advance, forced rebuild)
     cudaError_t e = launch_predict(d, k, vcur, 0, s, 0, 0);
@@ -439,3 +466,26 @@ cudaError_t launch_diagnostics(const DevPtrs &d, const KParams &k, int vcur, cud
 }
 
 }  // namespace pd
+
+extern "C" int pd_check_sqrt(long long n, unsigned long long seed, void *cuda_stream, long long *mismatches,
+                             double *first_mismatch) {
+    if (n < 0 || !mismatches) return pd::set_error(PD_EINVAL, "pd_check_sqrt: n >= 0 and a result pointer required");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    unsigned long long *dev = nullptr, host[2] = {0ull, 0ull};
+    if (cudaMalloc(&dev, sizeof(host)) != cudaSuccess) return pd::set_error(PD_ECUDA, "pd_check_sqrt: cudaMalloc");
+    cudaError_t e = cudaMemsetAsync(dev, 0, sizeof(host), s);
+    if (e == cudaSuccess) {
+        pd::k_check_sqrt<<<152 * 8, 256, 0, s>>>(n, seed, dev);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, dev, sizeof(host), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(dev);
+    if (e != cudaSuccess) return pd::set_error(PD_ECUDA, cudaGetErrorString(e));
+    *mismatches = (long long)host[0];
+    if (first_mismatch) {
+        long long bits = (long long)host[1];
+        std::memcpy(first_mismatch, &bits, sizeof(bits));
+    }
+    return PD_OK;
+}

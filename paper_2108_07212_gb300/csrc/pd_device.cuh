@@ -403,6 +403,131 @@ __device__ __forceinline__ void wall_force32(const KParams &k, const AggParams &
 }
 
 // ---------------------------------------------------------------------------
+// plain FP64 path on GB300's narrow FP64 pipe
+//
+// GB300 issues FP64 at 2 lanes per SM cycle, against 64 for 32-bit integer and
+// 128 for FP32 arithmetic.  The FP64 bond loop therefore keeps in FP64 only the
+// operations whose rounding the stretch s = (L - |xi|) / |xi| depends on (the
+// coordinate differences, |d|^2 and L - |xi|, which cancels), takes the correctly
+// rounded L = sqrt(|d|^2) from integer and FP32 arithmetic, and forms the rest of
+// the bond force in float-float arithmetic (about 2^-47 relative), far inside the
+// 1e-12 per-step force tolerance of the path.
+
+// Float-float (hi + lo) of a double from its bits: hi holds the top 24
+// significand bits, lo the next 24 (the last five are dropped: 2^-48 relative).
+// Integer operations and one conversion of a 24-bit integer, no FP64
+// instruction.  Magnitudes below 2^-79 lose lo, below 2^-126 become 0.
+__device__ __forceinline__ void dbl_to_ff(double x, float &hi, float &lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e < 897) {
+        hi = lo = 0.f;
+        return;
+    }
+    if (e > 1150) {                     // beyond the float range, inf or NaN: carried as inf or NaN
+        hi = lo = e == 2047 && (b & 0xFFFFFFFFFFFFFull) ? __int_as_float(0x7FC00000) : __uint_as_float(sign | 0x7F800000u);
+        return;
+    }
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)(m >> 29));
+    // fraction bits 28..5 carry the weight 2^(e - 1023 - 47)
+    const float scale = e > 943 ? __uint_as_float((unsigned)(e - 943) << 23) : 0.f;
+    lo = __uint_as_float(sign | __float_as_uint(__uint2float_rn((unsigned)(m >> 5) & 0xFFFFFFu) * scale));
+}
+
+// Correctly rounded (to nearest) square root of a positive normal double, in
+// integer and FP32 arithmetic.  With x = M 2^(E - 52), M the 53-bit significand,
+// let N = M 2^(52 + (E & 1)); then sqrt(x) = sqrt(N) 2^(floor(E / 2) - 52) with
+// sqrt(N) in [2^52, 2^53), and the result's significand is Q = round(sqrt(N)).
+//  1. y = sqrt(A), A = N 2^-104 in [1, 4): the FP32 reciprocal square root, one
+//     FP32 Newton step, then one Newton step with the float-float residual
+//     A - y^2 (relative error below 2^-44): Y = y 2^52 is within 2^9 of sqrt(N).
+//  2. Newton's correction in integers: Q = Y + round((N - Y^2) / (2 Y)), with the
+//     residual exact in 128 bits (|N - Y^2| < 2^63) and its top bits converted,
+//     leaves |Q - sqrt(N)| < 1.
+//  3. Exact decision from R = N - Q^2 (|R| < 2^55): Q - 1 if R < 0 (then
+//     R += 2 Q - 1), and round up when R > Q, since (Q + 1/2)^2 = Q^2 + Q + 1/4
+//     and sqrt(N) is never a half-integer.
+// The result equals the IEEE square root (checked against the hardware's on
+// random inputs by pd_check_sqrt).
+__device__ __forceinline__ double sqrt_rn_int(double x) {
+    const unsigned long long D = (unsigned long long)__double_as_longlong(x);
+    if (D == 0ull || (D >> 52) >= 0x7FFull) return x;   // 0, inf, NaN (negative inputs do not occur)
+    const int E = (int)(D >> 52) - 1023;
+    const unsigned long long M = (D & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int odd = E & 1;
+    const int eL = (E - odd) / 2;
+    // A = M 2^(odd - 52) as a float-float: the top 24 bits and the remaining 29
+    const float a_hi = __uint_as_float(((unsigned)(127 + odd) << 23) | (unsigned)((M >> 29) & 0x7FFFFFu));
+    const float a_lo = __uint2float_rn((unsigned)(M & 0x1FFFFFFFu)) * __uint_as_float((unsigned)(75 + odd) << 23);
+    float r;
+    asm("rsqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(a_hi));
+    r = r * fmaf(-0.5f * a_hi, r * r, 1.5f);
+    const float y0 = a_hi * r;
+    float p, pe;
+    two_prod(y0, y0, p, pe);
+    const float res = (__fsub_rn(a_hi, p) - pe) + a_lo;     // A - y0^2
+    const unsigned yb = __float_as_uint(y0);
+    const int ey = (int)(yb >> 23) - 127;                   // -1, 0 or 1
+    long long Y = (long long)((yb & 0x7FFFFFu) | 0x800000u) << (29 + ey);
+    Y += (long long)__float2int_rn(res * (0.5f * r) * 4503599627370496.0f);   // + (A - y0^2) / (2 y0) 2^52
+    // R = N - Y^2 in 128 bits (hi:lo)
+    const unsigned long long n_lo = M << (52 + odd), n_hi = M >> (12 - odd);
+    const unsigned long long yy_lo = (unsigned long long)Y * (unsigned long long)Y;
+    const unsigned long long yy_hi = __umul64hi((unsigned long long)Y, (unsigned long long)Y);
+    const unsigned long long r_lo = n_lo - yy_lo;
+    const unsigned long long r_hi = n_hi - yy_hi - (n_lo < yy_lo ? 1ull : 0ull);
+    // R / 2^32 fits 32 bits (|R| < 2^63); its dropped low bits move R / (2 Y) by < 2^-21
+    // (32-bit conversions only: GB300 converts 64-bit integers at the FP64 rate)
+    const float rf = __int2float_rn((int)(long long)((r_hi << 32) | (r_lo >> 32))) * 4294967296.0f;
+    long long Q = Y + __float2int_rn(rf * (r * 1.1102230246251565e-16f));   // R / (2 Y), 1 / (2 Y) = r 2^-53
+    long long R = (long long)(n_lo - (unsigned long long)Q * (unsigned long long)Q);
+    if (R < 0) {
+        Q -= 1;
+        R += 2 * Q + 1;
+    }
+    Q += R > Q ? 1 : 0;
+    return __longlong_as_double(((long long)(eL + 1023) << 52) + (Q - (1ll << 52)));
+}
+
+// float-float arithmetic (Dekker / Knuth error-free transformations with FMA)
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    float p, e;
+    two_prod(a.hi, b.hi, p, e);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    const float s = __fadd_rn(p, e);
+    return {s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e += a.lo + b.lo;
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+// 1 / a to about 2^-46 relative: the approximate reciprocal and two Newton
+// steps x + x (1 - a x) with the residual formed in float-float.
+__device__ __forceinline__ ff ff_rcp(ff a) {
+    float x;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(x) : "f"(a.hi));
+    float t = fmaf(-a.hi, x, 1.0f) - a.lo * x;
+    x = fmaf(x, t, x);
+    t = fmaf(-a.hi, x, 1.0f) - a.lo * x;
+    const float c = x * t;
+    const float h = __fadd_rn(x, c);
+    return {h, __fsub_rn(c, __fsub_rn(h, x))};
+}
+__device__ __forceinline__ ff to_ff(double x) {
+    ff r;
+    dbl_to_ff(x, r.hi, r.lo);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
 // per-node phases
 
 // Algorithm 1: u <- u + dt v + dt^2/2 a (when advancing) and the positions.
@@ -774,25 +899,57 @@ __device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k,
     const int r0 = active ? __ldg(&d.row_ptr[ii]) : 0, r1 = active ? __ldg(&d.row_ptr[ii + 1]) : 0;
     uint32_t *bw = d.bits + (size_t)ii * k.wpn;
 
-    // peridynamic bonds with breaking (eq:peri, eq:pmb, Sec. 3.1)
-    double Fbx = 0.0, Fby = 0.0;
-    for (int b = r0 + lane; b < r1; b += LANES) {
-        const int kk = b - r0;
-        if ((__ldcg(&bw[kk >> 5]) >> (kk & 31)) & 1u) continue;
-        const int j = __ldg(&d.col[b]);
-        const double xi = __ldg(&d.xi[b]);
-        const double2 pj = ldm<PERSIST>(&d.p[j]);
-        double dx = pj.x - pi.x, dy = pj.y - pi.y;
-        double L = sqrt(dx * dx + dy * dy);
-        double s = (L - xi) / xi;
-        if (fabs(s) > s0) {
-            atomicOr(&bw[kk >> 5], 1u << (kk & 31));
-            continue;
+    // peridynamic bonds with breaking (eq:peri, eq:pmb, Sec. 3.1).  The
+    // stretch's cancelling difference L - |xi| is formed exactly as the FP64
+    // definition rounds it: dx, dy and |d|^2 in FP64, L = sqrt(|d|^2) correctly
+    // rounded (integer square root), L - |xi| in FP64.  The quotient by |xi|,
+    // the break decision away from the threshold and the bond force
+    // c_w w s V_x V_y (d / L) are float-float (relative error ~1e-14; a bond
+    // whose stretch lies within 1e-6 of s0 is decided by the FP64 quotient).
+    ff Fbx = {0.f, 0.f}, Fby = {0.f, 0.f};
+    const uint32_t w0 = active ? __ldcg(bw) : 0u;      // the row's first 32 broken bits (own bonds only)
+    const float s0f = (float)s0;
+    const ff cwVV = to_ff(cw * Vi * Vi);                // one grain: V_y = V_x
+    const ff inv_eps = ff_rcp(to_ff(eps));
+    constexpr int kBondBatch64 = 4;
+    for (int b0 = r0 + lane; b0 < r1; b0 += kBondBatch64 * LANES) {
+        int jb[kBondBatch64];
+        uint32_t wb[kBondBatch64];
+        double xb[kBondBatch64];
+        double2 pb[kBondBatch64];
+#pragma unroll
+        for (int m = 0; m < kBondBatch64; ++m) {
+            const int b = b0 + m * LANES;
+            jb[m] = b < r1 ? __ldg(&d.col[b]) : -1;
+            xb[m] = b < r1 ? __ldg(&d.xi[b]) : 1.0;
+            wb[m] = b - r0 < 32 ? w0 : (b < r1 ? __ldcg(&bw[(b - r0) >> 5]) : 0u);
         }
-        double cws = (k.micro ? cw * (1.0 - xi / eps) : cw) * s;
-        double q = cws * Vi * __ldg(&d.V[j]) / L;
-        Fbx += q * dx;
-        Fby += q * dy;
+#pragma unroll
+        for (int m = 0; m < kBondBatch64; ++m) pb[m] = ldm<PERSIST>(&d.p[jb[m] < 0 ? ii : jb[m]]);
+#pragma unroll
+        for (int m = 0; m < kBondBatch64; ++m) {
+            const int kk = b0 + m * LANES - r0;
+            if (jb[m] < 0 || ((wb[m] >> (kk & 31)) & 1u)) continue;
+            const double xi = xb[m];
+            const double dx = __dsub_rn(pb[m].x, pi.x), dy = __dsub_rn(pb[m].y, pi.y);
+            const double L = sqrt_rn_int(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+            const double diff = __dsub_rn(L, xi);                       // |xi| s, exact as in FP64
+            const ff dff = to_ff(diff), xff = to_ff(xi);
+            // break test |diff| > s0 |xi| in float, the FP64 quotient near the threshold
+            const float lhs = fabsf(dff.hi), rhs = s0f * xff.hi;
+            bool brk = lhs > rhs;
+            if (fabsf(lhs - rhs) <= 1e-6f * rhs) brk = fabs(__ddiv_rn(diff, xi)) > s0;
+            if (brk) {
+                atomicOr(&bw[kk >> 5], 1u << (kk & 31));
+                continue;
+            }
+            // c_w w V_x V_y (diff / |xi|) / L  (w = 1 - |xi| / eps for the conic micromodulus)
+            ff c = cwVV;
+            if (k.micro) c = ff_mul(c, ff_add({1.0f, 0.f}, ff_mul({-xff.hi, -xff.lo}, inv_eps)));
+            const ff t = ff_mul(ff_mul(c, dff), ff_rcp(ff_mul(xff, to_ff(L))));
+            Fbx = ff_add(Fbx, ff_mul(t, to_ff(dx)));
+            Fby = ff_add(Fby, ff_mul(t, to_ff(dy)));
+        }
     }
     __syncwarp();
 
@@ -800,6 +957,9 @@ __device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k,
     // ascending node index), self-contact (Sec. 4.4), inter-grain contact
     // (Secs. 4.1-4.3)
     const double Rc = A.Rc;
+    // |d|^2 above R_c^2 (1 + 1e-12) means sqrt(|d|^2) rounds to R_c or more:
+    // candidates that far are dropped before the square root
+    const double rc2_out = Rc * Rc * (1.0 + 1e-12);
     const double rho_i = k.mat ? __ldg(&d.g_rho[gi]) : k.rho;
     const int nc = active ? ldm<PERSIST>(&d.nbr_cnt[ii]) : 0;
     const double2 vi = ldm<PERSIST>(&d.v[vin][ii]);
@@ -808,7 +968,9 @@ __device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k,
         const int j = ldm<PERSIST>(&d.nbr[(size_t)q * k.N + ii]);
         const double2 pj = ldm<PERSIST>(&d.p[j]);
         double dx = pj.x - pi.x, dy = pj.y - pi.y;
-        double dd = sqrt(dx * dx + dy * dy);
+        const double dd2 = dx * dx + dy * dy;
+        if (!(dd2 <= rc2_out)) continue;
+        double dd = dd2 > 0.0 ? sqrt_rn_int(dd2) : 0.0;
         if (!(dd < Rc)) continue;
         if (dd == 0.0) {
             atomicAdd(&d.status[PD_STATUS_COINCIDENT], 1);
@@ -849,8 +1011,8 @@ __device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k,
             Fny += gy;
         }
     }
-    out.bx = lane_sum<LANES>(Fbx);
-    out.by = lane_sum<LANES>(Fby);
+    out.bx = lane_sum<LANES>((double)Fbx.hi + (double)Fbx.lo);
+    out.by = lane_sum<LANES>((double)Fby.hi + (double)Fby.lo);
     out.sx = lane_sum<LANES>(Fsx);
     out.sy = lane_sum<LANES>(Fsy);
     out.nx = lane_sum<LANES>(Fnx);
