@@ -389,6 +389,30 @@ int pd_mlp_train_step(pd_mlp *mlp, const float *x, const float *t, int batch, fl
  * (relative, floored at the grain's weight), leaves the surrogate for good.
  * Bonds of a surrogate grain do not break between judge steps.
  */
+/*
+ * The modal basis of every template (host; after pd_build_bonds, before or
+ * after pd_bind_arena; one material only): the n_modes softest non-rigid
+ * eigenvectors of the template's linearised bond operator K / E, and their
+ * eigenvalues, in the layout pd_surrogate_setup takes.  Linearising the bond
+ * force of eq:pmb about the reference lattice, a bond of lattice offset d with
+ * micromodulus c_w w (Table 1, the library's own constants) adds the
+ * stiffness k = c_w w V^2 / (E h |d|) e e^T (e = d / |d|, V = h^2) to the
+ * diagonal 2 x 2 blocks of its node and subtracts it from the block coupling
+ * the two nodes, so that F / (E h) = -(K / E) u / h.  The three zero modes
+ * (rigid motions) are skipped; vectors are orthonormal over the template's 2 n_t
+ * unknowns (sign, and the basis of a repeated eigenvalue, are arbitrary).
+ *   basis     float[*basis_len]: per template t, per node l of the template
+ *             (meshing order), n_modes x-components then n_modes y-components;
+ *             NULL: write the required length sum_t 2 n_t n_modes to *basis_len
+ *   lambda    float[n_templates n_modes] eigenvalues, ascending per template
+ *   rigid     double[3 n_templates] (nullable): the three lowest eigenvalues
+ *             (zero up to round-off)
+ * Method: Chebyshev-filtered subspace iteration on the sparse operator (dense
+ * Jacobi below 400 unknowns).  Errors: PD_ESTATE (before pd_build_bonds),
+ * PD_EINVAL (sizes, several materials), PD_ENUMERIC (no convergence).
+ */
+int pd_surrogate_basis(pd_ctx *ctx, int n_modes, float *basis, size_t *basis_len, float *lambda, double *rigid);
+
 /* Before pd_bind_arena.  n_modes: 8, 16, 24 or 32.  basis: for t = 0, 1, ...
  * the template's nodes in meshing order, per node n_modes x-components then
  * n_modes y-components (copied; the library keeps its own layouts);

@@ -34,7 +34,8 @@ SYMBOLS = ("pd_last_error", "pd_create", "pd_destroy", "pd_mesh_grains", "pd_bui
            "pd_mlp_arena_bytes", "pd_mlp_bind_arena", "pd_mlp_set_params", "pd_mlp_get_params", "pd_mlp_forward",
            "pd_mlp_loss_grad", "pd_mlp_train_step", "pd_surrogate_setup", "pd_surrogate_set_mlp",
            "pd_surrogate_enable", "pd_surrogate_sample", "pd_surrogate_stats", "pd_surrogate_inspect",
-           "pd_diagnostics_noalloc", "pd_observables", "pd_set_materials", "pd_check_sqrt")
+           "pd_diagnostics_noalloc", "pd_observables", "pd_set_materials", "pd_check_sqrt",
+           "pd_surrogate_basis")
 
 
 class PdParams(ctypes.Structure):
@@ -101,6 +102,7 @@ def load():
             L.pd_surrogate_enable.argtypes = [vp, ip]
             L.pd_surrogate_sample.argtypes = [vp, vp, vp]
             L.pd_surrogate_stats.argtypes = [vp, vp, vp, vp]
+            L.pd_surrogate_basis.argtypes = [vp, ip, vp, ctypes.POINTER(c_size_t), vp, vp]
             L.pd_check_sqrt.argtypes = [ctypes.c_longlong, ctypes.c_ulonglong, vp, ctypes.POINTER(ctypes.c_longlong),
                                         ctypes.POINTER(c_double)]
             for name in SYMBOLS:

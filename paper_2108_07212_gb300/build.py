@@ -32,7 +32,7 @@ CU_SOURCES = [
     ("pd_mlp.cu", []),
     ("pd_surrogate.cu", []),
 ]
-CPP_SOURCES = ["pd_host.cpp"]
+CPP_SOURCES = ["pd_host.cpp", "pd_basis.cpp"]
 
 
 def _nvcc() -> str:

@@ -611,6 +611,38 @@ size_t field_bytes(pd_ctx *c, int f) {
 
 int pd::set_error(int code, const char *msg) { return fail(code, msg); }
 
+// Template data for the modal basis of the surrogate (pd_basis.cpp).
+namespace pd {
+struct TemplateView {
+    int n_tmpl;
+    const int32_t *tmpl_first, *tmpl_nodes;
+    const int64_t *g_start;
+    const int32_t *lat, *row_ptr, *col;
+    const double *g_cw, *g_eps, *g_h;
+    double E, horizon_ratio;
+    int micromodulus;
+};
+int template_view(pd_ctx *c, TemplateView *out) {
+    if (!c || !out) return fail(PD_EINVAL, "null context");
+    if (c->state < 2) return fail(PD_ESTATE, "the modal basis needs the bond lists (after pd_build_bonds)");
+    if (c->has_mat) return fail(PD_EINVAL, "the surrogate runs with one material");
+    out->n_tmpl = c->n_tmpl;
+    out->tmpl_first = c->tmpl_first.data();
+    out->tmpl_nodes = c->tmpl_nodes.data();
+    out->g_start = c->g_start.data();
+    out->lat = c->lat.data();
+    out->row_ptr = c->row_ptr.data();
+    out->col = c->col.data();
+    out->g_cw = c->g_cw.data();
+    out->g_eps = c->g_eps.data();
+    out->g_h = c->g_h.data();
+    out->E = c->prm.E;
+    out->horizon_ratio = c->prm.horizon_ratio;
+    out->micromodulus = c->prm.micromodulus;
+    return PD_OK;
+}
+}  // namespace pd
+
 // ===========================================================================
 // C ABI
 

@@ -2,10 +2,9 @@
 
 Per bond-network template (grains of one shape meshed at the same h/R) the
 basis is the n_modes softest non-rigid eigenvectors of the template's
-dimensionless linearised bond operator K/E (the bond law of eq:pmb linearised
-about the reference lattice: for a bond of lattice offset d, unit e and
-micromodulus c_w w, the stiffness block c_w w V^2 / (E h |d|) e e^T);
-``lambda_`` are their eigenvalues.  The network of a template learns the
+dimensionless linearised bond operator K/E, and ``lambda_`` their eigenvalues;
+the library assembles the operator from its own bond constants and solves for
+them (pd_surrogate_basis).  The network of a template learns the
 nonlinear part of the modal bond force, f - (-lambda q), from training pairs
 that the simulation itself produces (:func:`collect_samples`), and is trained
 on the GPU by the library's own forward/backward kernels (:class:`~.binding.MLP`).
@@ -17,36 +16,6 @@ import math
 import numpy as np
 
 from . import binding as B
-
-
-def template_operator(lat: np.ndarray, row_ptr: np.ndarray, col: np.ndarray, params: dict) -> np.ndarray:
-    """Dimensionless stiffness K/E (2n x 2n) of one template: F/(E h) = -(K/E) w/h."""
-    n = lat.shape[0]
-    r = params["horizon_ratio"]
-    nu = params["nu"]
-    conic = int(params["micromodulus"]) == 1
-    c = (24.0 if conic else 6.0) / (math.pi * r ** 3 * (1.0 - nu))   # c_w V^2 / (E h) with V = h^2, eps = r h
-    K = np.zeros((2 * n, 2 * n))
-    for a in range(n):
-        for b in col[row_ptr[a]:row_ptr[a + 1]]:
-            d = (lat[b] - lat[a]).astype(np.float64)
-            L = math.hypot(d[0], d[1])
-            w = (1.0 - L / r) if conic else 1.0
-            e = d / L
-            k = c * w / L * np.outer(e, e)
-            K[2 * a:2 * a + 2, 2 * a:2 * a + 2] += k
-            K[2 * a:2 * a + 2, 2 * b:2 * b + 2] -= k
-    return 0.5 * (K + K.T)
-
-
-def _lowest_eigenpairs(K: np.ndarray, k: int):
-    """The k smallest eigenpairs of the symmetric K (ascending)."""
-    try:
-        from scipy.linalg import eigh
-        return eigh(K, subset_by_index=[0, k - 1])
-    except ImportError:
-        vals, vecs = np.linalg.eigh(K)
-        return vals[:k], vecs[:, :k]
 
 
 def build_basis(sim: "B.Simulation", n_modes: int = 32, judge_every: int = 50, gate: float = 0.5,
@@ -73,29 +42,35 @@ def build_basis(sim: "B.Simulation", n_modes: int = 32, judge_every: int = 50, g
     my_keys = template_keys(sim, dict(template_of_grain=tmpl, templates=[
         dict(nodes=int(starts[int(np.argmax(tmpl == t)) + 1] - starts[int(np.argmax(tmpl == t))]))
         for t in range(int(tmpl.max()) + 1)])) if reuse else None
+    # every template's basis from the library (pd_surrogate_basis); templates
+    # shared with the source simulation keep the source's
+    import ctypes
+    L = B.load()
+    n_t = int(tmpl.max()) + 1
+    need = ctypes.c_size_t(0)
+    B._check(L.pd_surrogate_basis(sim._ctx, n_modes, None, ctypes.byref(need), None, None))
+    lib_basis = np.zeros(int(need.value), dtype=np.float32)
+    lib_lam = np.zeros(n_t * n_modes, dtype=np.float32)
+    rigid = np.zeros(3 * n_t)
+    B._check(L.pd_surrogate_basis(sim._ctx, n_modes, B._ptr(lib_basis), ctypes.byref(need), B._ptr(lib_lam),
+                                  B._ptr(rigid)))
     bases, lams, info = [], [], []
-    for t in range(int(tmpl.max()) + 1):
+    off = 0
+    for t in range(n_t):
         g = int(np.argmax(tmpl == t))
-        s0, s1 = int(starts[g]), int(starts[g + 1])
+        n = int(starts[g + 1] - starts[g])
+        piece = lib_basis[off:off + 2 * n * n_modes]
+        off += 2 * n * n_modes
         if reuse and my_keys[t] in reuse:
             b, l, d = reuse[my_keys[t]]
             bases.append(np.asarray(b, dtype=np.float64))
             lams.append(np.asarray(l, dtype=np.float64))
             info.append(dict(d, template=t))
             continue
-        r = row[s0:s1 + 1] - row[s0]
-        cl = col[row[s0]:row[s1]] - s0
-        K = template_operator(lat[s0:s1], r, cl, sim.workload.params)
-        vals, vecs = _lowest_eigenpairs(K, 3 + n_modes)
-        pick = slice(3, 3 + n_modes)                  # skip the two translations and the rotation
-        Phi = vecs[:, pick]                           # (2n, M), orthonormal columns
-        n = s1 - s0
-        per_node = np.empty((n, 2, n_modes))
-        per_node[:, 0, :] = Phi[0::2, :]
-        per_node[:, 1, :] = Phi[1::2, :]
-        bases.append(per_node.reshape(-1))
-        lams.append(vals[pick])
-        info.append(dict(template=t, nodes=n, rigid=vals[:3].tolist(), first=float(vals[3])))
+        bases.append(piece.astype(np.float64))
+        lams.append(lib_lam[t * n_modes:(t + 1) * n_modes].astype(np.float64))
+        info.append(dict(template=t, nodes=n, rigid=rigid[3 * t:3 * t + 3].tolist(),
+                         first=float(lib_lam[t * n_modes])))
     return dict(basis=np.concatenate(bases).astype(np.float32), lambda_=np.concatenate(lams).astype(np.float32),
                 n_modes=n_modes, judge_every=judge_every, gate=gate, err_tol=err_tol, templates=info,
                 template_of_grain=tmpl)
