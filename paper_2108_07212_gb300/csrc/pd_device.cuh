@@ -799,8 +799,10 @@ __device__ __forceinline__ bool bonded_intact(const DevPtrs &d, const KParams &k
 }
 
 // Acceleration and velocity update of node i (Algorithm 1) plus the optional
-// per-part force output; run by one lane per node.  m = rho V (FP64 path) or
-// inv_m = 1 / (rho V) (RECIP, FP32 split).
+// per-part force output; run by one lane per node.  m = rho V, or with RECIP
+// inv_m = 1 / (rho V): a = F (1 / m) + g and the velocity update fused, about
+// one ulp of a from the quotient (the forces themselves are unchanged), for
+// the two FP64 divisions per node that GB300's FP64 pipe makes costly.
 template <bool PERSIST, bool RECIP = false>
 __device__ __forceinline__ void finish_node(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
                                             double2 vi, double m, double Fbx, double Fby, double Fsx, double Fsy,
@@ -809,7 +811,6 @@ __device__ __forceinline__ void finish_node(const DevPtrs &d, const KParams &k, 
     const double Fy = __dadd_rn(__dadd_rn(__dadd_rn(Fby, Fsy), Fny), Fwy);
     double ax, ay;
     if constexpr (RECIP) {
-        // FP32-split path: F / m as F * (1 / m) + g, fused (far below the FP32 force error)
         ax = fma(Fx, inv_m, k.gx);
         ay = fma(Fy, inv_m, k.gy);
     } else {
@@ -1036,9 +1037,43 @@ __device__ __forceinline__ void node_epilogue64(const DevPtrs &d, const KParams 
         const double Kn = k.mat ? 18.0 * __ldg(&d.g_k[gi]) / A.pe5 : A.Kn;
         wall_force64(k, A, Kn, rho, ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, Vi, Fwx, Fwy, d.status);
     }
-    finish_node<PERSIST>(d, k, i, vin, update_v, vi, __dmul_rn(rho, Vi), f.bx, f.by, f.sx, f.sy, f.nx, f.ny, Fwx,
-                         Fwy);
+    finish_node<PERSIST, true>(d, k, i, vin, update_v, vi, 0.0, f.bx, f.by, f.sx, f.sy, f.nx, f.ny, Fwx, Fwy,
+                               __ldg(&d.g_invm[gi]));
 }
+
+// FP32-split bond force of one intact bond to a neighbour at qj (float-float
+// shifted position), lattice offset code nn = di^2 + dj^2: 0 = force added to
+// (Fbx, Fby), 1 = broken at this evaluation, 2 = stretch in the guard band
+// around s0 (decided in FP64 after the loop).
+__device__ __forceinline__ int bond_force32(float4 qj, float2 phi, float2 pli, float nn, float4 gq, float cw,
+                                            float s0, float s0_lo, float s0_hi, float eps, float VV, int micro,
+                                            float &Fbx, float &Fby) {
+    const float dxh = __fsub_rn(qj.x, phi.x), dxl = qj.z - pli.x;
+    const float dyh = __fsub_rn(qj.y, phi.y), dyl = qj.w - pli.y;
+    float L2h, L2l;
+    len2_ff(dxh, dxl, dyh, dyl, L2h, L2l);
+    float q, eq;
+    two_prod(nn, gq.y, q, eq);                           // |xi|^2 = n h^2
+    const float num = ff_diff(L2h, L2l, q, eq + nn * gq.z);
+    const float xi = gq.x * sqrt_approx(nn);
+    const float L = sqrt_approx(L2h);
+    const float s = __fdividef(num, xi * (L + xi));
+    const float as = fabsf(s);
+    // near the threshold the FP64 path decides, after the loop (its FP64
+    // registers stay out of the hot loop)
+    if (as > s0_lo && as < s0_hi) return 2;
+    if (as > s0) return 1;
+    const float cws = (micro ? cw * (1.0f - xi / eps) : cw) * s;
+    const float qf = __fdividef(cws * VV, L);
+    Fbx += qf * (dxh + dxl);
+    Fby += qf * (dyh + dyl);
+    return 0;
+}
+
+// Offset o (0..23) of the bond stencil: the 5 x 5 lattice block without its
+// centre, in (dj, di) order.
+__host__ __device__ constexpr int stn_di(int o) { return (o + (o >= 12 ? 1 : 0)) % 5 - 2; }
+__host__ __device__ constexpr int stn_dj(int o) { return (o + (o >= 12 ? 1 : 0)) / 5 - 2; }
 
 // FP32-split forces of node i: the same laws and lane layout, with the bond,
 // self-contact and contact arithmetic on the FP32 pipe.  Positions are
@@ -1064,7 +1099,18 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
     const float4 gc = __ldg(&d.gc[gi]);                   // (c_w, s0, eps) as floats
     const float cw = gc.x, s0 = gc.y, eps = gc.z;
     const float s0_lo = s0 * (1.0f - k.guard), s0_hi = s0 * (1.0f + k.guard);
-    const int r0 = active ? __ldg(&d.row_ptr[ii]) : 0, r1 = active ? __ldg(&d.row_ptr[ii + 1]) : 0;
+    // lattice stencil of the node's bonds (regular nodes: the neighbour at
+    // offset o is node ii + di + D[dj], no column load), else the CSR columns
+    const uint4 st = (k.stencil && active) ? __ldg(&d.stn[ii]) : make_uint4(kStnIrregular, 0u, 0u, 0u);
+    const bool stencil = !(st.x & kStnIrregular);
+    int r0 = 0, r1 = 0;
+    if (stencil) {
+        r0 = (int)st.w;
+        r1 = r0 + __popc(st.x);
+    } else if (active) {
+        r0 = __ldg(&d.row_ptr[ii]);
+        r1 = __ldg(&d.row_ptr[ii + 1]);
+    }
     uint32_t *bw = d.bits + (size_t)ii * k.wpn;
     const float Rc = A.rcf, Kn = A.knf;
 
@@ -1087,7 +1133,40 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
     // neighbour positions of a batch are all in flight before any is used (the
     // per-lane summation order is unchanged: bonds lane, lane + LANES, ...)
     constexpr int kBondBatch = 4;
-    for (int b0 = r0 + lane; b0 < r1 && !(sur && !judge); b0 += kBondBatch * LANES) {
+    if (stencil && !(sur && !judge)) {
+        const uint32_t mask = st.x;
+        const int Dm2 = (int)(short)(st.y & 0xFFFFu), Dm1 = (int)(short)(st.y >> 16);
+        const int Dp1 = (int)(short)(st.z & 0xFFFFu), Dp2 = (int)(short)(st.z >> 16);
+        constexpr int kPerLane = (24 + LANES - 1) / LANES;
+#pragma unroll
+        for (int m0 = 0; m0 < kPerLane; m0 += kBondBatch) {
+            float4 qb[kBondBatch];
+            bool live[kBondBatch];
+#pragma unroll
+            for (int m = 0; m < kBondBatch; ++m) {
+                const int o = (m0 + m) * LANES + lane;
+                const int dj = stn_dj(o), di = stn_di(o);
+                const int D = dj == -2 ? Dm2 : (dj == -1 ? Dm1 : (dj == 0 ? 0 : (dj == 1 ? Dp1 : Dp2)));
+                const int kk = __popc(mask & ((1u << o) - 1u));
+                live[m] = (m0 + m) < kPerLane && o < 24 && ((mask >> o) & 1u) && !((w0 >> kk) & 1u);
+                qb[m] = ldm<PERSIST>(&d.pq[live[m] ? ii + di + D : ii]);
+            }
+#pragma unroll
+            for (int m = 0; m < kBondBatch; ++m) {
+                if (!live[m]) continue;
+                const int o = (m0 + m) * LANES + lane;
+                const int dj = stn_dj(o), di = stn_di(o);
+                const int r = bond_force32(qb[m], phi, pli, (float)(di * di + dj * dj), gq, cw, s0, s0_lo, s0_hi, eps,
+                                           VV, k.micro, Fbx, Fby);
+                if (r == 2) pending = true;
+                if (r == 1) {
+                    const int kk = __popc(mask & ((1u << o) - 1u));
+                    atomicOr(bw, 1u << kk);
+                }
+            }
+        }
+    }
+    for (int b0 = r0 + lane; b0 < r1 && !stencil && !(sur && !judge); b0 += kBondBatch * LANES) {
         uint32_t cb[kBondBatch], wb[kBondBatch];
 #pragma unroll
         for (int m = 0; m < kBondBatch; ++m) {
@@ -1107,35 +1186,10 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
             const int b = b0 + m * LANES;
             const int kk = b - r0;
             if (cb[m] == 0xFFFFFFFFu || ((wb[m] >> (kk & 31)) & 1u)) continue;
-            const int j = (int)(cb[m] & kColMask);
-            const float4 qj = qb[m];
-            const float dxh = __fsub_rn(qj.x, phi.x), dxl = qj.z - pli.x;
-            const float dyh = __fsub_rn(qj.y, phi.y), dyl = qj.w - pli.y;
-            float L2h, L2l;
-            len2_ff(dxh, dxl, dyh, dyl, L2h, L2l);
             const float nn = (float)(cb[m] >> kColBits);         // lattice offset di^2 + dj^2
-            float q, eq;
-            two_prod(nn, gq.y, q, eq);                           // |xi|^2 = n h^2
-            const float num = ff_diff(L2h, L2l, q, eq + nn * gq.z);
-            const float xi = gq.x * sqrt_approx(nn);
-            const float L = sqrt_approx(L2h);
-            const float s = __fdividef(num, xi * (L + xi));
-            const float as = fabsf(s);
-            // near the threshold the FP64 path decides, after the loop (its FP64
-            // registers stay out of the hot loop)
-            if (as > s0_lo && as < s0_hi) {
-                pending = true;
-                continue;
-            }
-            const bool brk = as > s0;
-            if (brk) {
-                atomicOr(&bw[kk >> 5], 1u << (kk & 31));
-                continue;
-            }
-            const float cws = (k.micro ? cw * (1.0f - xi / eps) : cw) * s;
-            const float qf = __fdividef(cws * VV, L);
-            Fbx += qf * (dxh + dxl);
-            Fby += qf * (dyh + dyl);
+            const int r = bond_force32(qb[m], phi, pli, nn, gq, cw, s0, s0_lo, s0_hi, eps, VV, k.micro, Fbx, Fby);
+            if (r == 2) pending = true;
+            if (r == 1) atomicOr(&bw[kk >> 5], 1u << (kk & 31));
         }
     }
     if (pending) {

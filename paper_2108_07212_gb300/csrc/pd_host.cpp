@@ -191,6 +191,7 @@ struct pd_ctx {
     std::vector<int32_t> row_ptr, col;
     std::vector<double> xi;
     int max_row = 0, wpn = 1;
+    size_t stn_irregular = 0;   // FP32 split: nodes whose bonds do not follow the lattice stencil
     // derived
     double h_min = 0, Rc = 0, Kn = 0;   // of aggregate 0 (reported by pd_info)
     unsigned T = 0;
@@ -380,17 +381,18 @@ size_t layout(pd_ctx *c, char *base) {
         carve(base, off, d.pq, N);
         carve(base, off, d.xs, N);
         carve(base, off, d.colx, nb);
+        carve(base, off, d.stn, N);
         carve(base, off, d.gc, G);
-        carve(base, off, d.g_invm, G);
     } else {
         d.lat = nullptr;
         d.gq = nullptr;
         d.pq = nullptr;
         d.xs = nullptr;
         d.colx = nullptr;
+        d.stn = nullptr;
         d.gc = nullptr;
-        d.g_invm = nullptr;
     }
+    carve(base, off, d.g_invm, G);
     carve(base, off, d.bu, N);
     carve(base, off, d.bv, N);
     carve(base, off, d.ba, N);
@@ -1075,6 +1077,7 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     std::vector<float> gq, gcf;
     std::vector<double> invm;
     std::vector<uint32_t> colx;
+    std::vector<uint4> stn;
     std::vector<double> xs;
     if (p.precision == PD_FP32_SPLIT) {
         // per grain: h, h^2 as a float-float pair, V as float
@@ -1102,6 +1105,43 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
                 colx[b] = (uint32_t)j | ((uint32_t)n << pd::kColBits);
             }
         if (nb) PD_CUDA(cudaMemcpyAsync(d.colx, colx.data(), 4 * nb, cudaMemcpyHostToDevice, s));
+        // lattice stencil of the bonds (horizons with exactly the 24 offsets of the 5 x 5 block)
+        const double hr2 = p.horizon_ratio * p.horizon_ratio;
+        c->kp.stencil = (hr2 > 8.0 && hr2 <= 9.0) ? 1 : 0;
+        if (c->kp.stencil) {
+            stn.assign(N, make_uint4(pd::kStnIrregular, 0u, 0u, 0u));
+            size_t irregular = 0;
+            for (size_t x = 0; x < N; ++x) {
+                uint32_t mask = 0;
+                int D[5] = {0, 0, 0, 0, 0};
+                bool seen[5] = {false, false, false, false, false}, ok = true;
+                int last = -1;
+                for (int b = c->row_ptr[x]; b < c->row_ptr[x + 1] && ok; ++b) {
+                    const int j = c->col[b];
+                    const int di = c->lat[2 * (size_t)j] - c->lat[2 * x], dj = c->lat[2 * (size_t)j + 1] - c->lat[2 * x + 1];
+                    if (di < -2 || di > 2 || dj < -2 || dj > 2) { ok = false; break; }
+                    const int oo = (dj + 2) * 5 + (di + 2), o = oo < 12 ? oo : oo - 1;
+                    const long long base = (long long)j - (long long)x - di;
+                    if (o <= last) ok = false;                      // CSR order must be the offset order
+                    last = o;
+                    if (!seen[dj + 2]) { seen[dj + 2] = true; D[dj + 2] = (int)std::max<long long>(-40000, std::min<long long>(40000, base)); }
+                    else if (D[dj + 2] != base) ok = false;
+                    if (dj == 0 && base != 0) ok = false;
+                    if (D[dj + 2] < -32768 || D[dj + 2] > 32767) ok = false;
+                    mask |= 1u << o;
+                }
+                if (!ok) {
+                    stn[x] = make_uint4(pd::kStnIrregular, 0u, 0u, (unsigned)c->row_ptr[x]);
+                    ++irregular;
+                    continue;
+                }
+                auto u16 = [](int v) { return (uint32_t)(uint16_t)(int16_t)v; };
+                stn[x] = make_uint4(mask, u16(D[0]) | (u16(D[1]) << 16), u16(D[3]) | (u16(D[4]) << 16),
+                                    (unsigned)c->row_ptr[x]);
+            }
+            c->stn_irregular = irregular;
+            PD_CUDA(cudaMemcpyAsync(d.stn, stn.data(), 16 * N, cudaMemcpyHostToDevice, s));
+        }
         // X + the aggregate's shift (FP64): the FP32-split positions are (X + shift) + u
         xs.resize(2 * N);
         for (size_t x = 0; x < N; ++x) {
@@ -1119,10 +1159,12 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
             gcf[4 * g + 3] = (float)c->g_rho[g];
         }
         PD_CUDA(cudaMemcpyAsync(d.gc, gcf.data(), 16 * G, cudaMemcpyHostToDevice, s));
-        invm.resize(G);
-        for (size_t g = 0; g < G; ++g) invm[g] = 1.0 / (c->g_rho[g] * c->V[c->g_start[g]]);
-        PD_CUDA(cudaMemcpyAsync(d.g_invm, invm.data(), 8 * G, cudaMemcpyHostToDevice, s));
     }
+    // per grain 1 / (rho V): the update multiplies by it (an FP64 division per
+    // node and component costs about nine FP64 operations on GB300)
+    invm.resize(G);
+    for (size_t g = 0; g < G; ++g) invm[g] = 1.0 / (c->g_rho[g] * c->V[c->g_start[g]]);
+    PD_CUDA(cudaMemcpyAsync(d.g_invm, invm.data(), 8 * G, cudaMemcpyHostToDevice, s));
     c->vcur = 0;
     c->steps_done = 0;
     c->state = 3;

@@ -25,6 +25,16 @@ constexpr size_t kPrefetchMaxBytes = 24u << 20;
 // lattice offset di^2 + dj^2 (< 16 for horizons up to 4 h) in the top bits.
 constexpr int kColBits = 28;
 constexpr uint32_t kColMask = (1u << kColBits) - 1u;
+// FP32-split bond stencil (horizon 3 h: the 24 offsets (di, dj) of the 5 x 5
+// lattice block without its centre, numbered o = 0..23 in (dj, di) order).
+// Nodes of a grain are numbered row by row (j, then i), so for a node whose
+// neighbour rows are contiguous runs near it the neighbour at offset o is node
+// x + di + D[dj], and the CSR order of its bonds is the order of o.  Per node:
+//   x: bit o = bond at offset o exists (reference list), bit 31 = irregular
+//      (a row with a gap near the node: its bonds are read from the CSR columns)
+//   y: D[-2] | D[-1] << 16, z: D[1] | D[2] << 16 (16-bit two's complement)
+//   w: first bond of the node's CSR row
+constexpr uint32_t kStnIrregular = 0x80000000u;
 // Threads per block of the node-parallel multi-kernel path.
 constexpr int kBlock = 128;
 // Scan tile: threads x items per thread.
@@ -95,6 +105,7 @@ struct DevPtrs {
     float4 *pq;         // shifted position (p + shift) as a float-float pair: (hi x, hi y, lo x, lo y)
     double2 *xs;        // X + the aggregate's shift (FP64)
     uint32_t *colx;     // bond columns with the lattice offset n = di^2 + dj^2 in the top 4 bits
+    uint4 *stn;         // lattice stencil of every node's bonds (see kStnIrregular), when KParams::stencil
     float4 *gc;         // per grain: (c_w, s0, eps, rho) as floats
     double *g_invm;     // per grain: 1 / (rho V)
     int4 *wall_cell;    // per aggregate: hash-grid cells of its walls x_lo, x_hi, y_lo, y_hi at the current time
@@ -149,6 +160,7 @@ struct KParams {
     int split;          // 1: lane sums through global memory and a separate epilogue pass
     int fp32;           // precision of the force phase
     int pf_bonds;       // > 0: prefetch the force phase's read-only arrays (this many bonds) into L2
+    int stencil;        // FP32 split: bonds from the lattice stencil (DevPtrs::stn) instead of the columns
     // surrogate
     int sur;            // surrogate on
     int n_modes;        // modes of the basis (32)

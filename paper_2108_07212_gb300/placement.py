@@ -144,12 +144,15 @@ def security_disks(lo, hi, spacing: float, rc_ratio: float, h_ratio: int, r_min:
 
 
 def jammed_settling(box=(20e-3, 30e-3), spacing: float = 3.2e-3, h_ratio: int = 15, mix=None, seed: int = 1,
-                    n_steps: int = 20_000, dt: float = 5e-8, r_min_ratio: float = 0.15, **over):
+                    n_steps: int = 50_000, dt: float = 2e-8, r_min_ratio: float = 0.15, **over):
     """The settling workload with the shape-agnostic jammed placement in place
     of random sequential addition: every security disk of the box holds one
     grain (shapes cycled through the settling mix), of radius equal to the
     disk's, lattice spacing R / h_ratio, rotated at random (step 6).  Disks
-    smaller than r_min_ratio * spacing are left empty."""
+    smaller than r_min_ratio * spacing are left empty.  The smallest grains
+    (R ~ 0.5 mm, h ~ 32 um) make the bond and contact stiffness those of the
+    finest lattices here, so dt = 2e-8 s, as for the other h ~ 35 um
+    workloads (at 5e-8 s the first contacts blow up)."""
     from . import inputs as I
 
     mix = I.MIX_SETTLING if mix is None else mix
