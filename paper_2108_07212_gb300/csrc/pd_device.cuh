@@ -527,6 +527,24 @@ __device__ __forceinline__ ff to_ff(double x) {
     return r;
 }
 
+// Exact widening of a float to a double by bit operations: a conversion
+// instruction occupies GB300's 2-lane FP64 pipe like an FP64 operation.
+// Subnormal floats become zero; inf and NaN stay inf and NaN.
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(b >> 31) << 63;
+    if (e == 0u) return __longlong_as_double((long long)sign);
+    const unsigned long long ed = e == 255u ? 2047ull : (unsigned long long)(e + 896u);
+    return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+// The float part of a double's float-float split (its top 24 significand bits).
+__device__ __forceinline__ float d2f_hi_bits(double x) {
+    float hi, lo;
+    dbl_to_ff(x, hi, lo);
+    return hi;
+}
+
 // ---------------------------------------------------------------------------
 // per-node phases
 
@@ -552,8 +570,10 @@ __device__ __forceinline__ bool predict_node(const DevPtrs &d, const KParams &k,
         }
         const double2 xs = __ldg(&d.xs[i]);
         const double qx = xs.x + u.x, qy = xs.y + u.y;
-        const float hx = (float)qx, hy = (float)qy;
-        const float4 q = make_float4(hx, hy, (float)(qx - (double)hx), (float)(qy - (double)hy));
+        // float-float split by bit operations (no FP64-pipe conversions)
+        float4 q;
+        dbl_to_ff(qx, q.x, q.z);
+        dbl_to_ff(qy, q.y, q.w);
         d.pq[i] = q;
         // displacement since the last rebuild from the float-float positions
         // (error ~1e-7 of the displacement, far below the trigger's margin)
@@ -573,7 +593,7 @@ __device__ __forceinline__ bool predict_node(const DevPtrs &d, const KParams &k,
     // |u - u at the last rebuild| in float: its rounding (1e-7 |u|) is far below the margin
     // (1/2 - kSkinTrigger) skin of the trigger
     const float4 r = ldm<PERSIST>(&d.sref[i]);
-    const float ex = (float)u.x - r.x, ey = (float)u.y - r.y;
+    const float ex = d2f_hi_bits(u.x) - r.x, ey = d2f_hi_bits(u.y) - r.y;
     return !(ex * ex + ey * ey <= dmax2);
 }
 
@@ -830,7 +850,8 @@ __device__ __forceinline__ void finish_node(const DevPtrs &d, const KParams &k, 
         d.v[vin ^ 1][i] = vn;
     }
     d.a[i] = make_double2(ax, ay);
-    if (!isfinite(ax) || !isfinite(ay)) atomicAdd(&d.status[PD_STATUS_NONFINITE], 1);
+    if (((__double2hiint(ax) | 0x800FFFFF) == -1) || ((__double2hiint(ay) | 0x800FFFFF) == -1))   // inf or NaN
+        atomicAdd(&d.status[PD_STATUS_NONFINITE], 1);
     if (k.store) {
         d.F[i] = make_double2(Fx, Fy);
         d.parts[i] = make_double2(Fbx, Fby);
@@ -849,7 +870,7 @@ template <bool PERSIST>
 __device__ __forceinline__ void finish_node32_total(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
                                                     double2 vi, float fx, float fy, bool walls, double Fwx,
                                                     double Fwy, double inv_m) {
-    double Fx = (double)fx, Fy = (double)fy;
+    double Fx = f2d_bits(fx), Fy = f2d_bits(fy);
     if (walls) {
         Fx += Fwx;
         Fy += Fwy;
@@ -860,8 +881,11 @@ __device__ __forceinline__ void finish_node32_total(const DevPtrs &d, const KPar
         d.v[vin ^ 1][i] = make_double2(fma(k.half_dt, ao.x + ax, vi.x), fma(k.half_dt, ao.y + ay, vi.y));
     }
     d.a[i] = make_double2(ax, ay);
-    if (!isfinite(fx) || !isfinite(fy) || (walls && (!isfinite(Fwx) || !isfinite(Fwy))))
-        atomicAdd(&d.status[PD_STATUS_NONFINITE], 1);
+    // finiteness from the exponent bits (no FP64 compare)
+    const bool bad = ((__float_as_uint(fx) | 0x807FFFFFu) == 0xFFFFFFFFu) ||
+                     ((__float_as_uint(fy) | 0x807FFFFFu) == 0xFFFFFFFFu) ||
+                     (walls && (((__double2hiint(Fwx) | 0x800FFFFF) == -1) || ((__double2hiint(Fwy) | 0x800FFFFF) == -1)));
+    if (bad) atomicAdd(&d.status[PD_STATUS_NONFINITE], 1);
 }
 
 template <int LANES, class T>
@@ -1012,8 +1036,8 @@ __device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k,
             Fny += gy;
         }
     }
-    out.bx = lane_sum<LANES>((double)Fbx.hi + (double)Fbx.lo);
-    out.by = lane_sum<LANES>((double)Fby.hi + (double)Fby.lo);
+    out.bx = lane_sum<LANES>(f2d_bits(Fbx.hi) + f2d_bits(Fbx.lo));
+    out.by = lane_sum<LANES>(f2d_bits(Fby.hi) + f2d_bits(Fby.lo));
     out.sx = lane_sum<LANES>(Fsx);
     out.sy = lane_sum<LANES>(Fsy);
     out.nx = lane_sum<LANES>(Fnx);
@@ -1041,33 +1065,48 @@ __device__ __forceinline__ void node_epilogue64(const DevPtrs &d, const KParams 
                                __ldg(&d.g_invm[gi]));
 }
 
-// FP32-split bond force of one intact bond to a neighbour at qj (float-float
-// shifted position), lattice offset code nn = di^2 + dj^2: 0 = force added to
-// (Fbx, Fby), 1 = broken at this evaluation, 2 = stretch in the guard band
-// around s0 (decided in FP64 after the loop).
-__device__ __forceinline__ int bond_force32(float4 qj, float2 phi, float2 pli, float nn, float4 gq, float cw,
-                                            float s0, float s0_lo, float s0_hi, float eps, float VV, int micro,
-                                            float &Fbx, float &Fby) {
+// FP32-split geometry of one bond to a neighbour at qj (float-float shifted
+// position), lattice offset code nn = di^2 + dj^2 and sqn = sqrt(nn):
+// num = |d|^2 - |xi|^2 (float-float difference, |xi|^2 = n h^2 exact to
+// float-float), den = |xi| (L + |xi|), so that s = num / den.  Returns 0 =
+// intact, 1 = broken at this evaluation (|s| > s0), 2 = |s| in the guard band
+// around s0 (decided in FP64 after the loop).  The tests compare |num| with
+// s0 den: no division.
+struct BondGeom32 {
+    float dx, dy, L, num, den, xi;
+};
+__device__ __forceinline__ int bond_classify32(float4 qj, float2 phi, float2 pli, float nn, float sqn, float4 gq,
+                                               float s0, float s0_lo, float s0_hi, BondGeom32 &g) {
     const float dxh = __fsub_rn(qj.x, phi.x), dxl = qj.z - pli.x;
     const float dyh = __fsub_rn(qj.y, phi.y), dyl = qj.w - pli.y;
     float L2h, L2l;
     len2_ff(dxh, dxl, dyh, dyl, L2h, L2l);
     float q, eq;
     two_prod(nn, gq.y, q, eq);                           // |xi|^2 = n h^2
-    const float num = ff_diff(L2h, L2l, q, eq + nn * gq.z);
-    const float xi = gq.x * sqrt_approx(nn);
-    const float L = sqrt_approx(L2h);
-    const float s = __fdividef(num, xi * (L + xi));
-    const float as = fabsf(s);
-    // near the threshold the FP64 path decides, after the loop (its FP64
-    // registers stay out of the hot loop)
-    if (as > s0_lo && as < s0_hi) return 2;
-    if (as > s0) return 1;
-    const float cws = (micro ? cw * (1.0f - xi / eps) : cw) * s;
-    const float qf = __fdividef(cws * VV, L);
-    Fbx += qf * (dxh + dxl);
-    Fby += qf * (dyh + dyl);
-    return 0;
+    g.num = ff_diff(L2h, L2l, q, eq + nn * gq.z);
+    g.xi = gq.x * sqn;
+    g.L = sqrt_approx(L2h);
+    g.den = g.xi * (g.L + g.xi);
+    g.dx = dxh + dxl;
+    g.dy = dyh + dyl;
+    const float an = fabsf(g.num);
+    if (an > s0_lo * g.den && an < s0_hi * g.den) return 2;
+    return an > s0 * g.den ? 1 : 0;
+}
+
+// Adds the bond force c_w w V^2 s (d / L) of an intact bond (w = 1 - |xi| / eps
+// for the conic micromodulus).
+__device__ __forceinline__ void bond_add32(const BondGeom32 &g, float cw, float eps, float VV, int micro, float &Fbx,
+                                           float &Fby) {
+    const float c = micro ? cw * (1.0f - __fdividef(g.xi, eps)) : cw;
+    const float qf = __fdividef(c * VV * g.num, g.den * g.L);
+    Fbx += qf * g.dx;
+    Fby += qf * g.dy;
+}
+
+// sqrt(di^2 + dj^2) of the stencil offsets (compile-time for a fixed offset)
+__host__ __device__ constexpr float stn_sqrt_n(int n) {
+    return n == 1 ? 1.0f : (n == 2 ? 1.41421356f : (n == 4 ? 2.0f : (n == 5 ? 2.23606798f : 2.82842712f)));
 }
 
 // Offset o (0..23) of the bond stencil: the 5 x 5 lattice block without its
@@ -1156,13 +1195,12 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
                 if (!live[m]) continue;
                 const int o = (m0 + m) * LANES + lane;
                 const int dj = stn_dj(o), di = stn_di(o);
-                const int r = bond_force32(qb[m], phi, pli, (float)(di * di + dj * dj), gq, cw, s0, s0_lo, s0_hi, eps,
-                                           VV, k.micro, Fbx, Fby);
-                if (r == 2) pending = true;
-                if (r == 1) {
-                    const int kk = __popc(mask & ((1u << o) - 1u));
-                    atomicOr(bw, 1u << kk);
-                }
+                const int n = di * di + dj * dj;
+                BondGeom32 bg;
+                const int r = bond_classify32(qb[m], phi, pli, (float)n, stn_sqrt_n(n), gq, s0, s0_lo, s0_hi, bg);
+                if (r == 0) bond_add32(bg, cw, eps, VV, k.micro, Fbx, Fby);
+                else if (r == 2) pending = true;
+                else atomicOr(bw, 1u << __popc(mask & ((1u << o) - 1u)));
             }
         }
     }
@@ -1187,9 +1225,11 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
             const int kk = b - r0;
             if (cb[m] == 0xFFFFFFFFu || ((wb[m] >> (kk & 31)) & 1u)) continue;
             const float nn = (float)(cb[m] >> kColBits);         // lattice offset di^2 + dj^2
-            const int r = bond_force32(qb[m], phi, pli, nn, gq, cw, s0, s0_lo, s0_hi, eps, VV, k.micro, Fbx, Fby);
-            if (r == 2) pending = true;
-            if (r == 1) atomicOr(&bw[kk >> 5], 1u << (kk & 31));
+            BondGeom32 bg;
+            const int r = bond_classify32(qb[m], phi, pli, nn, sqrt_approx(nn), gq, s0, s0_lo, s0_hi, bg);
+            if (r == 0) bond_add32(bg, cw, eps, VV, k.micro, Fbx, Fby);
+            else if (r == 2) pending = true;
+            else atomicOr(&bw[kk >> 5], 1u << (kk & 31));
         }
     }
     if (pending) {
@@ -1201,19 +1241,11 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
             const uint32_t c = __ldg(&d.colx[b]);
             const int j = (int)(c & kColMask);
             const float4 qj = ldm<PERSIST>(&d.pq[j]);
-            const float dxh = __fsub_rn(qj.x, phi.x), dxl = qj.z - pli.x;
-            const float dyh = __fsub_rn(qj.y, phi.y), dyl = qj.w - pli.y;
-            float L2h, L2l;
-            len2_ff(dxh, dxl, dyh, dyl, L2h, L2l);
             const float nn = (float)(c >> kColBits);
-            float q, eq;
-            two_prod(nn, gq.y, q, eq);
-            const float num = ff_diff(L2h, L2l, q, eq + nn * gq.z);
-            const float xi = gq.x * sqrt_approx(nn);
-            const float L = sqrt_approx(L2h);
-            const float s = __fdividef(num, xi * (L + xi));
-            const float as = fabsf(s);
-            if (!(as > s0_lo && as < s0_hi)) continue;
+            // the same classification as the loop (stencil: sqrt(n) from the table)
+            const float sqn = stencil ? stn_sqrt_n((int)nn) : sqrt_approx(nn);
+            BondGeom32 bg;
+            if (bond_classify32(qj, phi, pli, nn, sqn, gq, s0, s0_lo, s0_hi, bg) != 2) continue;
             const double2 pi = position64<PERSIST>(d, ii), pj = position64<PERSIST>(d, j);
             const double ddx = __dsub_rn(pj.x, pi.x), ddy = __dsub_rn(pj.y, pi.y);
             const double L64 = __dsqrt_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)));
@@ -1222,10 +1254,7 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
                 atomicOr(&bw[kk >> 5], 1u << (kk & 31));
                 continue;
             }
-            const float cws = (k.micro ? cw * (1.0f - xi / eps) : cw) * s;
-            const float qf = __fdividef(cws * VV, L);
-            Fbx += qf * (dxh + dxl);
-            Fby += qf * (dyh + dyl);
+            bond_add32(bg, cw, eps, VV, k.micro, Fbx, Fby);
         }
     }
     __syncwarp();
