@@ -250,8 +250,28 @@ int pd_eval_forces(pd_ctx *ctx);
 int pd_diagnostics(pd_ctx *ctx, double *out);
 
 /* Copy the device status word into out[PD_STATUS_COUNT] (waits) and return
- * PD_OK, or the first error code it implies (PD_ENUMERIC, PD_EOVERFLOW). */
+ * PD_OK, or the first error code it implies (PD_ENUMERIC, PD_EOVERFLOW,
+ * PD_ETIMEOUT: a bounded device wait -- a grid barrier of the persistent
+ * kernel or a tensor-core wait of the surrogate -- gave up; the surrogate's
+ * results of that step are invalid and it is off from then on). */
 int pd_status(pd_ctx *ctx, int32_t *out);
+
+/* Zero the status counters, the surrogate networks' error word and the grid
+ * barrier of the persistent kernel, and make the next step rebuild the contact
+ * candidate lists (waits for the stream).  After PD_ETIMEOUT the step that gave
+ * up is partly done: restore DISP, VEL, ACC, BROKEN and STEP from a copy, then
+ * clear the status, before stepping on.  Errors: PD_ESTATE, PD_ECUDA. */
+int pd_clear_status(pd_ctx *ctx);
+
+/* Test hook of the bounded waits of the persistent kernel (pd_set_path modes 1
+ * and 3, surrogate off).  withhold_block >= 0: that block of every later
+ * launch returns before its first grid-barrier arrival, so the other blocks'
+ * waits run out after max_spins polls of about 64 ns each, set
+ * status[PD_STATUS_TIMEOUT] and return; no device fault is involved.
+ * withhold_block = -1 and max_spins = 0 restore the default (no block
+ * withheld, about 1 s of polling).  Re-captures the step graphs.
+ * Errors: PD_EINVAL (withhold_block < -1, max_spins < 0), PD_ESTATE, PD_ECUDA. */
+int pd_set_wait_test(pd_ctx *ctx, int withhold_block, long long max_spins);
 
 /* Scalar facts of the context (out has 15 slots): out[0] N, out[1] directed
  * bonds, out[2] grains, out[3] h_min, out[4] R_c, out[5] K_n (aggregate 0),

@@ -35,7 +35,7 @@ SYMBOLS = ("pd_last_error", "pd_create", "pd_destroy", "pd_mesh_grains", "pd_bui
            "pd_mlp_loss_grad", "pd_mlp_train_step", "pd_surrogate_setup", "pd_surrogate_set_mlp",
            "pd_surrogate_enable", "pd_surrogate_sample", "pd_surrogate_stats", "pd_surrogate_inspect",
            "pd_diagnostics_noalloc", "pd_observables", "pd_set_materials", "pd_check_sqrt",
-           "pd_surrogate_basis")
+           "pd_surrogate_basis", "pd_clear_status", "pd_set_wait_test")
 
 
 class PdParams(ctypes.Structure):
@@ -81,6 +81,8 @@ def load():
             L.pd_eval_forces.argtypes = [vp]
             L.pd_diagnostics.argtypes = [vp, vp]
             L.pd_status.argtypes = [vp, vp]
+            L.pd_clear_status.argtypes = [vp]
+            L.pd_set_wait_test.argtypes = [vp, ip, ctypes.c_longlong]
             L.pd_info.argtypes = [vp, vp]
             L.pd_set_timing.argtypes = [vp, ip]
             L.pd_kernel_times.argtypes = [vp, vp]
@@ -310,6 +312,15 @@ class Simulation:
         out = np.zeros(STATUS_COUNT, dtype=np.int32)
         rc = load().pd_status(self._ctx, _ptr(out))
         return rc, out
+
+    def clear_status(self):
+        """Zero the status words and the grid barrier; the next step rebuilds the
+        contact candidate lists (pd_clear_status)."""
+        _check(load().pd_clear_status(self._ctx))
+
+    def set_wait_test(self, withhold_block: int = -1, max_spins: int = 0):
+        """Test hook of the persistent kernel's bounded barrier waits (pd_set_wait_test)."""
+        _check(load().pd_set_wait_test(self._ctx, int(withhold_block), int(max_spins)))
 
     def set_timing(self, enable: bool):
         _check(load().pd_set_timing(self._ctx, 1 if enable else 0))

@@ -1124,6 +1124,14 @@ __host__ __device__ constexpr int stn_dj(int o) { return (o + (o >= 12 ? 1 : 0))
 // contact overlap R_c - |d| = (R_c^2 - |d|^2) / (R_c + |d|) keep ~1e-7 relative
 // accuracy.  Bonds whose FP32 stretch lies within guard * s0 of s0 are
 // re-decided with the FP64 stretch, so break decisions are the FP64 ones.
+// The learned surrogate is used only while none of its bounded tensor-core
+// waits has given up (status[PD_STATUS_TIMEOUT], the networks' error word): a
+// step in which one gives up still runs on the surrogate in the kernels that
+// started before it, every later step uses the full bond kernel.
+__device__ __forceinline__ bool sur_healthy(const DevPtrs &d) {
+    return __ldcg(&d.status[PD_STATUS_TIMEOUT]) == 0 && (d.mlp_err == nullptr || __ldcg(d.mlp_err) == 0);
+}
+
 template <bool PERSIST, int LANES>
 __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k, int i, int lane, bool active,
                                              int vin, Sums32 &out) {
@@ -1160,7 +1168,7 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
     bool sur = false, judge = false;
     if constexpr (!PERSIST) {
         if (k.sur && active) {
-            sur = d.sur_active[gi] != 0;
+            sur = d.sur_active[gi] != 0 && sur_healthy(d);
             judge = (*d.step) % k.judge_every == 0;
         }
     }
@@ -1177,6 +1185,8 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
         const int Dm2 = (int)(short)(st.y & 0xFFFFu), Dm1 = (int)(short)(st.y >> 16);
         const int Dp1 = (int)(short)(st.z & 0xFFFFu), Dp2 = (int)(short)(st.z >> 16);
         constexpr int kPerLane = (24 + LANES - 1) / LANES;
+        // fully unrolled: offsets, lattice codes and sqrt(n) are constants for one
+        // lane per node (a loop over the batches was 30 % slower on the compaction)
 #pragma unroll
         for (int m0 = 0; m0 < kPerLane; m0 += kBondBatch) {
             float4 qb[kBondBatch];
@@ -1339,7 +1349,7 @@ __device__ __forceinline__ void node_epilogue32(const DevPtrs &d, const KParams 
         // learned modal surrogate: between judge steps an active grain's bond force
         // is R(theta + phi) Phi f E h (expanded on the tensor cores), in place of
         // the bond loop the sums skipped
-        if (k.sur && d.sur_active[gi] && (*d.step) % k.judge_every != 0) {
+        if (k.sur && d.sur_active[gi] && (*d.step) % k.judge_every != 0 && sur_healthy(d)) {
             const float2 sf = d.sur_f[i];                     // Phi f, lattice frame, units of E h
             const float2 rot = d.sur_rot[gi];
             const float Eh = k.E * __ldg(&d.gq[gi]).x;

@@ -424,7 +424,6 @@ size_t layout(pd_ctx *c, char *base) {
         carve(base, off, d.sur_fc, G);
         carve(base, off, d.sur_active, G);
         carve(base, off, d.sur_rot, G);
-        carve(base, off, d.sur_phi, G);
         carve(base, off, d.sur_x, G * M);
         carve(base, off, d.sur_y, G * M);
         carve(base, off, d.sur_fb, N);
@@ -443,7 +442,7 @@ size_t layout(pd_ctx *c, char *base) {
         d.mlp_work = nullptr;
         d.mlp_err = nullptr;
         d.basis = d.sur_x = d.sur_y = d.sur_err = d.sur_maxs = d.sur_qs = d.sur_fs = d.sur_lambda = nullptr;
-        d.g_theta = d.sur_phi = nullptr;
+        d.g_theta = nullptr;
         d.sur_fc = nullptr;
         d.sur_rot = d.sur_fb = nullptr;
     }
@@ -458,17 +457,20 @@ int check_ctx(pd_ctx *c, int min_state) {
 
 // Surrogate phases before the force kernel: co-rotated local deformation of
 // the active grains, its projection on the basis (tensor cores), every
-// template's network on its batch of grains, f = -Lambda q + net(q), and the
-// expansion of f to nodal bond forces (tensor cores).
+// template's network on its batch of grains with f = -Lambda q + net(q) in
+// its output epilogue, and the expansion of f to nodal bond forces (tensor
+// cores).
 cudaError_t record_surrogate(pd_ctx *c, cudaStream_t s) {
     cudaError_t e;
+    // with 32 modes the networks subtract Lambda q on output themselves
+    const bool fused = c->sur_modes == PD_MLP_OUT;
     if ((e = pd::launch_sur_frame(c->d, c->kp, 0, s)) != cudaSuccess) return e;
     if ((e = pd::launch_sur_project_tc(c->d, c->kp, s)) != cudaSuccess) return e;
     if ((e = pd::launch_sur_reduce(c->d, c->kp, s)) != cudaSuccess) return e;
     if ((e = pd::launch_mlp_grouped(c->d.mlp_refs, c->d.mlp_work, (int)c->mlp_work.size(), c->d.sur_x, c->d.sur_y,
                                     c->d.mlp_err, s)) != cudaSuccess)
         return e;
-    if ((e = pd::launch_sur_combine(c->d, c->kp, s)) != cudaSuccess) return e;
+    if (!fused && (e = pd::launch_sur_combine(c->d, c->kp, s)) != cudaSuccess) return e;
     return pd::launch_sur_expand_tc(c->d, c->kp, s);
 }
 
@@ -967,6 +969,8 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     k.n_proj_work = (int)c->proj_work.size();
     k.n_exp_work = (int)c->exp_work.size();
     k.n_rows = (int)c->slot_grain.size();
+    k.bar_spins = pd::kBarrierSpins;
+    k.withhold_block = -1;
     k.micro = p.micromodulus;
     k.store = p.store_parts ? 1 : 0;
     k.lanes = p.lanes == 0 ? 4 : p.lanes;
@@ -1385,7 +1389,38 @@ int pd_status(pd_ctx *c, int32_t *out) {
     if (out) std::memcpy(out, st, sizeof(st));
     if (st[PD_STATUS_NONFINITE]) return fail(PD_ENUMERIC, "non-finite acceleration");
     if (st[PD_STATUS_OVERFLOW]) return fail(PD_EOVERFLOW, "contact candidate overflow");
+    int mlp_err = 0;
+    if (c->d.mlp_err) {
+        PD_CUDA(cudaMemcpy(&mlp_err, c->d.mlp_err, sizeof(int), cudaMemcpyDeviceToHost));
+    }
+    if (st[PD_STATUS_TIMEOUT] || mlp_err)
+        return fail(PD_ETIMEOUT, "a bounded device wait gave up (the surrogate is off from then on)");
     return PD_OK;
+}
+
+int pd_clear_status(pd_ctx *c) {
+    if (int r = check_ctx(c, 3)) return r;
+    const pd::DevPtrs &d = c->d;
+    cudaStream_t s = c->stream;
+    PD_CUDA(cudaMemsetAsync(d.status, 0, sizeof(int) * PD_STATUS_COUNT, s));
+    if (d.mlp_err) PD_CUDA(cudaMemsetAsync(d.mlp_err, 0, sizeof(int), s));
+    PD_CUDA(cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), s));
+    PD_CUDA(cudaMemsetAsync(d.pred_done, 0, sizeof(unsigned), s));
+    // a step that gave up inside a rebuild leaves bucket counts behind; they are
+    // zero between rebuilds, and the next step rebuilds the candidate lists
+    PD_CUDA(cudaMemsetAsync(d.count, 0, sizeof(int) * c->T, s));
+    PD_CUDA(cudaMemsetAsync(d.rebuild, 1, sizeof(int), s));
+    PD_CUDA(cudaStreamSynchronize(s));
+    return PD_OK;
+}
+
+int pd_set_wait_test(pd_ctx *c, int withhold_block, long long max_spins) {
+    if (int r = check_ctx(c, 3)) return r;
+    if (withhold_block < -1) return fail(PD_EINVAL, "withhold_block must be -1 or a block index");
+    if (max_spins < 0) return fail(PD_EINVAL, "negative spin limit");
+    c->kp.withhold_block = withhold_block;
+    c->kp.bar_spins = max_spins == 0 ? pd::kBarrierSpins : max_spins;
+    return capture_all(c);
 }
 
 int pd_set_materials(pd_ctx *c, int n_mat, const double *props, const int32_t *grain_material) {
@@ -1615,6 +1650,9 @@ int pd_surrogate_set_mlp(pd_ctx *c, int tmpl, pd_mlp *mlp) {
     if (tmpl < 0 || tmpl >= c->n_tmpl) return fail(PD_EINVAL, "template out of range");
     pd::MlpRef ref{};
     if (mlp && pd::mlp_ref(mlp, &ref) != PD_OK) return fail(PD_ESTATE, "network not bound to device memory");
+    // with 32 modes the linear modal part -Lambda q is applied in the network's
+    // output epilogue (no separate combination kernel)
+    if (mlp && c->sur_modes == PD_MLP_OUT) ref.lin = c->d.sur_lambda + (size_t)tmpl * PD_MLP_OUT;
     c->sur_mlp[tmpl] = mlp;
     // device table of the networks and the inference tiles (template, first row, end row)
     PD_CUDA(cudaMemcpyAsync(c->d.mlp_refs + tmpl, &ref, sizeof(ref), cudaMemcpyHostToDevice, c->stream));

@@ -135,7 +135,6 @@ struct DevPtrs {
     float4 *sur_fc;     // per grain: h as a float-float pair (hi, lo), centroid of its lattice indices (i, j)
     int *sur_active;    // 1 while the grain is advanced by the surrogate
     float2 *sur_rot;    // cos, sin of (theta + phi): lattice frame -> world
-    double *sur_phi;    // co-rotation angle phi of the current step
     float *sur_x;       // network input rows (modal coefficients / h)
     float *sur_y;       // network output rows (modal bond force / (E h))
     float2 *sur_fb;     // full bond force of surrogate nodes on judge steps
@@ -170,6 +169,10 @@ struct KParams {
     float err_tol;      // fall back when the judged relative error exceeds this
     int n_proj_work, n_exp_work;  // tensor-core tiles of the projection / expansion
     int n_rows;                   // network rows (templated grains)
+    // bounded waits of the persistent kernel: polls of a grid barrier before it
+    // gives up, and a block that withholds its arrival (-1: none; a wait test)
+    long long bar_spins;
+    int withhold_block;
 };
 
 
@@ -196,6 +199,7 @@ cudaError_t launch_sur_combine(const DevPtrs &d, const KParams &k, cudaStream_t 
 struct MlpRef {
     const void *W1, *W2, *W3;
     const float *p;
+    const float *lin;   // nullable: y = net(x) - lin (.) x (the surrogate's linear modal part, 32 values)
 };
 }  // namespace pd
 struct pd_mlp;

@@ -56,7 +56,7 @@ __device__ __forceinline__ float gelu_grad(float z) {
 __device__ __forceinline__ void fwd_tile(const __nv_bfloat16 *__restrict__ W1, const __nv_bfloat16 *__restrict__ W2,
                                          const __nv_bfloat16 *__restrict__ W3, const float *__restrict__ P,
                                          const float *__restrict__ X, float *__restrict__ Yout, int row0, int B,
-                                         int Bp, int train, const Net &n, int *err) {
+                                         int Bp, int train, const Net &n, int *err, const float *lin = nullptr) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_base;
@@ -171,7 +171,10 @@ __device__ __forceinline__ void fwd_tile(const __nv_bfloat16 *__restrict__ W1, c
                 const int c = c0 + q;
                 const float z = acc[q] + bias[c];
                 if (layer == 2) {
-                    if (row < B) Yout[(size_t)row * OUT + c] = z;
+                    // with lin: the surrogate's modal force f = net(q) - Lambda q (IN = OUT)
+                    // (x re-read from memory: indexing the register copy with the runtime
+                    // column would move it to local memory)
+                    if (row < B) Yout[(size_t)row * OUT + c] = lin ? z - lin[c] * X[(size_t)row * IN + c] : z;
                     if (train) n.Y[(size_t)row * OUT + c] = z;
                 } else {
                     if (train) (layer == 0 ? n.Z1 : n.Z2)[(size_t)row * HID + c] = z;
@@ -190,7 +193,13 @@ __device__ __forceinline__ void fwd_tile(const __nv_bfloat16 *__restrict__ W1, c
         __syncthreads();
         tc::fence_after_sync();
     }
-    if (!ok && tid == 0) atomicExch(err, 1);
+    if (!ok) {
+        // the MMAs committed on the phase that timed out may still be writing the
+        // accumulator: one more bounded wait on that phase before the columns are
+        // released (the outputs of a timed-out tile are invalid either way: err is set)
+        tc::mbar_wait(&mbar, phase ^ 1, kSpins);
+        if (tid == 0) atomicExch(err, 1);
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem_base, 128);
@@ -208,7 +217,7 @@ __global__ void __launch_bounds__(128) k_mlp_fwd_grouped(const MlpRef *__restric
     const int4 w = work[blockIdx.x];
     const MlpRef r = refs[w.x];
     fwd_tile(static_cast<const __nv_bfloat16 *>(r.W1), static_cast<const __nv_bfloat16 *>(r.W2),
-             static_cast<const __nv_bfloat16 *>(r.W3), r.p, X, Y, w.y, w.z, 0, 0, Net{}, err);
+             static_cast<const __nv_bfloat16 *>(r.W3), r.p, X, Y, w.y, w.z, 0, 0, Net{}, err, r.lin);
 }
 
 // ---------------------------------------------------------------------------
@@ -280,7 +289,13 @@ __global__ void __launch_bounds__(128) k_gemm(const __nv_bfloat16 *__restrict__ 
             }
         }
     }
-    if (!ok && tid == 0) atomicExch(err, 1);
+    if (!ok) {
+        // the MMAs committed on the phase that timed out may still be writing the
+        // accumulator: one more bounded wait on that phase before the columns are
+        // released (the outputs of a timed-out tile are invalid either way: err is set)
+        tc::mbar_wait(&mbar, phase ^ 1, kSpins);
+        if (tid == 0) atomicExch(err, 1);
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem_base, 128);
@@ -494,13 +509,14 @@ int pd::mlp_ref(pd_mlp *m, MlpRef *out) {
     out->W2 = m->n.W2;
     out->W3 = m->n.W3;
     out->p = m->n.p;
+    out->lin = nullptr;
     return PD_OK;
 }
 
 cudaError_t pd::launch_mlp_grouped(const MlpRef *refs, const int4 *work, int n_work, const float *x, float *y,
                                    int *err, cudaStream_t s) {
     if (n_work == 0) return cudaSuccess;
-    static_assert(sizeof(MlpRef) == 32, "MlpRef layout");
+    static_assert(sizeof(MlpRef) == 40, "MlpRef layout");
     pd::mlp::k_mlp_fwd_grouped<<<n_work, 128, kFwdSmem, s>>>(refs, work, x, y, err);
     return cudaGetLastError();
 }

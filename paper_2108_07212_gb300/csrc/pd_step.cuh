@@ -127,11 +127,11 @@ cudaError_t launch_force_impl(const DevPtrs &d, const KParams &k, int vin, int u
 
 // Grid barrier with a bounded wait: the last block to arrive resets the
 // arrival count and advances the generation; the others sleep-poll the
-// generation for at most kBarrierSpins rounds, then set
-// status[PD_STATUS_TIMEOUT] and report failure (the kernel then returns, so
-// the device never hangs).  Co-residency of all blocks is guaranteed by the
-// cooperative launch.
-__device__ __forceinline__ bool grid_barrier(const DevPtrs &d) {
+// generation for at most max_spins rounds (kBarrierSpins unless a test
+// shortens it), then set status[PD_STATUS_TIMEOUT] and report failure (the
+// kernel then returns, so the device never hangs).  Co-residency of all blocks
+// is guaranteed by the cooperative launch.
+__device__ __forceinline__ bool grid_barrier(const DevPtrs &d, long long max_spins) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -147,7 +147,7 @@ __device__ __forceinline__ bool grid_barrier(const DevPtrs &d) {
         } else {
             long long n = 0;
             while (*gen == g) {
-                if (++n > kBarrierSpins || *(volatile int *)&d.status[PD_STATUS_TIMEOUT]) {
+                if (++n > max_spins || *(volatile int *)&d.status[PD_STATUS_TIMEOUT]) {
                     atomicExch(&d.status[PD_STATUS_TIMEOUT], 1);
                     ok = 0;
                     break;
@@ -223,6 +223,8 @@ template <bool FP32, int LANES, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_persistent(DevPtrs d, KParams k, int vin, int nsteps) {
     __shared__ int sm[33];
     __shared__ long long s_step;
+    // wait test: the withheld block never arrives, so the others' barrier waits run out
+    if ((int)blockIdx.x == k.withhold_block) return;
     const int nthreads = gridDim.x * BLOCK;
     const int gtid = blockIdx.x * BLOCK + threadIdx.x;
     const unsigned T = k.T;
@@ -245,17 +247,17 @@ __global__ void __launch_bounds__(BLOCK) k_persistent(DevPtrs d, KParams k, int 
             __syncthreads();
             wall_cells(d, k, (double)s_step * k.dt);
         }
-        if (!grid_barrier(d)) return;
+        if (!grid_barrier(d, k.bar_spins)) return;
         if (__ldcg(d.rebuild)) {
             // R1
             for (int i = gtid; i < k.N; i += nthreads) bin_node<true>(d, k, i);
-            if (!grid_barrier(d)) return;
+            if (!grid_barrier(d, k.bar_spins)) return;
             // R2
             int part = 0;
             for (unsigned b = lo + threadIdx.x; b < hi; b += BLOCK) part += __ldcg(&d.count[b]);
             part = block_sum<BLOCK>(part, sm);
             if (threadIdx.x == 0) d.blocksums[blockIdx.x] = part;
-            if (!grid_barrier(d)) return;
+            if (!grid_barrier(d, k.bar_spins)) return;
             // R3
             int off = 0;
             for (int b = threadIdx.x; b < (int)blockIdx.x; b += BLOCK) off += __ldcg(&d.blocksums[b]);
@@ -272,30 +274,30 @@ __global__ void __launch_bounds__(BLOCK) k_persistent(DevPtrs d, KParams k, int 
                 off += tot;
             }
             if (gtid == 0) d.start[T] = k.N;
-            if (!grid_barrier(d)) return;
+            if (!grid_barrier(d, k.bar_spins)) return;
             // R4
             for (int i = gtid; i < k.N; i += nthreads) scatter_node<true>(d, k, i);
-            if (!grid_barrier(d)) return;
+            if (!grid_barrier(d, k.bar_spins)) return;
             // R5 (every block has read the flag: clear it for the next step)
             if (gtid == 0) {
                 *d.rebuild = 0;
                 atomicAdd(&d.status[PD_STATUS_REBUILDS], 1);
             }
             for (int i = gtid; i < k.N; i += nthreads) build_list_node<true>(d, k, i);
-            if (!grid_barrier(d)) return;
+            if (!grid_barrier(d, k.bar_spins)) return;
         }
         // E
         if (k.split) {
             const long long total = (((long long)LANES * k.N + 31) / 32) * 32;
             for (long long t = gtid; t < total; t += nthreads) sums_node<FP32, true, LANES>(d, k, (int)(t / LANES), (int)(t % LANES), vin);
-            if (!grid_barrier(d)) return;
+            if (!grid_barrier(d, k.bar_spins)) return;
             for (int i = gtid; i < k.N; i += nthreads) epilogue_node<FP32, true>(d, k, i, vin, 1);
         } else {
             for (int node0 = blockIdx.x * (BLOCK / LANES); node0 < k.N; node0 += gridDim.x * (BLOCK / LANES))
                 force_block<FP32, true, LANES, BLOCK>(d, k, node0, vin, 1);
         }
         // the end of the launch orders the last step before whatever follows
-        if (st + 1 < nsteps && !grid_barrier(d)) return;
+        if (st + 1 < nsteps && !grid_barrier(d, k.bar_spins)) return;
         vin ^= 1;
     }
 }

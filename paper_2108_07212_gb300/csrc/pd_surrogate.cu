@@ -112,7 +112,6 @@ __device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, f
 // plus the low parts), and the rotation R(-theta - phi) and the reference
 // offset h (lattice index - lattice centroid) are applied in float-float.
 __global__ void __launch_bounds__(kSurThreads) k_sur_frame(DevPtrs d, KParams k, int all_templated) {
-    __shared__ float smf[kSurThreads / 32];
     __shared__ float frame[6];
     const int g = blockIdx.x;
     const int t = d.g_tmpl[g];
@@ -150,9 +149,25 @@ __global__ void __launch_bounds__(kSurThreads) k_sur_frame(DevPtrs d, KParams k,
         sb += lx * dy - ly * dx;
       }
     }
-    const float Sx = block_sum_f(sx, smf), Sy = block_sum_f(sy, smf);
-    const float A = block_sum_f(sa, smf), Bs = block_sum_f(sb, smf);
+    // the four sums in one block reduction
+    __shared__ float4 sm4[kSurThreads / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, off);
+        sy += __shfl_xor_sync(0xffffffffu, sy, off);
+        sa += __shfl_xor_sync(0xffffffffu, sa, off);
+        sb += __shfl_xor_sync(0xffffffffu, sb, off);
+    }
+    if ((threadIdx.x & 31) == 0) sm4[threadIdx.x >> 5] = make_float4(sx, sy, sa, sb);
+    __syncthreads();
     if (threadIdx.x == 0) {
+        float Sx = 0.f, Sy = 0.f, A = 0.f, Bs = 0.f;
+        for (int w = 0; w < kSurThreads / 32; ++w) {
+            Sx += sm4[w].x;
+            Sy += sm4[w].y;
+            A += sm4[w].z;
+            Bs += sm4[w].w;
+        }
         // reference offsets X' = R(theta) h l: sum X' . p' = cos A + sin B, sum X' x p' = cos B - sin A,
         // so the best-fit phi = atan2(cos B - sin A, cos A + sin B), and the angle sum reduces to
         // (cos, sin)(theta + phi) = (A, B) / |(A, B)|: no trigonometry on the block's critical path
@@ -175,13 +190,6 @@ __global__ void __launch_bounds__(kSurThreads) k_sur_frame(DevPtrs d, KParams k,
         frame[5] = Sy / (float)n;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // the angle phi itself (state only; after the barrier, off the other threads' path)
-        const double th = d.g_theta[g];
-        double st, ct;
-        sincos(th, &st, &ct);
-        d.sur_phi[g] = atan2(ct * Bs - st * A, ct * A + st * Bs);
-    }
     const float ch = frame[0], cl = frame[1], sh = frame[2], sl = frame[3], cx = frame[4], cy = frame[5];
     const float hinv = 1.0f / fc.x;
     for (int i0 = s0 + threadIdx.x; i0 < s1; i0 += kFrameBatch * kSurThreads) {
@@ -396,8 +404,11 @@ __global__ void __launch_bounds__(128) k_sur_project_tc(DevPtrs d, KParams k) {
                 for (int q = 0; q < 16; ++q)
                     if (c0 + q < M) dst[c0 + q] = v[q];
         }
-    } else if (tid == 0) {
-        atomicAdd(&d.status[PD_STATUS_TIMEOUT], 1);
+    } else {
+        // drain the timed-out phase before the columns are released; the tile's
+        // results are invalid and the surrogate is not used from now on
+        tc::mbar_wait(&mbar, 0, kSurSpins);
+        if (tid == 0) atomicAdd(&d.status[PD_STATUS_TIMEOUT], 1);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -501,8 +512,11 @@ __global__ void __launch_bounds__(128) k_sur_expand_tc(DevPtrs d, KParams k) {
                     if (r < rows2) *reinterpret_cast<float2 *>(dst + r) = make_float2(v[q], v[q + 1]);
                 }
         }
-    } else if (tid == 0) {
-        atomicAdd(&d.status[PD_STATUS_TIMEOUT], 1);
+    } else {
+        // drain the timed-out phase before the columns are released; the tile's
+        // results are invalid and the surrogate is not used from now on
+        tc::mbar_wait(&mbar, 0, kSurSpins);
+        if (tid == 0) atomicAdd(&d.status[PD_STATUS_TIMEOUT], 1);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -517,12 +531,10 @@ __global__ void __launch_bounds__(128) k_sur_expand_tc(DevPtrs d, KParams k) {
 // of the modal bond force (what the network predicts), and the largest
 // |s| / s0 over the grain's intact bonds; a grain that exceeds the stretch
 // gate or the nodal error tolerance leaves the surrogate for good.
-__global__ void __launch_bounds__(kSurThreads) k_sur_judge(DevPtrs d, KParams k) {
+__device__ __forceinline__ void judge_grain(const DevPtrs &d, const KParams &k, int g) {
     __shared__ double smd[kSurThreads / 32];
     __shared__ float smf[kSurThreads / 32];
     __shared__ float smq[kMaxModes][kSurThreads];
-    const int g = blockIdx.x;
-    if ((*d.step) % k.judge_every != 0) return;
     if (d.g_tmpl[g] < 0 || !d.sur_active[g]) return;
     const int t = d.g_tmpl[g];
     const int s0 = d.g_start[g], s1 = d.g_start[g + 1], n = s1 - s0;
@@ -598,6 +610,22 @@ __global__ void __launch_bounds__(kSurThreads) k_sur_judge(DevPtrs d, KParams k)
     }
 }
 
+// One block per grain in a grid stride (the launch is in every step's graph;
+// between judge steps it returns at once).
+__global__ void __launch_bounds__(kSurThreads) k_sur_judge(DevPtrs d, KParams k) {
+    if (!sur_healthy(d)) {
+        // a tensor-core wait gave up: every grain leaves the surrogate
+        if (threadIdx.x == 0)
+            for (int g = blockIdx.x; g < k.G; g += gridDim.x) d.sur_active[g] = 0;
+        return;
+    }
+    if ((*d.step) % k.judge_every != 0) return;
+    for (int g = blockIdx.x; g < k.G; g += gridDim.x) {
+        judge_grain(d, k, g);
+        __syncthreads();          // shared scratch reused by the next grain
+    }
+}
+
 // f = -Lambda q + net(q), in place in the network output rows.
 __global__ void k_sur_combine(DevPtrs d, KParams k) {
     const int g = blockIdx.x;
@@ -650,7 +678,7 @@ cudaError_t launch_sur_expand_tc(const DevPtrs &d, const KParams &k, cudaStream_
 }
 
 cudaError_t launch_sur_judge(const DevPtrs &d, const KParams &k, cudaStream_t s) {
-    k_sur_judge<<<k.G, kSurThreads, 0, s>>>(d, k);
+    k_sur_judge<<<k.G < 152 * 8 ? k.G : 152 * 8, kSurThreads, 0, s>>>(d, k);
     return cudaGetLastError();
 }
 
