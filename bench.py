@@ -191,14 +191,19 @@ def _time_oracle(probs, omp: bool, n_steps: int) -> float:
     return time.perf_counter() - t0
 
 
-def cpu_baseline(w, budget_s: float = 20.0, min_nodes: int = 200_000):
+def cpu_baseline(w, advance: int = 0, budget_s: float = 20.0, min_nodes: int = 200_000):
     """The FP64 CPU oracle, as it stands, on a bounded sample of the same
-    workload: the single-threaded build and the all-core (OpenMP) build, each
-    for about half the budget, from t = 0."""
+    workload: advanced (all-core build, untimed) to the GPU's timed window, then
+    the single-threaded build and the all-core (OpenMP) build, each for about
+    half the budget.  Returns the baseline and the oracle problems (their final
+    state serves the oracle-parity report)."""
     from oracle import oracle as O
     probs, what = oracle_sample(w, min_nodes)
     for P in probs:
+        P.omp = True
         P.init_accel()
+    if advance:
+        _time_oracle(probs, True, advance)
     n_nodes = sum(P.N for P in probs)
     per = _time_oracle(probs, False, 2) / 2
     n1 = max(3, int(0.5 * budget_s / max(per, 1e-6)))
@@ -207,10 +212,61 @@ def cpu_baseline(w, budget_s: float = 20.0, min_nodes: int = 200_000):
     n2 = max(3, int(0.5 * budget_s / max(per, 1e-6)))
     dt2 = _time_oracle(probs, True, n2)
     cores = O.threads_available()
+    first = advance + 4 + n1
     return {"value": n_nodes * n2 / dt2, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{what}: {n2} time steps with the all-core build (OpenMP, {cores} threads), FP64 C",
+            "sample": f"{what}: steps {first}..{first + n2} with the all-core build (OpenMP, {cores} threads), "
+                      f"FP64 C (steps 0..{advance} run untimed first: the GPU's window)",
             "single_thread": {"value": n_nodes * n1 / dt1, "unit": "node-steps/s", "cores": 1,
-                              "sample": f"{what}: {n1} time steps, single-threaded build"}}
+                              "sample": f"{what}: steps {advance + 2}..{advance + 2 + n1}, single-threaded build"}}, probs
+
+
+def oracle_parity(B, probs, sims, w):
+    """The GPU paths against the oracle at the oracle's own state (the end of
+    the CPU-baseline run): the oracle's displacement, velocity, acceleration,
+    broken bonds and step are pushed into each GPU context over the sample's
+    aggregates, one force evaluation runs on both sides, and the nodal forces
+    rho V (a - g) and the broken-bond sets are compared over the sample."""
+    rho = w.params["rho"]
+    g = np.array([w.params["gx"], w.params["gy"]])
+    refs = []
+    for P in probs:
+        so = {"DISP": P.u.copy(), "VEL": P.v.copy(), "ACC": P.a.copy(), "BROKEN": P.broken[: len(P.col)].copy()}
+        F, parts = P.forces(keep_broken=False)
+        refs.append((so, F, parts, P.broken[: len(P.col)].copy(), rho * P.V[:, None]))
+    out = {"sample": f"the oracle's {len(probs)} sample aggregates ({sum(P.N for P in probs)} nodes) at its "
+                     f"step {probs[0].step}", "reference": "the FP64 oracle, one force evaluation at its state"}
+    for name, S in sims.items():
+        grain = S.get("GRAIN")
+        agg = w.grain_agg[grain] if getattr(w, "grain_agg", None) is not None else np.zeros(S.N, np.int64)
+        row = S.get("ROW_PTR")
+        st = {f: S.get(f) for f in ("DISP", "VEL", "ACC", "BROKEN")}
+        ranges = []
+        for a, (so, *_rest) in enumerate(refs):
+            nodes = np.flatnonzero(agg == a)
+            n0, n1 = int(nodes[0]), int(nodes[-1]) + 1
+            assert n1 - n0 == nodes.size == len(so["DISP"])
+            b0, b1 = int(row[n0]), int(row[n1])
+            ranges.append((n0, n1, b0, b1))
+            for f in ("DISP", "VEL", "ACC"):
+                st[f][n0:n1] = so[f]
+            st["BROKEN"][b0:b1] = so["BROKEN"]
+        for f, val in st.items():
+            S.set(f, val)
+        S.set("STEP", np.array([probs[0].step], np.int64))
+        S.eval_forces()
+        acc, br = S.get("ACC"), S.get("BROKEN")
+        err, scale, dis, nbroken = 0.0, 0.0, 0, 0
+        for (n0, n1, b0, b1), (so, F_or, parts_or, br_or, m) in zip(ranges, refs):
+            Fg = m * (acc[n0:n1] - g)
+            scale = max(scale, float(np.abs(F_or).max()), float(m.max()) * max(float(np.abs(g).max()), 100.0))
+            err = max(err, float(np.abs(Fg - F_or).max()))
+            dis += int(np.sum(br[b0:b1] != br_or))
+            nbroken += int(br_or.sum())
+        out[name] = {"force_rel_err_max_norm": err / scale, "break_disagreements": dis}
+        out["force_scale_N"] = scale
+        out["broken_bonds_oracle"] = nbroken
+        out["contact_active"] = bool(any(np.abs(r[2][2]).max() > 0 for r in refs))
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -219,7 +275,8 @@ def cpu_baseline(w, budget_s: float = 20.0, min_nodes: int = 200_000):
 def run_reference(args):
     """The oracle as the reference arm: the all-core build on a bounded sample of
     the main line's workload (for the ensemble: its first aggregates, about 1M
-    nodes), W untimed and K timed steps."""
+    nodes), advanced untimed to the GPU arm's window, then W untimed and K
+    timed steps."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
@@ -229,6 +286,10 @@ def run_reference(args):
     for P in probs:
         P.omp = True
         P.init_accel()
+    # the same window as the GPU arm: steps 0..advance run untimed first
+    advance = DEFAULT_ADVANCE.get(args.workload, 0) if args.advance is None else args.advance
+    if advance:
+        _time_oracle(probs, True, advance)
     _time_oracle(probs, True, args.warmup)
     dt = _time_oracle(probs, True, args.steps)
     n_nodes = sum(P.N for P in probs)
@@ -239,7 +300,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": describe(w, None, args) | {"sample": what, "sample_nodes": int(n_nodes),
-                                                 "sample_directed_bonds": int(n_bonds)},
+                                                 "sample_directed_bonds": int(n_bonds),
+                                                 "window": f"steps {advance + args.warmup}.."
+                                                           f"{advance + args.warmup + args.steps} of the run"},
             "cpu_baseline": {"value": value, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
                              "sample": f"{what}: {args.steps} time steps after {args.warmup} warm-up steps, "
                                        f"all-core build (OpenMP, {cores} threads)"},
@@ -768,7 +831,7 @@ def run_ours(args):
                           **({"fp64": rebuilds64} if sim64 is not None else {}),
                           "note": "contact candidate lists (radius R_c + 0.1 R_c) rebuilt in a conditional graph "
                                   "node only when a node has moved 0.45 skin"},
-        "cpu_baseline": cpu_baseline(w) if not args.no_cpu else None,
+        "cpu_baseline": None,
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": _launches(tuned[key]["mode"], args.steps, rebuilds)
@@ -777,6 +840,11 @@ def run_ours(args):
     }
     if sim64 is not None:
         line["precision_report"] = _same_state_force_report(B, sim, sim64, w)
+    if not args.no_cpu:
+        line["cpu_baseline"], probs = cpu_baseline(w, advance)
+        # the GPU paths at the oracle's state of the same sample
+        line["oracle_parity"] = oracle_parity(B, probs, {key: sim} | ({"fp64": sim64} if sim64 is not None else {}), w)
+        del probs
     del sim, sim64
     torch.cuda.empty_cache()
     if world == 1 and args.legs:

@@ -705,6 +705,11 @@ __device__ __forceinline__ bool far_from_walls(const DevPtrs &d, int i, int ag) 
     return c.x - w.x >= 2 && w.y - c.x >= 2 && c.y - w.z >= 2 && w.w - c.y >= 2;
 }
 
+// The same test on a cell and wall-cell record already loaded.
+__device__ __forceinline__ bool cells_far_from_walls(int2 c, int4 w) {
+    return c.x - w.x >= 2 && w.y - c.x >= 2 && c.y - w.z >= 2 && w.w - c.y >= 2;
+}
+
 // Counting-sort scatter of node i into its bucket, with its position record.
 template <bool PERSIST>
 __device__ __forceinline__ void scatter_node(const DevPtrs &d, const KParams &k, int i) {
@@ -866,26 +871,42 @@ __device__ __forceinline__ void finish_node(const DevPtrs &d, const KParams &k, 
 // force in FP64 where there is one, then a = F (1 / m) + g and the
 // velocity-Verlet update in FP64 with fused multiply-adds (the fewest FP64
 // operations on GB300's narrow FP64 pipe).
+// (ao: the previous acceleration, loaded by the caller with the node's other
+// independent loads)
 template <bool PERSIST>
 __device__ __forceinline__ void finish_node32_total(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
-                                                    double2 vi, float fx, float fy, bool walls, double Fwx,
-                                                    double Fwy, double inv_m) {
+                                                    double2 vi, double2 ao, float fx, float fy, bool walls,
+                                                    double Fwx, double Fwy, double inv_m) {
     double Fx = f2d_bits(fx), Fy = f2d_bits(fy);
     if (walls) {
         Fx += Fwx;
         Fy += Fwy;
     }
     const double ax = fma(Fx, inv_m, k.gx), ay = fma(Fy, inv_m, k.gy);
-    if (update_v) {
-        const double2 ao = ldm<PERSIST>(&d.a[i]);
+    if (update_v)
         d.v[vin ^ 1][i] = make_double2(fma(k.half_dt, ao.x + ax, vi.x), fma(k.half_dt, ao.y + ay, vi.y));
-    }
     d.a[i] = make_double2(ax, ay);
     // finiteness from the exponent bits (no FP64 compare)
     const bool bad = ((__float_as_uint(fx) | 0x807FFFFFu) == 0xFFFFFFFFu) ||
                      ((__float_as_uint(fy) | 0x807FFFFFu) == 0xFFFFFFFFu) ||
                      (walls && (((__double2hiint(Fwx) | 0x800FFFFF) == -1) || ((__double2hiint(Fwy) | 0x800FFFFF) == -1)));
     if (bad) atomicAdd(&d.status[PD_STATUS_NONFINITE], 1);
+}
+
+// FP64 update from the total of the lane-summed parts, T = (F_b + F_s) + F_n
+// (as finish_node forms it), and the wall force: the same roundings as
+// finish_node with the reciprocal mass, without the per-part output.
+template <bool PERSIST>
+__device__ __forceinline__ void finish_node64_total(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
+                                                    double2 vi, double2 ao, double Tx, double Ty, bool walls,
+                                                    double Fwx, double Fwy, double inv_m) {
+    const double Fx = walls ? __dadd_rn(Tx, Fwx) : Tx, Fy = walls ? __dadd_rn(Ty, Fwy) : Ty;
+    const double ax = fma(Fx, inv_m, k.gx), ay = fma(Fy, inv_m, k.gy);
+    if (update_v)
+        d.v[vin ^ 1][i] = make_double2(fma(k.half_dt, ao.x + ax, vi.x), fma(k.half_dt, ao.y + ay, vi.y));
+    d.a[i] = make_double2(ax, ay);
+    if (((__double2hiint(ax) | 0x800FFFFF) == -1) || ((__double2hiint(ay) | 0x800FFFFF) == -1))   // inf or NaN
+        atomicAdd(&d.status[PD_STATUS_NONFINITE], 1);
 }
 
 template <int LANES, class T>
@@ -1048,21 +1069,35 @@ __device__ __forceinline__ void force_node64(const DevPtrs &d, const KParams &k,
 // (the FP64 work runs with converged warps).
 template <bool PERSIST>
 __device__ __forceinline__ void node_epilogue64(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
-                                                const Sums64 &f) {
-    const double2 pi = ldm<PERSIST>(&d.p[i]);
+                                                const Sums64 &f, bool total = false) {
+    // the node's independent loads first, all in flight together (the pass is
+    // bound by memory latency): velocity, previous acceleration, grain, cell
     const double2 vi = ldm<PERSIST>(&d.v[vin][i]);
-    const double Vi = __ldg(&d.V[i]);
+    const double2 ao = update_v ? ldm<PERSIST>(&d.a[i]) : make_double2(0.0, 0.0);
     const int gi = __ldg(&d.grain[i]);
+    const int2 cell = ldm<PERSIST>(&d.cell[i]);
     const int ag = __ldg(&d.g_agg[gi]);
-    const AggParams &A = d.agg[ag];
-    const double rho = k.mat ? __ldg(&d.g_rho[gi]) : k.rho;
+    const double inv_m = __ldg(&d.g_invm[gi]);
+    const int4 wc = ldm<PERSIST>(&d.wall_cell[ag]);
     double Fwx = 0.0, Fwy = 0.0;
-    if (!far_from_walls<PERSIST>(d, i, ag)) {
+    const bool walls = !cells_far_from_walls(cell, wc);
+    if (walls) {
+        const double2 pi = ldm<PERSIST>(&d.p[i]);
+        const AggParams &A = d.agg[ag];
+        const double rho = k.mat ? __ldg(&d.g_rho[gi]) : k.rho;
         const double Kn = k.mat ? 18.0 * __ldg(&d.g_k[gi]) / A.pe5 : A.Kn;
-        wall_force64(k, A, Kn, rho, ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, Vi, Fwx, Fwy, d.status);
+        wall_force64(k, A, Kn, rho, ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, __ldg(&d.V[i]), Fwx, Fwy,
+                     d.status);
     }
-    finish_node<PERSIST, true>(d, k, i, vin, update_v, vi, 0.0, f.bx, f.by, f.sx, f.sy, f.nx, f.ny, Fwx, Fwy,
-                               __ldg(&d.g_invm[gi]));
+    if (k.store) {
+        finish_node<PERSIST, true>(d, k, i, vin, update_v, vi, 0.0, f.bx, f.by, f.sx, f.sy, f.nx, f.ny, Fwx, Fwy,
+                                   inv_m);
+    } else {
+        // total: the parts were summed by the lane-sum pass, f.bx / f.by hold T
+        const double Tx = total ? f.bx : __dadd_rn(__dadd_rn(f.bx, f.sx), f.nx);
+        const double Ty = total ? f.by : __dadd_rn(__dadd_rn(f.by, f.sy), f.ny);
+        finish_node64_total<PERSIST>(d, k, i, vin, update_v, vi, ao, Tx, Ty, walls, Fwx, Fwy, inv_m);
+    }
 }
 
 // FP32-split geometry of one bond to a neighbour at qj (float-float shifted
@@ -1341,9 +1376,16 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
 
 template <bool PERSIST>
 __device__ __forceinline__ void node_epilogue32(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
-                                                const Sums32 &fin) {
+                                                const Sums32 &fin, bool total = false) {
+    // the node's independent loads first, all in flight together (the pass is
+    // bound by memory latency): velocity, previous acceleration, grain, cell
     const double2 vi = ldm<PERSIST>(&d.v[vin][i]);
+    const double2 ao = update_v ? ldm<PERSIST>(&d.a[i]) : make_double2(0.0, 0.0);
     const int gi = __ldg(&d.grain[i]);
+    const int2 cell = ldm<PERSIST>(&d.cell[i]);
+    const int ag = __ldg(&d.g_agg[gi]);
+    const double inv_m = __ldg(&d.g_invm[gi]);
+    const int4 wc = ldm<PERSIST>(&d.wall_cell[ag]);
     Sums32 f = fin;
     if constexpr (!PERSIST) {
         // learned modal surrogate: between judge steps an active grain's bond force
@@ -1357,9 +1399,8 @@ __device__ __forceinline__ void node_epilogue32(const DevPtrs &d, const KParams 
             f.by += (rot.y * sf.x + rot.x * sf.y) * Eh;
         }
     }
-    const int ag = __ldg(&d.g_agg[gi]);
     double Fwx = 0.0, Fwy = 0.0;
-    const bool walls = !far_from_walls<PERSIST>(d, i, ag);
+    const bool walls = !cells_far_from_walls(cell, wc);
     if (walls) {
         const double2 pi = position64<PERSIST>(d, i);
         const AggParams &A = d.agg[ag];
@@ -1371,10 +1412,12 @@ __device__ __forceinline__ void node_epilogue32(const DevPtrs &d, const KParams 
     }
     if (k.store)
         finish_node<PERSIST, true>(d, k, i, vin, update_v, vi, 0.0, (double)f.bx, (double)f.by, (double)f.sx,
-                                   (double)f.sy, (double)f.nx, (double)f.ny, Fwx, Fwy, __ldg(&d.g_invm[gi]));
+                                   (double)f.sy, (double)f.nx, (double)f.ny, Fwx, Fwy, inv_m);
+    else if (total)      // the lane-sum pass summed the parts: f.bx / f.by hold the total
+        finish_node32_total<PERSIST>(d, k, i, vin, update_v, vi, ao, f.bx, f.by, walls, Fwx, Fwy, inv_m);
     else
-        finish_node32_total<PERSIST>(d, k, i, vin, update_v, vi, (f.bx + f.sx) + f.nx, (f.by + f.sy) + f.ny, walls,
-                                     Fwx, Fwy, __ldg(&d.g_invm[gi]));
+        finish_node32_total<PERSIST>(d, k, i, vin, update_v, vi, ao, (f.bx + f.sx) + f.nx, (f.by + f.sy) + f.ny,
+                                     walls, Fwx, Fwy, inv_m);
 }
 
 }  // namespace pd

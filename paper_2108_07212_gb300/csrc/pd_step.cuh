@@ -56,16 +56,26 @@ __device__ __forceinline__ void sums_node(const DevPtrs &d, const KParams &k, in
         force_node32<PERSIST, LANES>(d, k, i, lane, active, vin, f);
         if (active && lane == 0) {
             float *o = static_cast<float *>(d.fsum);
-            o[i] = f.bx, o[N + i] = f.by, o[2 * N + i] = f.sx, o[3 * N + i] = f.sy, o[4 * N + i] = f.nx,
-            o[5 * N + i] = f.ny;
+            if (k.store) {
+                o[i] = f.bx, o[N + i] = f.by, o[2 * N + i] = f.sx, o[3 * N + i] = f.sy, o[4 * N + i] = f.nx,
+                o[5 * N + i] = f.ny;
+            } else {
+                // only the total is needed: (F_b + F_s) + F_n, as the epilogue would form it
+                reinterpret_cast<float2 *>(o)[i] = make_float2((f.bx + f.sx) + f.nx, (f.by + f.sy) + f.ny);
+            }
         }
     } else {
         Sums64 f;
         force_node64<PERSIST, LANES>(d, k, i, lane, active, vin, f);
         if (active && lane == 0) {
             double *o = static_cast<double *>(d.fsum);
-            o[i] = f.bx, o[N + i] = f.by, o[2 * N + i] = f.sx, o[3 * N + i] = f.sy, o[4 * N + i] = f.nx,
-            o[5 * N + i] = f.ny;
+            if (k.store) {
+                o[i] = f.bx, o[N + i] = f.by, o[2 * N + i] = f.sx, o[3 * N + i] = f.sy, o[4 * N + i] = f.nx,
+                o[5 * N + i] = f.ny;
+            } else {
+                reinterpret_cast<double2 *>(o)[i] =
+                    make_double2(__dadd_rn(__dadd_rn(f.bx, f.sx), f.nx), __dadd_rn(__dadd_rn(f.by, f.sy), f.ny));
+            }
         }
     }
 }
@@ -73,16 +83,27 @@ __device__ __forceinline__ void sums_node(const DevPtrs &d, const KParams &k, in
 template <bool FP32, bool PERSIST>
 __device__ __forceinline__ void epilogue_node(const DevPtrs &d, const KParams &k, int i, int vin, int update_v) {
     const size_t N = (size_t)k.N;
+    // per-part sums (k.store) or the total of the parts
     if constexpr (FP32) {
         const float *o = static_cast<const float *>(d.fsum);
-        const Sums32 f{ldm<PERSIST>(o + i), ldm<PERSIST>(o + N + i), ldm<PERSIST>(o + 2 * N + i),
-                       ldm<PERSIST>(o + 3 * N + i), ldm<PERSIST>(o + 4 * N + i), ldm<PERSIST>(o + 5 * N + i)};
-        node_epilogue32<PERSIST>(d, k, i, vin, update_v, f);
+        if (k.store) {
+            const Sums32 f{ldm<PERSIST>(o + i), ldm<PERSIST>(o + N + i), ldm<PERSIST>(o + 2 * N + i),
+                           ldm<PERSIST>(o + 3 * N + i), ldm<PERSIST>(o + 4 * N + i), ldm<PERSIST>(o + 5 * N + i)};
+            node_epilogue32<PERSIST>(d, k, i, vin, update_v, f);
+        } else {
+            const float2 t = ldm<PERSIST>(reinterpret_cast<const float2 *>(o) + i);
+            node_epilogue32<PERSIST>(d, k, i, vin, update_v, Sums32{t.x, t.y, 0.f, 0.f, 0.f, 0.f}, true);
+        }
     } else {
         const double *o = static_cast<const double *>(d.fsum);
-        const Sums64 f{ldm<PERSIST>(o + i), ldm<PERSIST>(o + N + i), ldm<PERSIST>(o + 2 * N + i),
-                       ldm<PERSIST>(o + 3 * N + i), ldm<PERSIST>(o + 4 * N + i), ldm<PERSIST>(o + 5 * N + i)};
-        node_epilogue64<PERSIST>(d, k, i, vin, update_v, f);
+        if (k.store) {
+            const Sums64 f{ldm<PERSIST>(o + i), ldm<PERSIST>(o + N + i), ldm<PERSIST>(o + 2 * N + i),
+                           ldm<PERSIST>(o + 3 * N + i), ldm<PERSIST>(o + 4 * N + i), ldm<PERSIST>(o + 5 * N + i)};
+            node_epilogue64<PERSIST>(d, k, i, vin, update_v, f);
+        } else {
+            const double2 t = ldm<PERSIST>(reinterpret_cast<const double2 *>(o) + i);
+            node_epilogue64<PERSIST>(d, k, i, vin, update_v, Sums64{t.x, t.y, 0.0, 0.0, 0.0, 0.0}, true);
+        }
     }
 }
 
@@ -94,7 +115,7 @@ __global__ void __launch_bounds__(kBlock, FP32 ? 8 : 4) k_sums(DevPtrs d, KParam
 }
 
 template <bool FP32>
-__global__ void __launch_bounds__(256, 4) k_epilogue(DevPtrs d, KParams k, int vin, int update_v) {
+__global__ void __launch_bounds__(256, 6) k_epilogue(DevPtrs d, KParams k, int vin, int update_v) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < k.N) epilogue_node<FP32, false>(d, k, i, vin, update_v);
 }

@@ -4,12 +4,16 @@ At these sizes the kernels take paths the small parity cases never reach: the
 split force phase of the kernel graph (lane sums through device memory, then the
 per-node epilogue), hash grids of 2^20 to 2^24 buckets with the two-level
 scan, the aliased buckets of 64 aggregates sharing one grid, and the learned
-surrogate on 2000 grains.  Each test advances the GPU to a loaded state
-(collisions, wall contact, fracture), pushes that state into the oracle and
-compares one force evaluation element by element (Algorithm 1; eq:full):
-plain FP64 path within 1e-12 of the largest force, FP32-split path within 1e-5,
-with identical broken-bond sets.  Each force part (bond, self-contact, contact,
-wall) is also compared at the scale of its own largest value.
+surrogate on 2000 grains.  The oracle (all-core build) advances each workload
+from its initial state to a loaded one (collisions, wall contact, fracture);
+the GPU trajectory from the same initial state is compared with it, and the
+oracle's state is pushed into the GPU contexts for one force evaluation
+compared element by element (Algorithm 1; eq:full): plain FP64 path within
+1e-12 of the largest force, FP32-split path within 1e-5, with identical
+broken-bond sets.  Each force part (bond, self-contact, contact, wall) is also
+compared at the scale of its own largest value.  No oracle input comes from
+the GPU: the GPU runs only choose which aggregates of the ensemble the oracle
+advances.
 """
 import math
 
@@ -39,12 +43,14 @@ def _push_gpu(S, st):
         S.set(f, st[f])
 
 
-def _push_oracle(P, st, nodes=slice(None), bonds=slice(None)):
-    P.u[:] = st["DISP"][nodes]
-    P.v[:] = st["VEL"][nodes]
-    P.a[:] = st["ACC"][nodes]
-    P.broken[: len(P.col)] = st["BROKEN"][bonds]
-    P.step = int(st["STEP"][0])
+def _oracle_state(P):
+    """The oracle's state, in the layout of the GPU state fields."""
+    return {"DISP": P.u.copy(), "VEL": P.v.copy(), "ACC": P.a.copy(),
+            "BROKEN": P.broken[: len(P.col)].copy(), "STEP": np.array([P.step], np.int64)}
+
+
+def _l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def _eval(S):
@@ -68,57 +74,68 @@ def _compare(F, parts, broken, F_or, parts_or, broken_or, tol, label, floor=0.0)
 
 def test_compaction_521k_nodes_one_force_evaluation_against_oracle():
     """The 500-grain compaction (521,454 nodes, 11.4M directed bonds) with every
-    grain thrown at 5 m/s: after 500 FP64 steps grains collide and break bonds."""
+    grain thrown at 5 m/s: after 500 steps grains collide and break bonds.  The
+    GPU's FP64 trajectory follows the oracle's (1e-9 relative L2, identical
+    breaks); at the oracle's state both GPU paths match its forces."""
     w = I.compaction(agitation=5.0)
+    P = O.OracleProblem.from_workload(w)
+    P.omp = True
+    P.init_accel()
+    P.run(500)
+    st = _oracle_state(P)
+    F_or, parts_or = P.forces(keep_broken=False)
+    assert st["BROKEN"].sum() > 0 and np.abs(parts_or[2]).max() > 0
     A = B.Simulation(w, precision=B.PD_FP64, store_parts=True, device="cuda:0")
     info = A.info()
     assert A.N > 500_000 and info["buckets"] >= 2 ** 20 and int(info["mode"]) == 2
     A.step(500)
-    st = _state(A)
+    assert _l2(A.get("DISP"), st["DISP"]) <= 1e-9
+    assert np.array_equal(A.get("BROKEN"), st["BROKEN"])
+    _push_gpu(A, st)
     F64, parts64, br64 = _eval(A)
-    P = O.OracleProblem.from_workload(w)
-    P.omp = True
-    _push_oracle(P, st)
-    F_or, parts_or = P.forces(keep_broken=False)
-    assert st["BROKEN"].sum() > 0 and np.abs(parts_or[2]).max() > 0
-    _compare(F64, parts64, br64, F_or, parts_or, P.broken, FP64_TOL, "fp64")
+    _compare(F64, parts64, br64, F_or, parts_or, P.broken[: len(P.col)], FP64_TOL, "fp64")
     del A
     C = B.Simulation(w, precision=B.PD_FP32_SPLIT, store_parts=True, device="cuda:0")
     _push_gpu(C, st)
     F32, parts32, br32 = _eval(C)
-    _compare(F32, parts32, br32, F_or, parts_or, P.broken, FP32_TOL, "fp32")
+    _compare(F32, parts32, br32, F_or, parts_or, P.broken[: len(P.col)], FP32_TOL, "fp32")
 
 
 def test_ensemble_of_64_aggregates_against_oracle_per_aggregate():
     """The batched ensemble (64 aggregates, 6.69M nodes, one shared hash grid
-    whose buckets alias across aggregates) with every grain thrown at 5 m/s:
-    after 600 steps the batched FP64 and FP32-split contexts are compared, one
-    force evaluation at the same state, with the oracle run on single
-    aggregates (their own walls, R_c and K_n)."""
+    whose buckets alias across aggregates) with every grain thrown at 5 m/s.
+    The batched FP64 context runs 600 steps; on four of its aggregates (the
+    largest, the smallest and the two with the largest contact forces) the
+    oracle, run on the single aggregate (its own walls, R_c and K_n), gives the
+    same trajectory; at the oracle's states the batched FP64 and FP32-split
+    contexts match its forces."""
     w = I.ensemble()
     ang = np.random.Generator(np.random.PCG64(4242)).uniform(0.0, 2 * math.pi, w.n_grains)
     w.grain_geom[:, 4] = 5.0 * np.cos(ang)
     w.grain_geom[:, 5] = 5.0 * np.sin(ang)
+    # the same initial velocities in the single-aggregate workloads the oracle runs
+    g0 = 0
+    for part in w.parts:
+        part.grain_geom = part.grain_geom.copy()
+        part.grain_geom[:, 4:6] = w.grain_geom[g0:g0 + part.n_grains, 4:6]
+        g0 += part.n_grains
+    assert g0 == w.n_grains
+    n_steps = 600
     A = B.Simulation(w, precision=B.PD_FP64, store_parts=True, device="cuda:0")
     assert A.N > 6_000_000 and int(A.info()["n_agg"]) == 64
-    A.step(600)
+    A.step(n_steps)
     st = _state(A)
-    F64, parts64, br64 = _eval(A)
+    _, parts_gpu, _ = _eval(A)
     row = A.get("ROW_PTR")
     agg_of_node = w.grain_agg[A.get("GRAIN")]
-    del A
-    C = B.Simulation(w, precision=B.PD_FP32_SPLIT, store_parts=True, device="cuda:0")
-    _push_gpu(C, st)
-    F32, parts32, br32 = _eval(C)
-    del C
     # the largest and the smallest aggregate and the two with the largest contact forces
     counts = np.bincount(w.grain_agg)
     cmax = np.zeros(64)
-    np.maximum.at(cmax, agg_of_node, np.abs(parts64[2]).max(axis=1))
+    np.maximum.at(cmax, agg_of_node, np.abs(parts_gpu[2]).max(axis=1))
     pick = {int(np.argmax(counts)), int(np.argmin(counts))} | {int(a) for a in np.argsort(-cmax)[:2]}
-    # a node's weight: the scale below which a force is round-off of the float path
-    weight = w.params["rho"] * (w.grain_geom[:, 6].min() ** 2) * abs(w.params["gy"])
-    contact_seen = 0
+    del parts_gpu
+    # the oracle on each picked aggregate; its states replace the GPU's there
+    ref = {}
     for a in sorted(pick):
         nodes = np.flatnonzero(agg_of_node == a)
         n0, n1 = int(nodes[0]), int(nodes[-1]) + 1
@@ -127,12 +144,31 @@ def test_ensemble_of_64_aggregates_against_oracle_per_aggregate():
         P = O.OracleProblem.from_workload(w.parts[a])
         P.omp = True
         assert P.N == n1 - n0 and len(P.col) == b1 - b0
-        _push_oracle(P, st, slice(n0, n1), slice(b0, b1))
+        P.init_accel()
+        P.run(n_steps)
+        so = _oracle_state(P)
+        assert _l2(st["DISP"][n0:n1], so["DISP"]) <= 1e-9, a
+        assert np.array_equal(st["BROKEN"][b0:b1], so["BROKEN"]), a
+        for f in ("DISP", "VEL", "ACC"):
+            st[f][n0:n1] = so[f]
+        st["BROKEN"][b0:b1] = so["BROKEN"]
         F_or, parts_or = P.forces(keep_broken=False)
+        ref[a] = (n0, n1, b0, b1, F_or, parts_or, P.broken[: b1 - b0].copy())
+    _push_gpu(A, st)
+    F64, parts64, br64 = _eval(A)
+    del A
+    C = B.Simulation(w, precision=B.PD_FP32_SPLIT, store_parts=True, device="cuda:0")
+    _push_gpu(C, st)
+    F32, parts32, br32 = _eval(C)
+    del C
+    # a node's weight: the scale below which a force is round-off of the float path
+    weight = w.params["rho"] * (w.grain_geom[:, 6].min() ** 2) * abs(w.params["gy"])
+    contact_seen = 0
+    for a, (n0, n1, b0, b1, F_or, parts_or, br_or) in sorted(ref.items()):
         contact_seen += int(np.abs(parts_or[2]).max() > 0)
-        _compare(F64[n0:n1], parts64[:, n0:n1], br64[b0:b1], F_or, parts_or, P.broken[: b1 - b0], FP64_TOL,
+        _compare(F64[n0:n1], parts64[:, n0:n1], br64[b0:b1], F_or, parts_or, br_or, FP64_TOL,
                  f"fp64 aggregate {a}")
-        _compare(F32[n0:n1], parts32[:, n0:n1], br32[b0:b1], F_or, parts_or, P.broken[: b1 - b0], FP32_TOL,
+        _compare(F32[n0:n1], parts32[:, n0:n1], br32[b0:b1], F_or, parts_or, br_or, FP32_TOL,
                  f"fp32 aggregate {a}", floor=weight)
     assert contact_seen >= 2
 
@@ -143,11 +179,12 @@ def test_surrogate_2000_grains_against_oracle_bond_force():
     modal model (networks with a zero last layer) and the full bond kernel as
     judge every 50 steps.  The lowest grains land on the floor and deform; the
     judge takes off the surrogate every grain whose surrogate bond force is off
-    by more than 1e-3 (nodal error over the grain, floored at its weight).  At
-    step 1201 every grain still on the surrogate must meet that criterion
-    against the oracle's bond force at the same state; at a judge step the full
-    FP32 bond force the judge uses is within the FP32-split tolerance of the
-    oracle's, and the contact and wall parts are too."""
+    by more than 1e-3 (nodal error over the grain, floored at its weight).  The
+    oracle advances the full model over the same 1201 steps; at its state every
+    grain still on the surrogate must meet that criterion against the oracle's
+    bond force, and at a judge step the full FP32 bond force the judge uses is
+    within the FP32-split tolerance of the oracle's, as are the contact and
+    wall parts."""
     from paper_2108_07212_gb300 import surrogate as SU
 
     w = I.surrogate_settling()
@@ -164,16 +201,20 @@ def test_surrogate_2000_grains_against_oracle_bond_force():
         S.surrogate_set_mlp(t, net)
     S.surrogate_enable(True)
     S.step(1201)
-    st = _state(S)
+    # the oracle's full model over the same 1201 steps; its state goes into the
+    # surrogate context (the grains the judge kept on the surrogate stay on it)
+    P = O.OracleProblem.from_workload(w)
+    P.omp = True
+    P.init_accel()
+    P.run(1201)
+    st = _oracle_state(P)
+    F_or, parts_or = P.forces(keep_broken=False)
+    _push_gpu(S, st)
     S.surrogate_inspect()                       # force evaluation with the surrogate (not a judge step)
     parts = S.get("FORCE_PARTS")
     active, err, merr, maxs = S.surrogate_stats()
     grain = S.get("GRAIN")
     V = S.get("VOLUME")
-    P = O.OracleProblem.from_workload(w)
-    P.omp = True
-    _push_oracle(P, st)
-    F_or, parts_or = P.forces(keep_broken=False)
     for k in (1, 2, 3):
         if np.abs(parts_or[k]).max() > 0:
             assert _rel(parts[k], parts_or[k]) <= FP32_TOL, k

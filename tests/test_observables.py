@@ -96,14 +96,14 @@ def _lid_and_floor(n_grains=8, seed=4, lid_speed=3.0):
 @pytest.mark.parametrize("prec", [B.PD_FP64, B.PD_FP32_SPLIT])
 def test_gpu_observables_match_the_oracle(prec):
     w = _lid_and_floor()
+    # the oracle advances 300 steps; its state goes into the GPU context
+    P = O.OracleProblem.from_workload(w).init_accel()
+    P.run(300)
     S = B.Simulation(w, precision=prec, device="cuda:0")
-    S.step(300)
+    for f, val in (("DISP", P.u), ("VEL", P.v), ("ACC", P.a), ("BROKEN", P.broken[: S.n_bonds]),
+                   ("STEP", np.array([P.step], np.int64))):
+        S.set(f, val)
     obs = S.observables()
-    P = O.OracleProblem.from_workload(w)
-    P.u[:] = S.get("DISP")
-    P.v[:] = S.get("VEL")
-    P.broken[: S.n_bonds] = S.get("BROKEN")
-    P.step = int(S.get("STEP")[0])
     assert obs.shape == (1, 4)
     assert obs[0, 0] == pytest.approx(P.volume_fraction(), rel=1e-14)
     assert obs[0, 1] == pytest.approx(P.bulk_damage(), rel=1e-12, abs=1e-15)
