@@ -596,9 +596,63 @@ def leg_surrogate(B, I, SU, dev, stream, torch, steps=200):
     out.update(res)
     out["speedup_vs_plain_fp32"] = res["surrogate"]["value"] / res["plain_fp32"]["value"]
     out["speedup_vs_plain_fp64"] = res["surrogate"]["value"] / res["plain_fp64"]["value"]
-    del D, S, T
+    del D, S
+    torch.cuda.empty_cache()
+    out["landing"] = _surrogate_landing(B, I, SU, dev, stream, torch, T, data, steps)
+    del T
     torch.cuda.empty_cache()
     return out
+
+
+def _surrogate_landing(B, I, SU, dev, stream, torch, T, data, steps, advance=1200):
+    """The same 2000 grains lowered to 1.02 R_c above the floor and thrown down
+    at 2 m/s: the lowest grains land and deform, the judge (every 50 steps)
+    takes off the surrogate every grain whose nodal bond-force error exceeds
+    1e-3, the rest stay on it.  Both paths run `advance` steps from the same
+    initial state, then `steps` timed steps."""
+    w = I.surrogate_settling()
+    with torch.cuda.stream(stream):
+        X = B.Simulation(w, device=dev, stream=stream).get("X")        # meshing only (host)
+    rc = w.params["rc_ratio"] * w.grain_geom[:, 6].min()
+    w.grain_geom[:, 1] -= X[:, 1].min() - 1.02 * rc
+    w.grain_geom[:, 5] = -2.0
+    with torch.cuda.stream(stream):
+        S = B.Simulation(w, precision=B.PD_FP32_SPLIT, device=dev, stream=stream,
+                         surrogate=lambda s_: SU.build_basis(s_, source=(T, T.surrogate_basis)))
+    cfg = S.surrogate_basis
+    lam = cfg["lambda_"].reshape(-1, cfg["n_modes"])
+    src = {k: t for t, k in enumerate(SU.template_keys(T, T.surrogate_basis))}
+    counts = np.bincount(cfg["template_of_grain"])
+    nets = []
+    for t, key in enumerate(SU.template_keys(S, cfg)):
+        tt = src.get(key)
+        params = SU.train_template(*data[tt], lam[t], epochs=400)[0] if tt is not None and tt in data \
+            else SU.init_params(0)
+        nets.append(B.MLP(max_batch=int(counts[t]), stream=stream, params=params))
+        S.surrogate_set_mlp(t, nets[-1])
+    S.surrogate_enable(True)
+    S.autotune()
+    with torch.cuda.stream(stream):
+        P = B.Simulation(w, precision=B.PD_FP32_SPLIT, device=dev, stream=stream)
+    P.autotune()
+    res = {"workload": "the same grains 1.02 R_c above the floor, all moving down at 2 m/s (landing)",
+           "window": f"steps {advance}..{advance + steps}"}
+    for sim, name in ((P, "plain_fp32"), (S, "surrogate")):
+        sim.step(advance)
+        dt = _event_time(stream, torch, lambda: sim.step(steps))
+        res[name] = {"value": sim.N * steps / dt, "unit": "node-steps/s", "ms_per_step": 1e3 * dt / steps}
+    active, err, merr, maxs = S.surrogate_stats()
+    on = active == 1
+    res["surrogate"].update(
+        active_grains=int(on.sum()), grains=int(w.n_grains),
+        judged_err_max=float(err[on].max()) if on.any() else None,
+        max_stretch_over_s0_active=float(maxs[on].max()) if on.any() else None,
+        max_stretch_over_s0_all=float(maxs.max()), status=int(S.status()[0]))
+    u0, u1 = P.get("DISP"), S.get("DISP")
+    res["surrogate"]["traj_rel_l2_vs_plain"] = float(np.linalg.norm(u1 - u0) / max(np.linalg.norm(u0), 1e-300))
+    res["speedup_vs_plain_fp32"] = res["surrogate"]["value"] / res["plain_fp32"]["value"]
+    del P, S
+    return res
 
 
 def _same_state_force_report(B, sim32, sim64, w):

@@ -444,7 +444,8 @@ int pd_surrogate_setup(pd_ctx *ctx, int n_modes, const float *basis, const float
                        double gate, double err_tol);
 /* Network of template t (its max_batch >= grains of the template); NULL
  * removes it and its grains leave the surrogate.  The network must stay alive
- * while the context may step. */
+ * while the context may step.  A network takes the 32 modal coefficients of a
+ * grain: PD_EINVAL unless pd_surrogate_setup was given n_modes = 32. */
 int pd_surrogate_set_mlp(pd_ctx *ctx, int tmpl, pd_mlp *mlp);
 /* on = 1: every grain of a template with a network becomes active; 0: off. */
 int pd_surrogate_enable(pd_ctx *ctx, int on);

@@ -456,21 +456,18 @@ int check_ctx(pd_ctx *c, int min_state) {
 }
 
 // Surrogate phases before the force kernel: co-rotated local deformation of
-// the active grains, its projection on the basis (tensor cores), every
-// template's network on its batch of grains with f = -Lambda q + net(q) in
-// its output epilogue, and the expansion of f to nodal bond forces (tensor
-// cores).
+// the active grains, its projection on the basis (tensor cores), the chunk
+// partials summed in a fixed order, every template's network on its batch of
+// grains with f = -Lambda q + net(q) in its output epilogue, and the
+// expansion of f to nodal bond forces (tensor cores).
 cudaError_t record_surrogate(pd_ctx *c, cudaStream_t s) {
     cudaError_t e;
-    // with 32 modes the networks subtract Lambda q on output themselves
-    const bool fused = c->sur_modes == PD_MLP_OUT;
     if ((e = pd::launch_sur_frame(c->d, c->kp, 0, s)) != cudaSuccess) return e;
     if ((e = pd::launch_sur_project_tc(c->d, c->kp, s)) != cudaSuccess) return e;
     if ((e = pd::launch_sur_reduce(c->d, c->kp, s)) != cudaSuccess) return e;
     if ((e = pd::launch_mlp_grouped(c->d.mlp_refs, c->d.mlp_work, (int)c->mlp_work.size(), c->d.sur_x, c->d.sur_y,
                                     c->d.mlp_err, s)) != cudaSuccess)
         return e;
-    if (!fused && (e = pd::launch_sur_combine(c->d, c->kp, s)) != cudaSuccess) return e;
     return pd::launch_sur_expand_tc(c->d, c->kp, s);
 }
 
@@ -1648,11 +1645,12 @@ int pd_surrogate_set_mlp(pd_ctx *c, int tmpl, pd_mlp *mlp) {
     if (int r = check_ctx(c, 3)) return r;
     if (!c->sur_cfg) return fail(PD_ESTATE, "pd_surrogate_setup was not called");
     if (tmpl < 0 || tmpl >= c->n_tmpl) return fail(PD_EINVAL, "template out of range");
+    if (mlp && c->sur_modes != PD_MLP_IN)
+        return fail(PD_EINVAL, "a network takes 32 modal coefficients: the surrogate needs n_modes = 32");
     pd::MlpRef ref{};
     if (mlp && pd::mlp_ref(mlp, &ref) != PD_OK) return fail(PD_ESTATE, "network not bound to device memory");
-    // with 32 modes the linear modal part -Lambda q is applied in the network's
-    // output epilogue (no separate combination kernel)
-    if (mlp && c->sur_modes == PD_MLP_OUT) ref.lin = c->d.sur_lambda + (size_t)tmpl * PD_MLP_OUT;
+    // the linear modal part -Lambda q is applied in the network's output epilogue
+    if (mlp) ref.lin = c->d.sur_lambda + (size_t)tmpl * PD_MLP_OUT;
     c->sur_mlp[tmpl] = mlp;
     // device table of the networks and the inference tiles (template, first row, end row)
     PD_CUDA(cudaMemcpyAsync(c->d.mlp_refs + tmpl, &ref, sizeof(ref), cudaMemcpyHostToDevice, c->stream));

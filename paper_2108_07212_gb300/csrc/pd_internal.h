@@ -180,7 +180,7 @@ struct KParams {
 // active grains before the force phase, and the judge after it.
 // Tile sizes of the tensor-core projection (rows of 2 n_t per chunk) and expansion.
 constexpr int kSurChunk = 128;
-constexpr int kSurExpandRows = 256;
+constexpr int kSurExpandRows = 128;
 constexpr int kSurTile = 128;      // network rows (grains) per tile
 cudaError_t sur_init_attributes();   // shared-memory limits of the tensor-core kernels (not capturable)
 cudaError_t launch_sur_frame(const DevPtrs &d, const KParams &k, int all_templated, cudaStream_t s);
@@ -192,7 +192,6 @@ cudaError_t launch_sur_project_tc(const DevPtrs &d, const KParams &k, cudaStream
 cudaError_t launch_sur_reduce(const DevPtrs &d, const KParams &k, cudaStream_t s);
 cudaError_t launch_sur_expand_tc(const DevPtrs &d, const KParams &k, cudaStream_t s);
 cudaError_t launch_sur_judge(const DevPtrs &d, const KParams &k, cudaStream_t s);
-cudaError_t launch_sur_combine(const DevPtrs &d, const KParams &k, cudaStream_t s);
 
 // Device pointers of one network's inference parameters (BF16 weights, FP32
 // parameter vector with the biases).

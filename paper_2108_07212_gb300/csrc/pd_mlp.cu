@@ -17,16 +17,12 @@
 #include <vector>
 
 #include "pd_internal.h"
+#include "pd_mlp_tile.cuh"
 #include "pd_tc.cuh"
 #include "peridem.h"
 
 namespace pd {
 namespace mlp {
-
-constexpr int IN = PD_MLP_IN, HID = PD_MLP_HIDDEN, OUT = PD_MLP_OUT, TILE = 128;
-constexpr int OW1 = 0, OB1 = OW1 + HID * IN, OW2 = OB1 + HID, OB2 = OW2 + HID * HID, OW3 = OB2 + HID,
-              OB3 = OW3 + OUT * HID, NPARAM = OB3 + OUT;
-static_assert(NPARAM == PD_MLP_NPARAMS, "parameter layout");
 constexpr long long kSpins = 1LL << 24;      // bounded mbarrier waits (~0.5 s)
 constexpr int kFwdSmem = 160 * 1024;        // generous: no operand read can leave the allocation
 constexpr int kGemmSmem = 96 * 1024;
@@ -42,7 +38,6 @@ struct Net {
     int *err;
 };
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
 }
@@ -56,7 +51,7 @@ __device__ __forceinline__ float gelu_grad(float z) {
 __device__ __forceinline__ void fwd_tile(const __nv_bfloat16 *__restrict__ W1, const __nv_bfloat16 *__restrict__ W2,
                                          const __nv_bfloat16 *__restrict__ W3, const float *__restrict__ P,
                                          const float *__restrict__ X, float *__restrict__ Yout, int row0, int B,
-                                         int Bp, int train, const Net &n, int *err, const float *lin = nullptr) {
+                                         int Bp, int train, const Net &n, int *err) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_base;
@@ -171,10 +166,7 @@ __device__ __forceinline__ void fwd_tile(const __nv_bfloat16 *__restrict__ W1, c
                 const int c = c0 + q;
                 const float z = acc[q] + bias[c];
                 if (layer == 2) {
-                    // with lin: the surrogate's modal force f = net(q) - Lambda q (IN = OUT)
-                    // (x re-read from memory: indexing the register copy with the runtime
-                    // column would move it to local memory)
-                    if (row < B) Yout[(size_t)row * OUT + c] = lin ? z - lin[c] * X[(size_t)row * IN + c] : z;
+                    if (row < B) Yout[(size_t)row * OUT + c] = z;
                     if (train) n.Y[(size_t)row * OUT + c] = z;
                 } else {
                     if (train) (layer == 0 ? n.Z1 : n.Z2)[(size_t)row * HID + c] = z;
@@ -210,14 +202,124 @@ __global__ void __launch_bounds__(128) k_mlp_fwd(Net n, const float *__restrict_
     fwd_tile(n.W1, n.W2, n.W3, n.p, X, Yout, blockIdx.x * TILE, B, Bp, train, n, n.err);
 }
 
-// Inference of several networks in one launch: tile blockIdx.x is rows
-// [w.y, min(w.y + 128, w.z)) of X / Y through network refs[w.x].
-__global__ void __launch_bounds__(128) k_mlp_fwd_grouped(const MlpRef *__restrict__ refs, const int4 *__restrict__ work,
-                                                         const float *__restrict__ X, float *__restrict__ Y, int *err) {
-    const int4 w = work[blockIdx.x];
-    const MlpRef r = refs[w.x];
-    fwd_tile(static_cast<const __nv_bfloat16 *>(r.W1), static_cast<const __nv_bfloat16 *>(r.W2),
-             static_cast<const __nv_bfloat16 *>(r.W3), r.p, X, Y, w.y, w.z, 0, 0, Net{}, err, r.lin);
+// Inference of several networks in one launch (the surrogate's step): tile
+// blockIdx.x is rows [w.y, min(w.y + 128, w.z)) of X / Y through network
+// refs[w.x].  The MMAs are those of fwd_tile; operand staging and the layer
+// epilogues are spread over four warpgroups: warp w reads TMEM lanes
+// 32 (w % 4) .. 32 (w % 4) + 31 (its quarter of the rows) and warpgroup g
+// takes the g-th quarter of a hidden layer's columns, so four warps per
+// scheduler hide the latency of the activation chains and of the loads.  The
+// activation is the GELU with the error function of Abramowitz & Stegun
+// 7.1.26 (branch-free; its 1.5e-7 error is far below the BF16 rounding of
+// the activations).  With r.lin the output is the surrogate's modal force
+// f = net(q) - Lambda q.
+constexpr int kInferThreads = 512;
+constexpr int kInferGroups = kInferThreads / TILE;
+
+__global__ void __launch_bounds__(kInferThreads) k_mlp_infer(const MlpRef *__restrict__ refs,
+                                                             const int4 *__restrict__ work,
+                                                             const float *__restrict__ X, float *__restrict__ Y,
+                                                             int *err) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    uint8_t *sA = sm;                     // X tile   128 x 32  (8 KB)
+    uint8_t *sW1 = sm + 8 * 1024;         // W1       128 x 32  (8 KB)
+    uint8_t *sH = sm + 16 * 1024;         // H tile   128 x 128 (32 KB)
+    uint8_t *sW2 = sm + 48 * 1024;        // W2       128 x 128 (32 KB)
+    uint8_t *sW3 = sm + 80 * 1024;        // W3        32 x 128 (8 KB)
+    const int4 wk = work[blockIdx.x];
+    const MlpRef r = refs[wk.x];
+    const float *P = r.p, *lin = r.lin;
+    const int B = wk.z;
+    const int tid = threadIdx.x, warp = tid >> 5, wg = warp >> 2;
+    const int lrow = tid & 127;           // = 32 (warp % 4) + lane: the TMEM lane of the thread
+    const int row = wk.y + lrow;
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 128);
+    if (tid == 0) tc::mbar_init(&mbar, 1);
+    static_assert(IN == 8 * kInferGroups, "one 8-column piece of the input row per warpgroup");
+    {
+        // input: columns 8 wg .. 8 wg + 7 of the row (one 16-byte core-matrix row)
+        __align__(16) __nv_bfloat16 xb[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) xb[q] = __float2bfloat16(row < B ? X[(size_t)row * IN + 8 * wg + q] : 0.f);
+        *reinterpret_cast<uint4 *>(sA + tc::kmajor_off(lrow, 8 * wg, TILE)) = *reinterpret_cast<const uint4 *>(xb);
+    }
+    stage_weights<IN, HID, kInferThreads>(static_cast<const __nv_bfloat16 *>(r.W1), sW1, tid);
+    stage_weights<HID, HID, kInferThreads>(static_cast<const __nv_bfloat16 *>(r.W2), sW2, tid);
+    stage_weights<HID, OUT, kInferThreads>(static_cast<const __nv_bfloat16 *>(r.W3), sW3, tid);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    constexpr int kCols = HID / kInferGroups;            // hidden columns per warpgroup
+    static_assert(kCols % 16 == 0 && OUT / 16 <= kInferGroups, "16-column TMEM loads");
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int layer = 0; layer < 3 && ok; ++layer) {
+        const int K = layer == 0 ? IN : HID;
+        const int N = layer == 2 ? OUT : HID;
+        uint8_t *a = layer == 0 ? sA : sH;
+        uint8_t *b = layer == 0 ? sW1 : (layer == 1 ? sW2 : sW3);
+        if (tid == 0) {
+            const uint32_t lbo_a = tc::kmajor_lbo(TILE), lbo_b = tc::kmajor_lbo(N);
+            const uint32_t idesc = tc::idesc_bf16(TILE, N);
+            for (int ks = 0; ks < K / 16; ++ks) {
+                const uint64_t ad = tc::smem_desc(tc::smem_addr(a) + ks * 2 * lbo_a, lbo_a, tc::kSbo);
+                const uint64_t bd = tc::smem_desc(tc::smem_addr(b) + ks * 2 * lbo_b, lbo_b, tc::kSbo);
+                tc::mma_bf16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+            }
+            tc::mma_commit(&mbar);
+        }
+        ok = __syncthreads_and(tc::mbar_wait(&mbar, phase, kSpins)) != 0;   // uniform outcome
+        phase ^= 1;
+        if (!ok) break;
+        tc::fence_after_sync();
+        const float *bias = P + (layer == 0 ? OB1 : (layer == 1 ? OB2 : OB3));
+        if (layer < 2) {
+            // hidden layer: columns kCols wg .. kCols (wg + 1) of the thread's row
+#pragma unroll
+            for (int c0 = kCols * wg; c0 < kCols * (wg + 1); c0 += 16) {
+                float acc[16];
+                tc::tmem_ld16(tmem + lane_base + (uint32_t)c0, acc);
+                __align__(16) __nv_bfloat16 hb[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) hb[q] = __float2bfloat16(gelu_fast(acc[q] + bias[c0 + q]));
+                *reinterpret_cast<uint4 *>(sH + tc::kmajor_off(lrow, c0, TILE)) = *reinterpret_cast<const uint4 *>(hb);
+                *reinterpret_cast<uint4 *>(sH + tc::kmajor_off(lrow, c0 + 8, TILE)) =
+                    *reinterpret_cast<const uint4 *>(hb + 8);
+            }
+        } else if (wg < OUT / 16) {
+            // output layer: 16 columns per warpgroup (the first OUT / 16 groups; warp-uniform)
+            const int c0 = 16 * wg;
+            float acc[16];
+            tc::tmem_ld16(tmem + lane_base + (uint32_t)c0, acc);
+            if (row < B) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int c = c0 + q;
+                    const float z = acc[q] + bias[c];
+                    Y[(size_t)row * OUT + c] = lin ? z - lin[c] * X[(size_t)row * IN + c] : z;
+                }
+            }
+        }
+        tc::fence_before_sync();
+        tc::fence_async_smem();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    if (!ok) {
+        // the MMAs committed on the phase that timed out may still be writing the
+        // accumulator: one more bounded wait on that phase before the columns are
+        // released (the outputs of a timed-out tile are invalid either way: err is set)
+        tc::mbar_wait(&mbar, phase ^ 1, kSpins);
+        if (tid == 0) atomicExch(err, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem_base, 128);
 }
 
 // ---------------------------------------------------------------------------
@@ -517,12 +619,12 @@ cudaError_t pd::launch_mlp_grouped(const MlpRef *refs, const int4 *work, int n_w
                                    int *err, cudaStream_t s) {
     if (n_work == 0) return cudaSuccess;
     static_assert(sizeof(MlpRef) == 40, "MlpRef layout");
-    pd::mlp::k_mlp_fwd_grouped<<<n_work, 128, kFwdSmem, s>>>(refs, work, x, y, err);
+    pd::mlp::k_mlp_infer<<<n_work, pd::mlp::kInferThreads, kFwdSmem, s>>>(refs, work, x, y, err);
     return cudaGetLastError();
 }
 
 cudaError_t pd::mlp_init_attributes() {
-    return cudaFuncSetAttribute(pd::mlp::k_mlp_fwd_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
+    return cudaFuncSetAttribute(pd::mlp::k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
 }
 
 int pd::mlp_forward_stream(pd_mlp *m, const float *x, float *y, int batch, cudaStream_t s) {

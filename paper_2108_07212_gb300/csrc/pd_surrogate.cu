@@ -308,7 +308,14 @@ __device__ __forceinline__ void split_mma(uint32_t tmem, const uint8_t *ahi, con
 }
 
 constexpr int kProjSmem = 96 * 1024;     // A hi/lo 128 x 128, B hi/lo 32 x 128 (80 KB used)
-constexpr int kExpSmem = 100 * 1024;     // A hi/lo 128 x 32, B hi/lo 256 x 32 (48 KB used); <= 2 CTAs per SM
+// A hi/lo 128 x 32, B hi/lo 128 x 32 (32 KB) and the store staging, 4 x 128 rows of 32 + 1 floats (66 KB)
+constexpr int kExpSmem = 100 * 1024;
+// Threads of the expansion tile: four warpgroups.  Warp w reads TMEM lanes
+// 32 (w % 4) .. 32 (w % 4) + 31, so the thread's TMEM lane (its grain row of
+// the tile) is tid % 128 and warpgroup tid / 128 takes a quarter of the
+// operand staging and of the accumulator columns.
+constexpr int kExpThreads = 512;
+constexpr int kExpGroups = kExpThreads / kSurTile;
 
 // Projection tile: network rows [s0, s0 + 128) of template t times basis rows
 // [r0, r0 + kSurChunk): partial modal coefficients into sur_xpart[chunk].
@@ -423,15 +430,25 @@ __global__ void k_sur_reduce(DevPtrs d, KParams k) {
     const int g = d.slot_grain[row];
     const int t = d.g_tmpl[g];
     const int nch = tmpl_rows_pad(d, t) / kSurChunk;
+    // eight partials in flight at a time, added in chunk order
+    constexpr int kBatch = 8;
     float v = 0.f;
-    for (int c = 0; c < nch; ++c) v += d.sur_xpart[((size_t)c * k.G + row) * k.n_modes + m];
+    for (int c0 = 0; c0 < nch; c0 += kBatch) {
+        float p[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j)
+            p[j] = c0 + j < nch ? d.sur_xpart[((size_t)(c0 + j) * k.G + row) * k.n_modes + m] : 0.f;
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j)
+            if (c0 + j < nch) v += p[j];
+    }
     d.sur_x[(size_t)row * k.n_modes + m] = v;
 }
 
 // Expansion tile: network rows [s0, s0 + 128) of template t times basis rows
 // [r0, r0 + kSurExpandRows): surrogate bond force / (E h) of the tile's nodes
 // in the lattice frame, into sur_f (active grains only).
-__global__ void __launch_bounds__(128) k_sur_expand_tc(DevPtrs d, KParams k) {
+__global__ void __launch_bounds__(kExpThreads) k_sur_expand_tc(DevPtrs d, KParams k) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_base;
@@ -439,42 +456,51 @@ __global__ void __launch_bounds__(128) k_sur_expand_tc(DevPtrs d, KParams k) {
     uint8_t *sAh = sm, *sAl = sm + MR * KM * 2, *sBh = sm + 2 * MR * KM * 2, *sBl = sBh + NR * KM * 2;
     const int4 wk = d.exp_work[blockIdx.x];
     const int t = wk.x, s0 = wk.y, r0 = wk.z;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, wg = warp >> 2, lrow = tid & (MR - 1), lane = tid & 31;
     const int M = k.n_modes;
     const int slot0 = d.tmpl_slot[t], Gt = d.tmpl_slot[t + 1] - slot0;
     const int rows2 = 2 * (d.tmpl_node[t + 1] - d.tmpl_node[t]);
     if (warp == 0) tc::tmem_alloc(&tmem_base, NR);
     if (tid == 0) tc::mbar_init(&mbar, 1);
-    const int s = s0 + tid;
+    const int s = s0 + lrow;
     int g = -1;
     if (s < Gt) {
         g = d.slot_grain[slot0 + s];
         if (!d.sur_active[g]) g = -1;
     }
-    // A: network outputs (modal bond forces) of the tile's grains
+    // first node coordinate of the row's grain in the per-node arrays (-1: none)
+    const int fbase = g >= 0 ? 2 * d.g_start[g] : -1;
+    // A: network outputs (modal bond forces) of the tile's grains, modes
+    // [KM/4 wg, KM/4 (wg + 1)) per warpgroup
     {
+        constexpr int kPer = KM / kExpGroups;
+        static_assert(kPer % 2 == 0 && KM % kExpGroups == 0, "whole pairs per warpgroup");
         const float *y = g >= 0 ? d.sur_y + (size_t)(slot0 + s) * M : nullptr;
-        float yv[KM];                      // every load before the first store
+        float yv[kPer];                    // every load before the first store
 #pragma unroll
-        for (int kk = 0; kk < KM; ++kk) yv[kk] = (y && kk < M) ? y[kk] : 0.f;
+        for (int q = 0; q < kPer; ++q) {
+            const int kk = kPer * wg + q;
+            yv[q] = (y && kk < M) ? y[kk] : 0.f;
+        }
 #pragma unroll
-        for (int kk = 0; kk < KM; kk += 2) {
+        for (int q = 0; q < kPer; q += 2) {
+            const int kk = kPer * wg + q;
             uint32_t lo;
-            const uint32_t hi = split_pack(yv[kk], yv[kk + 1], lo);
-            *reinterpret_cast<uint32_t *>(sAh + tc::kmajor_off(tid, kk, MR)) = hi;
-            *reinterpret_cast<uint32_t *>(sAl + tc::kmajor_off(tid, kk, MR)) = lo;
+            const uint32_t hi = split_pack(yv[q], yv[q + 1], lo);
+            *reinterpret_cast<uint32_t *>(sAh + tc::kmajor_off(lrow, kk, MR)) = hi;
+            *reinterpret_cast<uint32_t *>(sAl + tc::kmajor_off(lrow, kk, MR)) = lo;
         }
     }
     // B: basis rows, node-major (each row: the modes of one node coordinate)
     {
         const uint16_t *bh = d.bnm_hi + ((size_t)d.tmpl_rows[t] + r0) * M;
         const uint16_t *bl = d.bnm_lo + ((size_t)d.tmpl_rows[t] + r0) * M;
-        constexpr int nb = NR * (KM / 8) / 128;
-        static_assert(NR * (KM / 8) % 128 == 0, "basis pieces must divide over the 128 threads");
+        constexpr int nb = NR * (KM / 8) / kExpThreads;
+        static_assert(NR * (KM / 8) % kExpThreads == 0, "basis pieces must divide over the threads");
         uint4 vh[nb], vl[nb];             // every load before the first store
 #pragma unroll
         for (int q = 0; q < nb; ++q) {
-            const int e = tid + q * 128, r = e / (KM / 8), k8 = (e % (KM / 8)) * 8;
+            const int e = tid + q * kExpThreads, r = e / (KM / 8), k8 = (e % (KM / 8)) * 8;
             vh[q] = vl[q] = make_uint4(0, 0, 0, 0);
             if (k8 < M) {
                 vh[q] = *reinterpret_cast<const uint4 *>(bh + (size_t)r * M + k8);
@@ -483,7 +509,7 @@ __global__ void __launch_bounds__(128) k_sur_expand_tc(DevPtrs d, KParams k) {
         }
 #pragma unroll
         for (int q = 0; q < nb; ++q) {
-            const int e = tid + q * 128, r = e / (KM / 8), k8 = (e % (KM / 8)) * 8;
+            const int e = tid + q * kExpThreads, r = e / (KM / 8), k8 = (e % (KM / 8)) * 8;
             *reinterpret_cast<uint4 *>(sBh + tc::kmajor_off(r, k8, NR)) = vh[q];
             *reinterpret_cast<uint4 *>(sBl + tc::kmajor_off(r, k8, NR)) = vl[q];
         }
@@ -500,17 +526,30 @@ __global__ void __launch_bounds__(128) k_sur_expand_tc(DevPtrs d, KParams k) {
     const bool ok = __syncthreads_and(tc::mbar_wait(&mbar, 0, kSurSpins)) != 0;
     if (ok) {
         tc::fence_after_sync();
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        float *dst = g >= 0 ? reinterpret_cast<float *>(d.sur_f) + 2 * (size_t)d.g_start[g] : nullptr;
-        for (int c0 = 0; c0 < NR; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
-            if (dst)
+        // columns [NR/4 wg, NR/4 (wg + 1)) of the thread's row, staged in shared
+        // memory so that a warp stores one grain's 32 consecutive values per
+        // instruction (the warp's rows are its own threads' rows: no block barrier)
+        constexpr int kCols = NR / kExpGroups, kStride = kCols + 1;
+        static_assert(kCols == 32, "one column per lane in the coalesced store");
+        static_assert(2 * MR * KM * 2 + 2 * NR * KM * 2 + kExpGroups * MR * kStride * 4 <= kExpSmem,
+                      "operands and staging fit the shared memory");
+        float *stage = reinterpret_cast<float *>(sm + 2 * MR * KM * 2 + 2 * NR * KM * 2) + (size_t)wg * MR * kStride;
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
 #pragma unroll
-                for (int q = 0; q < 16; q += 2) {
-                    const int r = r0 + c0 + q;
-                    if (r < rows2) *reinterpret_cast<float2 *>(dst + r) = make_float2(v[q], v[q + 1]);
-                }
+        for (int c0 = 0; c0 < kCols; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + lane_base + (uint32_t)(kCols * wg + c0), v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) stage[lrow * kStride + c0 + q] = v[q];
+        }
+        __syncwarp();
+        const int rw0 = (warp & 3) * 32;
+        const int r = r0 + kCols * wg + lane;
+        float *sf = reinterpret_cast<float *>(d.sur_f);
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+            const int bj = __shfl_sync(0xffffffffu, fbase, j);    // no load in the store loop
+            if (bj >= 0 && r < rows2) sf[(size_t)bj + r] = stage[(rw0 + j) * kStride + lane];
         }
     } else {
         // drain the timed-out phase before the columns are released; the tile's
@@ -626,22 +665,8 @@ __global__ void __launch_bounds__(kSurThreads) k_sur_judge(DevPtrs d, KParams k)
     }
 }
 
-// f = -Lambda q + net(q), in place in the network output rows.
-__global__ void k_sur_combine(DevPtrs d, KParams k) {
-    const int g = blockIdx.x;
-    const int t = d.g_tmpl[g];
-    if (t < 0 || !d.sur_active[g] || (int)threadIdx.x >= k.n_modes) return;
-    const size_t row = (size_t)(d.tmpl_slot[t] + d.g_slot[g]) * k.n_modes + threadIdx.x;
-    d.sur_y[row] -= d.sur_lambda[t * k.n_modes + threadIdx.x] * d.sur_x[row];
-}
-
 // ---------------------------------------------------------------------------
 // launchers
-
-cudaError_t launch_sur_combine(const DevPtrs &d, const KParams &k, cudaStream_t s) {
-    k_sur_combine<<<k.G, 32, 0, s>>>(d, k);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_sur_frame(const DevPtrs &d, const KParams &k, int all_templated, cudaStream_t s) {
     k_sur_frame<<<k.G, kSurThreads, 0, s>>>(d, k, all_templated);
@@ -673,7 +698,7 @@ cudaError_t launch_sur_reduce(const DevPtrs &d, const KParams &k, cudaStream_t s
 
 cudaError_t launch_sur_expand_tc(const DevPtrs &d, const KParams &k, cudaStream_t s) {
     if (k.n_exp_work == 0) return cudaSuccess;
-    k_sur_expand_tc<<<k.n_exp_work, 128, kExpSmem, s>>>(d, k);
+    k_sur_expand_tc<<<k.n_exp_work, kExpThreads, kExpSmem, s>>>(d, k);
     return cudaGetLastError();
 }
 

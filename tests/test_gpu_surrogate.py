@@ -140,6 +140,43 @@ def test_tensor_core_products_match_fp64_host():
     assert worst <= 1e-4, worst
 
 
+def test_in_step_networks_match_the_network_oracle():
+    """The networks as the step runs them (every template's tiles in one
+    launch, f = net(q) - Lambda q formed in the output epilogue) against the
+    oracle network with the same bfloat16 rounding, element by element, on the
+    modal coefficients the step fed them.  Random networks (every layer
+    non-zero), 150 hexagons (two 128-row tiles of one template) and 12 disks."""
+    from oracle import mlp_oracle as M
+    w = I.free_grains(shapes=("hexagon", "disk"), n_per_shape=150, h_ratio=10)
+    keep = np.r_[np.arange(150), np.arange(150, 162)]
+    w.grain_shape = w.grain_shape[keep]
+    w.grain_geom = w.grain_geom[keep]
+    S = B.Simulation(w, precision=B.PD_FP32_SPLIT, store_parts=True, device="cuda:0",
+                     surrogate=lambda s: SU.build_basis(s, judge_every=50))
+    cfg = S.surrogate_basis
+    tmpl = cfg["template_of_grain"]
+    counts = np.bincount(tmpl)
+    params = [M.init_params(11 + t) for t in range(len(counts))]
+    nets = [B.MLP(max_batch=int(c), params=params[t]) for t, c in enumerate(counts)]
+    for t, net in enumerate(nets):
+        S.surrogate_set_mlp(t, net)
+    S.surrogate_enable(True)
+    _, u = _deformed(S, cfg, amp=0.3, seed=5)
+    S.set("DISP", u)
+    S.set("STEP", np.array([7], np.int64))                   # not a judge step
+    q, y = S.surrogate_inspect()
+    lam = cfg["lambda_"].reshape(-1, 32)
+    worst = 0.0
+    for t in range(len(counts)):
+        m = tmpl == t
+        net_ref, _ = M.forward(params[t].astype(np.float64), q[m], bf16=True)
+        lin = lam[t] * q[m].astype(np.float64)
+        bound = 2.0 ** -6 * (np.abs(net_ref).max() + np.abs(net_ref)) + 1e-6 * np.abs(lin).max()
+        assert np.abs(net_ref).max() > 0
+        worst = max(worst, float((np.abs(y[m] - (net_ref - lin)) / bound).max()))
+    assert worst <= 1.0, worst
+
+
 def _static_samples(w, cfg_fn, amp, seed, draws):
     """Training pairs from the full bond kernel at random modal deformations
     (largest nodal displacement up to amp h) of every grain: (q, f) per template."""
