@@ -43,11 +43,14 @@ BYTES_PER_BOND_FP64 = 12
 # the FP64 pipe occupies it for 32 / 2 = 16 SM cycles whatever its active lanes
 FP64_LANES_PER_SM_CYCLE = 2
 N_SM = 152
-# algorithmic bytes of the FP32-split force phase: per node the float-float position pq (16 B),
-# grain, row pointer, broken-bond word and contact-list length (16 B), hash-grid cell for the wall
-# test (8 B), FP64 v and a read and written (64 B); per bond the column (4 B)
-BYTES_PER_NODE_FP32 = 104
-BYTES_PER_BOND_FP32 = 4
+# algorithmic bytes of the FP32-split force phase, bonds from the lattice stencil (every workload
+# here: horizon 3 h): the lane sums read the float-float position pq (16 B), the stencil record
+# (16 B), grain, broken-bond word and contact-list length (12 B) and write the force total (8 B);
+# the epilogue reads the force total (8 B), FP64 v and a (32 B), grain (4 B) and the hash-grid cell
+# of the wall test (8 B) and writes v and a (32 B).  136 B per node and no per-bond stream (nodes
+# whose lattice row has a gap read CSR columns instead, 4 B per bond, not counted).
+BYTES_PER_NODE_FP32 = 136
+BYTES_PER_BOND_FP32 = 0
 B_STATUS_REBUILDS = 5    # status slot counting the contact candidate-list rebuilds
 
 
@@ -353,21 +356,28 @@ def _timed_steps(sim, stream, flush, steps, warmup, torch):
 
 # algorithmic bytes of one whole FP32-split time step per node (displacement
 # update 112 B: X + shift, u, v, a and the rebuild reference read, u and pq
-# written; force phase 104 B) + 4 B per bond; the candidate-list rebuild runs
-# only in some steps and is not counted
-BYTES_PER_NODE_STEP_FP32 = 216
+# written; force phase 136 B); the candidate-list rebuild runs only in some
+# steps and is not counted
+BYTES_PER_NODE_STEP_FP32 = 248
 
 
 # DRAM bytes (read + write) per launch of the force-phase kernels, per workload,
-# from one ncu capture of the timed steps (the bench marks them with
-# cudaProfilerStart/Stop), e.g.
+# from one ncu capture (one pass) of the timed steps (the bench marks them with
+# cudaProfilerStart/Stop; path mode 6 = mode 2 without the conditional graph
+# node, which ncu cannot trace; the same kernels), e.g.
 #   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
-#       --profile-from-start off -k regex:k_sums -c 3 --csv python bench.py --steps 3 --warmup 3 --legs= --no-cpu
-# (medians over the captured launches; the summaries are committed under
-# profiles/).  They hold while the kernel sources hash to TRAFFIC_DIGEST;
-# otherwise, or for a kernel not captured, traffic is null.
-TRAFFIC = {}
-TRAFFIC_DIGEST = ""
+#       --profile-from-start off -k regex:"k_sums|k_epilogue" --csv
+#       python bench.py --steps 3 --warmup 3 --legs= --no-cpu --path 6,1
+# (medians over the three captured launches; summaries under profiles/).  They
+# hold while the kernel sources hash to TRAFFIC_DIGEST; otherwise, or for a
+# kernel not captured, traffic is null.
+TRAFFIC = {
+    "ensemble64": {"k_sums<1, 1>": 356492288, "k_epilogue<1>": 525755392,
+                   "k_sums<0, 1>": 2233876992, "k_epilogue<0>": 584006912},
+    "compaction500": {"k_sums<1, 1>": 23607808, "k_epilogue<1>": 27246336,
+                      "k_sums<0, 1>": 170567424, "k_epilogue<0>": 31435520},
+}
+TRAFFIC_DIGEST = "b99711edcaea1cc0470b2c7bdc3f27d74b69656e"
 TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu", "pd_common.cu", "pd_internal.h")
 
 
@@ -437,11 +447,13 @@ def _force_kernel_ms(sim, n=20):
     return float(np.median(ms))
 
 
-def _roof_fp32(sim, f_ms, hbm, label):
+def _roof_fp32(sim, f_ms, hbm, label, path=None, workload=None):
     nbytes = BYTES_PER_NODE_FP32 * sim.N + BYTES_PER_BOND_FP32 * sim.n_bonds
     a = nbytes / (f_ms / 1e3) / 1e9
-    return {"bound": "hbm", "kernel": "k_force32", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
-            "traffic": None, "note": f"{label}: {BYTES_PER_NODE_FP32} B/node + {BYTES_PER_BOND_FP32} B/bond x "
+    traffic = force_phase_traffic(path, True, workload) if path and workload else None
+    return {"bound": "hbm", "kernel": _force_kernels(path["mode"], True) if path else "k_force32", "achieved": a,
+            "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+            "traffic": traffic, "note": f"{label}: {BYTES_PER_NODE_FP32} B/node + {BYTES_PER_BOND_FP32} B/bond x "
                                      f"{sim.N} nodes / {sim.n_bonds} bonds, median event time {f_ms * 1e3:.1f} us (of measured)"}
 
 
@@ -449,8 +461,11 @@ def _roof_fp32(sim, f_ms, hbm, label):
 # (ncu smsp__inst_executed_pipe_fp64.sum, one launch each, --clock-control none;
 # profiles/force64_*.md), per workload; they hold while the kernel sources hash
 # to FP64_INST_DIGEST, otherwise the ALU roofline is left unmeasured.
-FP64_INST = {}
-FP64_INST_DIGEST = ""
+FP64_INST = {
+    "ensemble64": {"k_sums<0, 1>": 32548167, "k_epilogue<0>": 1674556},
+    "compaction500": {"k_sums<0, 1>": 2492904, "k_epilogue<0>": 130368},
+}
+FP64_INST_DIGEST = "b99711edcaea1cc0470b2c7bdc3f27d74b69656e"
 
 
 def _roof_fp64(sim, f_ms, path, workload, clk, hbm):
@@ -471,7 +486,8 @@ def _roof_fp64(sim, f_ms, path, workload, clk, hbm):
     hbm_a = nbytes / (f_ms / 1e3) / 1e9
     achieved = None if inst is None else 32.0 * inst / (f_ms / 1e3) / 1e12
     return {"bound": "alu", "kernel": _force_kernels(m, False), "achieved": achieved, "peak": peak,
-            "unit": "T FP64 lane-ops/s", "frac": None if achieved is None else achieved / peak, "traffic": None,
+            "unit": "T FP64 lane-ops/s", "frac": None if achieved is None else achieved / peak,
+            "traffic": force_phase_traffic(path, False, workload),
             "hbm": {"achieved": hbm_a, "peak": hbm, "unit": "GB/s", "frac": hbm_a / hbm,
                     "note": f"{BYTES_PER_NODE_FP64} B/node + {BYTES_PER_BOND_FP64} B/bond (of measured)"},
             "note": f"peak = {N_SM} SMs x {FP64_LANES_PER_SM_CYCLE} FP64 lanes/cycle x {mhz:.0f} MHz (derived); "
@@ -494,7 +510,8 @@ def leg_compaction(B, I, dev, stream, torch, hbm, clk, steps=200):
         f_ms = _force_kernel_ms(sim)
         out[name] = {"value": sim.N * steps / dt, "unit": "node-steps/s", "ms_per_step": 1e3 * dt / steps,
                      "bond_evals_per_s": sim.n_bonds * steps / dt, "force_kernel_us": 1e3 * f_ms,
-                     "roofline": _roof_fp32(sim, f_ms, hbm, "500-grain compaction") if name == "fp32"
+                     "roofline": _roof_fp32(sim, f_ms, hbm, "500-grain compaction", tune, "compaction500")
+                     if name == "fp32"
                      else _roof_fp64(sim, f_ms, tune, "compaction500", clk, hbm),
                      "step_path": tune, "status": int(sim.status()[0])}
         out["nodes"], out["directed_bonds"] = int(sim.N), int(sim.n_bonds)

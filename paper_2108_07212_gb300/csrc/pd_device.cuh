@@ -855,7 +855,7 @@ __device__ __forceinline__ void finish_node(const DevPtrs &d, const KParams &k, 
         d.v[vin ^ 1][i] = vn;
     }
     d.a[i] = make_double2(ax, ay);
-    if (((__double2hiint(ax) | 0x800FFFFF) == -1) || ((__double2hiint(ay) | 0x800FFFFF) == -1))   // inf or NaN
+    if ((((unsigned)__double2hiint(ax) | 0x800FFFFFu) == 0xFFFFFFFFu) || (((unsigned)__double2hiint(ay) | 0x800FFFFFu) == 0xFFFFFFFFu))   // inf or NaN
         atomicAdd(&d.status[PD_STATUS_NONFINITE], 1);
     if (k.store) {
         d.F[i] = make_double2(Fx, Fy);
@@ -889,7 +889,7 @@ __device__ __forceinline__ void finish_node32_total(const DevPtrs &d, const KPar
     // finiteness from the exponent bits (no FP64 compare)
     const bool bad = ((__float_as_uint(fx) | 0x807FFFFFu) == 0xFFFFFFFFu) ||
                      ((__float_as_uint(fy) | 0x807FFFFFu) == 0xFFFFFFFFu) ||
-                     (walls && (((__double2hiint(Fwx) | 0x800FFFFF) == -1) || ((__double2hiint(Fwy) | 0x800FFFFF) == -1)));
+                     (walls && ((((unsigned)__double2hiint(Fwx) | 0x800FFFFFu) == 0xFFFFFFFFu) || (((unsigned)__double2hiint(Fwy) | 0x800FFFFFu) == 0xFFFFFFFFu)));
     if (bad) atomicAdd(&d.status[PD_STATUS_NONFINITE], 1);
 }
 
@@ -905,7 +905,7 @@ __device__ __forceinline__ void finish_node64_total(const DevPtrs &d, const KPar
     if (update_v)
         d.v[vin ^ 1][i] = make_double2(fma(k.half_dt, ao.x + ax, vi.x), fma(k.half_dt, ao.y + ay, vi.y));
     d.a[i] = make_double2(ax, ay);
-    if (((__double2hiint(ax) | 0x800FFFFF) == -1) || ((__double2hiint(ay) | 0x800FFFFF) == -1))   // inf or NaN
+    if ((((unsigned)__double2hiint(ax) | 0x800FFFFFu) == 0xFFFFFFFFu) || (((unsigned)__double2hiint(ay) | 0x800FFFFFu) == 0xFFFFFFFFu))   // inf or NaN
         atomicAdd(&d.status[PD_STATUS_NONFINITE], 1);
 }
 
