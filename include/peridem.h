@@ -94,6 +94,8 @@ typedef struct pd_params {
 #define PD_FIELD_DISP 1         /* double[2N] displacement u (get/set)               */
 #define PD_FIELD_VEL 2          /* double[2N] velocity (get/set)                     */
 #define PD_FIELD_ACC 3          /* double[2N] acceleration of the last step (get/set)*/
+                                /* (FP32-split contexts keep it in FP32: a set      */
+                                /* rounds to float, a get returns the floats)       */
 #define PD_FIELD_POS 4          /* double[2N] current position X + u (get)           */
 #define PD_FIELD_FORCE 5        /* double[2N] total nodal force, last evaluation     */
 #define PD_FIELD_FORCE_PARTS 6  /* double[8N] bond|self|neighbour|wall (store_parts) */

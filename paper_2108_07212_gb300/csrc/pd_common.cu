@@ -335,6 +335,28 @@ cudaError_t launch_predict(const DevPtrs &d, const KParams &k, int vin, int adva
     return cudaGetLastError();
 }
 
+__global__ void k_widen(const float2 *__restrict__ src, double2 *__restrict__ dst, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = make_double2((double)src[i].x, (double)src[i].y);
+}
+
+__global__ void k_narrow(const double2 *__restrict__ src, float2 *__restrict__ dst, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = make_float2(__double2float_rn(src[i].x), __double2float_rn(src[i].y));
+}
+
+cudaError_t launch_widen(const float2 *src, double2 *dst, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_widen<<<(unsigned)std::min<size_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_narrow(const double2 *src, float2 *dst, size_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_narrow<<<(unsigned)std::min<size_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rebuild(const DevPtrs &d, const KParams &k, cudaStream_t s) {
     const int nb = nblk(k.T, kScanTile), nn = nblk(k.N, kBlock);
     k_bin<<<nn, kBlock, 0, s>>>(d, k);

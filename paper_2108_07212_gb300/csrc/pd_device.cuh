@@ -563,9 +563,10 @@ __device__ __forceinline__ bool predict_node(const DevPtrs &d, const KParams &k,
     const float dmax2 = k.dmax2;
     if (d.pq) {
         if (advance) {
-            const double2 v = ldm<PERSIST>(&d.v[vin][i]), a = ldm<PERSIST>(&d.a[i]);
-            u.x = fma(k.dt, v.x, fma(k.half_dt2, a.x, u.x));
-            u.y = fma(k.dt, v.y, fma(k.half_dt2, a.y, u.y));
+            const double2 v = ldm<PERSIST>(&d.v[vin][i]);
+            const float2 a = ldm<PERSIST>(&d.af[i]);       // FP32 acceleration, widened exactly
+            u.x = fma(k.dt, v.x, fma(k.half_dt2, f2d_bits(a.x), u.x));
+            u.y = fma(k.dt, v.y, fma(k.half_dt2, f2d_bits(a.y), u.y));
             d.u[i] = u;
         }
         const double2 xs = __ldg(&d.xs[i]);
@@ -866,31 +867,33 @@ __device__ __forceinline__ void finish_node(const DevPtrs &d, const KParams &k, 
     }
 }
 
-// FP32-split update without per-part output: the three lane-summed parts are
-// added in FP32 (their rounding is far below the path's force error), the wall
-// force in FP64 where there is one, then a = F (1 / m) + g and the
-// velocity-Verlet update in FP64 with fused multiply-adds (the fewest FP64
-// operations on GB300's narrow FP64 pipe).
-// (ao: the previous acceleration, loaded by the caller with the node's other
-// independent loads)
+// FP32-split update: the lane-summed parts are added in FP32 (their rounding is
+// far below the path's force error), the wall force in FP64 where there is one;
+// a = F (1 / m) + g is formed and stored in FP32 (the force carries FP32
+// precision already), the velocity-Verlet increment dt/2 (a_old + a) is
+// formed in FP32 and added to the FP64 velocity: two FP64 additions per node
+// on GB300's narrow FP64 pipe.  (ao: the previous acceleration, loaded by the
+// caller with the node's other independent loads.)
 template <bool PERSIST>
 __device__ __forceinline__ void finish_node32_total(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
-                                                    double2 vi, double2 ao, float fx, float fy, bool walls,
-                                                    double Fwx, double Fwy, double inv_m) {
-    double Fx = f2d_bits(fx), Fy = f2d_bits(fy);
+                                                    double2 vi, float2 ao, float fx, float fy, bool walls,
+                                                    double Fwx, double Fwy, float inv_m) {
+    float ax, ay;
     if (walls) {
-        Fx += Fwx;
-        Fy += Fwy;
+        ax = fmaf(__double2float_rn(f2d_bits(fx) + Fwx), inv_m, k.gxf);
+        ay = fmaf(__double2float_rn(f2d_bits(fy) + Fwy), inv_m, k.gyf);
+    } else {
+        ax = fmaf(fx, inv_m, k.gxf);
+        ay = fmaf(fy, inv_m, k.gyf);
     }
-    const double ax = fma(Fx, inv_m, k.gx), ay = fma(Fy, inv_m, k.gy);
-    if (update_v)
-        d.v[vin ^ 1][i] = make_double2(fma(k.half_dt, ao.x + ax, vi.x), fma(k.half_dt, ao.y + ay, vi.y));
-    d.a[i] = make_double2(ax, ay);
+    if (update_v) {
+        const float hdt = 0.5f * k.dtf;
+        d.v[vin ^ 1][i] = make_double2(vi.x + f2d_bits(hdt * (ao.x + ax)), vi.y + f2d_bits(hdt * (ao.y + ay)));
+    }
+    d.af[i] = make_float2(ax, ay);
     // finiteness from the exponent bits (no FP64 compare)
-    const bool bad = ((__float_as_uint(fx) | 0x807FFFFFu) == 0xFFFFFFFFu) ||
-                     ((__float_as_uint(fy) | 0x807FFFFFu) == 0xFFFFFFFFu) ||
-                     (walls && ((((unsigned)__double2hiint(Fwx) | 0x800FFFFFu) == 0xFFFFFFFFu) || (((unsigned)__double2hiint(Fwy) | 0x800FFFFFu) == 0xFFFFFFFFu)));
-    if (bad) atomicAdd(&d.status[PD_STATUS_NONFINITE], 1);
+    if (((__float_as_uint(ax) | 0x807FFFFFu) == 0xFFFFFFFFu) || ((__float_as_uint(ay) | 0x807FFFFFu) == 0xFFFFFFFFu))
+        atomicAdd(&d.status[PD_STATUS_NONFINITE], 1);
 }
 
 // FP64 update from the total of the lane-summed parts, T = (F_b + F_s) + F_n
@@ -1380,11 +1383,11 @@ __device__ __forceinline__ void node_epilogue32(const DevPtrs &d, const KParams 
     // the node's independent loads first, all in flight together (the pass is
     // bound by memory latency): velocity, previous acceleration, grain, cell
     const double2 vi = ldm<PERSIST>(&d.v[vin][i]);
-    const double2 ao = update_v ? ldm<PERSIST>(&d.a[i]) : make_double2(0.0, 0.0);
+    const float2 ao = update_v ? ldm<PERSIST>(&d.af[i]) : make_float2(0.f, 0.f);
     const int gi = __ldg(&d.grain[i]);
     const int2 cell = ldm<PERSIST>(&d.cell[i]);
     const int ag = __ldg(&d.g_agg[gi]);
-    const double inv_m = __ldg(&d.g_invm[gi]);
+    const float inv_m = __ldg(&d.g_invmf[gi]);
     const int4 wc = ldm<PERSIST>(&d.wall_cell[ag]);
     Sums32 f = fin;
     if constexpr (!PERSIST) {
@@ -1410,14 +1413,17 @@ __device__ __forceinline__ void node_epilogue32(const DevPtrs &d, const KParams 
         wall_force32(k, A, Knf, rhof, Kn, rho, ldm<PERSIST>(d.t_now), pi.x, pi.y, vi.x, vi.y, __ldg(&d.V[i]), Fwx,
                      Fwy, d.status);
     }
-    if (k.store)
-        finish_node<PERSIST, true>(d, k, i, vin, update_v, vi, 0.0, (double)f.bx, (double)f.by, (double)f.sx,
-                                   (double)f.sy, (double)f.nx, (double)f.ny, Fwx, Fwy, inv_m);
-    else if (total)      // the lane-sum pass summed the parts: f.bx / f.by hold the total
-        finish_node32_total<PERSIST>(d, k, i, vin, update_v, vi, ao, f.bx, f.by, walls, Fwx, Fwy, inv_m);
-    else
-        finish_node32_total<PERSIST>(d, k, i, vin, update_v, vi, ao, (f.bx + f.sx) + f.nx, (f.by + f.sy) + f.ny,
-                                     walls, Fwx, Fwy, inv_m);
+    // the lane-sum pass may have summed the parts already (f.bx / f.by hold the total)
+    const float fx = total ? f.bx : (f.bx + f.sx) + f.nx, fy = total ? f.by : (f.by + f.sy) + f.ny;
+    if (k.store) {
+        // per-part output in FP64 (the parts as the lanes summed them, the total as the update uses it)
+        d.F[i] = make_double2(f2d_bits(fx) + Fwx, f2d_bits(fy) + Fwy);
+        d.parts[i] = make_double2((double)f.bx, (double)f.by);
+        d.parts[k.N + i] = make_double2((double)f.sx, (double)f.sy);
+        d.parts[2 * (size_t)k.N + i] = make_double2((double)f.nx, (double)f.ny);
+        d.parts[3 * (size_t)k.N + i] = make_double2(Fwx, Fwy);
+    }
+    finish_node32_total<PERSIST>(d, k, i, vin, update_v, vi, ao, fx, fy, walls, Fwx, Fwy, inv_m);
 }
 
 }  // namespace pd

@@ -331,7 +331,11 @@ size_t layout(pd_ctx *c, char *base) {
     carve(base, off, d.u, N);
     carve(base, off, d.v[0], N);
     carve(base, off, d.v[1], N);
-    carve(base, off, d.a, N);
+    const bool fp32 = c->prm.precision == PD_FP32_SPLIT;
+    carve(base, off, d.a, fp32 ? 0 : N);
+    carve(base, off, d.af, fp32 ? N : 0);
+    if (fp32) d.a = nullptr;
+    else d.af = nullptr;
     carve(base, off, d.p, N);
     carve(base, off, d.F, c->prm.store_parts ? N : 0);
     carve(base, off, d.parts, c->prm.store_parts ? 4 * N : 0);
@@ -393,6 +397,7 @@ size_t layout(pd_ctx *c, char *base) {
         d.gc = nullptr;
     }
     carve(base, off, d.g_invm, G);
+    carve(base, off, d.g_invmf, G);
     carve(base, off, d.bu, N);
     carve(base, off, d.bv, N);
     carve(base, off, d.ba, N);
@@ -951,6 +956,8 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     k.rdf = (float)p.damping_ratio;
     k.muf = (float)p.friction;
     k.dtf = (float)p.dt;
+    k.gxf = (float)p.gravity[0];
+    k.gyf = (float)p.gravity[1];
     k.guard = 1e-4f;
     k.mat = c->has_mat ? 1 : 0;
     // one rebuild trigger for all aggregates: the smallest (the most cautious)
@@ -988,7 +995,8 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     PD_CUDA(cudaMemsetAsync(d.u, 0, 16 * N, s));
     PD_CUDA(cudaMemcpyAsync(d.v[0], c->v0.data(), 16 * N, cudaMemcpyHostToDevice, s));
     PD_CUDA(cudaMemsetAsync(d.v[1], 0, 16 * N, s));
-    PD_CUDA(cudaMemsetAsync(d.a, 0, 16 * N, s));
+    if (d.af) PD_CUDA(cudaMemsetAsync(d.af, 0, 8 * N, s));
+    else PD_CUDA(cudaMemsetAsync(d.a, 0, 16 * N, s));
     PD_CUDA(cudaMemcpyAsync(d.V, c->V.data(), 8 * N, cudaMemcpyHostToDevice, s));
     PD_CUDA(cudaMemcpyAsync(d.grain, c->grain.data(), 4 * N, cudaMemcpyHostToDevice, s));
     PD_CUDA(cudaMemcpyAsync(d.row_ptr, c->row_ptr.data(), 4 * (N + 1), cudaMemcpyHostToDevice, s));
@@ -1166,6 +1174,9 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     invm.resize(G);
     for (size_t g = 0; g < G; ++g) invm[g] = 1.0 / (c->g_rho[g] * c->V[c->g_start[g]]);
     PD_CUDA(cudaMemcpyAsync(d.g_invm, invm.data(), 8 * G, cudaMemcpyHostToDevice, s));
+    std::vector<float> invmf(invm.begin(), invm.end());
+    PD_CUDA(cudaMemcpyAsync(d.g_invmf, invmf.data(), 4 * G, cudaMemcpyHostToDevice, s));
+    PD_CUDA(cudaStreamSynchronize(s));
     c->vcur = 0;
     c->steps_done = 0;
     c->state = 3;
@@ -1255,7 +1266,17 @@ int pd_get_state(pd_ctx *c, int field, void *dst, size_t bytes, int dst_on_devic
     switch (field) {
         case PD_FIELD_DISP: PD_CUDA(cudaMemcpyAsync(dst, d.u, fb, kind, s)); break;
         case PD_FIELD_VEL: PD_CUDA(cudaMemcpyAsync(dst, d.v[c->vcur], fb, kind, s)); break;
-        case PD_FIELD_ACC: PD_CUDA(cudaMemcpyAsync(dst, d.a, fb, kind, s)); break;
+        case PD_FIELD_ACC:
+            if (!d.af) {
+                PD_CUDA(cudaMemcpyAsync(dst, d.a, fb, kind, s));
+            } else if (dst_on_device == PD_MEM_DEVICE) {
+                PD_CUDA(pd::launch_widen(d.af, static_cast<double2 *>(dst), (size_t)c->N, s));
+            } else {
+                // widened on the device into the backup buffer, then copied
+                PD_CUDA(pd::launch_widen(d.af, d.ba, (size_t)c->N, s));
+                PD_CUDA(cudaMemcpyAsync(dst, d.ba, fb, cudaMemcpyDeviceToHost, s));
+            }
+            break;
         case PD_FIELD_POS:
             PD_CUDA(pd::launch_positions(d, c->kp, s));
             PD_CUDA(cudaMemcpyAsync(dst, d.p, fb, kind, s));
@@ -1305,7 +1326,17 @@ int pd_set_state(pd_ctx *c, int field, const void *src, size_t bytes, int src_on
     switch (field) {
         case PD_FIELD_DISP: PD_CUDA(cudaMemcpyAsync(d.u, src, fb, kind, s)); break;
         case PD_FIELD_VEL: PD_CUDA(cudaMemcpyAsync(d.v[c->vcur], src, fb, kind, s)); break;
-        case PD_FIELD_ACC: PD_CUDA(cudaMemcpyAsync(d.a, src, fb, kind, s)); break;
+        case PD_FIELD_ACC:
+            if (!d.af) {
+                PD_CUDA(cudaMemcpyAsync(d.a, src, fb, kind, s));
+            } else if (src_on_device == PD_MEM_DEVICE) {
+                PD_CUDA(pd::launch_narrow(static_cast<const double2 *>(src), d.af, (size_t)c->N, s));
+            } else {
+                // through the backup buffer, rounded to float on the device
+                PD_CUDA(cudaMemcpyAsync(d.ba, src, fb, cudaMemcpyHostToDevice, s));
+                PD_CUDA(pd::launch_narrow(d.ba, d.af, (size_t)c->N, s));
+            }
+            break;
         case PD_FIELD_STEP: {
             int64_t st = 0;
             if (src_on_device == PD_MEM_DEVICE) PD_CUDA(cudaMemcpy(&st, src, 8, cudaMemcpyDeviceToHost));
@@ -1474,7 +1505,8 @@ int pd_autotune(pd_ctx *c, double *report) {
     // back up the state; every trial starts from it and it is restored at the end
     PD_CUDA(cudaMemcpyAsync(d.bu, d.u, 16 * N, cudaMemcpyDeviceToDevice, s));
     PD_CUDA(cudaMemcpyAsync(d.bv, d.v[c->vcur], 16 * N, cudaMemcpyDeviceToDevice, s));
-    PD_CUDA(cudaMemcpyAsync(d.ba, d.a, 16 * N, cudaMemcpyDeviceToDevice, s));
+    if (d.af) PD_CUDA(cudaMemcpyAsync(d.ba, d.af, 8 * N, cudaMemcpyDeviceToDevice, s));
+    else PD_CUDA(cudaMemcpyAsync(d.ba, d.a, 16 * N, cudaMemcpyDeviceToDevice, s));
     PD_CUDA(cudaMemcpyAsync(d.bbits, d.bits, 4 * N * c->wpn, cudaMemcpyDeviceToDevice, s));
     long long step0 = 0;
     int32_t st0[PD_STATUS_COUNT];
@@ -1484,7 +1516,8 @@ int pd_autotune(pd_ctx *c, double *report) {
     auto restore = [&]() -> int {
         PD_CUDA(cudaMemcpyAsync(d.u, d.bu, 16 * N, cudaMemcpyDeviceToDevice, s));
         PD_CUDA(cudaMemcpyAsync(d.v[c->vcur], d.bv, 16 * N, cudaMemcpyDeviceToDevice, s));
-        PD_CUDA(cudaMemcpyAsync(d.a, d.ba, 16 * N, cudaMemcpyDeviceToDevice, s));
+        if (d.af) PD_CUDA(cudaMemcpyAsync(d.af, d.ba, 8 * N, cudaMemcpyDeviceToDevice, s));
+        else PD_CUDA(cudaMemcpyAsync(d.a, d.ba, 16 * N, cudaMemcpyDeviceToDevice, s));
         PD_CUDA(cudaMemcpyAsync(d.bits, d.bbits, 4 * N * c->wpn, cudaMemcpyDeviceToDevice, s));
         PD_CUDA(cudaMemcpyAsync(d.step, &step0, 8, cudaMemcpyHostToDevice, s));
         PD_CUDA(cudaMemcpyAsync(d.status, st0, sizeof(st0), cudaMemcpyHostToDevice, s));

@@ -108,9 +108,11 @@ struct DevPtrs {
     uint4 *stn;         // lattice stencil of every node's bonds (see kStnIrregular), when KParams::stencil
     float4 *gc;         // per grain: (c_w, s0, eps, rho) as floats
     double *g_invm;     // per grain: 1 / (rho V)
+    float *g_invmf;     // the same as floats (FP32-split contexts)
     int4 *wall_cell;    // per aggregate: hash-grid cells of its walls x_lo, x_hi, y_lo, y_hi at the current time
     // autotuner backup of the state
     double2 *bu, *bv, *ba;
+    float2 *af;         // FP32-split contexts: the acceleration, a = F / m + g rounded to float (d.a unused)
     uint32_t *bbits;
     // learned modal surrogate (FP32-split path)
     int *g_start;       // first node of every grain (G + 1)
@@ -151,6 +153,7 @@ struct KParams {
     unsigned T;         // hash buckets (power of two)
     double rho, rd, mu, gx, gy, dt, half_dt, half_dt2;
     float rhof, rdf, muf, dtf;   // the same as floats (FP32-split contact laws)
+    float gxf, gyf;              // gravity as floats (FP32-split acceleration)
     float guard;        // FP32-split: |(|s| - s0)| < guard * s0 re-decides breaking in FP64
     float dmax2;        // smallest (kSkinTrigger skin)^2 of the aggregates: rebuild trigger
     int mat;            // 1: per-grain materials (K_n per pair, densities per grain)
@@ -228,6 +231,9 @@ cudaError_t launch_force(const DevPtrs &d, const KParams &k, int vin, int update
 cudaError_t launch_force64(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s, int phase = 0);
 cudaError_t launch_force32(const DevPtrs &d, const KParams &k, int vin, int update_v, cudaStream_t s, int phase = 0);
 cudaError_t launch_positions(const DevPtrs &d, const KParams &k, cudaStream_t s);
+// Element-wise conversions of n float2 / double2 pairs (the FP32-split acceleration field).
+cudaError_t launch_widen(const float2 *src, double2 *dst, size_t n, cudaStream_t s);
+cudaError_t launch_narrow(const double2 *src, float2 *dst, size_t n, cudaStream_t s);
 cudaError_t launch_diagnostics(const DevPtrs &d, const KParams &k, int vcur, cudaStream_t s);
 // Particle damage of every grain (gdam[G]) and per-aggregate sums of the wall
 // terms (wsum[16 n_agg]) at the current state.

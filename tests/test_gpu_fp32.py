@@ -168,3 +168,23 @@ def test_fp32_stiff_material_contact_and_walls_stay_finite():
     assert np.abs(parts_o[2]).max() > 0 and np.abs(parts_o[3]).max() > 0
     assert np.all(np.isfinite(F))
     assert np.abs(F - Fo).max() <= FORCE_RTOL_FP32 * np.abs(Fo).max()
+
+
+def test_fp32_acceleration_field_is_kept_in_float():
+    """The FP32-split context keeps the acceleration in FP32: ACC set from
+    doubles reads back as the float-rounded values, through host and device
+    buffers alike, and the next step starts from them."""
+    import torch
+    w = _contact_disks()
+    S = _sim(w, B.PD_FP32_SPLIT, store=False)
+    rng = np.random.default_rng(7)
+    a = rng.normal(scale=3.0e3, size=(S.N, 2))
+    S.set("ACC", a)
+    af = a.astype(np.float32).astype(np.float64)
+    assert np.array_equal(S.get("ACC"), af)
+    dev = torch.empty((S.N, 2), dtype=torch.float64, device="cuda:0")
+    S.get_device("ACC", dev)
+    torch.cuda.synchronize()
+    assert np.array_equal(dev.cpu().numpy(), af)
+    S.set("ACC", a[::-1].copy())
+    assert np.array_equal(S.get("ACC"), a[::-1].astype(np.float32).astype(np.float64))
