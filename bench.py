@@ -46,10 +46,11 @@ N_SM = 152
 # algorithmic bytes of the FP32-split force phase, bonds from the lattice stencil (every workload
 # here: horizon 3 h): the lane sums read the float-float position pq (16 B), the stencil record
 # (16 B), grain, broken-bond word and contact-list length (12 B) and write the force total (8 B);
-# the epilogue reads the force total (8 B), FP64 v and a (32 B), grain (4 B) and the hash-grid cell
-# of the wall test (8 B) and writes v and a (32 B).  136 B per node and no per-bond stream (nodes
-# whose lattice row has a gap read CSR columns instead, 4 B per bond, not counted).
-BYTES_PER_NODE_FP32 = 136
+# the epilogue reads the force total (8 B), the FP64 v (16 B), the FP32 a (8 B), grain (4 B) and
+# the hash-grid cell of the wall test (8 B) and writes v and a (24 B).  120 B per node and no
+# per-bond stream (nodes whose lattice row has a gap read CSR columns instead, 4 B per bond, not
+# counted).
+BYTES_PER_NODE_FP32 = 120
 BYTES_PER_BOND_FP32 = 0
 B_STATUS_REBUILDS = 5    # status slot counting the contact candidate-list rebuilds
 
@@ -355,10 +356,10 @@ def _timed_steps(sim, stream, flush, steps, warmup, torch):
 # (500-grain compaction, 64-aggregate ensemble, 2000-grain surrogate settling)
 
 # algorithmic bytes of one whole FP32-split time step per node (displacement
-# update 112 B: X + shift, u, v, a and the rebuild reference read, u and pq
-# written; force phase 136 B); the candidate-list rebuild runs only in some
-# steps and is not counted
-BYTES_PER_NODE_STEP_FP32 = 248
+# update 104 B: X + shift, u, v, the FP32 a and the rebuild reference read, u
+# and pq written; force phase 120 B); the candidate-list rebuild runs only in
+# some steps and is not counted
+BYTES_PER_NODE_STEP_FP32 = 224
 
 
 # DRAM bytes (read + write) per launch of the force-phase kernels, per workload,
@@ -372,12 +373,12 @@ BYTES_PER_NODE_STEP_FP32 = 248
 # hold while the kernel sources hash to TRAFFIC_DIGEST; otherwise, or for a
 # kernel not captured, traffic is null.
 TRAFFIC = {
-    "ensemble64": {"k_sums<1, 1>": 356492288, "k_epilogue<1>": 525755392,
-                   "k_sums<0, 1>": 2233876992, "k_epilogue<0>": 584006912},
-    "compaction500": {"k_sums<1, 1>": 23607808, "k_epilogue<1>": 27246336,
-                      "k_sums<0, 1>": 170567424, "k_epilogue<0>": 31435520},
+    "ensemble64": {"k_sums<1, 1>": 356915712, "k_epilogue<1>": 421788416,
+                   "k_sums<0, 1>": 2234222592, "k_epilogue<0>": 584603648},
+    "compaction500": {"k_sums<1, 1>": 23609088, "k_epilogue<1>": 23026944,
+                      "k_sums<0, 1>": 170643712, "k_epilogue<0>": 31436800},
 }
-TRAFFIC_DIGEST = "b99711edcaea1cc0470b2c7bdc3f27d74b69656e"
+TRAFFIC_DIGEST = "dabc524e236216bf338a80bc06c3e6bf8b3e9912"
 TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu", "pd_common.cu", "pd_internal.h")
 
 
@@ -465,7 +466,7 @@ FP64_INST = {
     "ensemble64": {"k_sums<0, 1>": 32548167, "k_epilogue<0>": 1674556},
     "compaction500": {"k_sums<0, 1>": 2492904, "k_epilogue<0>": 130368},
 }
-FP64_INST_DIGEST = "b99711edcaea1cc0470b2c7bdc3f27d74b69656e"
+FP64_INST_DIGEST = "dabc524e236216bf338a80bc06c3e6bf8b3e9912"
 
 
 def _roof_fp64(sim, f_ms, path, workload, clk, hbm):
