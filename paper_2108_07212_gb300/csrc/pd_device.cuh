@@ -1113,23 +1113,33 @@ __device__ __forceinline__ void node_epilogue64(const DevPtrs &d, const KParams 
 struct BondGeom32 {
     float dx, dy, L, num, den, xi;
 };
+// (pow2: n is a power of two, so n h^2 is exact in float-float without a
+// product residual; callers that know n at compile time pass it as a constant)
 __device__ __forceinline__ int bond_classify32(float4 qj, float2 phi, float2 pli, float nn, float sqn, float4 gq,
-                                               float s0, float s0_lo, float s0_hi, BondGeom32 &g) {
+                                               float s0_lo, float s0_hi, BondGeom32 &g, bool pow2 = false) {
     const float dxh = __fsub_rn(qj.x, phi.x), dxl = qj.z - pli.x;
     const float dyh = __fsub_rn(qj.y, phi.y), dyl = qj.w - pli.y;
     float L2h, L2l;
     len2_ff(dxh, dxl, dyh, dyl, L2h, L2l);
-    float q, eq;
-    two_prod(nn, gq.y, q, eq);                           // |xi|^2 = n h^2
-    g.num = ff_diff(L2h, L2l, q, eq + nn * gq.z);
+    float q, eq;                                         // |xi|^2 = n h^2 as a float-float pair
+    if (pow2) {
+        q = nn * gq.y;
+        eq = nn * gq.z;
+    } else {
+        two_prod(nn, gq.y, q, eq);
+        eq = fmaf(nn, gq.z, eq);
+    }
+    g.num = ff_diff(L2h, L2l, q, eq);
     g.xi = gq.x * sqn;
     g.L = sqrt_approx(L2h);
     g.den = g.xi * (g.L + g.xi);
     g.dx = dxh + dxl;
     g.dy = dyh + dyl;
+    // intact and clear of the guard band (the common case): one comparison; a
+    // NaN stretch counts as intact, as in the band tests
     const float an = fabsf(g.num);
-    if (an > s0_lo * g.den && an < s0_hi * g.den) return 2;
-    return an > s0 * g.den ? 1 : 0;
+    if (!(an > s0_lo * g.den)) return 0;
+    return an < s0_hi * g.den ? 2 : 1;
 }
 
 // Adds the bond force c_w w V^2 s (d / L) of an intact bond (w = 1 - |xi| / eps
@@ -1245,7 +1255,8 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
                 const int dj = stn_dj(o), di = stn_di(o);
                 const int n = di * di + dj * dj;
                 BondGeom32 bg;
-                const int r = bond_classify32(qb[m], phi, pli, (float)n, stn_sqrt_n(n), gq, s0, s0_lo, s0_hi, bg);
+                const int r = bond_classify32(qb[m], phi, pli, (float)n, stn_sqrt_n(n), gq, s0_lo, s0_hi, bg,
+                                              (n & (n - 1)) == 0);
                 if (r == 0) bond_add32(bg, cw, eps, VV, k.micro, Fbx, Fby);
                 else if (r == 2) pending = true;
                 else atomicOr(bw, 1u << __popc(mask & ((1u << o) - 1u)));
@@ -1274,7 +1285,7 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
             if (cb[m] == 0xFFFFFFFFu || ((wb[m] >> (kk & 31)) & 1u)) continue;
             const float nn = (float)(cb[m] >> kColBits);         // lattice offset di^2 + dj^2
             BondGeom32 bg;
-            const int r = bond_classify32(qb[m], phi, pli, nn, sqrt_approx(nn), gq, s0, s0_lo, s0_hi, bg);
+            const int r = bond_classify32(qb[m], phi, pli, nn, sqrt_approx(nn), gq, s0_lo, s0_hi, bg);
             if (r == 0) bond_add32(bg, cw, eps, VV, k.micro, Fbx, Fby);
             else if (r == 2) pending = true;
             else atomicOr(&bw[kk >> 5], 1u << (kk & 31));
@@ -1293,7 +1304,7 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
             // the same classification as the loop (stencil: sqrt(n) from the table)
             const float sqn = stencil ? stn_sqrt_n((int)nn) : sqrt_approx(nn);
             BondGeom32 bg;
-            if (bond_classify32(qj, phi, pli, nn, sqn, gq, s0, s0_lo, s0_hi, bg) != 2) continue;
+            if (bond_classify32(qj, phi, pli, nn, sqn, gq, s0_lo, s0_hi, bg) != 2) continue;
             const double2 pi = position64<PERSIST>(d, ii), pj = position64<PERSIST>(d, j);
             const double ddx = __dsub_rn(pj.x, pi.x), ddy = __dsub_rn(pj.y, pi.y);
             const double L64 = __dsqrt_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)));
