@@ -373,12 +373,12 @@ BYTES_PER_NODE_STEP_FP32 = 224
 # hold while the kernel sources hash to TRAFFIC_DIGEST; otherwise, or for a
 # kernel not captured, traffic is null.
 TRAFFIC = {
-    "ensemble64": {"k_sums<1, 1>": 356915712, "k_epilogue<1>": 421788416,
-                   "k_sums<0, 1>": 2234222592, "k_epilogue<0>": 584603648},
-    "compaction500": {"k_sums<1, 1>": 23609088, "k_epilogue<1>": 23026944,
-                      "k_sums<0, 1>": 170643712, "k_epilogue<0>": 31436800},
+    "ensemble64": {"k_sums<1, 1>": 356955392, "k_epilogue<1>": 421787648,
+                   "k_sums<0, 1>": 2233396736, "k_epilogue<0>": 584454400},
+    "compaction500": {"k_sums<1, 1>": 23607552, "k_epilogue<1>": 23025408,
+                      "k_sums<0, 1>": 170624512, "k_epilogue<0>": 31443968},
 }
-TRAFFIC_DIGEST = "dabc524e236216bf338a80bc06c3e6bf8b3e9912"
+TRAFFIC_DIGEST = "2de5c8921e47f61d35a4d9998c408acd0fcf327d"
 TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu", "pd_common.cu", "pd_internal.h")
 
 
@@ -466,7 +466,7 @@ FP64_INST = {
     "ensemble64": {"k_sums<0, 1>": 32548167, "k_epilogue<0>": 1674556},
     "compaction500": {"k_sums<0, 1>": 2492904, "k_epilogue<0>": 130368},
 }
-FP64_INST_DIGEST = "dabc524e236216bf338a80bc06c3e6bf8b3e9912"
+FP64_INST_DIGEST = "2de5c8921e47f61d35a4d9998c408acd0fcf327d"
 
 
 def _roof_fp64(sim, f_ms, path, workload, clk, hbm):
