@@ -1,6 +1,6 @@
-// pd_mlp_tile.cuh -- the surrogate network's layout, its activation and the
-// staging of its weights for the tensor cores, shared by the network kernels
-// (pd_mlp.cu) and the fused surrogate chain (pd_surrogate.cu).
+// pd_mlp_tile.cuh -- the surrogate network's layout, its activations and the
+// staging of its weights for the tensor cores (the training and inference
+// kernels of pd_mlp.cu).
 //
 // y = W3 gelu(W2 gelu(W1 x + b1) + b2) + b3, 32 -> 128 -> 128 -> 32; BF16
 // weights and activations as MMA operands (tcgen05.mma kind::f16), FP32
