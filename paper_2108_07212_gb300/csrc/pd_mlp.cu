@@ -238,16 +238,34 @@ __global__ void __launch_bounds__(kInferThreads) k_mlp_infer(const MlpRef *__res
     if (warp == 0) tc::tmem_alloc(&tmem_base, 128);
     if (tid == 0) tc::mbar_init(&mbar, 1);
     static_assert(IN == 8 * kInferGroups, "one 8-column piece of the input row per warpgroup");
+    float *sX = reinterpret_cast<float *>(sm + 88 * 1024);   // input rows in FP32, 128 x 32 (16 KB)
     {
-        // input: columns 8 wg .. 8 wg + 7 of the row (one 16-byte core-matrix row)
+        // every load first: the row's input columns 8 wg .. 8 wg + 7 and the
+        // thread's pieces of the three weight matrices; then the stores
+        WeightStage<IN, HID, kInferThreads> w1;
+        WeightStage<HID, HID, kInferThreads> w2;
+        WeightStage<HID, OUT, kInferThreads> w3;
+        float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+        if (row < B) {
+            const float4 *src = reinterpret_cast<const float4 *>(X + (size_t)row * IN + 8 * wg);
+            x0 = src[0];
+            x1 = src[1];
+        }
+        w1.load(static_cast<const __nv_bfloat16 *>(r.W1), tid);
+        w2.load(static_cast<const __nv_bfloat16 *>(r.W2), tid);
+        w3.load(static_cast<const __nv_bfloat16 *>(r.W3), tid);
+        const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
         __align__(16) __nv_bfloat16 xb[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) xb[q] = __float2bfloat16(row < B ? X[(size_t)row * IN + 8 * wg + q] : 0.f);
+        for (int q = 0; q < 8; ++q) {
+            xb[q] = __float2bfloat16(x[q]);
+            sX[lrow * IN + 8 * wg + q] = x[q];
+        }
         *reinterpret_cast<uint4 *>(sA + tc::kmajor_off(lrow, 8 * wg, TILE)) = *reinterpret_cast<const uint4 *>(xb);
+        w1.store(sW1, tid);
+        w2.store(sW2, tid);
+        w3.store(sW3, tid);
     }
-    stage_weights<IN, HID, kInferThreads>(static_cast<const __nv_bfloat16 *>(r.W1), sW1, tid);
-    stage_weights<HID, HID, kInferThreads>(static_cast<const __nv_bfloat16 *>(r.W2), sW2, tid);
-    stage_weights<HID, OUT, kInferThreads>(static_cast<const __nv_bfloat16 *>(r.W3), sW3, tid);
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -297,12 +315,17 @@ __global__ void __launch_bounds__(kInferThreads) k_mlp_infer(const MlpRef *__res
             float acc[16];
             tc::tmem_ld16(tmem + lane_base + (uint32_t)c0, acc);
             if (row < B) {
+                // y = z - lin (.) x with x from the staged rows; 16-byte stores
+                float y[16];
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     const int c = c0 + q;
                     const float z = acc[q] + bias[c];
-                    Y[(size_t)row * OUT + c] = lin ? z - lin[c] * X[(size_t)row * IN + c] : z;
+                    y[q] = lin ? z - lin[c] * sX[lrow * IN + c] : z;
                 }
+                float4 *dst = reinterpret_cast<float4 *>(Y + (size_t)row * OUT + c0);
+#pragma unroll
+                for (int q = 0; q < 16; q += 4) dst[q / 4] = make_float4(y[q], y[q + 1], y[q + 2], y[q + 3]);
             }
         }
         tc::fence_before_sync();
@@ -619,6 +642,9 @@ cudaError_t pd::launch_mlp_grouped(const MlpRef *refs, const int4 *work, int n_w
                                    int *err, cudaStream_t s) {
     if (n_work == 0) return cudaSuccess;
     static_assert(sizeof(MlpRef) == 40, "MlpRef layout");
+    static_assert(88 * 1024 + 128 * PD_MLP_IN * 4 <= kFwdSmem, "inference tile and its input rows fit");
+    // rows of 32 floats: 16-byte aligned when the arrays are
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) return cudaErrorMisalignedAddress;
     pd::mlp::k_mlp_infer<<<n_work, pd::mlp::kInferThreads, kFwdSmem, s>>>(refs, work, x, y, err);
     return cudaGetLastError();
 }

@@ -39,23 +39,29 @@ __device__ __forceinline__ float erf_as(float x) {
 
 __device__ __forceinline__ float gelu_fast(float z) { return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f)); }
 
-// The 16-byte pieces (8 BF16) of a [ROWS][K] weight matrix into the K-major
-// shared layout over NT threads: every load of a thread before its stores.
+// The 16-byte pieces (8 BF16) of a [ROWS][K] weight matrix, staged into the
+// K-major shared layout over NT threads in two halves, so that the loads of
+// several matrices can all be in flight before any store: load() fills the
+// thread's registers, store() writes them.
 template <int K, int ROWS, int NT>
-__device__ __forceinline__ void stage_weights(const __nv_bfloat16 *__restrict__ W, uint8_t *dst, int tid) {
-    constexpr int count = ROWS * K / 8, per = (count + NT - 1) / NT;
+struct WeightStage {
+    static constexpr int count = ROWS * K / 8, per = (count + NT - 1) / NT;
     uint4 v[per];
+    __device__ __forceinline__ void load(const __nv_bfloat16 *__restrict__ W, int tid) {
 #pragma unroll
-    for (int q = 0; q < per; ++q) {
-        const int e = tid + q * NT, rr = e / (K / 8), k8 = (e % (K / 8)) * 8;
-        if (e < count) v[q] = *reinterpret_cast<const uint4 *>(W + (size_t)rr * K + k8);
+        for (int q = 0; q < per; ++q) {
+            const int e = tid + q * NT, rr = e / (K / 8), k8 = (e % (K / 8)) * 8;
+            if (e < count) v[q] = *reinterpret_cast<const uint4 *>(W + (size_t)rr * K + k8);
+        }
     }
+    __device__ __forceinline__ void store(uint8_t *dst, int tid) const {
 #pragma unroll
-    for (int q = 0; q < per; ++q) {
-        const int e = tid + q * NT, rr = e / (K / 8), k8 = (e % (K / 8)) * 8;
-        if (e < count) *reinterpret_cast<uint4 *>(dst + tc::kmajor_off(rr, k8, ROWS)) = v[q];
+        for (int q = 0; q < per; ++q) {
+            const int e = tid + q * NT, rr = e / (K / 8), k8 = (e % (K / 8)) * 8;
+            if (e < count) *reinterpret_cast<uint4 *>(dst + tc::kmajor_off(rr, k8, ROWS)) = v[q];
+        }
     }
-}
+};
 
 }  // namespace mlp
 }  // namespace pd

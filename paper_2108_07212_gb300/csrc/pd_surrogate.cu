@@ -334,8 +334,24 @@ __global__ void __launch_bounds__(128) k_sur_project_tc(DevPtrs d, KParams k) {
     const int rp = tmpl_rows_pad(d, t);
     if (warp == 0) tc::tmem_alloc(&tmem_base, 32);
     if (tid == 0) tc::mbar_init(&mbar, 1);
-    // A: local deformation rows of the tile's grains (zero outside)
+    // B (the basis chunk, mode-major, 16-byte pieces) and A (local deformation
+    // rows of the tile's grains, zero outside) staged with their loads in flight
+    // together: the B pieces and the first half of the row, then the second half
     {
+        const uint16_t *bh = d.bmm_hi + (size_t)d.tmpl_rows[t] * M;
+        const uint16_t *bl = d.bmm_lo + (size_t)d.tmpl_rows[t] * M;
+        constexpr int nb = NM * (KC / 8) / 128;
+        static_assert(NM * (KC / 8) % 128 == 0, "basis pieces must divide over the 128 threads");
+        uint4 vh[nb], vl[nb];
+#pragma unroll
+        for (int q = 0; q < nb; ++q) {
+            const int e = tid + q * 128, m = e / (KC / 8), k8 = (e % (KC / 8)) * 8;
+            vh[q] = vl[q] = make_uint4(0, 0, 0, 0);
+            if (m < M) {
+                vh[q] = *reinterpret_cast<const uint4 *>(bh + (size_t)m * rp + r0 + k8);
+                vl[q] = *reinterpret_cast<const uint4 *>(bl + (size_t)m * rp + r0 + k8);
+            }
+        }
         const int s = s0 + tid;
         int g = -1;
         if (s < Gt) {
@@ -343,9 +359,7 @@ __global__ void __launch_bounds__(128) k_sur_project_tc(DevPtrs d, KParams k) {
             if (!d.sur_active[g]) g = -1;
         }
         const float *w = g >= 0 ? reinterpret_cast<const float *>(d.sur_w) + 2 * (size_t)d.g_start[g] : nullptr;
-        // batches of kLoadBatch pairs: all loads of a batch are in flight before
-        // its stores (one L2 latency per batch, not per pair)
-        constexpr int kLoadBatch = 16;
+        constexpr int kLoadBatch = 16;                   // pairs per batch: four batches per chunk
         static_assert(KC % (2 * kLoadBatch) == 0, "chunk must hold whole batches");
 #pragma unroll 1
         for (int kb = 0; kb < KC; kb += 2 * kLoadBatch) {
@@ -362,23 +376,6 @@ __global__ void __launch_bounds__(128) k_sur_project_tc(DevPtrs d, KParams k) {
                 const uint32_t hi = split_pack(v[q].x, v[q].y, lo);
                 *reinterpret_cast<uint32_t *>(sAh + tc::kmajor_off(tid, kk, MR)) = hi;
                 *reinterpret_cast<uint32_t *>(sAl + tc::kmajor_off(tid, kk, MR)) = lo;
-            }
-        }
-    }
-    // B: the basis, mode-major, padded rows (16-byte pieces of 8 values)
-    {
-        const uint16_t *bh = d.bmm_hi + (size_t)d.tmpl_rows[t] * M;
-        const uint16_t *bl = d.bmm_lo + (size_t)d.tmpl_rows[t] * M;
-        constexpr int nb = NM * (KC / 8) / 128;
-        static_assert(NM * (KC / 8) % 128 == 0, "basis pieces must divide over the 128 threads");
-        uint4 vh[nb], vl[nb];
-#pragma unroll
-        for (int q = 0; q < nb; ++q) {
-            const int e = tid + q * 128, m = e / (KC / 8), k8 = (e % (KC / 8)) * 8;
-            vh[q] = vl[q] = make_uint4(0, 0, 0, 0);
-            if (m < M) {
-                vh[q] = *reinterpret_cast<const uint4 *>(bh + (size_t)m * rp + r0 + k8);
-                vl[q] = *reinterpret_cast<const uint4 *>(bl + (size_t)m * rp + r0 + k8);
             }
         }
 #pragma unroll
@@ -470,34 +467,24 @@ __global__ void __launch_bounds__(kExpThreads) k_sur_expand_tc(DevPtrs d, KParam
     }
     // first node coordinate of the row's grain in the per-node arrays (-1: none)
     const int fbase = g >= 0 ? 2 * d.g_start[g] : -1;
-    // A: network outputs (modal bond forces) of the tile's grains, modes
-    // [KM/4 wg, KM/4 (wg + 1)) per warpgroup
+    // A (network outputs of the tile's grains, modes [KM/4 wg, KM/4 (wg + 1)) per
+    // warpgroup) and B (basis rows, node-major: each row the modes of one node
+    // coordinate): every load before the first store
     {
         constexpr int kPer = KM / kExpGroups;
         static_assert(kPer % 2 == 0 && KM % kExpGroups == 0, "whole pairs per warpgroup");
+        constexpr int nb = NR * (KM / 8) / kExpThreads;
+        static_assert(NR * (KM / 8) % kExpThreads == 0, "basis pieces must divide over the threads");
         const float *y = g >= 0 ? d.sur_y + (size_t)(slot0 + s) * M : nullptr;
-        float yv[kPer];                    // every load before the first store
+        const uint16_t *bh = d.bnm_hi + ((size_t)d.tmpl_rows[t] + r0) * M;
+        const uint16_t *bl = d.bnm_lo + ((size_t)d.tmpl_rows[t] + r0) * M;
+        float yv[kPer];
+        uint4 vh[nb], vl[nb];
 #pragma unroll
         for (int q = 0; q < kPer; ++q) {
             const int kk = kPer * wg + q;
             yv[q] = (y && kk < M) ? y[kk] : 0.f;
         }
-#pragma unroll
-        for (int q = 0; q < kPer; q += 2) {
-            const int kk = kPer * wg + q;
-            uint32_t lo;
-            const uint32_t hi = split_pack(yv[q], yv[q + 1], lo);
-            *reinterpret_cast<uint32_t *>(sAh + tc::kmajor_off(lrow, kk, MR)) = hi;
-            *reinterpret_cast<uint32_t *>(sAl + tc::kmajor_off(lrow, kk, MR)) = lo;
-        }
-    }
-    // B: basis rows, node-major (each row: the modes of one node coordinate)
-    {
-        const uint16_t *bh = d.bnm_hi + ((size_t)d.tmpl_rows[t] + r0) * M;
-        const uint16_t *bl = d.bnm_lo + ((size_t)d.tmpl_rows[t] + r0) * M;
-        constexpr int nb = NR * (KM / 8) / kExpThreads;
-        static_assert(NR * (KM / 8) % kExpThreads == 0, "basis pieces must divide over the threads");
-        uint4 vh[nb], vl[nb];             // every load before the first store
 #pragma unroll
         for (int q = 0; q < nb; ++q) {
             const int e = tid + q * kExpThreads, r = e / (KM / 8), k8 = (e % (KM / 8)) * 8;
@@ -506,6 +493,14 @@ __global__ void __launch_bounds__(kExpThreads) k_sur_expand_tc(DevPtrs d, KParam
                 vh[q] = *reinterpret_cast<const uint4 *>(bh + (size_t)r * M + k8);
                 vl[q] = *reinterpret_cast<const uint4 *>(bl + (size_t)r * M + k8);
             }
+        }
+#pragma unroll
+        for (int q = 0; q < kPer; q += 2) {
+            const int kk = kPer * wg + q;
+            uint32_t lo;
+            const uint32_t hi = split_pack(yv[q], yv[q + 1], lo);
+            *reinterpret_cast<uint32_t *>(sAh + tc::kmajor_off(lrow, kk, MR)) = hi;
+            *reinterpret_cast<uint32_t *>(sAl + tc::kmajor_off(lrow, kk, MR)) = lo;
         }
 #pragma unroll
         for (int q = 0; q < nb; ++q) {
