@@ -373,13 +373,16 @@ BYTES_PER_NODE_STEP_FP32 = 224
 # hold while the kernel sources hash to TRAFFIC_DIGEST; otherwise, or for a
 # kernel not captured, traffic is null.
 TRAFFIC = {
-    "ensemble64": {"k_sums<1, 1>": 356955392, "k_epilogue<1>": 421787648,
-                   "k_sums<0, 1>": 2233396736, "k_epilogue<0>": 584454400},
-    "compaction500": {"k_sums<1, 1>": 23607552, "k_epilogue<1>": 23025408,
-                      "k_sums<0, 1>": 170624512, "k_epilogue<0>": 31443968},
+    "ensemble64": {"k_persistent<1, 1, 256>": 1356252672, "k_persistent<0, 1, 256>": 3345293312,
+                   "k_sums<1, 1>": 356891136, "k_epilogue<1>": 422153216,
+                   "k_sums<0, 1>": 2234032896, "k_epilogue<0>": 585353216},
+    "compaction500": {"k_persistent<1, 1, 256>": 58068224, "k_persistent<0, 1, 256>": 243394560,
+                      "k_sums<1, 1>": 23608064, "k_epilogue<1>": 23024896,
+                      "k_sums<0, 1>": 170549504, "k_epilogue<0>": 31461632},
 }
-TRAFFIC_DIGEST = "2de5c8921e47f61d35a4d9998c408acd0fcf327d"
-TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu", "pd_common.cu", "pd_internal.h")
+TRAFFIC_DIGEST = "b6a5174d2a706f9631b53f2815d08100682cba80"
+TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu", "pd_persist.cu", "pd_common.cu",
+                   "pd_internal.h")
 
 
 def kernel_digest() -> str:
@@ -449,12 +452,16 @@ def _force_kernel_ms(sim, n=20):
 
 
 def _roof_fp32(sim, f_ms, hbm, label, path=None, workload=None):
-    nbytes = BYTES_PER_NODE_FP32 * sim.N + BYTES_PER_BOND_FP32 * sim.n_bonds
+    """HBM roofline of the FP32-split force group: the force phase (120 B/node)
+    on the kernel-graph paths, the whole step (224 B/node) when the persistent
+    kernel, which runs every phase of the step, is the timed group."""
+    per_node = BYTES_PER_NODE_STEP_FP32 if path and path["mode"] & 1 else BYTES_PER_NODE_FP32
+    nbytes = per_node * sim.N + BYTES_PER_BOND_FP32 * sim.n_bonds
     a = nbytes / (f_ms / 1e3) / 1e9
     traffic = force_phase_traffic(path, True, workload) if path and workload else None
     return {"bound": "hbm", "kernel": _force_kernels(path["mode"], True) if path else "k_force32", "achieved": a,
             "peak": hbm, "unit": "GB/s", "frac": a / hbm,
-            "traffic": traffic, "note": f"{label}: {BYTES_PER_NODE_FP32} B/node + {BYTES_PER_BOND_FP32} B/bond x "
+            "traffic": traffic, "note": f"{label}: {per_node} B/node + {BYTES_PER_BOND_FP32} B/bond x "
                                      f"{sim.N} nodes / {sim.n_bonds} bonds, median event time {f_ms * 1e3:.1f} us (of measured)"}
 
 
@@ -466,7 +473,7 @@ FP64_INST = {
     "ensemble64": {"k_sums<0, 1>": 32548167, "k_epilogue<0>": 1674556},
     "compaction500": {"k_sums<0, 1>": 2492904, "k_epilogue<0>": 130368},
 }
-FP64_INST_DIGEST = "2de5c8921e47f61d35a4d9998c408acd0fcf327d"
+FP64_INST_DIGEST = "b6a5174d2a706f9631b53f2815d08100682cba80"
 
 
 def _roof_fp64(sim, f_ms, path, workload, clk, hbm):

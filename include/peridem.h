@@ -320,7 +320,7 @@ int pd_set_materials(pd_ctx *ctx, int n_mat, const double *props, const int32_t 
 /*
  * Autotuner: time candidate step paths on the current state -- a graph of
  * separate kernels or one persistent cooperative kernel per 16 steps, each with
- * the force phase fused (4 or 8 threads per node) or split (1, 2, 4 or 8),
+ * the force phase fused or split, 1, 2, 4 or 8 threads per node,
  * pd_set_path modes 0-4 and 6 (threads per node fixed when pd_params.lanes is
  * nonzero), 128 or 256 threads per persistent block -- pick the fastest, and
  * re-capture the step graphs.  The
@@ -340,7 +340,11 @@ int pd_autotune(pd_ctx *ctx, double *report);
  * the persistent kernel ignores this bit; profilers that cannot trace kernels
  * of graphs with conditional nodes need it); lanes 1, 2, 4 or 8 threads per
  * node (1 = textbook summation order); block 128 or 256 threads (persistent
- * kernel).  The default path is mode 2 with 4 threads per node.  Re-captures
+ * kernel).  The FP32-split persistent kernel forms the next step's displacement
+ * and positions in its velocity update (device memory of the arena holds two
+ * buffers of each); the next launch starts from them unless the state was
+ * written (pd_set_state), evaluated (pd_eval_forces) or stepped on another path
+ * in between.  The default path is mode 2 with 4 threads per node.  Re-captures
  * the step graphs.  Errors: PD_ESTATE, PD_EINVAL, PD_ECUDA. */
 int pd_set_path(pd_ctx *ctx, int mode, int lanes, int block);
 

@@ -21,17 +21,21 @@ LIB = os.path.join(OUT, "libperidem.so")
 INC = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# (source, extra flags)
+# (source, extra flags[, object name]): pd_persist.cu builds once per precision
+# and thread count per node, so that the persistent kernels compile in parallel
+_FP64_FLAGS = ["-fmad=false"]
+# FP32-split force kernels: divisions and square roots to within 2 ulp (far
+# inside the path's 1e-5 force tolerance) instead of the IEEE sequences
+_FP32_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
 CU_SOURCES = [
-    ("pd_common.cu", ["-fmad=false"]),
-    ("pd_step64.cu", ["-fmad=false"]),
-    # FP32-split force kernels: divisions and square roots to within 2 ulp
-    # (far inside the path's 1e-5 force tolerance) instead of the IEEE sequences
-    ("pd_step32.cu", ["-prec-div=false", "-prec-sqrt=false"]),
+    ("pd_common.cu", _FP64_FLAGS),
+    ("pd_step64.cu", _FP64_FLAGS),
+    ("pd_step32.cu", _FP32_FLAGS),
     ("pd_noalloc.cu", []),
     ("pd_mlp.cu", []),
     ("pd_surrogate.cu", []),
-]
+] + [("pd_persist.cu", (_FP32_FLAGS if fp32 else _FP64_FLAGS) + [f"-DPD_PERSIST_FP32={fp32}", f"-DPD_PERSIST_LANES={lanes}"],
+      f"pd_persist{32 if fp32 else 64}_l{lanes}.o") for fp32 in (1, 0) for lanes in (1, 2, 4, 8)]
 CPP_SOURCES = ["pd_host.cpp", "pd_basis.cpp"]
 
 
@@ -47,7 +51,7 @@ def _cuda_include(nvcc: str) -> str:
 
 
 def _sources():
-    return [os.path.join(CSRC, s) for s, _ in CU_SOURCES] + [os.path.join(CSRC, s) for s in CPP_SOURCES] + [
+    return sorted({os.path.join(CSRC, e[0]) for e in CU_SOURCES}) + [os.path.join(CSRC, s) for s in CPP_SOURCES] + [
         os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))] + [
         os.path.join(INC, "peridem.h"), os.path.abspath(__file__)]
 
@@ -66,8 +70,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     cuinc = _cuda_include(nvcc)
     jobs = []
-    for src, extra in CU_SOURCES:
-        obj = os.path.join(OUT, src + ".o")
+    for entry in CU_SOURCES:
+        src, extra = entry[0], entry[1]
+        obj = os.path.join(OUT, entry[2] if len(entry) > 2 else src + ".o")
         cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC, "-I", CSRC,
                *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         jobs.append((cmd, obj))
@@ -83,7 +88,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError("build failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
         return r.stdout + r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(max(os.cpu_count() or 1, 1), 16, len(jobs))) as ex:
         outs = list(ex.map(run, [c for c, _ in jobs]))
     if verbose:
         for o in outs:

@@ -27,6 +27,8 @@ __global__ void __launch_bounds__(kBlock) k_predict(DevPtrs d, KParams k, int vi
         if (threadIdx.x == 0) {
             *d.t_now = (double)st * k.dt;
             if (advance) *d.step = st;
+            // the persistent kernel's prediction of the next step no longer holds
+            *d.pred_ok = 0;
         }
         wall_cells(d, k, (double)st * k.dt);
     }

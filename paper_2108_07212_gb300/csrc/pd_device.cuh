@@ -8,12 +8,16 @@
 
 namespace pd {
 
-// Loads of state that other blocks write during a persistent launch must not
-// be served from a stale L1 line: PERSIST selects L2-coherent loads (ld.cg).
+// Loads of state that other blocks write in an earlier phase of the same
+// persistent launch.  The persistent kernel's grid barrier orders them: every
+// block fences its writes before it arrives and fences again once it has seen
+// the new generation (the pattern of a cooperative grid synchronisation), so
+// ordinary loads after the barrier, L1 included, see the other blocks' writes
+// (the persistent-vs-graph tests compare FP64 trajectories bit for bit).
+// PERSIST is kept to mark those loads.
 template <bool PERSIST, class T>
 __device__ __forceinline__ T ldm(const T *p) {
-    if constexpr (PERSIST) return __ldcg(p);
-    else return *p;
+    return *p;
 }
 
 // ---------------------------------------------------------------------------
@@ -548,6 +552,58 @@ __device__ __forceinline__ float d2f_hi_bits(double x) {
 // ---------------------------------------------------------------------------
 // per-node phases
 
+// The persistent kernel's current displacement and positions: the buffers of
+// its step's parity, set by thread 0 of every block at the start of the step
+// (one kernel body serves both parities).
+__shared__ double2 *s_cur_u;
+__shared__ float4 *s_cur_pq;
+
+// Current displacement / positions of the kernel: the device pointers' own on
+// the multi-kernel path (the host sets them per launch), the persistent
+// kernel's per-step choice otherwise.
+template <bool PERSIST>
+__device__ __forceinline__ double2 *cur_u(const DevPtrs &d) {
+    if constexpr (PERSIST) return s_cur_u;
+    else return d.u;
+}
+template <bool PERSIST>
+__device__ __forceinline__ float4 *cur_pq(const DevPtrs &d) {
+    if constexpr (PERSIST) return s_cur_pq;
+    else return d.pq;
+}
+
+// Shifted position xs + u of node i as a float-float pair into q_out[i], and
+// the rebuild test: the displacement since the last rebuild from the float-float
+// positions (error ~1e-7 of the displacement, far below the trigger's margin).
+template <bool PERSIST>
+__device__ __forceinline__ bool position32(const DevPtrs &d, const KParams &k, int i, double2 u, float4 *q_out) {
+    const double2 xs = __ldg(&d.xs[i]);
+    const double qx = xs.x + u.x, qy = xs.y + u.y;
+    // float-float split by bit operations (no FP64-pipe conversions)
+    float4 q;
+    dbl_to_ff(qx, q.x, q.z);
+    dbl_to_ff(qy, q.y, q.w);
+    q_out[i] = q;
+    const float4 r = ldm<PERSIST>(&d.sref[i]);
+    const float ex = __fsub_rn(q.x, r.x) + (q.z - r.z), ey = __fsub_rn(q.y, r.y) + (q.w - r.w);
+    return !(ex * ex + ey * ey <= k.dmax2);
+}
+
+// FP32-split displacement update of node i (Algorithm 1): u += dt v + dt^2/2 a
+// with the FP32 acceleration widened exactly, written to u_out, and its shifted
+// position as a float-float pair to q_out; true when the node has moved
+// kSkinTrigger * skin since the last rebuild.  The persistent kernel's velocity
+// update calls it for the next step with the same operands that the update
+// phase would load, so both give the same bits.
+template <bool PERSIST>
+__device__ __forceinline__ bool advance_node32(const DevPtrs &d, const KParams &k, int i, double2 u, double2 v,
+                                               float ax, float ay, double2 *u_out, float4 *q_out) {
+    u.x = fma(k.dt, v.x, fma(k.half_dt2, f2d_bits(ax), u.x));
+    u.y = fma(k.dt, v.y, fma(k.half_dt2, f2d_bits(ay), u.y));
+    u_out[i] = u;
+    return position32<PERSIST>(d, k, i, u, q_out);
+}
+
 // Algorithm 1: u <- u + dt v + dt^2/2 a (when advancing) and the positions.
 // Returns true when the node has moved farther than kSkinTrigger * skin since
 // the last rebuild of the candidate lists (or its position is not finite).
@@ -557,37 +613,27 @@ __device__ __forceinline__ float d2f_hi_bits(double x) {
 //    p is formed where it is needed: walls, near-threshold bonds, readout).
 //    GB300 issues FP64 at 2 lanes per SM cycle, so the node update is written
 //    with as few FP64 operations as the FP64 state allows.
+// With advance, u^(n-1) is read from ub[vin] and u^n written to d.u
+// (= ub[vin ^ 1]); without, only the positions of d.u.
 template <bool PERSIST>
 __device__ __forceinline__ bool predict_node(const DevPtrs &d, const KParams &k, int i, int vin, int advance) {
-    double2 u = ldm<PERSIST>(&d.u[i]);
+    double2 *const uc = cur_u<PERSIST>(d);
+    double2 u = advance ? ldm<PERSIST>(&d.ub[vin][i]) : ldm<PERSIST>(&uc[i]);
     const float dmax2 = k.dmax2;
     if (d.pq) {
         if (advance) {
             const double2 v = ldm<PERSIST>(&d.v[vin][i]);
             const float2 a = ldm<PERSIST>(&d.af[i]);       // FP32 acceleration, widened exactly
-            u.x = fma(k.dt, v.x, fma(k.half_dt2, f2d_bits(a.x), u.x));
-            u.y = fma(k.dt, v.y, fma(k.half_dt2, f2d_bits(a.y), u.y));
-            d.u[i] = u;
+            return advance_node32<PERSIST>(d, k, i, u, v, a.x, a.y, uc, cur_pq<PERSIST>(d));
         }
-        const double2 xs = __ldg(&d.xs[i]);
-        const double qx = xs.x + u.x, qy = xs.y + u.y;
-        // float-float split by bit operations (no FP64-pipe conversions)
-        float4 q;
-        dbl_to_ff(qx, q.x, q.z);
-        dbl_to_ff(qy, q.y, q.w);
-        d.pq[i] = q;
-        // displacement since the last rebuild from the float-float positions
-        // (error ~1e-7 of the displacement, far below the trigger's margin)
-        const float4 r = ldm<PERSIST>(&d.sref[i]);
-        const float ex = __fsub_rn(q.x, r.x) + (q.z - r.z), ey = __fsub_rn(q.y, r.y) + (q.w - r.w);
-        return !(ex * ex + ey * ey <= dmax2);
+        return position32<PERSIST>(d, k, i, u, cur_pq<PERSIST>(d));
     }
     if (advance) {
         // explicit round-to-nearest operations: never contracted into FMAs
         const double2 v = ldm<PERSIST>(&d.v[vin][i]), a = ldm<PERSIST>(&d.a[i]);
         u.x = __dadd_rn(__dadd_rn(u.x, __dmul_rn(k.dt, v.x)), __dmul_rn(k.half_dt2, a.x));
         u.y = __dadd_rn(__dadd_rn(u.y, __dmul_rn(k.dt, v.y)), __dmul_rn(k.half_dt2, a.y));
-        d.u[i] = u;
+        uc[i] = u;
     }
     const double2 X = __ldg(&d.X[i]);
     d.p[i] = make_double2(__dadd_rn(X.x, u.x), __dadd_rn(X.y, u.y));
@@ -601,7 +647,7 @@ __device__ __forceinline__ bool predict_node(const DevPtrs &d, const KParams &k,
 // FP64 position X + u of node i (the FP32-split path does not store p).
 template <bool PERSIST>
 __device__ __forceinline__ double2 position64(const DevPtrs &d, int i) {
-    const double2 X = __ldg(&d.X[i]), u = ldm<PERSIST>(&d.u[i]);
+    const double2 X = __ldg(&d.X[i]), u = ldm<PERSIST>(&cur_u<PERSIST>(d)[i]);
     return make_double2(__dadd_rn(X.x, u.x), __dadd_rn(X.y, u.y));
 }
 
@@ -615,7 +661,7 @@ __device__ __forceinline__ void bin_node(const DevPtrs &d, const KParams &k, int
     if (d.pq) {
         // FP32-split: the cell from the shifted float position (error below 1e-3
         // cell; the cells of this path are 0.4 % wider to absorb it)
-        const float4 q = ldm<PERSIST>(&d.pq[i]);
+        const float4 q = ldm<PERSIST>(&cur_pq<PERSIST>(d)[i]);
         cx = cell_coord_f((q.x - A.oxs) + q.z, A.inv_cell_f);
         cy = cell_coord_f((q.y - A.oys) + q.w, A.inv_cell_f);
     } else {
@@ -718,7 +764,7 @@ __device__ __forceinline__ void scatter_node(const DevPtrs &d, const KParams &k,
     d.sorted[pos] = i;
     uint4 rec;
     if (k.fp32) {
-        const float4 q = ldm<PERSIST>(&d.pq[i]);
+        const float4 q = ldm<PERSIST>(&cur_pq<PERSIST>(d)[i]);
         rec = make_uint4(__float_as_uint(q.x), __float_as_uint(q.y), __float_as_uint(q.z), __float_as_uint(q.w));
     } else {
         const double2 p = ldm<PERSIST>(&d.p[i]);
@@ -753,7 +799,7 @@ __device__ __forceinline__ void build_list_node(const DevPtrs &d, const KParams 
     }
     float4 qi = make_float4(0.f, 0.f, 0.f, 0.f);
     double2 pi = make_double2(0.0, 0.0);
-    if (d.pq) qi = ldm<PERSIST>(&d.pq[i]);
+    if (d.pq) qi = ldm<PERSIST>(&cur_pq<PERSIST>(d)[i]);
     else pi = ldm<PERSIST>(&d.p[i]);
     int lst[kMaxList];
     int n = 0, over = 0;
@@ -803,7 +849,7 @@ __device__ __forceinline__ void build_list_node(const DevPtrs &d, const KParams 
     if (d.pq) {
         d.sref[i] = qi;
     } else {
-        const double2 u = ldm<PERSIST>(&d.u[i]);
+        const double2 u = ldm<PERSIST>(&cur_u<PERSIST>(d)[i]);
         d.sref[i] = make_float4((float)u.x, (float)u.y, 0.f, 0.f);
     }
     if (over) atomicAdd(&d.status[PD_STATUS_OVERFLOW], 1);
@@ -874,10 +920,17 @@ __device__ __forceinline__ void finish_node(const DevPtrs &d, const KParams &k, 
 // formed in FP32 and added to the FP64 velocity: two FP64 additions per node
 // on GB300's narrow FP64 pipe.  (ao: the previous acceleration, loaded by the
 // caller with the node's other independent loads.)
+//
+// The persistent kernel (PERSIST) also takes the next step's displacement
+// update here, from the velocity and acceleration just formed and the node's
+// current displacement ui: u and pq of the next step go to ub[vin] / pqb[vin]
+// (free: this step reads ub[vin ^ 1] / pqb[vin ^ 1]), and a node past the
+// rebuild trigger raises the next step's flag.  The next step then skips its
+// update phase, which would have read u, v and a back from memory.
 template <bool PERSIST>
 __device__ __forceinline__ void finish_node32_total(const DevPtrs &d, const KParams &k, int i, int vin, int update_v,
                                                     double2 vi, float2 ao, float fx, float fy, bool walls,
-                                                    double Fwx, double Fwy, float inv_m) {
+                                                    double Fwx, double Fwy, float inv_m, double2 ui = {}) {
     float ax, ay;
     if (walls) {
         ax = fmaf(__double2float_rn(f2d_bits(fx) + Fwx), inv_m, k.gxf);
@@ -888,7 +941,12 @@ __device__ __forceinline__ void finish_node32_total(const DevPtrs &d, const KPar
     }
     if (update_v) {
         const float hdt = 0.5f * k.dtf;
-        d.v[vin ^ 1][i] = make_double2(vi.x + f2d_bits(hdt * (ao.x + ax)), vi.y + f2d_bits(hdt * (ao.y + ay)));
+        const double2 vn = make_double2(vi.x + f2d_bits(hdt * (ao.x + ax)), vi.y + f2d_bits(hdt * (ao.y + ay)));
+        d.v[vin ^ 1][i] = vn;
+        if constexpr (PERSIST) {
+            if (advance_node32<PERSIST>(d, k, i, ui, vn, ax, ay, d.ub[vin], d.pqb[vin]))
+                *(volatile int *)d.rebuild_next = 1;
+        }
     }
     d.af[i] = make_float2(ax, ay);
     // finiteness from the exponent bits (no FP64 compare)
@@ -1184,7 +1242,7 @@ template <bool PERSIST, int LANES>
 __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k, int i, int lane, bool active,
                                              int vin, Sums32 &out) {
     const int ii = active ? i : 0;
-    const float4 qi = ldm<PERSIST>(&d.pq[ii]);
+    const float4 qi = ldm<PERSIST>(&cur_pq<PERSIST>(d)[ii]);
     const float2 phi = make_float2(qi.x, qi.y), pli = make_float2(qi.z, qi.w);
     const int gi = __ldg(&d.grain[ii]);
     const int ag = __ldg(&d.g_agg[gi]);
@@ -1246,7 +1304,7 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
                 const int D = dj == -2 ? Dm2 : (dj == -1 ? Dm1 : (dj == 0 ? 0 : (dj == 1 ? Dp1 : Dp2)));
                 const int kk = __popc(mask & ((1u << o) - 1u));
                 live[m] = (m0 + m) < kPerLane && o < 24 && ((mask >> o) & 1u) && !((w0 >> kk) & 1u);
-                qb[m] = ldm<PERSIST>(&d.pq[live[m] ? ii + di + D : ii]);
+                qb[m] = ldm<PERSIST>(&cur_pq<PERSIST>(d)[live[m] ? ii + di + D : ii]);
             }
 #pragma unroll
             for (int m = 0; m < kBondBatch; ++m) {
@@ -1276,7 +1334,7 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
 #pragma unroll
         for (int m = 0; m < kBondBatch; ++m) {
             const int j = cb[m] == 0xFFFFFFFFu ? ii : (int)(cb[m] & kColMask);
-            qb[m] = ldm<PERSIST>(&d.pq[j]);
+            qb[m] = ldm<PERSIST>(&cur_pq<PERSIST>(d)[j]);
         }
 #pragma unroll
         for (int m = 0; m < kBondBatch; ++m) {
@@ -1299,7 +1357,7 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
             if ((__ldcg(&bw[kk >> 5]) >> (kk & 31)) & 1u) continue;
             const uint32_t c = __ldg(&d.colx[b]);
             const int j = (int)(c & kColMask);
-            const float4 qj = ldm<PERSIST>(&d.pq[j]);
+            const float4 qj = ldm<PERSIST>(&cur_pq<PERSIST>(d)[j]);
             const float nn = (float)(c >> kColBits);
             // the same classification as the loop (stencil: sqrt(n) from the table)
             const float sqn = stencil ? stn_sqrt_n((int)nn) : sqrt_approx(nn);
@@ -1327,7 +1385,7 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
     float Fsx = 0.f, Fsy = 0.f, Fnx = 0.f, Fny = 0.f;
     for (int q = lane; q < nc; q += LANES) {
         const int j = ldm<PERSIST>(&d.nbr[(size_t)q * k.N + ii]);
-        const float4 qj = ldm<PERSIST>(&d.pq[j]);
+        const float4 qj = ldm<PERSIST>(&cur_pq<PERSIST>(d)[j]);
         const float dxh = __fsub_rn(qj.x, phi.x), dxl = qj.z - pli.x;
         const float dyh = __fsub_rn(qj.y, phi.y), dyl = qj.w - pli.y;
         float L2h, L2l;
@@ -1400,6 +1458,8 @@ __device__ __forceinline__ void node_epilogue32(const DevPtrs &d, const KParams 
     const int ag = __ldg(&d.g_agg[gi]);
     const float inv_m = __ldg(&d.g_invmf[gi]);
     const int4 wc = ldm<PERSIST>(&d.wall_cell[ag]);
+    // the displacement for the next step's update (persistent kernel)
+    const double2 ui = PERSIST && update_v ? ldm<PERSIST>(&cur_u<PERSIST>(d)[i]) : double2{};
     Sums32 f = fin;
     if constexpr (!PERSIST) {
         // learned modal surrogate: between judge steps an active grain's bond force
@@ -1434,7 +1494,7 @@ __device__ __forceinline__ void node_epilogue32(const DevPtrs &d, const KParams 
         d.parts[2 * (size_t)k.N + i] = make_double2((double)f.nx, (double)f.ny);
         d.parts[3 * (size_t)k.N + i] = make_double2(Fwx, Fwy);
     }
-    finish_node32_total<PERSIST>(d, k, i, vin, update_v, vi, ao, fx, fy, walls, Fwx, Fwy, inv_m);
+    finish_node32_total<PERSIST>(d, k, i, vin, update_v, vi, ao, fx, fy, walls, Fwx, Fwy, inv_m, ui);
 }
 
 }  // namespace pd

@@ -327,11 +327,13 @@ size_t layout(pd_ctx *c, char *base) {
     size_t off = 0;
     pd::DevPtrs &d = c->d;
     size_t N = (size_t)c->N, nb = c->col.size(), G = (size_t)c->G;
+    const bool fp32 = c->prm.precision == PD_FP32_SPLIT;
     carve(base, off, d.X, N);
-    carve(base, off, d.u, N);
+    carve(base, off, d.ub[0], N);
+    carve(base, off, d.ub[1], fp32 ? N : 0);
+    if (!fp32) d.ub[1] = d.ub[0];
     carve(base, off, d.v[0], N);
     carve(base, off, d.v[1], N);
-    const bool fp32 = c->prm.precision == PD_FP32_SPLIT;
     carve(base, off, d.a, fp32 ? 0 : N);
     carve(base, off, d.af, fp32 ? N : 0);
     if (fp32) d.a = nullptr;
@@ -366,6 +368,8 @@ size_t layout(pd_ctx *c, char *base) {
     carve(base, off, d.sref, N);
     carve(base, off, d.rebuild, 1);
     carve(base, off, d.pred_done, 1);
+    carve(base, off, d.rebuild_next, 1);
+    carve(base, off, d.pred_ok, 1);
     carve(base, off, d.fsum, 6 * N * (c->prm.precision == PD_FP32_SPLIT ? 4 : 8));
     // block sums of the scan: one per scan tile (multi-kernel path) or per
     // block of the persistent kernel (at most 16 blocks per SM)
@@ -382,7 +386,8 @@ size_t layout(pd_ctx *c, char *base) {
     if (c->prm.precision == PD_FP32_SPLIT) {
         carve(base, off, d.lat, N);
         carve(base, off, d.gq, G);
-        carve(base, off, d.pq, N);
+        carve(base, off, d.pqb[0], N);
+        carve(base, off, d.pqb[1], N);
         carve(base, off, d.xs, N);
         carve(base, off, d.colx, nb);
         carve(base, off, d.stn, N);
@@ -390,7 +395,7 @@ size_t layout(pd_ctx *c, char *base) {
     } else {
         d.lat = nullptr;
         d.gq = nullptr;
-        d.pq = nullptr;
+        d.pqb[0] = d.pqb[1] = nullptr;
         d.xs = nullptr;
         d.colx = nullptr;
         d.stn = nullptr;
@@ -451,6 +456,8 @@ size_t layout(pd_ctx *c, char *base) {
         d.sur_fc = nullptr;
         d.sur_rot = d.sur_fb = nullptr;
     }
+    d.u = d.ub[c->vcur];
+    d.pq = d.pqb[c->vcur];
     return off;
 }
 
@@ -465,15 +472,33 @@ int check_ctx(pd_ctx *c, int min_state) {
 // partials summed in a fixed order, every template's network on its batch of
 // grains with f = -Lambda q + net(q) in its output epilogue, and the
 // expansion of f to nodal bond forces (tensor cores).
-cudaError_t record_surrogate(pd_ctx *c, cudaStream_t s) {
+// The host-side current displacement and positions follow the velocity parity.
+void set_current(pd_ctx *c) {
+    c->d.u = c->d.ub[c->vcur];
+    c->d.pq = c->d.pqb[c->vcur];
+}
+
+// Device pointers for the kernels of a step recorded with velocity parity vin:
+// its displacement update writes, and its force phase reads, the displacement
+// and positions of parity vin ^ 1.
+pd::DevPtrs step_ptrs(const pd_ctx *c, int vin) {
+    pd::DevPtrs d = c->d;
+    d.u = d.ub[vin ^ 1];
+    d.pq = d.pqb[vin ^ 1];
+    return d;
+}
+
+cudaError_t record_surrogate(pd_ctx *c, const pd::DevPtrs &d, cudaStream_t s) {
     cudaError_t e;
-    if ((e = pd::launch_sur_frame(c->d, c->kp, 0, s)) != cudaSuccess) return e;
-    if ((e = pd::launch_sur_project_tc(c->d, c->kp, s)) != cudaSuccess) return e;
-    if ((e = pd::launch_sur_reduce(c->d, c->kp, s)) != cudaSuccess) return e;
-    if ((e = pd::launch_mlp_grouped(c->d.mlp_refs, c->d.mlp_work, (int)c->mlp_work.size(), c->d.sur_x, c->d.sur_y,
-                                    c->d.mlp_err, s)) != cudaSuccess)
+    // the kernels after the frame begin while their predecessor finishes
+    // (programmatic dependent launch) and stage their basis or weight operands
+    if ((e = pd::launch_sur_frame(d, c->kp, 0, s)) != cudaSuccess) return e;
+    if ((e = pd::launch_sur_project_tc(d, c->kp, s, true)) != cudaSuccess) return e;
+    if ((e = pd::launch_sur_reduce(d, c->kp, s, true)) != cudaSuccess) return e;
+    if ((e = pd::launch_mlp_grouped(d.mlp_refs, d.mlp_work, (int)c->mlp_work.size(), d.sur_x, d.sur_y, d.mlp_err, s,
+                                    true)) != cudaSuccess)
         return e;
-    return pd::launch_sur_expand_tc(c->d, c->kp, s);
+    return pd::launch_sur_expand_tc(d, c->kp, s, true);
 }
 
 // Record one time step (Algorithm 1) on the capturing stream s: displacement
@@ -483,6 +508,7 @@ cudaError_t record_surrogate(pd_ctx *c, cudaStream_t s) {
 // event records bracket the three kernel groups.
 cudaError_t record_step(pd_ctx *c, int vin, cudaStream_t s, bool timed = false) {
     cudaError_t e;
+    const pd::DevPtrs dv = step_ptrs(c, vin);
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
     if ((e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g)) != cudaSuccess) return e;
@@ -492,7 +518,7 @@ cudaError_t record_step(pd_ctx *c, int vin, cudaStream_t s, bool timed = false) 
     if (use_cond && (e = cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
         return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal)) != cudaSuccess) return e;
-    if ((e = pd::launch_predict(c->d, c->kp, vin, 1, s, cond, use_cond)) != cudaSuccess) return e;
+    if ((e = pd::launch_predict(dv, c->kp, vin, 1, s, cond, use_cond)) != cudaSuccess) return e;
     // surrogate with the split force phase: its chain (frame, projection,
     // networks, expansion) runs on a second stream beside the rebuild and the
     // lane sums, which skip the bond loop of surrogate grains; the epilogue,
@@ -501,14 +527,14 @@ cudaError_t record_step(pd_ctx *c, int vin, cudaStream_t s, bool timed = false) 
     if (fork) {
         if ((e = cudaEventRecord(c->ev_fork, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(c->sur_stream, c->ev_fork, 0)) != cudaSuccess) return e;
-        if ((e = record_surrogate(c, c->sur_stream)) != cudaSuccess) return e;
+        if ((e = record_surrogate(c, dv, c->sur_stream)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(c->ev_join, c->sur_stream)) != cudaSuccess) return e;
     }
     if (timed && (e = cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     if (c->mode & 4) {
         // path modes 4-7: the rebuild kernels run every step and return at once
         // when the flag is clear (no conditional node)
-        if ((e = pd::launch_rebuild(c->d, c->kp, s)) != cudaSuccess) return e;
+        if ((e = pd::launch_rebuild(dv, c->kp, s)) != cudaSuccess) return e;
     } else {
         const cudaGraphNode_t *deps = nullptr;
         size_t nd = 0;
@@ -527,22 +553,22 @@ cudaError_t record_step(pd_ctx *c, int vin, cudaStream_t s, bool timed = false) 
         if ((e = cudaStreamBeginCaptureToGraph(c->body_stream, body, nullptr, nullptr, 0,
                                                cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return e;
-        const cudaError_t eb = pd::launch_rebuild(c->d, c->kp, c->body_stream);
+        const cudaError_t eb = pd::launch_rebuild(dv, c->kp, c->body_stream);
         cudaGraph_t done = nullptr;
         const cudaError_t ee = cudaStreamEndCapture(c->body_stream, &done);
         if (eb != cudaSuccess) return eb;
         if (ee != cudaSuccess) return ee;
     }
-    if (c->kp.sur && !fork && (e = record_surrogate(c, s)) != cudaSuccess) return e;
+    if (c->kp.sur && !fork && (e = record_surrogate(c, dv, s)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     if (fork) {
-        if ((e = pd::launch_force(c->d, c->kp, vin, 1, s, 1)) != cudaSuccess) return e;
+        if ((e = pd::launch_force(dv, c->kp, vin, 1, s, 1)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(s, c->ev_join, 0)) != cudaSuccess) return e;
-        if ((e = pd::launch_force(c->d, c->kp, vin, 1, s, 2)) != cudaSuccess) return e;
-    } else if ((e = pd::launch_force(c->d, c->kp, vin, 1, s)) != cudaSuccess) {
+        if ((e = pd::launch_force(dv, c->kp, vin, 1, s, 2)) != cudaSuccess) return e;
+    } else if ((e = pd::launch_force(dv, c->kp, vin, 1, s)) != cudaSuccess) {
         return e;
     }
-    if (c->kp.sur && (e = pd::launch_sur_judge(c->d, c->kp, s)) != cudaSuccess) return e;
+    if (c->kp.sur && (e = pd::launch_sur_judge(dv, c->kp, s)) != cudaSuccess) return e;
     if (timed && (e = cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal)) != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -1023,6 +1049,8 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     PD_CUDA(cudaMemsetAsync(d.sref, 0, 16 * N, s));
     PD_CUDA(cudaMemsetAsync(d.rebuild, 1, sizeof(int), s));
     PD_CUDA(cudaMemsetAsync(d.pred_done, 0, sizeof(unsigned), s));
+    PD_CUDA(cudaMemsetAsync(d.rebuild_next, 0, sizeof(int), s));
+    PD_CUDA(cudaMemsetAsync(d.pred_ok, 0, sizeof(int), s));
     std::vector<int32_t> gstart32(c->g_start.begin(), c->g_start.end()), tnode, tslot;
     PD_CUDA(cudaMemcpyAsync(d.g_start, gstart32.data(), 4 * (G + 1), cudaMemcpyHostToDevice, s));
     std::vector<float> fc;
@@ -1178,6 +1206,7 @@ int pd_bind_arena(pd_ctx *c, void *arena, size_t bytes) {
     PD_CUDA(cudaMemcpyAsync(d.g_invmf, invmf.data(), 4 * G, cudaMemcpyHostToDevice, s));
     PD_CUDA(cudaStreamSynchronize(s));
     c->vcur = 0;
+    set_current(c);
     c->steps_done = 0;
     c->state = 3;
     // initial acceleration a^0 from the forces of the initial state
@@ -1202,7 +1231,7 @@ int pd_eval_forces(pd_ctx *c) {
     PD_CUDA(pd::launch_predict(c->d, c->kp, c->vcur, 0, s, 0, 0));
     PD_CUDA(cudaMemsetAsync(c->d.rebuild, 1, sizeof(int), s));     // fresh candidate lists
     PD_CUDA(pd::launch_rebuild(c->d, c->kp, s));
-    if (c->kp.sur) PD_CUDA(record_surrogate(c, s));
+    if (c->kp.sur) PD_CUDA(record_surrogate(c, c->d, s));
     PD_CUDA(pd::launch_force(c->d, c->kp, c->vcur, 0, s));
     return PD_OK;
 }
@@ -1215,6 +1244,7 @@ int pd_step(pd_ctx *c, int n_steps) {
         for (int k = 0; k < n; ++k) {
             PD_CUDA(cudaGraphLaunch(c->timed[c->vcur], c->stream));
             c->vcur ^= 1;
+            set_current(c);
         }
         c->steps_done += n_steps;
         return PD_OK;
@@ -1227,6 +1257,7 @@ int pd_step(pd_ctx *c, int n_steps) {
     while (n > 0) {
         PD_CUDA(cudaGraphLaunch(c->single[c->vcur], c->stream));
         c->vcur ^= 1;
+        set_current(c);
         --n;
     }
     c->steps_done += n_steps;
@@ -1323,6 +1354,8 @@ int pd_set_state(pd_ctx *c, int field, const void *src, size_t bytes, int src_on
     cudaMemcpyKind kind = src_on_device == PD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const pd::DevPtrs &d = c->d;
     cudaStream_t s = c->stream;
+    // the persistent kernel's prediction of the next step was made from the old state
+    PD_CUDA(cudaMemsetAsync(d.pred_ok, 0, sizeof(int), s));
     switch (field) {
         case PD_FIELD_DISP: PD_CUDA(cudaMemcpyAsync(d.u, src, fb, kind, s)); break;
         case PD_FIELD_VEL: PD_CUDA(cudaMemcpyAsync(d.v[c->vcur], src, fb, kind, s)); break;
@@ -1434,6 +1467,8 @@ int pd_clear_status(pd_ctx *c) {
     if (d.mlp_err) PD_CUDA(cudaMemsetAsync(d.mlp_err, 0, sizeof(int), s));
     PD_CUDA(cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), s));
     PD_CUDA(cudaMemsetAsync(d.pred_done, 0, sizeof(unsigned), s));
+    PD_CUDA(cudaMemsetAsync(d.pred_ok, 0, sizeof(int), s));
+    PD_CUDA(cudaMemsetAsync(d.rebuild_next, 0, sizeof(int), s));
     // a step that gave up inside a rebuild leaves bucket counts behind; they are
     // zero between rebuilds, and the next step rebuilds the candidate lists
     PD_CUDA(cudaMemsetAsync(d.count, 0, sizeof(int) * c->T, s));
@@ -1522,6 +1557,7 @@ int pd_autotune(pd_ctx *c, double *report) {
         PD_CUDA(cudaMemcpyAsync(d.step, &step0, 8, cudaMemcpyHostToDevice, s));
         PD_CUDA(cudaMemcpyAsync(d.status, st0, sizeof(st0), cudaMemcpyHostToDevice, s));
         PD_CUDA(cudaMemsetAsync(d.bar, 0, 2 * sizeof(unsigned), s));
+        PD_CUDA(cudaMemsetAsync(d.pred_ok, 0, sizeof(int), s));
         PD_CUDA(cudaStreamSynchronize(s));
         return PD_OK;
     };
@@ -1529,13 +1565,12 @@ int pd_autotune(pd_ctx *c, double *report) {
         int mode, lanes, block;
     };
     std::vector<Cand> cands;
-    // fused force phase: 4 or 8 threads per node; split: 1, 2, 4 or 8
+    // 1, 2, 4 or 8 threads per node for every mode
     // modes 4 and 6: the kernel graph with the rebuild kernels launched every
     // step (returning at once without the flag) instead of the conditional node
     for (int m : {0, 1, 2, 3, 4, 6}) {
-        const bool split = ((m >> 1) & 1) != 0;
         for (int lanes : {1, 2, 4, 8}) {
-            if (c->prm.lanes ? lanes != c->prm.lanes : (!split && lanes < 4)) continue;
+            if (c->prm.lanes && lanes != c->prm.lanes) continue;
             cands.push_back({m, lanes, 128});
             if (m & 1) cands.push_back({m, lanes, 256});
         }

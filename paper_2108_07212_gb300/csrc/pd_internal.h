@@ -63,8 +63,15 @@ struct AggParams {
 
 // Device pointers carved out of the caller's arena.
 struct DevPtrs {
-    // node state (N entries of (x, y))
+    // node state (N entries of (x, y)).  u and pq are the current step's
+    // displacement and positions: a launch gets the buffers of its parity (the
+    // host sets them per launch, the persistent kernel per step).  The FP32-split
+    // path keeps two buffers of each, ub / pqb: the step with velocity parity vin
+    // reads u^(n-1) from ub[vin] and holds u^n in ub[vin ^ 1], and its persistent
+    // form writes the next step's u and pq into ub[vin] / pqb[vin] while the
+    // others still read the current ones.  The FP64 path has one (ub[0] = ub[1]).
     double2 *X, *u, *v[2], *a, *p, *F, *parts;
+    double2 *ub[2];
     double *V;
     int *grain;
     // bonds: CSR, reference lengths |xi|, broken bits (wpn words per node)
@@ -88,6 +95,8 @@ struct DevPtrs {
     float4 *sref;       // at the last rebuild: FP32 split pq, FP64 path (float u, 0, 0)
     int *rebuild;       // nonzero: rebuild the lists before the next force phase (cleared by the force phase)
     unsigned *pred_done;  // blocks of the displacement update that have finished (last-block election)
+    int *rebuild_next;  // FP32-split persistent kernel: the next step's rebuild flag, raised in the velocity update
+    int *pred_ok;       // nonzero: ub / pqb of the other parity hold the next step's u and pq (persistent kernel)
     uint4 *srec;        // position of sorted[t] in bucket order: FP32 split pq, FP64 p (16 bytes)
     void *fsum;         // split force phase: per-node lane sums, six components of N floats (FP32) or doubles
     // globals
@@ -103,6 +112,7 @@ struct DevPtrs {
     int2 *lat;          // lattice indices (i, j) of every node in its grain frame
     float4 *gq;         // per grain: (h, h^2 hi, h^2 lo, V = h^2 as float)
     float4 *pq;         // shifted position (p + shift) as a float-float pair: (hi x, hi y, lo x, lo y)
+    float4 *pqb[2];     // its two buffers (see ub)
     double2 *xs;        // X + the aggregate's shift (FP64)
     uint32_t *colx;     // bond columns with the lattice offset n = di^2 + dj^2 in the top 4 bits
     uint4 *stn;         // lattice stencil of every node's bonds (see kStnIrregular), when KParams::stencil
@@ -191,9 +201,12 @@ cudaError_t launch_sur_frame(const DevPtrs &d, const KParams &k, int all_templat
 // templated grain: world-frame bond forces (rotated into the lattice frame and
 // scaled by 1/(E h)) when F is given, else the local deformation sur_w.
 cudaError_t launch_sur_project_cc(const DevPtrs &d, const KParams &k, const double2 *F, float *out, cudaStream_t s);
-cudaError_t launch_sur_project_tc(const DevPtrs &d, const KParams &k, cudaStream_t s);
-cudaError_t launch_sur_reduce(const DevPtrs &d, const KParams &k, cudaStream_t s);
-cudaError_t launch_sur_expand_tc(const DevPtrs &d, const KParams &k, cudaStream_t s);
+// The chain after the frame kernel; with pdl, each is launched with
+// programmatic stream serialisation (it may begin while its predecessor on the
+// stream finishes, staging its basis or weight operands meanwhile).
+cudaError_t launch_sur_project_tc(const DevPtrs &d, const KParams &k, cudaStream_t s, bool pdl = false);
+cudaError_t launch_sur_reduce(const DevPtrs &d, const KParams &k, cudaStream_t s, bool pdl = false);
+cudaError_t launch_sur_expand_tc(const DevPtrs &d, const KParams &k, cudaStream_t s, bool pdl = false);
 cudaError_t launch_sur_judge(const DevPtrs &d, const KParams &k, cudaStream_t s);
 
 // Device pointers of one network's inference parameters (BF16 weights, FP32
@@ -211,8 +224,27 @@ int mlp_forward_stream(pd_mlp *m, const float *x, float *y, int batch, cudaStrea
 int mlp_ref(pd_mlp *m, MlpRef *out);
 // Several networks in one launch: work item (network, first row, end row), rows of x / y.
 cudaError_t launch_mlp_grouped(const MlpRef *refs, const int4 *work, int n_work, const float *x, float *y, int *err,
-                               cudaStream_t s);
+                               cudaStream_t s, bool pdl = false);
 cudaError_t mlp_init_attributes();
+
+// Launch of kernel `kern` on stream s, with programmatic stream serialisation
+// when pdl is set (the kernel then has to call grid_dep_wait() before it reads
+// what the previous kernel of the stream writes).
+template <class... KArgs, class... Args>
+cudaError_t launch_ex(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                      Args... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 // Record an error for pd_last_error() and return `code`.
 int set_error(int code, const char *msg);

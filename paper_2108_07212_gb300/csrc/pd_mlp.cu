@@ -235,25 +235,27 @@ __global__ void __launch_bounds__(kInferThreads) k_mlp_infer(const MlpRef *__res
     const int tid = threadIdx.x, warp = tid >> 5, wg = warp >> 2;
     const int lrow = tid & 127;           // = 32 (warp % 4) + lane: the TMEM lane of the thread
     const int row = wk.y + lrow;
-    if (warp == 0) tc::tmem_alloc(&tmem_base, 128);
     if (tid == 0) tc::mbar_init(&mbar, 1);
     static_assert(IN == 8 * kInferGroups, "one 8-column piece of the input row per warpgroup");
     float *sX = reinterpret_cast<float *>(sm + 88 * 1024);   // input rows in FP32, 128 x 32 (16 KB)
     {
-        // every load first: the row's input columns 8 wg .. 8 wg + 7 and the
-        // thread's pieces of the three weight matrices; then the stores
+        // every load first: the thread's pieces of the three weight matrices
+        // (while the kernel that writes the inputs may still run), then the
+        // row's input columns 8 wg .. 8 wg + 7; then the stores
         WeightStage<IN, HID, kInferThreads> w1;
         WeightStage<HID, HID, kInferThreads> w2;
         WeightStage<HID, OUT, kInferThreads> w3;
+        w1.load(static_cast<const __nv_bfloat16 *>(r.W1), tid);
+        w2.load(static_cast<const __nv_bfloat16 *>(r.W2), tid);
+        w3.load(static_cast<const __nv_bfloat16 *>(r.W3), tid);
+        tc::grid_dep_wait();
+        if (warp == 0) tc::tmem_alloc(&tmem_base, 128);
         float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
         if (row < B) {
             const float4 *src = reinterpret_cast<const float4 *>(X + (size_t)row * IN + 8 * wg);
             x0 = src[0];
             x1 = src[1];
         }
-        w1.load(static_cast<const __nv_bfloat16 *>(r.W1), tid);
-        w2.load(static_cast<const __nv_bfloat16 *>(r.W2), tid);
-        w3.load(static_cast<const __nv_bfloat16 *>(r.W3), tid);
         const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
         __align__(16) __nv_bfloat16 xb[8];
 #pragma unroll
@@ -270,6 +272,7 @@ __global__ void __launch_bounds__(kInferThreads) k_mlp_infer(const MlpRef *__res
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    tc::grid_dep_launch();
     const uint32_t tmem = tmem_base;
     const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
     constexpr int kCols = HID / kInferGroups;            // hidden columns per warpgroup
@@ -639,14 +642,14 @@ int pd::mlp_ref(pd_mlp *m, MlpRef *out) {
 }
 
 cudaError_t pd::launch_mlp_grouped(const MlpRef *refs, const int4 *work, int n_work, const float *x, float *y,
-                                   int *err, cudaStream_t s) {
+                                   int *err, cudaStream_t s, bool pdl) {
     if (n_work == 0) return cudaSuccess;
     static_assert(sizeof(MlpRef) == 40, "MlpRef layout");
     static_assert(88 * 1024 + 128 * PD_MLP_IN * 4 <= kFwdSmem, "inference tile and its input rows fit");
     // rows of 32 floats: 16-byte aligned when the arrays are
     if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) return cudaErrorMisalignedAddress;
-    pd::mlp::k_mlp_infer<<<n_work, pd::mlp::kInferThreads, kFwdSmem, s>>>(refs, work, x, y, err);
-    return cudaGetLastError();
+    return launch_ex(pd::mlp::k_mlp_infer, dim3(n_work), dim3(pd::mlp::kInferThreads), kFwdSmem, s, pdl, refs, work,
+                     x, y, err);
 }
 
 cudaError_t pd::mlp_init_attributes() {

@@ -40,7 +40,7 @@ __device__ __forceinline__ void clear_rebuild(const DevPtrs &d) {
 
 // Multi-kernel path: one block per BLOCK / LANES nodes.
 template <bool FP32, int LANES>
-__global__ void __launch_bounds__(kBlock, FP32 ? 5 : 4) k_force(DevPtrs d, KParams k, int vin, int update_v) {
+__global__ void __launch_bounds__(kBlock, FP32 ? (LANES == 1 ? 8 : 5) : 4) k_force(DevPtrs d, KParams k, int vin, int update_v) {
     clear_rebuild(d);
     force_block<FP32, false, LANES, kBlock>(d, k, blockIdx.x * (kBlock / LANES), vin, update_v);
 }
@@ -230,8 +230,10 @@ __device__ __forceinline__ int block_scan1(int &v, int *sm) {
     return sm[32];
 }
 
-// All phases of nsteps time steps in one cooperative launch:
+// One time step of the persistent kernel, all phases:
 //   A  displacement update, positions, rebuild test       (Algorithm 1)
+//      (FP32 split: taken by the previous step's velocity update instead,
+//      except in the first step of a launch that finds no valid prediction)
 //   when some node moved kSkinTrigger * skin since the last rebuild:
 //     R1 bucket counts
 //     R2 per-block sums of the bucket counts
@@ -239,88 +241,125 @@ __device__ __forceinline__ int block_scan1(int &v, int *sm) {
 //     R4 counting-sort scatter of the node indices
 //     R5 candidate lists
 //   E  forces, acceleration and velocity update
-// Bucket counts are zero on entry and on exit.
+// s_cur_u / s_cur_pq hold this step's current displacement and positions
+// (parity vin ^ 1).  Bucket counts are zero on entry and on exit.  False when a
+// grid barrier gave up (the kernel then returns).
 template <bool FP32, int LANES, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_persistent(DevPtrs d, KParams k, int vin, int nsteps) {
-    __shared__ int sm[33];
-    __shared__ long long s_step;
-    // wait test: the withheld block never arrives, so the others' barrier waits run out
-    if ((int)blockIdx.x == k.withhold_block) return;
+__device__ __forceinline__ bool persistent_step(const DevPtrs &d, const KParams &k, int vin, int st, int nsteps,
+                                                bool predicted, int *sm, long long &s_step) {
     const int nthreads = gridDim.x * BLOCK;
     const int gtid = blockIdx.x * BLOCK + threadIdx.x;
     const unsigned T = k.T;
     const unsigned slice = (T + gridDim.x - 1) / gridDim.x;
     const unsigned lo = min(T, blockIdx.x * slice), hi = min(T, lo + slice);
-    for (int st = 0; st < nsteps; ++st) {
-        // A (the step counter's load is issued first, so that its latency
-        // overlaps the displacement update of block 0's nodes)
-        const long long s = (blockIdx.x == 0 && threadIdx.x == 0) ? __ldcg(d.step) + 1 : 0;
-        if (st == 0) prefetch_force_inputs(d, k, gtid, nthreads);
+    // A (the step counter's load is issued first, so that its latency
+    // overlaps the displacement update of block 0's nodes)
+    const long long s = (blockIdx.x == 0 && threadIdx.x == 0) ? __ldcg(d.step) + 1 : 0;
+    if (st == 0) prefetch_force_inputs(d, k, gtid, nthreads);
+    if (!predicted) {
         bool need = false;
         for (int i = gtid; i < k.N; i += nthreads) need |= predict_node<true>(d, k, i, vin, 1);
         if (__any_sync(0xffffffffu, need) && (threadIdx.x & 31) == 0) *(volatile int *)d.rebuild = 1;
-        if (blockIdx.x == 0) {
-            if (threadIdx.x == 0) {
-                *d.step = s;
-                *d.t_now = (double)s * k.dt;
-                s_step = s;
+    }
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) {
+            *d.step = s;
+            *d.t_now = (double)s * k.dt;
+            s_step = s;
+            if constexpr (FP32) {
+                // the previous velocity update's rebuild test becomes this step's
+                // flag (no block reads the flag before the barrier below)
+                if (predicted && *(volatile int *)d.rebuild_next) *(volatile int *)d.rebuild = 1;
+                *(volatile int *)d.rebuild_next = 0;
             }
-            __syncthreads();
-            wall_cells(d, k, (double)s_step * k.dt);
         }
-        if (!grid_barrier(d, k.bar_spins)) return;
-        if (__ldcg(d.rebuild)) {
-            // R1
-            for (int i = gtid; i < k.N; i += nthreads) bin_node<true>(d, k, i);
-            if (!grid_barrier(d, k.bar_spins)) return;
-            // R2
-            int part = 0;
-            for (unsigned b = lo + threadIdx.x; b < hi; b += BLOCK) part += __ldcg(&d.count[b]);
-            part = block_sum<BLOCK>(part, sm);
-            if (threadIdx.x == 0) d.blocksums[blockIdx.x] = part;
-            if (!grid_barrier(d, k.bar_spins)) return;
-            // R3
-            int off = 0;
-            for (int b = threadIdx.x; b < (int)blockIdx.x; b += BLOCK) off += __ldcg(&d.blocksums[b]);
-            off = block_sum<BLOCK>(off, sm);
-            for (unsigned b0 = lo; b0 < hi; b0 += BLOCK) {
-                const unsigned b = b0 + threadIdx.x;
-                int c = (b < hi) ? __ldcg(&d.count[b]) : 0;
-                if (b < hi) d.count[b] = 0;
-                const int tot = block_scan1<BLOCK>(c, sm);
-                if (b < hi) {
-                    d.start[b] = off + c;
-                    d.cursor[b] = off + c;
-                }
-                off += tot;
+        __syncthreads();
+        wall_cells(d, k, (double)s_step * k.dt);
+    }
+    if (!grid_barrier(d, k.bar_spins)) return false;
+    if (__ldcg(d.rebuild)) {
+        // R1
+        for (int i = gtid; i < k.N; i += nthreads) bin_node<true>(d, k, i);
+        if (!grid_barrier(d, k.bar_spins)) return false;
+        // R2
+        int part = 0;
+        for (unsigned b = lo + threadIdx.x; b < hi; b += BLOCK) part += __ldcg(&d.count[b]);
+        part = block_sum<BLOCK>(part, sm);
+        if (threadIdx.x == 0) d.blocksums[blockIdx.x] = part;
+        if (!grid_barrier(d, k.bar_spins)) return false;
+        // R3
+        int off = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += BLOCK) off += __ldcg(&d.blocksums[b]);
+        off = block_sum<BLOCK>(off, sm);
+        for (unsigned b0 = lo; b0 < hi; b0 += BLOCK) {
+            const unsigned b = b0 + threadIdx.x;
+            int c = (b < hi) ? __ldcg(&d.count[b]) : 0;
+            if (b < hi) d.count[b] = 0;
+            const int tot = block_scan1<BLOCK>(c, sm);
+            if (b < hi) {
+                d.start[b] = off + c;
+                d.cursor[b] = off + c;
             }
-            if (gtid == 0) d.start[T] = k.N;
-            if (!grid_barrier(d, k.bar_spins)) return;
-            // R4
-            for (int i = gtid; i < k.N; i += nthreads) scatter_node<true>(d, k, i);
-            if (!grid_barrier(d, k.bar_spins)) return;
-            // R5 (every block has read the flag: clear it for the next step)
-            if (gtid == 0) {
-                *d.rebuild = 0;
-                atomicAdd(&d.status[PD_STATUS_REBUILDS], 1);
-            }
-            for (int i = gtid; i < k.N; i += nthreads) build_list_node<true>(d, k, i);
-            if (!grid_barrier(d, k.bar_spins)) return;
+            off += tot;
         }
-        // E
-        if (k.split) {
-            const long long total = (((long long)LANES * k.N + 31) / 32) * 32;
-            for (long long t = gtid; t < total; t += nthreads) sums_node<FP32, true, LANES>(d, k, (int)(t / LANES), (int)(t % LANES), vin);
-            if (!grid_barrier(d, k.bar_spins)) return;
-            for (int i = gtid; i < k.N; i += nthreads) epilogue_node<FP32, true>(d, k, i, vin, 1);
-        } else {
-            for (int node0 = blockIdx.x * (BLOCK / LANES); node0 < k.N; node0 += gridDim.x * (BLOCK / LANES))
-                force_block<FP32, true, LANES, BLOCK>(d, k, node0, vin, 1);
+        if (gtid == 0) d.start[T] = k.N;
+        if (!grid_barrier(d, k.bar_spins)) return false;
+        // R4
+        for (int i = gtid; i < k.N; i += nthreads) scatter_node<true>(d, k, i);
+        if (!grid_barrier(d, k.bar_spins)) return false;
+        // R5 (every block has read the flag: clear it for the next step)
+        if (gtid == 0) {
+            *d.rebuild = 0;
+            atomicAdd(&d.status[PD_STATUS_REBUILDS], 1);
         }
-        // the end of the launch orders the last step before whatever follows
-        if (st + 1 < nsteps && !grid_barrier(d, k.bar_spins)) return;
+        for (int i = gtid; i < k.N; i += nthreads) build_list_node<true>(d, k, i);
+        if (!grid_barrier(d, k.bar_spins)) return false;
+    }
+    // E
+    if (k.split) {
+        const long long total = (((long long)LANES * k.N + 31) / 32) * 32;
+        for (long long t = gtid; t < total; t += nthreads) sums_node<FP32, true, LANES>(d, k, (int)(t / LANES), (int)(t % LANES), vin);
+        if (!grid_barrier(d, k.bar_spins)) return false;
+        for (int i = gtid; i < k.N; i += nthreads) epilogue_node<FP32, true>(d, k, i, vin, 1);
+    } else {
+        for (int node0 = blockIdx.x * (BLOCK / LANES); node0 < k.N; node0 += gridDim.x * (BLOCK / LANES))
+            force_block<FP32, true, LANES, BLOCK>(d, k, node0, vin, 1);
+    }
+    // the end of the launch orders the last step before whatever follows
+    return st + 1 >= nsteps || grid_barrier(d, k.bar_spins);
+}
+
+// nsteps time steps in one cooperative launch, phases separated by bounded
+// grid barriers.  Every step reads its current displacement and positions
+// through s_cur_u / s_cur_pq, the buffers of its parity (the FP32 split keeps
+// two of each; the FP64 path one).
+// (FP32 split, one thread per node: capped at 64 registers, eight blocks of 128
+// per SM, as the lane-sum kernel of the graph path; the phases that need more
+// spill a few hundred bytes, which costs less than the halved occupancy.  Two
+// or more threads per node, and the FP64 path: capped at 128 registers, four
+// blocks of 128.)
+template <bool FP32, int LANES, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, (FP32 && LANES == 1 ? 1024 : 512) / BLOCK)
+    k_persistent(DevPtrs d, KParams k, int vin, int nsteps) {
+    __shared__ int sm[33];
+    __shared__ long long s_step;
+    // wait test: the withheld block never arrives, so the others' barrier waits run out
+    if ((int)blockIdx.x == k.withhold_block) return;
+    // read by every thread before the first grid barrier; written only after it
+    const bool pred0 = FP32 && *(volatile int *)d.pred_ok != 0;
+    for (int st = 0; st < nsteps; ++st) {
+        if (threadIdx.x == 0) {
+            s_cur_u = d.ub[vin ^ 1];
+            s_cur_pq = d.pqb[vin ^ 1];
+        }
+        __syncthreads();
+        const bool predicted = FP32 && (st > 0 || pred0);
+        if (!persistent_step<FP32, LANES, BLOCK>(d, k, vin, st, nsteps, predicted, sm, s_step)) return;
         vin ^= 1;
     }
+    // the next launch may skip its first update phase (the end of this launch
+    // orders every node's prediction before it)
+    if (FP32 && blockIdx.x == 0 && threadIdx.x == 0) *(volatile int *)d.pred_ok = 1;
 }
 
 template <bool FP32, int LANES, int BLOCK>
@@ -346,18 +385,19 @@ cudaError_t launch_persistent_cfg(const DevPtrs &d, const KParams &k, int vin, i
     return cudaLaunchKernelEx(&cfg, kern, d, k, vin, nsteps);
 }
 
+// The persistent kernels of one precision and one thread count per node (both
+// block sizes), each instantiated in a translation unit of its own
+// (pd_persist.cu, compiled once per pair) so that they build in parallel.
+template <bool FP32, int LANES>
+cudaError_t launch_persistent_lanes(const DevPtrs &d, const KParams &k, int vin, int nsteps, int block,
+                                    cudaStream_t s);
+
 template <bool FP32>
 cudaError_t launch_persistent_impl(const DevPtrs &d, const KParams &k, int vin, int nsteps, int block, cudaStream_t s) {
-    if (block == 256) {
-        if (k.lanes == 8) return launch_persistent_cfg<FP32, 8, 256>(d, k, vin, nsteps, s);
-        if (k.lanes == 4) return launch_persistent_cfg<FP32, 4, 256>(d, k, vin, nsteps, s);
-        if (k.lanes == 2) return launch_persistent_cfg<FP32, 2, 256>(d, k, vin, nsteps, s);
-        return launch_persistent_cfg<FP32, 1, 256>(d, k, vin, nsteps, s);
-    }
-    if (k.lanes == 8) return launch_persistent_cfg<FP32, 8, 128>(d, k, vin, nsteps, s);
-    if (k.lanes == 4) return launch_persistent_cfg<FP32, 4, 128>(d, k, vin, nsteps, s);
-    if (k.lanes == 2) return launch_persistent_cfg<FP32, 2, 128>(d, k, vin, nsteps, s);
-    return launch_persistent_cfg<FP32, 1, 128>(d, k, vin, nsteps, s);
+    if (k.lanes == 8) return launch_persistent_lanes<FP32, 8>(d, k, vin, nsteps, block, s);
+    if (k.lanes == 4) return launch_persistent_lanes<FP32, 4>(d, k, vin, nsteps, block, s);
+    if (k.lanes == 2) return launch_persistent_lanes<FP32, 2>(d, k, vin, nsteps, block, s);
+    return launch_persistent_lanes<FP32, 1>(d, k, vin, nsteps, block, s);
 }
 
 }  // namespace pd

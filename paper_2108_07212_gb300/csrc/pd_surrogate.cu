@@ -113,6 +113,7 @@ __device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, f
 // offset h (lattice index - lattice centroid) are applied in float-float.
 __global__ void __launch_bounds__(kSurThreads) k_sur_frame(DevPtrs d, KParams k, int all_templated) {
     __shared__ float frame[6];
+    tc::grid_dep_launch();     // the projection may begin staging its basis chunks
     const int g = blockIdx.x;
     const int t = d.g_tmpl[g];
     if (t < 0 || (!all_templated && !d.sur_active[g])) return;
@@ -332,7 +333,6 @@ __global__ void __launch_bounds__(128) k_sur_project_tc(DevPtrs d, KParams k) {
     const int slot0 = d.tmpl_slot[t], Gt = d.tmpl_slot[t + 1] - slot0;
     const int rows2 = 2 * (d.tmpl_node[t + 1] - d.tmpl_node[t]);
     const int rp = tmpl_rows_pad(d, t);
-    if (warp == 0) tc::tmem_alloc(&tmem_base, 32);
     if (tid == 0) tc::mbar_init(&mbar, 1);
     // B (the basis chunk, mode-major, 16-byte pieces) and A (local deformation
     // rows of the tile's grains, zero outside) staged with their loads in flight
@@ -359,6 +359,9 @@ __global__ void __launch_bounds__(128) k_sur_project_tc(DevPtrs d, KParams k) {
             if (!d.sur_active[g]) g = -1;
         }
         const float *w = g >= 0 ? reinterpret_cast<const float *>(d.sur_w) + 2 * (size_t)d.g_start[g] : nullptr;
+        // the frame kernel's deformation rows are read only after it has finished
+        tc::grid_dep_wait();
+        if (warp == 0) tc::tmem_alloc(&tmem_base, 32);
         constexpr int kLoadBatch = 16;                   // pairs per batch: four batches per chunk
         static_assert(KC % (2 * kLoadBatch) == 0, "chunk must hold whole batches");
 #pragma unroll 1
@@ -389,6 +392,7 @@ __global__ void __launch_bounds__(128) k_sur_project_tc(DevPtrs d, KParams k) {
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    tc::grid_dep_launch();
     const uint32_t tmem = tmem_base;
     if (tid == 0) {
         split_mma(tmem, sAh, sAl, sBh, sBl, MR, NM, KC, tc::idesc_bf16(MR, NM));
@@ -423,10 +427,12 @@ __global__ void __launch_bounds__(128) k_sur_project_tc(DevPtrs d, KParams k) {
 __global__ void k_sur_reduce(DevPtrs d, KParams k) {
     const int row = blockIdx.x;                  // network row
     const int m = threadIdx.x;
+    tc::grid_dep_launch();                       // the networks may begin staging their weights
     if (m >= k.n_modes) return;
     const int g = d.slot_grain[row];
     const int t = d.g_tmpl[g];
     const int nch = tmpl_rows_pad(d, t) / kSurChunk;
+    tc::grid_dep_wait();                         // the projection's partials
     // eight partials in flight at a time, added in chunk order
     constexpr int kBatch = 8;
     float v = 0.f;
@@ -457,7 +463,6 @@ __global__ void __launch_bounds__(kExpThreads) k_sur_expand_tc(DevPtrs d, KParam
     const int M = k.n_modes;
     const int slot0 = d.tmpl_slot[t], Gt = d.tmpl_slot[t + 1] - slot0;
     const int rows2 = 2 * (d.tmpl_node[t + 1] - d.tmpl_node[t]);
-    if (warp == 0) tc::tmem_alloc(&tmem_base, NR);
     if (tid == 0) tc::mbar_init(&mbar, 1);
     const int s = s0 + lrow;
     int g = -1;
@@ -481,11 +486,6 @@ __global__ void __launch_bounds__(kExpThreads) k_sur_expand_tc(DevPtrs d, KParam
         float yv[kPer];
         uint4 vh[nb], vl[nb];
 #pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const int kk = kPer * wg + q;
-            yv[q] = (y && kk < M) ? y[kk] : 0.f;
-        }
-#pragma unroll
         for (int q = 0; q < nb; ++q) {
             const int e = tid + q * kExpThreads, r = e / (KM / 8), k8 = (e % (KM / 8)) * 8;
             vh[q] = vl[q] = make_uint4(0, 0, 0, 0);
@@ -493,6 +493,14 @@ __global__ void __launch_bounds__(kExpThreads) k_sur_expand_tc(DevPtrs d, KParam
                 vh[q] = *reinterpret_cast<const uint4 *>(bh + (size_t)r * M + k8);
                 vl[q] = *reinterpret_cast<const uint4 *>(bl + (size_t)r * M + k8);
             }
+        }
+        // the network outputs only after the networks have finished
+        tc::grid_dep_wait();
+        if (warp == 0) tc::tmem_alloc(&tmem_base, NR);
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int kk = kPer * wg + q;
+            yv[q] = (y && kk < M) ? y[kk] : 0.f;
         }
 #pragma unroll
         for (int q = 0; q < kPer; q += 2) {
@@ -513,6 +521,7 @@ __global__ void __launch_bounds__(kExpThreads) k_sur_expand_tc(DevPtrs d, KParam
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    tc::grid_dep_launch();
     const uint32_t tmem = tmem_base;
     if (tid == 0) {
         split_mma(tmem, sAh, sAl, sBh, sBl, MR, NR, KM, tc::idesc_bf16(MR, NR));
@@ -679,22 +688,19 @@ cudaError_t sur_init_attributes() {
     return cudaFuncSetAttribute(k_sur_expand_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kExpSmem);
 }
 
-cudaError_t launch_sur_project_tc(const DevPtrs &d, const KParams &k, cudaStream_t s) {
+cudaError_t launch_sur_project_tc(const DevPtrs &d, const KParams &k, cudaStream_t s, bool pdl) {
     if (k.n_proj_work == 0) return cudaSuccess;
-    k_sur_project_tc<<<k.n_proj_work, 128, kProjSmem, s>>>(d, k);
-    return cudaGetLastError();
+    return launch_ex(k_sur_project_tc, dim3(k.n_proj_work), dim3(128), kProjSmem, s, pdl, d, k);
 }
 
-cudaError_t launch_sur_reduce(const DevPtrs &d, const KParams &k, cudaStream_t s) {
+cudaError_t launch_sur_reduce(const DevPtrs &d, const KParams &k, cudaStream_t s, bool pdl) {
     if (k.n_rows == 0) return cudaSuccess;
-    k_sur_reduce<<<k.n_rows, 32, 0, s>>>(d, k);
-    return cudaGetLastError();
+    return launch_ex(k_sur_reduce, dim3(k.n_rows), dim3(32), 0, s, pdl, d, k);
 }
 
-cudaError_t launch_sur_expand_tc(const DevPtrs &d, const KParams &k, cudaStream_t s) {
+cudaError_t launch_sur_expand_tc(const DevPtrs &d, const KParams &k, cudaStream_t s, bool pdl) {
     if (k.n_exp_work == 0) return cudaSuccess;
-    k_sur_expand_tc<<<k.n_exp_work, kExpThreads, kExpSmem, s>>>(d, k);
-    return cudaGetLastError();
+    return launch_ex(k_sur_expand_tc, dim3(k.n_exp_work), dim3(kExpThreads), kExpSmem, s, pdl, d, k);
 }
 
 cudaError_t launch_sur_judge(const DevPtrs &d, const KParams &k, cudaStream_t s) {

@@ -36,6 +36,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
     return false;
 }
 
+// ---- programmatic dependent launch ------------------------------------------------
+// A kernel launched with programmatic stream serialisation may begin while the
+// previous kernel of its stream is still running.  grid_dep_wait() returns once
+// that kernel has completed and its writes are visible (at once for a kernel
+// launched without the attribute); a kernel must neither write global memory
+// nor read its predecessor's results before it.  grid_dep_launch() lets the
+// next kernel of the stream begin early.  Kernels that allocate tensor memory
+// allocate it only after grid_dep_wait() and call grid_dep_launch() only once
+// their own columns are held, so a waiting dependent never holds columns that
+// its predecessor still has to allocate.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---- tensor memory ------------------------------------------------------------
 
 // Warp-wide: allocate ncols TMEM columns (power of two >= 32); the TMEM

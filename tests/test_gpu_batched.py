@@ -96,6 +96,37 @@ def test_persistent_kernel_reproduces_kernel_graph(prec, lanes, block, modes):
         assert st[B.STATUS_REBUILDS] == a.status()[1][B.STATUS_REBUILDS]
 
 
+@pytest.mark.parametrize("field", ["DISP", "VEL", "ACC"])
+def test_state_written_between_persistent_launches_replaces_the_prediction(field):
+    """The FP32-split persistent kernel forms the next step's displacement and
+    positions in its velocity update, and the next launch starts from them.  A
+    state written between two launches must replace that prediction: the run
+    then equals a kernel-graph run given the same writes (a stale prediction
+    would differ by the size of the change)."""
+    w = I.merge_aggregates(_parts())
+    a = _sim(w, B.PD_FP32_SPLIT)
+    b = _sim(w, B.PD_FP32_SPLIT)
+    a.set_path(2, 1, 128)
+    b.set_path(1, 1, 256)
+    for k in (1, 16, 5):                     # single steps and a chunk: odd parity at the write
+        a.step(k)
+        b.step(k)
+    val = a.get(field)
+    assert np.linalg.norm(val - b.get(field)) <= 1e-9 * np.linalg.norm(val)
+    changed = val + 1e-3 * np.abs(val).max() * np.sin(np.arange(val.size)).reshape(val.shape)
+    for sim in (a, b):
+        sim.set(field, changed)
+    for k in (1, 16, 3):
+        a.step(k)
+        b.step(k)
+    ua, ub = a.get("DISP"), b.get("DISP")
+    assert np.linalg.norm(ua - ub) <= 1e-9 * np.linalg.norm(ua)
+    assert np.array_equal(a.get("BROKEN"), b.get("BROKEN"))
+    assert int(b.get("STEP")[0]) == 42
+    rc, st = b.status()
+    assert rc == B.PD_OK and st[4] == 0
+
+
 def _colliding_disks():
     """Two disks in oblique contact (damping and friction act every step)."""
     w = I.two_disks(Gc=0.5)
