@@ -39,6 +39,8 @@ METRIC = "node-steps/s and bond evals/s vs plain FP64 GPU path at stated error; 
 # directed bond the column and the FP64 reference length (12 B)
 BYTES_PER_NODE_FP64 = 112
 BYTES_PER_BOND_FP64 = 12
+# the FP64 displacement update: X, u, v and a read (64 B), u and p written (32 B)
+BYTES_UPDATE_FP64 = 96
 # GB300 FP64 pipe: 2 lanes per SM per cycle on 152 SMs; a warp instruction on
 # the FP64 pipe occupies it for 32 / 2 = 16 SM cycles whatever its active lanes
 FP64_LANES_PER_SM_CYCLE = 2
@@ -49,9 +51,26 @@ N_SM = 152
 # the epilogue reads the force total (8 B), the FP64 v (16 B), the FP32 a (8 B), grain (4 B) and
 # the hash-grid cell of the wall test (8 B) and writes v and a (24 B).  120 B per node and no
 # per-bond stream (nodes whose lattice row has a gap read CSR columns instead, 4 B per bond, not
-# counted).
+# counted).  The fused force phase (one kernel, the force total stays on chip) reads the same
+# inputs once: 100 B per node.
 BYTES_PER_NODE_FP32 = 120
+BYTES_PER_NODE_FP32_FUSED = 100
 BYTES_PER_BOND_FP32 = 0
+# the FP32-split displacement update as a phase of its own: X + shift, u, v, the FP32 a and the
+# rebuild reference read, u and pq written (104 B); inside the persistent kernel's velocity update,
+# where v and a are in registers: X + shift, u and the rebuild reference read, u and pq written (80 B)
+BYTES_UPDATE_FP32 = 104
+BYTES_UPDATE_FP32_FUSED = 80
+
+
+def fp32_bytes_per_node(mode: int, whole: bool) -> int:
+    """Algorithmic bytes per node of the FP32-split force phase of path `mode`
+    (pd_set_path: bit 0 persistent, bit 1 split force phase), or of its whole
+    step; the candidate-list rebuild runs only in some steps and is not counted."""
+    force = BYTES_PER_NODE_FP32 if (mode >> 1) & 1 else BYTES_PER_NODE_FP32_FUSED
+    if not whole:
+        return force
+    return force + (BYTES_UPDATE_FP32_FUSED if mode & 1 else BYTES_UPDATE_FP32)
 B_STATUS_REBUILDS = 5    # status slot counting the contact candidate-list rebuilds
 
 
@@ -355,11 +374,9 @@ def _timed_steps(sim, stream, flush, steps, warmup, torch):
 # workload legs at the sizes where HBM, not launch latency, bounds the step
 # (500-grain compaction, 64-aggregate ensemble, 2000-grain surrogate settling)
 
-# algorithmic bytes of one whole FP32-split time step per node (displacement
-# update 104 B: X + shift, u, v, the FP32 a and the rebuild reference read, u
-# and pq written; force phase 120 B); the candidate-list rebuild runs only in
-# some steps and is not counted
-BYTES_PER_NODE_STEP_FP32 = 224
+# the largest whole-step model (separate update phase, split force phase): the
+# workload size above which the inputs exceed L2 many times over
+BYTES_PER_NODE_STEP_FP32_MAX = BYTES_UPDATE_FP32 + BYTES_PER_NODE_FP32
 
 
 # DRAM bytes (read + write) per launch of the force-phase kernels, per workload,
@@ -373,14 +390,15 @@ BYTES_PER_NODE_STEP_FP32 = 224
 # hold while the kernel sources hash to TRAFFIC_DIGEST; otherwise, or for a
 # kernel not captured, traffic is null.
 TRAFFIC = {
-    "ensemble64": {"k_persistent<1, 1, 256>": 1356252672, "k_persistent<0, 1, 256>": 3345293312,
-                   "k_sums<1, 1>": 356891136, "k_epilogue<1>": 422153216,
-                   "k_sums<0, 1>": 2234032896, "k_epilogue<0>": 585353216},
-    "compaction500": {"k_persistent<1, 1, 256>": 58068224, "k_persistent<0, 1, 256>": 243394560,
-                      "k_sums<1, 1>": 23608064, "k_epilogue<1>": 23024896,
-                      "k_sums<0, 1>": 170549504, "k_epilogue<0>": 31461632},
+    "ensemble64": {"k_persistent<1, 1, 256>": 1197521408, "k_persistent<0, 1, 256>": 3345149184,
+                   "k_sums<1, 1>": 356157440, "k_epilogue<1>": 421333504,
+                   "k_sums<0, 1>": 2233688064, "k_epilogue<0>": 584942080},
+    "compaction500": {"k_persistent<1, 1, 256>": 69125120, "k_persistent<0, 1, 256>": 244200192,
+                      "k_persistent<1, 1, 128>": 69231872, "k_persistent<0, 1, 128>": 243573760,
+                      "k_sums<1, 1>": 23606272, "k_epilogue<1>": 23026432,
+                      "k_sums<0, 1>": 170530304, "k_epilogue<0>": 31458304},
 }
-TRAFFIC_DIGEST = "b6a5174d2a706f9631b53f2815d08100682cba80"
+TRAFFIC_DIGEST = "3eaabcaec80714d775abe6f88440fbab625b5f6f"
 TRAFFIC_SOURCES = ("pd_device.cuh", "pd_step.cuh", "pd_step32.cu", "pd_step64.cu", "pd_persist.cu", "pd_common.cu",
                    "pd_internal.h")
 
@@ -452,10 +470,10 @@ def _force_kernel_ms(sim, n=20):
 
 
 def _roof_fp32(sim, f_ms, hbm, label, path=None, workload=None):
-    """HBM roofline of the FP32-split force group: the force phase (120 B/node)
-    on the kernel-graph paths, the whole step (224 B/node) when the persistent
-    kernel, which runs every phase of the step, is the timed group."""
-    per_node = BYTES_PER_NODE_STEP_FP32 if path and path["mode"] & 1 else BYTES_PER_NODE_FP32
+    """HBM roofline of the FP32-split force group: the force phase on the
+    kernel-graph paths, the whole step when the persistent kernel, which runs
+    every phase of the step, is the timed group (fp32_bytes_per_node)."""
+    per_node = fp32_bytes_per_node(path["mode"], bool(path["mode"] & 1)) if path else BYTES_PER_NODE_FP32
     nbytes = per_node * sim.N + BYTES_PER_BOND_FP32 * sim.n_bonds
     a = nbytes / (f_ms / 1e3) / 1e9
     traffic = force_phase_traffic(path, True, workload) if path and workload else None
@@ -470,10 +488,11 @@ def _roof_fp32(sim, f_ms, hbm, label, path=None, workload=None):
 # profiles/force64_*.md), per workload; they hold while the kernel sources hash
 # to FP64_INST_DIGEST, otherwise the ALU roofline is left unmeasured.
 FP64_INST = {
-    "ensemble64": {"k_sums<0, 1>": 32548167, "k_epilogue<0>": 1674556},
-    "compaction500": {"k_sums<0, 1>": 2492904, "k_epilogue<0>": 130368},
+    "ensemble64": {"k_sums<0, 1>": 32548173, "k_epilogue<0>": 1674592, "k_persistent<0, 1, 256>": 36245494},
+    "compaction500": {"k_sums<0, 1>": 2492904, "k_epilogue<0>": 130368, "k_persistent<0, 1, 256>": 2784267,
+                      "k_persistent<0, 1, 128>": 2784259},
 }
-FP64_INST_DIGEST = "b6a5174d2a706f9631b53f2815d08100682cba80"
+FP64_INST_DIGEST = "3eaabcaec80714d775abe6f88440fbab625b5f6f"
 
 
 def _roof_fp64(sim, f_ms, path, workload, clk, hbm):
@@ -799,7 +818,7 @@ def run_ours(args):
     tuned = {key: pick(sim)}
     if sim64 is not None:
         tuned["fp64"] = pick(sim64)
-    big = sim.N * BYTES_PER_NODE_STEP_FP32 > 512 * 1024 * 1024
+    big = sim.N * BYTES_PER_NODE_STEP_FP32_MAX > 512 * 1024 * 1024
     flush_buf = None if big else torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
     def flush_l2():
@@ -868,7 +887,7 @@ def run_ours(args):
         roof = _roof_fp64(sim, f_ms, tuned["fp64"], args.workload, clk, hbm)
     else:
         whole = bool(tuned["fp32"]["mode"] & 1)          # persistent kernel: one launch for the whole step
-        per_node = BYTES_PER_NODE_STEP_FP32 if whole else BYTES_PER_NODE_FP32
+        per_node = fp32_bytes_per_node(tuned["fp32"]["mode"], whole)
         nbytes = per_node * sim.N + BYTES_PER_BOND_FP32 * sim.n_bonds
         achieved = nbytes / (f_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": _force_kernels(tuned["fp32"]["mode"], True), "achieved": achieved, "peak": hbm,
@@ -881,7 +900,11 @@ def run_ours(args):
                         + "; peak = measured copy bandwidth (of measured)"
                         + ("; the workload is too small to load 152 SMs, so the phase is latency-bound"
                            if sim.N < 100000 else "")}
-    step_bytes = BYTES_PER_NODE_STEP_FP32 * sim.N + BYTES_PER_BOND_FP32 * sim.n_bonds
+    if prec == B.PD_FP64:
+        step_per_node, step_per_bond = BYTES_UPDATE_FP64 + BYTES_PER_NODE_FP64, BYTES_PER_BOND_FP64
+    else:
+        step_per_node, step_per_bond = fp32_bytes_per_node(tuned[key]["mode"], True), BYTES_PER_BOND_FP32
+    step_bytes = step_per_node * sim.N + step_per_bond * sim.n_bonds
     step_s = elapsed / args.steps / world
     line = {
         "metric": METRIC, "value": value, "unit": "node-steps/s", "n_gpus": world, "steps": args.steps,
@@ -903,7 +926,7 @@ def run_ours(args):
         "roofline": roof,
         "step_roofline": {"bound": "hbm", "achieved": step_bytes / step_s / 1e9, "peak": hbm, "unit": "GB/s",
                           "frac": step_bytes / step_s / 1e9 / hbm,
-                          "note": f"whole step: {BYTES_PER_NODE_STEP_FP32} B/node + {BYTES_PER_BOND_FP32} B/bond "
+                          "note": f"whole step: {step_per_node} B/node + {step_per_bond} B/bond "
                                   "(rebuilds not counted) / event-timed step (of measured)"},
         "force_kernel_us": 1e3 * f_ms,
         "list_rebuilds": {"timed_steps": args.steps, key: rebuilds,
