@@ -509,14 +509,16 @@ def _roof_fp64(sim, f_ms, path, workload, clk, hbm):
         [f"k_sums<0, {l}>", f"k_epilogue<0>"] if (m >> 1) & 1 else [f"k_force<0, {l}>"])
     table = FP64_INST.get(workload, {}) if kernel_digest() == FP64_INST_DIGEST else {}
     inst = sum(table[n] for n in names) if all(n in table for n in names) else None
-    nbytes = BYTES_PER_NODE_FP64 * sim.N + BYTES_PER_BOND_FP64 * sim.n_bonds
+    # the persistent kernel is the whole step: the displacement update's bytes too
+    per_node = BYTES_PER_NODE_FP64 + (BYTES_UPDATE_FP64 if m & 1 else 0)
+    nbytes = per_node * sim.N + BYTES_PER_BOND_FP64 * sim.n_bonds
     hbm_a = nbytes / (f_ms / 1e3) / 1e9
     achieved = None if inst is None else 32.0 * inst / (f_ms / 1e3) / 1e12
     return {"bound": "alu", "kernel": _force_kernels(m, False), "achieved": achieved, "peak": peak,
             "unit": "T FP64 lane-ops/s", "frac": None if achieved is None else achieved / peak,
             "traffic": force_phase_traffic(path, False, workload),
             "hbm": {"achieved": hbm_a, "peak": hbm, "unit": "GB/s", "frac": hbm_a / hbm,
-                    "note": f"{BYTES_PER_NODE_FP64} B/node + {BYTES_PER_BOND_FP64} B/bond (of measured)"},
+                    "note": f"{per_node} B/node + {BYTES_PER_BOND_FP64} B/bond (of measured)"},
             "note": f"peak = {N_SM} SMs x {FP64_LANES_PER_SM_CYCLE} FP64 lanes/cycle x {mhz:.0f} MHz (derived); "
                     + ("achieved = 32 x %d FP64-pipe warp instructions (ncu) / mean event time %.1f us"
                        % (inst, f_ms * 1e3) if inst is not None else
