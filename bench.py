@@ -573,10 +573,12 @@ def leg_compaction(B, I, dev, stream, torch, hbm, clk, steps=200):
     return out
 
 
-def leg_surrogate(B, I, SU, dev, stream, torch, steps=200):
+def leg_surrogate(B, I, SU, dev, stream, torch, steps=200, profile_steps=0):
     """2000 grains (~2e6 nodes, h=R/23), FP32 split: surrogate (networks trained
     on snapshots of a small aggregate with the same templates) vs the plain
-    FP32 and FP64 paths."""
+    FP32 and FP64 paths.  With profile_steps, only that many surrogate steps
+    (not judge steps) run on path mode 6 (no conditional graph node, which ncu
+    cannot trace) between cudaProfilerStart/Stop, and the leg ends there."""
     w = I.surrogate_settling()
     # training snapshots: 60 grains of the same shapes and h/R, each thrown at
     # 1 m/s in a seeded random direction so that collisions load them
@@ -609,6 +611,15 @@ def leg_surrogate(B, I, SU, dev, stream, torch, steps=200):
         S.surrogate_set_mlp(t, nets[-1])
     t_train = time.perf_counter() - t0
     S.surrogate_enable(True)
+    if profile_steps:
+        S.set_path(6, 1, 128)
+        S.step(3)                                    # steps 1-3; the judge runs every 50th
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        S.step(profile_steps)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return {"profiled_surrogate_steps": profile_steps, "nodes": int(S.N), "status": int(S.status()[0])}
     S.autotune()
     with torch.cuda.stream(stream):
         P = B.Simulation(w, precision=B.PD_FP32_SPLIT, device=dev, stream=stream)
@@ -677,6 +688,15 @@ def _surrogate_landing(B, I, SU, dev, stream, torch, T, data, steps, advance=120
         nets.append(B.MLP(max_batch=int(counts[t]), stream=stream, params=params))
         S.surrogate_set_mlp(t, nets[-1])
     S.surrogate_enable(True)
+    if profile_steps:
+        S.set_path(6, 1, 128)
+        S.step(3)                                    # steps 1-3; the judge runs every 50th
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        S.step(profile_steps)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return {"profiled_surrogate_steps": profile_steps, "nodes": int(S.N), "status": int(S.status()[0])}
     S.autotune()
     with torch.cuda.stream(stream):
         P = B.Simulation(w, precision=B.PD_FP32_SPLIT, device=dev, stream=stream)
@@ -994,12 +1014,30 @@ def main():
     ap.add_argument("--advance", type=int, default=None,
                     help="untimed steps before the timed window (default: per workload; the window starts mid-run)")
     ap.add_argument("--path", default="", help="fix the step path: MODE,LANES[,BLOCK] (pd_set_path) instead of autotuning")
+    ap.add_argument("--sur-profile", type=int, default=0, metavar="N",
+                    help="only run N surrogate steps of the 2000-grain settling between cudaProfilerStart/Stop "
+                         "(for an ncu launch list) and print their status")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.sur_profile:
+        return run_surrogate_profile(args.sur_profile)
     return run_ours(args)
+
+
+def run_surrogate_profile(n):
+    import torch
+    from paper_2108_07212_gb300 import binding as B
+    from paper_2108_07212_gb300 import inputs as I
+    from paper_2108_07212_gb300 import surrogate as SU
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    out = leg_surrogate(B, I, SU, dev, stream, torch, profile_steps=n)
+    print(json.dumps(out))
+    return 0 if out["status"] == 0 else 1
 
 
 if __name__ == "__main__":

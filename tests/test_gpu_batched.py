@@ -127,6 +127,30 @@ def test_state_written_between_persistent_launches_replaces_the_prediction(field
     assert rc == B.PD_OK and st[4] == 0
 
 
+def test_switching_between_persistent_kernel_and_graph_mid_run():
+    """The persistent kernel leaves the next step's displacement predicted
+    (FP32 split); a kernel-graph step recomputes it, and a later persistent
+    launch must not take a prediction the graph steps made stale.  One context
+    switching paths between calls follows one that stays on the graph."""
+    w = I.merge_aggregates(_parts())
+    a = _sim(w, B.PD_FP32_SPLIT)
+    b = _sim(w, B.PD_FP32_SPLIT)
+    a.set_path(2, 1, 128)
+    for k, path in ((3, (1, 1, 256)), (16, (2, 1, 128)), (5, (1, 1, 128)), (16, (0, 1, 128)),
+                    (7, (3, 1, 256)), (1, (2, 1, 128)), (9, (1, 1, 256))):
+        b.set_path(*path)
+        a.step(k)
+        b.step(k)
+    ua, ub = a.get("DISP"), b.get("DISP")
+    assert np.linalg.norm(ua - ub) <= 1e-9 * np.linalg.norm(ua)
+    va, vb = a.get("VEL"), b.get("VEL")
+    assert np.linalg.norm(va - vb) <= 1e-9 * np.linalg.norm(va)
+    assert np.array_equal(a.get("BROKEN"), b.get("BROKEN"))
+    assert int(b.get("STEP")[0]) == 57
+    rc, st = b.status()
+    assert rc == B.PD_OK and st[4] == 0
+
+
 def _colliding_disks():
     """Two disks in oblique contact (damping and friction act every step)."""
     w = I.two_disks(Gc=0.5)
