@@ -1288,6 +1288,16 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
     constexpr int kBondBatch = 4;
     if (stencil && !(sur && !judge)) {
         const uint32_t mask = st.x;
+        // the intact bonds by stencil offset: the broken-bond bits follow the
+        // order of the node's bonds (the rank of the offset among the stencil
+        // bits), so each set bit clears the stencil bit of that rank (a node
+        // seldom has a broken bond: the loop is skipped)
+        uint32_t alive = mask;
+        for (uint32_t wb = w0; wb; wb &= wb - 1u) {
+            uint32_t m = mask;
+            for (int t = __ffs(wb) - 1; t > 0; --t) m &= m - 1u;
+            alive &= ~(m & (0u - m));
+        }
         const int Dm2 = (int)(short)(st.y & 0xFFFFu), Dm1 = (int)(short)(st.y >> 16);
         const int Dp1 = (int)(short)(st.z & 0xFFFFu), Dp2 = (int)(short)(st.z >> 16);
         constexpr int kPerLane = (24 + LANES - 1) / LANES;
@@ -1302,8 +1312,7 @@ __device__ __forceinline__ void force_node32(const DevPtrs &d, const KParams &k,
                 const int o = (m0 + m) * LANES + lane;
                 const int dj = stn_dj(o), di = stn_di(o);
                 const int D = dj == -2 ? Dm2 : (dj == -1 ? Dm1 : (dj == 0 ? 0 : (dj == 1 ? Dp1 : Dp2)));
-                const int kk = __popc(mask & ((1u << o) - 1u));
-                live[m] = (m0 + m) < kPerLane && o < 24 && ((mask >> o) & 1u) && !((w0 >> kk) & 1u);
+                live[m] = (m0 + m) < kPerLane && o < 24 && ((alive >> o) & 1u);
                 qb[m] = ldm<PERSIST>(&cur_pq<PERSIST>(d)[live[m] ? ii + di + D : ii]);
             }
 #pragma unroll
