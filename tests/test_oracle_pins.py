@@ -567,6 +567,56 @@ def test_energy_is_conserved_in_undamped_elastic_impact():
     assert worst < 2e-3
 
 
+def test_many_grain_collision_keeps_momentum_angular_momentum_and_energy():
+    """Six grains (three hexagons, three disks, random orientations) driven
+    together at 5 m/s in free space: no walls within reach, no gravity,
+    friction, damping or breaking.  Every bond force acts along its deformed
+    bond (eq:pmb) and every contact force along the line of centres (Sec. 4.1),
+    so all forces are central pair forces.  Velocity Verlet then keeps the total
+    linear momentum and the total angular momentum sum m (x cross v) to rounding
+    (each half step leaves x cross v unchanged for central forces), and
+    KE + bond + contact energy to its O(dt^2) error (Sec. 4.3).  A bond force
+    along the reference direction, or a contact force off the line of centres,
+    would make the angular momentum drift.  Every grain takes part in the
+    collisions."""
+    w = I.free_grains(shapes=("hexagon", "disk"), n_per_shape=3, R=1e-3, h_ratio=8, dt=2e-8)
+    w.params.update(friction=0.0, damping_ratio=0.0, Gc=1e9, k_bulk=5.0e5, wall_lo=(-1.0, -1.0),
+                    wall_hi=(1.0, 1.0))
+    c = w.grain_geom[:, :2].copy()
+    d = c.mean(axis=0) - c
+    w.grain_geom[:, 4:6] = 5.0 * d / np.linalg.norm(d, axis=1)[:, None]
+    P = O.OracleProblem.from_workload(w).init_accel()
+    m = P.prm[O.P_RHO] * P.V
+
+    def invariants():
+        x = P.X + P.u
+        mom = (m[:, None] * P.v).sum(axis=0)
+        ang = (m * (x[:, 0] * P.v[:, 1] - x[:, 1] * P.v[:, 0])).sum()
+        dg = P.diagnostics()
+        return mom, ang, dg["KE"] + dg["E_bond"] + dg["E_contact"], dg["E_contact"]
+
+    mom0, ang0, E0, _ = invariants()
+    x0 = P.X + P.u
+    mom_scale = (m * np.abs(P.v).sum(axis=1)).sum()
+    ang_scale = (m * np.hypot(x0[:, 0], x0[:, 1]) * np.hypot(P.v[:, 0], P.v[:, 1])).sum()
+    grain_v0 = np.array([P.v[P.grain == g].mean(axis=0) for g in range(w.n_grains)])
+    d_mom = d_ang = d_E = max_contact = 0.0
+    for _ in range(160):
+        P.run(100)
+        mom, ang, En, Ec = invariants()
+        d_mom = max(d_mom, np.abs(mom - mom0).max() / mom_scale)
+        d_ang = max(d_ang, abs(ang - ang0) / ang_scale)
+        d_E = max(d_E, abs(En - E0) / E0)
+        max_contact = max(max_contact, Ec / E0)
+    grain_v = np.array([P.v[P.grain == g].mean(axis=0) for g in range(w.n_grains)])
+    assert np.all(np.linalg.norm(grain_v - grain_v0, axis=1) > 0.3 * 5.0)
+    assert max_contact > 5e-3
+    assert not P.broken.any()
+    assert d_mom < 1e-12
+    assert d_ang < 1e-12
+    assert d_E < 1e-3
+
+
 def test_grid_search_matches_brute_force():
     """The oracle's cell grid returns the same S^nbr as the O(N^2) definition."""
     P = _colliding_disks(mu=0.5, rd=0.8, Gc=50.0)
