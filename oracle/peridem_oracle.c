@@ -30,8 +30,10 @@
  *     node past a wall is treated as touching it (d clamped to 0, counted);
  *     only adjacent (perpendicular) walls form corners.
  *
- * parity unpinned: multi-grain trajectories (only the GPU comparison checks
- * them; the paper gives no trajectory data).
+ * multi-grain trajectories are pinned by their invariants only (linear and
+ * angular momentum to rounding, energy to the velocity-Verlet error); parity
+ * unpinned beyond them (only the GPU comparison checks the exact trajectory;
+ * the paper gives no trajectory data).
  */
 #include <math.h>
 #include <stdlib.h>
