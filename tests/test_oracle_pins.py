@@ -69,6 +69,22 @@ def test_contact_stiffness_scaling():
     assert O.contact_stiffness(1e7, 2e-4) / k0 == pytest.approx(1.0 / 32.0, rel=1e-14)
 
 
+def test_contact_stiffness_is_the_3d_bond_micromodulus_over_the_horizon():
+    """Reading of Sec. 4.1: K_n = 18 k / (pi eps^5) is the micromodulus of the
+    3D bond-based model, c = 18 k / (pi eps^4), per unit length of the horizon
+    (the contact law is linear in the overlap R_c - |d|, a length, where the
+    bond law is linear in the stretch).  Here c comes from its own definition:
+    under a uniform dilation with stretch s every bond of the 3D horizon stores
+    (1/2) c s^2 |xi| (half per node), and the energy density, integrated by
+    quadrature over the ball, must equal the bulk energy (1/2) k (3 s)^2.  A
+    transcription with another constant (9/pi, 18 pi, ...) fails."""
+    k, eps, s = 1.3e6, 2.7e-4, 1e-3
+    # energy density per unit c: the integral over the ball of (1/4) s^2 |xi|
+    per_c = quad(lambda r: 0.25 * s * s * r * 4.0 * math.pi * r * r, 0.0, eps)[0]
+    c = 0.5 * k * (3.0 * s) ** 2 / per_c
+    assert O.contact_stiffness(k, eps) * eps == pytest.approx(c, rel=1e-12)
+
+
 # ---------------------------------------------------------------------------
 # bond law
 
