@@ -945,8 +945,9 @@ def run_ours(args):
         "force_kernel_us": 1e3 * f_ms,
         "list_rebuilds": {"timed_steps": args.steps, key: rebuilds,
                           **({"fp64": rebuilds64} if sim64 is not None else {}),
-                          "note": "contact candidate lists (radius R_c + 0.1 R_c) rebuilt in a conditional graph "
-                                  "node only when a node has moved 0.45 skin"},
+                          "note": "contact candidate lists (radius R_c + 0.1 R_c) rebuilt only when a node has "
+                                  "moved 0.45 skin (inside the persistent kernel, or in a conditional graph node "
+                                  "on the kernel-graph path)"},
         "cpu_baseline": None,
         "e2e": e2e,
         "clocks": clk,
