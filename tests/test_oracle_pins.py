@@ -239,6 +239,38 @@ def test_normal_contact_is_linear_spring_half_period():
     assert v_out == pytest.approx(-0.1, rel=1e-4)
 
 
+def test_friction_is_continuous_at_the_stick_slip_switch():
+    """Sec. 4.2 with the small-velocity sticking: the tangential contact force
+    is linear in the relative tangential velocity below the switch (sticking)
+    and of constant size above it (sliding), and the two branches meet where
+    they switch: the threshold is chosen so that the law is continuous.  The
+    force opposes the relative tangential velocity.  Located from the oracle's
+    own outputs (the slope of the small-speed branch and the size of the
+    large-speed one), not from the threshold formula."""
+    h, Rc = 1e-4, 0.95e-4
+    P, *_ = _two_grain_nodes(Rc, h, gap=-0.3 * Rc, v_rel=0.0, mu=0.5, dt=1e-8)   # overlapping: F_r > 0
+
+    def tangential(vt):
+        P.v[:] = 0.0
+        P.v[0, 1] = vt                          # normal along x, tangential along y
+        F, parts = P.forces()
+        return parts[2][0, 1]                   # contact part on node 0, tangential component
+
+    small, big = 1e-9, 10.0
+    f1, f2 = tangential(small), tangential(2 * small)
+    assert f1 < 0 and f2 == pytest.approx(2 * f1, rel=1e-9)            # sticking: linear, opposing
+    g1, g2 = tangential(big), tangential(2 * big)
+    assert g1 < 0 and g2 == pytest.approx(g1, rel=1e-12)               # sliding: constant size
+    assert tangential(-big) == pytest.approx(-g1, rel=1e-12)           # opposing either way
+    v_switch = g1 / (f1 / small)                 # where the linear branch reaches the sliding size
+    for side in (1.0 - 1e-6, 1.0 + 1e-6):
+        assert tangential(side * v_switch) == pytest.approx(g1, rel=2e-6)
+    # and the switch is there, not elsewhere: linear just below, constant well above
+    assert tangential(0.9 * v_switch) == pytest.approx(0.9 * g1, rel=1e-9)
+    assert tangential(1.5 * v_switch) == pytest.approx(g1, rel=1e-12)
+    assert abs(tangential(0.5 * v_switch)) == pytest.approx(0.5 * abs(g1), rel=1e-9)
+
+
 def test_normal_damping_restitution_matches_kelvin_voigt():
     """Sec. 4.3: spring K_n V^2 + dashpot beta_d V^2 with beta_d = 2 r_d sqrt(K_n rho / V)
     on reduced mass rho V / 2 has damping ratio zeta = sqrt(2) r_d and restitution
