@@ -121,6 +121,36 @@ def test_bond_force_is_minus_energy_gradient(micro):
     assert np.allclose(parts[0, 0], -parts[0, 1], rtol=0, atol=1e-15 * np.abs(parts[0, 0]).max())
 
 
+def test_rigid_motion_gives_zero_bond_force():
+    """eq:pmb depends on the deformed bond length only: a rigid rotation plus
+    translation of every grain (non-convex plus, holed annulus, drop) leaves
+    every stretch and so every bond force at zero, to rounding, while a uniform
+    dilation of 1e-3 gives forces of its own size.  A law that used displacement
+    differences instead of lengths would give forces of the rotation's size."""
+    w = I.free_grains(shapes=("plus", "annulus", "drop"), n_per_shape=1, h_ratio=10)
+    P = O.OracleProblem.from_workload(w)
+    rng = np.random.default_rng(4)
+    u_rigid = np.zeros_like(P.X)
+    u_dil = np.zeros_like(P.X)
+    for g in range(w.n_grains):
+        m = P.grain == g
+        c = P.X[m].mean(axis=0)
+        th = rng.uniform(0.3, 2.5)
+        R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+        r = P.X[m] - c
+        u_rigid[m] = r @ R.T - r + rng.uniform(-1e-3, 1e-3, 2)
+        u_dil[m] = 1e-3 * r
+    P.u[:] = u_dil
+    _, parts = P.forces()
+    scale = np.abs(parts[0]).max()
+    assert scale > 0
+    P.u[:] = u_rigid
+    F, parts = P.forces()
+    assert np.abs(parts[0]).max() <= 1e-9 * scale
+    assert np.abs(F).max() <= 1e-9 * scale
+    assert not P.broken.any()
+
+
 def test_bond_breaks_beyond_critical_stretch_and_stays_broken():
     """Sec. 3.1: |s| > s0 breaks the bond; it remains broken afterwards; also in
     compression (absolute value)."""
